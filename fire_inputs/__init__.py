@@ -1,0 +1,129 @@
+"""Seeded synthetic inputs shared by the oracle-side tests and the GPU-side
+tests/bench.  This module only builds atom positions and boxes (lattices,
+vacancies, strain, voids, random displacements) and holds the workload
+constants; it contains none of the relaxation method's arithmetic.
+
+Recipes (one numpy PCG64 generator per config, seeded as stated):
+  lj_fcc_vacancy      FCC 4x4x4 cells, a = 1.5874 sigma, 256 sites, one site
+                      removed at random, uniform +-0.1 sigma displacement per
+                      Cartesian component.
+  rgl_vacancy_box     FCC n^3 cells of Cu, a = 3.615 A, a fraction (or count)
+                      of sites removed at random, Gaussian displacements
+                      (std 0.05 A per component).
+  rgl_void_box        FCC 63^3 cells, box and positions stretched by 2 % along
+                      x, sites within 20 A of the box centre removed, Gaussian
+                      displacements (std 0.02 A).
+  rgl_batch           512 periodic FCC Cu boxes with n ~ U{3..12} cells per
+                      edge, 1-3 vacancies each, Gaussian 0.05 A displacements.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+# Workload constants ---------------------------------------------------------
+# Lennard-Jones (reduced units), cut and energy-shifted at 2.5 sigma.
+LJ = dict(eps=1.0, sigma=1.0, rc=2.5)
+LJ_A = 1.5874          # FCC lattice constant in sigma
+LJ_MASS = 1.0
+LJ_DT = 0.005          # dt_start in tau
+
+# Second-moment (RGL) Cu: A, xi in eV, r0, rs, rc in Angstrom.
+RGL_CU = dict(A=0.0855, xi=1.224, p=10.96, q=2.278, r0=2.556, rs=4.5, rc=5.0)
+CU_A = 3.615           # FCC lattice constant, Angstrom
+CU_MASS_AMU = 63.546
+# metal units: a[A/ps^2] = F[eV/A] / m[amu] * 9648.533212...
+EV_PER_A_AMU_TO_A_PS2 = 1.602176634e-19 / (1e-10 * 1.66053906660e-27) * 1e-14
+CU_MASS = CU_MASS_AMU / EV_PER_A_AMU_TO_A_PS2   # eV ps^2 / A^2, so that a = F / m
+CU_DT = 0.001          # ps
+
+FIRE_TABLE1 = dict(tmax=10.0, tmin=0.02, dtgrow=1.1, dtshrink=0.5, alpha0=0.25,
+                   alphashrink=0.99, delaystep=20, vdfmax=2000, halfstepback=True,
+                   initialdelay=True)
+
+_FCC_BASIS = np.array([[0.0, 0.0, 0.0], [0.5, 0.5, 0.0], [0.5, 0.0, 0.5], [0.0, 0.5, 0.5]])
+
+
+@dataclass
+class Config:
+    """One relaxation problem: positions (N x 3, float64), box lengths, flags."""
+    name: str
+    x: np.ndarray
+    box: np.ndarray
+    periodic: tuple = (1, 1, 1)
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n(self) -> int:
+        return int(self.x.shape[0])
+
+
+def fcc_sites(nx: int, ny: int, nz: int, a: float) -> np.ndarray:
+    """FCC sites of an nx x ny x nz block of cubic cells, cell-major order."""
+    ix, iy, iz = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="ij")
+    corners = np.stack([ix, iy, iz], axis=-1).reshape(-1, 1, 3).astype(np.float64)
+    return ((corners + _FCC_BASIS[None]) * a).reshape(-1, 3)
+
+
+def lj_fcc_vacancy(seed: int = 1, ncell: int = 4, a: float = LJ_A, amp: float = 0.1) -> Config:
+    rng = np.random.Generator(np.random.PCG64(seed))
+    x = fcc_sites(ncell, ncell, ncell, a)
+    vac = int(rng.integers(len(x)))
+    x = np.delete(x, vac, axis=0)
+    x = x + rng.uniform(-amp, amp, size=x.shape)
+    box = np.full(3, ncell * a)
+    return Config("lj_fcc4_vac1", x, box, meta=dict(vacancies=[vac], ncell=ncell))
+
+
+def rgl_vacancy_box(ncell: int = 20, seed: int = 2, vac_frac: float | None = 0.01,
+                    n_vac: int | None = None, sigma: float = 0.05, a: float = CU_A) -> Config:
+    rng = np.random.Generator(np.random.PCG64(seed))
+    sites = fcc_sites(ncell, ncell, ncell, a)
+    k = int(n_vac) if n_vac is not None else int(round(vac_frac * len(sites)))
+    vac = np.sort(rng.choice(len(sites), size=k, replace=False)) if k > 0 else np.zeros(0, int)
+    keep = np.ones(len(sites), bool)
+    keep[vac] = False
+    lattice = sites[keep]
+    x = lattice + rng.normal(0.0, sigma, size=lattice.shape)
+    box = np.full(3, ncell * a)
+    return Config(f"rgl_cu{ncell}_vac{k}", x, box,
+                  meta=dict(vacancies=vac.tolist(), vacancy_sites=sites[vac], lattice=lattice,
+                            ncell=ncell))
+
+
+def rgl_void_box(ncell: int = 63, seed: int = 3, strain: float = 0.02, void_r: float = 20.0,
+                 sigma: float = 0.02, a: float = CU_A) -> Config:
+    rng = np.random.Generator(np.random.PCG64(seed))
+    sites = fcc_sites(ncell, ncell, ncell, a)
+    box = np.full(3, ncell * a)
+    sites[:, 0] *= 1.0 + strain
+    box[0] *= 1.0 + strain
+    centre = 0.5 * box
+    keep = np.sum((sites - centre) ** 2, axis=1) >= void_r * void_r
+    lattice = sites[keep]
+    x = lattice + rng.normal(0.0, sigma, size=lattice.shape)
+    return Config(f"rgl_cu{ncell}_strain{strain:g}_void{void_r:g}", x, box,
+                  meta=dict(removed=int((~keep).sum()), ncell=ncell))
+
+
+def rgl_batch(n_sys: int = 512, seed: int = 4, nmin: int = 3, nmax: int = 12,
+              sigma: float = 0.05, a: float = CU_A):
+    """List of independent periodic Cu boxes of uneven sizes."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for s in range(n_sys):
+        n = int(rng.integers(nmin, nmax + 1))
+        k = int(rng.integers(1, 4))
+        sites = fcc_sites(n, n, n, a)
+        vac = rng.choice(len(sites), size=k, replace=False)
+        keep = np.ones(len(sites), bool)
+        keep[vac] = False
+        x = sites[keep] + rng.normal(0.0, sigma, size=(int(keep.sum()), 3))
+        out.append(Config(f"batch{s}_cu{n}_vac{k}", x, np.full(3, n * a),
+                          meta=dict(ncell=n, vacancies=np.sort(vac).tolist())))
+    return out
+
+
+def perfect_fcc(ncell: int, a: float) -> Config:
+    return Config(f"fcc{ncell}", fcc_sites(ncell, ncell, ncell, a), np.full(3, ncell * a))

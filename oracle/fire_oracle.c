@@ -1,0 +1,547 @@
+/*
+ * FIRE 2.0 reference oracle -- TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow, deliberately unoptimised FP64 CPU implementation of what the
+ * GPU library computes.  Only the test-suite, the smoke check and the
+ * benchmark's CPU-baseline leg may load it.  It shares no code, header, table
+ * or constant with the CUDA path.
+ *
+ * What it follows (Guenole et al., "Assessment and optimization of the fast
+ * inertial relaxation engine (FIRE) for energy minimization in atomistic
+ * simulations and its implementation in LAMMPS"):
+ *   - Sec. 2.1, Eq. 1:   F = -grad E; the power P = F . v decides uphill motion.
+ *   - Algorithm 2:       FIRE 2.0 control loop (counters N_P>0 / N_P<=0, dt and
+ *                        alpha adaptation, N_P<=0 cap, initial delay, dt_min
+ *                        guard, half step back on P <= 0).
+ *   - Algorithm 4:       semi-implicit (symplectic) Euler with the mixing
+ *                        placed just before the position update (Sec. 3.3).
+ *   - Table 1:           parameter names and defaults.
+ *   - Sec. 3.4:          f2norm and per-atom maximum force stopping norms.
+ *   - Sec. 5.2:          EAM = pair term + embedding functional of the local
+ *                        density; here in the second-moment (RGL) form.
+ *
+ * Readings where the paper is silent or garbled (all shared with the GPU path,
+ * listed again in the design notes):
+ *   - Algorithm 4 writes the mixing line with v(t); it is applied to the kicked
+ *     velocity, with the norm of the kicked velocity (as Algorithms 5 and 6 do).
+ *   - Mixing only when P > 0 (after P <= 0, v is zeroed, so the kicked v is
+ *     parallel to F and the mixing would be a no-op).
+ *   - The half step back uses the dt after the shrink (literal order of Alg. 2).
+ *   - The force is not re-evaluated after the half step back.
+ *   - dt is left unchanged (not clamped) when dt*f_dec < dt_min; alpha is
+ *     still reset.
+ *   - Convergence is tested once before the first iteration and after each
+ *     force evaluation.
+ *
+ * Force routines are O(N^2) all-pairs with the minimum-image convention
+ * (FORCE_BRUTE).  A cell-grid variant (FORCE_CELLS) visits the same candidate
+ * pairs in the same ascending-j order, so its results are bit-identical to
+ * the all-pairs routine; tests check that on boxes where both run.
+ *
+ * Parity status per function:
+ *   ora_energy_forces   pinned (finite differences, sum F = 0, zero force on
+ *                       perfect lattices, closed-form cohesive energies).
+ *   ora_fire2           pinned (hand-traced iterations of Alg. 2 + Alg. 4 on
+ *                       quadratic wells, MAXVDOTF and dt_min traces, LJ dimer
+ *                       bond length).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+enum { POT_LJ = 0, POT_RGL = 1, POT_QUAD = 2 };
+enum { FORCE_BRUTE = 0, FORCE_CELLS = 1 };
+enum { STOP_FTOL = 0, STOP_MAXITER = 1, STOP_MAXVDOTF = 2 };
+enum { NORM_MAX_ATOM = 0, NORM_TWO = 1, NORM_INF = 2 };
+enum { INT_EULER_IMPLICIT = 0 };
+
+typedef struct {
+    int64_t n;          /* number of atoms */
+    double box[3];      /* orthorhombic box lengths */
+    int32_t periodic[3];
+    double mass;        /* uniform mass, in units where a = F / mass */
+} ora_sys;
+
+typedef struct {
+    int32_t kind;
+    /* Lennard-Jones 12-6, energy shifted to zero at rc */
+    double eps, sigma, rc_lj;
+    /* second-moment (RGL) EAM with a quintic taper on [rs, rc) */
+    double A, xi, p, q, r0, rs, rc;
+    /* quadratic test well E = 1/2 sum_d k_d (x_d - x0_d)^2 (control-flow tests) */
+    const double *quad_k, *quad_x0;
+} ora_pot;
+
+typedef struct {
+    double dt_start, tmax, tmin, dtgrow, dtshrink, alpha0, alphashrink;
+    int32_t delaystep, vdfmax, halfstepback, initialdelay, integrator, norm;
+} ora_params;
+
+typedef struct {
+    double energy;
+    int64_t iterations, force_evals;
+    int32_t stop, pad;
+    double fmax_atom, f2norm, finf, dt_final, alpha_final;
+} ora_result;
+
+typedef struct {
+    int64_t i, npos, nneg;
+    double P, dt, alpha, energy, fnorm;
+} ora_trace;
+
+/* ------------------------------------------------------------------------ */
+/* Geometry                                                                  */
+
+static double min_image(double d, double L, int periodic) {
+    if (periodic) d -= L * nearbyint(d / L);
+    return d;
+}
+
+static double pot_cutoff(const ora_pot *pot) {
+    return pot->kind == POT_LJ ? pot->rc_lj : pot->rc;
+}
+
+/* Quintic taper S(r) = 1 - 10 t^3 + 15 t^4 - 6 t^5, t = (r - rs)/(rc - rs):
+ * 1 below rs, 0 at and above rc, C2-continuous at both ends. */
+static void taper(const ora_pot *pot, double r, double *S, double *dS) {
+    if (r <= pot->rs) { *S = 1.0; *dS = 0.0; return; }
+    if (r >= pot->rc) { *S = 0.0; *dS = 0.0; return; }
+    double w = pot->rc - pot->rs;
+    double t = (r - pot->rs) / w;
+    *S = 1.0 - 10.0 * t * t * t + 15.0 * t * t * t * t - 6.0 * t * t * t * t * t;
+    *dS = (-30.0 * t * t + 60.0 * t * t * t - 30.0 * t * t * t * t) / w;
+}
+
+/* RGL pair functions of Sec. 5.2's EAM family in second-moment form:
+ *   phi(r) = A exp(-p (r/r0 - 1)) S(r)         (repulsive pair term)
+ *   g(r)   = xi^2 exp(-2q (r/r0 - 1)) S(r)     (density contribution)   */
+static void rgl_pair(const ora_pot *pot, double r, double *phi, double *dphi,
+                     double *g, double *dg) {
+    double S, dS;
+    taper(pot, r, &S, &dS);
+    double s = r / pot->r0 - 1.0;
+    double ep = pot->A * exp(-pot->p * s);
+    double eq = pot->xi * pot->xi * exp(-2.0 * pot->q * s);
+    *phi = ep * S;
+    *dphi = ep * (-pot->p / pot->r0 * S + dS);
+    *g = eq * S;
+    *dg = eq * (-2.0 * pot->q / pot->r0 * S + dS);
+}
+
+/* LJ: phi(r) = 4 eps [(sigma/r)^12 - (sigma/r)^6] - phi(rc) for r < rc. */
+static double lj_phi(const ora_pot *pot, double r) {
+    double sr6 = pow(pot->sigma / r, 6.0);
+    return 4.0 * pot->eps * (sr6 * sr6 - sr6);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Candidate-neighbour enumeration.  Both modes yield, for atom i, every j != i
+ * in ascending order; the caller applies the cutoff test itself.             */
+
+typedef struct {
+    int mode;
+    int64_t n;
+    int nc[3];
+    int64_t *cell_start; /* ncell + 1 */
+    int64_t *cell_atoms; /* n, ascending within each cell */
+} ora_grid;
+
+static int cmp_i64(const void *a, const void *b) {
+    int64_t x = *(const int64_t *)a, y = *(const int64_t *)b;
+    return (x > y) - (x < y);
+}
+
+static int64_t cell_coord(double x, double L, int nc) {
+    double u = x / L;
+    u -= floor(u);
+    int64_t c = (int64_t)(u * nc);
+    if (c >= nc) c = nc - 1;
+    if (c < 0) c = 0;
+    return c;
+}
+
+static void grid_build(ora_grid *g, const ora_sys *sys, const double *x, double rc, int mode) {
+    memset(g, 0, sizeof(*g));
+    g->n = sys->n;
+    g->mode = FORCE_BRUTE;
+    if (mode != FORCE_CELLS) return;
+    for (int d = 0; d < 3; ++d) {
+        if (!sys->periodic[d]) return;
+        g->nc[d] = (int)floor(sys->box[d] / rc);
+        if (g->nc[d] < 3) return;
+    }
+    g->mode = FORCE_CELLS;
+    int64_t ncell = (int64_t)g->nc[0] * g->nc[1] * g->nc[2];
+    g->cell_start = (int64_t *)calloc((size_t)ncell + 1, sizeof(int64_t));
+    g->cell_atoms = (int64_t *)malloc((size_t)(sys->n > 0 ? sys->n : 1) * sizeof(int64_t));
+    int64_t *cid = (int64_t *)malloc((size_t)(sys->n > 0 ? sys->n : 1) * sizeof(int64_t));
+    for (int64_t i = 0; i < sys->n; ++i) {
+        int64_t cx = cell_coord(x[3 * i + 0], sys->box[0], g->nc[0]);
+        int64_t cy = cell_coord(x[3 * i + 1], sys->box[1], g->nc[1]);
+        int64_t cz = cell_coord(x[3 * i + 2], sys->box[2], g->nc[2]);
+        cid[i] = (cx * g->nc[1] + cy) * g->nc[2] + cz;
+        g->cell_start[cid[i] + 1]++;
+    }
+    for (int64_t c = 0; c < ncell; ++c) g->cell_start[c + 1] += g->cell_start[c];
+    int64_t *fill = (int64_t *)malloc((size_t)ncell * sizeof(int64_t));
+    memcpy(fill, g->cell_start, (size_t)ncell * sizeof(int64_t));
+    for (int64_t i = 0; i < sys->n; ++i) g->cell_atoms[fill[cid[i]]++] = i;
+    free(fill);
+    free(cid);
+}
+
+static void grid_free(ora_grid *g) {
+    free(g->cell_start);
+    free(g->cell_atoms);
+    memset(g, 0, sizeof(*g));
+}
+
+/* Fills cand[] with candidate j (ascending, j != i); returns the count. */
+static int64_t grid_candidates(const ora_grid *g, const ora_sys *sys, const double *x,
+                               int64_t i, int64_t *cand) {
+    int64_t m = 0;
+    if (g->mode == FORCE_BRUTE) {
+        for (int64_t j = 0; j < g->n; ++j)
+            if (j != i) cand[m++] = j;
+        return m;
+    }
+    int64_t c[3];
+    for (int d = 0; d < 3; ++d) c[d] = cell_coord(x[3 * i + d], sys->box[d], g->nc[d]);
+    for (int dx = -1; dx <= 1; ++dx)
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dz = -1; dz <= 1; ++dz) {
+                int64_t cx = (c[0] + dx + g->nc[0]) % g->nc[0];
+                int64_t cy = (c[1] + dy + g->nc[1]) % g->nc[1];
+                int64_t cz = (c[2] + dz + g->nc[2]) % g->nc[2];
+                int64_t cc = (cx * g->nc[1] + cy) * g->nc[2] + cz;
+                for (int64_t k = g->cell_start[cc]; k < g->cell_start[cc + 1]; ++k)
+                    if (g->cell_atoms[k] != i) cand[m++] = g->cell_atoms[k];
+            }
+    qsort(cand, (size_t)m, sizeof(int64_t), cmp_i64);
+    return m;
+}
+
+static int64_t grid_max_candidates(const ora_grid *g) {
+    if (g->mode == FORCE_BRUTE) return g->n;
+    int64_t ncell = (int64_t)g->nc[0] * g->nc[1] * g->nc[2], mx = 0;
+    for (int64_t c = 0; c < ncell; ++c) {
+        int64_t k = g->cell_start[c + 1] - g->cell_start[c];
+        if (k > mx) mx = k;
+    }
+    return 27 * mx;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Energy and forces.  F = -grad E (Sec. 2.1).                               */
+
+static int check_box(const ora_sys *sys, const ora_pot *pot) {
+    if (sys->n < 0) return -1;
+    if (pot->kind == POT_QUAD) return 0;
+    double rc = pot_cutoff(pot);
+    for (int d = 0; d < 3; ++d)
+        if (sys->periodic[d] && sys->box[d] < 2.0 * rc) return -2;
+    return 0;
+}
+
+/* Evaluates E and (if f != NULL) F for the atoms listed in `which` (or all
+ * atoms when which == NULL).  E is always the total energy. */
+static int energy_forces_impl(const ora_sys *sys, const ora_pot *pot, const double *x,
+                              double *f, double *energy, int mode,
+                              const int64_t *which, int64_t nwhich) {
+    int rc_ok = check_box(sys, pot);
+    if (rc_ok) return rc_ok;
+    const int64_t n = sys->n;
+    if (pot->kind == POT_QUAD) {
+        double e = 0.0;
+        for (int64_t k = 0; k < 3 * n; ++k) {
+            double d = x[k] - pot->quad_x0[k];
+            e += 0.5 * pot->quad_k[k] * d * d;
+            if (f) f[k] = -pot->quad_k[k] * d;
+        }
+        *energy = e;
+        return 0;
+    }
+    const double rc = pot_cutoff(pot), rc2 = rc * rc;
+    ora_grid g;
+    grid_build(&g, sys, x, rc, mode);
+    const int64_t cap = grid_max_candidates(&g) + 1;
+
+    if (pot->kind == POT_LJ) {
+        const double shift = lj_phi(pot, rc);
+        double etot = 0.0;
+        double *ei = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+#pragma omp parallel
+        {
+            int64_t *cand = (int64_t *)malloc((size_t)cap * sizeof(int64_t));
+#pragma omp for schedule(dynamic, 64)
+            for (int64_t i = 0; i < n; ++i) {
+                double fi[3] = {0.0, 0.0, 0.0}, e = 0.0;
+                int64_t m = grid_candidates(&g, sys, x, i, cand);
+                for (int64_t k = 0; k < m; ++k) {
+                    int64_t j = cand[k];
+                    double d[3];
+                    for (int a = 0; a < 3; ++a)
+                        d[a] = min_image(x[3 * i + a] - x[3 * j + a], sys->box[a], sys->periodic[a]);
+                    double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                    if (r2 >= rc2) continue;
+                    double r = sqrt(r2);
+                    e += 0.5 * (lj_phi(pot, r) - shift);
+                    /* -dphi/dr / r = 24 eps [2 (s/r)^12 - (s/r)^6] / r^2 */
+                    double sr6 = pow(pot->sigma / r, 6.0);
+                    double fpair = 24.0 * pot->eps * (2.0 * sr6 * sr6 - sr6) / r2;
+                    for (int a = 0; a < 3; ++a) fi[a] += fpair * d[a];
+                }
+                ei[i] = e;
+                if (f) for (int a = 0; a < 3; ++a) f[3 * i + a] = fi[a];
+            }
+            free(cand);
+        }
+        for (int64_t i = 0; i < n; ++i) etot += ei[i];
+        free(ei);
+        *energy = etot;
+        grid_free(&g);
+        return 0;
+    }
+
+    /* RGL: pass 1 -- density rho_i and repulsive energy per atom. */
+    double *rho = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+    double *erep = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+    double *dF = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+#pragma omp parallel
+    {
+        int64_t *cand = (int64_t *)malloc((size_t)cap * sizeof(int64_t));
+#pragma omp for schedule(dynamic, 64)
+        for (int64_t i = 0; i < n; ++i) {
+            double rh = 0.0, er = 0.0;
+            int64_t m = grid_candidates(&g, sys, x, i, cand);
+            for (int64_t k = 0; k < m; ++k) {
+                int64_t j = cand[k];
+                double d[3];
+                for (int a = 0; a < 3; ++a)
+                    d[a] = min_image(x[3 * i + a] - x[3 * j + a], sys->box[a], sys->periodic[a]);
+                double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                if (r2 >= rc2) continue;
+                double phi, dphi, gg, dg;
+                rgl_pair(pot, sqrt(r2), &phi, &dphi, &gg, &dg);
+                er += phi;
+                rh += gg;
+            }
+            rho[i] = rh;
+            erep[i] = er;
+            /* embedding F(rho) = -sqrt(rho); F'(rho) = -1 / (2 sqrt(rho)).
+             * An atom with rho = 0 has no pair inside rc, so F' is never used. */
+            dF[i] = rh > 0.0 ? -0.5 / sqrt(rh) : 0.0;
+        }
+        free(cand);
+    }
+    double etot = 0.0;
+    for (int64_t i = 0; i < n; ++i) etot += erep[i] - sqrt(rho[i]);
+    *energy = etot;
+
+    /* pass 2 -- forces: F_k = -sum_j [2 phi'(r) + (F'_k + F'_j) g'(r)] (x_k - x_j)/r */
+    if (f) {
+        int64_t cnt = which ? nwhich : n;
+#pragma omp parallel
+        {
+            int64_t *cand = (int64_t *)malloc((size_t)cap * sizeof(int64_t));
+#pragma omp for schedule(dynamic, 64)
+            for (int64_t w = 0; w < cnt; ++w) {
+                int64_t i = which ? which[w] : w;
+                double fi[3] = {0.0, 0.0, 0.0};
+                int64_t m = grid_candidates(&g, sys, x, i, cand);
+                for (int64_t k = 0; k < m; ++k) {
+                    int64_t j = cand[k];
+                    double d[3];
+                    for (int a = 0; a < 3; ++a)
+                        d[a] = min_image(x[3 * i + a] - x[3 * j + a], sys->box[a], sys->periodic[a]);
+                    double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                    if (r2 >= rc2) continue;
+                    double r = sqrt(r2);
+                    double phi, dphi, gg, dg;
+                    rgl_pair(pot, r, &phi, &dphi, &gg, &dg);
+                    double dEdr = 2.0 * dphi + (dF[i] + dF[j]) * dg;
+                    for (int a = 0; a < 3; ++a) fi[a] -= dEdr * d[a] / r;
+                }
+                for (int a = 0; a < 3; ++a) f[3 * w + a] = fi[a];
+            }
+            free(cand);
+        }
+    }
+    free(rho);
+    free(erep);
+    free(dF);
+    grid_free(&g);
+    return 0;
+}
+
+int ora_energy_forces(const ora_sys *sys, const ora_pot *pot, const double *x,
+                      double *f, double *energy, int mode) {
+    return energy_forces_impl(sys, pot, x, f, energy, mode, NULL, 0);
+}
+
+/* Forces of a subset of atoms (rows of f follow `which`), total energy. */
+int ora_energy_forces_subset(const ora_sys *sys, const ora_pot *pot, const double *x,
+                             const int64_t *which, int64_t nwhich, double *f,
+                             double *energy, int mode) {
+    return energy_forces_impl(sys, pot, x, f, energy, mode, which, nwhich);
+}
+
+/* Per-atom densities rho_i (RGL only) -- used by tests on vacancy boxes. */
+int ora_densities(const ora_sys *sys, const ora_pot *pot, const double *x, double *rho) {
+    int rc_ok = check_box(sys, pot);
+    if (rc_ok) return rc_ok;
+    if (pot->kind != POT_RGL) return -1;
+    const double rc2 = pot->rc * pot->rc;
+    for (int64_t i = 0; i < sys->n; ++i) {
+        double rh = 0.0;
+        for (int64_t j = 0; j < sys->n; ++j) {
+            if (j == i) continue;
+            double d[3];
+            for (int a = 0; a < 3; ++a)
+                d[a] = min_image(x[3 * i + a] - x[3 * j + a], sys->box[a], sys->periodic[a]);
+            double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            if (r2 >= rc2) continue;
+            double phi, dphi, gg, dg;
+            rgl_pair(pot, sqrt(r2), &phi, &dphi, &gg, &dg);
+            rh += gg;
+        }
+        rho[i] = rh;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Force norms of Sec. 3.4.                                                   */
+
+static void force_norms(const double *f, int64_t n, double *fmax_atom, double *f2, double *finf) {
+    double m = 0.0, s = 0.0, mi = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        double a2 = f[3 * i] * f[3 * i] + f[3 * i + 1] * f[3 * i + 1] + f[3 * i + 2] * f[3 * i + 2];
+        s += a2;
+        double a = sqrt(a2);
+        if (a > m) m = a;
+        for (int d = 0; d < 3; ++d)
+            if (fabs(f[3 * i + d]) > mi) mi = fabs(f[3 * i + d]);
+    }
+    *fmax_atom = m;
+    *f2 = sqrt(s);
+    *finf = mi;
+}
+
+static double pick_norm(int norm, double fmax_atom, double f2, double finf) {
+    if (norm == NORM_TWO) return f2;
+    if (norm == NORM_INF) return finf;
+    return fmax_atom;
+}
+
+static double dot3n(const double *a, const double *b, int64_t n3) {
+    double s = 0.0;
+    for (int64_t k = 0; k < n3; ++k) s += a[k] * b[k];
+    return s;
+}
+
+/* ------------------------------------------------------------------------ */
+/* FIRE 2.0 (Algorithm 2) with semi-implicit Euler integration (Algorithm 4). */
+
+int ora_fire2(const ora_sys *sys, const ora_pot *pot, const ora_params *par, double *x,
+              double ftol, int64_t maxiter, int mode, ora_result *out,
+              ora_trace *trace, int64_t trace_cap) {
+    if (par->integrator != INT_EULER_IMPLICIT) return -3;
+    if (maxiter < 0 || !(ftol >= 0.0) || !(par->dt_start > 0.0) || !(sys->mass > 0.0)) return -1;
+    const int64_t n = sys->n, n3 = 3 * n;
+    double *v = (double *)calloc((size_t)(n3 > 0 ? n3 : 1), sizeof(double));
+    double *f = (double *)calloc((size_t)(n3 > 0 ? n3 : 1), sizeof(double));
+    double E = 0.0;
+    int rc_ok = ora_energy_forces(sys, pot, x, f, &E, mode);
+    if (rc_ok) { free(v); free(f); return rc_ok; }
+
+    /* initialisation: v = 0, alpha = alpha_start, dt = dt_start, counters 0 */
+    double alpha = par->alpha0, dt = par->dt_start;
+    const double dtmax = par->tmax * par->dt_start, dtmin = par->tmin * par->dt_start;
+    int64_t npos = 0, nneg = 0, evals = 1, iters = 0;
+    int stop = STOP_MAXITER;
+    double fmax_atom, f2, finf;
+    force_norms(f, n, &fmax_atom, &f2, &finf);
+
+    if (pick_norm(par->norm, fmax_atom, f2, finf) < ftol) {
+        stop = STOP_FTOL;
+    } else {
+        for (int64_t i = 1; i <= maxiter; ++i) {
+            double P = dot3n(f, v, n3);
+            if (P > 0.0) {
+                npos += 1;
+                nneg = 0;
+                if (npos > par->delaystep) {
+                    dt = fmin(dt * par->dtgrow, dtmax);
+                    alpha *= par->alphashrink;
+                }
+            } else {
+                npos = 0;
+                nneg += 1;
+                if (nneg > par->vdfmax) { stop = STOP_MAXVDOTF; iters = i - 1; break; }
+                if (!(par->initialdelay && i < par->delaystep)) {
+                    if (dt * par->dtshrink >= dtmin) dt *= par->dtshrink;
+                    alpha = par->alpha0;
+                }
+                if (par->halfstepback)
+                    for (int64_t k = 0; k < n3; ++k) x[k] -= 0.5 * dt * v[k];
+                for (int64_t k = 0; k < n3; ++k) v[k] = 0.0;
+            }
+            /* Algorithm 4: kick, mix (P > 0 only), drift, new force. */
+            for (int64_t k = 0; k < n3; ++k) v[k] += dt * f[k] / sys->mass;
+            if (P > 0.0) {
+                double vn = sqrt(dot3n(v, v, n3)), fn = sqrt(dot3n(f, f, n3));
+                if (fn > 0.0)
+                    for (int64_t k = 0; k < n3; ++k)
+                        v[k] = (1.0 - alpha) * v[k] + alpha * vn * f[k] / fn;
+            }
+            for (int64_t k = 0; k < n3; ++k) x[k] += dt * v[k];
+            rc_ok = ora_energy_forces(sys, pot, x, f, &E, mode);
+            if (rc_ok) { free(v); free(f); return rc_ok; }
+            evals += 1;
+            iters = i;
+            force_norms(f, n, &fmax_atom, &f2, &finf);
+            double fn_conv = pick_norm(par->norm, fmax_atom, f2, finf);
+            if (trace && i - 1 < trace_cap) {
+                ora_trace *t = &trace[i - 1];
+                t->i = i; t->npos = npos; t->nneg = nneg;
+                t->P = P; t->dt = dt; t->alpha = alpha; t->energy = E; t->fnorm = fn_conv;
+            }
+            if (fn_conv < ftol) { stop = STOP_FTOL; break; }
+        }
+    }
+    force_norms(f, n, &fmax_atom, &f2, &finf);
+    out->energy = E;
+    out->iterations = iters;
+    out->force_evals = evals;
+    out->stop = stop;
+    out->pad = 0;
+    out->fmax_atom = fmax_atom;
+    out->f2norm = f2;
+    out->finf = finf;
+    out->dt_final = dt;
+    out->alpha_final = alpha;
+    free(v);
+    free(f);
+    return 0;
+}
+
+void ora_set_threads(int k) {
+#ifdef _OPENMP
+    if (k > 0) omp_set_num_threads(k);
+#else
+    (void)k;
+#endif
+}
+
+int ora_max_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
