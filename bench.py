@@ -1,0 +1,347 @@
+"""Benchmark: FIRE 2.0 relaxation of the ~1M-atom RGL-Cu configuration on one GB300.
+
+Workload (one "step"): relax the 63x63x63-cell FCC Cu box (2 % uniaxial
+strain along x, 20 A void removed at the centre, Gaussian 0.02 A noise,
+997,450 atoms) from its initial configuration until max_i |F_i| < 1e-6 eV/A,
+with FIRE 2.0 (Algorithm 2) + semi-implicit Euler (Algorithm 4), Table 1
+parameters, dt_start = 1 fs, m = 63.546 amu.  The whole relaxation -- list
+builds, both RGL force passes, the FP64 reductions, the dt/alpha control and
+the integration -- runs inside one CUDA graph launch (fire_minimize_dev).
+
+metric: atom-iterations per second (N x FIRE iterations / wall time), higher is
+better; ms_per_step is the time-to-ftol of one relaxation.
+
+`--impl reference` times the FP64 CPU oracle (plain C, OpenMP) on a bounded
+sample of the same workload (a few FIRE iterations of the same box).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import fire_inputs as fi  # noqa: E402
+
+METRIC = "FIRE2 atom-iters/s & time-to-ftol, EAM 1M atoms, 1 GB300; HBM roofline fraction"
+UNIT = "atom-iters/s"
+FTOL = 1e-6
+MAXITER = 200000
+CONFIGS = {
+    "rgl1m": lambda: fi.rgl_void_box(),
+    "rgl32k": lambda: fi.rgl_vacancy_box(ncell=20, seed=2),
+    "lj256": lambda: fi.lj_fcc_vacancy(seed=1),
+}
+# Algorithmic FP64 operations per pair inside the cut-off, counted from the
+# formulas (transcendentals count as one operation each): density pass = 32,
+# force pass = 18, LJ force pass = 24.
+ALG_FLOP_PER_PAIR = {"density": 32, "force": 18, "force_lj": 24}
+# Algorithmic HBM bytes per atom and iteration (x, v read+write, F'(rho)
+# write+read): 112 for RGL, 96 for LJ.
+ALG_BYTES_PER_ATOM_ITER = {"rgl": 112, "lj": 96}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--config", default="rgl1m", choices=sorted(CONFIGS))
+    ap.add_argument("--form", default="fp64", choices=["fp64"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0,
+                    help="target CPU time of the oracle sample")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def potential_for(cfg_name):
+    import paper_1908_02038_gb300 as fg
+    if cfg_name.startswith("lj"):
+        return (fg.Potential(fg.FIRE_POT_LJ, eps=1.0, sigma=1.0, rc_lj=2.5, skin=0.3),
+                fi.LJ_MASS, fi.LJ_DT, 1e-8)
+    return fg.Potential(fg.FIRE_POT_RGL, skin=0.3, **fi.RGL_CU), fi.CU_MASS, fi.CU_DT, FTOL
+
+
+def count_pairs(x, box, rc):
+    """Unordered pairs closer than rc (periodic), for the algorithmic op count."""
+    from scipy.spatial import cKDTree
+    t = cKDTree(np.mod(x, box), boxsize=box)
+    return int((t.count_neighbors(t, rc) - len(x)) // 2)
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def read_traffic(kernel):
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if its
+    recorded source hash matches the current kernel sources; else None."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    src = os.path.join(ROOT, "paper_1908_02038_gb300", "csrc", "fire2_device.cuh")
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    for line in open(path):
+        parts = line.split()
+        if len(parts) >= 4 and parts[0] == kernel and parts[1] == h:
+            return float(parts[3])
+    return None
+
+
+def run_gpu(args):
+    import torch
+
+    import paper_1908_02038_gb300 as fg
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    fg.build()
+    fg.load_library()
+
+    cfg = CONFIGS[args.config]()
+    pot, mass, dt, ftol = potential_for(args.config)
+    n = cfg.n
+    dev = torch.device("cuda", local)
+    x0 = torch.tensor(cfg.x, dtype=torch.float64, device=dev)
+    work = torch.empty_like(x0)
+    stream = torch.cuda.current_stream()
+    h = fg.FireHandle(n, mass, pot, dt_start=dt)
+
+    def step():
+        work.copy_(x0)
+        return h.minimize_dev(work, cfg.box, ftol, MAXITER, stream)
+
+    for _ in range(args.warmup):
+        r = step()
+    iters_total, launches, results = 0, 0, []
+    barrier = (lambda: __import__("torch.distributed").distributed.barrier()) if world > 1 else (lambda: None)
+    barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            r = step()
+            results.append(r.as_dict())
+            iters_total += r.iterations
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        it = torch.tensor([iters_total], device=dev, dtype=torch.float64)
+        dist.all_reduce(it)
+        iters_total_all = float(it.item())
+    else:
+        iters_total_all = float(iters_total)
+    value = n * iters_total_all / (ms * 1e-3)
+    is_rgl = not args.config.startswith("lj")
+    rc = pot.rc if is_rgl else pot.rc_lj
+    cell_mode = all(np.floor(np.asarray(cfg.box) / (rc + pot.skin)) >= 3)
+    build_k = 5 if cell_mode else 1
+    force_k = 3 if is_rgl else 1
+    # kernels per iteration: update, list-build chain (gated), force passes,
+    # reduce, control; per call: prepare + build + forces + reduce + control + finalize
+    per_iter = 1 + build_k + force_k + 2
+    for rr in results:
+        launches += (1 + build_k + force_k + 2 + 1) + per_iter * rr["iterations"]
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"{cfg.name} ({n} atoms), FIRE2 + semi-implicit Euler to "
+                                  f"max|F_i| < {ftol:g}",
+                      "atoms": n, "ftol": ftol, "form": args.form, "skin": pot.skin,
+                      "iterations_per_step": [rr["iterations"] for rr in results],
+                      "final_fmax_atom": [rr["fmax_atom"] for rr in results],
+                      "final_energy_per_atom": [rr["energy"] / n for rr in results],
+                      "nbr_builds": [rr["nbr_builds"] for rr in results],
+                      "l2": "inputs larger than L2 (working set > 1 GB at 1M atoms)"},
+           "gpu_launches": launches,
+           "clocks": clk.summary()}
+
+    # per-stage device times (CUDA events) for the roofline of the dominant kernel
+    stages = h.profile_stages(cfg.x, cfg.box, reps=5)
+    dom = "density" if is_rgl and stages["density"] >= stages["force"] else "force"
+    pairs = count_pairs(cfg.x, cfg.box, np.sqrt(pot.rc ** 2 if is_rgl else pot.rc_lj ** 2))
+    key = dom if is_rgl else "force_lj"
+    flop = ALG_FLOP_PER_PAIR[key] * pairs
+    achieved = flop / (stages[dom] * 1e-3)
+    peak64 = fg.fire_diag_fma_peak(0)
+    kname = {"density": "k_density", "force": "k_force_rgl" if is_rgl else "k_force_lj"}[dom]
+    out["roofline"] = {"bound": "alu", "kernel": kname, "achieved": achieved / 1e12,
+                       "peak": peak64 / 1e12, "unit": "TFLOP/s",
+                       "frac": achieved / peak64, "traffic": read_traffic(kname),
+                       "peak_source": "measured FP64 FMA issue rate (fire_diag_fma_peak)",
+                       "stage_ms": stages, "pairs_within_rc": pairs}
+    # HBM roofline of the whole iteration, as the metric asks
+    alg_b = ALG_BYTES_PER_ATOM_ITER["rgl" if is_rgl else "lj"]
+    hbm = None
+    try:
+        hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
+    except Exception:
+        hbm = 6800.0
+    out["hbm_roofline"] = {"alg_bytes_per_atom_iter": alg_b,
+                           "achieved_gbs": value * alg_b / 1e9, "peak_gbs": hbm,
+                           "frac": value * alg_b / 1e9 / hbm}
+
+    # end to end through the host-pointer API (H2D of positions, D2H of result)
+    if not args.no_e2e:
+        xh = np.empty_like(cfg.x)
+        t_e2e, it_e2e = 0.0, 0
+        for k in range(max(1, args.steps)):
+            xh[...] = cfg.x
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = h.minimize(xh, cfg.box, ftol, MAXITER)
+            t_e2e += time.perf_counter() - t0
+            it_e2e += r.iterations
+        out["e2e"] = {"value": n * it_e2e / t_e2e, "unit": UNIT,
+                      "h2d_bytes_per_step": int(cfg.x.nbytes) + 1024,
+                      "d2h_bytes_per_step": int(cfg.x.nbytes) + 1024}
+    h.close()
+    if rank == 0:
+        out["cpu_baseline"] = cpu_baseline(cfg, args) if world == 1 else None
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def cpu_baseline(cfg, args, target_s=None):
+    """The FP64 oracle as it stands, on the host cores, on a few FIRE iterations
+    of the same configuration (cell-grid force mode)."""
+    import oracle
+    target_s = target_s or args.cpu_seconds
+    opot = (oracle.Potential("lj", eps=1.0, sigma=1.0, rc_lj=2.5) if cfg.name.startswith("lj")
+            else oracle.Potential("rgl", **fi.RGL_CU))
+    mass = fi.LJ_MASS if cfg.name.startswith("lj") else fi.CU_MASS
+    dt = fi.LJ_DT if cfg.name.startswith("lj") else fi.CU_DT
+    params = oracle.Params(dt_start=dt)
+    mode = oracle.FORCE_CELLS
+    k = 1
+    t0 = time.perf_counter()
+    _, r, _ = oracle.fire2(cfg.x, cfg.box, opot, params, mass, 0.0, k, mode=mode)
+    t1 = time.perf_counter() - t0
+    # the first call includes one extra (initial) force evaluation per call
+    k = max(1, int(target_s / max(t1 / 2.0, 1e-3)) - 1)
+    t0 = time.perf_counter()
+    _, r, _ = oracle.fire2(cfg.x, cfg.box, opot, params, mass, 0.0, k, mode=mode)
+    t = time.perf_counter() - t0
+    return {"value": cfg.n * r.iterations / t, "unit": UNIT, "cores": oracle.max_threads(),
+            "kind": "oracle",
+            "sample": f"{r.iterations} FIRE iterations (+1 initial force evaluation) of the same "
+                      f"{cfg.n}-atom box, oracle cell-grid forces, {t:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    cfg = CONFIGS[args.config]()
+    per_step = max(2.0, min(args.cpu_seconds, 120.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        cpu_baseline(cfg, args, target_s=per_step / 4)
+    vals, secs = [], 0.0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        cb = cpu_baseline(cfg, args, target_s=per_step)
+        secs += time.perf_counter() - t0
+        vals.append(cb["value"])
+    v = statistics.median(vals)
+    out = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "impl": "reference",
+           "config": {"workload": f"{cfg.name} ({cfg.n} atoms), FP64 CPU oracle sample"},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": cb["cores"], "kind": "oracle",
+                            "sample": cb["sample"]},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

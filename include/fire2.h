@@ -1,0 +1,216 @@
+/*
+ * fire2.h -- C ABI of the GB300 FIRE 2.0 relaxation library.
+ *
+ * The library relaxes one atomistic configuration to a local energy minimum
+ * with FIRE 2.0 (Guenole et al., Algorithm 2), integrated with the
+ * semi-implicit Euler scheme of Algorithm 4 and the parameters of Table 1.
+ * Every iteration of the relaxation -- neighbour-list maintenance, the force
+ * evaluation F = -grad E (Sec. 2.1), the reductions of P = F.v, |F|^2, |v|^2
+ * and the stopping norms (Sec. 3.4), the dt / alpha control, the half step
+ * back on P <= 0, and the mixing + integration -- runs on the GPU; the host
+ * launches one CUDA graph per call and reads the result once at the end.
+ *
+ * Conventions for every entry point:
+ *   - Every function returns a fire_status and never throws or aborts across
+ *     the ABI.  On failure, fire_last_error(h) returns a message that stays
+ *     valid until the next call on the same handle.
+ *   - Host buffers are owned by the caller; the library copies in and out
+ *     and keeps no caller pointer after returning.  Device buffers passed to
+ *     the *_dev variants are owned by the caller and must stay valid until
+ *     the call returns (the call synchronises its stream before returning).
+ *   - The handle owns all device memory it allocates (fire_init) and frees
+ *     it in fire_destroy.  A handle must not be used by two threads at once.
+ *   - Positions are N x 3 row-major doubles (x0 y0 z0 x1 y1 z1 ...).  Boxes
+ *     are orthorhombic with lengths box[3]; a periodic axis must be at least
+ *     twice the interaction cut-off long (minimum-image convention).
+ *   - Units are the caller's.  `mass` is expressed so that the acceleration
+ *     is F / mass (for metal units with masses in amu divide the mass by
+ *     9648.533212 to get eV ps^2 / A^2).
+ */
+#ifndef FIRE2_GB300_H
+#define FIRE2_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FIRE2_ABI_VERSION 1
+
+typedef enum {
+    FIRE_OK = 0,
+    FIRE_ERR_ARG = 1,           /* invalid argument (NULL, size, box, parameter) */
+    FIRE_ERR_CUDA = 2,          /* a CUDA runtime call failed */
+    FIRE_ERR_NOMEM = 3,         /* device or host allocation failed */
+    FIRE_ERR_NONFINITE = 4,     /* a force, energy or position became NaN/Inf */
+    FIRE_ERR_NBR_OVERFLOW = 5,  /* a neighbour list or cell exceeded its capacity */
+    FIRE_ERR_TIMEOUT = 6,       /* the device loop exceeded its wall-clock budget */
+    FIRE_ERR_STATE = 7          /* call not valid for this handle (e.g. wrong size) */
+} fire_status;
+
+/* Stop reasons (Algorithm 2 and Sec. 3.4). */
+typedef enum {
+    FIRE_STOP_FTOL = 0,         /* force norm fell below ftol ("converged") */
+    FIRE_STOP_MAXITER = 1,      /* maxiter iterations done */
+    FIRE_STOP_MAXVDOTF = 2      /* more than vdfmax consecutive passes with P <= 0 */
+} fire_stop;
+
+/* Force norm used by the convergence test (Sec. 3.4). */
+typedef enum {
+    FIRE_NORM_MAX_ATOM = 0,     /* max_i |F_i| (Euclidean per atom) */
+    FIRE_NORM_TWO = 1,          /* f2norm: Euclidean norm of the 3N force vector */
+    FIRE_NORM_INF = 2           /* largest Cartesian force component */
+} fire_norm;
+
+typedef enum {
+    FIRE_POT_LJ = 0,            /* 12-6 Lennard-Jones, energy shifted to 0 at rc */
+    FIRE_POT_RGL = 1            /* second-moment (RGL) EAM, quintic taper on [rs, rc) */
+} fire_pot_kind;
+
+typedef enum {
+    FIRE_PREC_FP64 = 0,         /* all arithmetic in FP64 */
+    FIRE_PREC_FP32_PAIR = 1     /* pair/embedding math in FP32; positions, sums, control FP64 */
+} fire_precision;
+
+typedef enum {
+    FIRE_INT_EULER_IMPLICIT = 0 /* Algorithm 4 (semi-implicit / symplectic Euler) */
+} fire_integrator;
+
+typedef struct {
+    int64_t n_atoms;            /* N >= 1 */
+    double mass;                /* uniform mass (Sec. 2.1), > 0 */
+    int32_t periodic[3];        /* 1 = periodic axis, 0 = open */
+    int32_t reserved;
+} fire_system_t;
+
+typedef struct {
+    int32_t kind;               /* fire_pot_kind */
+    int32_t precision;          /* fire_precision */
+    /* LJ: phi(r) = 4 eps [(sigma/r)^12 - (sigma/r)^6] - phi(rc_lj), r < rc_lj */
+    double eps, sigma, rc_lj;
+    /* RGL: E_i = sum_j A e^{-p(r/r0-1)} S(r) - sqrt(sum_j xi^2 e^{-2q(r/r0-1)} S(r)),
+     * S = 1 - 10t^3 + 15t^4 - 6t^5, t = (r - rs)/(rc - rs) on [rs, rc) */
+    double A, xi, p, q, r0, rs, rc;
+    double skin;                /* neighbour-list skin (>= 0); lists rebuilt after
+                                   any atom moved more than skin/2 */
+} fire_potential_t;
+
+/* FIRE 2.0 parameters: Table 1 names; dt_start is the MD timestep. */
+typedef struct {
+    double dt_start;            /* initial timestep, > 0 */
+    double tmax;                /* dt_max = tmax * dt_start          (default 10) */
+    double tmin;                /* dt_min = tmin * dt_start          (default 0.02) */
+    double dtgrow;              /* f_inc                             (default 1.1) */
+    double dtshrink;            /* f_dec                             (default 0.5) */
+    double alpha0;              /* alpha_start                       (default 0.25) */
+    double alphashrink;         /* f_alpha                           (default 0.99) */
+    int32_t delaystep;          /* N_delay                           (default 20) */
+    int32_t vdfmax;             /* N_P<=0,max                        (default 2000) */
+    int32_t halfstepback;       /* 1 = correct uphill motion         (default 1) */
+    int32_t initialdelay;       /* 1 = no dt/alpha change while i < N_delay (default 1) */
+    int32_t integrator;         /* fire_integrator                   (default 0) */
+    int32_t norm;               /* fire_norm for the ftol test       (default 0) */
+} fire_params_t;
+
+typedef struct {
+    double energy;              /* E at the returned positions */
+    int64_t iterations;         /* completed FIRE iterations (= force evaluations - 1) */
+    int64_t force_evals;        /* force evaluations including the initial one */
+    int64_t nbr_builds;         /* neighbour-list builds during the call */
+    int32_t stop;               /* fire_stop */
+    int32_t reserved;
+    double fmax_atom;           /* max_i |F_i| at the returned positions */
+    double f2norm;              /* |F| of the 3N vector */
+    double finf;                /* max |F_i,d| */
+    double dt_final, alpha_final;
+} fire_result_t;
+
+typedef struct fire_handle fire_handle_t;
+
+/* Fills *out with the Table 1 defaults and the given dt_start.
+ * Returns FIRE_ERR_ARG if out is NULL or dt_start <= 0. */
+fire_status fire_default_params(fire_params_t* out, double dt_start);
+
+/* Creates a handle for systems of sys->n_atoms atoms with the given potential
+ * and FIRE parameters; allocates all device buffers on the current device.
+ * Errors: FIRE_ERR_ARG (bad field), FIRE_ERR_NOMEM, FIRE_ERR_CUDA. */
+fire_status fire_init(fire_handle_t** h, const fire_system_t* sys,
+                      const fire_potential_t* pot, const fire_params_t* params);
+
+/* Relaxes pos (host, N x 3, in/out) in box[3] until the chosen force norm is
+ * below ftol, maxiter iterations are done, or MAXVDOTF triggers (Alg. 2).
+ * pos is overwritten only when FIRE_OK is returned; a MAXITER or MAXVDOTF stop
+ * is FIRE_OK with out->stop set.  out may not be NULL.
+ * Errors: FIRE_ERR_ARG (ftol < 0, maxiter < 0, box), FIRE_ERR_NONFINITE,
+ * FIRE_ERR_NBR_OVERFLOW, FIRE_ERR_TIMEOUT, FIRE_ERR_CUDA. */
+fire_status fire_minimize(fire_handle_t* h, double* pos, const double box[3], double ftol,
+                          int64_t maxiter, fire_result_t* out);
+
+/* Same as fire_minimize with pos on the device (N x 3 doubles, in/out),
+ * running on `stream` (a cudaStream_t, NULL = legacy default stream).  The
+ * call returns after the stream has finished the relaxation. */
+fire_status fire_minimize_dev(fire_handle_t* h, double* d_pos, const double box[3], double ftol,
+                              int64_t maxiter, fire_result_t* out, void* stream);
+
+/* One force evaluation F = -grad E (Sec. 2.1) at pos (host, N x 3).
+ * forces (host, N x 3) may be NULL; energy may be NULL.
+ * Errors: FIRE_ERR_ARG, FIRE_ERR_NONFINITE, FIRE_ERR_NBR_OVERFLOW, FIRE_ERR_CUDA. */
+fire_status fire_energy_forces(fire_handle_t* h, const double* pos, const double box[3],
+                               double* forces, double* energy);
+
+/* Device-pointer variant: d_pos, d_forces (N x 3 doubles) and d_energy (one
+ * double) are device buffers; d_forces / d_energy may be NULL. */
+fire_status fire_energy_forces_dev(fire_handle_t* h, const double* d_pos, const double box[3],
+                                   double* d_forces, double* d_energy, void* stream);
+
+/* Wall-clock budget of one device relaxation loop (default 3600 s, 0 = none).
+ * When exceeded, the loop stops at the next iteration boundary and the call
+ * returns FIRE_ERR_TIMEOUT.  Errors: FIRE_ERR_ARG (h NULL or seconds < 0). */
+fire_status fire_set_time_budget(fire_handle_t* h, double seconds);
+
+/* Stages timed by fire_profile_stages. */
+typedef enum {
+    FIRE_STAGE_BUILD = 0,       /* cell binning + neighbour-list build */
+    FIRE_STAGE_DENSITY = 1,     /* RGL density pass (0 for LJ) */
+    FIRE_STAGE_EMBED = 2,       /* RGL embedding derivative (0 for LJ) */
+    FIRE_STAGE_FORCE = 3,       /* force pass (RGL pass 2, or LJ) */
+    FIRE_STAGE_REDUCE = 4,      /* FP64 reductions of P, |F|^2, |v|^2, max|F_i| */
+    FIRE_STAGE_CONTROL = 5,     /* scalar FIRE control (Algorithm 2) */
+    FIRE_STAGE_UPDATE = 6,      /* element-wise half step back / kick / mix / drift */
+    FIRE_NSTAGES = 7
+} fire_stage;
+
+/* Diagnostic: runs the kernels of one relaxation iteration `reps` times at
+ * pos (host, N x 3) on the handle's stream, each kernel bracketed by CUDA
+ * events, and writes the mean device time of each stage in milliseconds to
+ * stage_ms[FIRE_NSTAGES].  The neighbour list is rebuilt in every repetition
+ * (so FIRE_STAGE_BUILD is the cost of one rebuild); the update runs with
+ * dt = 0 so the positions stay fixed.  The paper has no counterpart (its cost
+ * metric is the number of force evaluations, Sec. 5.3).
+ * Errors: as fire_energy_forces; FIRE_ERR_ARG if reps < 1 or stage_ms NULL. */
+fire_status fire_profile_stages(fire_handle_t* h, const double* pos, const double box[3],
+                                int32_t reps, double* stage_ms);
+
+/* Diagnostic: measured issue rate of dependent-free fused multiply-adds on
+ * the current device, in floating-point operations per second (2 per FMA):
+ * which = 0 for FP64, 1 for FP32.  Used as the ALU roofline denominator of
+ * the force kernels.  The paper has no counterpart.
+ * Errors: FIRE_ERR_ARG (which, out), FIRE_ERR_CUDA. */
+fire_status fire_diag_fma_peak(int32_t which, double* flops_per_s);
+
+/* Message of the last failed call on h (or of the last failed fire_init when
+ * h is NULL).  Never NULL. */
+const char* fire_last_error(const fire_handle_t* h);
+
+/* Frees the handle and its device memory.  NULL is accepted. */
+void fire_destroy(fire_handle_t* h);
+
+/* FIRE2_ABI_VERSION of the loaded library. */
+int32_t fire_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FIRE2_GB300_H */

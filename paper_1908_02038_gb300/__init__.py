@@ -1,0 +1,301 @@
+"""Python binding of the GB300 FIRE 2.0 library (C ABI in include/fire2.h).
+
+Argument marshalling only: every step of a relaxation runs in the CUDA
+library ``_lib/libfire2gb300.so``.  The functions keep the C names
+(``fire_init``, ``fire_minimize``, ``fire_minimize_dev``, ``fire_energy_forces``,
+``fire_energy_forces_dev``, ...); ``FireHandle`` is a small owner object over
+them.  Importing this package never falls back to another implementation:
+if the library is missing or fails to load, the functions raise.
+
+Host-pointer entry points take numpy float64 arrays; the ``*_dev`` entry points
+take CUDA tensors (torch is used only for device memory and streams).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from ._build import LIB_PATH, build  # noqa: F401
+
+FIRE_OK, FIRE_ERR_ARG, FIRE_ERR_CUDA, FIRE_ERR_NOMEM = 0, 1, 2, 3
+FIRE_ERR_NONFINITE, FIRE_ERR_NBR_OVERFLOW, FIRE_ERR_TIMEOUT, FIRE_ERR_STATE = 4, 5, 6, 7
+FIRE_STOP_FTOL, FIRE_STOP_MAXITER, FIRE_STOP_MAXVDOTF = 0, 1, 2
+FIRE_NORM_MAX_ATOM, FIRE_NORM_TWO, FIRE_NORM_INF = 0, 1, 2
+FIRE_POT_LJ, FIRE_POT_RGL = 0, 1
+FIRE_PREC_FP64, FIRE_PREC_FP32_PAIR = 0, 1
+FIRE_INT_EULER_IMPLICIT = 0
+
+STATUS_NAMES = {0: "FIRE_OK", 1: "FIRE_ERR_ARG", 2: "FIRE_ERR_CUDA", 3: "FIRE_ERR_NOMEM",
+                4: "FIRE_ERR_NONFINITE", 5: "FIRE_ERR_NBR_OVERFLOW", 6: "FIRE_ERR_TIMEOUT",
+                7: "FIRE_ERR_STATE"}
+
+# Every symbol include/fire2.h declares (checked by the ABI test).
+EXPORTED = ("fire_abi_version", "fire_default_params", "fire_init", "fire_minimize",
+            "fire_minimize_dev", "fire_energy_forces", "fire_energy_forces_dev",
+            "fire_set_time_budget", "fire_profile_stages", "fire_diag_fma_peak",
+            "fire_last_error", "fire_destroy")
+STAGES = ("build", "density", "embed", "force", "reduce", "control", "update")
+
+
+class fire_system_t(C.Structure):
+    _fields_ = [("n_atoms", C.c_int64), ("mass", C.c_double), ("periodic", C.c_int32 * 3),
+                ("reserved", C.c_int32)]
+
+
+class fire_potential_t(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("precision", C.c_int32),
+                ("eps", C.c_double), ("sigma", C.c_double), ("rc_lj", C.c_double),
+                ("A", C.c_double), ("xi", C.c_double), ("p", C.c_double), ("q", C.c_double),
+                ("r0", C.c_double), ("rs", C.c_double), ("rc", C.c_double),
+                ("skin", C.c_double)]
+
+
+class fire_params_t(C.Structure):
+    _fields_ = [("dt_start", C.c_double), ("tmax", C.c_double), ("tmin", C.c_double),
+                ("dtgrow", C.c_double), ("dtshrink", C.c_double), ("alpha0", C.c_double),
+                ("alphashrink", C.c_double), ("delaystep", C.c_int32), ("vdfmax", C.c_int32),
+                ("halfstepback", C.c_int32), ("initialdelay", C.c_int32),
+                ("integrator", C.c_int32), ("norm", C.c_int32)]
+
+
+class fire_result_t(C.Structure):
+    _fields_ = [("energy", C.c_double), ("iterations", C.c_int64), ("force_evals", C.c_int64),
+                ("nbr_builds", C.c_int64), ("stop", C.c_int32), ("reserved", C.c_int32),
+                ("fmax_atom", C.c_double), ("f2norm", C.c_double), ("finf", C.c_double),
+                ("dt_final", C.c_double), ("alpha_final", C.c_double)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_ if name != "reserved"}
+
+
+_lib = None
+
+
+def load_library(path: str | None = None):
+    """Loads the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"FIRE CUDA library not built ({path}); run "
+                           "paper_1908_02038_gb300.build() first")
+    lib = C.CDLL(path)
+    H = C.c_void_p
+    lib.fire_abi_version.restype = C.c_int32
+    lib.fire_default_params.argtypes = [C.POINTER(fire_params_t), C.c_double]
+    lib.fire_init.argtypes = [C.POINTER(H), C.POINTER(fire_system_t), C.POINTER(fire_potential_t),
+                              C.POINTER(fire_params_t)]
+    lib.fire_minimize.argtypes = [H, C.c_void_p, C.POINTER(C.c_double), C.c_double, C.c_int64,
+                                  C.POINTER(fire_result_t)]
+    lib.fire_minimize_dev.argtypes = [H, C.c_void_p, C.POINTER(C.c_double), C.c_double,
+                                      C.c_int64, C.POINTER(fire_result_t), C.c_void_p]
+    lib.fire_energy_forces.argtypes = [H, C.c_void_p, C.POINTER(C.c_double), C.c_void_p,
+                                       C.POINTER(C.c_double)]
+    lib.fire_energy_forces_dev.argtypes = [H, C.c_void_p, C.POINTER(C.c_double), C.c_void_p,
+                                           C.c_void_p, C.c_void_p]
+    lib.fire_set_time_budget.argtypes = [H, C.c_double]
+    lib.fire_profile_stages.argtypes = [H, C.c_void_p, C.POINTER(C.c_double), C.c_int32,
+                                        C.POINTER(C.c_double)]
+    lib.fire_diag_fma_peak.argtypes = [C.c_int32, C.POINTER(C.c_double)]
+    lib.fire_last_error.restype = C.c_char_p
+    lib.fire_last_error.argtypes = [H]
+    lib.fire_destroy.argtypes = [H]
+    lib.fire_destroy.restype = None
+    for name in EXPORTED:
+        if name not in ("fire_last_error", "fire_destroy", "fire_abi_version"):
+            getattr(lib, name).restype = C.c_int
+    _lib = lib
+    return lib
+
+
+class FireError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _check(status: int, handle) -> None:
+    if status != FIRE_OK:
+        raise FireError(status, fire_last_error(handle))
+
+
+def _box(box):
+    b = (C.c_double * 3)(*[float(v) for v in box])
+    return b
+
+
+# --- same-name wrappers ------------------------------------------------------
+
+def fire_abi_version() -> int:
+    return int(load_library().fire_abi_version())
+
+
+def fire_default_params(dt_start: float) -> fire_params_t:
+    p = fire_params_t()
+    _check(load_library().fire_default_params(C.byref(p), float(dt_start)), None)
+    return p
+
+
+def fire_init(sys: fire_system_t, pot: fire_potential_t, params: fire_params_t):
+    h = C.c_void_p()
+    st = load_library().fire_init(C.byref(h), C.byref(sys), C.byref(pot), C.byref(params))
+    _check(st, None)
+    return h
+
+
+def fire_last_error(handle) -> str:
+    msg = load_library().fire_last_error(handle)
+    return msg.decode() if msg else ""
+
+
+def fire_destroy(handle) -> None:
+    if handle:
+        load_library().fire_destroy(handle)
+
+
+def fire_set_time_budget(handle, seconds: float) -> None:
+    _check(load_library().fire_set_time_budget(handle, float(seconds)), handle)
+
+
+def fire_minimize(handle, pos: np.ndarray, box, ftol: float, maxiter: int) -> fire_result_t:
+    """Relaxes pos (float64, N x 3, C-contiguous) in place."""
+    if pos.dtype != np.float64 or not pos.flags.c_contiguous:
+        raise ValueError("pos must be a C-contiguous float64 array")
+    res = fire_result_t()
+    st = load_library().fire_minimize(handle, pos.ctypes.data, _box(box), float(ftol),
+                                      int(maxiter), C.byref(res))
+    _check(st, handle)
+    return res
+
+
+def fire_minimize_dev(handle, d_pos, box, ftol: float, maxiter: int, stream=None) -> fire_result_t:
+    """d_pos: CUDA float64 tensor (N x 3, contiguous), relaxed in place."""
+    _check_dev(d_pos)
+    res = fire_result_t()
+    st = load_library().fire_minimize_dev(handle, d_pos.data_ptr(), _box(box), float(ftol),
+                                          int(maxiter), C.byref(res), _stream(stream))
+    _check(st, handle)
+    return res
+
+
+def fire_energy_forces(handle, pos: np.ndarray, box, want_forces: bool = True):
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    f = np.empty_like(pos) if want_forces else None
+    e = C.c_double(0.0)
+    st = load_library().fire_energy_forces(handle, pos.ctypes.data, _box(box),
+                                           f.ctypes.data if f is not None else None, C.byref(e))
+    _check(st, handle)
+    return float(e.value), f
+
+
+def fire_energy_forces_dev(handle, d_pos, box, d_forces=None, d_energy=None, stream=None):
+    _check_dev(d_pos)
+    st = load_library().fire_energy_forces_dev(
+        handle, d_pos.data_ptr(), _box(box),
+        d_forces.data_ptr() if d_forces is not None else None,
+        d_energy.data_ptr() if d_energy is not None else None, _stream(stream))
+    _check(st, handle)
+
+
+def fire_profile_stages(handle, pos: np.ndarray, box, reps: int = 10) -> dict:
+    """Mean device milliseconds per stage of one iteration (diagnostic)."""
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    out = (C.c_double * len(STAGES))()
+    _check(load_library().fire_profile_stages(handle, pos.ctypes.data, _box(box), int(reps), out),
+           handle)
+    return dict(zip(STAGES, list(out)))
+
+
+def fire_diag_fma_peak(which: int) -> float:
+    """Measured FMA issue rate in flop/s (which: 0 = FP64, 1 = FP32)."""
+    v = C.c_double(0.0)
+    _check(load_library().fire_diag_fma_peak(int(which), C.byref(v)), None)
+    return float(v.value)
+
+
+def _check_dev(t):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64
+            and t.is_contiguous()):
+        raise ValueError("expected a contiguous float64 CUDA tensor")
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+# --- owner object ------------------------------------------------------------
+
+@dataclass
+class Potential:
+    kind: int
+    precision: int = FIRE_PREC_FP64
+    eps: float = 1.0
+    sigma: float = 1.0
+    rc_lj: float = 2.5
+    A: float = 0.0
+    xi: float = 0.0
+    p: float = 0.0
+    q: float = 0.0
+    r0: float = 1.0
+    rs: float = 0.0
+    rc: float = 0.0
+    skin: float = 0.3
+
+    def c(self) -> fire_potential_t:
+        return fire_potential_t(self.kind, self.precision, self.eps, self.sigma, self.rc_lj,
+                                self.A, self.xi, self.p, self.q, self.r0, self.rs, self.rc,
+                                self.skin)
+
+
+class FireHandle:
+    """Owns one fire_handle_t; closes it on exit / garbage collection."""
+
+    def __init__(self, n_atoms: int, mass: float, pot: Potential, params=None,
+                 periodic=(1, 1, 1), dt_start: float | None = None, **param_overrides):
+        if params is None:
+            params = fire_default_params(dt_start)
+        for k, v in param_overrides.items():
+            setattr(params, k, int(v) if isinstance(getattr(params, k), int) else float(v))
+        sys = fire_system_t(int(n_atoms), float(mass), (C.c_int32 * 3)(*periodic), 0)
+        self.n = int(n_atoms)
+        self.h = fire_init(sys, pot.c(), params)
+
+    def minimize(self, pos, box, ftol, maxiter):
+        return fire_minimize(self.h, pos, box, ftol, maxiter)
+
+    def minimize_dev(self, d_pos, box, ftol, maxiter, stream=None):
+        return fire_minimize_dev(self.h, d_pos, box, ftol, maxiter, stream)
+
+    def energy_forces(self, pos, box, want_forces=True):
+        return fire_energy_forces(self.h, pos, box, want_forces)
+
+    def profile_stages(self, pos, box, reps=10):
+        return fire_profile_stages(self.h, pos, box, reps)
+
+    def set_time_budget(self, seconds):
+        fire_set_time_budget(self.h, seconds)
+
+    def close(self):
+        if getattr(self, "h", None):
+            fire_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

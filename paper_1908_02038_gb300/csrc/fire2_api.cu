@@ -1,0 +1,682 @@
+// Host side of the C ABI declared in include/fire2.h: handle management,
+// buffer sizing, the neighbour-mode choice, and the CUDA graph that runs a
+// whole FIRE 2.0 relaxation (Algorithm 2 + Algorithm 4) on the device with a
+// conditional WHILE node, so no host synchronisation happens per iteration.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "fire2.h"
+#include "fire2_device.cuh"
+
+using namespace fire2;
+
+struct fire_handle {
+    int device = 0;
+    fire_system_t sys{};
+    fire_potential_t pot{};
+    fire_params_t par{};
+    PotC potc{};
+    int n = 0;
+    int cap = 0;         // allocated half-list capacity per atom
+    int ncell_alloc = 0;
+    Bufs b{};
+    cudaStream_t stream = nullptr;   // default stream of host-pointer calls
+    cudaStream_t cap0 = nullptr, cap1 = nullptr;  // private capture streams
+    DevState* h_state = nullptr;     // pinned
+    double* h_pos = nullptr;         // pinned staging, N x 3
+    // cached relaxation graph
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    GeoC gkey{};
+    bool has_graph = false;
+    double budget_s = 3600.0;
+    std::string err;
+};
+
+namespace {
+
+std::string g_init_err = "no error";
+
+fire_status fail(fire_handle* h, fire_status code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (h) h->err = buf;
+    else g_init_err = buf;
+    return code;
+}
+
+#define CK(h, call)                                                                      \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess)                                                           \
+            return fail((h), e_ == cudaErrorMemoryAllocation ? FIRE_ERR_NOMEM : FIRE_ERR_CUDA, \
+                        "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+double cutoff(const fire_potential_t& p) { return p.kind == FIRE_POT_LJ ? p.rc_lj : p.rc; }
+
+// Neighbour geometry for a box.  The list radius is rc + skin, with the skin
+// reduced where a periodic axis is shorter than 2 (rc + skin) so that the
+// minimum image stays unique within the list radius.
+GeoC make_geo(const fire_handle* h, const double box[3]) {
+    GeoC g{};
+    const double rc = cutoff(h->pot);
+    double skin = h->pot.skin;
+    for (int a = 0; a < 3; ++a)
+        if (h->sys.periodic[a]) skin = std::min(skin, 0.5 * box[a] * (1.0 - 1e-12) - rc);
+    skin = std::max(skin, 0.0);
+    const double rl = rc + skin;
+    g.rlist2 = rl * rl;
+    g.half_skin2 = 0.25 * skin * skin;
+    g.brute = 0;
+    for (int a = 0; a < 3; ++a) {
+        g.L[a] = box[a];
+        g.Linv[a] = 1.0 / box[a];
+        g.per[a] = h->sys.periodic[a] ? 1 : 0;
+        g.nc[a] = (int)std::floor(box[a] / rl);
+        if (!g.per[a] || g.nc[a] < 3) g.brute = 1;
+    }
+    if (g.brute)
+        for (int a = 0; a < 3; ++a) g.nc[a] = 1;
+    for (int a = 0; a < 3; ++a) g.cinv[a] = g.nc[a] / box[a];
+    return g;
+}
+
+// Half-list capacity: 1.5x the expected upper-half-space count at the mean
+// density, plus a margin; never more than N - 1.
+int estimate_cap(const fire_handle* h, const GeoC& g) {
+    const double vol = g.L[0] * g.L[1] * g.L[2];
+    const double dens = h->n / vol;
+    const double rl = std::sqrt(g.rlist2);
+    const double half = 2.0 / 3.0 * M_PI * rl * rl * rl * dens;
+    long long cap = (long long)std::ceil(1.5 * half) + 16;
+    cap = std::min<long long>(cap, std::max(h->n - 1, 1));
+    return (int)std::max<long long>(cap, 1);
+}
+
+bool same_geo(const GeoC& a, const GeoC& b) { return std::memcmp(&a, &b, sizeof(GeoC)) == 0; }
+
+void drop_graph(fire_handle* h) {
+    if (h->exec) cudaGraphExecDestroy(h->exec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    h->exec = nullptr;
+    h->graph = nullptr;
+    h->has_graph = false;
+}
+
+fire_status ensure_buffers(fire_handle* h, const GeoC& g, int cap) {
+    if (cap > h->cap) {
+        drop_graph(h);
+        cudaFree(h->b.nbr);
+        cudaFree(h->b.crep);
+        cudaFree(h->b.cden);
+        h->b.nbr = nullptr;
+        h->b.crep = h->b.cden = nullptr;
+        const size_t slots = (size_t)cap * h->n;
+        CK(h, cudaMalloc(&h->b.nbr, slots * sizeof(uint32_t)));
+        if (h->pot.kind == FIRE_POT_RGL) {
+            CK(h, cudaMalloc(&h->b.crep, slots * sizeof(double)));
+            CK(h, cudaMalloc(&h->b.cden, slots * sizeof(double)));
+        }
+        h->cap = cap;
+    }
+    h->b.cap = h->cap;
+    const int ncell = g.brute ? 1 : g.nc[0] * g.nc[1] * g.nc[2];
+    if (ncell > h->ncell_alloc) {
+        drop_graph(h);
+        cudaFree(h->b.cell_count);
+        cudaFree(h->b.cell_start);
+        h->b.cell_count = h->b.cell_start = nullptr;
+        CK(h, cudaMalloc(&h->b.cell_count, (size_t)ncell * sizeof(int)));
+        CK(h, cudaMalloc(&h->b.cell_start, ((size_t)ncell + 1) * sizeof(int)));
+        h->ncell_alloc = ncell;
+    }
+    h->b.ncell = ncell;
+    return FIRE_OK;
+}
+
+// --- launch helpers (used both for direct launches and for capture) -------
+
+void launch_build(fire_handle* h, const GeoC& g, int force, cudaStream_t s) {
+    const int n = h->n;
+    if (!g.brute) {
+        k_cell_zero<<<ceil_div(h->b.ncell, kElemBlock), kElemBlock, 0, s>>>(h->b, g, force);
+        k_cell_count<<<ceil_div(n, kElemBlock), kElemBlock, 0, s>>>(h->b, g, force);
+        k_cell_scan<<<1, 1024, 0, s>>>(h->b, g, force);
+        k_cell_fill<<<ceil_div(n, kElemBlock), kElemBlock, 0, s>>>(h->b, g, force);
+    }
+    k_nbr_build<<<ceil_div(n, kForceBlock), kForceBlock, 0, s>>>(h->b, g, force);
+}
+
+void launch_forces(fire_handle* h, const GeoC& g, cudaStream_t s) {
+    const int n = h->n;
+    if (h->pot.kind == FIRE_POT_RGL) {
+        k_density<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
+        k_embed<<<h->b.nb_embed, kElemBlock, 0, s>>>(h->b);
+        k_force_rgl<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, g);
+    } else {
+        k_force_lj<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
+    }
+    (void)n;
+}
+
+void launch_reduce(fire_handle* h, cudaStream_t s) {
+    k_reduce<<<h->b.nb_red, kElemBlock, 0, s>>>(h->b);
+}
+
+int update_grid(int n) { return std::max(1, std::min(ceil_div(n, kElemBlock), 152 * 8)); }
+
+fire_status build_graph(fire_handle* h, const GeoC& g) {
+    drop_graph(h);
+    cudaGraph_t graph = nullptr;
+    CK(h, cudaGraphCreate(&graph, 0));
+    cudaGraphConditionalHandle hw;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&hw, graph, 0, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return fail(h, FIRE_ERR_CUDA, "cudaGraphConditionalHandleCreate: %s", cudaGetErrorString(e));
+    }
+    const int n = h->n;
+    e = cudaStreamBeginCaptureToGraph(h->cap0, graph, nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return fail(h, FIRE_ERR_CUDA, "begin capture: %s", cudaGetErrorString(e));
+    }
+    k_prepare<<<ceil_div(n, kElemBlock), kElemBlock, 0, h->cap0>>>(h->b);
+    launch_build(h, g, 1, h->cap0);
+    launch_forces(h, g, h->cap0);
+    launch_reduce(h, h->cap0);
+    k_control<<<1, kCtlThreads, 0, h->cap0>>>(h->b, CTL_INITIAL, hw, 1);
+
+    cudaStreamCaptureStatus cst;
+    cudaGraph_t cg = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    e = cudaStreamGetCaptureInfo(h->cap0, &cst, nullptr, &cg, &deps, nullptr, &ndeps);
+    cudaGraphNode_t cnode = nullptr;
+    alignas(cudaGraphNodeParams) unsigned char cp_raw[sizeof(cudaGraphNodeParams)];
+    std::memset(cp_raw, 0, sizeof cp_raw);
+    cudaGraphNodeParams& cp = *reinterpret_cast<cudaGraphNodeParams*>(cp_raw);
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = hw;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&cnode, cg, deps, nullptr, ndeps, &cp);
+    if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(h->cap0, &cnode, nullptr, 1,
+                                                                  cudaStreamSetCaptureDependencies);
+    if (e == cudaSuccess) {
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        e = cudaStreamBeginCaptureToGraph(h->cap1, body, nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeRelaxed);
+        if (e == cudaSuccess) {
+            k_update<<<update_grid(n), kElemBlock, 0, h->cap1>>>(h->b);
+            launch_build(h, g, 0, h->cap1);
+            launch_forces(h, g, h->cap1);
+            launch_reduce(h, h->cap1);
+            k_control<<<1, kCtlThreads, 0, h->cap1>>>(h->b, CTL_LOOP, hw, 1);
+            cudaGraph_t body_out = nullptr;
+            e = cudaStreamEndCapture(h->cap1, &body_out);
+        }
+    }
+    k_finalize<<<ceil_div(n, kElemBlock), kElemBlock, 0, h->cap0>>>(h->b);
+    cudaGraph_t out = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(h->cap0, &out);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return fail(h, FIRE_ERR_CUDA, "graph capture failed: %s / %s", cudaGetErrorString(e),
+                    cudaGetErrorString(e2));
+    }
+    e = cudaGraphInstantiate(&h->exec, graph, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        h->exec = nullptr;
+        return fail(h, FIRE_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+    }
+    h->graph = graph;
+    h->gkey = g;
+    h->has_graph = true;
+    return FIRE_OK;
+}
+
+fire_status check_box(fire_handle* h, const double box[3]) {
+    if (!box) return fail(h, FIRE_ERR_ARG, "box is NULL");
+    const double rc = cutoff(h->pot);
+    for (int a = 0; a < 3; ++a) {
+        if (!(box[a] > 0.0) || !std::isfinite(box[a]))
+            return fail(h, FIRE_ERR_ARG, "box[%d] = %g must be positive and finite", a, box[a]);
+        if (h->sys.periodic[a] && box[a] < 2.0 * rc)
+            return fail(h, FIRE_ERR_ARG,
+                        "periodic box[%d] = %g is shorter than twice the cut-off %g", a, box[a], rc);
+    }
+    return FIRE_OK;
+}
+
+void init_state(fire_handle* h, double ftol, int64_t maxiter) {
+    DevState& s = *h->h_state;
+    std::memset(&s, 0, sizeof s);
+    const fire_params_t& p = h->par;
+    s.ftol = ftol;
+    s.maxiter = maxiter;
+    s.dt_start = p.dt_start;
+    s.dtmax = p.tmax * p.dt_start;
+    s.dtmin = p.tmin * p.dt_start;
+    s.dtgrow = p.dtgrow;
+    s.dtshrink = p.dtshrink;
+    s.alpha0 = p.alpha0;
+    s.alphashrink = p.alphashrink;
+    s.mass = h->sys.mass;
+    s.delaystep = p.delaystep;
+    s.vdfmax = p.vdfmax;
+    s.halfstepback = p.halfstepback;
+    s.initialdelay = p.initialdelay;
+    s.norm = p.norm;
+    s.budget_ns = (unsigned long long)(h->budget_s * 1e9);
+    s.dt = p.dt_start;
+    s.alpha = p.alpha0;
+}
+
+fire_status status_to_error(fire_handle* h, int st) {
+    switch (st) {
+        case ST_OK: return FIRE_OK;
+        case ST_NONFINITE: return fail(h, FIRE_ERR_NONFINITE, "non-finite force, energy or velocity");
+        case ST_NBR_OVERFLOW: return fail(h, FIRE_ERR_NBR_OVERFLOW, "neighbour list overflow");
+        case ST_TIMEOUT: return fail(h, FIRE_ERR_TIMEOUT, "device loop exceeded its time budget");
+        case ST_RANGE:
+            return fail(h, FIRE_ERR_ARG, "positions lie more than one box length outside the box");
+        default: return fail(h, FIRE_ERR_CUDA, "unknown device status %d", st);
+    }
+}
+
+void fill_result(const fire_handle* h, fire_result_t* out) {
+    const DevState& s = *h->h_state;
+    out->energy = s.energy;
+    out->iterations = s.iter;
+    out->force_evals = s.evals;
+    out->nbr_builds = s.nbr_builds;
+    out->stop = s.stop;
+    out->reserved = 0;
+    out->fmax_atom = std::sqrt(s.fmax2);
+    out->f2norm = std::sqrt(s.F2);
+    out->finf = s.finf;
+    out->dt_final = s.dt;
+    out->alpha_final = s.alpha;
+}
+
+fire_status check_params(fire_handle* h, const fire_params_t& p) {
+    if (!(p.dt_start > 0.0) || !std::isfinite(p.dt_start)) return fail(h, FIRE_ERR_ARG, "dt_start must be > 0");
+    if (!(p.tmax > 0.0) || !(p.tmin >= 0.0)) return fail(h, FIRE_ERR_ARG, "tmax must be > 0, tmin >= 0");
+    if (!(p.dtgrow >= 1.0) || !(p.dtshrink > 0.0 && p.dtshrink <= 1.0))
+        return fail(h, FIRE_ERR_ARG, "need dtgrow >= 1 and 0 < dtshrink <= 1");
+    if (!(p.alpha0 >= 0.0 && p.alpha0 <= 1.0) || !(p.alphashrink > 0.0 && p.alphashrink <= 1.0))
+        return fail(h, FIRE_ERR_ARG, "need 0 <= alpha0 <= 1 and 0 < alphashrink <= 1");
+    if (p.delaystep < 0 || p.vdfmax < 0) return fail(h, FIRE_ERR_ARG, "delaystep and vdfmax must be >= 0");
+    if (p.integrator != FIRE_INT_EULER_IMPLICIT) return fail(h, FIRE_ERR_ARG, "unsupported integrator %d", p.integrator);
+    if (p.norm < 0 || p.norm > 2) return fail(h, FIRE_ERR_ARG, "unknown norm %d", p.norm);
+    return FIRE_OK;
+}
+
+fire_status prepare_call(fire_handle* h, const double box[3], GeoC* g) {
+    fire_status st = check_box(h, box);
+    if (st != FIRE_OK) return st;
+    CK(h, cudaSetDevice(h->device));
+    *g = make_geo(h, box);
+    const int cap = std::max(estimate_cap(h, *g), h->cap);
+    return ensure_buffers(h, *g, cap);
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t fire_abi_version(void) { return FIRE2_ABI_VERSION; }
+
+fire_status fire_default_params(fire_params_t* out, double dt_start) {
+    if (!out || !(dt_start > 0.0)) return FIRE_ERR_ARG;
+    out->dt_start = dt_start;
+    out->tmax = 10.0;
+    out->tmin = 0.02;
+    out->dtgrow = 1.1;
+    out->dtshrink = 0.5;
+    out->alpha0 = 0.25;
+    out->alphashrink = 0.99;
+    out->delaystep = 20;
+    out->vdfmax = 2000;
+    out->halfstepback = 1;
+    out->initialdelay = 1;
+    out->integrator = FIRE_INT_EULER_IMPLICIT;
+    out->norm = FIRE_NORM_MAX_ATOM;
+    return FIRE_OK;
+}
+
+fire_status fire_init(fire_handle_t** hp, const fire_system_t* sys, const fire_potential_t* pot,
+                      const fire_params_t* params) {
+    if (!hp || !sys || !pot || !params) return fail(nullptr, FIRE_ERR_ARG, "NULL argument to fire_init");
+    *hp = nullptr;
+    if (sys->n_atoms < 1 || sys->n_atoms > (int64_t)kIdxMask)
+        return fail(nullptr, FIRE_ERR_ARG, "n_atoms = %lld outside [1, %u]", (long long)sys->n_atoms, kIdxMask);
+    if (!(sys->mass > 0.0) || !std::isfinite(sys->mass)) return fail(nullptr, FIRE_ERR_ARG, "mass must be > 0");
+    if (pot->kind != FIRE_POT_LJ && pot->kind != FIRE_POT_RGL)
+        return fail(nullptr, FIRE_ERR_ARG, "unknown potential kind %d", pot->kind);
+    if (pot->precision != FIRE_PREC_FP64)
+        return fail(nullptr, FIRE_ERR_ARG, "precision %d not available", pot->precision);
+    if (!(pot->skin >= 0.0)) return fail(nullptr, FIRE_ERR_ARG, "skin must be >= 0");
+    if (pot->kind == FIRE_POT_LJ && !(pot->rc_lj > 0.0 && pot->sigma > 0.0 && pot->eps > 0.0))
+        return fail(nullptr, FIRE_ERR_ARG, "LJ needs eps, sigma, rc_lj > 0");
+    if (pot->kind == FIRE_POT_RGL &&
+        !(pot->rc > pot->rs && pot->rs > 0.0 && pot->r0 > 0.0 && pot->xi > 0.0 && pot->A >= 0.0))
+        return fail(nullptr, FIRE_ERR_ARG, "RGL needs 0 < rs < rc, r0 > 0, xi > 0, A >= 0");
+
+    fire_handle* h = new (std::nothrow) fire_handle();
+    if (!h) return fail(nullptr, FIRE_ERR_NOMEM, "host allocation failed");
+    h->sys = *sys;
+    h->pot = *pot;
+    h->par = *params;
+    h->n = (int)sys->n_atoms;
+    fire_status st = check_params(h, *params);
+    if (st != FIRE_OK) {
+        g_init_err = h->err;
+        delete h;
+        return st;
+    }
+    PotC& c = h->potc;
+    c.kind = pot->kind;
+    if (pot->kind == FIRE_POT_LJ) {
+        c.rc2 = pot->rc_lj * pot->rc_lj;
+        c.eps = pot->eps;
+        c.sigma2 = pot->sigma * pot->sigma;
+        const double sr6 = std::pow(pot->sigma / pot->rc_lj, 6.0);
+        c.lj_shift = 4.0 * pot->eps * (sr6 * sr6 - sr6);
+    } else {
+        c.rc2 = pot->rc * pot->rc;
+        c.A = pot->A;
+        c.xi2 = pot->xi * pot->xi;
+        c.p = pot->p;
+        c.q2 = 2.0 * pot->q;
+        c.r0inv = 1.0 / pot->r0;
+        c.p_r0 = pot->p / pot->r0;
+        c.q2_r0 = 2.0 * pot->q / pot->r0;
+        c.rs = pot->rs;
+        c.rc = pot->rc;
+        c.winv = 1.0 / (pot->rc - pot->rs);
+    }
+
+    auto bail = [&](fire_status s) {
+        g_init_err = h->err;
+        fire_destroy(h);
+        return s;
+    };
+#define CKI(call)                                                                         \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return bail(fail(h, e_ == cudaErrorMemoryAllocation ? FIRE_ERR_NOMEM : FIRE_ERR_CUDA, \
+                             "%s: %s", #call, cudaGetErrorString(e_)));                   \
+    } while (0)
+    CKI(cudaGetDevice(&h->device));
+    CKI(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+    CKI(cudaStreamCreateWithFlags(&h->cap0, cudaStreamNonBlocking));
+    CKI(cudaStreamCreateWithFlags(&h->cap1, cudaStreamNonBlocking));
+    const size_t n = (size_t)h->n;
+    Bufs& b = h->b;
+    b.n = h->n;
+    b.nb_force = ceil_div(h->n, kForceBlock);
+    b.nb_embed = pot->kind == FIRE_POT_RGL ? ceil_div(h->n, kElemBlock) : 0;
+    b.nb_red = std::max(1, std::min(ceil_div(h->n, kElemBlock), 152 * 4));
+    CKI(cudaMalloc(&b.x, n * sizeof(dvec4)));
+    CKI(cudaMalloc(&b.v, n * sizeof(dvec4)));
+    CKI(cudaMalloc(&b.f, n * sizeof(dvec4)));
+    CKI(cudaMalloc(&b.xref, n * sizeof(dvec4)));
+    CKI(cudaMalloc(&b.nnbr, n * sizeof(int)));
+    CKI(cudaMalloc(&b.cell_of, n * sizeof(int)));
+    CKI(cudaMalloc(&b.cell_atoms, n * sizeof(int)));
+    if (pot->kind == FIRE_POT_RGL) {
+        CKI(cudaMalloc(&b.rho, n * sizeof(double)));
+        CKI(cudaMalloc(&b.fp, n * sizeof(double)));
+    }
+    CKI(cudaMalloc(&b.epart, (size_t)(b.nb_force + b.nb_embed) * sizeof(double)));
+    CKI(cudaMalloc(&b.rpart, (size_t)5 * b.nb_red * sizeof(double)));
+    CKI(cudaMalloc(&b.st, sizeof(DevState)));
+    CKI(cudaMalloc(&b.pos_io, 3 * n * sizeof(double)));
+    CKI(cudaMallocHost(&h->h_state, sizeof(DevState)));
+    CKI(cudaMallocHost(&h->h_pos, 3 * n * sizeof(double)));
+#undef CKI
+    *hp = h;
+    return FIRE_OK;
+}
+
+void fire_destroy(fire_handle_t* h) {
+    if (!h) return;
+    cudaSetDevice(h->device);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    drop_graph(h);
+    Bufs& b = h->b;
+    void* ptrs[] = {b.x, b.v, b.f, b.xref, b.rho, b.fp, b.nbr, b.nnbr, b.crep, b.cden,
+                    b.cell_of, b.cell_count, b.cell_start, b.cell_atoms, b.epart, b.rpart,
+                    b.st, b.pos_io};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (h->h_state) cudaFreeHost(h->h_state);
+    if (h->h_pos) cudaFreeHost(h->h_pos);
+    if (h->stream) cudaStreamDestroy(h->stream);
+    if (h->cap0) cudaStreamDestroy(h->cap0);
+    if (h->cap1) cudaStreamDestroy(h->cap1);
+    delete h;
+}
+
+const char* fire_last_error(const fire_handle_t* h) {
+    return h ? h->err.c_str() : g_init_err.c_str();
+}
+
+fire_status fire_set_time_budget(fire_handle_t* h, double seconds) {
+    if (!h) return FIRE_ERR_ARG;
+    if (!(seconds >= 0.0)) return fail(h, FIRE_ERR_ARG, "time budget must be >= 0");
+    h->budget_s = seconds;
+    return FIRE_OK;
+}
+
+// One relaxation on the device: positions are already in b.pos_io.
+static fire_status run_minimize(fire_handle* h, const GeoC& g, double ftol, int64_t maxiter,
+                                cudaStream_t s) {
+    if (!h->has_graph || !same_geo(h->gkey, g)) {
+        fire_status st = build_graph(h, g);
+        if (st != FIRE_OK) return st;
+    }
+    init_state(h, ftol, maxiter);
+    CK(h, cudaMemcpyAsync(h->b.st, h->h_state, sizeof(DevState), cudaMemcpyHostToDevice, s));
+    CK(h, cudaGraphLaunch(h->exec, s));
+    CK(h, cudaMemcpyAsync(h->h_state, h->b.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+    CK(h, cudaStreamSynchronize(s));
+    return status_to_error(h, h->h_state->status);
+}
+
+fire_status fire_minimize_dev(fire_handle_t* h, double* d_pos, const double box[3], double ftol,
+                              int64_t maxiter, fire_result_t* out, void* stream) {
+    if (!h) return FIRE_ERR_ARG;
+    if (!d_pos || !out) return fail(h, FIRE_ERR_ARG, "NULL positions or result");
+    if (!(ftol >= 0.0) || maxiter < 0) return fail(h, FIRE_ERR_ARG, "need ftol >= 0 and maxiter >= 0");
+    GeoC g;
+    fire_status st = prepare_call(h, box, &g);
+    if (st != FIRE_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t bytes = (size_t)3 * h->n * sizeof(double);
+    for (int attempt = 0; attempt < 4; ++attempt) {
+        CK(h, cudaMemcpyAsync(h->b.pos_io, d_pos, bytes, cudaMemcpyDeviceToDevice, s));
+        st = run_minimize(h, g, ftol, maxiter, s);
+        if (st != FIRE_ERR_NBR_OVERFLOW || h->cap >= h->n - 1) break;
+        st = ensure_buffers(h, g, std::min(2 * h->cap, std::max(h->n - 1, 1)));
+        if (st != FIRE_OK) return st;
+    }
+    if (st != FIRE_OK) return st;
+    CK(h, cudaMemcpyAsync(d_pos, h->b.pos_io, bytes, cudaMemcpyDeviceToDevice, s));
+    CK(h, cudaStreamSynchronize(s));
+    fill_result(h, out);
+    return FIRE_OK;
+}
+
+fire_status fire_minimize(fire_handle_t* h, double* pos, const double box[3], double ftol,
+                          int64_t maxiter, fire_result_t* out) {
+    if (!h) return FIRE_ERR_ARG;
+    if (!pos || !out) return fail(h, FIRE_ERR_ARG, "NULL positions or result");
+    if (!(ftol >= 0.0) || maxiter < 0) return fail(h, FIRE_ERR_ARG, "need ftol >= 0 and maxiter >= 0");
+    GeoC g;
+    fire_status st = prepare_call(h, box, &g);
+    if (st != FIRE_OK) return st;
+    cudaStream_t s = h->stream;
+    const size_t bytes = (size_t)3 * h->n * sizeof(double);
+    for (int attempt = 0; attempt < 4; ++attempt) {
+        CK(h, cudaMemcpyAsync(h->b.pos_io, pos, bytes, cudaMemcpyHostToDevice, s));
+        st = run_minimize(h, g, ftol, maxiter, s);
+        if (st != FIRE_ERR_NBR_OVERFLOW || h->cap >= h->n - 1) break;
+        st = ensure_buffers(h, g, std::min(2 * h->cap, std::max(h->n - 1, 1)));
+        if (st != FIRE_OK) return st;
+    }
+    if (st != FIRE_OK) return st;
+    CK(h, cudaMemcpyAsync(h->h_pos, h->b.pos_io, bytes, cudaMemcpyDeviceToHost, s));
+    CK(h, cudaStreamSynchronize(s));
+    std::memcpy(pos, h->h_pos, bytes);
+    fill_result(h, out);
+    return FIRE_OK;
+}
+
+// Energy and forces at one configuration (plain stream launches).
+static fire_status run_eval(fire_handle* h, const GeoC& g, cudaStream_t s) {
+    init_state(h, 0.0, 0);
+    CK(h, cudaMemcpyAsync(h->b.st, h->h_state, sizeof(DevState), cudaMemcpyHostToDevice, s));
+    k_prepare<<<ceil_div(h->n, kElemBlock), kElemBlock, 0, s>>>(h->b);
+    launch_build(h, g, 1, s);
+    launch_forces(h, g, s);
+    launch_reduce(h, s);
+    k_control<<<1, kCtlThreads, 0, s>>>(h->b, CTL_EVAL, cudaGraphConditionalHandle{}, 0);
+    k_export_forces<<<ceil_div(h->n, kElemBlock), kElemBlock, 0, s>>>(h->b);
+    CK(h, cudaGetLastError());
+    CK(h, cudaMemcpyAsync(h->h_state, h->b.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+    CK(h, cudaStreamSynchronize(s));
+    return status_to_error(h, h->h_state->status);
+}
+
+fire_status fire_energy_forces_dev(fire_handle_t* h, const double* d_pos, const double box[3],
+                                   double* d_forces, double* d_energy, void* stream) {
+    if (!h) return FIRE_ERR_ARG;
+    if (!d_pos) return fail(h, FIRE_ERR_ARG, "NULL positions");
+    GeoC g;
+    fire_status st = prepare_call(h, box, &g);
+    if (st != FIRE_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t bytes = (size_t)3 * h->n * sizeof(double);
+    for (int attempt = 0; attempt < 4; ++attempt) {
+        CK(h, cudaMemcpyAsync(h->b.pos_io, d_pos, bytes, cudaMemcpyDeviceToDevice, s));
+        h->b.f_out = d_forces;
+        h->b.e_out = d_energy;
+        st = run_eval(h, g, s);
+        h->b.f_out = nullptr;
+        h->b.e_out = nullptr;
+        if (st != FIRE_ERR_NBR_OVERFLOW || h->cap >= h->n - 1) break;
+        st = ensure_buffers(h, g, std::min(2 * h->cap, std::max(h->n - 1, 1)));
+        if (st != FIRE_OK) return st;
+    }
+    return st;
+}
+
+fire_status fire_energy_forces(fire_handle_t* h, const double* pos, const double box[3],
+                               double* forces, double* energy) {
+    if (!h) return FIRE_ERR_ARG;
+    if (!pos) return fail(h, FIRE_ERR_ARG, "NULL positions");
+    GeoC g;
+    fire_status st = prepare_call(h, box, &g);
+    if (st != FIRE_OK) return st;
+    cudaStream_t s = h->stream;
+    const size_t bytes = (size_t)3 * h->n * sizeof(double);
+    for (int attempt = 0; attempt < 4; ++attempt) {
+        CK(h, cudaMemcpyAsync(h->b.pos_io, pos, bytes, cudaMemcpyHostToDevice, s));
+        st = run_eval(h, g, s);
+        if (st != FIRE_ERR_NBR_OVERFLOW || h->cap >= h->n - 1) break;
+        st = ensure_buffers(h, g, std::min(2 * h->cap, std::max(h->n - 1, 1)));
+        if (st != FIRE_OK) return st;
+    }
+    if (st != FIRE_OK) return st;
+    if (forces) {
+        // F is in the padded dvec4 layout; export it row-major through pos_io.
+        h->b.f_out = h->b.pos_io;
+        k_export_forces<<<ceil_div(h->n, kElemBlock), kElemBlock, 0, s>>>(h->b);
+        h->b.f_out = nullptr;
+        CK(h, cudaGetLastError());
+        CK(h, cudaMemcpyAsync(h->h_pos, h->b.pos_io, bytes, cudaMemcpyDeviceToHost, s));
+        CK(h, cudaStreamSynchronize(s));
+        std::memcpy(forces, h->h_pos, bytes);
+    }
+    if (energy) *energy = h->h_state->energy;
+    return FIRE_OK;
+}
+
+fire_status fire_profile_stages(fire_handle_t* h, const double* pos, const double box[3],
+                                int32_t reps, double* stage_ms) {
+    if (!h) return FIRE_ERR_ARG;
+    if (!pos || !stage_ms || reps < 1) return fail(h, FIRE_ERR_ARG, "need pos, stage_ms and reps >= 1");
+    GeoC g;
+    fire_status st = prepare_call(h, box, &g);
+    if (st != FIRE_OK) return st;
+    cudaStream_t s = h->stream;
+    const size_t bytes = (size_t)3 * h->n * sizeof(double);
+    CK(h, cudaMemcpyAsync(h->b.pos_io, pos, bytes, cudaMemcpyHostToDevice, s));
+    init_state(h, 0.0, 0);   // dt = 0 for the update stage: positions stay put
+    h->h_state->dt_cur = 0.0;
+    CK(h, cudaMemcpyAsync(h->b.st, h->h_state, sizeof(DevState), cudaMemcpyHostToDevice, s));
+    k_prepare<<<ceil_div(h->n, kElemBlock), kElemBlock, 0, s>>>(h->b);
+    cudaEvent_t ev[FIRE_NSTAGES + 1];
+    for (auto& e : ev) CK(h, cudaEventCreate(&e));
+    double acc[FIRE_NSTAGES] = {0};
+    const bool rgl = h->pot.kind == FIRE_POT_RGL;
+    for (int r = 0; r <= reps; ++r) {
+        cudaEventRecord(ev[0], s);
+        launch_build(h, g, 1, s);
+        cudaEventRecord(ev[1], s);
+        if (rgl) k_density<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
+        cudaEventRecord(ev[2], s);
+        if (rgl) k_embed<<<h->b.nb_embed, kElemBlock, 0, s>>>(h->b);
+        cudaEventRecord(ev[3], s);
+        if (rgl) k_force_rgl<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, g);
+        else k_force_lj<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
+        cudaEventRecord(ev[4], s);
+        launch_reduce(h, s);
+        cudaEventRecord(ev[5], s);
+        k_control<<<1, kCtlThreads, 0, s>>>(h->b, CTL_EVAL, cudaGraphConditionalHandle{}, 0);
+        cudaEventRecord(ev[6], s);
+        k_update<<<update_grid(h->n), kElemBlock, 0, s>>>(h->b);
+        cudaEventRecord(ev[7], s);
+        cudaError_t e = cudaEventSynchronize(ev[7]);
+        if (e != cudaSuccess) {
+            for (auto& x : ev) cudaEventDestroy(x);
+            return fail(h, FIRE_ERR_CUDA, "profile run failed: %s", cudaGetErrorString(e));
+        }
+        if (r == 0) continue;  // warm-up repetition
+        for (int k = 0; k < FIRE_NSTAGES; ++k) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
+            acc[k] += ms;
+        }
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+    CK(h, cudaGetLastError());
+    CK(h, cudaMemcpy(h->h_state, h->b.st, sizeof(DevState), cudaMemcpyDeviceToHost));
+    st = status_to_error(h, h->h_state->status);
+    if (st != FIRE_OK) return st;
+    for (int k = 0; k < FIRE_NSTAGES; ++k) stage_ms[k] = acc[k] / reps;
+    if (!rgl) stage_ms[FIRE_STAGE_DENSITY] = stage_ms[FIRE_STAGE_EMBED] = 0.0;
+    return FIRE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,672 @@
+// Device-side data structures and kernels of the FIRE 2.0 relaxation loop.
+//
+// One relaxation iteration (Algorithm 2 of Guenole et al. with the
+// semi-implicit Euler integrator of Algorithm 4) is the kernel chain
+//
+//   k_update -> [k_cell_* -> k_nbr_build, only when an atom moved > skin/2]
+//            -> k_density -> k_embed -> k_force      (RGL second-moment EAM)
+//               or k_force_lj                        (Lennard-Jones)
+//            -> k_reduce -> k_control
+//
+// k_control finishes the FP64 reductions of P = F.v, |F|^2, |v|^2 and the
+// stopping norms (Sec. 3.4), runs the scalar dt / alpha / counter logic of
+// Algorithm 2 for the next iteration, and sets the CUDA-graph WHILE
+// condition, so the whole relaxation runs on the device without host syncs.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fire2 {
+
+// Per-atom 3-vectors live in 32-byte aligned, zero-padded double quads so a
+// load or store of one atom is a single aligned 32-byte sector.
+using dvec4 = double4_32a;
+__host__ __device__ __forceinline__ dvec4 make_dvec4(double x, double y, double z, double w) {
+    return make_double4_32a(x, y, z, w);
+}
+
+constexpr uint32_t kIdxBits = 25;
+constexpr uint32_t kIdxMask = (1u << kIdxBits) - 1u;
+constexpr int kCodeZero = 62;  // image code of the zero shift, (2 + 5*2 + 25*2)
+constexpr int kForceBlock = 128;
+constexpr int kElemBlock = 256;
+constexpr int kCtlThreads = 512;
+
+enum { ST_OK = 0, ST_NONFINITE = 4, ST_NBR_OVERFLOW = 5, ST_TIMEOUT = 6, ST_RANGE = 8 };
+enum { STOP_FTOL = 0, STOP_MAXITER = 1, STOP_MAXVDOTF = 2 };
+enum { POT_LJ = 0, POT_RGL = 1 };
+enum { CTL_INITIAL = 0, CTL_LOOP = 1, CTL_EVAL = 2 };
+
+// Potential constants, passed by value.
+struct PotC {
+    int kind;
+    double rc2;            // interaction cut-off squared
+    // LJ
+    double eps, sigma2, lj_shift;
+    // RGL
+    double A, xi2, p, q2, r0inv, p_r0, q2_r0, rs, rc, winv;
+};
+
+// Box / neighbour geometry, passed by value.
+struct GeoC {
+    double L[3], Linv[3];
+    int per[3];
+    int nc[3];             // cells per axis (cell mode)
+    double cinv[3];        // nc / L
+    int brute;             // 1 = all-pairs list build (small or open boxes)
+    double rlist2;         // (rc + skin)^2
+    double half_skin2;     // (skin / 2)^2
+};
+
+// FIRE parameters (Table 1) and call arguments, device resident.
+struct DevState {
+    // call arguments
+    double ftol;
+    long long maxiter;
+    double dt_start, dtmax, dtmin, dtgrow, dtshrink, alpha0, alphashrink, mass;
+    int delaystep, vdfmax, halfstepback, initialdelay, norm, pad0;
+    unsigned long long budget_ns, t_start;
+    // FIRE state (Algorithm 2)
+    double dt, alpha;
+    long long npos, nneg, iter, evals, nbr_builds;
+    int done, stop, status, pad1;
+    // reductions of the current (F, v)
+    double P, F2, V2, fmax2, finf, energy;
+    // update coefficients for the next k_update (see k_control)
+    int zero_v, mix, pad2, pad3;
+    double halfstep, dt_cur, mix_a, mix_fv;  // x -= halfstep*v; v' = v + dt*F/m;
+                                             // v = (1-a) v' + a*|v'|*F/|F| when mix
+    unsigned long long max_disp2;           // bits of max |x - x_ref|^2 (>= 0)
+};
+
+struct Bufs {
+    int n, cap, ncell;
+    int nb_force, nb_embed, nb_red;
+    dvec4 *x, *v, *f, *xref;
+    double *rho, *fp;
+    uint32_t *nbr;
+    int *nnbr;
+    double *crep, *cden;
+    int *cell_of, *cell_count, *cell_start, *cell_atoms;
+    double *epart, *rpart;
+    DevState* st;
+    double* pos_io;        // N x 3 row-major, in/out of a relaxation
+    double* f_out;         // N x 3 row-major forces (evaluation only)
+    double* e_out;         // energy (evaluation only)
+};
+
+// ---------------------------------------------------------------------------
+// small helpers
+
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Block-wide sum; result valid in thread 0.  `sh` holds >= 32 doubles.
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (w == 0) {
+        r = (lane < (int)(blockDim.x >> 5)) ? sh[lane] : 0.0;
+        r = warp_sum(r);
+    }
+    return r;
+}
+__device__ __forceinline__ double block_max(double v, double* sh) {
+    v = warp_max(v);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (w == 0) {
+        r = (lane < (int)(blockDim.x >> 5)) ? sh[lane] : 0.0;
+        r = warp_max(r);
+    }
+    return r;
+}
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Image-shift table: code = (sx+2) + 5 (sy+2) + 25 (sz+2), shift = s * L.
+__device__ __forceinline__ void fill_shift_table(double3* tbl, const GeoC& g) {
+    for (int t = threadIdx.x; t < 125; t += blockDim.x) {
+        const int sx = t % 5 - 2, sy = (t / 5) % 5 - 2, sz = t / 25 - 2;
+        tbl[t] = make_double3(sx * g.L[0], sy * g.L[1], sz * g.L[2]);
+    }
+}
+
+__device__ __forceinline__ int cell_coord(double x, double Linv, int nc) {
+    double u = x * Linv;
+    u -= floor(u);
+    int c = (int)(u * nc);
+    return c < 0 ? 0 : (c >= nc ? nc - 1 : c);
+}
+
+// True when the rebuild chain must run this iteration.
+__device__ __forceinline__ bool need_rebuild(const DevState* st, const GeoC& g, int force) {
+    if (force) return true;
+    if (st->done) return false;
+    return __longlong_as_double((long long)st->max_disp2) > g.half_skin2;
+}
+
+// ---------------------------------------------------------------------------
+// set-up / tear-down kernels
+
+// Copies row-major positions into the padded dvec4 layout and clears v, F
+// and rho; a non-finite coordinate sets the NONFINITE status (the control
+// kernel then stops before the first iteration).  Thread 0 of block 0 stamps
+// the start time of the call.
+__global__ void k_prepare(Bufs b) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) b.st->t_start = globaltimer_ns();
+    if (i >= b.n) return;
+    const double* p = b.pos_io + 3 * (size_t)i;
+    if (!isfinite(p[0]) || !isfinite(p[1]) || !isfinite(p[2])) b.st->status = ST_NONFINITE;
+    b.x[i] = make_dvec4(p[0], p[1], p[2], 0.0);
+    b.v[i] = make_dvec4(0.0, 0.0, 0.0, 0.0);
+    b.f[i] = make_dvec4(0.0, 0.0, 0.0, 0.0);
+    if (b.rho) b.rho[i] = 0.0;
+}
+
+__global__ void k_finalize(Bufs b) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= b.n) return;
+    const dvec4 x = b.x[i];
+    double* p = b.pos_io + 3 * (size_t)i;
+    p[0] = x.x;
+    p[1] = x.y;
+    p[2] = x.z;
+}
+
+__global__ void k_export_forces(Bufs b) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0 && b.e_out) *b.e_out = b.st->energy;
+    if (i >= b.n || !b.f_out) return;
+    const dvec4 f = b.f[i];
+    double* p = b.f_out + 3 * (size_t)i;
+    p[0] = f.x;
+    p[1] = f.y;
+    p[2] = f.z;
+}
+
+// ---------------------------------------------------------------------------
+// neighbour list: sort-based cell binning + half list (each pair once)
+
+__global__ void k_cell_zero(Bufs b, GeoC g, int force) {
+    if (!need_rebuild(b.st, g, force)) return;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < b.ncell; c += gridDim.x * blockDim.x)
+        b.cell_count[c] = 0;
+}
+
+__global__ void k_cell_count(Bufs b, GeoC g, int force) {
+    if (!need_rebuild(b.st, g, force)) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= b.n) return;
+    const dvec4 x = b.x[i];
+    const int cx = cell_coord(x.x, g.Linv[0], g.nc[0]);
+    const int cy = cell_coord(x.y, g.Linv[1], g.nc[1]);
+    const int cz = cell_coord(x.z, g.Linv[2], g.nc[2]);
+    const int c = (cx * g.nc[1] + cy) * g.nc[2] + cz;
+    b.cell_of[i] = c;
+    atomicAdd(&b.cell_count[c], 1);
+}
+
+// Exclusive scan of the cell counts (one block); cell_start[ncell] = N.
+// cell_count is turned into a fill cursor (= cell_start) for k_cell_fill.
+__global__ void k_cell_scan(Bufs b, GeoC g, int force) {
+    if (!need_rebuild(b.st, g, force)) return;
+    __shared__ int sh[1024];
+    const int T = blockDim.x, t = threadIdx.x;
+    const int per = (b.ncell + T - 1) / T;
+    const int lo = min(t * per, b.ncell), hi = min(lo + per, b.ncell);
+    int s = 0;
+    for (int c = lo; c < hi; ++c) s += b.cell_count[c];
+    sh[t] = s;
+    __syncthreads();
+    for (int o = 1; o < T; o <<= 1) {
+        int add = t >= o ? sh[t - o] : 0;
+        __syncthreads();
+        sh[t] += add;
+        __syncthreads();
+    }
+    int run = sh[t] - s;
+    for (int c = lo; c < hi; ++c) {
+        const int k = b.cell_count[c];
+        b.cell_start[c] = run;
+        b.cell_count[c] = run;
+        run += k;
+    }
+    if (t == T - 1) b.cell_start[b.ncell] = sh[t];
+}
+
+__global__ void k_cell_fill(Bufs b, GeoC g, int force) {
+    if (!need_rebuild(b.st, g, force)) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= b.n) return;
+    const int slot = atomicAdd(&b.cell_count[b.cell_of[i]], 1);
+    b.cell_atoms[slot] = i;
+}
+
+// Upper half-space test on the minimum-image vector d = x_j - x_i: exactly
+// one of (i, j) and (j, i) passes because IEEE subtraction is sign-symmetric.
+__device__ __forceinline__ bool upper_half(double dx, double dy, double dz) {
+    return dz > 0.0 || (dz == 0.0 && (dy > 0.0 || (dy == 0.0 && dx > 0.0)));
+}
+
+__device__ __forceinline__ void try_add_pair(const Bufs& b, const GeoC& g, int i, dvec4 xi,
+                                             int j, int& cnt) {
+    const dvec4 xj = b.x[j];
+    double d[3] = {xj.x - xi.x, xj.y - xi.y, xj.z - xi.z};
+    int s[3] = {0, 0, 0};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (g.per[a]) {
+            s[a] = (int)rint(d[a] * g.Linv[a]);
+            d[a] -= s[a] * g.L[a];
+        }
+    }
+    const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    if (r2 >= g.rlist2 || !upper_half(d[0], d[1], d[2])) return;
+    // image codes cover shifts of -2..2 box lengths; atoms further apart than
+    // that in raw coordinates are a caller error (positions far outside the box)
+    if (s[0] < -2 || s[0] > 2 || s[1] < -2 || s[1] > 2 || s[2] < -2 || s[2] > 2) {
+        b.st->status = ST_RANGE;
+        return;
+    }
+    if (cnt < b.cap) {
+        const uint32_t code = (uint32_t)((s[0] + 2) + 5 * (s[1] + 2) + 25 * (s[2] + 2));
+        b.nbr[(size_t)cnt * b.n + i] = (code << kIdxBits) | (uint32_t)j;
+    }
+    ++cnt;
+}
+
+__global__ void k_nbr_build(Bufs b, GeoC g, int force) {
+    if (!need_rebuild(b.st, g, force)) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) b.st->nbr_builds += 1;
+    if (i >= b.n) return;
+    const dvec4 xi = b.x[i];
+    int cnt = 0;
+    if (g.brute) {
+        for (int j = 0; j < b.n; ++j)
+            if (j != i) try_add_pair(b, g, i, xi, j, cnt);
+    } else {
+        const int cx = cell_coord(xi.x, g.Linv[0], g.nc[0]);
+        const int cy = cell_coord(xi.y, g.Linv[1], g.nc[1]);
+        const int cz = cell_coord(xi.z, g.Linv[2], g.nc[2]);
+        for (int ox = -1; ox <= 1; ++ox) {
+            const int ax = (cx + ox + g.nc[0]) % g.nc[0];
+            for (int oy = -1; oy <= 1; ++oy) {
+                const int ay = (cy + oy + g.nc[1]) % g.nc[1];
+                for (int oz = -1; oz <= 1; ++oz) {
+                    const int az = (cz + oz + g.nc[2]) % g.nc[2];
+                    const int c = (ax * g.nc[1] + ay) * g.nc[2] + az;
+                    for (int k = b.cell_start[c]; k < b.cell_start[c + 1]; ++k) {
+                        const int j = b.cell_atoms[k];
+                        if (j != i) try_add_pair(b, g, i, xi, j, cnt);
+                    }
+                }
+            }
+        }
+    }
+    if (cnt > b.cap) {
+        b.st->status = ST_NBR_OVERFLOW;
+        cnt = b.cap;
+    }
+    b.nnbr[i] = cnt;
+    b.xref[i] = xi;
+}
+
+// ---------------------------------------------------------------------------
+// RGL second-moment EAM (Sec. 5.2 EAM family), two passes over the half list.
+
+// Pass 1: rho_i = sum_j xi^2 e^{-2q(r/r0-1)} S(r); repulsive energy; per-pair
+// cache of (2 phi'(r)/r, g'(r)/r) for pass 2.
+__global__ void __launch_bounds__(kForceBlock) k_density(Bufs b, PotC P, GeoC g) {
+    __shared__ double3 tbl[125];
+    __shared__ double red[32];
+    fill_shift_table(tbl, g);
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double erep = 0.0;
+    if (i < b.n) {
+        const dvec4 xi = b.x[i];
+        const int m = b.nnbr[i];
+        double rho_i = 0.0;
+        for (int k = 0; k < m; ++k) {
+            const size_t slot = (size_t)k * b.n + i;
+            const uint32_t e = b.nbr[slot];
+            const int j = (int)(e & kIdxMask);
+            const int code = (int)(e >> kIdxBits);
+            const dvec4 xj = b.x[j];
+            double dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
+            if (code != kCodeZero) {
+                const double3 s = tbl[code];
+                dx -= s.x;
+                dy -= s.y;
+                dz -= s.z;
+            }
+            const double r2 = dx * dx + dy * dy + dz * dz;
+            double crep = 0.0, cden = 0.0;
+            if (r2 < P.rc2) {
+                const double r = sqrt(r2);
+                const double s = r * P.r0inv - 1.0;
+                const double ep = P.A * exp(-P.p * s);
+                const double eq = P.xi2 * exp(-P.q2 * s);
+                double S = 1.0, dS = 0.0;
+                if (r > P.rs) {
+                    const double t = (r - P.rs) * P.winv;
+                    const double t2 = t * t, t3 = t2 * t;
+                    S = 1.0 - 10.0 * t3 + 15.0 * t3 * t - 6.0 * t3 * t2;
+                    dS = (-30.0 * t2 + 60.0 * t3 - 30.0 * t3 * t) * P.winv;
+                }
+                const double gg = eq * S;
+                rho_i += gg;
+                atomicAdd(&b.rho[j], gg);
+                erep += 2.0 * ep * S;
+                const double rinv = 1.0 / r;
+                crep = 2.0 * ep * (-P.p_r0 * S + dS) * rinv;
+                cden = eq * (-P.q2_r0 * S + dS) * rinv;
+            }
+            b.crep[slot] = crep;
+            b.cden[slot] = cden;
+        }
+        atomicAdd(&b.rho[i], rho_i);
+    }
+    const double s = block_sum(erep, red);
+    if (threadIdx.x == 0) b.epart[blockIdx.x] = s;
+}
+
+// Embedding F(rho) = -sqrt(rho), F'(rho) = -1/(2 sqrt(rho)); an atom with
+// rho = 0 has no pair inside rc, so its F' is never used (set to 0).
+__global__ void k_embed(Bufs b) {
+    __shared__ double red[32];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double emb = 0.0;
+    if (i < b.n) {
+        const double rho = b.rho[i];
+        const double sq = sqrt(rho);
+        b.fp[i] = rho > 0.0 ? -0.5 / sq : 0.0;
+        emb = -sq;
+    }
+    const double s = block_sum(emb, red);
+    if (threadIdx.x == 0) b.epart[b.nb_force + blockIdx.x] = s;
+}
+
+// Pass 2: F_i += fs d, F_j -= fs d with fs = [2 phi' + (F'_i + F'_j) g'] / r
+// and d = x_j - x_i (F = -grad E, Sec. 2.1).
+__global__ void __launch_bounds__(kForceBlock) k_force_rgl(Bufs b, GeoC g) {
+    __shared__ double3 tbl[125];
+    fill_shift_table(tbl, g);
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= b.n) return;
+    const dvec4 xi = b.x[i];
+    const double fpi = b.fp[i];
+    const int m = b.nnbr[i];
+    double fx = 0.0, fy = 0.0, fz = 0.0;
+    for (int k = 0; k < m; ++k) {
+        const size_t slot = (size_t)k * b.n + i;
+        const double crep = b.crep[slot], cden = b.cden[slot];
+        if (crep == 0.0 && cden == 0.0) continue;
+        const uint32_t e = b.nbr[slot];
+        const int j = (int)(e & kIdxMask);
+        const int code = (int)(e >> kIdxBits);
+        const dvec4 xj = b.x[j];
+        double dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
+        if (code != kCodeZero) {
+            const double3 s = tbl[code];
+            dx -= s.x;
+            dy -= s.y;
+            dz -= s.z;
+        }
+        const double fs = crep + (fpi + b.fp[j]) * cden;
+        fx += fs * dx;
+        fy += fs * dy;
+        fz += fs * dz;
+        atomicAdd(&b.f[j].x, -fs * dx);
+        atomicAdd(&b.f[j].y, -fs * dy);
+        atomicAdd(&b.f[j].z, -fs * dz);
+    }
+    atomicAdd(&b.f[i].x, fx);
+    atomicAdd(&b.f[i].y, fy);
+    atomicAdd(&b.f[i].z, fz);
+}
+
+// Lennard-Jones, one pass: w = 24 eps [2 (s/r)^12 - (s/r)^6] / r^2,
+// F_i -= w d, F_j += w d; pair energy 4 eps [(s/r)^12 - (s/r)^6] - phi(rc).
+__global__ void __launch_bounds__(kForceBlock) k_force_lj(Bufs b, PotC P, GeoC g) {
+    __shared__ double3 tbl[125];
+    __shared__ double red[32];
+    fill_shift_table(tbl, g);
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double epair = 0.0;
+    if (i < b.n) {
+        const dvec4 xi = b.x[i];
+        const int m = b.nnbr[i];
+        double fx = 0.0, fy = 0.0, fz = 0.0;
+        for (int k = 0; k < m; ++k) {
+            const uint32_t e = b.nbr[(size_t)k * b.n + i];
+            const int j = (int)(e & kIdxMask);
+            const int code = (int)(e >> kIdxBits);
+            const dvec4 xj = b.x[j];
+            double dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
+            if (code != kCodeZero) {
+                const double3 s = tbl[code];
+                dx -= s.x;
+                dy -= s.y;
+                dz -= s.z;
+            }
+            const double r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 >= P.rc2) continue;
+            const double sr2 = P.sigma2 / r2;
+            const double sr6 = sr2 * sr2 * sr2;
+            epair += 4.0 * P.eps * (sr6 * sr6 - sr6) - P.lj_shift;
+            const double w = 24.0 * P.eps * (2.0 * sr6 * sr6 - sr6) / r2;
+            fx -= w * dx;
+            fy -= w * dy;
+            fz -= w * dz;
+            atomicAdd(&b.f[j].x, w * dx);
+            atomicAdd(&b.f[j].y, w * dy);
+            atomicAdd(&b.f[j].z, w * dz);
+        }
+        atomicAdd(&b.f[i].x, fx);
+        atomicAdd(&b.f[i].y, fy);
+        atomicAdd(&b.f[i].z, fz);
+    }
+    const double s = block_sum(epair, red);
+    if (threadIdx.x == 0) b.epart[blockIdx.x] = s;
+}
+
+// ---------------------------------------------------------------------------
+// FP64 reductions of the current (F, v): P = F.v, |F|^2, |v|^2 (Alg. 2 and
+// the mixing of Alg. 4) and the per-atom / per-component force maxima (Sec. 3.4).
+__global__ void k_reduce(Bufs b) {
+    __shared__ double red[32];
+    double P = 0.0, F2 = 0.0, V2 = 0.0, fa2 = 0.0, fin = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < b.n; i += gridDim.x * blockDim.x) {
+        const dvec4 f = b.f[i], v = b.v[i];
+        P += f.x * v.x + f.y * v.y + f.z * v.z;
+        const double a2 = f.x * f.x + f.y * f.y + f.z * f.z;
+        F2 += a2;
+        V2 += v.x * v.x + v.y * v.y + v.z * v.z;
+        fa2 = fmax(fa2, a2);
+        fin = fmax(fin, fmax(fabs(f.x), fmax(fabs(f.y), fabs(f.z))));
+    }
+    const int nb = gridDim.x;
+    double r;
+    r = block_sum(P, red);
+    if (threadIdx.x == 0) b.rpart[0 * nb + blockIdx.x] = r;
+    r = block_sum(F2, red);
+    if (threadIdx.x == 0) b.rpart[1 * nb + blockIdx.x] = r;
+    r = block_sum(V2, red);
+    if (threadIdx.x == 0) b.rpart[2 * nb + blockIdx.x] = r;
+    r = block_max(fa2, red);
+    if (threadIdx.x == 0) b.rpart[3 * nb + blockIdx.x] = r;
+    r = block_max(fin, red);
+    if (threadIdx.x == 0) b.rpart[4 * nb + blockIdx.x] = r;
+}
+
+// Fixed-order reduction of `cnt` partials by one block (deterministic).
+__device__ double ctl_sum(const double* a, int cnt, double* sh) {
+    double s = 0.0;
+    for (int k = threadIdx.x; k < cnt; k += blockDim.x) s += a[k];
+    return block_sum(s, sh);
+}
+__device__ double ctl_max(const double* a, int cnt, double* sh) {
+    double s = 0.0;
+    for (int k = threadIdx.x; k < cnt; k += blockDim.x) s = fmax(s, a[k]);
+    return block_max(s, sh);
+}
+
+// Scalar FIRE 2.0 control (Algorithm 2), one block.  After the force
+// evaluation of iteration `iter` it tests convergence (after the evaluation,
+// Alg. 2), then prepares iteration iter+1: the P > 0 / P <= 0 branch, the
+// counters, dt growth capped at dt_max, alpha decay, the N_P<=0 cap
+// (MAXVDOTF), the initial delay, the dt_min guard and the half step back.
+// It writes the coefficients k_update applies and sets the WHILE condition.
+__global__ void k_control(Bufs b, int mode, cudaGraphConditionalHandle h, int has_handle) {
+    __shared__ double sh[32];
+    const double P = ctl_sum(b.rpart + 0 * b.nb_red, b.nb_red, sh);
+    const double F2 = ctl_sum(b.rpart + 1 * b.nb_red, b.nb_red, sh);
+    const double V2 = ctl_sum(b.rpart + 2 * b.nb_red, b.nb_red, sh);
+    const double fa2 = ctl_max(b.rpart + 3 * b.nb_red, b.nb_red, sh);
+    const double fin = ctl_max(b.rpart + 4 * b.nb_red, b.nb_red, sh);
+    const double E = ctl_sum(b.epart, b.nb_force + b.nb_embed, sh);
+    if (threadIdx.x != 0) return;
+    DevState& s = *b.st;
+    s.P = P;
+    s.F2 = F2;
+    s.V2 = V2;
+    s.fmax2 = fa2;
+    s.finf = fin;
+    s.energy = E;
+    s.max_disp2 = 0ull;
+    if (mode == CTL_EVAL) {
+        if (!isfinite(E) || !isfinite(F2)) s.status = ST_NONFINITE;
+        s.done = 1;
+        return;
+    }
+    s.evals += 1;
+    bool stop = false;
+    if (!isfinite(E) || !isfinite(F2) || !isfinite(V2)) {
+        s.status = ST_NONFINITE;
+        stop = true;
+    } else if (s.status != ST_OK) {
+        stop = true;
+    } else if (s.budget_ns && globaltimer_ns() - s.t_start > s.budget_ns) {
+        s.status = ST_TIMEOUT;
+        stop = true;
+    } else {
+        const double fn = s.norm == 1 ? sqrt(F2) : (s.norm == 2 ? fin : sqrt(fa2));
+        if (fn < s.ftol) {
+            s.stop = STOP_FTOL;
+            stop = true;
+        } else if (s.iter >= s.maxiter) {
+            s.stop = STOP_MAXITER;
+            stop = true;
+        } else {
+            const long long i = ++s.iter;
+            if (P > 0.0) {
+                s.npos += 1;
+                s.nneg = 0;
+                if (s.npos > s.delaystep) {
+                    s.dt = fmin(s.dt * s.dtgrow, s.dtmax);
+                    s.alpha *= s.alphashrink;
+                }
+                s.zero_v = 0;
+                s.halfstep = 0.0;
+                // |v'|^2 of the kicked velocity v' = v + dt F / m
+                const double dtm = s.dt / s.mass;
+                const double vk2 = fmax(V2 + 2.0 * dtm * P + dtm * dtm * F2, 0.0);
+                const double fn2 = sqrt(F2);
+                s.mix = fn2 > 0.0;
+                s.mix_a = s.alpha;
+                s.mix_fv = fn2 > 0.0 ? sqrt(vk2) / fn2 : 0.0;
+            } else {
+                s.npos = 0;
+                s.nneg += 1;
+                if (s.nneg > s.vdfmax) {
+                    s.stop = STOP_MAXVDOTF;
+                    s.iter = i - 1;
+                    stop = true;
+                } else {
+                    if (!(s.initialdelay && i < s.delaystep)) {
+                        if (s.dt * s.dtshrink >= s.dtmin) s.dt *= s.dtshrink;
+                        s.alpha = s.alpha0;
+                    }
+                    s.zero_v = 1;
+                    s.halfstep = s.halfstepback ? 0.5 * s.dt : 0.0;
+                    s.mix = 0;
+                    s.mix_a = 0.0;
+                    s.mix_fv = 0.0;
+                }
+            }
+            s.dt_cur = s.dt;
+        }
+    }
+    s.done = stop ? 1 : 0;
+    if (has_handle) cudaGraphSetConditional(h, stop ? 0u : 1u);
+}
+
+// Element-wise part of one iteration: optional half step back and v = 0
+// (P <= 0, Alg. 2), then Algorithm 4: v += dt F / m, mixing
+// v = (1 - alpha) v + alpha |v| F / |F| (P > 0), x += dt v.  Clears F and rho
+// for the next force evaluation and tracks max |x - x_ref|^2.
+__global__ void k_update(Bufs b) {
+    __shared__ double red[32];
+    const DevState& s = *b.st;
+    const int zero_v = s.zero_v, mix = s.mix;
+    const double hs = s.halfstep, dt = s.dt_cur, m = s.mass;
+    const double a = s.mix_a, fv = s.mix_fv;
+    double dmax = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < b.n; i += gridDim.x * blockDim.x) {
+        dvec4 x = b.x[i], v = b.v[i];
+        const dvec4 f = b.f[i];
+        if (zero_v) {
+            x.x -= hs * v.x;
+            x.y -= hs * v.y;
+            x.z -= hs * v.z;
+            v = make_dvec4(0.0, 0.0, 0.0, 0.0);
+        }
+        v.x += dt * f.x / m;
+        v.y += dt * f.y / m;
+        v.z += dt * f.z / m;
+        if (mix) {
+            v.x = (1.0 - a) * v.x + a * fv * f.x;
+            v.y = (1.0 - a) * v.y + a * fv * f.y;
+            v.z = (1.0 - a) * v.z + a * fv * f.z;
+        }
+        x.x += dt * v.x;
+        x.y += dt * v.y;
+        x.z += dt * v.z;
+        b.x[i] = x;
+        b.v[i] = v;
+        b.f[i] = make_dvec4(0.0, 0.0, 0.0, 0.0);
+        if (b.rho) b.rho[i] = 0.0;
+        const dvec4 r = b.xref[i];
+        const double ddx = x.x - r.x, ddy = x.y - r.y, ddz = x.z - r.z;
+        dmax = fmax(dmax, ddx * ddx + ddy * ddy + ddz * ddz);
+    }
+    const double bm = block_max(dmax, red);
+    if (threadIdx.x == 0)
+        atomicMax(&b.st->max_disp2, (unsigned long long)__double_as_longlong(bm));
+}
+
+}  // namespace fire2

@@ -1,0 +1,68 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every function the
+public header declares.  No compute call is made (no GPU needed)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+import paper_1908_02038_gb300 as fg
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_functions():
+    txt = open(os.path.join(ROOT, "include", "fire2.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(fire_[a-z_]+)\s*\(", txt)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    fg.build()
+    return fg.load_library()
+
+
+def test_header_declares_expected_set():
+    assert header_functions() == sorted(fg.EXPORTED)
+
+
+def test_library_exports_every_header_symbol(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", fg.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (fire_[a-z_]+)$", out, flags=re.M))
+    missing = set(header_functions()) - exported
+    assert not missing, missing
+
+
+def test_abi_version_and_defaults(lib):
+    assert fg.fire_abi_version() == 1
+    p = fg.fire_default_params(0.001)
+    assert (p.tmax, p.tmin, p.dtgrow, p.dtshrink, p.alpha0, p.alphashrink) == \
+        (10.0, 0.02, 1.1, 0.5, 0.25, 0.99)
+    assert (p.delaystep, p.vdfmax, p.halfstepback, p.initialdelay, p.integrator, p.norm) == \
+        (20, 2000, 1, 1, 0, 0)
+    with pytest.raises(fg.FireError) as e:
+        fg.fire_default_params(0.0)
+    assert e.value.status == fg.FIRE_ERR_ARG
+
+
+def test_struct_layouts_match_header(lib):
+    # sizes of the C structs as the header lays them out on LP64
+    assert ctypes.sizeof(fg.fire_system_t) == 8 + 8 + 12 + 4
+    assert ctypes.sizeof(fg.fire_potential_t) == 4 + 4 + 8 * 11
+    assert ctypes.sizeof(fg.fire_params_t) == 7 * 8 + 6 * 4 + 0
+    assert ctypes.sizeof(fg.fire_result_t) == 8 + 8 * 3 + 4 + 4 + 8 * 5
+
+
+def test_init_rejects_bad_arguments_before_touching_the_gpu(lib):
+    pot = fg.Potential(fg.FIRE_POT_LJ).c()
+    par = fg.fire_default_params(0.005)
+    sys = fg.fire_system_t(0, 1.0, (ctypes.c_int32 * 3)(1, 1, 1), 0)
+    with pytest.raises(fg.FireError) as e:
+        fg.fire_init(sys, pot, par)
+    assert e.value.status == fg.FIRE_ERR_ARG and "n_atoms" in str(e.value)
+    sys = fg.fire_system_t(10, -1.0, (ctypes.c_int32 * 3)(1, 1, 1), 0)
+    with pytest.raises(fg.FireError):
+        fg.fire_init(sys, pot, par)

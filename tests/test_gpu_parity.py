@@ -1,0 +1,286 @@
+"""GPU path vs the FP64 CPU oracle, through the C ABI.
+
+Bars (FP64 path): forces within 1e-10 relative (max-abs difference over the
+max-abs oracle force, at the displaced starting configurations where forces
+are O(0.1-1)), energies within 1e-12 relative for single evaluations, and for
+relaxations the final energy within 1e-8 eV/atom and the iteration count
+within 5 % of the oracle's, both runs converged.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import fire_inputs as fi
+import oracle
+import paper_1908_02038_gb300 as fg
+
+pytestmark = pytest.mark.gpu
+
+F_REL = 1e-10
+E_REL = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    fg.build()
+    fg.load_library()
+
+
+def lj_pot(**kw):
+    return fg.Potential(fg.FIRE_POT_LJ, eps=1.0, sigma=1.0, rc_lj=2.5, skin=kw.pop("skin", 0.3))
+
+
+def rgl_pot(skin=0.3, precision=fg.FIRE_PREC_FP64):
+    return fg.Potential(fg.FIRE_POT_RGL, precision=precision, skin=skin, **fi.RGL_CU)
+
+
+def ora_lj():
+    return oracle.Potential("lj", eps=1.0, sigma=1.0, rc_lj=2.5)
+
+
+def ora_rgl():
+    return oracle.Potential("rgl", **fi.RGL_CU)
+
+
+def force_rel_err(fg_, fo):
+    return np.abs(fg_ - fo).max() / np.abs(fo).max()
+
+
+# ----------------------------------------------------------------------------
+# single evaluations
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_lj_energy_forces_match_oracle(seed):
+    c = fi.lj_fcc_vacancy(seed=seed)
+    eo, fo = oracle.energy_forces(c.x, c.box, ora_lj())
+    with fg.FireHandle(c.n, fi.LJ_MASS, lj_pot(), dt_start=fi.LJ_DT) as h:
+        e, f = h.energy_forces(c.x, c.box)
+    assert force_rel_err(f, fo) < F_REL
+    assert e == pytest.approx(eo, rel=E_REL)
+
+
+@pytest.mark.parametrize("ncell,nvac", [(3, 2), (4, 1), (5, 3), (7, 10)])
+def test_rgl_energy_forces_match_oracle(ncell, nvac):
+    # 3^3 and 4^3 boxes take the all-pairs list build, 5^3 and 7^3 the cell build
+    c = fi.rgl_vacancy_box(ncell=ncell, seed=20 + ncell, n_vac=nvac, sigma=0.08)
+    eo, fo = oracle.energy_forces(c.x, c.box, ora_rgl())
+    with fg.FireHandle(c.n, fi.CU_MASS, rgl_pot(), dt_start=fi.CU_DT) as h:
+        e, f = h.energy_forces(c.x, c.box)
+    assert force_rel_err(f, fo) < F_REL
+    assert e == pytest.approx(eo, rel=E_REL)
+
+
+def test_rgl_32k_energy_forces_match_oracle():
+    c = fi.rgl_vacancy_box(ncell=20, seed=2)
+    assert c.n == 31680
+    eo, fo = oracle.energy_forces(c.x, c.box, ora_rgl(), mode=oracle.FORCE_CELLS)
+    with fg.FireHandle(c.n, fi.CU_MASS, rgl_pot(), dt_start=fi.CU_DT) as h:
+        e, f = h.energy_forces(c.x, c.box)
+    assert force_rel_err(f, fo) < F_REL
+    assert e == pytest.approx(eo, rel=E_REL)
+
+
+def test_rgl_1m_sampled_forces_match_oracle():
+    c = fi.rgl_void_box()
+    assert c.n == 997450
+    rng = np.random.default_rng(5)
+    which = np.sort(rng.choice(c.n, size=2048, replace=False))
+    eo, fo = oracle.energy_forces_subset(c.x, c.box, ora_rgl(), which, mode=oracle.FORCE_CELLS)
+    with fg.FireHandle(c.n, fi.CU_MASS, rgl_pot(), dt_start=fi.CU_DT) as h:
+        e, f = h.energy_forces(c.x, c.box)
+    assert force_rel_err(f[which], fo) < F_REL
+    assert e == pytest.approx(eo, rel=E_REL)
+    # properties that hold at any size
+    assert np.abs(f.sum(0)).max() < 1e-9 * np.abs(f).max() * np.sqrt(c.n)
+
+
+def test_perfect_lattice_zero_force_and_cohesive_energy():
+    c = fi.perfect_fcc(8, fi.CU_A)
+    with fg.FireHandle(c.n, fi.CU_MASS, rgl_pot(), dt_start=fi.CU_DT) as h:
+        e, f = h.energy_forces(c.x, c.box)
+        res = h.minimize(c.x.copy(), c.box, 1e-6, 100)
+    assert np.abs(f).max() < 1e-12
+    assert e / c.n == pytest.approx(-3.508821531217027, rel=1e-13)
+    assert res.iterations == 0 and res.stop == fg.FIRE_STOP_FTOL
+
+
+def test_dev_pointer_variants_match_host():
+    torch = pytest.importorskip("torch")
+    c = fi.rgl_vacancy_box(ncell=5, seed=9, n_vac=2)
+    with fg.FireHandle(c.n, fi.CU_MASS, rgl_pot(), dt_start=fi.CU_DT) as h:
+        e, f = h.energy_forces(c.x, c.box)
+        d_pos = torch.tensor(c.x, dtype=torch.float64, device="cuda")
+        d_f = torch.empty_like(d_pos)
+        d_e = torch.zeros(1, dtype=torch.float64, device="cuda")
+        fg.fire_energy_forces_dev(h.h, d_pos, c.box, d_f, d_e)
+        torch.cuda.synchronize()
+        assert np.array_equal(d_f.cpu().numpy(), f) or force_rel_err(d_f.cpu().numpy(), f) < 1e-14
+        assert d_e.item() == pytest.approx(e, rel=1e-14)
+        x = c.x.copy()
+        r1 = h.minimize(x, c.box, 1e-6, 5000)
+        r2 = h.minimize_dev(d_pos, c.box, 1e-6, 5000)
+        assert r2.stop == fg.FIRE_STOP_FTOL
+        assert abs(r1.iterations - r2.iterations) <= max(2, 0.05 * r1.iterations)
+        assert r2.energy == pytest.approx(r1.energy, abs=1e-8 * c.n)
+
+
+# ----------------------------------------------------------------------------
+# relaxations
+
+
+def relax_pair(c, pot, opot, mass, dt, ftol, maxiter, mode=oracle.FORCE_BRUTE, periodic=(1, 1, 1)):
+    xo, ro, _ = oracle.fire2(c.x, c.box, opot, oracle.Params(dt_start=dt), mass, ftol, maxiter,
+                             periodic=periodic, mode=mode)
+    x = c.x.copy()
+    with fg.FireHandle(c.n, mass, pot, dt_start=dt, periodic=periodic) as h:
+        r = h.minimize(x, c.box, ftol, maxiter)
+    return x, r, xo, ro
+
+
+def assert_relax_parity(c, r, ro, ftol):
+    assert ro.stop == oracle.STOP_FTOL, "oracle did not converge"
+    assert r.stop == fg.FIRE_STOP_FTOL
+    assert r.fmax_atom < ftol
+    assert r.force_evals == r.iterations + 1
+    assert abs(r.energy - ro.energy) / c.n < 1e-8
+    assert abs(r.iterations - ro.iterations) <= max(2, 0.05 * ro.iterations), \
+        (r.iterations, ro.iterations)
+
+
+def test_lj_relaxation_parity():
+    c = fi.lj_fcc_vacancy(seed=1)
+    x, r, xo, ro = relax_pair(c, lj_pot(), ora_lj(), fi.LJ_MASS, fi.LJ_DT, 1e-8, 200000)
+    assert_relax_parity(c, r, ro, 1e-8)
+
+
+@pytest.mark.parametrize("ncell,nvac", [(3, 1), (5, 2)])
+def test_rgl_small_relaxation_parity(ncell, nvac):
+    c = fi.rgl_vacancy_box(ncell=ncell, seed=30 + ncell, n_vac=nvac)
+    x, r, xo, ro = relax_pair(c, rgl_pot(), ora_rgl(), fi.CU_MASS, fi.CU_DT, 1e-6, 100000)
+    assert_relax_parity(c, r, ro, 1e-6)
+
+
+def test_rgl_32k_relaxation_parity():
+    c = fi.rgl_vacancy_box(ncell=20, seed=2)
+    x, r, xo, ro = relax_pair(c, rgl_pot(), ora_rgl(), fi.CU_MASS, fi.CU_DT, 1e-6, 100000,
+                              mode=oracle.FORCE_CELLS)
+    assert_relax_parity(c, r, ro, 1e-6)
+    assert r.nbr_builds >= 1
+
+
+def test_lj_dimer_open_boundaries():
+    c = fi.Config("dimer", np.array([[5.0, 5.0, 5.0], [6.3, 5.1, 4.9]]), np.array([20.0] * 3),
+                  periodic=(0, 0, 0))
+    x, r, xo, ro = relax_pair(c, lj_pot(), ora_lj(), 1.0, fi.LJ_DT, 1e-10, 100000,
+                              periodic=(0, 0, 0))
+    assert r.stop == fg.FIRE_STOP_FTOL
+    assert abs(np.linalg.norm(x[1] - x[0]) - 2 ** (1 / 6)) < 1e-10
+    assert abs(r.iterations - ro.iterations) <= 2
+
+
+# ----------------------------------------------------------------------------
+# edge cases and error paths
+
+
+def test_single_atom_is_converged_at_start():
+    x = np.array([[1.0, 2.0, 3.0]])
+    with fg.FireHandle(1, 1.0, lj_pot(), dt_start=fi.LJ_DT) as h:
+        e, f = h.energy_forces(x, [10.0] * 3)
+        r = h.minimize(x, [10.0] * 3, 1e-8, 10)
+    assert e == 0.0 and np.all(f == 0.0)
+    assert r.iterations == 0 and r.stop == fg.FIRE_STOP_FTOL
+
+
+def test_maxiter_zero_and_vdfmax_zero():
+    c = fi.lj_fcc_vacancy(seed=1)
+    with fg.FireHandle(c.n, fi.LJ_MASS, lj_pot(), dt_start=fi.LJ_DT) as h:
+        x = c.x.copy()
+        r = h.minimize(x, c.box, 1e-8, 0)
+        assert r.stop == fg.FIRE_STOP_MAXITER and r.iterations == 0
+        assert np.array_equal(x, c.x)
+    # vdfmax = 0: the first pass has P = 0 and stops with MAXVDOTF, as in the oracle
+    with fg.FireHandle(c.n, fi.LJ_MASS, lj_pot(), dt_start=fi.LJ_DT, vdfmax=0) as h:
+        r = h.minimize(c.x.copy(), c.box, 1e-8, 100)
+    _, ro, _ = oracle.fire2(c.x, c.box, ora_lj(), oracle.Params(dt_start=fi.LJ_DT, vdfmax=0),
+                            1.0, 1e-8, 100)
+    assert r.stop == fg.FIRE_STOP_MAXVDOTF == ro.stop
+    assert r.iterations == ro.iterations == 0
+
+
+def test_maxiter_stop_matches_oracle_state():
+    c = fi.rgl_vacancy_box(ncell=4, seed=3, n_vac=2)
+    x, r, xo, ro = relax_pair(c, rgl_pot(), ora_rgl(), fi.CU_MASS, fi.CU_DT, 1e-12, 60)
+    assert r.stop == fg.FIRE_STOP_MAXITER == ro.stop
+    assert r.iterations == 60
+    assert r.dt_final == pytest.approx(ro.dt_final, rel=1e-12)
+    assert r.alpha_final == pytest.approx(ro.alpha_final, rel=1e-12)
+    assert np.abs(x - xo).max() < 1e-9
+
+
+def test_nonfinite_positions_rejected_and_untouched():
+    c = fi.lj_fcc_vacancy(seed=1)
+    x = c.x.copy()
+    x[17, 1] = np.nan
+    with fg.FireHandle(c.n, fi.LJ_MASS, lj_pot(), dt_start=fi.LJ_DT) as h:
+        with pytest.raises(fg.FireError) as e:
+            h.minimize(x, c.box, 1e-8, 100)
+        assert e.value.status == fg.FIRE_ERR_NONFINITE
+        assert np.isnan(x[17, 1]) and np.array_equal(np.delete(x, 17, 0), np.delete(c.x, 17, 0))
+        with pytest.raises(fg.FireError) as e:
+            h.energy_forces(x, c.box)
+        assert e.value.status == fg.FIRE_ERR_NONFINITE
+        # the handle stays usable
+        r = h.minimize(c.x.copy(), c.box, 1e-8, 200000)
+        assert r.stop == fg.FIRE_STOP_FTOL
+
+
+def test_box_too_small_rejected():
+    with fg.FireHandle(4, 1.0, lj_pot(), dt_start=fi.LJ_DT) as h:
+        with pytest.raises(fg.FireError) as e:
+            h.minimize(np.zeros((4, 3)), [4.0, 10.0, 10.0], 1e-6, 10)
+        assert e.value.status == fg.FIRE_ERR_ARG
+        with pytest.raises(fg.FireError) as e:
+            h.minimize(np.zeros((4, 3)), [10.0, 10.0, 10.0], -1.0, 10)
+        assert e.value.status == fg.FIRE_ERR_ARG
+
+
+def test_time_budget_stops_the_device_loop():
+    c = fi.rgl_vacancy_box(ncell=5, seed=9, n_vac=2)
+    with fg.FireHandle(c.n, fi.CU_MASS, rgl_pot(), dt_start=fi.CU_DT) as h:
+        h.set_time_budget(1e-9)
+        x = c.x.copy()
+        with pytest.raises(fg.FireError) as e:
+            h.minimize(x, c.box, 1e-6, 100000)
+        assert e.value.status == fg.FIRE_ERR_TIMEOUT
+        assert np.array_equal(x, c.x)
+        h.set_time_budget(0)
+        r = h.minimize(x, c.box, 1e-6, 100000)
+        assert r.stop == fg.FIRE_STOP_FTOL
+
+
+def test_neighbour_overflow_retry_on_dense_cluster():
+    # a dense FCC cluster in a large open box: the mean density underestimates
+    # the local one, the first list overflows and the call retries with more room
+    c = fi.perfect_fcc(4, fi.LJ_A)
+    x = c.x + np.random.default_rng(3).uniform(-0.05, 0.05, c.x.shape) + 20.0
+    box = [60.0, 60.0, 60.0]
+    eo, fo = oracle.energy_forces(x, box, ora_lj(), periodic=(0, 0, 0))
+    with fg.FireHandle(c.n, 1.0, lj_pot(), dt_start=fi.LJ_DT, periodic=(0, 0, 0)) as h:
+        e, f = h.energy_forces(x, box)
+    assert force_rel_err(f, fo) < F_REL
+    assert e == pytest.approx(eo, rel=E_REL)
+
+
+def test_graph_reuse_and_box_change():
+    c = fi.rgl_vacancy_box(ncell=5, seed=11, n_vac=1)
+    with fg.FireHandle(c.n, fi.CU_MASS, rgl_pot(), dt_start=fi.CU_DT) as h:
+        r1 = h.minimize(c.x.copy(), c.box, 1e-6, 100000)
+        r2 = h.minimize(c.x.copy(), c.box, 1e-6, 100000)
+        assert abs(r1.iterations - r2.iterations) <= max(2, 0.05 * r1.iterations)
+        box2 = c.box * 1.01
+        x3 = c.x * 1.01
+        e3, f3 = h.energy_forces(x3, box2)
+    eo, fo = oracle.energy_forces(x3, box2, ora_rgl())
+    assert force_rel_err(f3, fo) < F_REL
