@@ -52,12 +52,15 @@ ALG_BYTES_PER_ATOM_ITER = {"rgl": 112, "lj": 96}
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--config", default="rgl1m", choices=sorted(CONFIGS))
     ap.add_argument("--form", default="fp64", choices=["fp64"])
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--eval-only", action="store_true",
+                    help="one energy/force evaluation of the config (profiling aid)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="target CPU time of the oracle sample")
     return ap.parse_args()
@@ -175,6 +178,13 @@ def run_gpu(args):
     work = torch.empty_like(x0)
     stream = torch.cuda.current_stream()
     h = fg.FireHandle(n, mass, pot, dt_start=dt)
+    if args.eval_only:
+        t0 = time.perf_counter()
+        e, _ = h.energy_forces(cfg.x, cfg.box)
+        print(json.dumps({"eval_only": cfg.name, "atoms": n, "energy": e,
+                          "seconds": time.perf_counter() - t0}))
+        h.close()
+        return
 
     def step():
         work.copy_(x0)
@@ -274,54 +284,64 @@ def run_gpu(args):
                       "d2h_bytes_per_step": int(cfg.x.nbytes) + 1024}
     h.close()
     if rank == 0:
-        out["cpu_baseline"] = cpu_baseline(cfg, args) if world == 1 else None
+        if world == 1 and not args.no_cpu:
+            out["cpu_baseline"] = cpu_baseline(cfg, args)
         print(json.dumps(out), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
 
 
-def cpu_baseline(cfg, args, target_s=None):
-    """The FP64 oracle as it stands, on the host cores, on a few FIRE iterations
-    of the same configuration (cell-grid force mode)."""
+def _oracle_setup(cfg):
     import oracle
-    target_s = target_s or args.cpu_seconds
-    opot = (oracle.Potential("lj", eps=1.0, sigma=1.0, rc_lj=2.5) if cfg.name.startswith("lj")
+    oracle.build()
+    lj = cfg.name.startswith("lj")
+    opot = (oracle.Potential("lj", eps=1.0, sigma=1.0, rc_lj=2.5) if lj
             else oracle.Potential("rgl", **fi.RGL_CU))
-    mass = fi.LJ_MASS if cfg.name.startswith("lj") else fi.CU_MASS
-    dt = fi.LJ_DT if cfg.name.startswith("lj") else fi.CU_DT
-    params = oracle.Params(dt_start=dt)
-    mode = oracle.FORCE_CELLS
-    k = 1
+    mass = fi.LJ_MASS if lj else fi.CU_MASS
+    params = oracle.Params(dt_start=fi.LJ_DT if lj else fi.CU_DT)
+    return oracle, opot, mass, params
+
+
+def _oracle_iterations_for(cfg, target_s):
+    """Number of oracle FIRE iterations that take about target_s seconds."""
+    oracle, opot, mass, params = _oracle_setup(cfg)
     t0 = time.perf_counter()
-    _, r, _ = oracle.fire2(cfg.x, cfg.box, opot, params, mass, 0.0, k, mode=mode)
-    t1 = time.perf_counter() - t0
-    # the first call includes one extra (initial) force evaluation per call
-    k = max(1, int(target_s / max(t1 / 2.0, 1e-3)) - 1)
+    oracle.fire2(cfg.x, cfg.box, opot, params, mass, 0.0, 1, mode=oracle.FORCE_CELLS)
+    per_eval = (time.perf_counter() - t0) / 2.0     # initial evaluation + one iteration
+    return max(1, int(target_s / max(per_eval, 1e-4)) - 1)
+
+
+def cpu_sample(cfg, k):
+    """The FP64 oracle as it stands, on the host cores: k FIRE iterations of the
+    same configuration with the oracle's cell-grid forces."""
+    oracle, opot, mass, params = _oracle_setup(cfg)
     t0 = time.perf_counter()
-    _, r, _ = oracle.fire2(cfg.x, cfg.box, opot, params, mass, 0.0, k, mode=mode)
+    _, r, _ = oracle.fire2(cfg.x, cfg.box, opot, params, mass, 0.0, k, mode=oracle.FORCE_CELLS)
     t = time.perf_counter() - t0
     return {"value": cfg.n * r.iterations / t, "unit": UNIT, "cores": oracle.max_threads(),
-            "kind": "oracle",
+            "kind": "oracle", "seconds": t,
             "sample": f"{r.iterations} FIRE iterations (+1 initial force evaluation) of the same "
                       f"{cfg.n}-atom box, oracle cell-grid forces, {t:.1f} s"}
+
+
+def cpu_baseline(cfg, args):
+    return cpu_sample(cfg, _oracle_iterations_for(cfg, args.cpu_seconds))
 
 
 def run_reference(args):
     rank, world, local = dist_env()
     if rank != 0:
         return
-    import oracle
-    oracle.build()
     cfg = CONFIGS[args.config]()
-    per_step = max(2.0, min(args.cpu_seconds, 120.0 / max(1, args.steps + args.warmup)))
+    per_step = max(2.0, min(args.cpu_seconds, 150.0 / max(1, args.steps + args.warmup)))
+    k = _oracle_iterations_for(cfg, per_step)
     for _ in range(args.warmup):
-        cpu_baseline(cfg, args, target_s=per_step / 4)
+        cpu_sample(cfg, 1)
     vals, secs = [], 0.0
     for _ in range(args.steps):
-        t0 = time.perf_counter()
-        cb = cpu_baseline(cfg, args, target_s=per_step)
-        secs += time.perf_counter() - t0
+        cb = cpu_sample(cfg, k)
+        secs += cb["seconds"]
         vals.append(cb["value"])
     v = statistics.median(vals)
     out = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -157,6 +157,11 @@ __device__ __forceinline__ int cell_coord(double x, double Linv, int nc) {
     return c < 0 ? 0 : (c >= nc ? nc - 1 : c);
 }
 
+// Records the first error of a call; later errors do not overwrite it.
+__device__ __forceinline__ void set_status(DevState* st, int code) {
+    atomicCAS(&st->status, ST_OK, code);
+}
+
 // True when the rebuild chain must run this iteration.
 __device__ __forceinline__ bool need_rebuild(const DevState* st, const GeoC& g, int force) {
     if (force) return true;
@@ -176,7 +181,7 @@ __global__ void k_prepare(Bufs b) {
     if (i == 0) b.st->t_start = globaltimer_ns();
     if (i >= b.n) return;
     const double* p = b.pos_io + 3 * (size_t)i;
-    if (!isfinite(p[0]) || !isfinite(p[1]) || !isfinite(p[2])) b.st->status = ST_NONFINITE;
+    if (!isfinite(p[0]) || !isfinite(p[1]) || !isfinite(p[2])) set_status(b.st, ST_NONFINITE);
     b.x[i] = make_dvec4(p[0], p[1], p[2], 0.0);
     b.v[i] = make_dvec4(0.0, 0.0, 0.0, 0.0);
     b.f[i] = make_dvec4(0.0, 0.0, 0.0, 0.0);
@@ -281,11 +286,11 @@ __device__ __forceinline__ void try_add_pair(const Bufs& b, const GeoC& g, int i
         }
     }
     const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-    if (r2 >= g.rlist2 || !upper_half(d[0], d[1], d[2])) return;
+    if (!(r2 < g.rlist2) || !upper_half(d[0], d[1], d[2])) return;  // NaN fails too
     // image codes cover shifts of -2..2 box lengths; atoms further apart than
     // that in raw coordinates are a caller error (positions far outside the box)
     if (s[0] < -2 || s[0] > 2 || s[1] < -2 || s[1] > 2 || s[2] < -2 || s[2] > 2) {
-        b.st->status = ST_RANGE;
+        set_status(b.st, ST_RANGE);
         return;
     }
     if (cnt < b.cap) {
@@ -325,7 +330,7 @@ __global__ void k_nbr_build(Bufs b, GeoC g, int force) {
         }
     }
     if (cnt > b.cap) {
-        b.st->status = ST_NBR_OVERFLOW;
+        set_status(b.st, ST_NBR_OVERFLOW);
         cnt = b.cap;
     }
     b.nnbr[i] = cnt;
@@ -474,7 +479,7 @@ __global__ void __launch_bounds__(kForceBlock) k_force_lj(Bufs b, PotC P, GeoC g
                 dz -= s.z;
             }
             const double r2 = dx * dx + dy * dy + dz * dz;
-            if (r2 >= P.rc2) continue;
+            if (!(r2 < P.rc2)) continue;
             const double sr2 = P.sigma2 / r2;
             const double sr6 = sr2 * sr2 * sr2;
             epair += 4.0 * P.eps * (sr6 * sr6 - sr6) - P.lj_shift;
@@ -559,16 +564,16 @@ __global__ void k_control(Bufs b, int mode, cudaGraphConditionalHandle h, int ha
     s.energy = E;
     s.max_disp2 = 0ull;
     if (mode == CTL_EVAL) {
-        if (!isfinite(E) || !isfinite(F2)) s.status = ST_NONFINITE;
+        if ((!isfinite(E) || !isfinite(F2)) && s.status == ST_OK) s.status = ST_NONFINITE;
         s.done = 1;
         return;
     }
     s.evals += 1;
     bool stop = false;
-    if (!isfinite(E) || !isfinite(F2) || !isfinite(V2)) {
-        s.status = ST_NONFINITE;
+    if (s.status != ST_OK) {
         stop = true;
-    } else if (s.status != ST_OK) {
+    } else if (!isfinite(E) || !isfinite(F2) || !isfinite(V2)) {
+        s.status = ST_NONFINITE;
         stop = true;
     } else if (s.budget_ns && globaltimer_ns() - s.t_start > s.budget_ns) {
         s.status = ST_TIMEOUT;
