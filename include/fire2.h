@@ -199,6 +199,35 @@ fire_status fire_profile_stages(fire_handle_t* h, const double* pos, const doubl
  * Errors: FIRE_ERR_ARG (which, out), FIRE_ERR_CUDA. */
 fire_status fire_diag_fma_peak(int32_t which, double* flops_per_s);
 
+/* Energy and forces of one configuration without allocating device memory.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot call cudaMalloc when they need forces -- code running while a stream
+ * is captured into a CUDA graph (allocation is not capturable), plug-ins
+ * whose host program's memory pool owns all device memory, and
+ * latency-critical loops where an allocation could synchronise the device.
+ * It needs no handle: the caller passes the potential, the periodic flags,
+ * device buffers d_pos (n_atoms x 3 doubles, row-major, read) and d_forces
+ * (n_atoms x 3, written; may be NULL) and d_energy (one double, written; may
+ * be NULL), and the stream to run on (a cudaStream_t, NULL = legacy default).
+ * The call only enqueues kernels; the results are ready when the stream is.
+ * Forces come from an all-pairs (minimum-image) sum, FP64 only.
+ * Scratch: a static device array inside the library sized for at most 32768
+ * atoms (~0.5 MiB, held by every GPU that loads the library until the
+ * process exits).  It is shared by all calls and keeps the last call's
+ * contents; every value a call reads is written earlier in the same call, so
+ * nothing needs clearing between calls, but calls that overlap on the GPU
+ * race on it and must be serialised by the caller.  The first call on each
+ * device looks up the array's device address (cudaGetSymbolAddress); make
+ * that first call before any stream capture on that device.
+ * Errors (message in fire_last_error(NULL)): FIRE_ERR_ARG for NULL
+ * arguments, n_atoms outside [1, 32768], precision other than FP64, bad
+ * potential parameters or a periodic box shorter than twice the cut-off;
+ * FIRE_ERR_CUDA if a CUDA call or a kernel launch fails. */
+fire_status fire_energy_forces_noalloc(const fire_potential_t* pot, int64_t n_atoms,
+                                       const int32_t periodic[3], const double* d_pos,
+                                       const double box[3], double* d_forces, double* d_energy,
+                                       void* stream);
+
 /* Message of the last failed call on h (or of the last failed fire_init when
  * h is NULL).  Never NULL. */
 const char* fire_last_error(const fire_handle_t* h);

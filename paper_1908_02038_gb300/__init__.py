@@ -36,7 +36,7 @@ STATUS_NAMES = {0: "FIRE_OK", 1: "FIRE_ERR_ARG", 2: "FIRE_ERR_CUDA", 3: "FIRE_ER
 EXPORTED = ("fire_abi_version", "fire_default_params", "fire_init", "fire_minimize",
             "fire_minimize_dev", "fire_energy_forces", "fire_energy_forces_dev",
             "fire_set_time_budget", "fire_profile_stages", "fire_diag_fma_peak",
-            "fire_last_error", "fire_destroy")
+            "fire_energy_forces_noalloc", "fire_last_error", "fire_destroy")
 STAGES = ("build", "density", "embed", "force", "reduce", "control", "update")
 
 
@@ -101,6 +101,10 @@ def load_library(path: str | None = None):
     lib.fire_profile_stages.argtypes = [H, C.c_void_p, C.POINTER(C.c_double), C.c_int32,
                                         C.POINTER(C.c_double)]
     lib.fire_diag_fma_peak.argtypes = [C.c_int32, C.POINTER(C.c_double)]
+    lib.fire_energy_forces_noalloc.argtypes = [C.POINTER(fire_potential_t), C.c_int64,
+                                               C.POINTER(C.c_int32), C.c_void_p,
+                                               C.POINTER(C.c_double), C.c_void_p, C.c_void_p,
+                                               C.c_void_p]
     lib.fire_last_error.restype = C.c_char_p
     lib.fire_last_error.argtypes = [H]
     lib.fire_destroy.argtypes = [H]
@@ -215,6 +219,19 @@ def fire_diag_fma_peak(which: int) -> float:
     v = C.c_double(0.0)
     _check(load_library().fire_diag_fma_peak(int(which), C.byref(v)), None)
     return float(v.value)
+
+
+def fire_energy_forces_noalloc(pot: fire_potential_t, d_pos, box, periodic=(1, 1, 1),
+                               d_forces=None, d_energy=None, stream=None) -> None:
+    """Allocation-free evaluation into caller-owned CUDA tensors (enqueued on
+    `stream`; synchronise before reading the results)."""
+    _check_dev(d_pos)
+    per = (C.c_int32 * 3)(*[int(bool(p)) for p in periodic])
+    st = load_library().fire_energy_forces_noalloc(
+        C.byref(pot), int(d_pos.shape[0]), per, d_pos.data_ptr(), _box(box),
+        d_forces.data_ptr() if d_forces is not None else None,
+        d_energy.data_ptr() if d_energy is not None else None, _stream(stream))
+    _check(st, None)
 
 
 def _check_dev(t):

@@ -340,6 +340,12 @@ fire_status prepare_call(fire_handle* h, const double box[3], GeoC* g) {
 
 }  // namespace
 
+// Lets the allocation-free entry point (its own translation unit) report a
+// message through fire_last_error(NULL).  Not exported from the library.
+__attribute__((visibility("hidden"))) void fire2_set_global_error(const char* msg) {
+    g_init_err = msg ? msg : "unknown error";
+}
+
 extern "C" {
 
 int32_t fire_abi_version(void) { return FIRE2_ABI_VERSION; }
