@@ -58,6 +58,9 @@ def parse():
     ap.add_argument("--config", default="rgl1m", choices=sorted(CONFIGS))
     ap.add_argument("--form", default="fp64", choices=["fp64"])
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--exec", default="graph", choices=["graph", "chunked"],
+                    help="graph: one CUDA graph with a WHILE node per relaxation (default); "
+                         "chunked: plain graphs of 32 iterations (lets ncu list the kernels)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--eval-only", action="store_true",
                     help="one energy/force evaluation of the config (profiling aid)")
@@ -178,6 +181,8 @@ def run_gpu(args):
     work = torch.empty_like(x0)
     stream = torch.cuda.current_stream()
     h = fg.FireHandle(n, mass, pot, dt_start=dt)
+    if args.exec == "chunked":
+        h.set_exec_mode(fg.FIRE_EXEC_CHUNKED, 32)
     if args.eval_only:
         t0 = time.perf_counter()
         e, _ = h.energy_forces(cfg.x, cfg.box)
@@ -235,6 +240,7 @@ def run_gpu(args):
            "config": {"workload": f"{cfg.name} ({n} atoms), FIRE2 + semi-implicit Euler to "
                                   f"max|F_i| < {ftol:g}",
                       "atoms": n, "ftol": ftol, "form": args.form, "skin": pot.skin,
+                      "exec": args.exec,
                       "iterations_per_step": [rr["iterations"] for rr in results],
                       "final_fmax_atom": [rr["fmax_atom"] for rr in results],
                       "final_energy_per_atom": [rr["energy"] / n for rr in results],

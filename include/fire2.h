@@ -164,6 +164,22 @@ fire_status fire_energy_forces(fire_handle_t* h, const double* pos, const double
 fire_status fire_energy_forces_dev(fire_handle_t* h, const double* d_pos, const double box[3],
                                    double* d_forces, double* d_energy, void* stream);
 
+/* How fire_minimize drives the iterations on the device. */
+typedef enum {
+    FIRE_EXEC_GRAPH_WHILE = 0,  /* one CUDA graph with a conditional WHILE node (default):
+                                   no host synchronisation until the relaxation ends */
+    FIRE_EXEC_CHUNKED = 1       /* plain CUDA graphs of `chunk` iterations; the host reads
+                                   the stop flag once per chunk (for profilers, which
+                                   cannot look inside conditional graphs) */
+} fire_exec_mode;
+
+/* Selects the execution mode of later fire_minimize* calls on h; chunk is the
+ * number of iterations per graph launch in FIRE_EXEC_CHUNKED (1..4096,
+ * ignored otherwise).  Results do not depend on the mode.  The paper has no
+ * counterpart (it describes the loop of Algorithm 2, not how it is driven).
+ * Errors: FIRE_ERR_ARG. */
+fire_status fire_set_exec_mode(fire_handle_t* h, int32_t mode, int32_t chunk);
+
 /* Wall-clock budget of one device relaxation loop (default 3600 s, 0 = none).
  * When exceeded, the loop stops at the next iteration boundary and the call
  * returns FIRE_ERR_TIMEOUT.  Errors: FIRE_ERR_ARG (h NULL or seconds < 0). */
@@ -227,6 +243,13 @@ fire_status fire_energy_forces_noalloc(const fire_potential_t* pot, int64_t n_at
                                        const int32_t periodic[3], const double* d_pos,
                                        const double box[3], double* d_forces, double* d_energy,
                                        void* stream);
+
+/* Diagnostic: evaluates the library's FP64 exponential (the table-driven
+ * method of P. T. P. Tang, ACM TOMS 15(2), 1989, used by the RGL pair terms)
+ * at n points: d_x and d_out are device arrays of n doubles; valid for
+ * |x| < 700.  Synchronises `stream` before returning.  The paper has no
+ * counterpart.  Errors: FIRE_ERR_ARG, FIRE_ERR_NOMEM, FIRE_ERR_CUDA. */
+fire_status fire_diag_exp(int64_t n, const double* d_x, double* d_out, void* stream);
 
 /* Message of the last failed call on h (or of the last failed fire_init when
  * h is NULL).  Never NULL. */

@@ -36,7 +36,9 @@ STATUS_NAMES = {0: "FIRE_OK", 1: "FIRE_ERR_ARG", 2: "FIRE_ERR_CUDA", 3: "FIRE_ER
 EXPORTED = ("fire_abi_version", "fire_default_params", "fire_init", "fire_minimize",
             "fire_minimize_dev", "fire_energy_forces", "fire_energy_forces_dev",
             "fire_set_time_budget", "fire_profile_stages", "fire_diag_fma_peak",
-            "fire_energy_forces_noalloc", "fire_last_error", "fire_destroy")
+            "fire_energy_forces_noalloc", "fire_set_exec_mode", "fire_diag_exp",
+            "fire_last_error", "fire_destroy")
+FIRE_EXEC_GRAPH_WHILE, FIRE_EXEC_CHUNKED = 0, 1
 STAGES = ("build", "density", "embed", "force", "reduce", "control", "update")
 
 
@@ -98,6 +100,8 @@ def load_library(path: str | None = None):
     lib.fire_energy_forces_dev.argtypes = [H, C.c_void_p, C.POINTER(C.c_double), C.c_void_p,
                                            C.c_void_p, C.c_void_p]
     lib.fire_set_time_budget.argtypes = [H, C.c_double]
+    lib.fire_set_exec_mode.argtypes = [H, C.c_int32, C.c_int32]
+    lib.fire_diag_exp.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]
     lib.fire_profile_stages.argtypes = [H, C.c_void_p, C.POINTER(C.c_double), C.c_int32,
                                         C.POINTER(C.c_double)]
     lib.fire_diag_fma_peak.argtypes = [C.c_int32, C.POINTER(C.c_double)]
@@ -163,6 +167,10 @@ def fire_destroy(handle) -> None:
 
 def fire_set_time_budget(handle, seconds: float) -> None:
     _check(load_library().fire_set_time_budget(handle, float(seconds)), handle)
+
+
+def fire_set_exec_mode(handle, mode: int, chunk: int = 32) -> None:
+    _check(load_library().fire_set_exec_mode(handle, int(mode), int(chunk)), handle)
 
 
 def fire_minimize(handle, pos: np.ndarray, box, ftol: float, maxiter: int) -> fire_result_t:
@@ -234,6 +242,14 @@ def fire_energy_forces_noalloc(pot: fire_potential_t, d_pos, box, periodic=(1, 1
     _check(st, None)
 
 
+def fire_diag_exp(d_x, d_out, stream=None) -> None:
+    """The library's FP64 exponential at the points of d_x (CUDA float64)."""
+    _check_dev(d_x)
+    _check_dev(d_out)
+    _check(load_library().fire_diag_exp(int(d_x.numel()), d_x.data_ptr(), d_out.data_ptr(),
+                                        _stream(stream)), None)
+
+
 def _check_dev(t):
     import torch
     if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64
@@ -296,6 +312,9 @@ class FireHandle:
 
     def profile_stages(self, pos, box, reps=10):
         return fire_profile_stages(self.h, pos, box, reps)
+
+    def set_exec_mode(self, mode, chunk=32):
+        fire_set_exec_mode(self.h, mode, chunk)
 
     def set_time_budget(self, seconds):
         fire_set_time_budget(self.h, seconds)

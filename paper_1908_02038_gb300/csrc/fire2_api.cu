@@ -37,6 +37,9 @@ struct fire_handle {
     GeoC gkey{};
     bool has_graph = false;
     double budget_s = 3600.0;
+    int exec_mode = FIRE_EXEC_GRAPH_WHILE;
+    int chunk = 32;                  // iterations per graph launch, chunked mode
+    cudaGraphExec_t exec_init = nullptr, exec_chunk = nullptr, exec_final = nullptr;
     std::string err;
 };
 
@@ -91,6 +94,16 @@ GeoC make_geo(const fire_handle* h, const double box[3]) {
     if (g.brute)
         for (int a = 0; a < 3; ++a) g.nc[a] = 1;
     for (int a = 0; a < 3; ++a) g.cinv[a] = g.nc[a] / box[a];
+    double lmax = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        g.Lf[a] = (float)box[a];
+        g.Linvf[a] = (float)(1.0 / box[a]);
+        lmax = std::max(lmax, box[a]);
+    }
+    // FP32 positions carry absolute errors up to ~1.2e-7 of the coordinate
+    // magnitude (positions stay within about one box length of the box)
+    const double margin = 1e-3 * rc + 8.0 * 1.2e-7 * (2.0 * lmax);
+    g.rlist2f = (float)((rl + margin) * (rl + margin));
     return g;
 }
 
@@ -111,6 +124,9 @@ bool same_geo(const GeoC& a, const GeoC& b) { return std::memcmp(&a, &b, sizeof(
 void drop_graph(fire_handle* h) {
     if (h->exec) cudaGraphExecDestroy(h->exec);
     if (h->graph) cudaGraphDestroy(h->graph);
+    for (cudaGraphExec_t* e : {&h->exec_init, &h->exec_chunk, &h->exec_final})
+        if (*e) cudaGraphExecDestroy(*e);
+    h->exec_init = h->exec_chunk = h->exec_final = nullptr;
     h->exec = nullptr;
     h->graph = nullptr;
     h->has_graph = false;
@@ -247,6 +263,61 @@ fire_status build_graph(fire_handle* h, const GeoC& g) {
         return fail(h, FIRE_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
     }
     h->graph = graph;
+    h->gkey = g;
+    h->has_graph = true;
+    return FIRE_OK;
+}
+
+// Captures the kernels `fn` launches on cap0 into an executable plain graph.
+template <typename Fn>
+fire_status capture_plain(fire_handle* h, cudaGraphExec_t* out, Fn fn) {
+    cudaError_t e = cudaStreamBeginCapture(h->cap0, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) return fail(h, FIRE_ERR_CUDA, "begin capture: %s", cudaGetErrorString(e));
+    fn(h->cap0);
+    cudaGraph_t gr = nullptr;
+    e = cudaStreamEndCapture(h->cap0, &gr);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(h, FIRE_ERR_CUDA, "capture failed: %s", cudaGetErrorString(e));
+    }
+    e = cudaGraphInstantiate(out, gr, 0);
+    cudaGraphDestroy(gr);
+    if (e != cudaSuccess) return fail(h, FIRE_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+    return FIRE_OK;
+}
+
+// Chunked execution: three plain graphs (set-up, `chunk` loop bodies, write
+// back); every body kernel returns at once when the state says "done", and
+// the host reads that flag once per chunk.  Used where conditional graph
+// nodes are not wanted (profilers cannot look inside them).
+fire_status build_chunked(fire_handle* h, const GeoC& g) {
+    drop_graph(h);
+    const int n = h->n;
+    fire_status st = capture_plain(h, &h->exec_init, [&](cudaStream_t s) {
+        k_prepare<<<ceil_div(n, kElemBlock), kElemBlock, 0, s>>>(h->b);
+        launch_build(h, g, 1, s);
+        launch_forces(h, g, s);
+        launch_reduce(h, s);
+        k_control<<<1, kCtlThreads, 0, s>>>(h->b, CTL_INITIAL, cudaGraphConditionalHandle{}, 0);
+    });
+    if (st == FIRE_OK)
+        st = capture_plain(h, &h->exec_chunk, [&](cudaStream_t s) {
+            for (int c = 0; c < h->chunk; ++c) {
+                k_update<<<update_grid(n), kElemBlock, 0, s>>>(h->b);
+                launch_build(h, g, 0, s);
+                launch_forces(h, g, s);
+                launch_reduce(h, s);
+                k_control<<<1, kCtlThreads, 0, s>>>(h->b, CTL_LOOP, cudaGraphConditionalHandle{}, 0);
+            }
+        });
+    if (st == FIRE_OK)
+        st = capture_plain(h, &h->exec_final, [&](cudaStream_t s) {
+            k_finalize<<<ceil_div(n, kElemBlock), kElemBlock, 0, s>>>(h->b);
+        });
+    if (st != FIRE_OK) {
+        drop_graph(h);
+        return st;
+    }
     h->gkey = g;
     h->has_graph = true;
     return FIRE_OK;
@@ -418,7 +489,16 @@ fire_status fire_init(fire_handle_t** hp, const fire_system_t* sys, const fire_p
         c.rs = pot->rs;
         c.rc = pot->rc;
         c.winv = 1.0 / (pot->rc - pot->rs);
+        // exponent arguments -p s and -2q s with s in [-1, rc/r0 - 1]
+        const double smax = std::max(1.0, pot->rc / pot->r0 - 1.0);
+        if (!(std::fabs(pot->p) * smax < 700.0 && std::fabs(2.0 * pot->q) * smax < 700.0)) {
+            g_init_err = "RGL exponents p, q too large for the exponential's range";
+            delete h;
+            return FIRE_ERR_ARG;
+        }
     }
+    double exp_table_host[kExpTableSize];
+    h->potc.ex = make_exp_constants(exp_table_host);
 
     auto bail = [&](fire_status s) {
         g_init_err = h->err;
@@ -446,6 +526,13 @@ fire_status fire_init(fire_handle_t** hp, const fire_system_t* sys, const fire_p
     CKI(cudaMalloc(&b.v, n * sizeof(dvec4)));
     CKI(cudaMalloc(&b.f, n * sizeof(dvec4)));
     CKI(cudaMalloc(&b.xref, n * sizeof(dvec4)));
+    CKI(cudaMalloc(&b.xf, n * sizeof(float4)));
+    {
+        double* t = nullptr;
+        CKI(cudaMalloc(&t, kExpTableSize * sizeof(double)));
+        b.exp_table = t;
+        CKI(cudaMemcpy(t, exp_table_host, kExpTableSize * sizeof(double), cudaMemcpyHostToDevice));
+    }
     CKI(cudaMalloc(&b.nnbr, n * sizeof(int)));
     CKI(cudaMalloc(&b.cell_of, n * sizeof(int)));
     CKI(cudaMalloc(&b.cell_atoms, n * sizeof(int)));
@@ -470,7 +557,7 @@ void fire_destroy(fire_handle_t* h) {
     if (h->stream) cudaStreamSynchronize(h->stream);
     drop_graph(h);
     Bufs& b = h->b;
-    void* ptrs[] = {b.x, b.v, b.f, b.xref, b.rho, b.fp, b.nbr, b.nnbr, b.crep, b.cden,
+    void* ptrs[] = {b.x, b.v, b.f, b.xref, b.xf, (void*)b.exp_table, b.rho, b.fp, b.nbr, b.nnbr, b.crep, b.cden,
                     b.cell_of, b.cell_count, b.cell_start, b.cell_atoms, b.epart, b.rpart,
                     b.st, b.pos_io};
     for (void* p : ptrs)
@@ -497,16 +584,42 @@ fire_status fire_set_time_budget(fire_handle_t* h, double seconds) {
 // One relaxation on the device: positions are already in b.pos_io.
 static fire_status run_minimize(fire_handle* h, const GeoC& g, double ftol, int64_t maxiter,
                                 cudaStream_t s) {
-    if (!h->has_graph || !same_geo(h->gkey, g)) {
-        fire_status st = build_graph(h, g);
+    const bool chunked = h->exec_mode == FIRE_EXEC_CHUNKED;
+    const bool have = chunked ? h->exec_chunk != nullptr : h->exec != nullptr;
+    if (!h->has_graph || !have || !same_geo(h->gkey, g)) {
+        fire_status st = chunked ? build_chunked(h, g) : build_graph(h, g);
         if (st != FIRE_OK) return st;
     }
     init_state(h, ftol, maxiter);
     CK(h, cudaMemcpyAsync(h->b.st, h->h_state, sizeof(DevState), cudaMemcpyHostToDevice, s));
-    CK(h, cudaGraphLaunch(h->exec, s));
+    if (!chunked) {
+        CK(h, cudaGraphLaunch(h->exec, s));
+    } else {
+        CK(h, cudaGraphLaunch(h->exec_init, s));
+        const long long max_chunks = maxiter / h->chunk + 2;
+        for (long long c = 0; c < max_chunks; ++c) {
+            CK(h, cudaMemcpyAsync(h->h_state, h->b.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+            CK(h, cudaStreamSynchronize(s));
+            if (h->h_state->done) break;
+            CK(h, cudaGraphLaunch(h->exec_chunk, s));
+        }
+        CK(h, cudaGraphLaunch(h->exec_final, s));
+    }
     CK(h, cudaMemcpyAsync(h->h_state, h->b.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
     CK(h, cudaStreamSynchronize(s));
     return status_to_error(h, h->h_state->status);
+}
+
+fire_status fire_set_exec_mode(fire_handle_t* h, int32_t mode, int32_t chunk) {
+    if (!h) return FIRE_ERR_ARG;
+    if (mode != FIRE_EXEC_GRAPH_WHILE && mode != FIRE_EXEC_CHUNKED)
+        return fail(h, FIRE_ERR_ARG, "unknown execution mode %d", mode);
+    if (mode == FIRE_EXEC_CHUNKED && (chunk < 1 || chunk > 4096))
+        return fail(h, FIRE_ERR_ARG, "chunk must be in [1, 4096]");
+    drop_graph(h);
+    h->exec_mode = mode;
+    if (mode == FIRE_EXEC_CHUNKED) h->chunk = chunk;
+    return FIRE_OK;
 }
 
 fire_status fire_minimize_dev(fire_handle_t* h, double* d_pos, const double box[3], double ftol,

@@ -17,6 +17,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "fire2_math.cuh"
+
 namespace fire2 {
 
 // Per-atom 3-vectors live in 32-byte aligned, zero-padded double quads so a
@@ -46,6 +48,7 @@ struct PotC {
     double eps, sigma2, lj_shift;
     // RGL
     double A, xi2, p, q2, r0inv, p_r0, q2_r0, rs, rc, winv;
+    ExpC ex;               // constants of the table-driven exponential
 };
 
 // Box / neighbour geometry, passed by value.
@@ -57,6 +60,9 @@ struct GeoC {
     int brute;             // 1 = all-pairs list build (small or open boxes)
     double rlist2;         // (rc + skin)^2
     double half_skin2;     // (skin / 2)^2
+    // FP32 copies for the list build's candidate test
+    float Lf[3], Linvf[3];
+    float rlist2f;         // (rc + skin + margin)^2, margin covers FP32 rounding
 };
 
 // FIRE parameters (Table 1) and call arguments, device resident.
@@ -75,6 +81,7 @@ struct DevState {
     double P, F2, V2, fmax2, finf, energy;
     // update coefficients for the next k_update (see k_control)
     int zero_v, mix, pad2, pad3;
+    double dtm;                              // dt / m of the next kick
     double halfstep, dt_cur, mix_a, mix_fv;  // x -= halfstep*v; v' = v + dt*F/m;
                                              // v = (1-a) v' + a*|v'|*F/|F| when mix
     unsigned long long max_disp2;           // bits of max |x - x_ref|^2 (>= 0)
@@ -84,7 +91,9 @@ struct Bufs {
     int n, cap, ncell;
     int nb_force, nb_embed, nb_red;
     dvec4 *x, *v, *f, *xref;
+    float4* xf;            // FP32 copy of x for the list build
     double *rho, *fp;
+    const double* exp_table;  // 2^(j/256), j = 0..255
     uint32_t *nbr;
     int *nnbr;
     double *crep, *cden;
@@ -183,6 +192,7 @@ __global__ void k_prepare(Bufs b) {
     const double* p = b.pos_io + 3 * (size_t)i;
     if (!isfinite(p[0]) || !isfinite(p[1]) || !isfinite(p[2])) set_status(b.st, ST_NONFINITE);
     b.x[i] = make_dvec4(p[0], p[1], p[2], 0.0);
+    b.xf[i] = make_float4((float)p[0], (float)p[1], (float)p[2], 0.f);
     b.v[i] = make_dvec4(0.0, 0.0, 0.0, 0.0);
     b.f[i] = make_dvec4(0.0, 0.0, 0.0, 0.0);
     if (b.rho) b.rho[i] = 0.0;
@@ -268,25 +278,30 @@ __global__ void k_cell_fill(Bufs b, GeoC g, int force) {
 }
 
 // Upper half-space test on the minimum-image vector d = x_j - x_i: exactly
-// one of (i, j) and (j, i) passes because IEEE subtraction is sign-symmetric.
-__device__ __forceinline__ bool upper_half(double dx, double dy, double dz) {
-    return dz > 0.0 || (dz == 0.0 && (dy > 0.0 || (dy == 0.0 && dx > 0.0)));
+// one of (i, j) and (j, i) passes because IEEE subtraction, rounding to the
+// nearest integer and the squares are all symmetric under d -> -d.
+__device__ __forceinline__ bool upper_half(float dx, float dy, float dz) {
+    return dz > 0.f || (dz == 0.f && (dy > 0.f || (dy == 0.f && dx > 0.f)));
 }
 
-__device__ __forceinline__ void try_add_pair(const Bufs& b, const GeoC& g, int i, dvec4 xi,
+// Candidate test in FP32 (the FP64 unit is ~58x slower on this part): the
+// list radius carries a margin larger than the FP32 rounding of the
+// positions, so every pair closer than rc + skin is kept; the force kernels
+// test r < rc again in FP64.
+__device__ __forceinline__ void try_add_pair(const Bufs& b, const GeoC& g, int i, float4 xi,
                                              int j, int& cnt) {
-    const dvec4 xj = b.x[j];
-    double d[3] = {xj.x - xi.x, xj.y - xi.y, xj.z - xi.z};
+    const float4 xj = b.xf[j];
+    float d[3] = {xj.x - xi.x, xj.y - xi.y, xj.z - xi.z};
     int s[3] = {0, 0, 0};
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         if (g.per[a]) {
-            s[a] = (int)rint(d[a] * g.Linv[a]);
-            d[a] -= s[a] * g.L[a];
+            s[a] = __float2int_rn(d[a] * g.Linvf[a]);
+            d[a] -= (float)s[a] * g.Lf[a];
         }
     }
-    const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-    if (!(r2 < g.rlist2) || !upper_half(d[0], d[1], d[2])) return;  // NaN fails too
+    const float r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    if (!(r2 < g.rlist2f) || !upper_half(d[0], d[1], d[2])) return;  // NaN fails too
     // image codes cover shifts of -2..2 box lengths; atoms further apart than
     // that in raw coordinates are a caller error (positions far outside the box)
     if (s[0] < -2 || s[0] > 2 || s[1] < -2 || s[1] > 2 || s[2] < -2 || s[2] > 2) {
@@ -306,10 +321,11 @@ __global__ void k_nbr_build(Bufs b, GeoC g, int force) {
     if (i == 0) b.st->nbr_builds += 1;
     if (i >= b.n) return;
     const dvec4 xi = b.x[i];
+    const float4 xif = b.xf[i];
     int cnt = 0;
     if (g.brute) {
         for (int j = 0; j < b.n; ++j)
-            if (j != i) try_add_pair(b, g, i, xi, j, cnt);
+            if (j != i) try_add_pair(b, g, i, xif, j, cnt);
     } else {
         const int cx = cell_coord(xi.x, g.Linv[0], g.nc[0]);
         const int cy = cell_coord(xi.y, g.Linv[1], g.nc[1]);
@@ -323,7 +339,7 @@ __global__ void k_nbr_build(Bufs b, GeoC g, int force) {
                     const int c = (ax * g.nc[1] + ay) * g.nc[2] + az;
                     for (int k = b.cell_start[c]; k < b.cell_start[c + 1]; ++k) {
                         const int j = b.cell_atoms[k];
-                        if (j != i) try_add_pair(b, g, i, xi, j, cnt);
+                        if (j != i) try_add_pair(b, g, i, xif, j, cnt);
                     }
                 }
             }
@@ -344,8 +360,11 @@ __global__ void k_nbr_build(Bufs b, GeoC g, int force) {
 // cache of (2 phi'(r)/r, g'(r)/r) for pass 2.
 __global__ void __launch_bounds__(kForceBlock) k_density(Bufs b, PotC P, GeoC g) {
     __shared__ double3 tbl[125];
+    __shared__ double etab[kExpTableSize];
     __shared__ double red[32];
+    if (b.st->done) return;
     fill_shift_table(tbl, g);
+    for (int t = threadIdx.x; t < kExpTableSize; t += blockDim.x) etab[t] = b.exp_table[t];
     __syncthreads();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     double erep = 0.0;
@@ -369,10 +388,11 @@ __global__ void __launch_bounds__(kForceBlock) k_density(Bufs b, PotC P, GeoC g)
             const double r2 = dx * dx + dy * dy + dz * dz;
             double crep = 0.0, cden = 0.0;
             if (r2 < P.rc2) {
-                const double r = sqrt(r2);
+                const double rinv = rsqrt(r2);
+                const double r = r2 * rinv;
                 const double s = r * P.r0inv - 1.0;
-                const double ep = P.A * exp(-P.p * s);
-                const double eq = P.xi2 * exp(-P.q2 * s);
+                const double ep = P.A * exp_tang(-P.p * s, P.ex, etab);
+                const double eq = P.xi2 * exp_tang(-P.q2 * s, P.ex, etab);
                 double S = 1.0, dS = 0.0;
                 if (r > P.rs) {
                     const double t = (r - P.rs) * P.winv;
@@ -384,7 +404,6 @@ __global__ void __launch_bounds__(kForceBlock) k_density(Bufs b, PotC P, GeoC g)
                 rho_i += gg;
                 atomicAdd(&b.rho[j], gg);
                 erep += 2.0 * ep * S;
-                const double rinv = 1.0 / r;
                 crep = 2.0 * ep * (-P.p_r0 * S + dS) * rinv;
                 cden = eq * (-P.q2_r0 * S + dS) * rinv;
             }
@@ -401,6 +420,7 @@ __global__ void __launch_bounds__(kForceBlock) k_density(Bufs b, PotC P, GeoC g)
 // rho = 0 has no pair inside rc, so its F' is never used (set to 0).
 __global__ void k_embed(Bufs b) {
     __shared__ double red[32];
+    if (b.st->done) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     double emb = 0.0;
     if (i < b.n) {
@@ -417,6 +437,7 @@ __global__ void k_embed(Bufs b) {
 // and d = x_j - x_i (F = -grad E, Sec. 2.1).
 __global__ void __launch_bounds__(kForceBlock) k_force_rgl(Bufs b, GeoC g) {
     __shared__ double3 tbl[125];
+    if (b.st->done) return;
     fill_shift_table(tbl, g);
     __syncthreads();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -428,7 +449,8 @@ __global__ void __launch_bounds__(kForceBlock) k_force_rgl(Bufs b, GeoC g) {
     for (int k = 0; k < m; ++k) {
         const size_t slot = (size_t)k * b.n + i;
         const double crep = b.crep[slot], cden = b.cden[slot];
-        if (crep == 0.0 && cden == 0.0) continue;
+        // pairs beyond rc carry an all-zero cache entry (integer test, no FP64 op)
+        if ((__double_as_longlong(crep) | __double_as_longlong(cden)) == 0) continue;
         const uint32_t e = b.nbr[slot];
         const int j = (int)(e & kIdxMask);
         const int code = (int)(e >> kIdxBits);
@@ -458,6 +480,7 @@ __global__ void __launch_bounds__(kForceBlock) k_force_rgl(Bufs b, GeoC g) {
 __global__ void __launch_bounds__(kForceBlock) k_force_lj(Bufs b, PotC P, GeoC g) {
     __shared__ double3 tbl[125];
     __shared__ double red[32];
+    if (b.st->done) return;
     fill_shift_table(tbl, g);
     __syncthreads();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -504,6 +527,7 @@ __global__ void __launch_bounds__(kForceBlock) k_force_lj(Bufs b, PotC P, GeoC g
 // the mixing of Alg. 4) and the per-atom / per-component force maxima (Sec. 3.4).
 __global__ void k_reduce(Bufs b) {
     __shared__ double red[32];
+    if (b.st->done) return;
     double P = 0.0, F2 = 0.0, V2 = 0.0, fa2 = 0.0, fin = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < b.n; i += gridDim.x * blockDim.x) {
         const dvec4 f = b.f[i], v = b.v[i];
@@ -548,6 +572,11 @@ __device__ double ctl_max(const double* a, int cnt, double* sh) {
 // It writes the coefficients k_update applies and sets the WHILE condition.
 __global__ void k_control(Bufs b, int mode, cudaGraphConditionalHandle h, int has_handle) {
     __shared__ double sh[32];
+    // chunked execution runs loop bodies past the stop; they must not count
+    if (mode == CTL_LOOP && b.st->done) {
+        if (has_handle && threadIdx.x == 0) cudaGraphSetConditional(h, 0u);
+        return;
+    }
     const double P = ctl_sum(b.rpart + 0 * b.nb_red, b.nb_red, sh);
     const double F2 = ctl_sum(b.rpart + 1 * b.nb_red, b.nb_red, sh);
     const double V2 = ctl_sum(b.rpart + 2 * b.nb_red, b.nb_red, sh);
@@ -565,7 +594,6 @@ __global__ void k_control(Bufs b, int mode, cudaGraphConditionalHandle h, int ha
     s.max_disp2 = 0ull;
     if (mode == CTL_EVAL) {
         if ((!isfinite(E) || !isfinite(F2)) && s.status == ST_OK) s.status = ST_NONFINITE;
-        s.done = 1;
         return;
     }
     s.evals += 1;
@@ -624,6 +652,7 @@ __global__ void k_control(Bufs b, int mode, cudaGraphConditionalHandle h, int ha
                 }
             }
             s.dt_cur = s.dt;
+            s.dtm = s.dt / s.mass;
         }
     }
     s.done = stop ? 1 : 0;
@@ -637,8 +666,9 @@ __global__ void k_control(Bufs b, int mode, cudaGraphConditionalHandle h, int ha
 __global__ void k_update(Bufs b) {
     __shared__ double red[32];
     const DevState& s = *b.st;
+    if (s.done) return;
     const int zero_v = s.zero_v, mix = s.mix;
-    const double hs = s.halfstep, dt = s.dt_cur, m = s.mass;
+    const double hs = s.halfstep, dt = s.dt_cur, dtm = s.dtm;
     const double a = s.mix_a, fv = s.mix_fv;
     double dmax = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < b.n; i += gridDim.x * blockDim.x) {
@@ -650,9 +680,9 @@ __global__ void k_update(Bufs b) {
             x.z -= hs * v.z;
             v = make_dvec4(0.0, 0.0, 0.0, 0.0);
         }
-        v.x += dt * f.x / m;
-        v.y += dt * f.y / m;
-        v.z += dt * f.z / m;
+        v.x += dtm * f.x;
+        v.y += dtm * f.y;
+        v.z += dtm * f.z;
         if (mix) {
             v.x = (1.0 - a) * v.x + a * fv * f.x;
             v.y = (1.0 - a) * v.y + a * fv * f.y;
@@ -662,6 +692,7 @@ __global__ void k_update(Bufs b) {
         x.y += dt * v.y;
         x.z += dt * v.z;
         b.x[i] = x;
+        b.xf[i] = make_float4((float)x.x, (float)x.y, (float)x.z, 0.f);
         b.v[i] = v;
         b.f[i] = make_dvec4(0.0, 0.0, 0.0, 0.0);
         if (b.rho) b.rho[i] = 0.0;

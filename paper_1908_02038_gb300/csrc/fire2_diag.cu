@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include "fire2.h"
+#include "fire2_math.cuh"
 
 namespace {
 
@@ -43,7 +44,34 @@ cudaError_t time_fma(int sms, int iters, double* ms) {
     return e;
 }
 
+__global__ void k_exp_tang(int64_t n, const double* x, double* out, const double* table,
+                           fire2::ExpC c) {
+    __shared__ double tbl[fire2::kExpTableSize];
+    for (int t = threadIdx.x; t < fire2::kExpTableSize; t += blockDim.x) tbl[t] = table[t];
+    __syncthreads();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = fire2::exp_tang(x[i], c, tbl);
+}
+
 }  // namespace
+
+extern "C" fire_status fire_diag_exp(int64_t n, const double* d_x, double* d_out, void* stream) {
+    if (n < 0 || (n > 0 && (!d_x || !d_out))) return FIRE_ERR_ARG;
+    if (n == 0) return FIRE_OK;
+    double host_table[fire2::kExpTableSize];
+    const fire2::ExpC c = fire2::make_exp_constants(host_table);
+    double* d_table = nullptr;
+    if (cudaMalloc(&d_table, sizeof host_table) != cudaSuccess) return FIRE_ERR_NOMEM;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(d_table, host_table, sizeof host_table, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+        k_exp_tang<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, d_x, d_out, d_table, c);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(d_table);
+    return e == cudaSuccess ? FIRE_OK : FIRE_ERR_CUDA;
+}
 
 extern "C" fire_status fire_diag_fma_peak(int32_t which, double* flops_per_s) {
     if (!flops_per_s || (which != 0 && which != 1)) return FIRE_ERR_ARG;

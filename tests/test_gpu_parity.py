@@ -284,3 +284,33 @@ def test_graph_reuse_and_box_change():
         e3, f3 = h.energy_forces(x3, box2)
     eo, fo = oracle.energy_forces(x3, box2, ora_rgl())
     assert force_rel_err(f3, fo) < F_REL
+
+
+def test_table_exponential_against_libm():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(0)
+    x = np.concatenate([rng.uniform(-30.0, 12.0, 200000), np.linspace(-1, 1, 20001),
+                        [0.0, -0.0, 1e-300, -1e-17, np.log(2.0), -np.log(2.0), 11.0, -25.0]])
+    d_x = torch.tensor(x, dtype=torch.float64, device="cuda")
+    d_y = torch.empty_like(d_x)
+    fg.fire_diag_exp(d_x, d_y)
+    torch.cuda.synchronize()
+    y = d_y.cpu().numpy()
+    rel = np.abs(y - np.exp(x)) / np.exp(x)
+    assert rel.max() < 4.5e-16, rel.max()       # within 2 ulp of the libm value
+    assert y[np.flatnonzero(x == 0.0)].tolist() == [1.0, 1.0]
+
+
+def test_chunked_execution_matches_graph_loop():
+    c = fi.rgl_vacancy_box(ncell=5, seed=12, n_vac=2)
+    with fg.FireHandle(c.n, fi.CU_MASS, rgl_pot(), dt_start=fi.CU_DT) as h:
+        x1 = c.x.copy()
+        r1 = h.minimize(x1, c.box, 1e-6, 100000)
+        h.set_exec_mode(fg.FIRE_EXEC_CHUNKED, 7)
+        x2 = c.x.copy()
+        r2 = h.minimize(x2, c.box, 1e-6, 100000)
+        r3 = h.minimize(c.x.copy(), c.box, 1e-6, 50)
+    assert r2.stop == r1.stop == fg.FIRE_STOP_FTOL
+    assert abs(r1.iterations - r2.iterations) <= max(2, 0.05 * r1.iterations)
+    assert abs(r1.energy - r2.energy) / c.n < 1e-10
+    assert r3.stop == fg.FIRE_STOP_MAXITER and r3.iterations == 50 and r3.force_evals == 51
