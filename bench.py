@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--config", default="rgl1m", choices=sorted(CONFIGS))
-    ap.add_argument("--form", default="fp64", choices=["fp64"])
+    ap.add_argument("--form", default="fp64", choices=["fp64", "fp32pair"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--exec", default="graph", choices=["graph", "chunked"],
                     help="graph: one CUDA graph with a WHILE node per relaxation (default); "
@@ -76,12 +76,14 @@ def dist_env():
     return rank, world, local
 
 
-def potential_for(cfg_name):
+def potential_for(cfg_name, form="fp64"):
     import paper_1908_02038_gb300 as fg
     if cfg_name.startswith("lj"):
         return (fg.Potential(fg.FIRE_POT_LJ, eps=1.0, sigma=1.0, rc_lj=2.5, skin=0.3),
                 fi.LJ_MASS, fi.LJ_DT, 1e-8)
-    return fg.Potential(fg.FIRE_POT_RGL, skin=0.3, **fi.RGL_CU), fi.CU_MASS, fi.CU_DT, FTOL
+    prec = fg.FIRE_PREC_FP32_PAIR if form == "fp32pair" else fg.FIRE_PREC_FP64
+    return (fg.Potential(fg.FIRE_POT_RGL, precision=prec, skin=0.3, **fi.RGL_CU), fi.CU_MASS,
+            fi.CU_DT, FTOL)
 
 
 def count_pairs(x, box, rc):
@@ -174,7 +176,7 @@ def run_gpu(args):
     fg.load_library()
 
     cfg = CONFIGS[args.config]()
-    pot, mass, dt, ftol = potential_for(args.config)
+    pot, mass, dt, ftol = potential_for(args.config, args.form)
     n = cfg.n
     dev = torch.device("cuda", local)
     x0 = torch.tensor(cfg.x, dtype=torch.float64, device=dev)
@@ -227,7 +229,8 @@ def run_gpu(args):
     rc = pot.rc if is_rgl else pot.rc_lj
     cell_mode = all(np.floor(np.asarray(cfg.box) / (rc + pot.skin)) >= 3)
     build_k = 5 if cell_mode else 1
-    force_k = 3 if is_rgl else 1
+    fp32 = args.form == "fp32pair"
+    force_k = (2 if fp32 else 3) if is_rgl else 1
     # kernels per iteration: update, list-build chain (gated), force passes,
     # reduce, control; per call: prepare + build + forces + reduce + control + finalize
     per_iter = 1 + build_k + force_k + 2
@@ -236,7 +239,8 @@ def run_gpu(args):
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32-pair/f64" if fp32 else "f64", "data": "synthetic",
            "config": {"workload": f"{cfg.name} ({n} atoms), FIRE2 + semi-implicit Euler to "
                                   f"max|F_i| < {ftol:g}",
                       "atoms": n, "ftol": ftol, "form": args.form, "skin": pot.skin,
@@ -254,15 +258,21 @@ def run_gpu(args):
     dom = "density" if is_rgl and stages["density"] >= stages["force"] else "force"
     pairs = count_pairs(cfg.x, cfg.box, np.sqrt(pot.rc ** 2 if is_rgl else pot.rc_lj ** 2))
     key = dom if is_rgl else "force_lj"
-    flop = ALG_FLOP_PER_PAIR[key] * pairs
+    # the FP32-pair form walks a full list: every pair is evaluated from both ends
+    evals = pairs * (2 if fp32 else 1)
+    flop = ALG_FLOP_PER_PAIR[key] * evals
     achieved = flop / (stages[dom] * 1e-3)
-    peak64 = fg.fire_diag_fma_peak(0)
-    kname = {"density": "k_density", "force": "k_force_rgl" if is_rgl else "k_force_lj"}[dom]
+    peak = fg.fire_diag_fma_peak(1 if fp32 else 0)
+    if fp32:
+        kname = {"density": "k_density32", "force": "k_force32"}[dom]
+    else:
+        kname = {"density": "k_density", "force": "k_force_rgl" if is_rgl else "k_force_lj"}[dom]
     out["roofline"] = {"bound": "alu", "kernel": kname, "achieved": achieved / 1e12,
-                       "peak": peak64 / 1e12, "unit": "TFLOP/s",
-                       "frac": achieved / peak64, "traffic": read_traffic(kname),
-                       "peak_source": "measured FP64 FMA issue rate (fire_diag_fma_peak)",
-                       "stage_ms": stages, "pairs_within_rc": pairs}
+                       "peak": peak / 1e12, "unit": "TFLOP/s",
+                       "frac": achieved / peak, "traffic": read_traffic(kname),
+                       "peak_source": ("measured %s FMA issue rate (fire_diag_fma_peak)"
+                                       % ("FP32" if fp32 else "FP64")),
+                       "stage_ms": stages, "pairs_within_rc": pairs, "pair_evaluations": evals}
     # HBM roofline of the whole iteration, as the metric asks
     alg_b = ALG_BYTES_PER_ATOM_ITER["rgl" if is_rgl else "lj"]
     hbm = None

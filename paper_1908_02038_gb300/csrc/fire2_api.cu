@@ -104,6 +104,9 @@ GeoC make_geo(const fire_handle* h, const double box[3]) {
     // magnitude (positions stay within about one box length of the box)
     const double margin = 1e-3 * rc + 8.0 * 1.2e-7 * (2.0 * lmax);
     g.rlist2f = (float)((rl + margin) * (rl + margin));
+    g.full = h->pot.precision == FIRE_PREC_FP32_PAIR ? 1 : 0;
+    for (int a = 0; a < 3; ++a)
+        g.Lq[a] = (int)(unsigned)(unsigned long long)std::llrint(box[a] * h->b.qscale);
     return g;
 }
 
@@ -114,7 +117,7 @@ int estimate_cap(const fire_handle* h, const GeoC& g) {
     const double dens = h->n / vol;
     const double rl = std::sqrt(g.rlist2);
     const double half = 2.0 / 3.0 * M_PI * rl * rl * rl * dens;
-    long long cap = (long long)std::ceil(1.5 * half) + 16;
+    long long cap = (long long)std::ceil(1.5 * half * (g.full ? 2.0 : 1.0)) + 16;
     cap = std::min<long long>(cap, std::max(h->n - 1, 1));
     return (int)std::max<long long>(cap, 1);
 }
@@ -142,7 +145,7 @@ fire_status ensure_buffers(fire_handle* h, const GeoC& g, int cap) {
         h->b.crep = h->b.cden = nullptr;
         const size_t slots = (size_t)cap * h->n;
         CK(h, cudaMalloc(&h->b.nbr, slots * sizeof(uint32_t)));
-        if (h->pot.kind == FIRE_POT_RGL) {
+        if (h->pot.kind == FIRE_POT_RGL && h->pot.precision == FIRE_PREC_FP64) {
             CK(h, cudaMalloc(&h->b.crep, slots * sizeof(double)));
             CK(h, cudaMalloc(&h->b.cden, slots * sizeof(double)));
         }
@@ -178,7 +181,10 @@ void launch_build(fire_handle* h, const GeoC& g, int force, cudaStream_t s) {
 
 void launch_forces(fire_handle* h, const GeoC& g, cudaStream_t s) {
     const int n = h->n;
-    if (h->pot.kind == FIRE_POT_RGL) {
+    if (h->pot.kind == FIRE_POT_RGL && h->pot.precision == FIRE_PREC_FP32_PAIR) {
+        k_density32<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
+        k_force32<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
+    } else if (h->pot.kind == FIRE_POT_RGL) {
         k_density<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
         k_embed<<<h->b.nb_embed, kElemBlock, 0, s>>>(h->b);
         k_force_rgl<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, g);
@@ -448,8 +454,11 @@ fire_status fire_init(fire_handle_t** hp, const fire_system_t* sys, const fire_p
     if (!(sys->mass > 0.0) || !std::isfinite(sys->mass)) return fail(nullptr, FIRE_ERR_ARG, "mass must be > 0");
     if (pot->kind != FIRE_POT_LJ && pot->kind != FIRE_POT_RGL)
         return fail(nullptr, FIRE_ERR_ARG, "unknown potential kind %d", pot->kind);
-    if (pot->precision != FIRE_PREC_FP64)
-        return fail(nullptr, FIRE_ERR_ARG, "precision %d not available", pot->precision);
+    if (pot->precision != FIRE_PREC_FP64 &&
+        !(pot->precision == FIRE_PREC_FP32_PAIR && pot->kind == FIRE_POT_RGL))
+        return fail(nullptr, FIRE_ERR_ARG,
+                    "precision %d not available for this potential (FP32-pair is RGL only)",
+                    pot->precision);
     if (!(pot->skin >= 0.0)) return fail(nullptr, FIRE_ERR_ARG, "skin must be >= 0");
     if (pot->kind == FIRE_POT_LJ && !(pot->rc_lj > 0.0 && pot->sigma > 0.0 && pot->eps > 0.0))
         return fail(nullptr, FIRE_ERR_ARG, "LJ needs eps, sigma, rc_lj > 0");
@@ -499,6 +508,30 @@ fire_status fire_init(fire_handle_t** hp, const fire_system_t* sys, const fire_p
     }
     double exp_table_host[kExpTableSize];
     h->potc.ex = make_exp_constants(exp_table_host);
+    float exp32_table_host[kExp32TableSize];
+    h->potc.ex32 = make_exp32_constants(exp32_table_host);
+    const bool fp32pair = pot->precision == FIRE_PREC_FP32_PAIR;
+    if (fp32pair) {
+        // fixed-point scale: a power of two with (rc + 3 skin + 2) * qscale < 2^31,
+        // so every list pair's separation and r^2 fit their integer types
+        const double span = pot->rc + 3.0 * pot->skin + 2.0;
+        const int k = (int)std::floor(std::log2(2147483648.0 / span));
+        h->b.qscale = std::ldexp(1.0, k);
+        c.A_f = (float)pot->A;
+        c.xi2_f = (float)(pot->xi * pot->xi);
+        c.p_f = (float)pot->p;
+        c.q2_f = (float)(2.0 * pot->q);
+        c.r0_f = (float)pot->r0;
+        c.p_r0_f = (float)(pot->p / pot->r0);
+        c.q2_r0_f = (float)(2.0 * pot->q / pot->r0);
+        c.rs_f = (float)pot->rs;
+        c.winv_f = (float)(1.0 / (pot->rc - pot->rs));
+        const double q2 = h->b.qscale * h->b.qscale;
+        c.rc2q = (long long)std::floor(pot->rc * pot->rc * q2);
+        c.r0sq_q = std::llrint(pot->r0 * pot->r0 * q2);
+        c.qinv = (float)(1.0 / h->b.qscale);
+        c.qinv2 = (float)(1.0 / q2);
+    }
 
     auto bail = [&](fire_status s) {
         g_init_err = h->err;
@@ -520,13 +553,21 @@ fire_status fire_init(fire_handle_t** hp, const fire_system_t* sys, const fire_p
     Bufs& b = h->b;
     b.n = h->n;
     b.nb_force = ceil_div(h->n, kForceBlock);
-    b.nb_embed = pot->kind == FIRE_POT_RGL ? ceil_div(h->n, kElemBlock) : 0;
+    b.nb_embed = (pot->kind == FIRE_POT_RGL && !fp32pair) ? ceil_div(h->n, kElemBlock) : 0;
     b.nb_red = std::max(1, std::min(ceil_div(h->n, kElemBlock), 152 * 4));
     CKI(cudaMalloc(&b.x, n * sizeof(dvec4)));
     CKI(cudaMalloc(&b.v, n * sizeof(dvec4)));
     CKI(cudaMalloc(&b.f, n * sizeof(dvec4)));
     CKI(cudaMalloc(&b.xref, n * sizeof(dvec4)));
     CKI(cudaMalloc(&b.xf, n * sizeof(float4)));
+    if (fp32pair) {
+        CKI(cudaMalloc(&b.xq, n * sizeof(int4)));
+        CKI(cudaMalloc(&b.fp32, n * sizeof(float)));
+        float* t = nullptr;
+        CKI(cudaMalloc(&t, kExp32TableSize * sizeof(float)));
+        b.exp32_table = t;
+        CKI(cudaMemcpy(t, exp32_table_host, kExp32TableSize * sizeof(float), cudaMemcpyHostToDevice));
+    }
     {
         double* t = nullptr;
         CKI(cudaMalloc(&t, kExpTableSize * sizeof(double)));
@@ -557,7 +598,8 @@ void fire_destroy(fire_handle_t* h) {
     if (h->stream) cudaStreamSynchronize(h->stream);
     drop_graph(h);
     Bufs& b = h->b;
-    void* ptrs[] = {b.x, b.v, b.f, b.xref, b.xf, (void*)b.exp_table, b.rho, b.fp, b.nbr, b.nnbr, b.crep, b.cden,
+    void* ptrs[] = {b.x, b.v, b.f, b.xref, b.xf, b.xq, b.fp32, (void*)b.exp32_table,
+                    (void*)b.exp_table, b.rho, b.fp, b.nbr, b.nnbr, b.crep, b.cden,
                     b.cell_of, b.cell_count, b.cell_start, b.cell_atoms, b.epart, b.rpart,
                     b.st, b.pos_io};
     for (void* p : ptrs)
@@ -759,15 +801,18 @@ fire_status fire_profile_stages(fire_handle_t* h, const double* pos, const doubl
     for (auto& e : ev) CK(h, cudaEventCreate(&e));
     double acc[FIRE_NSTAGES] = {0};
     const bool rgl = h->pot.kind == FIRE_POT_RGL;
+    const bool f32 = h->pot.precision == FIRE_PREC_FP32_PAIR;
     for (int r = 0; r <= reps; ++r) {
         cudaEventRecord(ev[0], s);
         launch_build(h, g, 1, s);
         cudaEventRecord(ev[1], s);
-        if (rgl) k_density<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
+        if (rgl && f32) k_density32<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
+        else if (rgl) k_density<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
         cudaEventRecord(ev[2], s);
-        if (rgl) k_embed<<<h->b.nb_embed, kElemBlock, 0, s>>>(h->b);
+        if (rgl && !f32) k_embed<<<h->b.nb_embed, kElemBlock, 0, s>>>(h->b);
         cudaEventRecord(ev[3], s);
-        if (rgl) k_force_rgl<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, g);
+        if (rgl && f32) k_force32<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
+        else if (rgl) k_force_rgl<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, g);
         else k_force_lj<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
         cudaEventRecord(ev[4], s);
         launch_reduce(h, s);

@@ -49,6 +49,11 @@ struct PotC {
     // RGL
     double A, xi2, p, q2, r0inv, p_r0, q2_r0, rs, rc, winv;
     ExpC ex;               // constants of the table-driven exponential
+    // FP32-pair form: FP32 copies of the constants; r^2 tests in fixed point
+    Exp32C ex32;
+    float A_f, xi2_f, p_f, q2_f, r0_f, p_r0_f, q2_r0_f, rs_f, winv_f;
+    long long rc2q, r0sq_q;   // rc^2 and r0^2 in (fixed-point unit)^2
+    float qinv, qinv2;        // 1 / qscale, 1 / qscale^2
 };
 
 // Box / neighbour geometry, passed by value.
@@ -63,6 +68,8 @@ struct GeoC {
     // FP32 copies for the list build's candidate test
     float Lf[3], Linvf[3];
     float rlist2f;         // (rc + skin + margin)^2, margin covers FP32 rounding
+    int full;              // 1 = full list (both directions), 0 = half list
+    int Lq[3];             // box lengths in fixed-point units, modulo 2^32
 };
 
 // FIRE parameters (Table 1) and call arguments, device resident.
@@ -92,6 +99,10 @@ struct Bufs {
     int nb_force, nb_embed, nb_red;
     dvec4 *x, *v, *f, *xref;
     float4* xf;            // FP32 copy of x for the list build
+    int4* xq;              // FP32-pair form: x in fixed point (qscale units), modulo 2^32
+    float* fp32;           // FP32-pair form: F'(rho_i)
+    const float* exp32_table;
+    double qscale;         // fixed-point units per length unit (a power of two)
     double *rho, *fp;
     const double* exp_table;  // 2^(j/256), j = 0..255
     uint32_t *nbr;
@@ -178,6 +189,16 @@ __device__ __forceinline__ bool need_rebuild(const DevState* st, const GeoC& g, 
     return __longlong_as_double((long long)st->max_disp2) > g.half_skin2;
 }
 
+// Fixed-point coordinate (units of 1/qscale) modulo 2^32.  Differences of two
+// such values, taken in 32-bit wrap-around arithmetic, are exact whenever the
+// true separation is below 2^31 / qscale (qscale is chosen so that every list
+// pair qualifies), whatever periodic image the raw coordinates sit in.
+__device__ __forceinline__ int to_fixed(double x, double qscale) {
+    return (int)(unsigned)(unsigned long long)__double2ll_rn(x * qscale);
+}
+
+__device__ __forceinline__ int wrap_sub(int a, int b) { return (int)((unsigned)a - (unsigned)b); }
+
 // ---------------------------------------------------------------------------
 // set-up / tear-down kernels
 
@@ -193,6 +214,9 @@ __global__ void k_prepare(Bufs b) {
     if (!isfinite(p[0]) || !isfinite(p[1]) || !isfinite(p[2])) set_status(b.st, ST_NONFINITE);
     b.x[i] = make_dvec4(p[0], p[1], p[2], 0.0);
     b.xf[i] = make_float4((float)p[0], (float)p[1], (float)p[2], 0.f);
+    if (b.xq)
+        b.xq[i] = make_int4(to_fixed(p[0], b.qscale), to_fixed(p[1], b.qscale),
+                            to_fixed(p[2], b.qscale), 0);
     b.v[i] = make_dvec4(0.0, 0.0, 0.0, 0.0);
     b.f[i] = make_dvec4(0.0, 0.0, 0.0, 0.0);
     if (b.rho) b.rho[i] = 0.0;
@@ -301,7 +325,8 @@ __device__ __forceinline__ void try_add_pair(const Bufs& b, const GeoC& g, int i
         }
     }
     const float r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-    if (!(r2 < g.rlist2f) || !upper_half(d[0], d[1], d[2])) return;  // NaN fails too
+    if (!(r2 < g.rlist2f)) return;  // NaN fails too
+    if (!g.full && !upper_half(d[0], d[1], d[2])) return;
     // image codes cover shifts of -2..2 box lengths; atoms further apart than
     // that in raw coordinates are a caller error (positions far outside the box)
     if (s[0] < -2 || s[0] > 2 || s[1] < -2 || s[1] > 2 || s[2] < -2 || s[2] > 2) {
@@ -523,6 +548,135 @@ __global__ void __launch_bounds__(kForceBlock) k_force_lj(Bufs b, PotC P, GeoC g
 }
 
 // ---------------------------------------------------------------------------
+// FP32-pair form of the RGL passes (full list, one thread per atom, no atomics).
+//
+// Pair separations are exact fixed-point integers (x_j - x_i - image shift,
+// 32-bit wrap-around); r^2 and r^2 - r0^2 are exact in 64-bit integers and
+// rounded once to float, so s = r/r0 - 1 = (r^2 - r0^2) / (r0 (r + r0)) keeps
+// ~1e-7 relative accuracy even for nearest neighbours, where FP32 rounding
+// of r itself would shift distances by ~1e-7 A.  The exponentials, taper,
+// embedding and pair forces are FP32; per-atom sums are Kahan-compensated;
+// forces, positions, energies and all reductions stay FP64.
+
+__device__ __forceinline__ void fill_qshift_table(int3* tbl, const GeoC& g) {
+    for (int t = threadIdx.x; t < 125; t += blockDim.x) {
+        const int sx = t % 5 - 2, sy = (t / 5) % 5 - 2, sz = t / 25 - 2;
+        tbl[t] = make_int3((int)((unsigned)sx * (unsigned)g.Lq[0]),
+                           (int)((unsigned)sy * (unsigned)g.Lq[1]),
+                           (int)((unsigned)sz * (unsigned)g.Lq[2]));
+    }
+}
+
+// Fixed-point separation of list slot e from atom i; returns r^2 in
+// (fixed-point unit)^2.
+__device__ __forceinline__ long long pair_sep_q(const Bufs& b, const int3* qt, int4 qi,
+                                                uint32_t e, int& dx, int& dy, int& dz, int& j) {
+    j = (int)(e & kIdxMask);
+    const int code = (int)(e >> kIdxBits);
+    const int4 qj = b.xq[j];
+    dx = wrap_sub(qj.x, qi.x);
+    dy = wrap_sub(qj.y, qi.y);
+    dz = wrap_sub(qj.z, qi.z);
+    if (code != kCodeZero) {
+        const int3 s = qt[code];
+        dx = wrap_sub(dx, s.x);
+        dy = wrap_sub(dy, s.y);
+        dz = wrap_sub(dz, s.z);
+    }
+    return (long long)dx * dx + (long long)dy * dy + (long long)dz * dz;
+}
+
+// RGL pair terms in FP32 from the exact fixed-point r^2.
+__device__ __forceinline__ void rgl_pair32(const PotC& P, long long r2q, const float* et,
+                                           float& rinv, float& phi, float& dphi, float& g,
+                                           float& dg) {
+    const float r2 = __ll2float_rn(r2q) * P.qinv2;
+    const float u = __ll2float_rn(r2q - P.r0sq_q) * P.qinv2;   // r^2 - r0^2
+    rinv = rsqrtf(r2);
+    const float r = r2 * rinv;
+    const float s = u / (P.r0_f * (r + P.r0_f));                // r/r0 - 1
+    const float ep = P.A_f * exp32_tang(-P.p_f * s, P.ex32, et);
+    const float eq = P.xi2_f * exp32_tang(-P.q2_f * s, P.ex32, et);
+    float S = 1.f, dS = 0.f;
+    if (r > P.rs_f) {
+        const float t = (r - P.rs_f) * P.winv_f;
+        const float t2 = t * t, t3 = t2 * t;
+        S = 1.f - 10.f * t3 + 15.f * t3 * t - 6.f * t3 * t2;
+        dS = (-30.f * t2 + 60.f * t3 - 30.f * t3 * t) * P.winv_f;
+    }
+    phi = ep * S;
+    g = eq * S;
+    dphi = ep * (-P.p_r0_f * S + dS);
+    dg = eq * (-P.q2_r0_f * S + dS);
+}
+
+// Pass 1 (FP32-pair): rho_i, F'(rho_i) = -1/(2 sqrt(rho_i)) and the atom's
+// energy sum_j phi - sqrt(rho_i); the full list makes rho_i complete in one
+// thread, so the embedding step is fused here.
+__global__ void __launch_bounds__(kForceBlock) k_density32(Bufs b, PotC P, GeoC g) {
+    __shared__ int3 qt[125];
+    __shared__ float et[kExp32TableSize];
+    __shared__ double red[32];
+    if (b.st->done) return;
+    fill_qshift_table(qt, g);
+    for (int t = threadIdx.x; t < kExp32TableSize; t += blockDim.x) et[t] = b.exp32_table[t];
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double e_atom = 0.0;
+    if (i < b.n) {
+        const int4 qi = b.xq[i];
+        const int m = b.nnbr[i];
+        Kahan32 rho, erep;
+        for (int k = 0; k < m; ++k) {
+            int dx, dy, dz, j;
+            const long long r2q = pair_sep_q(b, qt, qi, b.nbr[(size_t)k * b.n + i], dx, dy, dz, j);
+            if (r2q >= P.rc2q) continue;
+            float rinv, phi, dphi, gg, dg;
+            rgl_pair32(P, r2q, et, rinv, phi, dphi, gg, dg);
+            rho.add(gg);
+            erep.add(phi);
+        }
+        const double rho_d = rho.value();
+        const float rf = (float)rho_d;
+        const float sq = sqrtf(rf);
+        b.fp32[i] = rf > 0.f ? -0.5f / sq : 0.f;
+        b.rho[i] = rho_d;
+        e_atom = erep.value() - (double)sq;
+    }
+    const double bs = block_sum(e_atom, red);
+    if (threadIdx.x == 0) b.epart[blockIdx.x] = bs;
+}
+
+// Pass 2 (FP32-pair): F_i = sum_j [2 phi' + (F'_i + F'_j) g'] (x_j - x_i) / r,
+// Kahan-compensated per component, written as FP64 (no atomics).
+__global__ void __launch_bounds__(kForceBlock) k_force32(Bufs b, PotC P, GeoC g) {
+    __shared__ int3 qt[125];
+    __shared__ float et[kExp32TableSize];
+    if (b.st->done) return;
+    fill_qshift_table(qt, g);
+    for (int t = threadIdx.x; t < kExp32TableSize; t += blockDim.x) et[t] = b.exp32_table[t];
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= b.n) return;
+    const int4 qi = b.xq[i];
+    const float fpi = b.fp32[i];
+    const int m = b.nnbr[i];
+    Kahan32 fx, fy, fz;
+    for (int k = 0; k < m; ++k) {
+        int dx, dy, dz, j;
+        const long long r2q = pair_sep_q(b, qt, qi, b.nbr[(size_t)k * b.n + i], dx, dy, dz, j);
+        if (r2q >= P.rc2q) continue;
+        float rinv, phi, dphi, gg, dg;
+        rgl_pair32(P, r2q, et, rinv, phi, dphi, gg, dg);
+        const float fs = (2.f * dphi + (fpi + b.fp32[j]) * dg) * rinv * P.qinv;
+        fx.add(fs * (float)dx);
+        fy.add(fs * (float)dy);
+        fz.add(fs * (float)dz);
+    }
+    b.f[i] = make_dvec4(fx.value(), fy.value(), fz.value(), 0.0);
+}
+
+// ---------------------------------------------------------------------------
 // FP64 reductions of the current (F, v): P = F.v, |F|^2, |v|^2 (Alg. 2 and
 // the mixing of Alg. 4) and the per-atom / per-component force maxima (Sec. 3.4).
 __global__ void k_reduce(Bufs b) {
@@ -693,6 +847,9 @@ __global__ void k_update(Bufs b) {
         x.z += dt * v.z;
         b.x[i] = x;
         b.xf[i] = make_float4((float)x.x, (float)x.y, (float)x.z, 0.f);
+        if (b.xq)
+            b.xq[i] = make_int4(to_fixed(x.x, b.qscale), to_fixed(x.y, b.qscale),
+                                to_fixed(x.z, b.qscale), 0);
         b.v[i] = v;
         b.f[i] = make_dvec4(0.0, 0.0, 0.0, 0.0);
         if (b.rho) b.rho[i] = 0.0;

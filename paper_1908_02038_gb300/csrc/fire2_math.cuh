@@ -67,4 +67,62 @@ __device__ __forceinline__ double exp_tang(double x, const ExpC& c, const double
     return __hiloint2double(__double2hiint(y) + (m << 20), __double2loint(y));
 }
 
+// ---------------------------------------------------------------------------
+// FP32 version for the FP32-pair form: the same method with N = 64 and
+// e^r - 1 to r^3/6 (truncation below 4e-11 for |r| <= 5.5e-3), valid for
+// |x| < 87.  The table holds 2^(j/64) rounded to float; the result is within
+// about one float ulp.
+
+constexpr int kExp32TableBits = 6;
+constexpr int kExp32TableSize = 1 << kExp32TableBits;
+
+struct Exp32C {
+    float inv_c;      // 64 / ln2
+    float c_hi;       // ln2 / 64 with 12 significant bits (k c_hi exact for |k| < 2^11)
+    float c_lo;       // ln2 / 64 - c_hi
+};
+
+inline Exp32C make_exp32_constants(float* table) {
+    const double LN2_HI = 0x1.62e42fefa39efp-1;
+    Exp32C c;
+    const double cn = LN2_HI / kExp32TableSize;
+    int e = 0;
+    std::frexp(cn, &e);
+    const double hi = std::ldexp(std::trunc(std::ldexp(cn, 12 - e)), e - 12);
+    c.c_hi = (float)hi;
+    c.c_lo = (float)(cn - hi);
+    c.inv_c = (float)(kExp32TableSize / LN2_HI);
+    for (int j = 0; j < kExp32TableSize; ++j) table[j] = (float)std::exp2((double)j / kExp32TableSize);
+    return c;
+}
+
+__device__ __forceinline__ float exp32_tang(float x, const Exp32C& c, const float* tbl) {
+    const float magic = 0x1.8p23f;                // 1.5 * 2^23
+    const float t = fmaf(x, c.inv_c, magic);
+    const float kd = t - magic;
+    const int k = __float_as_int(t) - 0x4B400000;  // the integer kd
+    float r = fmaf(-kd, c.c_hi, x);
+    r = fmaf(-kd, c.c_lo, r);
+    float q = fmaf(r, 1.0f / 6.0f, 0.5f);
+    q = fmaf(q, r, 1.0f);
+    const float p = q * r;
+    const float tj = tbl[k & (kExp32TableSize - 1)];
+    const float y = fmaf(tj, p, tj);
+    const int m = k >> kExp32TableBits;
+    return __int_as_float(__float_as_int(y) + (m << 23));
+}
+
+// Compensated (Kahan) accumulation in FP32: sum + c carries the running
+// total to about one float ulp of the sum.
+struct Kahan32 {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float v) {
+        const float y = v - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
 }  // namespace fire2

@@ -66,3 +66,11 @@ def test_init_rejects_bad_arguments_before_touching_the_gpu(lib):
     sys = fg.fire_system_t(10, -1.0, (ctypes.c_int32 * 3)(1, 1, 1), 0)
     with pytest.raises(fg.FireError):
         fg.fire_init(sys, pot, par)
+
+
+def test_fp32pair_rejected_for_lj(lib):
+    pot = fg.Potential(fg.FIRE_POT_LJ, precision=fg.FIRE_PREC_FP32_PAIR).c()
+    sys = fg.fire_system_t(10, 1.0, (ctypes.c_int32 * 3)(1, 1, 1), 0)
+    with pytest.raises(fg.FireError) as e:
+        fg.fire_init(sys, pot, fg.fire_default_params(0.005))
+    assert e.value.status == fg.FIRE_ERR_ARG and "FP32-pair" in str(e.value)

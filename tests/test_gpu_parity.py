@@ -314,3 +314,52 @@ def test_chunked_execution_matches_graph_loop():
     assert abs(r1.iterations - r2.iterations) <= max(2, 0.05 * r1.iterations)
     assert abs(r1.energy - r2.energy) / c.n < 1e-10
     assert r3.stop == fg.FIRE_STOP_MAXITER and r3.iterations == 50 and r3.force_evals == 51
+
+
+# ----------------------------------------------------------------------------
+# FP32-pair form (pair/embedding math FP32; positions, sums, control FP64)
+
+F32_ABS = 3e-6      # eV/A, max-abs force difference against the FP64 oracle
+E32_PER_ATOM = 1e-6  # eV/atom
+
+
+@pytest.mark.parametrize("ncell,nvac", [(3, 2), (5, 3), (7, 10)])
+def test_fp32pair_energy_forces_vs_oracle(ncell, nvac):
+    c = fi.rgl_vacancy_box(ncell=ncell, seed=20 + ncell, n_vac=nvac, sigma=0.08)
+    eo, fo = oracle.energy_forces(c.x, c.box, ora_rgl())
+    with fg.FireHandle(c.n, fi.CU_MASS, rgl_pot(precision=fg.FIRE_PREC_FP32_PAIR),
+                       dt_start=fi.CU_DT) as h:
+        e, f = h.energy_forces(c.x, c.box)
+    err = np.abs(f - fo).max()
+    print(f"FP32-pair vs FP64 oracle: max|dF| = {err:.3e} eV/A, dE/N = {abs(e - eo) / c.n:.3e} eV")
+    assert err < F32_ABS
+    assert abs(e - eo) / c.n < E32_PER_ATOM
+
+
+def test_fp32pair_1m_sampled_forces_vs_oracle():
+    c = fi.rgl_void_box()
+    which = np.sort(np.random.default_rng(6).choice(c.n, size=2048, replace=False))
+    eo, fo = oracle.energy_forces_subset(c.x, c.box, ora_rgl(), which, mode=oracle.FORCE_CELLS)
+    with fg.FireHandle(c.n, fi.CU_MASS, rgl_pot(precision=fg.FIRE_PREC_FP32_PAIR),
+                       dt_start=fi.CU_DT) as h:
+        e, f = h.energy_forces(c.x, c.box)
+    assert np.abs(f[which] - fo).max() < F32_ABS
+    assert abs(e - eo) / c.n < E32_PER_ATOM
+
+
+def test_fp32pair_relaxation_reaches_fp64_converged_state():
+    c = fi.rgl_vacancy_box(ncell=20, seed=2)
+    x64, x32 = c.x.copy(), c.x.copy()
+    with fg.FireHandle(c.n, fi.CU_MASS, rgl_pot(), dt_start=fi.CU_DT) as h64, \
+            fg.FireHandle(c.n, fi.CU_MASS, rgl_pot(precision=fg.FIRE_PREC_FP32_PAIR),
+                          dt_start=fi.CU_DT) as h32:
+        r64 = h64.minimize(x64, c.box, 1e-6, 100000)
+        r32 = h32.minimize(x32, c.box, 1e-6, 100000)
+        # the FP32 solution judged by FP64 forces
+        e_chk, f_chk = h64.energy_forces(x32, c.box)
+    fmax64_at32 = np.sqrt((f_chk ** 2).sum(1)).max()
+    print(f"iterations FP64 {r64.iterations}, FP32-pair {r32.iterations}; FP64 max|F| at the "
+          f"FP32-pair minimum {fmax64_at32:.3e}; dE/N {abs(e_chk - r64.energy) / c.n:.3e}")
+    assert r32.stop == fg.FIRE_STOP_FTOL and r32.fmax_atom < 1e-6
+    assert fmax64_at32 < 2e-6
+    assert abs(e_chk - r64.energy) / c.n < 1e-8
