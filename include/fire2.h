@@ -251,6 +251,63 @@ fire_status fire_energy_forces_noalloc(const fire_potential_t* pot, int64_t n_at
  * counterpart.  Errors: FIRE_ERR_ARG, FIRE_ERR_NOMEM, FIRE_ERR_CUDA. */
 fire_status fire_diag_exp(int64_t n, const double* d_x, double* d_out, void* stream);
 
+/* ---- Batched form ----------------------------------------------------------
+ * Hundreds of independent relaxations (Algorithm 2 + Algorithm 4 each, with
+ * its own dt, alpha, counters, neighbour list and stop reason) of uneven atom
+ * counts in one persistent kernel launch: each CTA takes the next system from
+ * a device queue (largest first) and relaxes it to its own stop.  RGL
+ * potential only; FP64 or FP32-pair precision as in fire_potential_t.  The
+ * paper relaxes one configuration per run; the batch is this library's
+ * throughput form (e.g. for ensembles of defect configurations). */
+
+/* Launch shape of the batched kernel. */
+typedef struct {
+    int32_t threads_per_block;  /* multiple of 32 in [32, 512] (default 256) */
+    int32_t ctas_per_sm;        /* resident CTAs per SM, 1..32 (default 2) */
+    int32_t reserved0, reserved1;
+} fire_batch_tuning_t;
+
+/* Creates a batched handle for n_sys systems; system s owns atoms
+ * atom_offsets[s] .. atom_offsets[s+1]-1 of the packed position arrays
+ * (atom_offsets has n_sys + 1 entries, atom_offsets[0] = 0, every system
+ * >= 1 atom).  sys->mass and sys->periodic apply to every system
+ * (sys->n_atoms is ignored).  Only fire_minimize_batch*, fire_batch_* and
+ * fire_destroy / fire_last_error / fire_set_time_budget accept the handle.
+ * Errors: FIRE_ERR_ARG, FIRE_ERR_NOMEM, FIRE_ERR_CUDA. */
+fire_status fire_batch_init(fire_handle_t** h, int32_t n_sys, const int64_t* atom_offsets,
+                            const fire_system_t* sys, const fire_potential_t* pot,
+                            const fire_params_t* params);
+
+/* Relaxes every system of the batch: pos (host, packed N_total x 3, in/out),
+ * boxes (host, n_sys x 3 orthorhombic lengths), the shared ftol / maxiter,
+ * out[n_sys] per-system results (out[s].reserved holds the system's device
+ * status, 0 = ok), forces (host, packed N_total x 3, optional: forces at the
+ * returned positions).  pos is written only on FIRE_OK; the call fails with
+ * the first system's error code if any system failed.
+ * Errors: FIRE_ERR_STATE (not a batched handle), FIRE_ERR_ARG, FIRE_ERR_NONFINITE,
+ * FIRE_ERR_NBR_OVERFLOW, FIRE_ERR_TIMEOUT, FIRE_ERR_CUDA. */
+fire_status fire_minimize_batch(fire_handle_t* h, double* pos, const double* boxes, double ftol,
+                                int64_t maxiter, fire_result_t* out, double* forces);
+
+/* Device-pointer variant: d_pos and d_forces (optional) are device buffers of
+ * N_total x 3 doubles, boxes and out stay on the host; runs on `stream` and
+ * synchronises it before returning. */
+fire_status fire_minimize_batch_dev(fire_handle_t* h, double* d_pos, const double* boxes,
+                                    double ftol, int64_t maxiter, fire_result_t* out,
+                                    double* d_forces, void* stream);
+
+/* Sets the launch shape of later batched calls.  Errors: FIRE_ERR_STATE, FIRE_ERR_ARG. */
+fire_status fire_batch_set_tuning(fire_handle_t* h, const fire_batch_tuning_t* tuning);
+
+/* Autotuner: times every candidate launch shape (threads per CTA 64..512,
+ * CTAs per SM 1..8, at most 2048 threads per SM) on this batch -- positions
+ * pos and boxes as for fire_minimize_batch, `iters` FIRE iterations of every
+ * system from the same start -- keeps the fastest for later calls and
+ * returns it in *chosen (may be NULL).  pos is not modified.
+ * Errors: FIRE_ERR_STATE, FIRE_ERR_ARG, FIRE_ERR_CUDA. */
+fire_status fire_batch_autotune(fire_handle_t* h, const double* pos, const double* boxes,
+                                int32_t iters, fire_batch_tuning_t* chosen);
+
 /* Message of the last failed call on h (or of the last failed fire_init when
  * h is NULL).  Never NULL. */
 const char* fire_last_error(const fire_handle_t* h);

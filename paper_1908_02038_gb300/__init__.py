@@ -37,7 +37,8 @@ EXPORTED = ("fire_abi_version", "fire_default_params", "fire_init", "fire_minimi
             "fire_minimize_dev", "fire_energy_forces", "fire_energy_forces_dev",
             "fire_set_time_budget", "fire_profile_stages", "fire_diag_fma_peak",
             "fire_energy_forces_noalloc", "fire_set_exec_mode", "fire_diag_exp",
-            "fire_last_error", "fire_destroy")
+            "fire_batch_init", "fire_minimize_batch", "fire_minimize_batch_dev",
+            "fire_batch_set_tuning", "fire_batch_autotune", "fire_last_error", "fire_destroy")
 FIRE_EXEC_GRAPH_WHILE, FIRE_EXEC_CHUNKED = 0, 1
 STAGES = ("build", "density", "embed", "force", "reduce", "control", "update")
 
@@ -61,6 +62,11 @@ class fire_params_t(C.Structure):
                 ("alphashrink", C.c_double), ("delaystep", C.c_int32), ("vdfmax", C.c_int32),
                 ("halfstepback", C.c_int32), ("initialdelay", C.c_int32),
                 ("integrator", C.c_int32), ("norm", C.c_int32)]
+
+
+class fire_batch_tuning_t(C.Structure):
+    _fields_ = [("threads_per_block", C.c_int32), ("ctas_per_sm", C.c_int32),
+                ("reserved0", C.c_int32), ("reserved1", C.c_int32)]
 
 
 class fire_result_t(C.Structure):
@@ -102,6 +108,15 @@ def load_library(path: str | None = None):
     lib.fire_set_time_budget.argtypes = [H, C.c_double]
     lib.fire_set_exec_mode.argtypes = [H, C.c_int32, C.c_int32]
     lib.fire_diag_exp.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.fire_batch_init.argtypes = [C.POINTER(H), C.c_int32, C.c_void_p, C.POINTER(fire_system_t),
+                                    C.POINTER(fire_potential_t), C.POINTER(fire_params_t)]
+    lib.fire_minimize_batch.argtypes = [H, C.c_void_p, C.c_void_p, C.c_double, C.c_int64,
+                                        C.c_void_p, C.c_void_p]
+    lib.fire_minimize_batch_dev.argtypes = [H, C.c_void_p, C.c_void_p, C.c_double, C.c_int64,
+                                            C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.fire_batch_set_tuning.argtypes = [H, C.POINTER(fire_batch_tuning_t)]
+    lib.fire_batch_autotune.argtypes = [H, C.c_void_p, C.c_void_p, C.c_int32,
+                                        C.POINTER(fire_batch_tuning_t)]
     lib.fire_profile_stages.argtypes = [H, C.c_void_p, C.POINTER(C.c_double), C.c_int32,
                                         C.POINTER(C.c_double)]
     lib.fire_diag_fma_peak.argtypes = [C.c_int32, C.POINTER(C.c_double)]
@@ -250,6 +265,57 @@ def fire_diag_exp(d_x, d_out, stream=None) -> None:
                                         _stream(stream)), None)
 
 
+def fire_batch_init(offsets, sys: fire_system_t, pot: fire_potential_t, params: fire_params_t):
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    h = C.c_void_p()
+    st = load_library().fire_batch_init(C.byref(h), int(len(off) - 1), off.ctypes.data,
+                                        C.byref(sys), C.byref(pot), C.byref(params))
+    _check(st, None)
+    return h
+
+
+def fire_minimize_batch(handle, pos: np.ndarray, boxes, ftol: float, maxiter: int,
+                        want_forces: bool = False):
+    """Relaxes the packed positions in place; returns (results, forces or None)."""
+    if pos.dtype != np.float64 or not pos.flags.c_contiguous:
+        raise ValueError("pos must be a C-contiguous float64 array")
+    bx = np.ascontiguousarray(boxes, dtype=np.float64).reshape(-1, 3)
+    out = (fire_result_t * len(bx))()
+    f = np.empty_like(pos) if want_forces else None
+    st = load_library().fire_minimize_batch(handle, pos.ctypes.data, bx.ctypes.data, float(ftol),
+                                            int(maxiter), C.cast(out, C.c_void_p),
+                                            f.ctypes.data if f is not None else None)
+    _check(st, handle)
+    return list(out), f
+
+
+def fire_minimize_batch_dev(handle, d_pos, boxes, ftol: float, maxiter: int, d_forces=None,
+                            stream=None):
+    _check_dev(d_pos)
+    bx = np.ascontiguousarray(boxes, dtype=np.float64).reshape(-1, 3)
+    out = (fire_result_t * len(bx))()
+    st = load_library().fire_minimize_batch_dev(
+        handle, d_pos.data_ptr(), bx.ctypes.data, float(ftol), int(maxiter),
+        C.cast(out, C.c_void_p), d_forces.data_ptr() if d_forces is not None else None,
+        _stream(stream))
+    _check(st, handle)
+    return list(out)
+
+
+def fire_batch_set_tuning(handle, threads_per_block: int, ctas_per_sm: int) -> None:
+    t = fire_batch_tuning_t(int(threads_per_block), int(ctas_per_sm), 0, 0)
+    _check(load_library().fire_batch_set_tuning(handle, C.byref(t)), handle)
+
+
+def fire_batch_autotune(handle, pos: np.ndarray, boxes, iters: int = 20):
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    bx = np.ascontiguousarray(boxes, dtype=np.float64).reshape(-1, 3)
+    t = fire_batch_tuning_t()
+    _check(load_library().fire_batch_autotune(handle, pos.ctypes.data, bx.ctypes.data,
+                                              int(iters), C.byref(t)), handle)
+    return {"threads_per_block": t.threads_per_block, "ctas_per_sm": t.ctas_per_sm}
+
+
 def _check_dev(t):
     import torch
     if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64
@@ -286,6 +352,52 @@ class Potential:
         return fire_potential_t(self.kind, self.precision, self.eps, self.sigma, self.rc_lj,
                                 self.A, self.xi, self.p, self.q, self.r0, self.rs, self.rc,
                                 self.skin)
+
+
+class FireBatch:
+    """Owns one batched fire_handle_t (fire_batch_init)."""
+
+    def __init__(self, counts, mass: float, pot: Potential, params=None, periodic=(1, 1, 1),
+                 dt_start: float | None = None, **param_overrides):
+        if params is None:
+            params = fire_default_params(dt_start)
+        for k, v in param_overrides.items():
+            setattr(params, k, int(v) if isinstance(getattr(params, k), int) else float(v))
+        self.offsets = np.concatenate([[0], np.cumsum(np.asarray(counts, dtype=np.int64))])
+        sys = fire_system_t(int(self.offsets[-1]), float(mass), (C.c_int32 * 3)(*periodic), 0)
+        self.h = fire_batch_init(self.offsets, sys, pot.c(), params)
+
+    def minimize(self, pos, boxes, ftol, maxiter, want_forces=False):
+        return fire_minimize_batch(self.h, pos, boxes, ftol, maxiter, want_forces)
+
+    def minimize_dev(self, d_pos, boxes, ftol, maxiter, d_forces=None, stream=None):
+        return fire_minimize_batch_dev(self.h, d_pos, boxes, ftol, maxiter, d_forces, stream)
+
+    def set_tuning(self, threads_per_block, ctas_per_sm):
+        fire_batch_set_tuning(self.h, threads_per_block, ctas_per_sm)
+
+    def autotune(self, pos, boxes, iters=20):
+        return fire_batch_autotune(self.h, pos, boxes, iters)
+
+    def set_time_budget(self, seconds):
+        fire_set_time_budget(self.h, seconds)
+
+    def close(self):
+        if getattr(self, "h", None):
+            fire_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class FireHandle:

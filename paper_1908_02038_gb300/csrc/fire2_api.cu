@@ -17,6 +17,11 @@
 
 using namespace fire2;
 
+struct fire_batch_state;
+void fire2_batch_free(fire_batch_state* b);
+fire_status fire2_batch_create(fire_handle_t* h, int32_t n_sys, const int64_t* offsets,
+                               fire_batch_state** out);
+
 struct fire_handle {
     int device = 0;
     fire_system_t sys{};
@@ -40,6 +45,7 @@ struct fire_handle {
     int exec_mode = FIRE_EXEC_GRAPH_WHILE;
     int chunk = 32;                  // iterations per graph launch, chunked mode
     cudaGraphExec_t exec_init = nullptr, exec_chunk = nullptr, exec_final = nullptr;
+    fire_batch_state* batch = nullptr;   // set for handles made by fire_batch_init
     std::string err;
 };
 
@@ -346,24 +352,24 @@ void init_state(fire_handle* h, double ftol, int64_t maxiter) {
     DevState& s = *h->h_state;
     std::memset(&s, 0, sizeof s);
     const fire_params_t& p = h->par;
-    s.ftol = ftol;
-    s.maxiter = maxiter;
-    s.dt_start = p.dt_start;
-    s.dtmax = p.tmax * p.dt_start;
-    s.dtmin = p.tmin * p.dt_start;
-    s.dtgrow = p.dtgrow;
-    s.dtshrink = p.dtshrink;
-    s.alpha0 = p.alpha0;
-    s.alphashrink = p.alphashrink;
-    s.mass = h->sys.mass;
-    s.delaystep = p.delaystep;
-    s.vdfmax = p.vdfmax;
-    s.halfstepback = p.halfstepback;
-    s.initialdelay = p.initialdelay;
-    s.norm = p.norm;
+    FireParamsD& q = s.prm;
+    q.ftol = ftol;
+    q.maxiter = maxiter;
+    q.dt_start = p.dt_start;
+    q.dtmax = p.tmax * p.dt_start;
+    q.dtmin = p.tmin * p.dt_start;
+    q.dtgrow = p.dtgrow;
+    q.dtshrink = p.dtshrink;
+    q.alpha0 = p.alpha0;
+    q.alphashrink = p.alphashrink;
+    q.mass = h->sys.mass;
+    q.delaystep = p.delaystep;
+    q.vdfmax = p.vdfmax;
+    q.halfstepback = p.halfstepback;
+    q.initialdelay = p.initialdelay;
+    q.norm = p.norm;
+    fire_scal_init(q, s.fs);
     s.budget_ns = (unsigned long long)(h->budget_s * 1e9);
-    s.dt = p.dt_start;
-    s.alpha = p.alpha0;
 }
 
 fire_status status_to_error(fire_handle* h, int st) {
@@ -381,16 +387,16 @@ fire_status status_to_error(fire_handle* h, int st) {
 void fill_result(const fire_handle* h, fire_result_t* out) {
     const DevState& s = *h->h_state;
     out->energy = s.energy;
-    out->iterations = s.iter;
-    out->force_evals = s.evals;
+    out->iterations = s.fs.iter;
+    out->force_evals = s.fs.evals;
     out->nbr_builds = s.nbr_builds;
-    out->stop = s.stop;
+    out->stop = s.fs.stop;
     out->reserved = 0;
     out->fmax_atom = std::sqrt(s.fmax2);
     out->f2norm = std::sqrt(s.F2);
     out->finf = s.finf;
-    out->dt_final = s.dt;
-    out->alpha_final = s.alpha;
+    out->dt_final = s.fs.dt;
+    out->alpha_final = s.fs.alpha;
 }
 
 fire_status check_params(fire_handle* h, const fire_params_t& p) {
@@ -407,6 +413,7 @@ fire_status check_params(fire_handle* h, const fire_params_t& p) {
 }
 
 fire_status prepare_call(fire_handle* h, const double box[3], GeoC* g) {
+    if (h->batch) return fail(h, FIRE_ERR_STATE, "batched handle: use fire_minimize_batch");
     fire_status st = check_box(h, box);
     if (st != FIRE_OK) return st;
     CK(h, cudaSetDevice(h->device));
@@ -422,6 +429,22 @@ fire_status prepare_call(fire_handle* h, const double box[3], GeoC* g) {
 __attribute__((visibility("hidden"))) void fire2_set_global_error(const char* msg) {
     g_init_err = msg ? msg : "unknown error";
 }
+
+// Accessors for the batched form (fire2_batch.cu).  Not exported.
+#define FIRE2_HIDDEN __attribute__((visibility("hidden")))
+FIRE2_HIDDEN fire_status fire2_batch_fail(fire_handle_t* h, fire_status code, const char* msg) {
+    return fail(h, code, "%s", msg);
+}
+FIRE2_HIDDEN fire_batch_state* fire2_batch_of(fire_handle_t* h) { return h->batch; }
+FIRE2_HIDDEN const PotC& fire2_potc(fire_handle_t* h) { return h->potc; }
+FIRE2_HIDDEN const fire_potential_t& fire2_pot(fire_handle_t* h) { return h->pot; }
+FIRE2_HIDDEN const fire_params_t& fire2_params(fire_handle_t* h) { return h->par; }
+FIRE2_HIDDEN const fire_system_t& fire2_sys(fire_handle_t* h) { return h->sys; }
+FIRE2_HIDDEN double fire2_budget(fire_handle_t* h) { return h->budget_s; }
+FIRE2_HIDDEN const double* fire2_exp_table(fire_handle_t* h) { return h->b.exp_table; }
+FIRE2_HIDDEN const float* fire2_exp32_table(fire_handle_t* h) { return h->b.exp32_table; }
+FIRE2_HIDDEN double fire2_qscale(fire_handle_t* h) { return h->b.qscale; }
+FIRE2_HIDDEN cudaStream_t fire2_stream(fire_handle_t* h) { return h->stream; }
 
 extern "C" {
 
@@ -445,8 +468,9 @@ fire_status fire_default_params(fire_params_t* out, double dt_start) {
     return FIRE_OK;
 }
 
-fire_status fire_init(fire_handle_t** hp, const fire_system_t* sys, const fire_potential_t* pot,
-                      const fire_params_t* params) {
+static fire_status init_handle(fire_handle_t** hp, const fire_system_t* sys,
+                               const fire_potential_t* pot, const fire_params_t* params,
+                               bool single) {
     if (!hp || !sys || !pot || !params) return fail(nullptr, FIRE_ERR_ARG, "NULL argument to fire_init");
     *hp = nullptr;
     if (sys->n_atoms < 1 || sys->n_atoms > (int64_t)kIdxMask)
@@ -551,6 +575,22 @@ fire_status fire_init(fire_handle_t** hp, const fire_system_t* sys, const fire_p
     CKI(cudaStreamCreateWithFlags(&h->cap1, cudaStreamNonBlocking));
     const size_t n = (size_t)h->n;
     Bufs& b = h->b;
+    {
+        double* t = nullptr;
+        CKI(cudaMalloc(&t, kExpTableSize * sizeof(double)));
+        b.exp_table = t;
+        CKI(cudaMemcpy(t, exp_table_host, kExpTableSize * sizeof(double), cudaMemcpyHostToDevice));
+    }
+    if (fp32pair) {
+        float* t = nullptr;
+        CKI(cudaMalloc(&t, kExp32TableSize * sizeof(float)));
+        b.exp32_table = t;
+        CKI(cudaMemcpy(t, exp32_table_host, kExp32TableSize * sizeof(float), cudaMemcpyHostToDevice));
+    }
+    if (!single) {
+        *hp = h;
+        return FIRE_OK;
+    }
     b.n = h->n;
     b.nb_force = ceil_div(h->n, kForceBlock);
     b.nb_embed = (pot->kind == FIRE_POT_RGL && !fp32pair) ? ceil_div(h->n, kElemBlock) : 0;
@@ -563,16 +603,6 @@ fire_status fire_init(fire_handle_t** hp, const fire_system_t* sys, const fire_p
     if (fp32pair) {
         CKI(cudaMalloc(&b.xq, n * sizeof(int4)));
         CKI(cudaMalloc(&b.fp32, n * sizeof(float)));
-        float* t = nullptr;
-        CKI(cudaMalloc(&t, kExp32TableSize * sizeof(float)));
-        b.exp32_table = t;
-        CKI(cudaMemcpy(t, exp32_table_host, kExp32TableSize * sizeof(float), cudaMemcpyHostToDevice));
-    }
-    {
-        double* t = nullptr;
-        CKI(cudaMalloc(&t, kExpTableSize * sizeof(double)));
-        b.exp_table = t;
-        CKI(cudaMemcpy(t, exp_table_host, kExpTableSize * sizeof(double), cudaMemcpyHostToDevice));
     }
     CKI(cudaMalloc(&b.nnbr, n * sizeof(int)));
     CKI(cudaMalloc(&b.cell_of, n * sizeof(int)));
@@ -592,6 +622,43 @@ fire_status fire_init(fire_handle_t** hp, const fire_system_t* sys, const fire_p
     return FIRE_OK;
 }
 
+fire_status fire_init(fire_handle_t** hp, const fire_system_t* sys, const fire_potential_t* pot,
+                      const fire_params_t* params) {
+    return init_handle(hp, sys, pot, params, true);
+}
+
+fire_status fire_batch_init(fire_handle_t** hp, int32_t n_sys, const int64_t* atom_offsets,
+                            const fire_system_t* sys, const fire_potential_t* pot,
+                            const fire_params_t* params) {
+    if (!hp || !atom_offsets || !sys || !pot || !params)
+        return fail(nullptr, FIRE_ERR_ARG, "NULL argument to fire_batch_init");
+    *hp = nullptr;
+    if (n_sys < 1) return fail(nullptr, FIRE_ERR_ARG, "n_sys must be >= 1");
+    if (atom_offsets[0] != 0) return fail(nullptr, FIRE_ERR_ARG, "atom_offsets[0] must be 0");
+    for (int32_t s = 0; s < n_sys; ++s) {
+        const int64_t k = atom_offsets[s + 1] - atom_offsets[s];
+        if (k < 1 || k > (int64_t)kIdxMask)
+            return fail(nullptr, FIRE_ERR_ARG, "system %d has %lld atoms, outside [1, %u]", s,
+                        (long long)k, kIdxMask);
+    }
+    if (atom_offsets[n_sys] > (int64_t)INT32_MAX)
+        return fail(nullptr, FIRE_ERR_ARG, "more than 2^31 - 1 atoms in the batch");
+    if (pot->kind != FIRE_POT_RGL)
+        return fail(nullptr, FIRE_ERR_ARG, "the batched form supports the RGL potential only");
+    fire_system_t s2 = *sys;
+    s2.n_atoms = atom_offsets[n_sys];
+    fire_status st = init_handle(hp, &s2, pot, params, false);
+    if (st != FIRE_OK) return st;
+    fire_handle* h = *hp;
+    st = fire2_batch_create(h, n_sys, atom_offsets, &h->batch);
+    if (st != FIRE_OK) {
+        g_init_err = h->err;
+        fire_destroy(h);
+        *hp = nullptr;
+    }
+    return st;
+}
+
 void fire_destroy(fire_handle_t* h) {
     if (!h) return;
     cudaSetDevice(h->device);
@@ -604,6 +671,7 @@ void fire_destroy(fire_handle_t* h) {
                     b.st, b.pos_io};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    if (h->batch) fire2_batch_free(h->batch);
     if (h->h_state) cudaFreeHost(h->h_state);
     if (h->h_pos) cudaFreeHost(h->h_pos);
     if (h->stream) cudaStreamDestroy(h->stream);
@@ -794,7 +862,8 @@ fire_status fire_profile_stages(fire_handle_t* h, const double* pos, const doubl
     const size_t bytes = (size_t)3 * h->n * sizeof(double);
     CK(h, cudaMemcpyAsync(h->b.pos_io, pos, bytes, cudaMemcpyHostToDevice, s));
     init_state(h, 0.0, 0);   // dt = 0 for the update stage: positions stay put
-    h->h_state->dt_cur = 0.0;
+    h->h_state->fs.dt_cur = 0.0;
+    h->h_state->fs.dtm = 0.0;
     CK(h, cudaMemcpyAsync(h->b.st, h->h_state, sizeof(DevState), cudaMemcpyHostToDevice, s));
     k_prepare<<<ceil_div(h->n, kElemBlock), kElemBlock, 0, s>>>(h->b);
     cudaEvent_t ev[FIRE_NSTAGES + 1];

@@ -1,0 +1,849 @@
+// Batched FIRE 2.0: hundreds of independent relaxations of uneven size in one
+// persistent launch.
+//
+// Each CTA takes the next system from a device work queue (systems sorted
+// largest first, so the long relaxations start early), relaxes it completely
+// -- list build, RGL density and force passes, FP64 block reductions,
+// Algorithm 2 control, Algorithm 4 update -- with __syncthreads() as the only
+// synchronisation, and then takes the next one.  Every system keeps its own
+// FIRE state (dt, alpha, counters), list and stop reason.  No CTA ever waits
+// on another, so there is no grid barrier and nothing to time out; each
+// relaxation is bounded by maxiter and by the wall-clock budget.
+//
+// The launch shape (threads per CTA, CTAs per SM) is chosen by the autotuner
+// in fire_batch_autotune: it times every candidate shape on the caller's
+// batch for a fixed number of iterations and keeps the fastest.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "fire2.h"
+#include "fire2_common.cuh"
+
+using namespace fire2;
+
+namespace fire2 {
+
+// Per-system description (device array).
+struct BInst {
+    long long off;          // first atom in the packed arrays
+    long long list_off;     // first list slot: nbr[list_off + k * n + i]
+    int n, cap;             // atoms, list capacity per atom
+    int nc[3];              // cells per axis; nc[0] == 0 -> all-pairs build
+    int per[3];
+    int Lq[3];              // box in fixed-point units (FP32-pair form)
+    double L[3], Linv[3];
+    float Lf[3], Linvf[3];
+    float rlist2f;
+    double half_skin2;
+};
+
+// Per-system result (device array).
+struct BRes {
+    double energy, fmax2, F2, finf, dt, alpha;
+    long long iter, evals, builds;
+    int stop, status;
+};
+
+struct BArgs {
+    int n_sys;
+    const int* order;       // systems, largest first
+    int* queue;             // next index into `order`
+    const BInst* inst;
+    BRes* res;
+    dvec4 *x, *v, *f, *xref;
+    int4* xq;
+    float4* xf;
+    double* fp64;           // F'(rho) (FP64 form)
+    float* fp32;            // F'(rho) (FP32-pair form)
+    uint32_t* nbr;
+    int* nnbr;
+    double* pos_io;         // packed N x 3, in/out
+    double* f_out;          // packed N x 3 final forces, optional
+    FireParamsD prm;
+    unsigned long long budget_ns;
+    PotC P;
+    const double* exp_table;
+    const float* exp32_table;
+    double qscale;
+    int max_cells;          // capacity of the shared cell arrays
+    int max_atoms_smem;     // capacity of the shared cell-sorted atom array
+};
+
+struct BShared {            // per-CTA scalars
+    FireScal fs;
+    int sys, done, status, rebuild;
+    long long builds;
+    double P, F2, V2, fa2, fin, E, dmax;
+};
+
+// Block reductions into shared scalars (all threads must call).
+__device__ __forceinline__ double bsum(double v, double* red) {
+    const double r = block_sum(v, red);
+    __shared__ double out;
+    if (threadIdx.x == 0) out = r;
+    __syncthreads();
+    return out;
+}
+__device__ __forceinline__ double bmax(double v, double* red) {
+    const double r = block_max(v, red);
+    __shared__ double out;
+    if (threadIdx.x == 0) out = r;
+    __syncthreads();
+    return out;
+}
+
+// Adds pair (i, j) to i's full list when the FP32 candidate test passes.
+__device__ __forceinline__ void b_try_pair(const BArgs& a, const BInst& I, int i, float4 xi, int j,
+                                           int& cnt, int& bad) {
+    const float4 xj = a.xf[I.off + j];
+    float d[3] = {xj.x - xi.x, xj.y - xi.y, xj.z - xi.z};
+    int s[3] = {0, 0, 0};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        if (I.per[k]) {
+            s[k] = __float2int_rn(d[k] * I.Linvf[k]);
+            d[k] -= (float)s[k] * I.Lf[k];
+        }
+    }
+    const float r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    if (!(r2 < I.rlist2f)) return;
+    if (s[0] < -2 || s[0] > 2 || s[1] < -2 || s[1] > 2 || s[2] < -2 || s[2] > 2) {
+        bad = ST_RANGE;
+        return;
+    }
+    if (cnt < I.cap) {
+        const uint32_t code = (uint32_t)((s[0] + 2) + 5 * (s[1] + 2) + 25 * (s[2] + 2));
+        a.nbr[I.list_off + (long long)cnt * I.n + i] = (code << kIdxBits) | (uint32_t)j;
+    }
+    ++cnt;
+}
+
+// Full neighbour list of one system; cell-sorted atoms in shared memory when
+// the box holds at least 3 cells per axis, all pairs otherwise.
+__device__ __forceinline__ void b_build(const BArgs& a, const BInst& I, int* s_count, int* s_start, int* s_atoms,
+                        BShared& sh, double* red) {
+    const int T = blockDim.x, t = threadIdx.x;
+    const bool cells = I.nc[0] > 0;
+    const int ncell = cells ? I.nc[0] * I.nc[1] * I.nc[2] : 0;
+    if (cells) {
+        for (int c = t; c < ncell; c += T) s_count[c] = 0;
+        __syncthreads();
+        for (int i = t; i < I.n; i += T) {
+            const dvec4 x = a.x[I.off + i];
+            const int c = (cell_coord(x.x, I.Linv[0], I.nc[0]) * I.nc[1] +
+                           cell_coord(x.y, I.Linv[1], I.nc[1])) * I.nc[2] +
+                          cell_coord(x.z, I.Linv[2], I.nc[2]);
+            atomicAdd(&s_count[c], 1);
+        }
+        __syncthreads();
+        if (t == 0) {
+            int run = 0;
+            for (int c = 0; c < ncell; ++c) {
+                s_start[c] = run;
+                run += s_count[c];
+                s_count[c] = s_start[c];
+            }
+            s_start[ncell] = run;
+        }
+        __syncthreads();
+        for (int i = t; i < I.n; i += T) {
+            const dvec4 x = a.x[I.off + i];
+            const int c = (cell_coord(x.x, I.Linv[0], I.nc[0]) * I.nc[1] +
+                           cell_coord(x.y, I.Linv[1], I.nc[1])) * I.nc[2] +
+                          cell_coord(x.z, I.Linv[2], I.nc[2]);
+            s_atoms[atomicAdd(&s_count[c], 1)] = i;
+        }
+        __syncthreads();
+    }
+    int bad = ST_OK, over = 0;
+    for (int i = t; i < I.n; i += T) {
+        const float4 xi = a.xf[I.off + i];
+        int cnt = 0;
+        if (!cells) {
+            for (int j = 0; j < I.n; ++j)
+                if (j != i) b_try_pair(a, I, i, xi, j, cnt, bad);
+        } else {
+            const dvec4 x = a.x[I.off + i];
+            const int cx = cell_coord(x.x, I.Linv[0], I.nc[0]);
+            const int cy = cell_coord(x.y, I.Linv[1], I.nc[1]);
+            const int cz = cell_coord(x.z, I.Linv[2], I.nc[2]);
+            for (int ox = -1; ox <= 1; ++ox) {
+                const int ax = (cx + ox + I.nc[0]) % I.nc[0];
+                for (int oy = -1; oy <= 1; ++oy) {
+                    const int ay = (cy + oy + I.nc[1]) % I.nc[1];
+                    for (int oz = -1; oz <= 1; ++oz) {
+                        const int az = (cz + oz + I.nc[2]) % I.nc[2];
+                        const int c = (ax * I.nc[1] + ay) * I.nc[2] + az;
+                        for (int k = s_start[c]; k < s_start[c + 1]; ++k) {
+                            const int j = s_atoms[k];
+                            if (j != i) b_try_pair(a, I, i, xi, j, cnt, bad);
+                        }
+                    }
+                }
+            }
+        }
+        if (cnt > I.cap) {
+            over = 1;
+            cnt = I.cap;
+        }
+        a.nnbr[I.off + i] = cnt;
+        a.xref[I.off + i] = a.x[I.off + i];
+    }
+    const double flag = bmax((double)(bad != ST_OK ? bad : (over ? ST_NBR_OVERFLOW : 0)), red);
+    if (t == 0) {
+        if (flag > 0.0 && sh.status == ST_OK) sh.status = (int)flag;
+        sh.builds += 1;
+    }
+    __syncthreads();
+}
+
+// Energy and forces of one system (full list, no atomics); returns E.
+template <bool F32>
+__device__ __forceinline__ double b_forces(const BArgs& a, const BInst& I, const double* etab, const float* et32,
+                           double* red) {
+    const PotC& P = a.P;
+    const int T = blockDim.x, t = threadIdx.x;
+    double e_sum = 0.0;
+    // pass 1: densities, embedding derivative, atom energies
+    for (int i = t; i < I.n; i += T) {
+        const long long gi = I.off + i;
+        const int m = a.nnbr[gi];
+        if (F32) {
+            const int4 qi = a.xq[gi];
+            Kahan32 rho, erep;
+            for (int k = 0; k < m; ++k) {
+                const uint32_t e = a.nbr[I.list_off + (long long)k * I.n + i];
+                const int j = (int)(e & kIdxMask), code = (int)(e >> kIdxBits);
+                const int4 qj = a.xq[I.off + j];
+                int dx = wrap_sub(qj.x, qi.x), dy = wrap_sub(qj.y, qi.y), dz = wrap_sub(qj.z, qi.z);
+                if (code != kCodeZero) {
+                    dx = wrap_sub(dx, (int)((unsigned)(code % 5 - 2) * (unsigned)I.Lq[0]));
+                    dy = wrap_sub(dy, (int)((unsigned)((code / 5) % 5 - 2) * (unsigned)I.Lq[1]));
+                    dz = wrap_sub(dz, (int)((unsigned)(code / 25 - 2) * (unsigned)I.Lq[2]));
+                }
+                const long long r2q = (long long)dx * dx + (long long)dy * dy + (long long)dz * dz;
+                if (r2q >= P.rc2q) continue;
+                float rinv, phi, dphi, g, dg;
+                rgl_pair32(P, r2q, et32, rinv, phi, dphi, g, dg);
+                rho.add(g);
+                erep.add(phi);
+            }
+            const float rf = (float)rho.value();
+            const float sq = sqrtf(rf);
+            a.fp32[gi] = rf > 0.f ? -0.5f / sq : 0.f;
+            e_sum += erep.value() - (double)sq;
+        } else {
+            const dvec4 xi = a.x[gi];
+            double rho = 0.0, erep = 0.0;
+            for (int k = 0; k < m; ++k) {
+                const uint32_t e = a.nbr[I.list_off + (long long)k * I.n + i];
+                const int j = (int)(e & kIdxMask), code = (int)(e >> kIdxBits);
+                const dvec4 xj = a.x[I.off + j];
+                double dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
+                if (code != kCodeZero) {
+                    dx -= (code % 5 - 2) * I.L[0];
+                    dy -= ((code / 5) % 5 - 2) * I.L[1];
+                    dz -= (code / 25 - 2) * I.L[2];
+                }
+                const double r2 = dx * dx + dy * dy + dz * dz;
+                if (!(r2 < P.rc2)) continue;
+                double rinv, phi, dphi, g, dg;
+                rgl_pair64(P, r2, etab, rinv, phi, dphi, g, dg);
+                rho += g;
+                erep += phi;
+            }
+            const double sq = sqrt(rho);
+            a.fp64[gi] = rho > 0.0 ? -0.5 / sq : 0.0;
+            e_sum += erep - sq;
+        }
+    }
+    const double E = bsum(e_sum, red);  // also orders pass 1 before pass 2
+    // pass 2: forces
+    for (int i = t; i < I.n; i += T) {
+        const long long gi = I.off + i;
+        const int m = a.nnbr[gi];
+        if (F32) {
+            const int4 qi = a.xq[gi];
+            const float fpi = a.fp32[gi];
+            Kahan32 fx, fy, fz;
+            for (int k = 0; k < m; ++k) {
+                const uint32_t e = a.nbr[I.list_off + (long long)k * I.n + i];
+                const int j = (int)(e & kIdxMask), code = (int)(e >> kIdxBits);
+                const int4 qj = a.xq[I.off + j];
+                int dx = wrap_sub(qj.x, qi.x), dy = wrap_sub(qj.y, qi.y), dz = wrap_sub(qj.z, qi.z);
+                if (code != kCodeZero) {
+                    dx = wrap_sub(dx, (int)((unsigned)(code % 5 - 2) * (unsigned)I.Lq[0]));
+                    dy = wrap_sub(dy, (int)((unsigned)((code / 5) % 5 - 2) * (unsigned)I.Lq[1]));
+                    dz = wrap_sub(dz, (int)((unsigned)(code / 25 - 2) * (unsigned)I.Lq[2]));
+                }
+                const long long r2q = (long long)dx * dx + (long long)dy * dy + (long long)dz * dz;
+                if (r2q >= P.rc2q) continue;
+                float rinv, phi, dphi, g, dg;
+                rgl_pair32(P, r2q, et32, rinv, phi, dphi, g, dg);
+                const float fs = (2.f * dphi + (fpi + a.fp32[I.off + j]) * dg) * rinv * P.qinv;
+                fx.add(fs * (float)dx);
+                fy.add(fs * (float)dy);
+                fz.add(fs * (float)dz);
+            }
+            a.f[gi] = make_dvec4(fx.value(), fy.value(), fz.value(), 0.0);
+        } else {
+            const dvec4 xi = a.x[gi];
+            const double fpi = a.fp64[gi];
+            double fx = 0.0, fy = 0.0, fz = 0.0;
+            for (int k = 0; k < m; ++k) {
+                const uint32_t e = a.nbr[I.list_off + (long long)k * I.n + i];
+                const int j = (int)(e & kIdxMask), code = (int)(e >> kIdxBits);
+                const dvec4 xj = a.x[I.off + j];
+                double dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
+                if (code != kCodeZero) {
+                    dx -= (code % 5 - 2) * I.L[0];
+                    dy -= ((code / 5) % 5 - 2) * I.L[1];
+                    dz -= (code / 25 - 2) * I.L[2];
+                }
+                const double r2 = dx * dx + dy * dy + dz * dz;
+                if (!(r2 < P.rc2)) continue;
+                double rinv, phi, dphi, g, dg;
+                rgl_pair64(P, r2, etab, rinv, phi, dphi, g, dg);
+                const double fs = (2.0 * dphi + (fpi + a.fp64[I.off + j]) * dg) * rinv;
+                fx += fs * dx;
+                fy += fs * dy;
+                fz += fs * dz;
+            }
+            a.f[gi] = make_dvec4(fx, fy, fz, 0.0);
+        }
+    }
+    return E;
+}
+
+// FP64 reductions of (F, v) of one system into sh, then Algorithm 2.
+__device__ __forceinline__ void b_reduce_control(const BArgs& a, const BInst& I, BShared& sh, double E,
+                                 double* red, bool first, unsigned long long t0) {
+    double P = 0.0, F2 = 0.0, V2 = 0.0, fa2 = 0.0, fin = 0.0;
+    for (int i = threadIdx.x; i < I.n; i += blockDim.x) {
+        const dvec4 f = a.f[I.off + i], v = a.v[I.off + i];
+        P += f.x * v.x + f.y * v.y + f.z * v.z;
+        const double q = f.x * f.x + f.y * f.y + f.z * f.z;
+        F2 += q;
+        V2 += v.x * v.x + v.y * v.y + v.z * v.z;
+        fa2 = fmax(fa2, q);
+        fin = fmax(fin, fmax(fabs(f.x), fmax(fabs(f.y), fabs(f.z))));
+    }
+    P = bsum(P, red);
+    F2 = bsum(F2, red);
+    V2 = bsum(V2, red);
+    fa2 = bmax(fa2, red);
+    fin = bmax(fin, red);
+    if (threadIdx.x == 0) {
+        sh.P = P;
+        sh.F2 = F2;
+        sh.V2 = V2;
+        sh.fa2 = fa2;
+        sh.fin = fin;
+        sh.E = E;
+        bool stop;
+        if (sh.status != ST_OK) {
+            sh.fs.evals += 1;
+            stop = true;
+        } else if (!isfinite(E) || !isfinite(F2) || !isfinite(V2)) {
+            sh.fs.evals += 1;
+            sh.status = ST_NONFINITE;
+            stop = true;
+        } else if (a.budget_ns && globaltimer_ns() - t0 > a.budget_ns) {
+            sh.fs.evals += 1;
+            sh.status = ST_TIMEOUT;
+            stop = true;
+        } else {
+            stop = fire_control_step(a.prm, sh.fs, P, F2, V2, fa2, fin);
+        }
+        sh.done = stop ? 1 : 0;
+    }
+    __syncthreads();
+    (void)first;
+}
+
+template <bool F32>
+__global__ void __launch_bounds__(512, 1) k_batch_relax(BArgs a) {
+    extern __shared__ int smem[];
+    __shared__ double etab[kExpTableSize];
+    __shared__ float et32[kExp32TableSize];
+    __shared__ double red[32];
+    __shared__ BShared sh;
+    int* s_count = smem;
+    int* s_start = smem + a.max_cells;
+    int* s_atoms = smem + 2 * a.max_cells + 1;
+    for (int t = threadIdx.x; t < kExpTableSize; t += blockDim.x) etab[t] = a.exp_table[t];
+    for (int t = threadIdx.x; t < kExp32TableSize; t += blockDim.x) et32[t] = a.exp32_table[t];
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const int k = atomicAdd(a.queue, 1);
+            sh.sys = k < a.n_sys ? a.order[k] : -1;
+        }
+        __syncthreads();
+        const int sys = sh.sys;
+        if (sys < 0) return;
+        const BInst I = a.inst[sys];
+        const unsigned long long t0 = globaltimer_ns();
+        // set-up: positions in, v = 0, FIRE state (Algorithm 2 initialisation)
+        int bad = 0;
+        for (int i = threadIdx.x; i < I.n; i += blockDim.x) {
+            const long long gi = I.off + i;
+            const double* p = a.pos_io + 3 * gi;
+            if (!isfinite(p[0]) || !isfinite(p[1]) || !isfinite(p[2])) bad = 1;
+            a.x[gi] = make_dvec4(p[0], p[1], p[2], 0.0);
+            a.xf[gi] = make_float4((float)p[0], (float)p[1], (float)p[2], 0.f);
+            if (F32)
+                a.xq[gi] = make_int4(to_fixed(p[0], a.qscale), to_fixed(p[1], a.qscale),
+                                     to_fixed(p[2], a.qscale), 0);
+            a.v[gi] = make_dvec4(0.0, 0.0, 0.0, 0.0);
+        }
+        const double anybad = bmax((double)bad, red);
+        if (threadIdx.x == 0) {
+            fire_scal_init(a.prm, sh.fs);
+            sh.status = anybad > 0.0 ? ST_NONFINITE : ST_OK;
+            sh.builds = 0;
+            sh.done = 0;
+        }
+        __syncthreads();
+        b_build(a, I, s_count, s_start, s_atoms, sh, red);
+        double E = b_forces<F32>(a, I, etab, et32, red);
+        b_reduce_control(a, I, sh, E, red, true, t0);
+        while (!sh.done) {
+            const FireScal fs = sh.fs;
+            double dmax = 0.0;
+            for (int i = threadIdx.x; i < I.n; i += blockDim.x) {
+                const long long gi = I.off + i;
+                dvec4 x = a.x[gi], v = a.v[gi];
+                fire_update_atom(fs, x, v, a.f[gi]);
+                a.x[gi] = x;
+                a.v[gi] = v;
+                a.xf[gi] = make_float4((float)x.x, (float)x.y, (float)x.z, 0.f);
+                if (F32)
+                    a.xq[gi] = make_int4(to_fixed(x.x, a.qscale), to_fixed(x.y, a.qscale),
+                                         to_fixed(x.z, a.qscale), 0);
+                const dvec4 r = a.xref[gi];
+                const double ddx = x.x - r.x, ddy = x.y - r.y, ddz = x.z - r.z;
+                dmax = fmax(dmax, ddx * ddx + ddy * ddy + ddz * ddz);
+            }
+            dmax = bmax(dmax, red);
+            if (dmax > I.half_skin2) b_build(a, I, s_count, s_start, s_atoms, sh, red);
+            E = b_forces<F32>(a, I, etab, et32, red);
+            b_reduce_control(a, I, sh, E, red, false, t0);
+        }
+        // write back
+        for (int i = threadIdx.x; i < I.n; i += blockDim.x) {
+            const long long gi = I.off + i;
+            const dvec4 x = a.x[gi];
+            double* p = a.pos_io + 3 * gi;
+            p[0] = x.x;
+            p[1] = x.y;
+            p[2] = x.z;
+            if (a.f_out) {
+                const dvec4 f = a.f[gi];
+                double* q = a.f_out + 3 * gi;
+                q[0] = f.x;
+                q[1] = f.y;
+                q[2] = f.z;
+            }
+        }
+        if (threadIdx.x == 0) {
+            BRes& r = a.res[sys];
+            r.energy = sh.E;
+            r.fmax2 = sh.fa2;
+            r.F2 = sh.F2;
+            r.finf = sh.fin;
+            r.dt = sh.fs.dt;
+            r.alpha = sh.fs.alpha;
+            r.iter = sh.fs.iter;
+            r.evals = sh.fs.evals;
+            r.builds = sh.builds;
+            r.stop = sh.fs.stop;
+            r.status = sh.status;
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace fire2
+
+// ---------------------------------------------------------------------------
+// host side
+
+struct fire_batch_state {
+    int n_sys = 0;
+    long long n_total = 0;
+    std::vector<long long> off;      // n_sys + 1
+    BArgs args{};
+    BInst* d_inst = nullptr;
+    BRes* d_res = nullptr;
+    int* d_order = nullptr;
+    int* d_queue = nullptr;
+    std::vector<BInst> inst;
+    std::vector<int> order;
+    long long list_slots = 0;
+    fire_batch_tuning_t tune{256, 2, 0, 0};
+    int sms = 0;
+    size_t smem_bytes = 0;
+};
+
+// Shared host helpers implemented in fire2_api.cu.
+fire_status fire2_batch_fail(fire_handle_t* h, fire_status code, const char* msg);
+fire_batch_state* fire2_batch_of(fire_handle_t* h);
+const PotC& fire2_potc(fire_handle_t* h);
+const fire_potential_t& fire2_pot(fire_handle_t* h);
+const fire_params_t& fire2_params(fire_handle_t* h);
+const fire_system_t& fire2_sys(fire_handle_t* h);
+double fire2_budget(fire_handle_t* h);
+const double* fire2_exp_table(fire_handle_t* h);
+const float* fire2_exp32_table(fire_handle_t* h);
+double fire2_qscale(fire_handle_t* h);
+cudaStream_t fire2_stream(fire_handle_t* h);
+
+#define BCK(call)                                                                         \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return fire2_batch_fail(h, e_ == cudaErrorMemoryAllocation ? FIRE_ERR_NOMEM    \
+                                                                       : FIRE_ERR_CUDA,   \
+                                    cudaGetErrorString(e_));                              \
+    } while (0)
+
+#define FIRE2_HIDDEN __attribute__((visibility("hidden")))
+
+static void free_batch(fire_batch_state* b) {
+    if (!b) return;
+    BArgs& a = b->args;
+    void* ptrs[] = {a.x, a.v, a.f, a.xref, a.xq, a.xf, a.fp64, a.fp32, a.nbr, a.nnbr, a.pos_io,
+                    b->d_inst, b->d_res, b->d_order, b->d_queue};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    delete b;
+}
+
+FIRE2_HIDDEN void fire2_batch_free(fire_batch_state* b) { free_batch(b); }
+
+// Geometry of every system for the given boxes; sizes the lists.
+static fire_status batch_geometry(fire_handle_t* h, fire_batch_state* b, const double* boxes) {
+    const fire_potential_t& pot = fire2_pot(h);
+    const fire_system_t& sys = fire2_sys(h);
+    const double rc = pot.rc;
+    const double qscale = fire2_qscale(h);
+    long long slots = 0;
+    int max_cells = 1, max_atoms = 1;
+    for (int s = 0; s < b->n_sys; ++s) {
+        BInst& I = b->inst[s];
+        I.off = b->off[s];
+        I.n = (int)(b->off[s + 1] - b->off[s]);
+        double skin = pot.skin;
+        for (int k = 0; k < 3; ++k) {
+            const double L = boxes[3 * s + k];
+            if (!(L > 0.0) || !std::isfinite(L)) return fire2_batch_fail(h, FIRE_ERR_ARG, "box lengths must be > 0");
+            if (sys.periodic[k] && L < 2.0 * rc)
+                return fire2_batch_fail(h, FIRE_ERR_ARG, "a periodic box is shorter than twice the cut-off");
+            if (sys.periodic[k]) skin = std::min(skin, 0.5 * L * (1.0 - 1e-12) - rc);
+        }
+        skin = std::max(skin, 0.0);
+        const double rl = rc + skin;
+        bool cells = true;
+        double lmax = 0.0, vol = 1.0;
+        for (int k = 0; k < 3; ++k) {
+            const double L = boxes[3 * s + k];
+            I.L[k] = L;
+            I.Linv[k] = 1.0 / L;
+            I.Lf[k] = (float)L;
+            I.Linvf[k] = (float)(1.0 / L);
+            I.per[k] = sys.periodic[k] ? 1 : 0;
+            I.Lq[k] = (int)(unsigned)(unsigned long long)std::llrint(L * qscale);
+            I.nc[k] = (int)std::floor(L / rl);
+            if (!I.per[k] || I.nc[k] < 3) cells = false;
+            lmax = std::max(lmax, L);
+            vol *= L;
+        }
+        if (!cells) I.nc[0] = I.nc[1] = I.nc[2] = 0;
+        else {
+            max_cells = std::max(max_cells, I.nc[0] * I.nc[1] * I.nc[2]);
+            max_atoms = std::max(max_atoms, I.n);
+        }
+        const double margin = 1e-3 * rc + 8.0 * 1.2e-7 * (2.0 * lmax);
+        I.rlist2f = (float)((rl + margin) * (rl + margin));
+        I.half_skin2 = 0.25 * skin * skin;
+        const double full = 4.0 / 3.0 * M_PI * rl * rl * rl * (I.n / vol);
+        I.cap = (int)std::min<long long>(std::max(I.n - 1, 1), (long long)std::ceil(1.6 * full) + 16);
+        I.list_off = slots;
+        slots += (long long)I.cap * I.n;
+    }
+    b->args.max_cells = max_cells;
+    b->args.max_atoms_smem = max_atoms;
+    b->smem_bytes = (size_t)(2 * max_cells + 1 + max_atoms) * sizeof(int);
+    if (slots > b->list_slots) {
+        cudaFree(b->args.nbr);
+        b->args.nbr = nullptr;
+        BCK(cudaMalloc(&b->args.nbr, (size_t)slots * sizeof(uint32_t)));
+        b->list_slots = slots;
+    }
+    return FIRE_OK;
+}
+
+FIRE2_HIDDEN fire_status fire2_batch_create(fire_handle_t* h, int32_t n_sys,
+                                            const int64_t* offsets, fire_batch_state** out) {
+    fire_batch_state* b = new (std::nothrow) fire_batch_state();
+    if (!b) return fire2_batch_fail(h, FIRE_ERR_NOMEM, "host allocation failed");
+    b->n_sys = n_sys;
+    b->off.assign(offsets, offsets + n_sys + 1);
+    b->n_total = offsets[n_sys];
+    b->inst.resize(n_sys);
+    b->order.resize(n_sys);
+    std::iota(b->order.begin(), b->order.end(), 0);
+    std::stable_sort(b->order.begin(), b->order.end(), [&](int x, int y) {
+        return (offsets[x + 1] - offsets[x]) > (offsets[y + 1] - offsets[y]);
+    });
+    const size_t n = (size_t)b->n_total;
+    BArgs& a = b->args;
+    const bool f32 = fire2_pot(h).precision == FIRE_PREC_FP32_PAIR;
+    auto fail_free = [&](cudaError_t e) {
+        free_batch(b);
+        return fire2_batch_fail(h, e == cudaErrorMemoryAllocation ? FIRE_ERR_NOMEM : FIRE_ERR_CUDA,
+                                cudaGetErrorString(e));
+    };
+    cudaError_t e = cudaSuccess;
+#define BA(ptr, bytes) \
+    if (e == cudaSuccess) e = cudaMalloc(&(ptr), (bytes))
+    BA(a.x, n * sizeof(dvec4));
+    BA(a.v, n * sizeof(dvec4));
+    BA(a.f, n * sizeof(dvec4));
+    BA(a.xref, n * sizeof(dvec4));
+    BA(a.xf, n * sizeof(float4));
+    if (f32) {
+        BA(a.xq, n * sizeof(int4));
+        BA(a.fp32, n * sizeof(float));
+    } else {
+        BA(a.fp64, n * sizeof(double));
+    }
+    BA(a.nnbr, n * sizeof(int));
+    BA(a.pos_io, 3 * n * sizeof(double));
+    BA(b->d_inst, (size_t)n_sys * sizeof(BInst));
+    BA(b->d_res, (size_t)n_sys * sizeof(BRes));
+    BA(b->d_order, (size_t)n_sys * sizeof(int));
+    BA(b->d_queue, sizeof(int));
+#undef BA
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->d_order, b->order.data(), (size_t)n_sys * sizeof(int), cudaMemcpyHostToDevice);
+    int dev = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return fail_free(e);
+    *out = b;
+    return FIRE_OK;
+}
+
+// Launches one batched relaxation with the current tuning (asynchronous).
+static fire_status batch_launch(fire_handle_t* h, fire_batch_state* b, double ftol,
+                                int64_t maxiter, double* d_fout, cudaStream_t s) {
+    BArgs& a = b->args;
+    a.n_sys = b->n_sys;
+    a.order = b->d_order;
+    a.queue = b->d_queue;
+    a.inst = b->d_inst;
+    a.res = b->d_res;
+    a.f_out = d_fout;
+    const fire_params_t& p = fire2_params(h);
+    FireParamsD& q = a.prm;
+    std::memset(&q, 0, sizeof q);
+    q.ftol = ftol;
+    q.maxiter = maxiter;
+    q.dt_start = p.dt_start;
+    q.dtmax = p.tmax * p.dt_start;
+    q.dtmin = p.tmin * p.dt_start;
+    q.dtgrow = p.dtgrow;
+    q.dtshrink = p.dtshrink;
+    q.alpha0 = p.alpha0;
+    q.alphashrink = p.alphashrink;
+    q.mass = fire2_sys(h).mass;
+    q.delaystep = p.delaystep;
+    q.vdfmax = p.vdfmax;
+    q.halfstepback = p.halfstepback;
+    q.initialdelay = p.initialdelay;
+    q.norm = p.norm;
+    a.budget_ns = (unsigned long long)(fire2_budget(h) * 1e9);
+    a.P = fire2_potc(h);
+    a.exp_table = fire2_exp_table(h);
+    a.exp32_table = fire2_exp32_table(h);
+    a.qscale = fire2_qscale(h);
+    const bool f32 = fire2_pot(h).precision == FIRE_PREC_FP32_PAIR;
+    const int threads = b->tune.threads_per_block;
+    const int grid = std::max(1, std::min(b->n_sys, b->sms * b->tune.ctas_per_sm));
+    BCK(cudaMemcpyAsync(b->d_inst, b->inst.data(), (size_t)b->n_sys * sizeof(BInst),
+                        cudaMemcpyHostToDevice, s));
+    BCK(cudaMemsetAsync(b->d_queue, 0, sizeof(int), s));
+    if (f32) {
+        BCK(cudaFuncSetAttribute(k_batch_relax<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)b->smem_bytes));
+        k_batch_relax<true><<<grid, threads, b->smem_bytes, s>>>(a);
+    } else {
+        BCK(cudaFuncSetAttribute(k_batch_relax<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)b->smem_bytes));
+        k_batch_relax<false><<<grid, threads, b->smem_bytes, s>>>(a);
+    }
+    BCK(cudaGetLastError());
+    return FIRE_OK;
+}
+
+static fire_status batch_collect(fire_handle_t* h, fire_batch_state* b, fire_result_t* out,
+                                 cudaStream_t s) {
+    std::vector<BRes> res(b->n_sys);
+    BCK(cudaMemcpyAsync(res.data(), b->d_res, (size_t)b->n_sys * sizeof(BRes),
+                        cudaMemcpyDeviceToHost, s));
+    BCK(cudaStreamSynchronize(s));
+    int worst = ST_OK;
+    for (int k = 0; k < b->n_sys; ++k) {
+        const BRes& r = res[k];
+        if (r.status != ST_OK && worst == ST_OK) worst = r.status;
+        if (out) {
+            fire_result_t& o = out[k];
+            o.energy = r.energy;
+            o.iterations = r.iter;
+            o.force_evals = r.evals;
+            o.nbr_builds = r.builds;
+            o.stop = r.stop;
+            o.reserved = r.status;
+            o.fmax_atom = std::sqrt(r.fmax2);
+            o.f2norm = std::sqrt(r.F2);
+            o.finf = r.finf;
+            o.dt_final = r.dt;
+            o.alpha_final = r.alpha;
+        }
+    }
+    switch (worst) {
+        case ST_OK: return FIRE_OK;
+        case ST_NONFINITE: return fire2_batch_fail(h, FIRE_ERR_NONFINITE, "non-finite force, energy or position in a system");
+        case ST_NBR_OVERFLOW: return fire2_batch_fail(h, FIRE_ERR_NBR_OVERFLOW, "neighbour list overflow in a system");
+        case ST_TIMEOUT: return fire2_batch_fail(h, FIRE_ERR_TIMEOUT, "a relaxation exceeded the time budget");
+        case ST_RANGE: return fire2_batch_fail(h, FIRE_ERR_ARG, "positions lie more than one box length outside their box");
+        default: return fire2_batch_fail(h, FIRE_ERR_CUDA, "unknown device status");
+    }
+}
+
+extern "C" {
+
+fire_status fire_minimize_batch_dev(fire_handle_t* h, double* d_pos, const double* boxes,
+                                    double ftol, int64_t maxiter, fire_result_t* out,
+                                    double* d_forces, void* stream) {
+    fire_batch_state* b = h ? fire2_batch_of(h) : nullptr;
+    if (!b) return h ? fire2_batch_fail(h, FIRE_ERR_STATE, "handle was not created by fire_batch_init")
+                     : FIRE_ERR_ARG;
+    if (!d_pos || !boxes || !out) return fire2_batch_fail(h, FIRE_ERR_ARG, "NULL argument");
+    if (!(ftol >= 0.0) || maxiter < 0) return fire2_batch_fail(h, FIRE_ERR_ARG, "need ftol >= 0 and maxiter >= 0");
+    fire_status st = batch_geometry(h, b, boxes);
+    if (st != FIRE_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t bytes = (size_t)3 * b->n_total * sizeof(double);
+    BCK(cudaMemcpyAsync(b->args.pos_io, d_pos, bytes, cudaMemcpyDeviceToDevice, s));
+    st = batch_launch(h, b, ftol, maxiter, d_forces, s);
+    if (st != FIRE_OK) return st;
+    st = batch_collect(h, b, out, s);
+    if (st != FIRE_OK) return st;
+    BCK(cudaMemcpyAsync(d_pos, b->args.pos_io, bytes, cudaMemcpyDeviceToDevice, s));
+    BCK(cudaStreamSynchronize(s));
+    return FIRE_OK;
+}
+
+fire_status fire_minimize_batch(fire_handle_t* h, double* pos, const double* boxes, double ftol,
+                                int64_t maxiter, fire_result_t* out, double* forces) {
+    fire_batch_state* b = h ? fire2_batch_of(h) : nullptr;
+    if (!b) return h ? fire2_batch_fail(h, FIRE_ERR_STATE, "handle was not created by fire_batch_init")
+                     : FIRE_ERR_ARG;
+    if (!pos || !boxes || !out) return fire2_batch_fail(h, FIRE_ERR_ARG, "NULL argument");
+    if (!(ftol >= 0.0) || maxiter < 0) return fire2_batch_fail(h, FIRE_ERR_ARG, "need ftol >= 0 and maxiter >= 0");
+    fire_status st = batch_geometry(h, b, boxes);
+    if (st != FIRE_OK) return st;
+    cudaStream_t s = fire2_stream(h);
+    const size_t bytes = (size_t)3 * b->n_total * sizeof(double);
+    double* d_f = nullptr;
+    if (forces) BCK(cudaMalloc(&d_f, bytes));
+    BCK(cudaMemcpyAsync(b->args.pos_io, pos, bytes, cudaMemcpyHostToDevice, s));
+    st = batch_launch(h, b, ftol, maxiter, d_f, s);
+    if (st == FIRE_OK) st = batch_collect(h, b, out, s);
+    if (st == FIRE_OK) {
+        std::vector<double> tmp((size_t)3 * b->n_total);
+        cudaError_t e = cudaMemcpy(tmp.data(), b->args.pos_io, bytes, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess && forces) e = cudaMemcpy(forces, d_f, bytes, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) st = fire2_batch_fail(h, FIRE_ERR_CUDA, cudaGetErrorString(e));
+        else std::memcpy(pos, tmp.data(), bytes);
+    }
+    if (d_f) cudaFree(d_f);
+    return st;
+}
+
+fire_status fire_batch_set_tuning(fire_handle_t* h, const fire_batch_tuning_t* t) {
+    fire_batch_state* b = h ? fire2_batch_of(h) : nullptr;
+    if (!b) return h ? fire2_batch_fail(h, FIRE_ERR_STATE, "handle was not created by fire_batch_init")
+                     : FIRE_ERR_ARG;
+    if (!t || t->threads_per_block < 32 || t->threads_per_block > 512 ||
+        t->threads_per_block % 32 != 0 || t->ctas_per_sm < 1 || t->ctas_per_sm > 32)
+        return fire2_batch_fail(h, FIRE_ERR_ARG, "threads_per_block must be a multiple of 32 in "
+                                                 "[32, 512] and ctas_per_sm in [1, 32]");
+    b->tune = *t;
+    return FIRE_OK;
+}
+
+fire_status fire_batch_autotune(fire_handle_t* h, const double* pos, const double* boxes,
+                                int32_t iters, fire_batch_tuning_t* chosen) {
+    fire_batch_state* b = h ? fire2_batch_of(h) : nullptr;
+    if (!b) return h ? fire2_batch_fail(h, FIRE_ERR_STATE, "handle was not created by fire_batch_init")
+                     : FIRE_ERR_ARG;
+    if (!pos || !boxes || iters < 1) return fire2_batch_fail(h, FIRE_ERR_ARG, "need pos, boxes, iters >= 1");
+    fire_status st = batch_geometry(h, b, boxes);
+    if (st != FIRE_OK) return st;
+    cudaStream_t s = fire2_stream(h);
+    const size_t bytes = (size_t)3 * b->n_total * sizeof(double);
+    double* d_src = nullptr;
+    BCK(cudaMalloc(&d_src, bytes));
+    BCK(cudaMemcpy(d_src, pos, bytes, cudaMemcpyHostToDevice));
+    const int threads_c[] = {64, 128, 256, 512};
+    const int ctas_c[] = {1, 2, 4, 8};
+    const fire_batch_tuning_t saved = b->tune;
+    double best = 1e300;
+    fire_batch_tuning_t best_t = saved;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    for (int th : threads_c) {
+        for (int c : ctas_c) {
+            if (th * c > 2048) continue;   // more threads than an SM holds
+            b->tune.threads_per_block = th;
+            b->tune.ctas_per_sm = c;
+            cudaMemcpyAsync(b->args.pos_io, d_src, bytes, cudaMemcpyDeviceToDevice, s);
+            cudaEventRecord(e0, s);
+            st = batch_launch(h, b, 0.0, iters, nullptr, s);   // ftol = 0: every system runs `iters`
+            cudaEventRecord(e1, s);
+            if (st != FIRE_OK) break;
+            if (cudaEventSynchronize(e1) != cudaSuccess) {
+                st = fire2_batch_fail(h, FIRE_ERR_CUDA, "autotune launch failed");
+                break;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) {
+                best = ms;
+                best_t = b->tune;
+            }
+        }
+        if (st != FIRE_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(d_src);
+    if (st != FIRE_OK) {
+        b->tune = saved;
+        return st;
+    }
+    b->tune = best_t;
+    if (chosen) *chosen = best_t;
+    return FIRE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,281 @@
+// Device definitions shared by the single-system kernels (fire2_device.cuh)
+// and the batched persistent kernel (fire2_batch.cu): data types, launch
+// constants, block reductions, geometry helpers and the RGL pair functions.
+// Only inline functions and types live here, so several translation units
+// may include it.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fire2_math.cuh"
+
+namespace fire2 {
+
+// Per-atom 3-vectors live in 32-byte aligned, zero-padded double quads so a
+// load or store of one atom is a single aligned 32-byte sector.
+using dvec4 = double4_32a;
+__host__ __device__ __forceinline__ dvec4 make_dvec4(double x, double y, double z, double w) {
+    return make_double4_32a(x, y, z, w);
+}
+
+constexpr uint32_t kIdxBits = 25;
+constexpr uint32_t kIdxMask = (1u << kIdxBits) - 1u;
+constexpr int kCodeZero = 62;  // image code of the zero shift, (2 + 5*2 + 25*2)
+constexpr int kForceBlock = 128;
+constexpr int kElemBlock = 256;
+constexpr int kCtlThreads = 512;
+
+enum { ST_OK = 0, ST_NONFINITE = 4, ST_NBR_OVERFLOW = 5, ST_TIMEOUT = 6, ST_RANGE = 8 };
+enum { STOP_FTOL = 0, STOP_MAXITER = 1, STOP_MAXVDOTF = 2 };
+enum { POT_LJ = 0, POT_RGL = 1 };
+enum { CTL_INITIAL = 0, CTL_LOOP = 1, CTL_EVAL = 2 };
+
+// Potential constants, passed by value.
+struct PotC {
+    int kind;
+    double rc2;            // interaction cut-off squared
+    // LJ
+    double eps, sigma2, lj_shift;
+    // RGL
+    double A, xi2, p, q2, r0inv, p_r0, q2_r0, rs, rc, winv;
+    ExpC ex;               // constants of the table-driven exponential
+    // FP32-pair form: FP32 copies of the constants; r^2 tests in fixed point
+    Exp32C ex32;
+    float A_f, xi2_f, p_f, q2_f, r0_f, p_r0_f, q2_r0_f, rs_f, winv_f;
+    long long rc2q, r0sq_q;   // rc^2 and r0^2 in (fixed-point unit)^2
+    float qinv, qinv2;        // 1 / qscale, 1 / qscale^2
+};
+
+// ---------------------------------------------------------------------------
+// small helpers
+
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Block-wide sum; result valid in thread 0.  `sh` holds >= 32 doubles.
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (w == 0) {
+        r = (lane < (int)(blockDim.x >> 5)) ? sh[lane] : 0.0;
+        r = warp_sum(r);
+    }
+    return r;
+}
+__device__ __forceinline__ double block_max(double v, double* sh) {
+    v = warp_max(v);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (w == 0) {
+        r = (lane < (int)(blockDim.x >> 5)) ? sh[lane] : 0.0;
+        r = warp_max(r);
+    }
+    return r;
+}
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ int cell_coord(double x, double Linv, int nc) {
+    double u = x * Linv;
+    u -= floor(u);
+    int c = (int)(u * nc);
+    return c < 0 ? 0 : (c >= nc ? nc - 1 : c);
+}
+
+// Fixed-point coordinate (units of 1/qscale) modulo 2^32.  Differences of two
+// such values, taken in 32-bit wrap-around arithmetic, are exact whenever the
+// true separation is below 2^31 / qscale (qscale is chosen so that every list
+// pair qualifies), whatever periodic image the raw coordinates sit in.
+__device__ __forceinline__ int to_fixed(double x, double qscale) {
+    return (int)(unsigned)(unsigned long long)__double2ll_rn(x * qscale);
+}
+
+__device__ __forceinline__ int wrap_sub(int a, int b) { return (int)((unsigned)a - (unsigned)b); }
+
+// Upper half-space test on the minimum-image vector d = x_j - x_i: exactly
+// one of (i, j) and (j, i) passes because IEEE subtraction, rounding to the
+// nearest integer and the squares are all symmetric under d -> -d.
+__device__ __forceinline__ bool upper_half(float dx, float dy, float dz) {
+    return dz > 0.f || (dz == 0.f && (dy > 0.f || (dy == 0.f && dx > 0.f)));
+}
+
+// RGL pair terms in FP64 (Sec. 5.2 EAM family, second-moment form):
+// phi = A e^{-p s} S(r), g = xi^2 e^{-2q s} S(r), s = r/r0 - 1, with the
+// quintic taper S on [rs, rc).  Returns 1/r and the derivatives.
+__device__ __forceinline__ void rgl_pair64(const PotC& P, double r2, const double* etab,
+                                           double& rinv, double& phi, double& dphi, double& g,
+                                           double& dg) {
+    rinv = rsqrt(r2);
+    const double r = r2 * rinv;
+    const double s = r * P.r0inv - 1.0;
+    const double ep = P.A * exp_tang(-P.p * s, P.ex, etab);
+    const double eq = P.xi2 * exp_tang(-P.q2 * s, P.ex, etab);
+    double S = 1.0, dS = 0.0;
+    if (r > P.rs) {
+        const double t = (r - P.rs) * P.winv;
+        const double t2 = t * t, t3 = t2 * t;
+        S = 1.0 - 10.0 * t3 + 15.0 * t3 * t - 6.0 * t3 * t2;
+        dS = (-30.0 * t2 + 60.0 * t3 - 30.0 * t3 * t) * P.winv;
+    }
+    phi = ep * S;
+    g = eq * S;
+    dphi = ep * (-P.p_r0 * S + dS);
+    dg = eq * (-P.q2_r0 * S + dS);
+}
+
+// RGL pair terms in FP32 from the exact fixed-point r^2.
+__device__ __forceinline__ void rgl_pair32(const PotC& P, long long r2q, const float* et,
+                                           float& rinv, float& phi, float& dphi, float& g,
+                                           float& dg) {
+    const float r2 = __ll2float_rn(r2q) * P.qinv2;
+    const float u = __ll2float_rn(r2q - P.r0sq_q) * P.qinv2;   // r^2 - r0^2
+    rinv = rsqrtf(r2);
+    const float r = r2 * rinv;
+    const float s = u / (P.r0_f * (r + P.r0_f));                // r/r0 - 1
+    const float ep = P.A_f * exp32_tang(-P.p_f * s, P.ex32, et);
+    const float eq = P.xi2_f * exp32_tang(-P.q2_f * s, P.ex32, et);
+    float S = 1.f, dS = 0.f;
+    if (r > P.rs_f) {
+        const float t = (r - P.rs_f) * P.winv_f;
+        const float t2 = t * t, t3 = t2 * t;
+        S = 1.f - 10.f * t3 + 15.f * t3 * t - 6.f * t3 * t2;
+        dS = (-30.f * t2 + 60.f * t3 - 30.f * t3 * t) * P.winv_f;
+    }
+    phi = ep * S;
+    g = eq * S;
+    dphi = ep * (-P.p_r0_f * S + dS);
+    dg = eq * (-P.q2_r0_f * S + dS);
+}
+
+// ---------------------------------------------------------------------------
+// FIRE 2.0 scalar control (Algorithm 2) and the element-wise update
+// (Algorithm 4), shared by the single-system and the batched kernels.
+
+// Parameters of Table 1 and the call arguments, device copy.
+struct FireParamsD {
+    double ftol;
+    long long maxiter;
+    double dt_start, dtmax, dtmin, dtgrow, dtshrink, alpha0, alphashrink, mass;
+    int delaystep, vdfmax, halfstepback, initialdelay, norm, pad;
+};
+
+// Scalar state of Algorithm 2 plus the coefficients the next update applies.
+struct FireScal {
+    double dt, alpha;
+    long long npos, nneg, iter, evals;
+    int stop, zero_v, mix, pad;
+    double dtm;                              // dt / m of the next kick
+    double halfstep, dt_cur, mix_a, mix_fv;  // x -= halfstep v; v = (1-a) v' + a |v'| F/|F|
+};
+
+__host__ __device__ inline void fire_scal_init(const FireParamsD& p, FireScal& s) {
+    s.dt = p.dt_start;
+    s.alpha = p.alpha0;
+    s.npos = s.nneg = s.iter = s.evals = 0;
+    s.stop = STOP_MAXITER;
+    s.zero_v = s.mix = s.pad = 0;
+    s.dtm = s.halfstep = s.dt_cur = s.mix_a = s.mix_fv = 0.0;
+}
+
+// Called after every force evaluation with the FP64 reductions of the
+// current (F, v).  Tests convergence (Alg. 2, after the integration), the
+// iteration budget, then prepares the next iteration: the P > 0 / P <= 0
+// branch with its counters, dt growth capped at dt_max after N_delay
+// positive steps, alpha decay, the N_P<=0 cap (MAXVDOTF, before any
+// correction), the initial delay, the dt_min guard, the half step back
+// with the shrunk dt, and the mixing coefficients of the kicked velocity
+// (|v'|^2 = |v|^2 + 2 (dt/m) P + (dt/m)^2 |F|^2).  Returns true to stop.
+__device__ inline bool fire_control_step(const FireParamsD& p, FireScal& s, double P, double F2,
+                                         double V2, double fa2, double fin) {
+    s.evals += 1;
+    const double fn = p.norm == 1 ? sqrt(F2) : (p.norm == 2 ? fin : sqrt(fa2));
+    if (fn < p.ftol) {
+        s.stop = STOP_FTOL;
+        return true;
+    }
+    if (s.iter >= p.maxiter) {
+        s.stop = STOP_MAXITER;
+        return true;
+    }
+    const long long i = ++s.iter;
+    if (P > 0.0) {
+        s.npos += 1;
+        s.nneg = 0;
+        if (s.npos > p.delaystep) {
+            s.dt = fmin(s.dt * p.dtgrow, p.dtmax);
+            s.alpha *= p.alphashrink;
+        }
+        s.zero_v = 0;
+        s.halfstep = 0.0;
+        const double dtm = s.dt / p.mass;
+        const double vk2 = fmax(V2 + 2.0 * dtm * P + dtm * dtm * F2, 0.0);
+        const double fn2 = sqrt(F2);
+        s.mix = fn2 > 0.0;
+        s.mix_a = s.alpha;
+        s.mix_fv = fn2 > 0.0 ? sqrt(vk2) / fn2 : 0.0;
+    } else {
+        s.npos = 0;
+        s.nneg += 1;
+        if (s.nneg > p.vdfmax) {
+            s.stop = STOP_MAXVDOTF;
+            s.iter = i - 1;
+            return true;
+        }
+        if (!(p.initialdelay && i < p.delaystep)) {
+            if (s.dt * p.dtshrink >= p.dtmin) s.dt *= p.dtshrink;
+            s.alpha = p.alpha0;
+        }
+        s.zero_v = 1;
+        s.halfstep = p.halfstepback ? 0.5 * s.dt : 0.0;
+        s.mix = 0;
+        s.mix_a = 0.0;
+        s.mix_fv = 0.0;
+    }
+    s.dt_cur = s.dt;
+    s.dtm = s.dt / p.mass;
+    return false;
+}
+
+// One atom of the element-wise step: half step back and v = 0 after P <= 0
+// (Alg. 2), then Algorithm 4: v += dt F / m, mixing (P > 0), x += dt v.
+__device__ __forceinline__ void fire_update_atom(const FireScal& s, dvec4& x, dvec4& v,
+                                                 const dvec4& f) {
+    if (s.zero_v) {
+        x.x -= s.halfstep * v.x;
+        x.y -= s.halfstep * v.y;
+        x.z -= s.halfstep * v.z;
+        v = make_dvec4(0.0, 0.0, 0.0, 0.0);
+    }
+    v.x += s.dtm * f.x;
+    v.y += s.dtm * f.y;
+    v.z += s.dtm * f.z;
+    if (s.mix) {
+        const double a = s.mix_a, afv = s.mix_a * s.mix_fv;
+        v.x = (1.0 - a) * v.x + afv * f.x;
+        v.y = (1.0 - a) * v.y + afv * f.y;
+        v.z = (1.0 - a) * v.z + afv * f.z;
+    }
+    x.x += s.dt_cur * v.x;
+    x.y += s.dt_cur * v.y;
+    x.z += s.dt_cur * v.z;
+}
+
+}  // namespace fire2

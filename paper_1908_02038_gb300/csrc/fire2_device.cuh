@@ -17,44 +17,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "fire2_math.cuh"
+#include "fire2_common.cuh"
 
 namespace fire2 {
-
-// Per-atom 3-vectors live in 32-byte aligned, zero-padded double quads so a
-// load or store of one atom is a single aligned 32-byte sector.
-using dvec4 = double4_32a;
-__host__ __device__ __forceinline__ dvec4 make_dvec4(double x, double y, double z, double w) {
-    return make_double4_32a(x, y, z, w);
-}
-
-constexpr uint32_t kIdxBits = 25;
-constexpr uint32_t kIdxMask = (1u << kIdxBits) - 1u;
-constexpr int kCodeZero = 62;  // image code of the zero shift, (2 + 5*2 + 25*2)
-constexpr int kForceBlock = 128;
-constexpr int kElemBlock = 256;
-constexpr int kCtlThreads = 512;
-
-enum { ST_OK = 0, ST_NONFINITE = 4, ST_NBR_OVERFLOW = 5, ST_TIMEOUT = 6, ST_RANGE = 8 };
-enum { STOP_FTOL = 0, STOP_MAXITER = 1, STOP_MAXVDOTF = 2 };
-enum { POT_LJ = 0, POT_RGL = 1 };
-enum { CTL_INITIAL = 0, CTL_LOOP = 1, CTL_EVAL = 2 };
-
-// Potential constants, passed by value.
-struct PotC {
-    int kind;
-    double rc2;            // interaction cut-off squared
-    // LJ
-    double eps, sigma2, lj_shift;
-    // RGL
-    double A, xi2, p, q2, r0inv, p_r0, q2_r0, rs, rc, winv;
-    ExpC ex;               // constants of the table-driven exponential
-    // FP32-pair form: FP32 copies of the constants; r^2 tests in fixed point
-    Exp32C ex32;
-    float A_f, xi2_f, p_f, q2_f, r0_f, p_r0_f, q2_r0_f, rs_f, winv_f;
-    long long rc2q, r0sq_q;   // rc^2 and r0^2 in (fixed-point unit)^2
-    float qinv, qinv2;        // 1 / qscale, 1 / qscale^2
-};
 
 // Box / neighbour geometry, passed by value.
 struct GeoC {
@@ -74,23 +39,13 @@ struct GeoC {
 
 // FIRE parameters (Table 1) and call arguments, device resident.
 struct DevState {
-    // call arguments
-    double ftol;
-    long long maxiter;
-    double dt_start, dtmax, dtmin, dtgrow, dtshrink, alpha0, alphashrink, mass;
-    int delaystep, vdfmax, halfstepback, initialdelay, norm, pad0;
+    FireParamsD prm;       // Table 1 parameters and call arguments
+    FireScal fs;           // Algorithm 2 state + update coefficients
     unsigned long long budget_ns, t_start;
-    // FIRE state (Algorithm 2)
-    double dt, alpha;
-    long long npos, nneg, iter, evals, nbr_builds;
-    int done, stop, status, pad1;
+    long long nbr_builds;
+    int done, status;
     // reductions of the current (F, v)
     double P, F2, V2, fmax2, finf, energy;
-    // update coefficients for the next k_update (see k_control)
-    int zero_v, mix, pad2, pad3;
-    double dtm;                              // dt / m of the next kick
-    double halfstep, dt_cur, mix_a, mix_fv;  // x -= halfstep*v; v' = v + dt*F/m;
-                                             // v = (1-a) v' + a*|v'|*F/|F| when mix
     unsigned long long max_disp2;           // bits of max |x - x_ref|^2 (>= 0)
 };
 
@@ -116,65 +71,12 @@ struct Bufs {
     double* e_out;         // energy (evaluation only)
 };
 
-// ---------------------------------------------------------------------------
-// small helpers
-
-__device__ __forceinline__ double warp_sum(double v) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    return v;
-}
-__device__ __forceinline__ double warp_max(double v) {
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
-    return v;
-}
-
-// Block-wide sum; result valid in thread 0.  `sh` holds >= 32 doubles.
-__device__ __forceinline__ double block_sum(double v, double* sh) {
-    v = warp_sum(v);
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) sh[w] = v;
-    __syncthreads();
-    double r = 0.0;
-    if (w == 0) {
-        r = (lane < (int)(blockDim.x >> 5)) ? sh[lane] : 0.0;
-        r = warp_sum(r);
-    }
-    return r;
-}
-__device__ __forceinline__ double block_max(double v, double* sh) {
-    v = warp_max(v);
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) sh[w] = v;
-    __syncthreads();
-    double r = 0.0;
-    if (w == 0) {
-        r = (lane < (int)(blockDim.x >> 5)) ? sh[lane] : 0.0;
-        r = warp_max(r);
-    }
-    return r;
-}
-
-__device__ __forceinline__ unsigned long long globaltimer_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
 // Image-shift table: code = (sx+2) + 5 (sy+2) + 25 (sz+2), shift = s * L.
 __device__ __forceinline__ void fill_shift_table(double3* tbl, const GeoC& g) {
     for (int t = threadIdx.x; t < 125; t += blockDim.x) {
         const int sx = t % 5 - 2, sy = (t / 5) % 5 - 2, sz = t / 25 - 2;
         tbl[t] = make_double3(sx * g.L[0], sy * g.L[1], sz * g.L[2]);
     }
-}
-
-__device__ __forceinline__ int cell_coord(double x, double Linv, int nc) {
-    double u = x * Linv;
-    u -= floor(u);
-    int c = (int)(u * nc);
-    return c < 0 ? 0 : (c >= nc ? nc - 1 : c);
 }
 
 // Records the first error of a call; later errors do not overwrite it.
@@ -188,16 +90,6 @@ __device__ __forceinline__ bool need_rebuild(const DevState* st, const GeoC& g, 
     if (st->done) return false;
     return __longlong_as_double((long long)st->max_disp2) > g.half_skin2;
 }
-
-// Fixed-point coordinate (units of 1/qscale) modulo 2^32.  Differences of two
-// such values, taken in 32-bit wrap-around arithmetic, are exact whenever the
-// true separation is below 2^31 / qscale (qscale is chosen so that every list
-// pair qualifies), whatever periodic image the raw coordinates sit in.
-__device__ __forceinline__ int to_fixed(double x, double qscale) {
-    return (int)(unsigned)(unsigned long long)__double2ll_rn(x * qscale);
-}
-
-__device__ __forceinline__ int wrap_sub(int a, int b) { return (int)((unsigned)a - (unsigned)b); }
 
 // ---------------------------------------------------------------------------
 // set-up / tear-down kernels
@@ -299,13 +191,6 @@ __global__ void k_cell_fill(Bufs b, GeoC g, int force) {
     if (i >= b.n) return;
     const int slot = atomicAdd(&b.cell_count[b.cell_of[i]], 1);
     b.cell_atoms[slot] = i;
-}
-
-// Upper half-space test on the minimum-image vector d = x_j - x_i: exactly
-// one of (i, j) and (j, i) passes because IEEE subtraction, rounding to the
-// nearest integer and the squares are all symmetric under d -> -d.
-__device__ __forceinline__ bool upper_half(float dx, float dy, float dz) {
-    return dz > 0.f || (dz == 0.f && (dy > 0.f || (dy == 0.f && dx > 0.f)));
 }
 
 // Candidate test in FP32 (the FP64 unit is ~58x slower on this part): the
@@ -586,30 +471,6 @@ __device__ __forceinline__ long long pair_sep_q(const Bufs& b, const int3* qt, i
     return (long long)dx * dx + (long long)dy * dy + (long long)dz * dz;
 }
 
-// RGL pair terms in FP32 from the exact fixed-point r^2.
-__device__ __forceinline__ void rgl_pair32(const PotC& P, long long r2q, const float* et,
-                                           float& rinv, float& phi, float& dphi, float& g,
-                                           float& dg) {
-    const float r2 = __ll2float_rn(r2q) * P.qinv2;
-    const float u = __ll2float_rn(r2q - P.r0sq_q) * P.qinv2;   // r^2 - r0^2
-    rinv = rsqrtf(r2);
-    const float r = r2 * rinv;
-    const float s = u / (P.r0_f * (r + P.r0_f));                // r/r0 - 1
-    const float ep = P.A_f * exp32_tang(-P.p_f * s, P.ex32, et);
-    const float eq = P.xi2_f * exp32_tang(-P.q2_f * s, P.ex32, et);
-    float S = 1.f, dS = 0.f;
-    if (r > P.rs_f) {
-        const float t = (r - P.rs_f) * P.winv_f;
-        const float t2 = t * t, t3 = t2 * t;
-        S = 1.f - 10.f * t3 + 15.f * t3 * t - 6.f * t3 * t2;
-        dS = (-30.f * t2 + 60.f * t3 - 30.f * t3 * t) * P.winv_f;
-    }
-    phi = ep * S;
-    g = eq * S;
-    dphi = ep * (-P.p_r0_f * S + dS);
-    dg = eq * (-P.q2_r0_f * S + dS);
-}
-
 // Pass 1 (FP32-pair): rho_i, F'(rho_i) = -1/(2 sqrt(rho_i)) and the atom's
 // energy sum_j phi - sqrt(rho_i); the full list makes rho_i complete in one
 // thread, so the embedding step is fused here.
@@ -718,12 +579,9 @@ __device__ double ctl_max(const double* a, int cnt, double* sh) {
     return block_max(s, sh);
 }
 
-// Scalar FIRE 2.0 control (Algorithm 2), one block.  After the force
-// evaluation of iteration `iter` it tests convergence (after the evaluation,
-// Alg. 2), then prepares iteration iter+1: the P > 0 / P <= 0 branch, the
-// counters, dt growth capped at dt_max, alpha decay, the N_P<=0 cap
-// (MAXVDOTF), the initial delay, the dt_min guard and the half step back.
-// It writes the coefficients k_update applies and sets the WHILE condition.
+// Scalar FIRE 2.0 control (Algorithm 2, fire_control_step), one block: the
+// fixed-order final reductions, the error checks, then the convergence test
+// and the preparation of the next iteration; sets the WHILE condition.
 __global__ void k_control(Bufs b, int mode, cudaGraphConditionalHandle h, int has_handle) {
     __shared__ double sh[32];
     // chunked execution runs loop bodies past the stop; they must not count
@@ -750,64 +608,20 @@ __global__ void k_control(Bufs b, int mode, cudaGraphConditionalHandle h, int ha
         if ((!isfinite(E) || !isfinite(F2)) && s.status == ST_OK) s.status = ST_NONFINITE;
         return;
     }
-    s.evals += 1;
     bool stop = false;
     if (s.status != ST_OK) {
+        s.fs.evals += 1;
         stop = true;
     } else if (!isfinite(E) || !isfinite(F2) || !isfinite(V2)) {
+        s.fs.evals += 1;
         s.status = ST_NONFINITE;
         stop = true;
     } else if (s.budget_ns && globaltimer_ns() - s.t_start > s.budget_ns) {
+        s.fs.evals += 1;
         s.status = ST_TIMEOUT;
         stop = true;
     } else {
-        const double fn = s.norm == 1 ? sqrt(F2) : (s.norm == 2 ? fin : sqrt(fa2));
-        if (fn < s.ftol) {
-            s.stop = STOP_FTOL;
-            stop = true;
-        } else if (s.iter >= s.maxiter) {
-            s.stop = STOP_MAXITER;
-            stop = true;
-        } else {
-            const long long i = ++s.iter;
-            if (P > 0.0) {
-                s.npos += 1;
-                s.nneg = 0;
-                if (s.npos > s.delaystep) {
-                    s.dt = fmin(s.dt * s.dtgrow, s.dtmax);
-                    s.alpha *= s.alphashrink;
-                }
-                s.zero_v = 0;
-                s.halfstep = 0.0;
-                // |v'|^2 of the kicked velocity v' = v + dt F / m
-                const double dtm = s.dt / s.mass;
-                const double vk2 = fmax(V2 + 2.0 * dtm * P + dtm * dtm * F2, 0.0);
-                const double fn2 = sqrt(F2);
-                s.mix = fn2 > 0.0;
-                s.mix_a = s.alpha;
-                s.mix_fv = fn2 > 0.0 ? sqrt(vk2) / fn2 : 0.0;
-            } else {
-                s.npos = 0;
-                s.nneg += 1;
-                if (s.nneg > s.vdfmax) {
-                    s.stop = STOP_MAXVDOTF;
-                    s.iter = i - 1;
-                    stop = true;
-                } else {
-                    if (!(s.initialdelay && i < s.delaystep)) {
-                        if (s.dt * s.dtshrink >= s.dtmin) s.dt *= s.dtshrink;
-                        s.alpha = s.alpha0;
-                    }
-                    s.zero_v = 1;
-                    s.halfstep = s.halfstepback ? 0.5 * s.dt : 0.0;
-                    s.mix = 0;
-                    s.mix_a = 0.0;
-                    s.mix_fv = 0.0;
-                }
-            }
-            s.dt_cur = s.dt;
-            s.dtm = s.dt / s.mass;
-        }
+        stop = fire_control_step(s.prm, s.fs, P, F2, V2, fa2, fin);
     }
     s.done = stop ? 1 : 0;
     if (has_handle) cudaGraphSetConditional(h, stop ? 0u : 1u);
@@ -819,32 +633,13 @@ __global__ void k_control(Bufs b, int mode, cudaGraphConditionalHandle h, int ha
 // for the next force evaluation and tracks max |x - x_ref|^2.
 __global__ void k_update(Bufs b) {
     __shared__ double red[32];
-    const DevState& s = *b.st;
-    if (s.done) return;
-    const int zero_v = s.zero_v, mix = s.mix;
-    const double hs = s.halfstep, dt = s.dt_cur, dtm = s.dtm;
-    const double a = s.mix_a, fv = s.mix_fv;
+    if (b.st->done) return;
+    const FireScal s = b.st->fs;
     double dmax = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < b.n; i += gridDim.x * blockDim.x) {
         dvec4 x = b.x[i], v = b.v[i];
         const dvec4 f = b.f[i];
-        if (zero_v) {
-            x.x -= hs * v.x;
-            x.y -= hs * v.y;
-            x.z -= hs * v.z;
-            v = make_dvec4(0.0, 0.0, 0.0, 0.0);
-        }
-        v.x += dtm * f.x;
-        v.y += dtm * f.y;
-        v.z += dtm * f.z;
-        if (mix) {
-            v.x = (1.0 - a) * v.x + a * fv * f.x;
-            v.y = (1.0 - a) * v.y + a * fv * f.y;
-            v.z = (1.0 - a) * v.z + a * fv * f.z;
-        }
-        x.x += dt * v.x;
-        x.y += dt * v.y;
-        x.z += dt * v.z;
+        fire_update_atom(s, x, v, f);
         b.x[i] = x;
         b.xf[i] = make_float4((float)x.x, (float)x.y, (float)x.z, 0.f);
         if (b.xq)

@@ -74,3 +74,18 @@ def test_fp32pair_rejected_for_lj(lib):
     with pytest.raises(fg.FireError) as e:
         fg.fire_init(sys, pot, fg.fire_default_params(0.005))
     assert e.value.status == fg.FIRE_ERR_ARG and "FP32-pair" in str(e.value)
+
+
+def test_batch_init_rejects_bad_offsets(lib):
+    pot = fg.Potential(fg.FIRE_POT_RGL, A=0.0855, xi=1.224, p=10.96, q=2.278, r0=2.556,
+                       rs=4.5, rc=5.0).c()
+    sys = fg.fire_system_t(0, 1.0, (ctypes.c_int32 * 3)(1, 1, 1), 0)
+    par = fg.fire_default_params(0.001)
+    for off in ([1, 5], [0, 5, 5], [0]):
+        with pytest.raises(fg.FireError) as e:
+            fg.fire_batch_init(off, sys, pot, par)
+        assert e.value.status == fg.FIRE_ERR_ARG
+    lj = fg.Potential(fg.FIRE_POT_LJ).c()
+    with pytest.raises(fg.FireError) as e:
+        fg.fire_batch_init([0, 4], sys, lj, par)
+    assert "RGL" in str(e.value)
