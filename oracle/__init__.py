@@ -9,7 +9,10 @@ this package.  It shares no code with the CUDA library and never imports it.
 Parity status: ``energy_forces`` and ``fire2`` are pinned by the tests in
 ``tests/test_oracle_pins.py`` (finite differences, sum F = 0, zero force on a
 perfect lattice, closed-form cohesive energies, hand-traced FIRE iterations,
-the LJ dimer bond length).
+the LJ dimer bond length); ``rgl_param_derivs``, ``rgl_hvp``, ``rgl_cg`` and
+``implicit_grad`` by ``tests/test_oracle_derivs.py`` (central differences in
+theta and x, Hessian symmetry and translation modes, finite differences of
+full relaxations).
 """
 from __future__ import annotations
 
@@ -96,6 +99,15 @@ def _load():
         lib.ora_fire2.argtypes = [C.POINTER(_Sys), C.POINTER(_Pot), C.POINTER(_Params), C.c_void_p,
                                   C.c_double, C.c_int64, C.c_int, C.POINTER(_Result),
                                   C.c_void_p, C.c_int64]
+        lib.ora_rgl_param_derivs.restype = C.c_int
+        lib.ora_rgl_param_derivs.argtypes = [C.POINTER(_Sys), C.POINTER(_Pot), C.c_void_p,
+                                             C.c_void_p, C.c_void_p, C.c_int]
+        lib.ora_rgl_hvp.restype = C.c_int
+        lib.ora_rgl_hvp.argtypes = [C.POINTER(_Sys), C.POINTER(_Pot), C.c_void_p, C.c_void_p,
+                                    C.c_void_p, C.c_int]
+        lib.ora_rgl_cg.restype = C.c_int64
+        lib.ora_rgl_cg.argtypes = [C.POINTER(_Sys), C.POINTER(_Pot), C.c_void_p, C.c_void_p,
+                                   C.c_double, C.c_int64, C.c_void_p, C.c_int]
         lib.ora_set_threads.argtypes = [C.c_int]
         lib.ora_max_threads.restype = C.c_int
         _lib = lib
@@ -224,6 +236,53 @@ def densities(x, box, pot: Potential, periodic=(1, 1, 1)):
     _check(_load().ora_densities(C.byref(s), C.byref(p), x.ctypes.data, rho.ctypes.data),
            "densities")
     return rho
+
+
+def rgl_param_derivs(x, box, pot: Potential, periodic=(1, 1, 1), mode: int = FORCE_BRUTE):
+    """dE/dtheta (4,) and dF/dtheta (4, N, 3) for theta = (A, xi, p, q)."""
+    x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 3)
+    dE = np.zeros(4)
+    dF = np.zeros((4, len(x), 3))
+    keep: list = []
+    s, p = _sys(len(x), box, periodic, 1.0), _pot(pot, keep)
+    _check(_load().ora_rgl_param_derivs(C.byref(s), C.byref(p), x.ctypes.data, dE.ctypes.data,
+                                        dF.ctypes.data, int(mode)), "rgl_param_derivs")
+    return dE, dF
+
+
+def rgl_hvp(x, box, pot: Potential, u, periodic=(1, 1, 1), mode: int = FORCE_BRUTE):
+    """Hessian-vector product (d^2 E/dx^2) u, N x 3."""
+    x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 3)
+    u = np.ascontiguousarray(u, dtype=np.float64).reshape(-1, 3)
+    hu = np.zeros_like(x)
+    keep: list = []
+    s, p = _sys(len(x), box, periodic, 1.0), _pot(pot, keep)
+    _check(_load().ora_rgl_hvp(C.byref(s), C.byref(p), x.ctypes.data, u.ctypes.data,
+                               hu.ctypes.data, int(mode)), "rgl_hvp")
+    return hu
+
+
+def rgl_cg(x, box, pot: Potential, b, tol=1e-12, maxit=10000, periodic=(1, 1, 1),
+           mode: int = FORCE_BRUTE):
+    """Solves H lambda = b (translations projected out); returns (lambda, iterations)."""
+    x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 3)
+    b = np.ascontiguousarray(b, dtype=np.float64).reshape(-1, 3)
+    lam = np.zeros_like(x)
+    keep: list = []
+    s, p = _sys(len(x), box, periodic, 1.0), _pot(pot, keep)
+    it = _load().ora_rgl_cg(C.byref(s), C.byref(p), x.ctypes.data, b.ctypes.data, float(tol),
+                            int(maxit), lam.ctypes.data, int(mode))
+    if it < 0:
+        raise RuntimeError("oracle CG failed")
+    return lam, int(it)
+
+
+def implicit_grad(x_star, box, pot: Potential, g, tol=1e-12, maxit=10000, periodic=(1, 1, 1),
+                  mode: int = FORCE_BRUTE):
+    """dL/dtheta at a minimum x*: lambda^T dF/dtheta with H lambda = dL/dx."""
+    lam, it = rgl_cg(x_star, box, pot, g, tol, maxit, periodic, mode)
+    _, dF = rgl_param_derivs(x_star, box, pot, periodic, mode)
+    return np.einsum("kna,na->k", dF, lam), it
 
 
 def fire2(x, box, pot: Potential, params: Params, mass: float, ftol: float, maxiter: int,

@@ -44,6 +44,9 @@
  *   ora_fire2           pinned (hand-traced iterations of Alg. 2 + Alg. 4 on
  *                       quadratic wells, MAXVDOTF and dt_min traces, LJ dimer
  *                       bond length).
+ *   ora_rgl_param_derivs  pinned (central differences of E and F in theta).
+ *   ora_rgl_hvp         pinned (central differences of F along u, symmetry
+ *                       u.Hv = v.Hu, zero translation mode).
  */
 #include <math.h>
 #include <stdint.h>
@@ -92,6 +95,8 @@ typedef struct {
     int64_t i, npos, nneg;
     double P, dt, alpha, energy, fnorm;
 } ora_trace;
+
+static double dot3n(const double *a, const double *b, int64_t n3);
 
 /* ------------------------------------------------------------------------ */
 /* Geometry                                                                  */
@@ -412,6 +417,311 @@ int ora_densities(const ora_sys *sys, const ora_pot *pot, const double *x, doubl
         rho[i] = rh;
     }
     return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Derivatives for the differentiable form (RGL only).                       */
+/*                                                                          */
+/* theta = (A, xi, p, q).  With d = x_j - x_i, r = |d|, s = r/r0 - 1,       */
+/* e_p = exp(-p s), e_q = exp(-2 q s) and the taper S(r):                    */
+/*   phi  = A e_p S,  phi'  = A e_p (-(p/r0) S + S'),                        */
+/*   phi''= A e_p ((p/r0)^2 S - 2 (p/r0) S' + S''),                          */
+/*   g    = xi^2 e_q S, g' and g'' likewise with 2q in place of p,           */
+/*   rho_i = sum_j g,  F'_i = -1/(2 sqrt(rho_i)),  F''_i = 1/(4 rho_i^1.5),  */
+/*   F_i = sum_j [2 phi' + (F'_i + F'_j) g'] d / r.                          */
+
+static void taper2(const ora_pot *pot, double r, double *S, double *dS, double *d2S) {
+    if (r <= pot->rs) { *S = 1.0; *dS = 0.0; *d2S = 0.0; return; }
+    if (r >= pot->rc) { *S = 0.0; *dS = 0.0; *d2S = 0.0; return; }
+    double w = pot->rc - pot->rs;
+    double t = (r - pot->rs) / w;
+    *S = 1.0 - 10.0 * t * t * t + 15.0 * t * t * t * t - 6.0 * t * t * t * t * t;
+    *dS = (-30.0 * t * t + 60.0 * t * t * t - 30.0 * t * t * t * t) / w;
+    *d2S = (-60.0 * t + 180.0 * t * t - 120.0 * t * t * t) / (w * w);
+}
+
+typedef struct {
+    double r, s, ep, eq, S, dS, d2S;
+    double phi, dphi, d2phi, g, dg, d2g;
+} ora_pair2;
+
+static void rgl_pair2(const ora_pot *pot, double r, ora_pair2 *q) {
+    q->r = r;
+    q->s = r / pot->r0 - 1.0;
+    taper2(pot, r, &q->S, &q->dS, &q->d2S);
+    double a = pot->p / pot->r0, b = 2.0 * pot->q / pot->r0;
+    q->ep = exp(-pot->p * q->s);
+    q->eq = exp(-2.0 * pot->q * q->s);
+    q->phi = pot->A * q->ep * q->S;
+    q->dphi = pot->A * q->ep * (-a * q->S + q->dS);
+    q->d2phi = pot->A * q->ep * (a * a * q->S - 2.0 * a * q->dS + q->d2S);
+    double xi2 = pot->xi * pot->xi;
+    q->g = xi2 * q->eq * q->S;
+    q->dg = xi2 * q->eq * (-b * q->S + q->dS);
+    q->d2g = xi2 * q->eq * (b * b * q->S - 2.0 * b * q->dS + q->d2S);
+}
+
+/* Neighbour lists within rc in CSR form (ascending j per atom), from the
+ * same candidate enumeration as the force routines. */
+typedef struct {
+    int64_t *start, *nbr;
+} ora_csr;
+
+static void csr_build(const ora_sys *sys, const ora_pot *pot, const double *x, int mode,
+                      ora_csr *L) {
+    const int64_t n = sys->n;
+    const double rc2 = pot->rc * pot->rc;
+    ora_grid g;
+    grid_build(&g, sys, x, pot->rc, mode);
+    const int64_t cap = grid_max_candidates(&g) + 1;
+    int64_t *cnt = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+    int64_t **tmp = (int64_t **)calloc((size_t)(n > 0 ? n : 1), sizeof(int64_t *));
+#pragma omp parallel
+    {
+        int64_t *cand = (int64_t *)malloc((size_t)cap * sizeof(int64_t));
+#pragma omp for schedule(dynamic, 64)
+        for (int64_t i = 0; i < n; ++i) {
+            int64_t m = grid_candidates(&g, sys, x, i, cand), k = 0;
+            tmp[i] = (int64_t *)malloc((size_t)(m > 0 ? m : 1) * sizeof(int64_t));
+            for (int64_t c = 0; c < m; ++c) {
+                int64_t j = cand[c];
+                double d[3];
+                for (int a = 0; a < 3; ++a)
+                    d[a] = min_image(x[3 * j + a] - x[3 * i + a], sys->box[a], sys->periodic[a]);
+                if (d[0] * d[0] + d[1] * d[1] + d[2] * d[2] < rc2) tmp[i][k++] = j;
+            }
+            cnt[i + 1] = k;
+        }
+        free(cand);
+    }
+    for (int64_t i = 0; i < n; ++i) cnt[i + 1] += cnt[i];
+    L->start = cnt;
+    L->nbr = (int64_t *)malloc((size_t)(cnt[n] > 0 ? cnt[n] : 1) * sizeof(int64_t));
+    for (int64_t i = 0; i < n; ++i) {
+        memcpy(L->nbr + cnt[i], tmp[i], (size_t)(cnt[i + 1] - cnt[i]) * sizeof(int64_t));
+        free(tmp[i]);
+    }
+    free(tmp);
+    grid_free(&g);
+}
+
+static void csr_free(ora_csr *L) {
+    free(L->start);
+    free(L->nbr);
+}
+
+/* Minimum-image d = x_j - x_i, r and the pair functions of pair (i, j). */
+static void pair_geom(const ora_sys *sys, const ora_pot *pot, const double *x, int64_t i,
+                      int64_t j, double d[3], ora_pair2 *q) {
+    for (int a = 0; a < 3; ++a)
+        d[a] = min_image(x[3 * j + a] - x[3 * i + a], sys->box[a], sys->periodic[a]);
+    rgl_pair2(pot, sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]), q);
+}
+
+/* Per-atom rho_i, F'_i, F''_i and drho_i/dq. */
+static void rgl_atom_terms(const ora_sys *sys, const ora_pot *pot, const double *x,
+                           const ora_csr *L, double *rho, double *F1, double *F2,
+                           double *drho_dq) {
+    const int64_t n = sys->n;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < n; ++i) {
+        double rh = 0.0, dq = 0.0, d[3];
+        for (int64_t k = L->start[i]; k < L->start[i + 1]; ++k) {
+            ora_pair2 q;
+            pair_geom(sys, pot, x, i, L->nbr[k], d, &q);
+            rh += q.g;
+            dq += -2.0 * q.s * q.g;
+        }
+        rho[i] = rh;
+        F1[i] = rh > 0.0 ? -0.5 / sqrt(rh) : 0.0;
+        F2[i] = rh > 0.0 ? 0.25 / (rh * sqrt(rh)) : 0.0;
+        if (drho_dq) drho_dq[i] = dq;
+    }
+}
+
+/* dE/dtheta (4 values) and, if dF != NULL, dF/dtheta laid out as
+ * dF[k * 3N + 3 i + a] for theta_k = (A, xi, p, q). */
+int ora_rgl_param_derivs(const ora_sys *sys, const ora_pot *pot, const double *x, double *dE,
+                         double *dF, int mode) {
+    int rc_ok = check_box(sys, pot);
+    if (rc_ok) return rc_ok;
+    if (pot->kind != POT_RGL) return -1;
+    const int64_t n = sys->n, n1 = n > 0 ? n : 1;
+    ora_csr L;
+    csr_build(sys, pot, x, mode, &L);
+    double *rho = (double *)calloc((size_t)n1, sizeof(double));
+    double *F1 = (double *)calloc((size_t)n1, sizeof(double));
+    double *F2 = (double *)calloc((size_t)n1, sizeof(double));
+    double *dq = (double *)calloc((size_t)n1, sizeof(double));
+    double *eAi = (double *)calloc((size_t)n1, sizeof(double));
+    double *ePi = (double *)calloc((size_t)n1, sizeof(double));
+    rgl_atom_terms(sys, pot, x, &L, rho, F1, F2, dq);
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < n; ++i) {
+        double fA[3] = {0, 0, 0}, fX[3] = {0, 0, 0}, fP[3] = {0, 0, 0}, fQ[3] = {0, 0, 0};
+        double sA = 0.0, sP = 0.0, d[3];
+        for (int64_t k = L.start[i]; k < L.start[i + 1]; ++k) {
+            const int64_t j = L.nbr[k];
+            ora_pair2 q;
+            pair_geom(sys, pot, x, i, j, d, &q);
+            sA += q.ep * q.S;
+            sP += -q.s * q.phi;
+            double c = F1[i] + F1[j];
+            double dphi_dp = -q.s * q.dphi - pot->A * q.ep * q.S / pot->r0;
+            double dg_dq = -2.0 * q.s * q.dg - 2.0 * pot->xi * pot->xi * q.eq * q.S / pot->r0;
+            double dc_dq = F2[i] * dq[i] + F2[j] * dq[j];
+            double wA = 2.0 * q.dphi / pot->A / q.r;
+            double wX = c * q.dg / pot->xi / q.r;
+            double wP = 2.0 * dphi_dp / q.r;
+            double wQ = (dc_dq * q.dg + c * dg_dq) / q.r;
+            for (int a = 0; a < 3; ++a) {
+                fA[a] += wA * d[a];
+                fX[a] += wX * d[a];
+                fP[a] += wP * d[a];
+                fQ[a] += wQ * d[a];
+            }
+        }
+        eAi[i] = sA;
+        ePi[i] = sP;
+        if (dF) {
+            for (int a = 0; a < 3; ++a) {
+                dF[0 * 3 * n + 3 * i + a] = fA[a];
+                dF[1 * 3 * n + 3 * i + a] = fX[a];
+                dF[2 * 3 * n + 3 * i + a] = fP[a];
+                dF[3 * 3 * n + 3 * i + a] = fQ[a];
+            }
+        }
+    }
+    /* dE/dA = sum_i sum_j e_p S; dE/dxi = sum_i F'_i 2 rho_i / xi;
+     * dE/dp = sum_i sum_j (-s) phi; dE/dq = sum_i F'_i drho_i/dq */
+    double eA = 0.0, eXi = 0.0, eP = 0.0, eQ = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        eA += eAi[i];
+        eP += ePi[i];
+        eXi += F1[i] * 2.0 * rho[i] / pot->xi;
+        eQ += F1[i] * dq[i];
+    }
+    dE[0] = eA;
+    dE[1] = eXi;
+    dE[2] = eP;
+    dE[3] = eQ;
+    free(rho); free(F1); free(F2); free(dq); free(eAi); free(ePi);
+    csr_free(&L);
+    return 0;
+}
+
+/* Hu = -(d/de) F(x + e u) at e = 0, the directional derivative of the
+ * two-pass force written out (L: lists at x, F1/F2: F'(rho), F''(rho)). */
+static void hvp_apply(const ora_sys *sys, const ora_pot *pot, const double *x, const ora_csr *L,
+                      const double *F1, const double *F2, double *drho, const double *u,
+                      double *Hu) {
+    const int64_t n = sys->n;
+    /* d rho_i = sum_j g'(r_ij) dr_ij,  dr_ij = d . (u_j - u_i) / r */
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < n; ++i) {
+        double acc = 0.0, d[3];
+        for (int64_t k = L->start[i]; k < L->start[i + 1]; ++k) {
+            const int64_t j = L->nbr[k];
+            ora_pair2 q;
+            pair_geom(sys, pot, x, i, j, d, &q);
+            double dr = 0.0;
+            for (int a = 0; a < 3; ++a) dr += d[a] * (u[3 * j + a] - u[3 * i + a]);
+            acc += q.dg * dr / q.r;
+        }
+        drho[i] = acc;
+    }
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < n; ++i) {
+        double dF[3] = {0, 0, 0}, d[3], du[3];
+        for (int64_t k = L->start[i]; k < L->start[i + 1]; ++k) {
+            const int64_t j = L->nbr[k];
+            ora_pair2 q;
+            pair_geom(sys, pot, x, i, j, d, &q);
+            for (int a = 0; a < 3; ++a) du[a] = u[3 * j + a] - u[3 * i + a];
+            double c = F1[i] + F1[j];
+            double fs = (2.0 * q.dphi + c * q.dg) / q.r;
+            double dr = (d[0] * du[0] + d[1] * du[1] + d[2] * du[2]) / q.r;
+            double dc = F2[i] * drho[i] + F2[j] * drho[j];
+            double dfs = ((2.0 * q.d2phi + c * q.d2g) / q.r - fs / q.r) * dr + dc * q.dg / q.r;
+            for (int a = 0; a < 3; ++a) dF[a] += dfs * d[a] + fs * du[a];
+        }
+        for (int a = 0; a < 3; ++a) Hu[3 * i + a] = -dF[a];
+    }
+}
+
+int ora_rgl_hvp(const ora_sys *sys, const ora_pot *pot, const double *x, const double *u,
+                double *Hu, int mode) {
+    int rc_ok = check_box(sys, pot);
+    if (rc_ok) return rc_ok;
+    if (pot->kind != POT_RGL) return -1;
+    const int64_t n1 = sys->n > 0 ? sys->n : 1;
+    ora_csr L;
+    csr_build(sys, pot, x, mode, &L);
+    double *rho = (double *)calloc((size_t)n1, sizeof(double));
+    double *F1 = (double *)calloc((size_t)n1, sizeof(double));
+    double *F2 = (double *)calloc((size_t)n1, sizeof(double));
+    double *drho = (double *)calloc((size_t)n1, sizeof(double));
+    rgl_atom_terms(sys, pot, x, &L, rho, F1, F2, NULL);
+    hvp_apply(sys, pot, x, &L, F1, F2, drho, u, Hu);
+    free(rho); free(F1); free(F2); free(drho);
+    csr_free(&L);
+    return 0;
+}
+
+/* Removes the mean of each Cartesian component (the translation modes). */
+static void project_translations(double *v, int64_t n) {
+    for (int a = 0; a < 3; ++a) {
+        double m = 0.0;
+        for (int64_t i = 0; i < n; ++i) m += v[3 * i + a];
+        m /= (double)(n > 0 ? n : 1);
+        for (int64_t i = 0; i < n; ++i) v[3 * i + a] -= m;
+    }
+}
+
+/* Conjugate gradients for H lambda = b in the subspace orthogonal to the
+ * three translations (H is singular along them under periodic boundaries).
+ * Stops when |r| <= tol |b|.  Returns the iteration count (or -1). */
+int64_t ora_rgl_cg(const ora_sys *sys, const ora_pot *pot, const double *x, const double *b_in,
+                   double tol, int64_t maxit, double *lambda, int mode) {
+    int rc_ok = check_box(sys, pot);
+    if (rc_ok || pot->kind != POT_RGL) return -1;
+    const int64_t n = sys->n, m = 3 * n, n1 = n > 0 ? n : 1;
+    ora_csr L;
+    csr_build(sys, pot, x, mode, &L);
+    double *rho = (double *)calloc((size_t)n1, sizeof(double));
+    double *F1 = (double *)calloc((size_t)n1, sizeof(double));
+    double *F2 = (double *)calloc((size_t)n1, sizeof(double));
+    double *drho = (double *)calloc((size_t)n1, sizeof(double));
+    rgl_atom_terms(sys, pot, x, &L, rho, F1, F2, NULL);
+    double *b = (double *)malloc((size_t)3 * n1 * sizeof(double));
+    double *r = (double *)malloc((size_t)3 * n1 * sizeof(double));
+    double *p = (double *)malloc((size_t)3 * n1 * sizeof(double));
+    double *Ap = (double *)malloc((size_t)3 * n1 * sizeof(double));
+    memcpy(b, b_in, (size_t)m * sizeof(double));
+    project_translations(b, n);
+    for (int64_t k = 0; k < m; ++k) { lambda[k] = 0.0; r[k] = b[k]; p[k] = b[k]; }
+    double rr = dot3n(r, r, m);
+    const double stop2 = tol * tol * rr;
+    int64_t it = 0;
+    while (it < maxit && rr > stop2 && rr > 0.0) {
+        hvp_apply(sys, pot, x, &L, F1, F2, drho, p, Ap);
+        project_translations(Ap, n);
+        double pAp = dot3n(p, Ap, m);
+        if (!(pAp > 0.0)) break;
+        double alpha = rr / pAp;
+        for (int64_t k = 0; k < m; ++k) {
+            lambda[k] += alpha * p[k];
+            r[k] -= alpha * Ap[k];
+        }
+        double rr_new = dot3n(r, r, m);
+        double beta = rr_new / rr;
+        for (int64_t k = 0; k < m; ++k) p[k] = r[k] + beta * p[k];
+        rr = rr_new;
+        ++it;
+    }
+    free(rho); free(F1); free(F2); free(drho); free(b); free(r); free(p); free(Ap);
+    csr_free(&L);
+    return it;
 }
 
 /* ------------------------------------------------------------------------ */
