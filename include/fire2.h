@@ -308,6 +308,47 @@ fire_status fire_batch_set_tuning(fire_handle_t* h, const fire_batch_tuning_t* t
 fire_status fire_batch_autotune(fire_handle_t* h, const double* pos, const double* boxes,
                                 int32_t iters, fire_batch_tuning_t* chosen);
 
+/* ---- Differentiable form (RGL, FP64) ------------------------------------------
+ * theta = (A, xi, p, q) are the RGL parameters of fire_potential_t.  The
+ * paper treats the force field as fixed; these entry points add gradients
+ * with respect to it: dE/dtheta (the hand-written backward of E(x, theta)),
+ * the Hessian-vector product H u = (d^2 E / dx^2) u, and the implicit
+ * gradient of a loss L(x*) of the relaxed configuration x*(theta): at a
+ * minimum the forces vanish, so dL/dtheta = lambda . dF/dtheta with
+ * H lambda = dL/dx, solved by conjugate gradients in FP64 with the three
+ * translation modes projected out (H is singular along them).  All take
+ * device arrays of N x 3 doubles (row-major) and run on `stream` (a
+ * cudaStream_t), synchronising it before returning; they use a full
+ * neighbour list built at d_pos on each call.  Handle: a single-system RGL
+ * handle (either precision; the derivatives are always FP64). */
+
+/* Replaces the RGL parameters A, xi, p, q of h (later relaxations and
+ * evaluations use them).  Errors: FIRE_ERR_ARG (not RGL, xi <= 0, A < 0,
+ * exponents out of range). */
+fire_status fire_set_rgl_params(fire_handle_t* h, const double theta[4]);
+
+/* E(x, theta) (*energy, host, may be NULL), dE/dtheta (host, 4 doubles, may
+ * be NULL) and F = -dE/dx (d_forces, device, may be NULL) at d_pos.
+ * Errors: FIRE_ERR_ARG, FIRE_ERR_NONFINITE, FIRE_ERR_NBR_OVERFLOW, FIRE_ERR_CUDA. */
+fire_status fire_rgl_energy_grad_dev(fire_handle_t* h, const double* d_pos, const double box[3],
+                                     const double theta[4], double* d_forces, double* energy,
+                                     double dE_dtheta[4], void* stream);
+
+/* d_hu = H(d_pos, theta) d_u (device arrays, N x 3).  Errors: as above. */
+fire_status fire_rgl_hvp_dev(fire_handle_t* h, const double* d_pos, const double box[3],
+                             const double theta[4], const double* d_u, double* d_hu,
+                             void* stream);
+
+/* Implicit gradient at a relaxed d_pos: d_g = dL/dx (device, N x 3),
+ * CG until |r| <= tol |g| or maxit iterations; dL_dtheta (host, 4) receives
+ * lambda . dF/dtheta, d_lambda (device, N x 3, may be NULL) the solution,
+ * *cg_iters (may be NULL) the iteration count.
+ * Errors: FIRE_ERR_ARG (tol <= 0, maxit < 1, NULL), FIRE_ERR_NBR_OVERFLOW, FIRE_ERR_CUDA. */
+fire_status fire_rgl_implicit_grad_dev(fire_handle_t* h, const double* d_pos, const double box[3],
+                                       const double theta[4], const double* d_g, double tol,
+                                       int64_t maxit, double dL_dtheta[4], double* d_lambda,
+                                       int64_t* cg_iters, void* stream);
+
 /* Message of the last failed call on h (or of the last failed fire_init when
  * h is NULL).  Never NULL. */
 const char* fire_last_error(const fire_handle_t* h);

@@ -38,7 +38,9 @@ EXPORTED = ("fire_abi_version", "fire_default_params", "fire_init", "fire_minimi
             "fire_set_time_budget", "fire_profile_stages", "fire_diag_fma_peak",
             "fire_energy_forces_noalloc", "fire_set_exec_mode", "fire_diag_exp",
             "fire_batch_init", "fire_minimize_batch", "fire_minimize_batch_dev",
-            "fire_batch_set_tuning", "fire_batch_autotune", "fire_last_error", "fire_destroy")
+            "fire_batch_set_tuning", "fire_batch_autotune", "fire_set_rgl_params",
+            "fire_rgl_energy_grad_dev", "fire_rgl_hvp_dev", "fire_rgl_implicit_grad_dev",
+            "fire_last_error", "fire_destroy")
 FIRE_EXEC_GRAPH_WHILE, FIRE_EXEC_CHUNKED = 0, 1
 STAGES = ("build", "density", "embed", "force", "reduce", "control", "update")
 
@@ -115,6 +117,13 @@ def load_library(path: str | None = None):
     lib.fire_minimize_batch_dev.argtypes = [H, C.c_void_p, C.c_void_p, C.c_double, C.c_int64,
                                             C.c_void_p, C.c_void_p, C.c_void_p]
     lib.fire_batch_set_tuning.argtypes = [H, C.POINTER(fire_batch_tuning_t)]
+    D4 = C.POINTER(C.c_double)
+    lib.fire_set_rgl_params.argtypes = [H, D4]
+    lib.fire_rgl_energy_grad_dev.argtypes = [H, C.c_void_p, D4, D4, C.c_void_p, D4, D4, C.c_void_p]
+    lib.fire_rgl_hvp_dev.argtypes = [H, C.c_void_p, D4, D4, C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.fire_rgl_implicit_grad_dev.argtypes = [H, C.c_void_p, D4, D4, C.c_void_p, C.c_double,
+                                               C.c_int64, D4, C.c_void_p,
+                                               C.POINTER(C.c_int64), C.c_void_p]
     lib.fire_batch_autotune.argtypes = [H, C.c_void_p, C.c_void_p, C.c_int32,
                                         C.POINTER(fire_batch_tuning_t)]
     lib.fire_profile_stages.argtypes = [H, C.c_void_p, C.POINTER(C.c_double), C.c_int32,
@@ -316,6 +325,49 @@ def fire_batch_autotune(handle, pos: np.ndarray, boxes, iters: int = 20):
     return {"threads_per_block": t.threads_per_block, "ctas_per_sm": t.ctas_per_sm}
 
 
+def _theta(theta):
+    return (C.c_double * 4)(*[float(v) for v in theta])
+
+
+def fire_set_rgl_params(handle, theta) -> None:
+    _check(load_library().fire_set_rgl_params(handle, _theta(theta)), handle)
+
+
+def fire_rgl_energy_grad_dev(handle, d_pos, box, theta, d_forces=None, stream=None):
+    """Returns (E, dE/dtheta as a numpy (4,)); fills d_forces if given."""
+    _check_dev(d_pos)
+    e = C.c_double(0.0)
+    de = (C.c_double * 4)()
+    st = load_library().fire_rgl_energy_grad_dev(
+        handle, d_pos.data_ptr(), _box(box), _theta(theta),
+        d_forces.data_ptr() if d_forces is not None else None, C.byref(e), de, _stream(stream))
+    _check(st, handle)
+    return float(e.value), np.array(list(de))
+
+
+def fire_rgl_hvp_dev(handle, d_pos, box, theta, d_u, d_hu, stream=None) -> None:
+    for t in (d_pos, d_u, d_hu):
+        _check_dev(t)
+    st = load_library().fire_rgl_hvp_dev(handle, d_pos.data_ptr(), _box(box), _theta(theta),
+                                         d_u.data_ptr(), d_hu.data_ptr(), _stream(stream))
+    _check(st, handle)
+
+
+def fire_rgl_implicit_grad_dev(handle, d_pos, box, theta, d_g, tol=1e-10, maxit=20000,
+                               d_lambda=None, stream=None):
+    """Returns (dL/dtheta as numpy (4,), CG iterations)."""
+    _check_dev(d_pos)
+    _check_dev(d_g)
+    out = (C.c_double * 4)()
+    it = C.c_int64(0)
+    st = load_library().fire_rgl_implicit_grad_dev(
+        handle, d_pos.data_ptr(), _box(box), _theta(theta), d_g.data_ptr(), float(tol),
+        int(maxit), out, d_lambda.data_ptr() if d_lambda is not None else None, C.byref(it),
+        _stream(stream))
+    _check(st, handle)
+    return np.array(list(out)), int(it.value)
+
+
 def _check_dev(t):
     import torch
     if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64
@@ -424,6 +476,9 @@ class FireHandle:
 
     def profile_stages(self, pos, box, reps=10):
         return fire_profile_stages(self.h, pos, box, reps)
+
+    def set_rgl_params(self, theta):
+        fire_set_rgl_params(self.h, theta)
 
     def set_exec_mode(self, mode, chunk=32):
         fire_set_exec_mode(self.h, mode, chunk)

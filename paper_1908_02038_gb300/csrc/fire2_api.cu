@@ -14,6 +14,7 @@
 
 #include "fire2.h"
 #include "fire2_device.cuh"
+#include "fire2_grad.cuh"
 
 using namespace fire2;
 
@@ -21,6 +22,20 @@ struct fire_batch_state;
 void fire2_batch_free(fire_batch_state* b);
 fire_status fire2_batch_create(fire_handle_t* h, int32_t n_sys, const int64_t* offsets,
                                fire_batch_state** out);
+
+// Buffers of the differentiable form (allocated on first use).
+struct GradState {
+    int cap = 0, nb = 0;
+    dvec4 *x = nullptr, *xref = nullptr;
+    float4* xf = nullptr;
+    uint32_t* nbr = nullptr;
+    int* nnbr = nullptr;
+    double *rho = nullptr, *F1 = nullptr, *F2 = nullptr, *drho = nullptr, *dq = nullptr;
+    double* part = nullptr;        // 9 x nb block partials
+    double* vec = nullptr;         // 4 work vectors of 3N (r, p, Ap, lambda)
+    double* h_part = nullptr;      // pinned copy of part
+    DevState* st = nullptr;        // status word of the list build
+};
 
 struct fire_handle {
     int device = 0;
@@ -46,6 +61,7 @@ struct fire_handle {
     int chunk = 32;                  // iterations per graph launch, chunked mode
     cudaGraphExec_t exec_init = nullptr, exec_chunk = nullptr, exec_final = nullptr;
     fire_batch_state* batch = nullptr;   // set for handles made by fire_batch_init
+    GradState grad;
     std::string err;
 };
 
@@ -468,6 +484,59 @@ fire_status fire_default_params(fire_params_t* out, double dt_start) {
     return FIRE_OK;
 }
 
+// Potential constants for the kernels from h->pot (and the fixed-point scale
+// of the FP32-pair form).  Returns false if the exponent range is exceeded.
+static bool fill_potc(fire_handle* h) {
+    const fire_potential_t* pot = &h->pot;
+    PotC& c = h->potc;
+    c.kind = pot->kind;
+    if (pot->kind == FIRE_POT_LJ) {
+        c.rc2 = pot->rc_lj * pot->rc_lj;
+        c.eps = pot->eps;
+        c.sigma2 = pot->sigma * pot->sigma;
+        const double sr6 = std::pow(pot->sigma / pot->rc_lj, 6.0);
+        c.lj_shift = 4.0 * pot->eps * (sr6 * sr6 - sr6);
+        return true;
+    }
+    c.rc2 = pot->rc * pot->rc;
+    c.A = pot->A;
+    c.xi2 = pot->xi * pot->xi;
+    c.xi_inv = 1.0 / pot->xi;
+    c.p = pot->p;
+    c.q2 = 2.0 * pot->q;
+    c.r0inv = 1.0 / pot->r0;
+    c.p_r0 = pot->p / pot->r0;
+    c.q2_r0 = 2.0 * pot->q / pot->r0;
+    c.rs = pot->rs;
+    c.rc = pot->rc;
+    c.winv = 1.0 / (pot->rc - pot->rs);
+    // exponent arguments -p s and -2q s with s in [-1, rc/r0 - 1]
+    const double smax = std::max(1.0, pot->rc / pot->r0 - 1.0);
+    if (!(std::fabs(pot->p) * smax < 80.0 && std::fabs(2.0 * pot->q) * smax < 80.0)) return false;
+    if (pot->precision == FIRE_PREC_FP32_PAIR) {
+        // fixed-point scale: a power of two with (rc + 3 skin + 2) * qscale < 2^31,
+        // so every list pair's separation and r^2 fit their integer types
+        const double span = pot->rc + 3.0 * pot->skin + 2.0;
+        const int k = (int)std::floor(std::log2(2147483648.0 / span));
+        h->b.qscale = std::ldexp(1.0, k);
+        c.A_f = (float)pot->A;
+        c.xi2_f = (float)(pot->xi * pot->xi);
+        c.p_f = (float)pot->p;
+        c.q2_f = (float)(2.0 * pot->q);
+        c.r0_f = (float)pot->r0;
+        c.p_r0_f = (float)(pot->p / pot->r0);
+        c.q2_r0_f = (float)(2.0 * pot->q / pot->r0);
+        c.rs_f = (float)pot->rs;
+        c.winv_f = (float)(1.0 / (pot->rc - pot->rs));
+        const double q2 = h->b.qscale * h->b.qscale;
+        c.rc2q = (long long)std::floor(pot->rc * pot->rc * q2);
+        c.r0sq_q = std::llrint(pot->r0 * pot->r0 * q2);
+        c.qinv = (float)(1.0 / h->b.qscale);
+        c.qinv2 = (float)(1.0 / q2);
+    }
+    return true;
+}
+
 static fire_status init_handle(fire_handle_t** hp, const fire_system_t* sys,
                                const fire_potential_t* pot, const fire_params_t* params,
                                bool single) {
@@ -502,60 +571,16 @@ static fire_status init_handle(fire_handle_t** hp, const fire_system_t* sys,
         delete h;
         return st;
     }
-    PotC& c = h->potc;
-    c.kind = pot->kind;
-    if (pot->kind == FIRE_POT_LJ) {
-        c.rc2 = pot->rc_lj * pot->rc_lj;
-        c.eps = pot->eps;
-        c.sigma2 = pot->sigma * pot->sigma;
-        const double sr6 = std::pow(pot->sigma / pot->rc_lj, 6.0);
-        c.lj_shift = 4.0 * pot->eps * (sr6 * sr6 - sr6);
-    } else {
-        c.rc2 = pot->rc * pot->rc;
-        c.A = pot->A;
-        c.xi2 = pot->xi * pot->xi;
-        c.p = pot->p;
-        c.q2 = 2.0 * pot->q;
-        c.r0inv = 1.0 / pot->r0;
-        c.p_r0 = pot->p / pot->r0;
-        c.q2_r0 = 2.0 * pot->q / pot->r0;
-        c.rs = pot->rs;
-        c.rc = pot->rc;
-        c.winv = 1.0 / (pot->rc - pot->rs);
-        // exponent arguments -p s and -2q s with s in [-1, rc/r0 - 1]
-        const double smax = std::max(1.0, pot->rc / pot->r0 - 1.0);
-        if (!(std::fabs(pot->p) * smax < 700.0 && std::fabs(2.0 * pot->q) * smax < 700.0)) {
-            g_init_err = "RGL exponents p, q too large for the exponential's range";
-            delete h;
-            return FIRE_ERR_ARG;
-        }
+    if (!fill_potc(h)) {
+        g_init_err = "RGL exponents p, q too large for the exponential's range";
+        delete h;
+        return FIRE_ERR_ARG;
     }
     double exp_table_host[kExpTableSize];
     h->potc.ex = make_exp_constants(exp_table_host);
     float exp32_table_host[kExp32TableSize];
     h->potc.ex32 = make_exp32_constants(exp32_table_host);
     const bool fp32pair = pot->precision == FIRE_PREC_FP32_PAIR;
-    if (fp32pair) {
-        // fixed-point scale: a power of two with (rc + 3 skin + 2) * qscale < 2^31,
-        // so every list pair's separation and r^2 fit their integer types
-        const double span = pot->rc + 3.0 * pot->skin + 2.0;
-        const int k = (int)std::floor(std::log2(2147483648.0 / span));
-        h->b.qscale = std::ldexp(1.0, k);
-        c.A_f = (float)pot->A;
-        c.xi2_f = (float)(pot->xi * pot->xi);
-        c.p_f = (float)pot->p;
-        c.q2_f = (float)(2.0 * pot->q);
-        c.r0_f = (float)pot->r0;
-        c.p_r0_f = (float)(pot->p / pot->r0);
-        c.q2_r0_f = (float)(2.0 * pot->q / pot->r0);
-        c.rs_f = (float)pot->rs;
-        c.winv_f = (float)(1.0 / (pot->rc - pot->rs));
-        const double q2 = h->b.qscale * h->b.qscale;
-        c.rc2q = (long long)std::floor(pot->rc * pot->rc * q2);
-        c.r0sq_q = std::llrint(pot->r0 * pot->r0 * q2);
-        c.qinv = (float)(1.0 / h->b.qscale);
-        c.qinv2 = (float)(1.0 / q2);
-    }
 
     auto bail = [&](fire_status s) {
         g_init_err = h->err;
@@ -672,6 +697,14 @@ void fire_destroy(fire_handle_t* h) {
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->batch) fire2_batch_free(h->batch);
+    {
+        GradState& gs = h->grad;
+        void* gp[] = {gs.x, gs.xref, gs.xf, gs.nbr, gs.nnbr, gs.rho, gs.F1, gs.F2, gs.drho,
+                      gs.dq, gs.part, gs.vec, gs.st};
+        for (void* p : gp)
+            if (p) cudaFree(p);
+        if (gs.h_part) cudaFreeHost(gs.h_part);
+    }
     if (h->h_state) cudaFreeHost(h->h_state);
     if (h->h_pos) cudaFreeHost(h->h_pos);
     if (h->stream) cudaStreamDestroy(h->stream);
@@ -848,6 +881,279 @@ fire_status fire_energy_forces(fire_handle_t* h, const double* pos, const double
         std::memcpy(forces, h->h_pos, bytes);
     }
     if (energy) *energy = h->h_state->energy;
+    return FIRE_OK;
+}
+
+// ---- differentiable form ----------------------------------------------------
+
+static void apply_theta(PotC& c, const double th[4]) {
+    c.A = th[0];
+    c.xi2 = th[1] * th[1];
+    c.xi_inv = 1.0 / th[1];
+    c.p = th[2];
+    c.q2 = 2.0 * th[3];
+    c.p_r0 = th[2] * c.r0inv;
+    c.q2_r0 = 2.0 * th[3] * c.r0inv;
+}
+
+static fire_status check_theta(fire_handle* h, const double th[4]) {
+    if (!th) return fail(h, FIRE_ERR_ARG, "theta is NULL");
+    if (!(th[0] >= 0.0 && th[1] > 0.0 && std::isfinite(th[2]) && std::isfinite(th[3])))
+        return fail(h, FIRE_ERR_ARG, "theta needs A >= 0, xi > 0, finite p and q");
+    const double smax = std::max(1.0, h->pot.rc / h->pot.r0 - 1.0);
+    if (!(std::fabs(th[2]) * smax < 80.0 && std::fabs(2.0 * th[3]) * smax < 80.0))
+        return fail(h, FIRE_ERR_ARG, "theta: p, q too large for the exponential's range");
+    return FIRE_OK;
+}
+
+// Loads positions, (re)allocates the derivative buffers, builds the full
+// list at pos and runs pass 1 (rho, F', F'', drho/dq, energy partials).
+static fire_status grad_setup(fire_handle* h, const double* d_pos, const double box[3],
+                              const double th[4], cudaStream_t s, GeoC* gout, PotC* pc,
+                              GradBufs* gb) {
+    if (h->pot.kind != FIRE_POT_RGL) return fail(h, FIRE_ERR_ARG, "derivatives need the RGL potential");
+    if (!d_pos) return fail(h, FIRE_ERR_ARG, "NULL positions");
+    fire_status st = check_theta(h, th);
+    if (st != FIRE_OK) return st;
+    GeoC g;
+    st = prepare_call(h, box, &g);
+    if (st != FIRE_OK) return st;
+    g.full = 1;
+    GradState& gs = h->grad;
+    const int n = h->n;
+    const int cap = std::min(std::max(n - 1, 1), 2 * estimate_cap(h, make_geo(h, box)) + 16);
+    if (!gs.x) {
+        gs.nb = ceil_div(n, kForceBlock);
+        CK(h, cudaMalloc(&gs.x, (size_t)n * sizeof(dvec4)));
+        CK(h, cudaMalloc(&gs.xref, (size_t)n * sizeof(dvec4)));
+        CK(h, cudaMalloc(&gs.xf, (size_t)n * sizeof(float4)));
+        CK(h, cudaMalloc(&gs.nnbr, (size_t)n * sizeof(int)));
+        for (double** p : {&gs.rho, &gs.F1, &gs.F2, &gs.drho, &gs.dq})
+            CK(h, cudaMalloc(p, (size_t)n * sizeof(double)));
+        CK(h, cudaMalloc(&gs.part, (size_t)9 * gs.nb * sizeof(double)));
+        CK(h, cudaMalloc(&gs.vec, (size_t)4 * 3 * n * sizeof(double)));
+        CK(h, cudaMallocHost(&gs.h_part, (size_t)9 * gs.nb * sizeof(double)));
+        CK(h, cudaMalloc(&gs.st, sizeof(DevState)));
+    }
+    if (cap > gs.cap) {
+        cudaFree(gs.nbr);
+        gs.nbr = nullptr;
+        CK(h, cudaMalloc(&gs.nbr, (size_t)cap * n * sizeof(uint32_t)));
+        gs.cap = cap;
+    }
+    // list build through the single-system kernels, on the derivative buffers
+    Bufs lb = h->b;
+    lb.x = gs.x;
+    lb.xf = gs.xf;
+    lb.xref = gs.xref;
+    lb.xq = nullptr;
+    lb.nbr = gs.nbr;
+    lb.nnbr = gs.nnbr;
+    lb.cap = gs.cap;
+    lb.st = gs.st;
+    CK(h, cudaMemsetAsync(gs.st, 0, sizeof(DevState), s));
+    k_g_load<<<ceil_div(n, kElemBlock), kElemBlock, 0, s>>>(n, d_pos, gs.x, gs.xf);
+    const bool brute = g.brute != 0;
+    if (!brute) {
+        k_cell_zero<<<ceil_div(lb.ncell, kElemBlock), kElemBlock, 0, s>>>(lb, g, 1);
+        k_cell_count<<<ceil_div(n, kElemBlock), kElemBlock, 0, s>>>(lb, g, 1);
+        k_cell_scan<<<1, 1024, 0, s>>>(lb, g, 1);
+        k_cell_fill<<<ceil_div(n, kElemBlock), kElemBlock, 0, s>>>(lb, g, 1);
+    }
+    k_nbr_build<<<ceil_div(n, kForceBlock), kForceBlock, 0, s>>>(lb, g, 1);
+    CK(h, cudaGetLastError());
+    int status = 0;
+    CK(h, cudaMemcpyAsync(&status, &gs.st->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(h, cudaStreamSynchronize(s));
+    if (status != ST_OK) return status_to_error(h, status);
+    *pc = h->potc;
+    apply_theta(*pc, th);
+    GradBufs b{};
+    b.n = n;
+    b.cap = gs.cap;
+    b.x = gs.x;
+    b.nbr = gs.nbr;
+    b.nnbr = gs.nnbr;
+    b.rho = gs.rho;
+    b.F1 = gs.F1;
+    b.F2 = gs.F2;
+    b.drho = gs.drho;
+    b.dq = gs.dq;
+    b.part = gs.part;
+    GeoL L{{box[0], box[1], box[2]}};
+    k_g_atom<<<gs.nb, kForceBlock, 0, s>>>(b, *pc, L, h->b.exp_table);
+    CK(h, cudaGetLastError());
+    *gout = g;
+    *gb = b;
+    return FIRE_OK;
+}
+
+// Fixed-order host sums of partial rows [k0, k0 + nk) of the derivative partials.
+static fire_status grad_sums(fire_handle* h, int k0, int nk, double* out, cudaStream_t s) {
+    GradState& gs = h->grad;
+    CK(h, cudaMemcpyAsync(gs.h_part + (size_t)k0 * gs.nb, gs.part + (size_t)k0 * gs.nb,
+                          (size_t)nk * gs.nb * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(h, cudaStreamSynchronize(s));
+    for (int k = 0; k < nk; ++k) {
+        double acc = 0.0;
+        for (int b = 0; b < gs.nb; ++b) acc += gs.h_part[(size_t)(k0 + k) * gs.nb + b];
+        out[k] = acc;
+    }
+    return FIRE_OK;
+}
+
+fire_status fire_set_rgl_params(fire_handle_t* h, const double theta[4]) {
+    if (!h) return FIRE_ERR_ARG;
+    if (h->pot.kind != FIRE_POT_RGL) return fail(h, FIRE_ERR_ARG, "not an RGL handle");
+    fire_status st = check_theta(h, theta);
+    if (st != FIRE_OK) return st;
+    h->pot.A = theta[0];
+    h->pot.xi = theta[1];
+    h->pot.p = theta[2];
+    h->pot.q = theta[3];
+    fill_potc(h);
+    drop_graph(h);   // the graphs hold the potential constants by value
+    return FIRE_OK;
+}
+
+fire_status fire_rgl_energy_grad_dev(fire_handle_t* h, const double* d_pos, const double box[3],
+                                     const double theta[4], double* d_forces, double* energy,
+                                     double dE_dtheta[4], void* stream) {
+    if (!h) return FIRE_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    GeoC g;
+    PotC pc;
+    GradBufs b;
+    fire_status st = grad_setup(h, d_pos, box, theta, s, &g, &pc, &b);
+    if (st != FIRE_OK) return st;
+    if (d_forces) {
+        GeoL L{{box[0], box[1], box[2]}};
+        k_g_force<<<h->grad.nb, kForceBlock, 0, s>>>(b, pc, L, h->b.exp_table, d_forces, nullptr,
+                                                     nullptr);
+        CK(h, cudaGetLastError());
+    }
+    double sums[5];
+    st = grad_sums(h, 0, 5, sums, s);
+    if (st != FIRE_OK) return st;
+    if (!std::isfinite(sums[0])) return fail(h, FIRE_ERR_NONFINITE, "non-finite energy");
+    if (energy) *energy = sums[0];
+    if (dE_dtheta)
+        for (int k = 0; k < 4; ++k) dE_dtheta[k] = sums[1 + k];
+    return FIRE_OK;
+}
+
+static void launch_hvp(fire_handle* h, const GradBufs& b, const PotC& pc, const double box[3],
+                       const double* u, double* hu, cudaStream_t s) {
+    GeoL L{{box[0], box[1], box[2]}};
+    k_g_hvp1<<<h->grad.nb, kForceBlock, 0, s>>>(b, pc, L, h->b.exp_table, u);
+    k_g_hvp2<<<h->grad.nb, kForceBlock, 0, s>>>(b, pc, L, h->b.exp_table, u, hu);
+}
+
+fire_status fire_rgl_hvp_dev(fire_handle_t* h, const double* d_pos, const double box[3],
+                             const double theta[4], const double* d_u, double* d_hu,
+                             void* stream) {
+    if (!h) return FIRE_ERR_ARG;
+    if (!d_u || !d_hu) return fail(h, FIRE_ERR_ARG, "NULL u or Hu");
+    cudaStream_t s = (cudaStream_t)stream;
+    GeoC g;
+    PotC pc;
+    GradBufs b;
+    fire_status st = grad_setup(h, d_pos, box, theta, s, &g, &pc, &b);
+    if (st != FIRE_OK) return st;
+    launch_hvp(h, b, pc, box, d_u, d_hu, s);
+    CK(h, cudaGetLastError());
+    CK(h, cudaStreamSynchronize(s));
+    return FIRE_OK;
+}
+
+// v -= mean over atoms of each Cartesian component (translation modes).
+static fire_status project_out_translations(fire_handle* h, double* v, cudaStream_t s) {
+    GradState& gs = h->grad;
+    const int n = h->n;
+    const int nb = std::min(gs.nb, 1024);
+    k_g_colsum<<<nb, kElemBlock, 0, s>>>(n, v, gs.part);
+    CK(h, cudaGetLastError());
+    CK(h, cudaMemcpyAsync(gs.h_part, gs.part, (size_t)3 * nb * sizeof(double),
+                          cudaMemcpyDeviceToHost, s));
+    CK(h, cudaStreamSynchronize(s));
+    double m[3];
+    for (int k = 0; k < 3; ++k) {
+        double acc = 0.0;
+        for (int b = 0; b < nb; ++b) acc += gs.h_part[(size_t)k * nb + b];
+        m[k] = acc / n;
+    }
+    k_g_sub_mean<<<nb, kElemBlock, 0, s>>>(n, v, m[0], m[1], m[2]);
+    CK(h, cudaGetLastError());
+    return FIRE_OK;
+}
+
+static fire_status dev_dot(fire_handle* h, const double* a, const double* b, double* out,
+                           cudaStream_t s) {
+    GradState& gs = h->grad;
+    const int nb = std::min(gs.nb, 1024);
+    k_g_dot<<<nb, kElemBlock, 0, s>>>(h->n, a, b, gs.part);
+    CK(h, cudaGetLastError());
+    CK(h, cudaMemcpyAsync(gs.h_part, gs.part, (size_t)nb * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(h, cudaStreamSynchronize(s));
+    double acc = 0.0;
+    for (int k = 0; k < nb; ++k) acc += gs.h_part[k];
+    *out = acc;
+    return FIRE_OK;
+}
+
+fire_status fire_rgl_implicit_grad_dev(fire_handle_t* h, const double* d_pos, const double box[3],
+                                       const double theta[4], const double* d_g, double tol,
+                                       int64_t maxit, double dL_dtheta[4], double* d_lambda,
+                                       int64_t* cg_iters, void* stream) {
+    if (!h) return FIRE_ERR_ARG;
+    if (!d_g || !dL_dtheta) return fail(h, FIRE_ERR_ARG, "NULL g or result");
+    if (!(tol > 0.0) || maxit < 1) return fail(h, FIRE_ERR_ARG, "need tol > 0 and maxit >= 1");
+    cudaStream_t s = (cudaStream_t)stream;
+    GeoC g;
+    PotC pc;
+    GradBufs b;
+    fire_status st = grad_setup(h, d_pos, box, theta, s, &g, &pc, &b);
+    if (st != FIRE_OK) return st;
+    const int n = h->n, m = 3 * n;
+    const size_t bytes = (size_t)m * sizeof(double);
+    double* r = h->grad.vec;
+    double* p = r + m;
+    double* Ap = p + m;
+    double* lam = Ap + m;
+    const int nb = std::min(h->grad.nb, 1024);
+    CK(h, cudaMemcpyAsync(r, d_g, bytes, cudaMemcpyDeviceToDevice, s));
+    if ((st = project_out_translations(h, r, s)) != FIRE_OK) return st;
+    CK(h, cudaMemsetAsync(lam, 0, bytes, s));
+    CK(h, cudaMemcpyAsync(p, r, bytes, cudaMemcpyDeviceToDevice, s));
+    double rr = 0.0;
+    if ((st = dev_dot(h, r, r, &rr, s)) != FIRE_OK) return st;
+    const double stop2 = tol * tol * rr;
+    int64_t it = 0;
+    while (it < maxit && rr > stop2 && rr > 0.0) {
+        launch_hvp(h, b, pc, box, p, Ap, s);
+        CK(h, cudaGetLastError());
+        if ((st = project_out_translations(h, Ap, s)) != FIRE_OK) return st;
+        double pAp = 0.0;
+        if ((st = dev_dot(h, p, Ap, &pAp, s)) != FIRE_OK) return st;
+        if (!(pAp > 0.0)) break;   // not positive definite along p
+        const double alpha = rr / pAp;
+        k_g_cg_step<<<nb, kElemBlock, 0, s>>>(m, alpha, p, Ap, lam, r);
+        double rr_new = 0.0;
+        if ((st = dev_dot(h, r, r, &rr_new, s)) != FIRE_OK) return st;
+        k_g_cg_dir<<<nb, kElemBlock, 0, s>>>(m, rr_new / rr, r, p);
+        CK(h, cudaGetLastError());
+        rr = rr_new;
+        ++it;
+    }
+    GeoL L{{box[0], box[1], box[2]}};
+    k_g_force<<<h->grad.nb, kForceBlock, 0, s>>>(b, pc, L, h->b.exp_table, nullptr, nullptr, lam);
+    CK(h, cudaGetLastError());
+    double sums[4];
+    if ((st = grad_sums(h, 5, 4, sums, s)) != FIRE_OK) return st;
+    for (int k = 0; k < 4; ++k) dL_dtheta[k] = sums[k];
+    if (d_lambda) CK(h, cudaMemcpyAsync(d_lambda, lam, bytes, cudaMemcpyDeviceToDevice, s));
+    CK(h, cudaStreamSynchronize(s));
+    if (cg_iters) *cg_iters = it;
     return FIRE_OK;
 }
 

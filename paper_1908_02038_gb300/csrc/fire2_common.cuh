@@ -45,6 +45,7 @@ struct PotC {
     float A_f, xi2_f, p_f, q2_f, r0_f, p_r0_f, q2_r0_f, rs_f, winv_f;
     long long rc2q, r0sq_q;   // rc^2 and r0^2 in (fixed-point unit)^2
     float qinv, qinv2;        // 1 / qscale, 1 / qscale^2
+    double xi_inv;            // 1 / xi (theta-derivatives)
 };
 
 // ---------------------------------------------------------------------------

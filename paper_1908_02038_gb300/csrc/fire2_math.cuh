@@ -2,7 +2,7 @@
 //
 // GB300 issues FP64 at about 1/58 of its FP32 rate, so the two exponentials
 // per pair dominate the density pass.  Their arguments, -p (r/r0 - 1) and
-// -2q (r/r0 - 1), lie in a bounded interval (|x| < 700 is checked when the
+// -2q (r/r0 - 1), lie in a bounded interval (|x| < 80 is checked when the
 // potential is set up), so no overflow, underflow or special-value handling
 // is needed.  The method is P. T. P. Tang's table-driven exponential
 // ("Table-driven implementation of the exponential function in IEEE
