@@ -36,7 +36,7 @@
 extern "C" {
 #endif
 
-#define FIRE2_ABI_VERSION 1
+#define FIRE2_ABI_VERSION 2
 
 typedef enum {
     FIRE_OK = 0,
@@ -73,9 +73,24 @@ typedef enum {
     FIRE_PREC_FP32_PAIR = 1     /* pair/embedding math in FP32; positions, sums, control FP64 */
 } fire_precision;
 
+/* Integrators of the appendix (Algorithms 3-6); Sec. 3.1 compares them. */
 typedef enum {
-    FIRE_INT_EULER_IMPLICIT = 0 /* Algorithm 4 (semi-implicit / symplectic Euler) */
+    FIRE_INT_EULER_IMPLICIT = 0, /* Algorithm 4, semi-implicit (symplectic) Euler (default) */
+    FIRE_INT_EULER_EXPLICIT = 1, /* Algorithm 3, explicit Euler: mix v(t), x += dt v(t),
+                                    v += dt F(x(t)) / m */
+    FIRE_INT_VERLET = 2,         /* Algorithm 6, velocity Verlet */
+    FIRE_INT_LEAPFROG = 3        /* Algorithm 5, Leapfrog: as Algorithm 4 with the initial
+                                    v(-dt/2) = -dt/2 F / m in place of v = 0 */
 } fire_integrator;
+
+/* Minimizer variant. */
+typedef enum {
+    FIRE_VARIANT_FIRE2 = 0,      /* FIRE 2.0, Algorithm 2 (default) */
+    FIRE_VARIANT_FIRE1 = 1       /* the original FIRE, Algorithm 1: mixing of v(t) at the
+                                    start of a P > 0 step, dt *= f_dec, alpha reset and
+                                    v = 0 on P <= 0; no N_P<=0 cap, no initial delay, no
+                                    dt_min, no half step back */
+} fire_variant;
 
 typedef struct {
     int64_t n_atoms;            /* N >= 1 */
@@ -111,6 +126,8 @@ typedef struct {
     int32_t initialdelay;       /* 1 = no dt/alpha change while i < N_delay (default 1) */
     int32_t integrator;         /* fire_integrator                   (default 0) */
     int32_t norm;               /* fire_norm for the ftol test       (default 0) */
+    int32_t variant;            /* fire_variant                      (default 0) */
+    int32_t reserved;
 } fire_params_t;
 
 typedef struct {

@@ -31,6 +31,8 @@ POT_LJ, POT_RGL, POT_QUAD = 0, 1, 2
 FORCE_BRUTE, FORCE_CELLS = 0, 1
 STOP_FTOL, STOP_MAXITER, STOP_MAXVDOTF = 0, 1, 2
 NORM_MAX_ATOM, NORM_TWO, NORM_INF = 0, 1, 2
+INT_EULER_IMPLICIT, INT_EULER_EXPLICIT, INT_VERLET, INT_LEAPFROG = 0, 1, 2, 3
+VAR_FIRE2, VAR_FIRE1 = 0, 1
 
 
 class _Sys(C.Structure):
@@ -51,7 +53,8 @@ class _Params(C.Structure):
                 ("dtgrow", C.c_double), ("dtshrink", C.c_double), ("alpha0", C.c_double),
                 ("alphashrink", C.c_double), ("delaystep", C.c_int32), ("vdfmax", C.c_int32),
                 ("halfstepback", C.c_int32), ("initialdelay", C.c_int32),
-                ("integrator", C.c_int32), ("norm", C.c_int32)]
+                ("integrator", C.c_int32), ("norm", C.c_int32), ("variant", C.c_int32),
+                ("pad", C.c_int32)]
 
 
 class _Result(C.Structure):
@@ -156,6 +159,8 @@ class Params:
     initialdelay: bool = True
     integrator: int = 0
     norm: int = NORM_MAX_ATOM
+    variant: int = 0
+    pad: int = 0
 
 
 @dataclass

@@ -14,7 +14,9 @@
  *                        alpha adaptation, N_P<=0 cap, initial delay, dt_min
  *                        guard, half step back on P <= 0).
  *   - Algorithm 4:       semi-implicit (symplectic) Euler with the mixing
- *                        placed just before the position update (Sec. 3.3).
+ *                        placed just before the position update (Sec. 3.3);
+ *                        Algorithms 3, 5, 6: explicit Euler, Leapfrog and
+ *                        velocity Verlet; Algorithm 1: the original FIRE.
  *   - Table 1:           parameter names and defaults.
  *   - Sec. 3.4:          f2norm and per-atom maximum force stopping norms.
  *   - Sec. 5.2:          EAM = pair term + embedding functional of the local
@@ -32,6 +34,14 @@
  *     still reset.
  *   - Convergence is tested once before the first iteration and after each
  *     force evaluation.
+ *   - Algorithm 3's velocity update is written with F(x(t+dt)) before that
+ *     force is computed; it uses the force at x(t) (forward Euler, the
+ *     non-symplectic scheme the paper advises against).
+ *   - The Leapfrog initialisation v(-dt/2) = -dt/2 F/m of Algorithm 5 is
+ *     applied once, in place of v = 0 at the start of the run.
+ *   - Algorithm 1 (original FIRE) has no N_P<=0 counter, initial delay,
+ *     dt_min guard or half step back, and mixes v(t) at the start of the
+ *     step (before the integration) when P > 0.
  *
  * Force routines are O(N^2) all-pairs with the minimum-image convention
  * (FORCE_BRUTE).  A cell-grid variant (FORCE_CELLS) visits the same candidate
@@ -60,7 +70,8 @@ enum { POT_LJ = 0, POT_RGL = 1, POT_QUAD = 2 };
 enum { FORCE_BRUTE = 0, FORCE_CELLS = 1 };
 enum { STOP_FTOL = 0, STOP_MAXITER = 1, STOP_MAXVDOTF = 2 };
 enum { NORM_MAX_ATOM = 0, NORM_TWO = 1, NORM_INF = 2 };
-enum { INT_EULER_IMPLICIT = 0 };
+enum { INT_EULER_IMPLICIT = 0, INT_EULER_EXPLICIT = 1, INT_VERLET = 2, INT_LEAPFROG = 3 };
+enum { VAR_FIRE2 = 0, VAR_FIRE1 = 1 };
 
 typedef struct {
     int64_t n;          /* number of atoms */
@@ -82,6 +93,7 @@ typedef struct {
 typedef struct {
     double dt_start, tmax, tmin, dtgrow, dtshrink, alpha0, alphashrink;
     int32_t delaystep, vdfmax, halfstepback, initialdelay, integrator, norm;
+    int32_t variant, pad;   /* VAR_FIRE2 (Algorithm 2) or VAR_FIRE1 (Algorithm 1) */
 } ora_params;
 
 typedef struct {
@@ -755,14 +767,24 @@ static double dot3n(const double *a, const double *b, int64_t n3) {
 }
 
 /* ------------------------------------------------------------------------ */
-/* FIRE 2.0 (Algorithm 2) with semi-implicit Euler integration (Algorithm 4). */
+/* FIRE 2.0 (Algorithm 2) or FIRE (Algorithm 1), with the integrators of      */
+/* Algorithms 3-6.                                                            */
+
+/* v = (1 - alpha) v + alpha |v| F / |F| (the mixing of Algs. 1 and 3-6). */
+static void mix_velocity(double *v, const double *f, int64_t n3, double alpha) {
+    double vn = sqrt(dot3n(v, v, n3)), fn = sqrt(dot3n(f, f, n3));
+    if (fn > 0.0)
+        for (int64_t k = 0; k < n3; ++k) v[k] = (1.0 - alpha) * v[k] + alpha * vn * f[k] / fn;
+}
 
 int ora_fire2(const ora_sys *sys, const ora_pot *pot, const ora_params *par, double *x,
               double ftol, int64_t maxiter, int mode, ora_result *out,
               ora_trace *trace, int64_t trace_cap) {
-    if (par->integrator != INT_EULER_IMPLICIT) return -3;
+    if (par->integrator < INT_EULER_IMPLICIT || par->integrator > INT_LEAPFROG) return -3;
+    if (par->variant != VAR_FIRE2 && par->variant != VAR_FIRE1) return -3;
     if (maxiter < 0 || !(ftol >= 0.0) || !(par->dt_start > 0.0) || !(sys->mass > 0.0)) return -1;
     const int64_t n = sys->n, n3 = 3 * n;
+    const double m = sys->mass;
     double *v = (double *)calloc((size_t)(n3 > 0 ? n3 : 1), sizeof(double));
     double *f = (double *)calloc((size_t)(n3 > 0 ? n3 : 1), sizeof(double));
     double E = 0.0;
@@ -774,6 +796,9 @@ int ora_fire2(const ora_sys *sys, const ora_pot *pot, const ora_params *par, dou
     const double dtmax = par->tmax * par->dt_start, dtmin = par->tmin * par->dt_start;
     int64_t npos = 0, nneg = 0, evals = 1, iters = 0;
     int stop = STOP_MAXITER;
+    /* Leapfrog initialisation (Algorithm 5): v(-dt/2) = -dt/2 F(x) / m */
+    if (par->integrator == INT_LEAPFROG)
+        for (int64_t k = 0; k < n3; ++k) v[k] = -0.5 * dt * f[k] / m;
     double fmax_atom, f2, finf;
     force_norms(f, n, &fmax_atom, &f2, &finf);
 
@@ -782,35 +807,66 @@ int ora_fire2(const ora_sys *sys, const ora_pot *pot, const ora_params *par, dou
     } else {
         for (int64_t i = 1; i <= maxiter; ++i) {
             double P = dot3n(f, v, n3);
-            if (P > 0.0) {
-                npos += 1;
-                nneg = 0;
-                if (npos > par->delaystep) {
-                    dt = fmin(dt * par->dtgrow, dtmax);
-                    alpha *= par->alphashrink;
-                }
-            } else {
-                npos = 0;
-                nneg += 1;
-                if (nneg > par->vdfmax) { stop = STOP_MAXVDOTF; iters = i - 1; break; }
-                if (!(par->initialdelay && i < par->delaystep)) {
-                    if (dt * par->dtshrink >= dtmin) dt *= par->dtshrink;
+            int mix_in_integrator = 0;
+            if (par->variant == VAR_FIRE1) {
+                /* Algorithm 1: mixing at the start of the step when P > 0 */
+                if (P > 0.0) {
+                    npos += 1;
+                    mix_velocity(v, f, n3, alpha);
+                    if (npos > par->delaystep) {
+                        dt = fmin(dt * par->dtgrow, dtmax);
+                        alpha *= par->alphashrink;
+                    }
+                } else {
+                    npos = 0;
+                    for (int64_t k = 0; k < n3; ++k) v[k] = 0.0;
+                    dt *= par->dtshrink;
                     alpha = par->alpha0;
                 }
-                if (par->halfstepback)
-                    for (int64_t k = 0; k < n3; ++k) x[k] -= 0.5 * dt * v[k];
-                for (int64_t k = 0; k < n3; ++k) v[k] = 0.0;
+            } else {
+                /* Algorithm 2 */
+                if (P > 0.0) {
+                    npos += 1;
+                    nneg = 0;
+                    if (npos > par->delaystep) {
+                        dt = fmin(dt * par->dtgrow, dtmax);
+                        alpha *= par->alphashrink;
+                    }
+                    mix_in_integrator = 1;
+                } else {
+                    npos = 0;
+                    nneg += 1;
+                    if (nneg > par->vdfmax) { stop = STOP_MAXVDOTF; iters = i - 1; break; }
+                    if (!(par->initialdelay && i < par->delaystep)) {
+                        if (dt * par->dtshrink >= dtmin) dt *= par->dtshrink;
+                        alpha = par->alpha0;
+                    }
+                    if (par->halfstepback)
+                        for (int64_t k = 0; k < n3; ++k) x[k] -= 0.5 * dt * v[k];
+                    for (int64_t k = 0; k < n3; ++k) v[k] = 0.0;
+                }
             }
-            /* Algorithm 4: kick, mix (P > 0 only), drift, new force. */
-            for (int64_t k = 0; k < n3; ++k) v[k] += dt * f[k] / sys->mass;
-            if (P > 0.0) {
-                double vn = sqrt(dot3n(v, v, n3)), fn = sqrt(dot3n(f, f, n3));
-                if (fn > 0.0)
-                    for (int64_t k = 0; k < n3; ++k)
-                        v[k] = (1.0 - alpha) * v[k] + alpha * vn * f[k] / fn;
+            /* MD integration (Algorithms 3-6); the FIRE 2.0 mixing sits inside */
+            if (par->integrator == INT_EULER_EXPLICIT) {
+                /* Algorithm 3: mix v(t), x += dt v(t), v += dt F(x(t)) / m */
+                if (mix_in_integrator) mix_velocity(v, f, n3, alpha);
+                for (int64_t k = 0; k < n3; ++k) x[k] += dt * v[k];
+                for (int64_t k = 0; k < n3; ++k) v[k] += dt * f[k] / m;
+                rc_ok = ora_energy_forces(sys, pot, x, f, &E, mode);
+            } else if (par->integrator == INT_VERLET) {
+                /* Algorithm 6: half kick, mix, drift, new force, half kick */
+                for (int64_t k = 0; k < n3; ++k) v[k] += 0.5 * dt * f[k] / m;
+                if (mix_in_integrator) mix_velocity(v, f, n3, alpha);
+                for (int64_t k = 0; k < n3; ++k) x[k] += dt * v[k];
+                rc_ok = ora_energy_forces(sys, pot, x, f, &E, mode);
+                for (int64_t k = 0; k < n3; ++k) v[k] += 0.5 * dt * f[k] / m;
+            } else {
+                /* Algorithms 4 and 5: kick, mix (of the kicked v), drift, new force */
+                for (int64_t k = 0; k < n3; ++k) v[k] += dt * f[k] / m;
+                if (mix_in_integrator) mix_velocity(v, f, n3, alpha);
+                for (int64_t k = 0; k < n3; ++k) x[k] += dt * v[k];
+                rc_ok = ora_energy_forces(sys, pot, x, f, &E, mode);
             }
-            for (int64_t k = 0; k < n3; ++k) x[k] += dt * v[k];
-            rc_ok = ora_energy_forces(sys, pot, x, f, &E, mode);
             if (rc_ok) { free(v); free(f); return rc_ok; }
             evals += 1;
             iters = i;

@@ -26,7 +26,8 @@ FIRE_STOP_FTOL, FIRE_STOP_MAXITER, FIRE_STOP_MAXVDOTF = 0, 1, 2
 FIRE_NORM_MAX_ATOM, FIRE_NORM_TWO, FIRE_NORM_INF = 0, 1, 2
 FIRE_POT_LJ, FIRE_POT_RGL = 0, 1
 FIRE_PREC_FP64, FIRE_PREC_FP32_PAIR = 0, 1
-FIRE_INT_EULER_IMPLICIT = 0
+FIRE_INT_EULER_IMPLICIT, FIRE_INT_EULER_EXPLICIT, FIRE_INT_VERLET, FIRE_INT_LEAPFROG = 0, 1, 2, 3
+FIRE_VARIANT_FIRE2, FIRE_VARIANT_FIRE1 = 0, 1
 
 STATUS_NAMES = {0: "FIRE_OK", 1: "FIRE_ERR_ARG", 2: "FIRE_ERR_CUDA", 3: "FIRE_ERR_NOMEM",
                 4: "FIRE_ERR_NONFINITE", 5: "FIRE_ERR_NBR_OVERFLOW", 6: "FIRE_ERR_TIMEOUT",
@@ -63,7 +64,8 @@ class fire_params_t(C.Structure):
                 ("dtgrow", C.c_double), ("dtshrink", C.c_double), ("alpha0", C.c_double),
                 ("alphashrink", C.c_double), ("delaystep", C.c_int32), ("vdfmax", C.c_int32),
                 ("halfstepback", C.c_int32), ("initialdelay", C.c_int32),
-                ("integrator", C.c_int32), ("norm", C.c_int32)]
+                ("integrator", C.c_int32), ("norm", C.c_int32), ("variant", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class fire_batch_tuning_t(C.Structure):

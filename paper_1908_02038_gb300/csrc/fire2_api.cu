@@ -384,6 +384,8 @@ void init_state(fire_handle* h, double ftol, int64_t maxiter) {
     q.halfstepback = p.halfstepback;
     q.initialdelay = p.initialdelay;
     q.norm = p.norm;
+    q.integrator = p.integrator;
+    q.variant = p.variant;
     fire_scal_init(q, s.fs);
     s.budget_ns = (unsigned long long)(h->budget_s * 1e9);
 }
@@ -423,7 +425,10 @@ fire_status check_params(fire_handle* h, const fire_params_t& p) {
     if (!(p.alpha0 >= 0.0 && p.alpha0 <= 1.0) || !(p.alphashrink > 0.0 && p.alphashrink <= 1.0))
         return fail(h, FIRE_ERR_ARG, "need 0 <= alpha0 <= 1 and 0 < alphashrink <= 1");
     if (p.delaystep < 0 || p.vdfmax < 0) return fail(h, FIRE_ERR_ARG, "delaystep and vdfmax must be >= 0");
-    if (p.integrator != FIRE_INT_EULER_IMPLICIT) return fail(h, FIRE_ERR_ARG, "unsupported integrator %d", p.integrator);
+    if (p.integrator < FIRE_INT_EULER_IMPLICIT || p.integrator > FIRE_INT_LEAPFROG)
+        return fail(h, FIRE_ERR_ARG, "unknown integrator %d", p.integrator);
+    if (p.variant != FIRE_VARIANT_FIRE2 && p.variant != FIRE_VARIANT_FIRE1)
+        return fail(h, FIRE_ERR_ARG, "unknown variant %d", p.variant);
     if (p.norm < 0 || p.norm > 2) return fail(h, FIRE_ERR_ARG, "unknown norm %d", p.norm);
     return FIRE_OK;
 }
@@ -481,6 +486,8 @@ fire_status fire_default_params(fire_params_t* out, double dt_start) {
     out->initialdelay = 1;
     out->integrator = FIRE_INT_EULER_IMPLICIT;
     out->norm = FIRE_NORM_MAX_ATOM;
+    out->variant = FIRE_VARIANT_FIRE2;
+    out->reserved = 0;
     return FIRE_OK;
 }
 

@@ -324,8 +324,14 @@ __device__ __forceinline__ double b_forces(const BArgs& a, const BInst& I, const
 __device__ __forceinline__ void b_reduce_control(const BArgs& a, const BInst& I, BShared& sh, double E,
                                  double* red, bool first, unsigned long long t0) {
     double P = 0.0, F2 = 0.0, V2 = 0.0, fa2 = 0.0, fin = 0.0;
+    const FireScal fs = sh.fs;
     for (int i = threadIdx.x; i < I.n; i += blockDim.x) {
-        const dvec4 f = a.f[I.off + i], v = a.v[I.off + i];
+        const dvec4 f = a.f[I.off + i];
+        dvec4 v = a.v[I.off + i];
+        if (fs.vv) {   // second half kick of velocity Verlet (Alg. 6)
+            fire_vv_kick(fs, v, f);
+            a.v[I.off + i] = v;
+        }
         P += f.x * v.x + f.y * v.y + f.z * v.z;
         const double q = f.x * f.x + f.y * f.y + f.z * f.z;
         F2 += q;
@@ -668,6 +674,8 @@ static fire_status batch_launch(fire_handle_t* h, fire_batch_state* b, double ft
     q.halfstepback = p.halfstepback;
     q.initialdelay = p.initialdelay;
     q.norm = p.norm;
+    q.integrator = p.integrator;
+    q.variant = p.variant;
     a.budget_ns = (unsigned long long)(fire2_budget(h) * 1e9);
     a.P = fire2_potc(h);
     a.exp_table = fire2_exp_table(h);

@@ -170,21 +170,31 @@ __device__ __forceinline__ void rgl_pair32(const PotC& P, long long r2q, const f
 // FIRE 2.0 scalar control (Algorithm 2) and the element-wise update
 // (Algorithm 4), shared by the single-system and the batched kernels.
 
+enum { INT_EULER_IMPLICIT = 0, INT_EULER_EXPLICIT = 1, INT_VERLET = 2, INT_LEAPFROG = 3 };
+enum { VAR_FIRE2 = 0, VAR_FIRE1 = 1 };
+
 // Parameters of Table 1 and the call arguments, device copy.
 struct FireParamsD {
     double ftol;
     long long maxiter;
     double dt_start, dtmax, dtmin, dtgrow, dtshrink, alpha0, alphashrink, mass;
-    int delaystep, vdfmax, halfstepback, initialdelay, norm, pad;
+    int delaystep, vdfmax, halfstepback, initialdelay, norm, integrator, variant, pad;
 };
 
-// Scalar state of Algorithm 2 plus the coefficients the next update applies.
+// Scalar state of Algorithms 1/2 plus the coefficients the next element-wise
+// update applies (see fire_update_atom).
 struct FireScal {
     double dt, alpha;
     long long npos, nneg, iter, evals;
-    int stop, zero_v, mix, pad;
-    double dtm;                              // dt / m of the next kick
-    double halfstep, dt_cur, mix_a, mix_fv;  // x -= halfstep v; v = (1-a) v' + a |v'| F/|F|
+    int stop, zero_v, premix, postmix, lf_init, vv, pad0, pad1;
+    double dtm;                  // dt / m
+    double halfstep;             // x -= halfstep v before v = 0
+    double kick_pre;             // v += kick_pre F before the drift
+    double kick_after;           // v += kick_after F after the drift (explicit Euler)
+    double vv_half;              // v += vv_half F_new after the force (velocity Verlet)
+    double lf_c;                 // v(-dt/2) = lf_c F (Leapfrog initialisation)
+    double dt_cur;               // drift x += dt_cur v
+    double mix_a, mix_fv_pre, mix_fv_post;   // mixing coefficients
 };
 
 __host__ __device__ inline void fire_scal_init(const FireParamsD& p, FireScal& s) {
@@ -192,18 +202,27 @@ __host__ __device__ inline void fire_scal_init(const FireParamsD& p, FireScal& s
     s.alpha = p.alpha0;
     s.npos = s.nneg = s.iter = s.evals = 0;
     s.stop = STOP_MAXITER;
-    s.zero_v = s.mix = s.pad = 0;
-    s.dtm = s.halfstep = s.dt_cur = s.mix_a = s.mix_fv = 0.0;
+    s.zero_v = s.premix = s.postmix = s.lf_init = s.vv = s.pad0 = s.pad1 = 0;
+    s.dtm = s.halfstep = s.kick_pre = s.kick_after = s.vv_half = s.lf_c = s.dt_cur = 0.0;
+    s.mix_a = s.mix_fv_pre = s.mix_fv_post = 0.0;
 }
 
 // Called after every force evaluation with the FP64 reductions of the
-// current (F, v).  Tests convergence (Alg. 2, after the integration), the
-// iteration budget, then prepares the next iteration: the P > 0 / P <= 0
-// branch with its counters, dt growth capped at dt_max after N_delay
-// positive steps, alpha decay, the N_P<=0 cap (MAXVDOTF, before any
-// correction), the initial delay, the dt_min guard, the half step back
-// with the shrunk dt, and the mixing coefficients of the kicked velocity
-// (|v'|^2 = |v|^2 + 2 (dt/m) P + (dt/m)^2 |F|^2).  Returns true to stop.
+// current (F, v) (for velocity Verlet after its second half kick).  Tests
+// convergence (after the integration, Alg. 2) and the iteration budget,
+// then prepares the next iteration:
+//  * FIRE 2.0 (Algorithm 2): the P > 0 / P <= 0 branch with its counters,
+//    dt growth capped at dt_max after N_delay positive steps, alpha decay,
+//    the N_P<=0 cap (MAXVDOTF, before any correction), the initial delay,
+//    the dt_min guard and the half step back with the shrunk dt; mixing
+//    inside the integrator when P > 0 (of the kicked velocity for
+//    Algorithms 4-6, of v(t) for Algorithm 3);
+//  * FIRE (Algorithm 1): mixing of v(t) at the start of the step when
+//    P > 0, plain dt * f_dec, alpha reset and v = 0 when P <= 0;
+//  * the integrator coefficients of Algorithms 3-6 with the new dt; the
+//    Leapfrog initialisation v(-dt/2) = -dt/2 F / m at the first iteration.
+// Norms of mixed velocities come from the reductions:
+// |v + c F|^2 = |v|^2 + 2 c P + c^2 |F|^2.  Returns true to stop.
 __device__ inline bool fire_control_step(const FireParamsD& p, FireScal& s, double P, double F2,
                                          double V2, double fa2, double fin) {
     s.evals += 1;
@@ -217,21 +236,43 @@ __device__ inline bool fire_control_step(const FireParamsD& p, FireScal& s, doub
         return true;
     }
     const long long i = ++s.iter;
-    if (P > 0.0) {
+    s.lf_init = 0;
+    if (p.integrator == INT_LEAPFROG && i == 1) {
+        s.lf_init = 1;
+        s.lf_c = -0.5 * p.dt_start / p.mass;
+        P = s.lf_c * F2;                 // F . v(-dt/2)
+        V2 = s.lf_c * s.lf_c * F2;
+    }
+    const double fnorm = sqrt(F2);
+    s.zero_v = 0;
+    s.halfstep = 0.0;
+    s.premix = 0;
+    s.postmix = 0;
+    bool mix_in_integrator = false;
+    if (p.variant == VAR_FIRE1) {
+        if (P > 0.0) {
+            s.npos += 1;
+            s.premix = fnorm > 0.0;
+            s.mix_a = s.alpha;
+            s.mix_fv_pre = fnorm > 0.0 ? sqrt(V2) / fnorm : 0.0;
+            if (s.npos > p.delaystep) {
+                s.dt = fmin(s.dt * p.dtgrow, p.dtmax);
+                s.alpha *= p.alphashrink;
+            }
+        } else {
+            s.npos = 0;
+            s.zero_v = 1;
+            s.dt *= p.dtshrink;
+            s.alpha = p.alpha0;
+        }
+    } else if (P > 0.0) {
         s.npos += 1;
         s.nneg = 0;
         if (s.npos > p.delaystep) {
             s.dt = fmin(s.dt * p.dtgrow, p.dtmax);
             s.alpha *= p.alphashrink;
         }
-        s.zero_v = 0;
-        s.halfstep = 0.0;
-        const double dtm = s.dt / p.mass;
-        const double vk2 = fmax(V2 + 2.0 * dtm * P + dtm * dtm * F2, 0.0);
-        const double fn2 = sqrt(F2);
-        s.mix = fn2 > 0.0;
-        s.mix_a = s.alpha;
-        s.mix_fv = fn2 > 0.0 ? sqrt(vk2) / fn2 : 0.0;
+        mix_in_integrator = true;
     } else {
         s.npos = 0;
         s.nneg += 1;
@@ -246,30 +287,54 @@ __device__ inline bool fire_control_step(const FireParamsD& p, FireScal& s, doub
         }
         s.zero_v = 1;
         s.halfstep = p.halfstepback ? 0.5 * s.dt : 0.0;
-        s.mix = 0;
-        s.mix_a = 0.0;
-        s.mix_fv = 0.0;
     }
+    const double dtm = s.dt / p.mass;
+    s.dtm = dtm;
     s.dt_cur = s.dt;
-    s.dtm = s.dt / p.mass;
+    s.kick_pre = p.integrator == INT_EULER_EXPLICIT ? 0.0
+                 : (p.integrator == INT_VERLET ? 0.5 * dtm : dtm);
+    s.kick_after = p.integrator == INT_EULER_EXPLICIT ? dtm : 0.0;
+    s.vv = p.integrator == INT_VERLET;
+    s.vv_half = p.integrator == INT_VERLET ? 0.5 * dtm : 0.0;
+    if (mix_in_integrator && fnorm > 0.0) {
+        s.mix_a = s.alpha;
+        if (p.integrator == INT_EULER_EXPLICIT) {
+            s.premix = 1;
+            s.mix_fv_pre = sqrt(V2) / fnorm;
+        } else {
+            const double c = s.kick_pre;
+            s.postmix = 1;
+            s.mix_fv_post = sqrt(fmax(V2 + 2.0 * c * P + c * c * F2, 0.0)) / fnorm;
+        }
+    }
     return false;
 }
 
-// One atom of the element-wise step: half step back and v = 0 after P <= 0
-// (Alg. 2), then Algorithm 4: v += dt F / m, mixing (P > 0), x += dt v.
+// One atom of the element-wise step, in the order of the algorithms: the
+// Leapfrog initial velocity, the half step back and v = 0 after P <= 0
+// (Alg. 2, or v = 0 only for Alg. 1), mixing of v(t) (Algs. 1 and 3), the
+// kick before the drift, mixing of the kicked velocity (Algs. 4-6), the
+// drift x += dt v, and the explicit-Euler kick with the force at x(t).
 __device__ __forceinline__ void fire_update_atom(const FireScal& s, dvec4& x, dvec4& v,
                                                  const dvec4& f) {
+    if (s.lf_init) v = make_dvec4(s.lf_c * f.x, s.lf_c * f.y, s.lf_c * f.z, 0.0);
     if (s.zero_v) {
         x.x -= s.halfstep * v.x;
         x.y -= s.halfstep * v.y;
         x.z -= s.halfstep * v.z;
         v = make_dvec4(0.0, 0.0, 0.0, 0.0);
     }
-    v.x += s.dtm * f.x;
-    v.y += s.dtm * f.y;
-    v.z += s.dtm * f.z;
-    if (s.mix) {
-        const double a = s.mix_a, afv = s.mix_a * s.mix_fv;
+    if (s.premix) {
+        const double a = s.mix_a, afv = s.mix_a * s.mix_fv_pre;
+        v.x = (1.0 - a) * v.x + afv * f.x;
+        v.y = (1.0 - a) * v.y + afv * f.y;
+        v.z = (1.0 - a) * v.z + afv * f.z;
+    }
+    v.x += s.kick_pre * f.x;
+    v.y += s.kick_pre * f.y;
+    v.z += s.kick_pre * f.z;
+    if (s.postmix) {
+        const double a = s.mix_a, afv = s.mix_a * s.mix_fv_post;
         v.x = (1.0 - a) * v.x + afv * f.x;
         v.y = (1.0 - a) * v.y + afv * f.y;
         v.z = (1.0 - a) * v.z + afv * f.z;
@@ -277,6 +342,16 @@ __device__ __forceinline__ void fire_update_atom(const FireScal& s, dvec4& x, dv
     x.x += s.dt_cur * v.x;
     x.y += s.dt_cur * v.y;
     x.z += s.dt_cur * v.z;
+    v.x += s.kick_after * f.x;
+    v.y += s.kick_after * f.y;
+    v.z += s.kick_after * f.z;
+}
+
+// Velocity Verlet's second half kick with the new force (Algorithm 6).
+__device__ __forceinline__ void fire_vv_kick(const FireScal& s, dvec4& v, const dvec4& f) {
+    v.x += s.vv_half * f.x;
+    v.y += s.vv_half * f.y;
+    v.z += s.vv_half * f.z;
 }
 
 }  // namespace fire2

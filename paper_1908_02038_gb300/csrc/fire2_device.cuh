@@ -539,13 +539,21 @@ __global__ void __launch_bounds__(kForceBlock) k_force32(Bufs b, PotC P, GeoC g)
 
 // ---------------------------------------------------------------------------
 // FP64 reductions of the current (F, v): P = F.v, |F|^2, |v|^2 (Alg. 2 and
-// the mixing of Alg. 4) and the per-atom / per-component force maxima (Sec. 3.4).
+// the mixing of Algs. 3-6) and the per-atom / per-component force maxima
+// (Sec. 3.4); for velocity Verlet first the second half kick (Alg. 6).
 __global__ void k_reduce(Bufs b) {
     __shared__ double red[32];
     if (b.st->done) return;
+    const bool vv = b.st->fs.vv != 0;
+    const FireScal fs = b.st->fs;
     double P = 0.0, F2 = 0.0, V2 = 0.0, fa2 = 0.0, fin = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < b.n; i += gridDim.x * blockDim.x) {
-        const dvec4 f = b.f[i], v = b.v[i];
+        const dvec4 f = b.f[i];
+        dvec4 v = b.v[i];
+        if (vv) {   // second half kick of velocity Verlet, with the new force
+            fire_vv_kick(fs, v, f);
+            b.v[i] = v;
+        }
         P += f.x * v.x + f.y * v.y + f.z * v.z;
         const double a2 = f.x * f.x + f.y * f.y + f.z * f.z;
         F2 += a2;

@@ -363,3 +363,55 @@ def test_fp32pair_relaxation_reaches_fp64_converged_state():
     assert r32.stop == fg.FIRE_STOP_FTOL and r32.fmax_atom < 1e-6
     assert fmax64_at32 < 2e-6
     assert abs(e_chk - r64.energy) / c.n < 1e-8
+
+
+# ----------------------------------------------------------------------------
+# integrators (Algorithms 3-6) and the original FIRE (Algorithm 1)
+
+INTEGRATORS = [fg.FIRE_INT_EULER_IMPLICIT, fg.FIRE_INT_EULER_EXPLICIT, fg.FIRE_INT_VERLET,
+               fg.FIRE_INT_LEAPFROG]
+
+
+@pytest.mark.parametrize("integ", INTEGRATORS)
+@pytest.mark.parametrize("variant", [fg.FIRE_VARIANT_FIRE2, fg.FIRE_VARIANT_FIRE1])
+def test_integrator_variant_state_after_40_iterations(integ, variant):
+    c = fi.rgl_vacancy_box(ncell=4, seed=81, n_vac=2)
+    xo, ro, _ = oracle.fire2(c.x, c.box, ora_rgl(),
+                             oracle.Params(dt_start=fi.CU_DT, integrator=integ, variant=variant),
+                             fi.CU_MASS, 1e-12, 40)
+    x = c.x.copy()
+    with fg.FireHandle(c.n, fi.CU_MASS, rgl_pot(), dt_start=fi.CU_DT, integrator=integ,
+                       variant=variant) as h:
+        r = h.minimize(x, c.box, 1e-12, 40)
+    assert r.stop == ro.stop == fg.FIRE_STOP_MAXITER
+    assert r.dt_final == pytest.approx(ro.dt_final, rel=1e-12)
+    assert r.alpha_final == pytest.approx(ro.alpha_final, rel=1e-12)
+    assert np.abs(x - xo).max() < 1e-9
+    assert r.energy == pytest.approx(ro.energy, rel=1e-12)
+
+
+@pytest.mark.parametrize("integ", INTEGRATORS)
+@pytest.mark.parametrize("variant", [fg.FIRE_VARIANT_FIRE2, fg.FIRE_VARIANT_FIRE1])
+def test_integrator_variant_relaxation_parity(integ, variant):
+    c = fi.lj_fcc_vacancy(seed=1)
+    xo, ro, _ = oracle.fire2(c.x, c.box, ora_lj(),
+                             oracle.Params(dt_start=fi.LJ_DT, integrator=integ, variant=variant),
+                             fi.LJ_MASS, 1e-6, 200000)
+    x = c.x.copy()
+    with fg.FireHandle(c.n, fi.LJ_MASS, lj_pot(), dt_start=fi.LJ_DT, integrator=integ,
+                       variant=variant) as h:
+        r = h.minimize(x, c.box, 1e-6, 200000)
+    assert_relax_parity(c, r, ro, 1e-6)
+
+
+def test_fire2_needs_fewer_force_evaluations_than_fire1():
+    # the paper's central comparison (Table 2, Sec. 5.3.2), on the 32k vacancy box
+    c = fi.rgl_vacancy_box(ncell=20, seed=2)
+    evals = {}
+    for variant in (fg.FIRE_VARIANT_FIRE2, fg.FIRE_VARIANT_FIRE1):
+        with fg.FireHandle(c.n, fi.CU_MASS, rgl_pot(), dt_start=fi.CU_DT, variant=variant) as h:
+            r = h.minimize(c.x.copy(), c.box, 1e-6, 100000)
+        assert r.stop == fg.FIRE_STOP_FTOL
+        evals[variant] = r.force_evals
+    print(f"force evaluations to 1e-6 eV/A: FIRE 2.0 {evals[0]}, FIRE {evals[1]}")
+    assert evals[fg.FIRE_VARIANT_FIRE2] < evals[fg.FIRE_VARIANT_FIRE1]

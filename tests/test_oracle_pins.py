@@ -318,3 +318,87 @@ def test_rgl_vacancy_relaxation_converges_and_lowers_energy():
     ev = res.energy - c.n * -3.508821531217027
     assert 0.5 < ev < 2.0
     assert res.force_evals == res.iterations + 1
+
+
+# --------------------------------------------------------------------------
+# integrators of Algorithms 3, 5, 6 and the original FIRE (Algorithm 1),
+# hand-traced on E = x^2/2 (k = m = 1, x = 1, dt = 0.1, Table 1 defaults)
+
+
+def test_explicit_euler_first_iterations():
+    # i=1: P = 0 -> v = 0; mix no-op; x = 1 + 0.1*0 = 1; v = 0 + 0.1*F(1) = -0.1
+    # i=2: P = (-1)(-0.1) = 0.1; x = 1 - 0.01 = 0.99; v = -0.1 + 0.1*(-1) = -0.2
+    # i=3: P = (-0.99)(-0.2) = 0.198; x = 0.99 - 0.02 = 0.97; v = -0.2 - 0.099 = -0.299
+    for it, (xe, pe) in enumerate([(1.0, 0.0), (0.99, 0.1), (0.97, 0.198)], start=1):
+        xf, res, rows = run_quad([1, 0, 0], [1, 0, 0], it, integrator=oracle.INT_EULER_EXPLICIT)
+        assert xf[0] == pytest.approx(xe, abs=1e-15)
+        assert rows[-1]["P"] == pytest.approx(pe, abs=1e-15)
+
+
+def test_velocity_verlet_first_iterations():
+    # i=1: P = 0 -> v = 0; half kick v = -0.05; x = 1 - 0.005 = 0.995;
+    #      F = -0.995; half kick v = -0.05 - 0.04975 = -0.09975
+    # i=2: P = 0.995 * 0.09975 = 0.09925125; v = -0.09975 - 0.04975 = -0.1495;
+    #      x = 0.995 - 0.01495 = 0.98005
+    xf, res, rows = run_quad([1, 0, 0], [1, 0, 0], 1, integrator=oracle.INT_VERLET)
+    assert xf[0] == pytest.approx(0.995, abs=1e-15)
+    xf, res, rows = run_quad([1, 0, 0], [1, 0, 0], 2, integrator=oracle.INT_VERLET)
+    assert xf[0] == pytest.approx(0.98005, abs=1e-15)
+    assert rows[-1]["P"] == pytest.approx(0.09925125, abs=1e-15)
+
+
+def test_leapfrog_first_iterations():
+    # v(-dt/2) = -0.05 * F(1) = +0.05.
+    # i=1: P = -0.05 <= 0 -> half step back x = 1 - 0.05*0.05 = 0.9975, v = 0;
+    #      kick v = -0.1 (force at x = 1); x = 0.9975 - 0.01 = 0.9875
+    # i=2: P = 0.9875 * 0.1 = 0.09875; v = -0.1 - 0.09875 = -0.19875;
+    #      x = 0.9875 - 0.019875 = 0.967625
+    xf, res, rows = run_quad([1, 0, 0], [1, 0, 0], 1, integrator=oracle.INT_LEAPFROG)
+    assert xf[0] == pytest.approx(0.9875, abs=1e-15)
+    assert rows[-1]["P"] == pytest.approx(-0.05, abs=1e-15) and rows[-1]["nneg"] == 1
+    xf, res, rows = run_quad([1, 0, 0], [1, 0, 0], 2, integrator=oracle.INT_LEAPFROG)
+    assert xf[0] == pytest.approx(0.967625, abs=1e-15)
+
+
+def test_original_fire_first_iterations():
+    # Algorithm 1 with the semi-implicit Euler step:
+    # i=1: P = 0 -> v = 0, dt = 0.05 (no initial delay), alpha = 0.25;
+    #      v = -0.05, x = 1 - 0.0025 = 0.9975
+    # i=2: P = 0.049875 > 0, no growth yet; v = -0.05 - 0.049875 = -0.099875;
+    #      x = 0.9975 - 0.05*0.099875 = 0.99250625
+    xf, res, rows = run_quad([1, 0, 0], [1, 0, 0], 2, variant=oracle.VAR_FIRE1)
+    assert xf[0] == pytest.approx(0.99250625, abs=1e-15)
+    assert res.dt_final == 0.05
+
+
+def test_original_fire_mixes_before_the_kick():
+    # E = (x^2 + 10 y^2)/2, (x, y) = (1, 1), dt = 0.1, Algorithm 1:
+    # i=1: P = 0 -> dt = 0.05; v = 0.05 F = (-0.05, -0.5); x = (0.9975, 0.975)
+    # i=2: F = (-0.9975, -9.75), P > 0: mix v(t) with |v| = sqrt(0.2525),
+    #      |F| = sqrt(96.05750625): v = 0.75 v + 0.25 |v| F/|F|; kick v += 0.05 F;
+    #      x += 0.05 v
+    nv, nF = math.sqrt(0.2525), math.sqrt(96.05750625)
+    vx = 0.75 * -0.05 + 0.25 * nv * -0.9975 / nF + 0.05 * -0.9975
+    vy = 0.75 * -0.5 + 0.25 * nv * -9.75 / nF + 0.05 * -9.75
+    xf, res, rows = run_quad([1, 10, 0], [1, 1, 0], 2, variant=oracle.VAR_FIRE1)
+    assert xf[0] == pytest.approx(0.9975 + 0.05 * vx, abs=1e-15)
+    assert xf[1] == pytest.approx(0.975 + 0.05 * vy, abs=1e-15)
+
+
+def test_original_fire_has_no_dt_floor_or_maxvdotf():
+    # F = 0: every pass has P = 0; dt halves every pass and no MAXVDOTF stop
+    xf, res, rows = run_quad([1, 0, 0], [0, 0, 0], 12, dt_start=1.0, vdfmax=3,
+                             variant=oracle.VAR_FIRE1)
+    assert res.stop == oracle.STOP_MAXITER
+    assert res.dt_final == 0.5 ** 12
+
+
+@pytest.mark.parametrize("integ", [oracle.INT_EULER_IMPLICIT, oracle.INT_EULER_EXPLICIT,
+                                   oracle.INT_VERLET, oracle.INT_LEAPFROG])
+@pytest.mark.parametrize("variant", [oracle.VAR_FIRE2, oracle.VAR_FIRE1])
+def test_every_integrator_and_variant_relaxes_the_lj_box(integ, variant):
+    c = fi.lj_fcc_vacancy(seed=1)
+    xf, res, _ = oracle.fire2(c.x, c.box, lj(), oracle.Params(dt_start=fi.LJ_DT, integrator=integ,
+                                                                variant=variant),
+                              1.0, 1e-6, 100000)
+    assert res.stop == oracle.STOP_FTOL and res.fmax_atom < 1e-6
