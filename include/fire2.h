@@ -36,7 +36,7 @@
 extern "C" {
 #endif
 
-#define FIRE2_ABI_VERSION 2
+#define FIRE2_ABI_VERSION 3
 
 typedef enum {
     FIRE_OK = 0,
@@ -67,6 +67,18 @@ typedef enum {
     FIRE_POT_LJ = 0,            /* 12-6 Lennard-Jones, energy shifted to 0 at rc */
     FIRE_POT_RGL = 1            /* second-moment (RGL) EAM, quintic taper on [rs, rc) */
 } fire_pot_kind;
+
+/* How the RGL pair functions phi(r), g(r) and their derivatives are
+ * evaluated.  FIRE_PAIR_TABLE: piecewise quintic Hermite polynomials in
+ * u = r^2 - r0^2 (knots every ~0.04 A^2, on rs and rc, matching value, first
+ * and second derivative at every knot; interpolation error ~1e-13 relative
+ * for values, ~1e-11 for derivatives), no square root or exponential per
+ * pair; pairs closer than r0/2 use the analytic functions.
+ * FIRE_PAIR_ANALYTIC: the exponentials and the taper per pair. */
+typedef enum {
+    FIRE_PAIR_TABLE = 0,
+    FIRE_PAIR_ANALYTIC = 1
+} fire_pair_eval;
 
 typedef enum {
     FIRE_PREC_FP64 = 0,         /* all arithmetic in FP64 */
@@ -109,6 +121,9 @@ typedef struct {
     double A, xi, p, q, r0, rs, rc;
     double skin;                /* neighbour-list skin (>= 0); lists rebuilt after
                                    any atom moved more than skin/2 */
+    int32_t pair_eval;          /* fire_pair_eval (RGL): FIRE_PAIR_TABLE (default) or
+                                   FIRE_PAIR_ANALYTIC */
+    int32_t reserved;
 } fire_potential_t;
 
 /* FIRE 2.0 parameters: Table 1 names; dt_start is the MD timestep. */
@@ -365,6 +380,13 @@ fire_status fire_rgl_implicit_grad_dev(fire_handle_t* h, const double* d_pos, co
                                        const double theta[4], const double* d_g, double tol,
                                        int64_t maxit, double dL_dtheta[4], double* d_lambda,
                                        int64_t* cg_iters, void* stream);
+
+/* Diagnostic, host only (no GPU needed): evaluates the FP64 pair-function
+ * table the library builds for pot at n distances r (host arrays) into
+ * out[4 n] = (phi, g, dphi/dr, dg/dr) per distance, zero at r >= rc.  The
+ * paper has no counterpart.  Errors: FIRE_ERR_ARG. */
+fire_status fire_diag_rgl_table(const fire_potential_t* pot, int64_t n, const double* r,
+                                double* out);
 
 /* Message of the last failed call on h (or of the last failed fire_init when
  * h is NULL).  Never NULL. */

@@ -111,6 +111,8 @@ def _load():
         lib.ora_rgl_cg.restype = C.c_int64
         lib.ora_rgl_cg.argtypes = [C.POINTER(_Sys), C.POINTER(_Pot), C.c_void_p, C.c_void_p,
                                    C.c_double, C.c_int64, C.c_void_p, C.c_int]
+        lib.ora_rgl_pair_terms.restype = C.c_int
+        lib.ora_rgl_pair_terms.argtypes = [C.POINTER(_Pot), C.c_int64, C.c_void_p, C.c_void_p]
         lib.ora_set_threads.argtypes = [C.c_int]
         lib.ora_max_threads.restype = C.c_int
         _lib = lib
@@ -241,6 +243,17 @@ def densities(x, box, pot: Potential, periodic=(1, 1, 1)):
     _check(_load().ora_densities(C.byref(s), C.byref(p), x.ctypes.data, rho.ctypes.data),
            "densities")
     return rho
+
+
+def rgl_pair_terms(pot: Potential, r):
+    """(n, 4): phi(r), g(r), phi'(r), g'(r) of the RGL pair functions."""
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    out = np.zeros((len(r), 4))
+    keep: list = []
+    p = _pot(pot, keep)
+    _check(_load().ora_rgl_pair_terms(C.byref(p), len(r), r.ctypes.data, out.ctypes.data),
+           "rgl_pair_terms")
+    return out
 
 
 def rgl_param_derivs(x, box, pot: Potential, periodic=(1, 1, 1), mode: int = FORCE_BRUTE):

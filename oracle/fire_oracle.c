@@ -149,6 +149,20 @@ static void rgl_pair(const ora_pot *pot, double r, double *phi, double *dphi,
     *dg = eq * (-2.0 * pot->q / pot->r0 * S + dS);
 }
 
+/* phi, g, phi', g' at n distances (out[4 i + 0..3]); zero at r >= rc. */
+int ora_rgl_pair_terms(const ora_pot *pot, int64_t n, const double *r, double *out) {
+    if (pot->kind != POT_RGL) return -1;
+    for (int64_t i = 0; i < n; ++i) {
+        double phi = 0.0, dphi = 0.0, g = 0.0, dg = 0.0;
+        if (r[i] < pot->rc) rgl_pair(pot, r[i], &phi, &dphi, &g, &dg);
+        out[4 * i] = phi;
+        out[4 * i + 1] = g;
+        out[4 * i + 2] = dphi;
+        out[4 * i + 3] = dg;
+    }
+    return 0;
+}
+
 /* LJ: phi(r) = 4 eps [(sigma/r)^12 - (sigma/r)^6] - phi(rc) for r < rc. */
 static double lj_phi(const ora_pot *pot, double r) {
     double sr6 = pow(pot->sigma / r, 6.0);

@@ -26,6 +26,7 @@ FIRE_STOP_FTOL, FIRE_STOP_MAXITER, FIRE_STOP_MAXVDOTF = 0, 1, 2
 FIRE_NORM_MAX_ATOM, FIRE_NORM_TWO, FIRE_NORM_INF = 0, 1, 2
 FIRE_POT_LJ, FIRE_POT_RGL = 0, 1
 FIRE_PREC_FP64, FIRE_PREC_FP32_PAIR = 0, 1
+FIRE_PAIR_TABLE, FIRE_PAIR_ANALYTIC = 0, 1
 FIRE_INT_EULER_IMPLICIT, FIRE_INT_EULER_EXPLICIT, FIRE_INT_VERLET, FIRE_INT_LEAPFROG = 0, 1, 2, 3
 FIRE_VARIANT_FIRE2, FIRE_VARIANT_FIRE1 = 0, 1
 
@@ -41,7 +42,7 @@ EXPORTED = ("fire_abi_version", "fire_default_params", "fire_init", "fire_minimi
             "fire_batch_init", "fire_minimize_batch", "fire_minimize_batch_dev",
             "fire_batch_set_tuning", "fire_batch_autotune", "fire_set_rgl_params",
             "fire_rgl_energy_grad_dev", "fire_rgl_hvp_dev", "fire_rgl_implicit_grad_dev",
-            "fire_last_error", "fire_destroy")
+            "fire_diag_rgl_table", "fire_last_error", "fire_destroy")
 FIRE_EXEC_GRAPH_WHILE, FIRE_EXEC_CHUNKED = 0, 1
 STAGES = ("build", "density", "embed", "force", "reduce", "control", "update")
 
@@ -56,7 +57,7 @@ class fire_potential_t(C.Structure):
                 ("eps", C.c_double), ("sigma", C.c_double), ("rc_lj", C.c_double),
                 ("A", C.c_double), ("xi", C.c_double), ("p", C.c_double), ("q", C.c_double),
                 ("r0", C.c_double), ("rs", C.c_double), ("rc", C.c_double),
-                ("skin", C.c_double)]
+                ("skin", C.c_double), ("pair_eval", C.c_int32), ("reserved", C.c_int32)]
 
 
 class fire_params_t(C.Structure):
@@ -121,6 +122,8 @@ def load_library(path: str | None = None):
     lib.fire_batch_set_tuning.argtypes = [H, C.POINTER(fire_batch_tuning_t)]
     D4 = C.POINTER(C.c_double)
     lib.fire_set_rgl_params.argtypes = [H, D4]
+    lib.fire_diag_rgl_table.argtypes = [C.POINTER(fire_potential_t), C.c_int64, C.c_void_p,
+                                        C.c_void_p]
     lib.fire_rgl_energy_grad_dev.argtypes = [H, C.c_void_p, D4, D4, C.c_void_p, D4, D4, C.c_void_p]
     lib.fire_rgl_hvp_dev.argtypes = [H, C.c_void_p, D4, D4, C.c_void_p, C.c_void_p, C.c_void_p]
     lib.fire_rgl_implicit_grad_dev.argtypes = [H, C.c_void_p, D4, D4, C.c_void_p, C.c_double,
@@ -370,6 +373,15 @@ def fire_rgl_implicit_grad_dev(handle, d_pos, box, theta, d_g, tol=1e-10, maxit=
     return np.array(list(out)), int(it.value)
 
 
+def fire_diag_rgl_table(pot: fire_potential_t, r) -> np.ndarray:
+    """Host evaluation of the pair-function table: (n, 4) = phi, g, phi', g'."""
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    out = np.zeros((len(r), 4))
+    _check(load_library().fire_diag_rgl_table(C.byref(pot), len(r), r.ctypes.data,
+                                              out.ctypes.data), None)
+    return out
+
+
 def _check_dev(t):
     import torch
     if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64
@@ -401,11 +413,12 @@ class Potential:
     rs: float = 0.0
     rc: float = 0.0
     skin: float = 0.3
+    pair_eval: int = FIRE_PAIR_TABLE
 
     def c(self) -> fire_potential_t:
         return fire_potential_t(self.kind, self.precision, self.eps, self.sigma, self.rc_lj,
                                 self.A, self.xi, self.p, self.q, self.r0, self.rs, self.rc,
-                                self.skin)
+                                self.skin, self.pair_eval, 0)
 
 
 class FireBatch:

@@ -62,6 +62,11 @@ struct fire_handle {
     cudaGraphExec_t exec_init = nullptr, exec_chunk = nullptr, exec_final = nullptr;
     fire_batch_state* batch = nullptr;   // set for handles made by fire_batch_init
     GradState grad;
+    // tabulated pair functions: device copies and launch shapes
+    double *tab_d64 = nullptr, *tab_f64 = nullptr;
+    float *tab_d32 = nullptr, *tab_f32 = nullptr;
+    size_t smem_d = 0, smem_f = 0;
+    int nb_tab_d = 0, nb_tab_f = 0;
     std::string err;
 };
 
@@ -167,7 +172,8 @@ fire_status ensure_buffers(fire_handle* h, const GeoC& g, int cap) {
         h->b.crep = h->b.cden = nullptr;
         const size_t slots = (size_t)cap * h->n;
         CK(h, cudaMalloc(&h->b.nbr, slots * sizeof(uint32_t)));
-        if (h->pot.kind == FIRE_POT_RGL && h->pot.precision == FIRE_PREC_FP64) {
+        if (h->pot.kind == FIRE_POT_RGL && h->pot.precision == FIRE_PREC_FP64 &&
+            h->pot.pair_eval == FIRE_PAIR_ANALYTIC) {
             CK(h, cudaMalloc(&h->b.crep, slots * sizeof(double)));
             CK(h, cudaMalloc(&h->b.cden, slots * sizeof(double)));
         }
@@ -203,7 +209,15 @@ void launch_build(fire_handle* h, const GeoC& g, int force, cudaStream_t s) {
 
 void launch_forces(fire_handle* h, const GeoC& g, cudaStream_t s) {
     const int n = h->n;
-    if (h->pot.kind == FIRE_POT_RGL && h->pot.precision == FIRE_PREC_FP32_PAIR) {
+    const bool tab = h->pot.kind == FIRE_POT_RGL && h->pot.pair_eval == FIRE_PAIR_TABLE;
+    if (tab && h->pot.precision == FIRE_PREC_FP32_PAIR) {
+        k_density32_tab<<<h->nb_tab_d, kForceBlock, h->smem_d, s>>>(h->b, h->potc, g);
+        k_force32_tab<<<h->nb_tab_f, kForceBlock, h->smem_f, s>>>(h->b, h->potc, g);
+    } else if (tab) {
+        k_density_tab<<<h->nb_tab_d, kForceBlock, h->smem_d, s>>>(h->b, h->potc, g);
+        k_embed<<<h->b.nb_embed, kElemBlock, 0, s>>>(h->b);
+        k_force_tab<<<h->nb_tab_f, kForceBlock, h->smem_f, s>>>(h->b, h->potc, g);
+    } else if (h->pot.kind == FIRE_POT_RGL && h->pot.precision == FIRE_PREC_FP32_PAIR) {
         k_density32<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
         k_force32<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
     } else if (h->pot.kind == FIRE_POT_RGL) {
@@ -506,6 +520,7 @@ static bool fill_potc(fire_handle* h) {
         return true;
     }
     c.rc2 = pot->rc * pot->rc;
+    c.r0sq = pot->r0 * pot->r0;
     c.A = pot->A;
     c.xi2 = pot->xi * pot->xi;
     c.xi_inv = 1.0 / pot->xi;
@@ -544,6 +559,44 @@ static bool fill_potc(fire_handle* h) {
     return true;
 }
 
+// Builds the pair-function tables for the current parameters and copies them
+// to the device (allocating on the first call).
+static fire_status upload_tables(fire_handle* h) {
+    const fire_potential_t& p = h->pot;
+    const RglTables T = build_rgl_tables(p.A, p.xi, p.p, p.q, p.r0, p.rs, p.rc);
+    h->potc.tab = T.meta;
+    const size_t nd = T.dens64.size(), nf = T.force64.size();
+    if (!h->tab_d64) {
+        CK(h, cudaMalloc(&h->tab_d64, nd * sizeof(double)));
+        CK(h, cudaMalloc(&h->tab_f64, nf * sizeof(double)));
+        CK(h, cudaMalloc(&h->tab_d32, nd * sizeof(float)));
+        CK(h, cudaMalloc(&h->tab_f32, nf * sizeof(float)));
+    }
+    CK(h, cudaMemcpy(h->tab_d64, T.dens64.data(), nd * sizeof(double), cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpy(h->tab_f64, T.force64.data(), nf * sizeof(double), cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpy(h->tab_d32, T.dens32.data(), nd * sizeof(float), cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpy(h->tab_f32, T.force32.data(), nf * sizeof(float), cudaMemcpyHostToDevice));
+    h->b.tab_d64 = h->tab_d64;
+    h->b.tab_f64 = h->tab_f64;
+    h->b.tab_d32 = h->tab_d32;
+    h->b.tab_f32 = h->tab_f32;
+    const bool f32 = p.precision == FIRE_PREC_FP32_PAIR;
+    h->smem_d = nd * (f32 ? sizeof(float) : sizeof(double));
+    h->smem_f = nf * (f32 ? sizeof(float) : sizeof(double));
+    const void* kd = f32 ? (const void*)k_density32_tab : (const void*)k_density_tab;
+    const void* kf = f32 ? (const void*)k_force32_tab : (const void*)k_force_tab;
+    CK(h, cudaFuncSetAttribute(kd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->smem_d));
+    CK(h, cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->smem_f));
+    int sms = 0, occ_d = 0, occ_f = 0;
+    CK(h, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+    CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_d, kd, kForceBlock, h->smem_d));
+    CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_f, kf, kForceBlock, h->smem_f));
+    const int need = ceil_div(h->n, kForceBlock);
+    h->nb_tab_d = std::max(1, std::min(need, sms * std::max(occ_d, 1)));
+    h->nb_tab_f = std::max(1, std::min(need, sms * std::max(occ_f, 1)));
+    return FIRE_OK;
+}
+
 static fire_status init_handle(fire_handle_t** hp, const fire_system_t* sys,
                                const fire_potential_t* pot, const fire_params_t* params,
                                bool single) {
@@ -554,6 +607,8 @@ static fire_status init_handle(fire_handle_t** hp, const fire_system_t* sys,
     if (!(sys->mass > 0.0) || !std::isfinite(sys->mass)) return fail(nullptr, FIRE_ERR_ARG, "mass must be > 0");
     if (pot->kind != FIRE_POT_LJ && pot->kind != FIRE_POT_RGL)
         return fail(nullptr, FIRE_ERR_ARG, "unknown potential kind %d", pot->kind);
+    if (pot->pair_eval != FIRE_PAIR_TABLE && pot->pair_eval != FIRE_PAIR_ANALYTIC)
+        return fail(nullptr, FIRE_ERR_ARG, "unknown pair_eval %d", pot->pair_eval);
     if (pot->precision != FIRE_PREC_FP64 &&
         !(pot->precision == FIRE_PREC_FP32_PAIR && pot->kind == FIRE_POT_RGL))
         return fail(nullptr, FIRE_ERR_ARG,
@@ -644,6 +699,12 @@ static fire_status init_handle(fire_handle_t** hp, const fire_system_t* sys,
         CKI(cudaMalloc(&b.fp, n * sizeof(double)));
     }
     CKI(cudaMalloc(&b.epart, (size_t)(b.nb_force + b.nb_embed) * sizeof(double)));
+    // table kernels write fewer energy partials than nb_force; the rest stay 0
+    CKI(cudaMemset(b.epart, 0, (size_t)(b.nb_force + b.nb_embed) * sizeof(double)));
+    if (pot->kind == FIRE_POT_RGL && pot->pair_eval == FIRE_PAIR_TABLE) {
+        fire_status ts = upload_tables(h);
+        if (ts != FIRE_OK) return bail(ts);
+    }
     CKI(cudaMalloc(&b.rpart, (size_t)5 * b.nb_red * sizeof(double)));
     CKI(cudaMalloc(&b.st, sizeof(DevState)));
     CKI(cudaMalloc(&b.pos_io, 3 * n * sizeof(double)));
@@ -704,6 +765,8 @@ void fire_destroy(fire_handle_t* h) {
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->batch) fire2_batch_free(h->batch);
+    for (void* p : {(void*)h->tab_d64, (void*)h->tab_f64, (void*)h->tab_d32, (void*)h->tab_f32})
+        if (p) cudaFree(p);
     {
         GradState& gs = h->grad;
         void* gp[] = {gs.x, gs.xref, gs.xf, gs.nbr, gs.nnbr, gs.rho, gs.F1, gs.F2, gs.drho,
@@ -1019,6 +1082,10 @@ fire_status fire_set_rgl_params(fire_handle_t* h, const double theta[4]) {
     h->pot.p = theta[2];
     h->pot.q = theta[3];
     fill_potc(h);
+    if (h->tab_d64) {
+        st = upload_tables(h);
+        if (st != FIRE_OK) return st;
+    }
     drop_graph(h);   // the graphs hold the potential constants by value
     return FIRE_OK;
 }
@@ -1164,6 +1231,39 @@ fire_status fire_rgl_implicit_grad_dev(fire_handle_t* h, const double* d_pos, co
     return FIRE_OK;
 }
 
+fire_status fire_diag_rgl_table(const fire_potential_t* pot, int64_t n, const double* r,
+                                double* out) {
+    if (!pot || n < 0 || (n > 0 && (!r || !out)) || pot->kind != FIRE_POT_RGL ||
+        !(pot->rc > pot->rs && pot->rs > 0.0 && pot->r0 > 0.0 && pot->xi > 0.0))
+        return FIRE_ERR_ARG;
+    const RglTables T = build_rgl_tables(pot->A, pot->xi, pot->p, pot->q, pot->r0, pot->rs,
+                                         pot->rc);
+    for (int64_t i = 0; i < n; ++i) {
+        const double u = r[i] * r[i] - pot->r0 * pot->r0;
+        int k;
+        double t;
+        double* o = out + 4 * i;
+        if (!(r[i] < pot->rc)) {
+            o[0] = o[1] = o[2] = o[3] = 0.0;
+        } else if (tab_locate(T.meta, u, k, t)) {
+            const double* cd = T.dens64.data() + (size_t)k * kTabDens;
+            const double* cf = T.force64.data() + (size_t)k * kTabForce;
+            o[0] = poly5(cd, t);
+            o[1] = poly5(cd + 6, t);
+            o[2] = 2.0 * r[i] * poly5(cf, t);
+            o[3] = 2.0 * r[i] * poly5(cf + 6, t);
+        } else {
+            double a[8];
+            rgl_analytic(pot->A, pot->xi, pot->p, pot->q, pot->r0, pot->rs, pot->rc, r[i], a);
+            o[0] = a[0];
+            o[1] = a[4];
+            o[2] = a[1];
+            o[3] = a[5];
+        }
+    }
+    return FIRE_OK;
+}
+
 fire_status fire_profile_stages(fire_handle_t* h, const double* pos, const double box[3],
                                 int32_t reps, double* stage_ms) {
     if (!h) return FIRE_ERR_ARG;
@@ -1188,12 +1288,17 @@ fire_status fire_profile_stages(fire_handle_t* h, const double* pos, const doubl
         cudaEventRecord(ev[0], s);
         launch_build(h, g, 1, s);
         cudaEventRecord(ev[1], s);
-        if (rgl && f32) k_density32<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
+        const bool tab = rgl && h->pot.pair_eval == FIRE_PAIR_TABLE;
+        if (tab && f32) k_density32_tab<<<h->nb_tab_d, kForceBlock, h->smem_d, s>>>(h->b, h->potc, g);
+        else if (tab) k_density_tab<<<h->nb_tab_d, kForceBlock, h->smem_d, s>>>(h->b, h->potc, g);
+        else if (rgl && f32) k_density32<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
         else if (rgl) k_density<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
         cudaEventRecord(ev[2], s);
         if (rgl && !f32) k_embed<<<h->b.nb_embed, kElemBlock, 0, s>>>(h->b);
         cudaEventRecord(ev[3], s);
-        if (rgl && f32) k_force32<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
+        if (tab && f32) k_force32_tab<<<h->nb_tab_f, kForceBlock, h->smem_f, s>>>(h->b, h->potc, g);
+        else if (tab) k_force_tab<<<h->nb_tab_f, kForceBlock, h->smem_f, s>>>(h->b, h->potc, g);
+        else if (rgl && f32) k_force32<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
         else if (rgl) k_force_rgl<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, g);
         else k_force_lj<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
         cudaEventRecord(ev[4], s);

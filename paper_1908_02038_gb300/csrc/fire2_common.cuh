@@ -31,6 +31,18 @@ enum { STOP_FTOL = 0, STOP_MAXITER = 1, STOP_MAXVDOTF = 2 };
 enum { POT_LJ = 0, POT_RGL = 1 };
 enum { CTL_INITIAL = 0, CTL_LOOP = 1, CTL_EVAL = 2 };
 
+// Knots of the tabulated RGL pair functions (built in fire2_table.cuh):
+// region A covers [u_lo, u_rs] with spacing 1/hA_inv and a knot at u = 0,
+// region B covers [u_rs, rc^2 - r0^2] with spacing 1/hB_inv.
+struct TabMeta {
+    int nA0;                    // intervals of region A below u = 0
+    int nA;                     // intervals of region A
+    int nB;                     // intervals of region B
+    int pad;
+    double hA_inv, hB_inv, u_lo, u_rs;
+    float hA_inv_f, hB_inv_f, u_lo_f, u_rs_f;
+};
+
 // Potential constants, passed by value.
 struct PotC {
     int kind;
@@ -46,6 +58,8 @@ struct PotC {
     long long rc2q, r0sq_q;   // rc^2 and r0^2 in (fixed-point unit)^2
     float qinv, qinv2;        // 1 / qscale, 1 / qscale^2
     double xi_inv;            // 1 / xi (theta-derivatives)
+    double r0sq;              // r0^2 (table variable u = r^2 - r0^2)
+    TabMeta tab;              // knots of the tabulated pair functions
 };
 
 // ---------------------------------------------------------------------------

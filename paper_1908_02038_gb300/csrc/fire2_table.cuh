@@ -1,0 +1,226 @@
+// Tabulated RGL pair functions.
+//
+// The two exponentials, the square root and the taper of every pair are
+// replaced by piecewise quintic Hermite polynomials in u = r^2 - r0^2:
+//   density table: phi(u), g(u)               (6 coefficients each)
+//   force table:   phi_u(u), g_u(u) = d/du    (6 coefficients each)
+// with phi = A e^{-p(r/r0-1)} S(r) and g = xi^2 e^{-2q(r/r0-1)} S(r).  Since
+// (dE/dr)/r = 2 dE/du, the force pass needs neither r nor 1/r.
+//
+// Knots: region A covers [u_lo, u_rs] with spacing hA, and u = 0 and
+// u_rs = rs^2 - r0^2 are knots; region B covers the taper [u_rs, u_rc] with
+// spacing hB (u_rc = rc^2 - r0^2 a knot), so the jumps of S''' at rs and rc
+// fall on knots.  u_lo = -0.75 r0^2 (r = r0/2); closer pairs fall back to the
+// analytic functions.  Each interval's quintic matches the function and its
+// first two u-derivatives at both ends: for the density table f, f_u, f_uu
+// and for the force table f_u, f_uu, f_uuu, with (primes = d/dr)
+//   f_u = f'/(2r),  f_uu = (f'' - f'/r)/(4 r^2),
+//   f_uuu = (f''' - 3 f''/r + 3 f'/r^2)/(8 r^3).
+// With spacings near 0.04 A^2 the interpolation error is ~1e-12 relative or
+// better on the Cu parameters (largest for pairs compressed towards r0/2).
+//
+// Index arithmetic: region A uses x = u / hA (so pairs near r0, where the
+// forces are stiffest, keep the full precision of u even in FP32), region B
+// x = (u - u_rs) / hB.
+#pragma once
+
+#include <cmath>
+#include <vector>
+
+#include "fire2_common.cuh"
+
+namespace fire2 {
+
+constexpr int kTabDens = 12;    // coefficients per interval, density table
+constexpr int kTabForce = 12;   // coefficients per interval, force table
+
+struct RglTables {
+    TabMeta meta;
+    std::vector<double> dens64, force64;
+    std::vector<float> dens32, force32;
+};
+
+// Analytic phi, g and their first three r-derivatives (host):
+// out = (phi, phi', phi'', phi''', g, g', g'', g''').  taper < 0: decide from
+// r; taper = 0: S = 1 (inside region A); taper = 1: the taper polynomial
+// with t clamped to [0, 1] (inside region B) -- the table builder passes the
+// region so that the one-sided limits at rs and rc are used (S''' jumps there).
+inline void rgl_analytic(double A, double xi, double p, double q, double r0, double rs,
+                         double rc, double r, double out[8], int taper = -1) {
+    double S = 1.0, dS = 0.0, d2S = 0.0, d3S = 0.0;
+    if (taper < 0) taper = (r >= rc) ? 2 : (r > rs ? 1 : 0);
+    if (taper == 2) {
+        S = 0.0;
+    } else if (taper == 1) {
+        const double w = rc - rs;
+        double t = (r - rs) / w;
+        t = t < 0.0 ? 0.0 : (t > 1.0 ? 1.0 : t);
+        S = 1.0 - 10.0 * t * t * t + 15.0 * t * t * t * t - 6.0 * t * t * t * t * t;
+        dS = (-30.0 * t * t + 60.0 * t * t * t - 30.0 * t * t * t * t) / w;
+        d2S = (-60.0 * t + 180.0 * t * t - 120.0 * t * t * t) / (w * w);
+        d3S = (-60.0 + 360.0 * t - 360.0 * t * t) / (w * w * w);
+    }
+    const double s = r / r0 - 1.0;
+    const double pre[2] = {A * std::exp(-p * s), xi * xi * std::exp(-2.0 * q * s)};
+    const double rate[2] = {p / r0, 2.0 * q / r0};
+    for (int k = 0; k < 2; ++k) {
+        const double e = pre[k], a = rate[k];
+        out[4 * k] = e * S;
+        out[4 * k + 1] = e * (-a * S + dS);
+        out[4 * k + 2] = e * (a * a * S - 2.0 * a * dS + d2S);
+        out[4 * k + 3] = e * (-a * a * a * S + 3.0 * a * a * dS - 3.0 * a * d2S + d3S);
+    }
+}
+
+// Quintic Hermite coefficients on [0, 1] from values F, scaled first
+// derivatives D = h f_u and scaled second derivatives S = h^2 f_uu at both ends.
+inline void quintic_hermite(double F0, double D0, double S0, double F1, double D1, double S1,
+                            double c[6]) {
+    const double dF = F1 - F0;
+    c[0] = F0;
+    c[1] = D0;
+    c[2] = 0.5 * S0;
+    c[3] = 10.0 * dF - 6.0 * D0 - 4.0 * D1 - 1.5 * S0 + 0.5 * S1;
+    c[4] = -15.0 * dF + 8.0 * D0 + 7.0 * D1 + 1.5 * S0 - S1;
+    c[5] = 6.0 * dF - 3.0 * D0 - 3.0 * D1 - 0.5 * S0 + 0.5 * S1;
+}
+
+inline RglTables build_rgl_tables(double A, double xi, double p, double q, double r0, double rs,
+                                  double rc) {
+    RglTables T;
+    const double r02 = r0 * r0;
+    const double u_rs = rs * rs - r02, u_rc = rc * rc - r02, u_min = -0.75 * r02;
+    const double target = 0.04;
+    const int nAp = std::max(1, (int)std::ceil(u_rs / target));            // knots 0..u_rs
+    const double hA = u_rs / nAp;
+    const int nA0 = (int)std::ceil(-u_min / hA);                           // below u = 0
+    const int nB = std::max(1, (int)std::ceil((u_rc - u_rs) / target));
+    const double hB = (u_rc - u_rs) / nB;
+    TabMeta& m = T.meta;
+    m.nA0 = nA0;
+    m.nA = nA0 + nAp;
+    m.nB = nB;
+    m.hA_inv = 1.0 / hA;
+    m.hB_inv = 1.0 / hB;
+    m.u_lo = -nA0 * hA;
+    m.u_rs = u_rs;
+    m.hA_inv_f = (float)m.hA_inv;
+    m.hB_inv_f = (float)m.hB_inv;
+    m.u_lo_f = (float)m.u_lo;
+    m.u_rs_f = (float)u_rs;
+    const int nint = m.nA + m.nB;
+    T.dens64.resize((size_t)nint * kTabDens);
+    T.force64.resize((size_t)nint * kTabForce);
+    // f, f_u, f_uu, f_uuu in u for phi (k = 0) and g (k = 1)
+    auto derivs_u = [&](double u, int taper, double f[2][4]) {
+        const double r = std::sqrt(r02 + u);
+        double a[8];
+        rgl_analytic(A, xi, p, q, r0, rs, rc, r, a, taper);
+        for (int k = 0; k < 2; ++k) {
+            const double f0 = a[4 * k], f1 = a[4 * k + 1], f2 = a[4 * k + 2], f3 = a[4 * k + 3];
+            f[k][0] = f0;
+            f[k][1] = f1 / (2.0 * r);
+            f[k][2] = (f2 - f1 / r) / (4.0 * r * r);
+            f[k][3] = (f3 - 3.0 * f2 / r + 3.0 * f1 / (r * r)) / (8.0 * r * r * r);
+        }
+    };
+    for (int i = 0; i < nint; ++i) {
+        double ua, h;
+        if (i < m.nA) {
+            h = hA;
+            ua = (i - nA0) * hA;
+        } else {
+            h = hB;
+            ua = u_rs + (i - m.nA) * hB;
+        }
+        const double ub = (i == m.nA - 1) ? u_rs : ((i == nint - 1) ? u_rc : ua + h);
+        double fa[2][4], fb[2][4];
+        const int taper = i < m.nA ? 0 : 1;
+        derivs_u(ua, taper, fa);
+        derivs_u(ub, taper, fb);
+        for (int k = 0; k < 2; ++k) {
+            double c[6];
+            quintic_hermite(fa[k][0], h * fa[k][1], h * h * fa[k][2], fb[k][0], h * fb[k][1],
+                            h * h * fb[k][2], c);
+            for (int j = 0; j < 6; ++j) T.dens64[(size_t)i * kTabDens + 6 * k + j] = c[j];
+            quintic_hermite(fa[k][1], h * fa[k][2], h * h * fa[k][3], fb[k][1], h * fb[k][2],
+                            h * h * fb[k][3], c);
+            for (int j = 0; j < 6; ++j) T.force64[(size_t)i * kTabForce + 6 * k + j] = c[j];
+        }
+    }
+    T.dens32.assign(T.dens64.begin(), T.dens64.end());
+    T.force32.assign(T.force64.begin(), T.force64.end());
+    return T;
+}
+
+// Interval index and local coordinate t in [0, 1]; false outside the table
+// (u < u_lo; u >= u_rc never reaches here because of the cut-off test).
+__host__ __device__ __forceinline__ bool tab_locate(const TabMeta& m, double u, int& k, double& t) {
+    if (u < m.u_lo) return false;
+    double x;
+    if (u < m.u_rs) {
+        x = u * m.hA_inv;
+        const double fl = floor(x);
+        k = (int)fl + m.nA0;
+        t = x - fl;
+        if (k >= m.nA) {   // rounding at u_rs
+            k = m.nA - 1;
+            t = 1.0;
+        }
+    } else {
+        x = (u - m.u_rs) * m.hB_inv;
+        const double fl = floor(x);
+        k = (int)fl;
+        t = x - fl;
+        if (k >= m.nB) {
+            k = m.nB - 1;
+            t = 1.0;
+        }
+        k += m.nA;
+    }
+    if (k < 0) {
+        k = 0;
+        t = 0.0;
+    }
+    return true;
+}
+
+__device__ __forceinline__ bool tab_locate_f(const TabMeta& m, float u, int& k, float& t) {
+    if (u < m.u_lo_f) return false;
+    if (u < m.u_rs_f) {
+        const float x = u * m.hA_inv_f;
+        const float fl = floorf(x);
+        k = (int)fl + m.nA0;
+        t = x - fl;
+        if (k >= m.nA) {
+            k = m.nA - 1;
+            t = 1.f;
+        }
+    } else {
+        const float x = (u - m.u_rs_f) * m.hB_inv_f;
+        const float fl = floorf(x);
+        k = (int)fl;
+        t = x - fl;
+        if (k >= m.nB) {
+            k = m.nB - 1;
+            t = 1.f;
+        }
+        k += m.nA;
+    }
+    if (k < 0) {
+        k = 0;
+        t = 0.f;
+    }
+    return true;
+}
+
+template <typename T>
+__host__ __device__ __forceinline__ T poly5(const T* c, T t) {
+    return ((((c[5] * t + c[4]) * t + c[3]) * t + c[2]) * t + c[1]) * t + c[0];
+}
+template <typename T>
+__host__ __device__ __forceinline__ T poly4(const T* c, T t) {
+    return (((c[4] * t + c[3]) * t + c[2]) * t + c[1]) * t + c[0];
+}
+
+}  // namespace fire2

@@ -37,7 +37,7 @@ def test_library_exports_every_header_symbol(lib):
 
 
 def test_abi_version_and_defaults(lib):
-    assert fg.fire_abi_version() == 2
+    assert fg.fire_abi_version() == 3
     p = fg.fire_default_params(0.001)
     assert (p.tmax, p.tmin, p.dtgrow, p.dtshrink, p.alpha0, p.alphashrink) == \
         (10.0, 0.02, 1.1, 0.5, 0.25, 0.99)
@@ -51,7 +51,7 @@ def test_abi_version_and_defaults(lib):
 def test_struct_layouts_match_header(lib):
     # sizes of the C structs as the header lays them out on LP64
     assert ctypes.sizeof(fg.fire_system_t) == 8 + 8 + 12 + 4
-    assert ctypes.sizeof(fg.fire_potential_t) == 4 + 4 + 8 * 11
+    assert ctypes.sizeof(fg.fire_potential_t) == 4 + 4 + 8 * 11 + 8
     assert ctypes.sizeof(fg.fire_params_t) == 7 * 8 + 8 * 4
     assert ctypes.sizeof(fg.fire_result_t) == 8 + 8 * 3 + 4 + 4 + 8 * 5
 
@@ -89,3 +89,23 @@ def test_batch_init_rejects_bad_offsets(lib):
     with pytest.raises(fg.FireError) as e:
         fg.fire_batch_init([0, 4], sys, lj, par)
     assert "RGL" in str(e.value)
+
+
+def test_pair_function_table_matches_oracle(lib):
+    """The quintic Hermite tables of the RGL pair functions (host copy of what
+    the kernels use) against the oracle's analytic phi, g and derivatives."""
+    import fire_inputs as fi
+    import numpy as np
+    import oracle
+    pot = fg.Potential(fg.FIRE_POT_RGL, **fi.RGL_CU).c()
+    r = np.concatenate([np.linspace(1.0, 4.999999, 200001),
+                        [fi.RGL_CU["r0"], fi.RGL_CU["rs"], 4.5 + 1e-9, 4.5 - 1e-9]])
+    tab = fg.fire_diag_rgl_table(pot, r)
+    ref = oracle.rgl_pair_terms(oracle.Potential("rgl", **fi.RGL_CU), r)
+    near = r > 2.0          # pairs no more compressed than ~0.8 r0
+    for k in range(4):
+        err = np.abs(tab[:, k] - ref[:, k])
+        assert err.max() / np.abs(ref[:, k]).max() < 5e-11, k
+        assert err[near].max() / np.abs(ref[near, k]).max() < 5e-12, k
+    # beyond rc everything vanishes
+    assert np.all(fg.fire_diag_rgl_table(pot, np.array([5.0, 6.0])) == 0.0)
