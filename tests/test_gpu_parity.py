@@ -422,3 +422,34 @@ def test_fire2_and_fire1_reach_the_same_minimum():
            for (v, i), r in res.items()})
     e = [r.energy / c.n for r in res.values()]
     assert max(e) - min(e) < 1e-8
+
+
+@pytest.mark.parametrize("precision", [fg.FIRE_PREC_FP64, fg.FIRE_PREC_FP32_PAIR])
+def test_analytic_and_tabulated_pair_functions_agree(precision):
+    c = fi.rgl_vacancy_box(ncell=7, seed=91, n_vac=6, sigma=0.1)
+    eo, fo = oracle.energy_forces(c.x, c.box, ora_rgl())
+    out = {}
+    for mode in (fg.FIRE_PAIR_TABLE, fg.FIRE_PAIR_ANALYTIC):
+        pot = rgl_pot(precision=precision)
+        pot.pair_eval = mode
+        with fg.FireHandle(c.n, fi.CU_MASS, pot, dt_start=fi.CU_DT) as h:
+            out[mode] = h.energy_forces(c.x, c.box)
+    for mode, (e, f) in out.items():
+        if precision == fg.FIRE_PREC_FP64:
+            assert force_rel_err(f, fo) < F_REL, mode
+            assert e == pytest.approx(eo, rel=E_REL), mode
+        else:
+            assert np.abs(f - fo).max() < F32_ABS, mode
+            assert abs(e - eo) / c.n < E32_PER_ATOM, mode
+
+
+def test_compressed_pairs_fall_back_to_analytic_terms():
+    # a dimer at 0.45 r0 lies below the table; forces must still match the oracle
+    x = np.array([[5.0, 5.0, 5.0], [5.0 + 0.45 * fi.RGL_CU["r0"], 5.0, 5.0],
+                  [8.0, 7.5, 5.5]])
+    box = [20.0, 20.0, 20.0]
+    eo, fo = oracle.energy_forces(x, box, ora_rgl())
+    with fg.FireHandle(3, fi.CU_MASS, rgl_pot(), dt_start=fi.CU_DT) as h:
+        e, f = h.energy_forces(x, box)
+    assert force_rel_err(f, fo) < F_REL
+    assert e == pytest.approx(eo, rel=E_REL)
