@@ -172,8 +172,7 @@ fire_status ensure_buffers(fire_handle* h, const GeoC& g, int cap) {
         h->b.crep = h->b.cden = nullptr;
         const size_t slots = (size_t)cap * h->n;
         CK(h, cudaMalloc(&h->b.nbr, slots * sizeof(uint32_t)));
-        if (h->pot.kind == FIRE_POT_RGL && h->pot.precision == FIRE_PREC_FP64 &&
-            h->pot.pair_eval == FIRE_PAIR_ANALYTIC) {
+        if (h->pot.kind == FIRE_POT_RGL && h->pot.precision == FIRE_PREC_FP64) {
             CK(h, cudaMalloc(&h->b.crep, slots * sizeof(double)));
             CK(h, cudaMalloc(&h->b.cden, slots * sizeof(double)));
         }
@@ -211,12 +210,12 @@ void launch_forces(fire_handle* h, const GeoC& g, cudaStream_t s) {
     const int n = h->n;
     const bool tab = h->pot.kind == FIRE_POT_RGL && h->pot.pair_eval == FIRE_PAIR_TABLE;
     if (tab && h->pot.precision == FIRE_PREC_FP32_PAIR) {
-        k_density32_tab<<<h->nb_tab_d, kForceBlock, h->smem_d, s>>>(h->b, h->potc, g);
-        k_force32_tab<<<h->nb_tab_f, kForceBlock, h->smem_f, s>>>(h->b, h->potc, g);
+        k_density32_tab<<<h->nb_tab_d, kTabBlock, h->smem_d, s>>>(h->b, h->potc, g);
+        k_force32_tab<<<h->nb_tab_f, kTabBlock, h->smem_f, s>>>(h->b, h->potc, g);
     } else if (tab) {
         k_density_tab<<<h->nb_tab_d, kForceBlock, h->smem_d, s>>>(h->b, h->potc, g);
         k_embed<<<h->b.nb_embed, kElemBlock, 0, s>>>(h->b);
-        k_force_tab<<<h->nb_tab_f, kForceBlock, h->smem_f, s>>>(h->b, h->potc, g);
+        k_force_rgl<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, g);
     } else if (h->pot.kind == FIRE_POT_RGL && h->pot.precision == FIRE_PREC_FP32_PAIR) {
         k_density32<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
         k_force32<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
@@ -563,35 +562,42 @@ static bool fill_potc(fire_handle* h) {
 // to the device (allocating on the first call).
 static fire_status upload_tables(fire_handle* h) {
     const fire_potential_t& p = h->pot;
-    const RglTables T = build_rgl_tables(p.A, p.xi, p.p, p.q, p.r0, p.rs, p.rc);
+    const RglTables T = build_rgl_tables(p.A, p.xi, p.p, p.q, p.r0, p.rs, p.rc, 0.04);
+    const RglTables T32 = build_rgl_tables(p.A, p.xi, p.p, p.q, p.r0, p.rs, p.rc, 0.12);
     h->potc.tab = T.meta;
+    h->potc.tab32 = T32.meta;
     const size_t nd = T.dens64.size(), nf = T.force64.size();
+    const size_t nd32 = T32.dens32.size(), nf32 = T32.force32.size();
     if (!h->tab_d64) {
         CK(h, cudaMalloc(&h->tab_d64, nd * sizeof(double)));
         CK(h, cudaMalloc(&h->tab_f64, nf * sizeof(double)));
-        CK(h, cudaMalloc(&h->tab_d32, nd * sizeof(float)));
-        CK(h, cudaMalloc(&h->tab_f32, nf * sizeof(float)));
+        CK(h, cudaMalloc(&h->tab_d32, nd32 * sizeof(float)));
+        CK(h, cudaMalloc(&h->tab_f32, nf32 * sizeof(float)));
     }
     CK(h, cudaMemcpy(h->tab_d64, T.dens64.data(), nd * sizeof(double), cudaMemcpyHostToDevice));
     CK(h, cudaMemcpy(h->tab_f64, T.force64.data(), nf * sizeof(double), cudaMemcpyHostToDevice));
-    CK(h, cudaMemcpy(h->tab_d32, T.dens32.data(), nd * sizeof(float), cudaMemcpyHostToDevice));
-    CK(h, cudaMemcpy(h->tab_f32, T.force32.data(), nf * sizeof(float), cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpy(h->tab_d32, T32.dens32.data(), nd32 * sizeof(float), cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpy(h->tab_f32, T32.force32.data(), nf32 * sizeof(float), cudaMemcpyHostToDevice));
     h->b.tab_d64 = h->tab_d64;
     h->b.tab_f64 = h->tab_f64;
     h->b.tab_d32 = h->tab_d32;
     h->b.tab_f32 = h->tab_f32;
     const bool f32 = p.precision == FIRE_PREC_FP32_PAIR;
-    h->smem_d = nd * (f32 ? sizeof(float) : sizeof(double));
-    h->smem_f = nf * (f32 ? sizeof(float) : sizeof(double));
+    // FP64: one kernel holds both tables; FP32: one table per kernel
+    h->smem_d = f32 ? nd32 * sizeof(float) : (nd + nf) * sizeof(double);
+    h->smem_f = f32 ? nf32 * sizeof(float) : 0;
+    const int block = f32 ? kTabBlock : kForceBlock;
     const void* kd = f32 ? (const void*)k_density32_tab : (const void*)k_density_tab;
-    const void* kf = f32 ? (const void*)k_force32_tab : (const void*)k_force_tab;
     CK(h, cudaFuncSetAttribute(kd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->smem_d));
-    CK(h, cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->smem_f));
-    int sms = 0, occ_d = 0, occ_f = 0;
+    int sms = 0, occ_d = 0, occ_f = 1;
     CK(h, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
-    CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_d, kd, kForceBlock, h->smem_d));
-    CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_f, kf, kForceBlock, h->smem_f));
-    const int need = ceil_div(h->n, kForceBlock);
+    CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_d, kd, block, h->smem_d));
+    if (f32) {
+        const void* kf = (const void*)k_force32_tab;
+        CK(h, cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->smem_f));
+        CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_f, kf, block, h->smem_f));
+    }
+    const int need = ceil_div(h->n, block);
     h->nb_tab_d = std::max(1, std::min(need, sms * std::max(occ_d, 1)));
     h->nb_tab_f = std::max(1, std::min(need, sms * std::max(occ_f, 1)));
     return FIRE_OK;
@@ -1237,7 +1243,7 @@ fire_status fire_diag_rgl_table(const fire_potential_t* pot, int64_t n, const do
         !(pot->rc > pot->rs && pot->rs > 0.0 && pot->r0 > 0.0 && pot->xi > 0.0))
         return FIRE_ERR_ARG;
     const RglTables T = build_rgl_tables(pot->A, pot->xi, pot->p, pot->q, pot->r0, pot->rs,
-                                         pot->rc);
+                                         pot->rc, 0.04);
     for (int64_t i = 0; i < n; ++i) {
         const double u = r[i] * r[i] - pot->r0 * pot->r0;
         int k;
@@ -1289,15 +1295,14 @@ fire_status fire_profile_stages(fire_handle_t* h, const double* pos, const doubl
         launch_build(h, g, 1, s);
         cudaEventRecord(ev[1], s);
         const bool tab = rgl && h->pot.pair_eval == FIRE_PAIR_TABLE;
-        if (tab && f32) k_density32_tab<<<h->nb_tab_d, kForceBlock, h->smem_d, s>>>(h->b, h->potc, g);
+        if (tab && f32) k_density32_tab<<<h->nb_tab_d, kTabBlock, h->smem_d, s>>>(h->b, h->potc, g);
         else if (tab) k_density_tab<<<h->nb_tab_d, kForceBlock, h->smem_d, s>>>(h->b, h->potc, g);
         else if (rgl && f32) k_density32<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
         else if (rgl) k_density<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
         cudaEventRecord(ev[2], s);
         if (rgl && !f32) k_embed<<<h->b.nb_embed, kElemBlock, 0, s>>>(h->b);
         cudaEventRecord(ev[3], s);
-        if (tab && f32) k_force32_tab<<<h->nb_tab_f, kForceBlock, h->smem_f, s>>>(h->b, h->potc, g);
-        else if (tab) k_force_tab<<<h->nb_tab_f, kForceBlock, h->smem_f, s>>>(h->b, h->potc, g);
+        if (tab && f32) k_force32_tab<<<h->nb_tab_f, kTabBlock, h->smem_f, s>>>(h->b, h->potc, g);
         else if (rgl && f32) k_force32<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
         else if (rgl) k_force_rgl<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, g);
         else k_force_lj<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);

@@ -23,6 +23,7 @@ constexpr uint32_t kIdxBits = 25;
 constexpr uint32_t kIdxMask = (1u << kIdxBits) - 1u;
 constexpr int kCodeZero = 62;  // image code of the zero shift, (2 + 5*2 + 25*2)
 constexpr int kForceBlock = 128;
+constexpr int kTabBlock = 256;    // FP32 table kernels (more warps per shared table copy)
 constexpr int kElemBlock = 256;
 constexpr int kCtlThreads = 512;
 
@@ -59,7 +60,8 @@ struct PotC {
     float qinv, qinv2;        // 1 / qscale, 1 / qscale^2
     double xi_inv;            // 1 / xi (theta-derivatives)
     double r0sq;              // r0^2 (table variable u = r^2 - r0^2)
-    TabMeta tab;              // knots of the tabulated pair functions
+    TabMeta tab;              // knots of the tabulated pair functions (FP64)
+    TabMeta tab32;            // knots of the FP32 tables
 };
 
 // ---------------------------------------------------------------------------
@@ -156,12 +158,20 @@ __device__ __forceinline__ void rgl_pair64(const PotC& P, double r2, const doubl
     dg = eq * (-P.q2_r0 * S + dS);
 }
 
+// int64 -> float through two exact 32-bit halves (the 64-bit conversion
+// would occupy the FP64 pipe, 1/58 of the FP32 rate on this part).
+__device__ __forceinline__ float ll_to_float(long long v) {
+    const int hi = (int)(v >> 32);
+    const unsigned lo = (unsigned)(v & 0xffffffffll);
+    return fmaf((float)hi, 4294967296.0f, (float)lo);
+}
+
 // RGL pair terms in FP32 from the exact fixed-point r^2.
 __device__ __forceinline__ void rgl_pair32(const PotC& P, long long r2q, const float* et,
                                            float& rinv, float& phi, float& dphi, float& g,
                                            float& dg) {
-    const float r2 = __ll2float_rn(r2q) * P.qinv2;
-    const float u = __ll2float_rn(r2q - P.r0sq_q) * P.qinv2;   // r^2 - r0^2
+    const float r2 = ll_to_float(r2q) * P.qinv2;
+    const float u = ll_to_float(r2q - P.r0sq_q) * P.qinv2;   // r^2 - r0^2
     rinv = rsqrtf(r2);
     const float r = r2 * rinv;
     const float s = u / (P.r0_f * (r + P.r0_f));                // r/r0 - 1

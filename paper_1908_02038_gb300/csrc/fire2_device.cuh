@@ -551,15 +551,20 @@ __device__ __forceinline__ void load_table(T* dst, const T* src, int count) {
     for (int t = threadIdx.x; t < count; t += blockDim.x) dst[t] = src[t];
 }
 
-// FP64 pass 1 (half list): rho_i, rho_j (atomics) and 2 phi per pair.
+// FP64 pass 1 (half list): rho_i, rho_j (atomics), 2 phi per pair, and the
+// pair cache of pass 2 (2 phi'/r = 4 phi_u, g'/r = 2 g_u) from the tables.
 __global__ void __launch_bounds__(kForceBlock) k_density_tab(Bufs b, PotC P, GeoC g) {
-    extern __shared__ double tabd[];
+    extern __shared__ double tabs[];   // density table, then force table
     __shared__ double3 tbl[125];
     __shared__ double etab[kExpTableSize];
     __shared__ double red[32];
     if (b.st->done) return;
+    const int nint = P.tab.nA + P.tab.nB;
+    double* tabd = tabs;
+    double* tabf = tabs + nint * kTabDens;
     fill_shift_table(tbl, g);
-    load_table(tabd, b.tab_d64, (P.tab.nA + P.tab.nB) * kTabDens);
+    load_table(tabd, b.tab_d64, nint * kTabDens);
+    load_table(tabf, b.tab_f64, nint * kTabForce);
     load_table(etab, b.exp_table, kExpTableSize);
     __syncthreads();
     double erep = 0.0;
@@ -568,7 +573,8 @@ __global__ void __launch_bounds__(kForceBlock) k_density_tab(Bufs b, PotC P, Geo
         const int m = b.nnbr[i];
         double rho_i = 0.0;
         for (int k = 0; k < m; ++k) {
-            const uint32_t e = b.nbr[(size_t)k * b.n + i];
+            const size_t slot = (size_t)k * b.n + i;
+            const uint32_t e = b.nbr[slot];
             const int j = (int)(e & kIdxMask);
             const int code = (int)(e >> kIdxBits);
             const dvec4 xj = b.x[j];
@@ -580,20 +586,29 @@ __global__ void __launch_bounds__(kForceBlock) k_density_tab(Bufs b, PotC P, Geo
                 dz -= sh.z;
             }
             const double r2 = dx * dx + dy * dy + dz * dz;
-            if (!(r2 < P.rc2)) continue;
-            int ki;
-            double t, phi, gg;
-            if (tab_locate(P.tab, r2 - P.r0sq, ki, t)) {
-                const double* c = tabd + ki * kTabDens;
-                phi = poly5(c, t);
-                gg = poly5(c + 6, t);
-            } else {
-                double rinv, dphi, dg;
-                rgl_pair64(P, r2, etab, rinv, phi, dphi, gg, dg);
+            double crep = 0.0, cden = 0.0;
+            if (r2 < P.rc2) {
+                int ki;
+                double t, phi, gg;
+                if (tab_locate(P.tab, r2 - P.r0sq, ki, t)) {
+                    const double* cd = tabd + ki * kTabDens;
+                    const double* cf = tabf + ki * kTabForce;
+                    phi = poly5(cd, t);
+                    gg = poly5(cd + 6, t);
+                    crep = 4.0 * poly5(cf, t);
+                    cden = 2.0 * poly5(cf + 6, t);
+                } else {
+                    double rinv, dphi, dg;
+                    rgl_pair64(P, r2, etab, rinv, phi, dphi, gg, dg);
+                    crep = 2.0 * dphi * rinv;
+                    cden = dg * rinv;
+                }
+                rho_i += gg;
+                atomicAdd(&b.rho[j], gg);
+                erep += 2.0 * phi;
             }
-            rho_i += gg;
-            atomicAdd(&b.rho[j], gg);
-            erep += 2.0 * phi;
+            b.crep[slot] = crep;
+            b.cden[slot] = cden;
         }
         atomicAdd(&b.rho[i], rho_i);
     }
@@ -601,80 +616,16 @@ __global__ void __launch_bounds__(kForceBlock) k_density_tab(Bufs b, PotC P, Geo
     if (threadIdx.x == 0) b.epart[blockIdx.x] = s;
 }
 
-// FP64 pass 2 (half list): fs = (dE/dr)/r = 2 [2 phi_u + (F'_i + F'_j) g_u],
-// F_i += fs d, F_j -= fs d.
-__global__ void __launch_bounds__(kForceBlock) k_force_tab(Bufs b, PotC P, GeoC g) {
-    extern __shared__ double tabf[];
-    __shared__ double3 tbl[125];
-    __shared__ double etab[kExpTableSize];
-    if (b.st->done) return;
-    fill_shift_table(tbl, g);
-    load_table(tabf, b.tab_f64, (P.tab.nA + P.tab.nB) * kTabForce);
-    load_table(etab, b.exp_table, kExpTableSize);
-    __syncthreads();
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < b.n; i += gridDim.x * blockDim.x) {
-        const dvec4 xi = b.x[i];
-        const double fpi = b.fp[i];
-        const int m = b.nnbr[i];
-        double fx = 0.0, fy = 0.0, fz = 0.0;
-        for (int k = 0; k < m; ++k) {
-            const uint32_t e = b.nbr[(size_t)k * b.n + i];
-            const int j = (int)(e & kIdxMask);
-            const int code = (int)(e >> kIdxBits);
-            const dvec4 xj = b.x[j];
-            double dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
-            if (code != kCodeZero) {
-                const double3 sh = tbl[code];
-                dx -= sh.x;
-                dy -= sh.y;
-                dz -= sh.z;
-            }
-            const double r2 = dx * dx + dy * dy + dz * dz;
-            if (!(r2 < P.rc2)) continue;
-            int ki;
-            double t, phiu, gu;
-            if (tab_locate(P.tab, r2 - P.r0sq, ki, t)) {
-                const double* c = tabf + ki * kTabForce;
-                phiu = poly5(c, t);
-                gu = poly5(c + 6, t);
-            } else {
-                double rinv, phi, dphi, gg, dg;
-                rgl_pair64(P, r2, etab, rinv, phi, dphi, gg, dg);
-                phiu = 0.5 * dphi * rinv;
-                gu = 0.5 * dg * rinv;
-            }
-            const double fs = 2.0 * (2.0 * phiu + (fpi + b.fp[j]) * gu);
-            fx += fs * dx;
-            fy += fs * dy;
-            fz += fs * dz;
-            atomicAdd(&b.f[j].x, -fs * dx);
-            atomicAdd(&b.f[j].y, -fs * dy);
-            atomicAdd(&b.f[j].z, -fs * dz);
-        }
-        atomicAdd(&b.f[i].x, fx);
-        atomicAdd(&b.f[i].y, fy);
-        atomicAdd(&b.f[i].z, fz);
-    }
-}
-
-// int64 -> float through two exact 32-bit halves (the 64-bit conversion
-// would occupy the FP64 pipe).
-__device__ __forceinline__ float ll_to_float(long long v) {
-    const int hi = (int)(v >> 32);
-    const unsigned lo = (unsigned)(v & 0xffffffffll);
-    return fmaf((float)hi, 4294967296.0f, (float)lo);
-}
-
 // FP32-pair pass 1 (full list, tables): u = r^2 - r0^2 exact in fixed point,
 // rounded once to float.
-__global__ void __launch_bounds__(kForceBlock) k_density32_tab(Bufs b, PotC P, GeoC g) {
+__global__ void __launch_bounds__(kTabBlock) k_density32_tab(Bufs b, PotC P, GeoC g) {
     extern __shared__ float tabd32[];
     __shared__ int3 qt[125];
     __shared__ float et[kExp32TableSize];
     __shared__ double red[32];
     if (b.st->done) return;
     fill_qshift_table(qt, g);
-    load_table(tabd32, b.tab_d32, (P.tab.nA + P.tab.nB) * kTabDens);
+    load_table(tabd32, b.tab_d32, (P.tab32.nA + P.tab32.nB) * kTabDens);
     load_table(et, b.exp32_table, kExp32TableSize);
     __syncthreads();
     double e_sum = 0.0;
@@ -688,7 +639,7 @@ __global__ void __launch_bounds__(kForceBlock) k_density32_tab(Bufs b, PotC P, G
             if (r2q >= P.rc2q) continue;
             int ki;
             float t, phi, gg;
-            if (tab_locate_f(P.tab, ll_to_float(r2q - P.r0sq_q) * P.qinv2, ki, t)) {
+            if (tab_locate_f(P.tab32, ll_to_float(r2q - P.r0sq_q) * P.qinv2, ki, t)) {
                 const float* c = tabd32 + ki * kTabDens;
                 phi = poly5(c, t);
                 gg = poly5(c + 6, t);
@@ -711,13 +662,13 @@ __global__ void __launch_bounds__(kForceBlock) k_density32_tab(Bufs b, PotC P, G
 }
 
 // FP32-pair pass 2 (full list, tables): F_i = sum_j fs d, Kahan per component.
-__global__ void __launch_bounds__(kForceBlock) k_force32_tab(Bufs b, PotC P, GeoC g) {
+__global__ void __launch_bounds__(kTabBlock) k_force32_tab(Bufs b, PotC P, GeoC g) {
     extern __shared__ float tabf32[];
     __shared__ int3 qt[125];
     __shared__ float et[kExp32TableSize];
     if (b.st->done) return;
     fill_qshift_table(qt, g);
-    load_table(tabf32, b.tab_f32, (P.tab.nA + P.tab.nB) * kTabForce);
+    load_table(tabf32, b.tab_f32, (P.tab32.nA + P.tab32.nB) * kTabForce);
     load_table(et, b.exp32_table, kExp32TableSize);
     __syncthreads();
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < b.n; i += gridDim.x * blockDim.x) {
@@ -731,7 +682,7 @@ __global__ void __launch_bounds__(kForceBlock) k_force32_tab(Bufs b, PotC P, Geo
             if (r2q >= P.rc2q) continue;
             int ki;
             float t, phiu, gu;
-            if (tab_locate_f(P.tab, ll_to_float(r2q - P.r0sq_q) * P.qinv2, ki, t)) {
+            if (tab_locate_f(P.tab32, ll_to_float(r2q - P.r0sq_q) * P.qinv2, ki, t)) {
                 const float* c = tabf32 + ki * kTabForce;
                 phiu = poly5(c, t);
                 gu = poly5(c + 6, t);

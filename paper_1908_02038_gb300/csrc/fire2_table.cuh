@@ -16,8 +16,10 @@
 // and for the force table f_u, f_uu, f_uuu, with (primes = d/dr)
 //   f_u = f'/(2r),  f_uu = (f'' - f'/r)/(4 r^2),
 //   f_uuu = (f''' - 3 f''/r + 3 f'/r^2)/(8 r^3).
-// With spacings near 0.04 A^2 the interpolation error is ~1e-12 relative or
-// better on the Cu parameters (largest for pairs compressed towards r0/2).
+// With spacings near 0.04 A^2 (FP64 tables) the interpolation error is
+// ~1e-11 relative or better on the Cu parameters (largest for pairs
+// compressed towards r0/2, ~1e-12 above 0.8 r0); the FP32 tables use
+// 0.12 A^2, still far below float rounding.
 //
 // Index arithmetic: region A uses x = u / hA (so pairs near r0, where the
 // forces are stiffest, keep the full precision of u even in FP32), region B
@@ -85,12 +87,12 @@ inline void quintic_hermite(double F0, double D0, double S0, double F1, double D
     c[5] = 6.0 * dF - 3.0 * D0 - 3.0 * D1 - 0.5 * S0 + 0.5 * S1;
 }
 
+// target: knot spacing in A^2 (0.04 for the FP64 tables, 0.12 for FP32).
 inline RglTables build_rgl_tables(double A, double xi, double p, double q, double r0, double rs,
-                                  double rc) {
+                                  double rc, double target = 0.04) {
     RglTables T;
     const double r02 = r0 * r0;
     const double u_rs = rs * rs - r02, u_rc = rc * rc - r02, u_min = -0.75 * r02;
-    const double target = 0.04;
     const int nAp = std::max(1, (int)std::ceil(u_rs / target));            // knots 0..u_rs
     const double hA = u_rs / nAp;
     const int nA0 = (int)std::ceil(-u_min / hA);                           // below u = 0
