@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--config", default="rgl1m", choices=sorted(CONFIGS))
     ap.add_argument("--form", default="fp64", choices=["fp64", "fp32pair"])
+    ap.add_argument("--pair", default="table", choices=["table", "analytic"],
+                    help="RGL pair functions: quintic tables (default) or exponentials")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--exec", default="graph", choices=["graph", "chunked"],
                     help="graph: one CUDA graph with a WHILE node per relaxation (default); "
@@ -177,6 +179,7 @@ def run_gpu(args):
 
     cfg = CONFIGS[args.config]()
     pot, mass, dt, ftol = potential_for(args.config, args.form)
+    pot.pair_eval = fg.FIRE_PAIR_ANALYTIC if args.pair == "analytic" else fg.FIRE_PAIR_TABLE
     n = cfg.n
     dev = torch.device("cuda", local)
     x0 = torch.tensor(cfg.x, dtype=torch.float64, device=dev)
@@ -244,7 +247,7 @@ def run_gpu(args):
            "config": {"workload": f"{cfg.name} ({n} atoms), FIRE2 + semi-implicit Euler to "
                                   f"max|F_i| < {ftol:g}",
                       "atoms": n, "ftol": ftol, "form": args.form, "skin": pot.skin,
-                      "exec": args.exec,
+                      "exec": args.exec, "pair_eval": args.pair,
                       "iterations_per_step": [rr["iterations"] for rr in results],
                       "final_fmax_atom": [rr["fmax_atom"] for rr in results],
                       "final_energy_per_atom": [rr["energy"] / n for rr in results],

@@ -213,7 +213,7 @@ void launch_forces(fire_handle* h, const GeoC& g, cudaStream_t s) {
         k_density32_tab<<<h->nb_tab_d, kTabBlock, h->smem_d, s>>>(h->b, h->potc, g);
         k_force32_tab<<<h->nb_tab_f, kTabBlock, h->smem_f, s>>>(h->b, h->potc, g);
     } else if (tab) {
-        k_density_tab<<<h->nb_tab_d, kForceBlock, h->smem_d, s>>>(h->b, h->potc, g);
+        k_density_tab<<<h->nb_tab_d, kTabBlock64, h->smem_d, s>>>(h->b, h->potc, g);
         k_embed<<<h->b.nb_embed, kElemBlock, 0, s>>>(h->b);
         k_force_rgl<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, g);
     } else if (h->pot.kind == FIRE_POT_RGL && h->pot.precision == FIRE_PREC_FP32_PAIR) {
@@ -586,7 +586,7 @@ static fire_status upload_tables(fire_handle* h) {
     // FP64: one kernel holds both tables; FP32: one table per kernel
     h->smem_d = f32 ? nd32 * sizeof(float) : (nd + nf) * sizeof(double);
     h->smem_f = f32 ? nf32 * sizeof(float) : 0;
-    const int block = f32 ? kTabBlock : kForceBlock;
+    const int block = f32 ? kTabBlock : kTabBlock64;
     const void* kd = f32 ? (const void*)k_density32_tab : (const void*)k_density_tab;
     CK(h, cudaFuncSetAttribute(kd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->smem_d));
     int sms = 0, occ_d = 0, occ_f = 1;
@@ -1296,7 +1296,7 @@ fire_status fire_profile_stages(fire_handle_t* h, const double* pos, const doubl
         cudaEventRecord(ev[1], s);
         const bool tab = rgl && h->pot.pair_eval == FIRE_PAIR_TABLE;
         if (tab && f32) k_density32_tab<<<h->nb_tab_d, kTabBlock, h->smem_d, s>>>(h->b, h->potc, g);
-        else if (tab) k_density_tab<<<h->nb_tab_d, kForceBlock, h->smem_d, s>>>(h->b, h->potc, g);
+        else if (tab) k_density_tab<<<h->nb_tab_d, kTabBlock64, h->smem_d, s>>>(h->b, h->potc, g);
         else if (rgl && f32) k_density32<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
         else if (rgl) k_density<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
         cudaEventRecord(ev[2], s);

@@ -24,6 +24,7 @@ constexpr uint32_t kIdxMask = (1u << kIdxBits) - 1u;
 constexpr int kCodeZero = 62;  // image code of the zero shift, (2 + 5*2 + 25*2)
 constexpr int kForceBlock = 128;
 constexpr int kTabBlock = 256;    // FP32 table kernels (more warps per shared table copy)
+constexpr int kTabBlock64 = 512;  // FP64 table kernel (both tables, ~112 KB, in shared memory)
 constexpr int kElemBlock = 256;
 constexpr int kCtlThreads = 512;
 

@@ -553,7 +553,7 @@ __device__ __forceinline__ void load_table(T* dst, const T* src, int count) {
 
 // FP64 pass 1 (half list): rho_i, rho_j (atomics), 2 phi per pair, and the
 // pair cache of pass 2 (2 phi'/r = 4 phi_u, g'/r = 2 g_u) from the tables.
-__global__ void __launch_bounds__(kForceBlock) k_density_tab(Bufs b, PotC P, GeoC g) {
+__global__ void __launch_bounds__(kTabBlock64) k_density_tab(Bufs b, PotC P, GeoC g) {
     extern __shared__ double tabs[];   // density table, then force table
     __shared__ double3 tbl[125];
     __shared__ double etab[kExpTableSize];
