@@ -127,3 +127,35 @@ def rgl_batch(n_sys: int = 512, seed: int = 4, nmin: int = 3, nmax: int = 12,
 
 def perfect_fcc(ncell: int, a: float) -> Config:
     return Config(f"fcc{ncell}", fcc_sites(ncell, ncell, ncell, a), np.full(3, ncell * a))
+
+
+def neb_vacancy_hop(ncell: int = 3, seed: int = 6, n_img: int = 5, sigma: float = 0.0,
+                    a: float = CU_A) -> Config:
+    """End states and straight-line initial path of a nearest-neighbour
+    vacancy hop in a periodic Cu FCC box (the NEB workload): site v is
+    vacant in state 0; in state 1 the atom of the neighbouring site w has
+    moved into v.  Atom order is the same in both states (the hopping atom
+    keeps its index).  x holds the (n_img + 2, n, 3) path, images 0 and
+    n_img + 1 the (unrelaxed) end states; sigma adds the same seeded
+    Gaussian noise to every image."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    sites = fcc_sites(ncell, ncell, ncell, a)
+    box = np.full(3, ncell * a)
+    v = int(rng.integers(len(sites)))
+    d = sites - sites[v]
+    d -= box * np.rint(d / box)
+    r = np.sqrt(np.sum(d * d, axis=1))
+    nn = np.flatnonzero(np.abs(r - a / np.sqrt(2.0)) < 1e-6)
+    w = int(nn[rng.integers(len(nn))])
+    keep = np.ones(len(sites), bool)
+    keep[v] = False
+    end0 = sites[keep].copy()
+    k = int(np.flatnonzero(np.flatnonzero(keep) == w)[0])   # index of the hopping atom
+    end1 = end0.copy()
+    end1[k] = end0[k] - d[w]          # w -> v along the minimum-image bond
+    noise = rng.normal(0.0, sigma, size=end0.shape) if sigma > 0 else np.zeros_like(end0)
+    t = np.linspace(0.0, 1.0, n_img + 2)[:, None, None]
+    path = end0[None] + t * (end1 - end0)[None] + noise[None]
+    return Config(f"neb_cu{ncell}_hop", path, box,
+                  meta=dict(vacancy_site=sites[v], target_site=sites[w], hopper=k, ncell=ncell,
+                            n_img=n_img))

@@ -27,7 +27,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "fire_oracle.c")
 _LIB = os.path.join(_HERE, "_build", "libfire_oracle.so")
 
-POT_LJ, POT_RGL, POT_QUAD = 0, 1, 2
+POT_LJ, POT_RGL, POT_QUAD, POT_DWELL = 0, 1, 2, 3
 FORCE_BRUTE, FORCE_CELLS = 0, 1
 STOP_FTOL, STOP_MAXITER, STOP_MAXVDOTF = 0, 1, 2
 NORM_MAX_ATOM, NORM_TWO, NORM_INF = 0, 1, 2
@@ -45,7 +45,8 @@ class _Pot(C.Structure):
                 ("eps", C.c_double), ("sigma", C.c_double), ("rc_lj", C.c_double),
                 ("A", C.c_double), ("xi", C.c_double), ("p", C.c_double), ("q", C.c_double),
                 ("r0", C.c_double), ("rs", C.c_double), ("rc", C.c_double),
-                ("quad_k", C.POINTER(C.c_double)), ("quad_x0", C.POINTER(C.c_double))]
+                ("quad_k", C.POINTER(C.c_double)), ("quad_x0", C.POINTER(C.c_double)),
+                ("dwell", C.POINTER(C.c_double))]
 
 
 class _Params(C.Structure):
@@ -54,7 +55,7 @@ class _Params(C.Structure):
                 ("alphashrink", C.c_double), ("delaystep", C.c_int32), ("vdfmax", C.c_int32),
                 ("halfstepback", C.c_int32), ("initialdelay", C.c_int32),
                 ("integrator", C.c_int32), ("norm", C.c_int32), ("variant", C.c_int32),
-                ("pad", C.c_int32)]
+                ("pad", C.c_int32), ("dmax", C.c_double), ("frozen", C.c_void_p)]
 
 
 class _Result(C.Structure):
@@ -98,6 +99,10 @@ def _load():
                                                  C.POINTER(C.c_double), C.c_int]
         lib.ora_densities.restype = C.c_int
         lib.ora_densities.argtypes = [C.POINTER(_Sys), C.POINTER(_Pot), C.c_void_p, C.c_void_p]
+        lib.ora_neb.restype = C.c_int
+        lib.ora_neb.argtypes = [C.POINTER(_Sys), C.POINTER(_Pot), C.POINTER(_Params), C.c_int64,
+                                C.c_void_p, C.c_double, C.c_int, C.c_double, C.c_int64, C.c_int,
+                                C.POINTER(_Result), C.c_void_p, C.POINTER(C.c_int64)]
         lib.ora_fire2.restype = C.c_int
         lib.ora_fire2.argtypes = [C.POINTER(_Sys), C.POINTER(_Pot), C.POINTER(_Params), C.c_void_p,
                                   C.c_double, C.c_int64, C.c_int, C.POINTER(_Result),
@@ -129,7 +134,8 @@ def max_threads() -> int:
 
 @dataclass
 class Potential:
-    """Potential description.  kind: 'lj', 'rgl' or 'quad' (test well)."""
+    """Potential description.  kind: 'lj', 'rgl', 'quad' (test well) or 'dwell'
+    (double-well test surface, dwell = (h, a, c, ky, kz))."""
     kind: str
     eps: float = 1.0
     sigma: float = 1.0
@@ -143,6 +149,7 @@ class Potential:
     rc: float = 0.0
     quad_k: np.ndarray | None = None
     quad_x0: np.ndarray | None = None
+    dwell: tuple | None = None
 
 
 @dataclass
@@ -163,6 +170,7 @@ class Params:
     norm: int = NORM_MAX_ATOM
     variant: int = 0
     pad: int = 0
+    dmax: float = 0.0
 
 
 @dataclass
@@ -189,7 +197,7 @@ def _sys(n, box, periodic, mass):
 
 
 def _pot(pot: Potential, keep: list):
-    kinds = {"lj": POT_LJ, "rgl": POT_RGL, "quad": POT_QUAD}
+    kinds = {"lj": POT_LJ, "rgl": POT_RGL, "quad": POT_QUAD, "dwell": POT_DWELL}
     p = _Pot()
     p.kind = kinds[pot.kind]
     for name in ("eps", "sigma", "rc_lj", "A", "xi", "p", "q", "r0", "rs", "rc"):
@@ -200,6 +208,11 @@ def _pot(pot: Potential, keep: list):
         keep += [k, x0]
         p.quad_k = k.ctypes.data_as(C.POINTER(C.c_double))
         p.quad_x0 = x0.ctypes.data_as(C.POINTER(C.c_double))
+    if pot.kind == "dwell":
+        dw = np.ascontiguousarray(pot.dwell, dtype=np.float64)
+        assert dw.shape == (5,)
+        keep.append(dw)
+        p.dwell = dw.ctypes.data_as(C.POINTER(C.c_double))
     return p
 
 
@@ -304,15 +317,24 @@ def implicit_grad(x_star, box, pot: Potential, g, tol=1e-12, maxit=10000, period
 
 
 def fire2(x, box, pot: Potential, params: Params, mass: float, ftol: float, maxiter: int,
-          periodic=(1, 1, 1), mode: int = FORCE_BRUTE, trace: int = 0):
-    """Relaxes x (copied) with FIRE 2.0; returns (x_final, Result, trace_rows)."""
+          periodic=(1, 1, 1), mode: int = FORCE_BRUTE, trace: int = 0, frozen=None):
+    """Relaxes x (copied) with FIRE 2.0; returns (x_final, Result, trace_rows).
+    frozen: None or one uint8 per atom, bit d set = component d frozen."""
     x = np.array(x, dtype=np.float64).reshape(-1, 3)
     keep: list = []
     s, p = _sys(len(x), box, periodic, mass), _pot(pot, keep)
     pr = _Params()
     for name, _ in _Params._fields_:
+        if name == "frozen":
+            continue
         setattr(pr, name, int(getattr(params, name)) if isinstance(getattr(pr, name), int)
                 else float(getattr(params, name)))
+    if frozen is not None:
+        fz = np.ascontiguousarray(frozen, dtype=np.uint8)
+        if fz.shape != (len(x),):
+            raise ValueError("frozen must hold one byte per atom")
+        keep.append(fz)
+        pr.frozen = fz.ctypes.data
     res = _Result()
     tr = (_Trace * max(int(trace), 1))()
     _check(_load().ora_fire2(C.byref(s), C.byref(p), C.byref(pr), x.ctypes.data, float(ftol),
@@ -323,3 +345,37 @@ def fire2(x, box, pot: Potential, params: Params, mass: float, ftol: float, maxi
     rows = [dict(i=t.i, npos=t.npos, nneg=t.nneg, P=t.P, dt=t.dt, alpha=t.alpha,
                  energy=t.energy, fnorm=t.fnorm) for t in tr[:min(int(trace), r.iterations)]]
     return x, r, rows
+
+
+def neb(path, box, pot: Potential, params: Params, mass: float, k_spring: float, climb: bool,
+        ftol: float, maxiter: int, periodic=(1, 1, 1), mode: int = FORCE_BRUTE, frozen=None):
+    """Nudged elastic band relaxed with FIRE: path is (m + 2, n, 3) with the
+    fixed end states first and last.  Returns (path_out, Result, energies
+    (m + 2), climbing-image index or 0)."""
+    path = np.array(path, dtype=np.float64)
+    if path.ndim != 3 or path.shape[2] != 3 or path.shape[0] < 3:
+        raise ValueError("path must be (m + 2, n, 3) with m >= 1")
+    m, n = path.shape[0] - 2, path.shape[1]
+    keep: list = []
+    s, p = _sys(n, box, periodic, mass), _pot(pot, keep)
+    pr = _Params()
+    for name, _ in _Params._fields_:
+        if name == "frozen":
+            continue
+        setattr(pr, name, int(getattr(params, name)) if isinstance(getattr(pr, name), int)
+                else float(getattr(params, name)))
+    if frozen is not None:
+        fz = np.ascontiguousarray(frozen, dtype=np.uint8)
+        if fz.shape != (n,):
+            raise ValueError("frozen must hold one byte per atom of an image")
+        keep.append(fz)
+        pr.frozen = fz.ctypes.data
+    res = _Result()
+    energies = np.zeros(m + 2)
+    climber = C.c_int64(0)
+    _check(_load().ora_neb(C.byref(s), C.byref(p), C.byref(pr), int(m), path.ctypes.data,
+                           float(k_spring), int(bool(climb)), float(ftol), int(maxiter), int(mode),
+                           C.byref(res), energies.ctypes.data, C.byref(climber)), "neb")
+    r = Result(res.energy, res.iterations, res.force_evals, res.stop, res.fmax_atom, res.f2norm,
+               res.finf, res.dt_final, res.alpha_final)
+    return path, r, energies, int(climber.value)

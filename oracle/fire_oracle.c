@@ -66,7 +66,7 @@
 #include <omp.h>
 #endif
 
-enum { POT_LJ = 0, POT_RGL = 1, POT_QUAD = 2 };
+enum { POT_LJ = 0, POT_RGL = 1, POT_QUAD = 2, POT_DWELL = 3 };
 enum { FORCE_BRUTE = 0, FORCE_CELLS = 1 };
 enum { STOP_FTOL = 0, STOP_MAXITER = 1, STOP_MAXVDOTF = 2 };
 enum { NORM_MAX_ATOM = 0, NORM_TWO = 1, NORM_INF = 2 };
@@ -88,12 +88,25 @@ typedef struct {
     double A, xi, p, q, r0, rs, rc;
     /* quadratic test well E = 1/2 sum_d k_d (x_d - x0_d)^2 (control-flow tests) */
     const double *quad_k, *quad_x0;
+    /* double-well test surface per atom (NEB tests), dwell = {h, a, c, ky, kz}:
+     * E = h ((x/a)^2 - 1)^2 + ky (y - c x^2)^2 + kz z^2; minima (+-a, c a^2, 0)
+     * with E = 0, first-order saddle (0, 0, 0) with E = h. */
+    const double *dwell;
 } ora_pot;
 
 typedef struct {
     double dt_start, tmax, tmin, dtgrow, dtshrink, alpha0, alphashrink;
     int32_t delaystep, vdfmax, halfstepback, initialdelay, integrator, norm;
     int32_t variant, pad;   /* VAR_FIRE2 (Algorithm 2) or VAR_FIRE1 (Algorithm 1) */
+    /* Maximum displacement of any atom per step (the paper's dmax, Sec. 4
+     * cases 1 and 7); 0 = no cap.  The drift x += dt v of the step then uses
+     * dt_eff = min(dt, dmax / max_i |v_i|); the FIRE dt is unchanged. */
+    double dmax;
+    /* Frozen degrees of freedom (Sec. 4 cases 1 and 7: borders frozen in x
+     * and y): NULL, or one byte per atom with bit d set = component d
+     * frozen.  Frozen force components are set to zero after every force
+     * evaluation, so they enter neither P, the norms nor the motion. */
+    const uint8_t *frozen;
 } ora_params;
 
 typedef struct {
@@ -271,7 +284,7 @@ static int64_t grid_max_candidates(const ora_grid *g) {
 
 static int check_box(const ora_sys *sys, const ora_pot *pot) {
     if (sys->n < 0) return -1;
-    if (pot->kind == POT_QUAD) return 0;
+    if (pot->kind == POT_QUAD || pot->kind == POT_DWELL) return 0;
     double rc = pot_cutoff(pot);
     for (int d = 0; d < 3; ++d)
         if (sys->periodic[d] && sys->box[d] < 2.0 * rc) return -2;
@@ -292,6 +305,23 @@ static int energy_forces_impl(const ora_sys *sys, const ora_pot *pot, const doub
             double d = x[k] - pot->quad_x0[k];
             e += 0.5 * pot->quad_k[k] * d * d;
             if (f) f[k] = -pot->quad_k[k] * d;
+        }
+        *energy = e;
+        return 0;
+    }
+    if (pot->kind == POT_DWELL) {
+        const double h = pot->dwell[0], a = pot->dwell[1], c = pot->dwell[2];
+        const double ky = pot->dwell[3], kz = pot->dwell[4];
+        double e = 0.0;
+        for (int64_t i = 0; i < n; ++i) {
+            const double X = x[3 * i], Y = x[3 * i + 1], Z = x[3 * i + 2];
+            const double w = X * X / (a * a) - 1.0, y = Y - c * X * X;
+            e += h * w * w + ky * y * y + kz * Z * Z;
+            if (f) {
+                f[3 * i] = -(4.0 * h * w * X / (a * a) - 4.0 * ky * c * X * y);
+                f[3 * i + 1] = -2.0 * ky * y;
+                f[3 * i + 2] = -2.0 * kz * Z;
+            }
         }
         *energy = e;
         return 0;
@@ -784,6 +814,31 @@ static double dot3n(const double *a, const double *b, int64_t n3) {
 /* FIRE 2.0 (Algorithm 2) or FIRE (Algorithm 1), with the integrators of      */
 /* Algorithms 3-6.                                                            */
 
+/* Zero the frozen force components (see ora_params.frozen). */
+static void apply_frozen(double *f, int64_t n, const uint8_t *frozen) {
+    if (!frozen) return;
+    for (int64_t i = 0; i < n; ++i)
+        for (int d = 0; d < 3; ++d)
+            if (frozen[i] & (1u << d)) f[3 * i + d] = 0.0;
+}
+
+/* x += dt_eff v with dt_eff = dt, or dmax / max_i |v_i| when that is smaller
+ * (see ora_params.dmax). */
+static void drift(double *x, const double *v, int64_t n, double dt, double dmax) {
+    double dt_eff = dt;
+    if (dmax > 0.0) {
+        double vmax2 = 0.0;
+        for (int64_t i = 0; i < n; ++i) {
+            double a2 = v[3 * i] * v[3 * i] + v[3 * i + 1] * v[3 * i + 1] +
+                        v[3 * i + 2] * v[3 * i + 2];
+            if (a2 > vmax2) vmax2 = a2;
+        }
+        double vmax = sqrt(vmax2);
+        if (dt * vmax > dmax) dt_eff = dmax / vmax;
+    }
+    for (int64_t k = 0; k < 3 * n; ++k) x[k] += dt_eff * v[k];
+}
+
 /* v = (1 - alpha) v + alpha |v| F / |F| (the mixing of Algs. 1 and 3-6). */
 static void mix_velocity(double *v, const double *f, int64_t n3, double alpha) {
     double vn = sqrt(dot3n(v, v, n3)), fn = sqrt(dot3n(f, f, n3));
@@ -791,18 +846,54 @@ static void mix_velocity(double *v, const double *f, int64_t n3, double alpha) {
         for (int64_t k = 0; k < n3; ++k) v[k] = (1.0 - alpha) * v[k] + alpha * vn * f[k] / fn;
 }
 
+/* The force of the system being relaxed: E and F at x (3 n values); returns
+ * 0 or an error code.  Plain relaxations evaluate the potential (with the
+ * frozen components zeroed); the nudged elastic band evaluates every image
+ * and projects. */
+typedef int (*ora_force_fn)(void *ctx, const double *x, double *f, double *E);
+
+typedef struct {
+    const ora_sys *sys;
+    const ora_pot *pot;
+    const uint8_t *frozen;
+    int mode;
+} plain_ctx;
+
+static int plain_force(void *ctx, const double *x, double *f, double *E) {
+    plain_ctx *c = (plain_ctx *)ctx;
+    int rc_ok = ora_energy_forces(c->sys, c->pot, x, f, E, c->mode);
+    if (rc_ok == 0) apply_frozen(f, c->sys->n, c->frozen);
+    return rc_ok;
+}
+
+static int fire_loop(int64_t n, double m, ora_force_fn force, void *ctx, const ora_params *par,
+                     double *x, double ftol, int64_t maxiter, ora_result *out,
+                     ora_trace *trace, int64_t trace_cap);
+
 int ora_fire2(const ora_sys *sys, const ora_pot *pot, const ora_params *par, double *x,
               double ftol, int64_t maxiter, int mode, ora_result *out,
               ora_trace *trace, int64_t trace_cap) {
+    plain_ctx c = {sys, pot, par->frozen, mode};
+    int rc_ok = check_box(sys, pot);
+    if (rc_ok) return rc_ok;
+    return fire_loop(sys->n, sys->mass, plain_force, &c, par, x, ftol, maxiter, out, trace,
+                     trace_cap);
+}
+
+/* FIRE 2.0 (Algorithm 2) or FIRE (Algorithm 1) on n atoms of mass m under
+ * `force`, with the integrators of Algorithms 3-6. */
+static int fire_loop(int64_t n, double m, ora_force_fn force, void *ctx, const ora_params *par,
+                     double *x, double ftol, int64_t maxiter, ora_result *out,
+                     ora_trace *trace, int64_t trace_cap) {
     if (par->integrator < INT_EULER_IMPLICIT || par->integrator > INT_LEAPFROG) return -3;
     if (par->variant != VAR_FIRE2 && par->variant != VAR_FIRE1) return -3;
-    if (maxiter < 0 || !(ftol >= 0.0) || !(par->dt_start > 0.0) || !(sys->mass > 0.0)) return -1;
-    const int64_t n = sys->n, n3 = 3 * n;
-    const double m = sys->mass;
+    if (maxiter < 0 || !(ftol >= 0.0) || !(par->dt_start > 0.0) || !(m > 0.0)) return -1;
+    if (!(par->dmax >= 0.0)) return -1;
+    const int64_t n3 = 3 * n;
     double *v = (double *)calloc((size_t)(n3 > 0 ? n3 : 1), sizeof(double));
     double *f = (double *)calloc((size_t)(n3 > 0 ? n3 : 1), sizeof(double));
     double E = 0.0;
-    int rc_ok = ora_energy_forces(sys, pot, x, f, &E, mode);
+    int rc_ok = force(ctx, x, f, &E);
     if (rc_ok) { free(v); free(f); return rc_ok; }
 
     /* initialisation: v = 0, alpha = alpha_start, dt = dt_start, counters 0 */
@@ -864,22 +955,22 @@ int ora_fire2(const ora_sys *sys, const ora_pot *pot, const ora_params *par, dou
             if (par->integrator == INT_EULER_EXPLICIT) {
                 /* Algorithm 3: mix v(t), x += dt v(t), v += dt F(x(t)) / m */
                 if (mix_in_integrator) mix_velocity(v, f, n3, alpha);
-                for (int64_t k = 0; k < n3; ++k) x[k] += dt * v[k];
+                drift(x, v, n, dt, par->dmax);
                 for (int64_t k = 0; k < n3; ++k) v[k] += dt * f[k] / m;
-                rc_ok = ora_energy_forces(sys, pot, x, f, &E, mode);
+                rc_ok = force(ctx, x, f, &E);
             } else if (par->integrator == INT_VERLET) {
                 /* Algorithm 6: half kick, mix, drift, new force, half kick */
                 for (int64_t k = 0; k < n3; ++k) v[k] += 0.5 * dt * f[k] / m;
                 if (mix_in_integrator) mix_velocity(v, f, n3, alpha);
-                for (int64_t k = 0; k < n3; ++k) x[k] += dt * v[k];
-                rc_ok = ora_energy_forces(sys, pot, x, f, &E, mode);
+                drift(x, v, n, dt, par->dmax);
+                rc_ok = force(ctx, x, f, &E);
                 for (int64_t k = 0; k < n3; ++k) v[k] += 0.5 * dt * f[k] / m;
             } else {
                 /* Algorithms 4 and 5: kick, mix (of the kicked v), drift, new force */
                 for (int64_t k = 0; k < n3; ++k) v[k] += dt * f[k] / m;
                 if (mix_in_integrator) mix_velocity(v, f, n3, alpha);
-                for (int64_t k = 0; k < n3; ++k) x[k] += dt * v[k];
-                rc_ok = ora_energy_forces(sys, pot, x, f, &E, mode);
+                drift(x, v, n, dt, par->dmax);
+                rc_ok = force(ctx, x, f, &E);
             }
             if (rc_ok) { free(v); free(f); return rc_ok; }
             evals += 1;
@@ -924,4 +1015,157 @@ int ora_max_threads(void) {
 #else
     return 1;
 #endif
+}
+
+/* ------------------------------------------------------------------------ */
+/* Nudged elastic band.  The paper's cases 7 and 8 relax, with FIRE 2.0, an   */
+/* ensemble of images between two fixed end states under modified forces     */
+/* (Sec. 4); it states no formulas and cites Sheppard et al. (2008), whose    */
+/* standard method is written out here:                                      */
+/*   tangent t_i (improved estimate of Henkelman and Jonsson, 2000) from the  */
+/*   neighbour separations t+ = R_{i+1} - R_i, t- = R_i - R_{i-1} (minimum    */
+/*   image) and the energies: t+ if E_{i+1} > E_i > E_{i-1}, t- if            */
+/*   E_{i+1} < E_i < E_{i-1}, else dEmax t+ + dEmin t- (E_{i+1} > E_{i-1}) or */
+/*   dEmin t+ + dEmax t- with dEmax/min = max/min(|E_{i+1}-E_i|,              */
+/*   |E_{i-1}-E_i|); normalised;                                             */
+/*   F_i^NEB = F_i - (F_i.t) t + k (|t+| - |t-|) t, or, for the climbing      */
+/*   image (the movable image of highest energy, when enabled),               */
+/*   F_i - 2 (F_i.t) t.                                                       */
+/* The m movable images form one system of m n atoms for FIRE: one dt, one    */
+/* alpha and one P over the whole band, and the stopping norm is taken over   */
+/* all images -- a simultaneous minimisation of the ensemble.  Frozen         */
+/* components (if any) are zeroed in the true force, the tangent and the     */
+/* NEB force.  If the tangent vanishes (equal energies on both sides), t+ + t- */
+/* is used; if that vanishes too, the force is left unprojected.             */
+
+typedef struct {
+    const ora_sys *sys;
+    const ora_pot *pot;
+    const uint8_t *frozen;
+    int mode;
+    int64_t m;
+    const double *end0, *end1;
+    double e_end0, e_end1;
+    double k;
+    int climb;
+    double *E;          /* m + 2 energies */
+    int64_t climber;    /* 1..m, or 0 */
+} neb_ctx;
+
+static const double *neb_image(const neb_ctx *c, const double *x, int64_t i) {
+    if (i == 0) return c->end0;
+    if (i == c->m + 1) return c->end1;
+    return x + 3 * c->sys->n * (i - 1);
+}
+
+static int neb_force(void *ctx, const double *x, double *f, double *Etot) {
+    neb_ctx *c = (neb_ctx *)ctx;
+    const ora_sys *sys = c->sys;
+    const int64_t n = sys->n, n3 = 3 * n, M = c->m;
+    c->E[0] = c->e_end0;
+    c->E[M + 1] = c->e_end1;
+    for (int64_t i = 1; i <= M; ++i) {
+        int rc_ok = ora_energy_forces(sys, c->pot, neb_image(c, x, i), f + n3 * (i - 1), &c->E[i],
+                                      c->mode);
+        if (rc_ok) return rc_ok;
+        apply_frozen(f + n3 * (i - 1), n, c->frozen);
+    }
+    c->climber = 0;
+    if (c->climb) {
+        c->climber = 1;
+        for (int64_t i = 2; i <= M; ++i)
+            if (c->E[i] > c->E[c->climber]) c->climber = i;
+    }
+    double tot = 0.0;
+    for (int64_t i = 1; i <= M; ++i) tot += c->E[i];
+    *Etot = tot;
+    const size_t bytes = (size_t)(n3 > 0 ? n3 : 1) * sizeof(double);
+    double *tp = (double *)malloc(bytes), *tm = (double *)malloc(bytes);
+    double *t = (double *)malloc(bytes);
+    for (int64_t i = 1; i <= M; ++i) {
+        const double *R = neb_image(c, x, i), *Rp = neb_image(c, x, i + 1);
+        const double *Rm = neb_image(c, x, i - 1);
+        for (int64_t q = 0; q < n3; ++q) {
+            const int a = (int)(q % 3);
+            tp[q] = min_image(Rp[q] - R[q], sys->box[a], sys->periodic[a]);
+            tm[q] = min_image(R[q] - Rm[q], sys->box[a], sys->periodic[a]);
+        }
+        const double Ep = c->E[i + 1], Ei = c->E[i], Em = c->E[i - 1];
+        double wp, wm;
+        if (Ep > Ei && Ei > Em) {
+            wp = 1.0;
+            wm = 0.0;
+        } else if (Ep < Ei && Ei < Em) {
+            wp = 0.0;
+            wm = 1.0;
+        } else {
+            const double dmx = fmax(fabs(Ep - Ei), fabs(Em - Ei));
+            const double dmn = fmin(fabs(Ep - Ei), fabs(Em - Ei));
+            if (Ep > Em) {
+                wp = dmx;
+                wm = dmn;
+            } else {
+                wp = dmn;
+                wm = dmx;
+            }
+        }
+        for (int64_t q = 0; q < n3; ++q) t[q] = wp * tp[q] + wm * tm[q];
+        apply_frozen(t, n, c->frozen);
+        double tn = sqrt(dot3n(t, t, n3));
+        if (!(tn > 0.0)) {
+            for (int64_t q = 0; q < n3; ++q) t[q] = tp[q] + tm[q];
+            apply_frozen(t, n, c->frozen);
+            tn = sqrt(dot3n(t, t, n3));
+        }
+        double *fi = f + n3 * (i - 1);
+        if (tn > 0.0) {
+            for (int64_t q = 0; q < n3; ++q) t[q] /= tn;
+            const double ft = dot3n(fi, t, n3);
+            if (i == c->climber) {
+                for (int64_t q = 0; q < n3; ++q) fi[q] -= 2.0 * ft * t[q];
+            } else {
+                const double sp = c->k * (sqrt(dot3n(tp, tp, n3)) - sqrt(dot3n(tm, tm, n3)));
+                for (int64_t q = 0; q < n3; ++q) fi[q] += (sp - ft) * t[q];
+            }
+        }
+        apply_frozen(fi, n, c->frozen);
+    }
+    free(tp);
+    free(tm);
+    free(t);
+    return 0;
+}
+
+/* path: (m + 2) images of n atoms (x, y, z), image 0 and m + 1 the fixed end
+ * states; the m movable images are relaxed in place.  energies: m + 2
+ * values out; climber: index of the climbing image at the end (0 = none).
+ * out->energy is the sum of the movable images' energies. */
+int ora_neb(const ora_sys *sys, const ora_pot *pot, const ora_params *par, int64_t m,
+            double *path, double k, int climb, double ftol, int64_t maxiter, int mode,
+            ora_result *out, double *energies, int64_t *climber) {
+    if (m < 1 || !(k >= 0.0)) return -1;
+    int rc_ok = check_box(sys, pot);
+    if (rc_ok) return rc_ok;
+    const int64_t n3 = 3 * sys->n;
+    neb_ctx c;
+    c.sys = sys;
+    c.pot = pot;
+    c.frozen = par->frozen;
+    c.mode = mode;
+    c.m = m;
+    c.end0 = path;
+    c.end1 = path + n3 * (m + 1);
+    c.k = k;
+    c.climb = climb;
+    c.E = energies;
+    c.climber = 0;
+    double *fw = (double *)malloc((size_t)(n3 > 0 ? n3 : 1) * sizeof(double));
+    rc_ok = ora_energy_forces(sys, pot, c.end0, fw, &c.e_end0, mode);
+    if (!rc_ok) rc_ok = ora_energy_forces(sys, pot, c.end1, fw, &c.e_end1, mode);
+    free(fw);
+    if (rc_ok) return rc_ok;
+    rc_ok = fire_loop(sys->n * m, sys->mass, neb_force, &c, par, path + n3, ftol, maxiter, out,
+                      NULL, 0);
+    *climber = c.climber;
+    return rc_ok;
 }

@@ -402,3 +402,87 @@ def test_every_integrator_and_variant_relaxes_the_lj_box(integ, variant):
                                                                 variant=variant),
                               1.0, 1e-6, 100000)
     assert res.stop == oracle.STOP_FTOL and res.fmax_atom < 1e-6
+
+
+# ----------------------------------------------------------------------------
+# Maximum displacement per step (dmax) and frozen degrees of freedom (Sec. 4,
+# cases 1 and 7)
+
+def test_dmax_caps_the_drift_by_hand():
+    # E = x^2/2, m = 1, x = 1, dt = 0.1, dmax = 0.005.
+    # i=1: P = 0; v = -0.1; dt |v| = 0.01 > dmax -> dt_eff = 0.05, x = 0.995
+    # i=2: F = -0.995, P = 0.0995 > 0; v = -0.1 - 0.0995 = -0.1995;
+    #      dt |v| = 0.01995 > dmax -> x = 0.995 - 0.005 = 0.99
+    # i=3: F = -0.99; v = -0.1995 - 0.099 = -0.2985 -> x = 0.985
+    # The FIRE dt itself is untouched (still 0.1).
+    expect_x = [0.995, 0.99, 0.985]
+    for it in (1, 2, 3):
+        xf, res, rows = run_quad([1, 0, 0], [1, 0, 0], it, dmax=0.005)
+        assert xf[0] == pytest.approx(expect_x[it - 1], abs=1e-15)
+        assert res.dt_final == 0.1
+    # a cap larger than every step changes nothing, bit for bit
+    xa, ra, _ = run_quad([1, 10, 0], [1, 1, 0], 60)
+    xb, rb, _ = run_quad([1, 10, 0], [1, 1, 0], 60, dmax=10.0)
+    assert np.array_equal(xa, xb) and ra.energy == rb.energy
+
+
+def test_dmax_bounds_every_step_of_a_relaxation():
+    c = fi.rgl_vacancy_box(ncell=4, seed=31, n_vac=1, sigma=0.1)
+    prev = c.x.copy()
+    pot = oracle.Potential("rgl", **fi.RGL_CU)
+    params = oracle.Params(dt_start=fi.CU_DT, dmax=0.002)
+    # a P <= 0 pass would add the half step back, which the cap does not
+    # cover; in these iterations only the first pass has P <= 0
+    _, _, rows = oracle.fire2(c.x, c.box, pot, params, fi.CU_MASS, 0.0, 39, trace=39)
+    assert [r["i"] for r in rows if r["P"] <= 0] == [1]
+    steps = []
+    for it in range(1, 40):
+        xf, res, _ = oracle.fire2(c.x, c.box, pot, params, fi.CU_MASS, 0.0, it)
+        steps.append(np.linalg.norm(xf - prev, axis=1).max())
+        prev = xf
+    assert max(steps) <= 0.002 * (1 + 1e-12)
+    assert min(steps[5:]) > 0.002 * (1 - 1e-12)    # the cap is active
+
+
+def test_frozen_component_reduces_to_the_lower_dimensional_well():
+    # E = (x^2 + 10 y^2 + 3 z^2)/2 with z frozen at 0.7 follows exactly the
+    # trajectory of E = (x^2 + 10 y^2)/2 in (x, y): the frozen component
+    # has zero force, stays put and adds nothing to P, |F| or |v|.
+    x3 = np.array([[1.0, 1.0, 0.7]])
+    x2 = np.array([[1.0, 1.0, 0.0]])
+    params = oracle.Params(dt_start=0.1)
+    a, ra, _ = oracle.fire2(x3, [100.0] * 3, quad([1, 10, 3], [0, 0, 0]), params, 1.0, 1e-10,
+                            5000, periodic=(0, 0, 0), frozen=np.array([4], np.uint8))
+    b, rb, _ = oracle.fire2(x2, [100.0] * 3, quad([1, 10, 0], [0, 0, 0]), params, 1.0, 1e-10,
+                            5000, periodic=(0, 0, 0))
+    assert a[0, 2] == 0.7
+    assert np.array_equal(a[0, :2], b[0, :2])
+    assert ra.iterations == rb.iterations and ra.stop == rb.stop == oracle.STOP_FTOL
+    # the reported norms are those of the masked force
+    assert ra.fmax_atom == rb.fmax_atom
+
+
+def test_all_frozen_takes_zero_iterations():
+    c = fi.lj_fcc_vacancy(seed=1)
+    xf, res, _ = oracle.fire2(c.x, c.box, lj(), oracle.Params(dt_start=fi.LJ_DT), 1.0, 1e-8, 100,
+                              frozen=np.full(c.n, 7, np.uint8))
+    assert res.iterations == 0 and res.stop == oracle.STOP_FTOL and np.array_equal(xf, c.x)
+
+
+def test_frozen_slab_stays_put_and_the_rest_relaxes():
+    c = fi.rgl_vacancy_box(ncell=4, seed=32, n_vac=1, sigma=0.05)
+    fz = np.zeros(c.n, np.uint8)
+    fz[c.x[:, 0] < 3.0] = 3            # frozen in x and y, free in z
+    pot = oracle.Potential("rgl", **fi.RGL_CU)
+    xf, res, _ = oracle.fire2(c.x, c.box, pot, oracle.Params(dt_start=fi.CU_DT), fi.CU_MASS, 1e-6,
+                              100000, frozen=fz)
+    assert res.stop == oracle.STOP_FTOL
+    sel = fz == 3
+    assert np.array_equal(xf[sel, :2], c.x[sel, :2])
+    assert not np.array_equal(xf[sel, 2], c.x[sel, 2])
+    # the masked force is converged; the frozen components still carry force
+    e, f = oracle.energy_forces(xf, c.box, pot)
+    fm = f.copy()
+    fm[sel, :2] = 0.0
+    assert np.linalg.norm(fm, axis=1).max() < 1e-6
+    assert np.abs(f[sel, :2]).max() > 1e-4
