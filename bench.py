@@ -40,10 +40,27 @@ CONFIGS = {
     "rgl32k": lambda: fi.rgl_vacancy_box(ncell=20, seed=2),
     "lj256": lambda: fi.lj_fcc_vacancy(seed=1),
 }
-# Algorithmic FP64 operations per pair inside the cut-off, counted from the
-# formulas (transcendentals count as one operation each): density pass = 32,
-# force pass = 18, LJ force pass = 24.
-ALG_FLOP_PER_PAIR = {"density": 32, "force": 18, "force_lj": 24}
+# Algorithmic floating-point operations per pair inside the cut-off (an FMA
+# counts 2, a transcendental 1), counted from the formulas each pass
+# evaluates:
+#   density (exponentials)     32   k_density, k_density32 (FP32)
+#   density_tab (quintic tables, phi, g, phi_u, g_u: 4 x 5 FMA + 18) 58
+#   force (cached 2 phi'/r, g'/r, both atoms)                       18
+#   force32 (exponentials, one atom of the pair, full list)         30
+#   force_lj                   24
+ALG_FLOP_PER_PAIR = {"density": 32, "density_tab": 58, "force": 18, "force32": 30,
+                     "force_lj": 24}
+# the kernel each stage runs, per (form, pair evaluation)
+STAGE_KERNELS = {
+    ("fp64", "table"): {"density": ("k_density_tab", "density_tab"),
+                        "force": ("k_force_rgl", "force")},
+    ("fp64", "analytic"): {"density": ("k_density", "density"),
+                           "force": ("k_force_rgl", "force")},
+    ("fp32pair", "analytic"): {"density": ("k_density32", "density"),
+                               "force": ("k_force32", "force32")},
+    ("fp32pair", "table"): {"density": ("k_density32_tab", "density_tab"),
+                            "force": ("k_force32_tab", "force")},
+}
 # Algorithmic HBM bytes per atom and iteration (x, v read+write, F'(rho)
 # write+read): 112 for RGL, 96 for LJ.
 ALG_BYTES_PER_ATOM_ITER = {"rgl": 112, "lj": 96}
@@ -57,8 +74,11 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--config", default="rgl1m", choices=sorted(CONFIGS))
     ap.add_argument("--form", default="fp64", choices=["fp64", "fp32pair"])
-    ap.add_argument("--pair", default="table", choices=["table", "analytic"],
-                    help="RGL pair functions: quintic tables (default) or exponentials")
+    ap.add_argument("--pair", default=None, choices=["table", "analytic"],
+                    help="RGL pair functions: quintic tables or exponentials (default: "
+                         "tables for fp64, exponentials for fp32pair, the faster of each)")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the second form (FP32-pair next to FP64 and vice versa)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--exec", default="graph", choices=["graph", "chunked"],
                     help="graph: one CUDA graph with a WHILE node per relaxation (default); "
@@ -164,6 +184,68 @@ def read_traffic(kernel):
     return None
 
 
+def default_pair(form):
+    return "analytic" if form == "fp32pair" else "table"
+
+
+def relax_form(fg, torch, cfg, form, pair, args, dev, stream, clocks=True):
+    """Times args.steps relaxations of cfg (after args.warmup untimed ones) in
+    one form; returns the measurement, the handle (still open) and the
+    relaxed positions of the last step."""
+    pot, mass, dt, ftol = potential_for(args.config, form)
+    pot.pair_eval = fg.FIRE_PAIR_ANALYTIC if pair == "analytic" else fg.FIRE_PAIR_TABLE
+    x0 = torch.tensor(cfg.x, dtype=torch.float64, device=dev)
+    work = torch.empty_like(x0)
+    h = fg.FireHandle(cfg.n, mass, pot, dt_start=dt)
+    if args.exec == "chunked":
+        h.set_exec_mode(fg.FIRE_EXEC_CHUNKED, 32)
+
+    def step():
+        work.copy_(x0)
+        return h.minimize_dev(work, cfg.box, ftol, MAXITER, stream)
+
+    for _ in range(args.warmup):
+        step()
+    results = []
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with (ClockSampler(dev.index) if clocks else _NoClock()) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            results.append(step().as_dict())
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    return {"ms": ev0.elapsed_time(ev1), "results": results, "clocks": clk.summary(),
+            "pot": pot, "ftol": ftol}, h, work
+
+
+class _NoClock:
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        pass
+
+    def summary(self):
+        return None
+
+
+def launches_of(results, is_rgl, fp32, cell_mode):
+    """Kernels one relaxation launches: prepare, list build, forces, reduce,
+    control, finalize once; per iteration update, forces, reduce (FP64 forms:
+    the FP32-pair force pass fuses it), control; the build chain (binning +
+    list) once per rebuild."""
+    build_k = 6 if cell_mode else 1
+    force_k = (2 if fp32 else 3) if is_rgl else 1
+    reduce_k = 0 if fp32 else 1
+    total = 0
+    for rr in results:
+        total += (1 + build_k + force_k + reduce_k + 1 + 1)
+        total += (1 + force_k + reduce_k + 1) * rr["iterations"]
+        total += build_k * max(0, rr["nbr_builds"] - 1)
+    return total
+
+
 def run_gpu(args):
     import torch
 
@@ -178,17 +260,16 @@ def run_gpu(args):
     fg.load_library()
 
     cfg = CONFIGS[args.config]()
-    pot, mass, dt, ftol = potential_for(args.config, args.form)
-    pot.pair_eval = fg.FIRE_PAIR_ANALYTIC if args.pair == "analytic" else fg.FIRE_PAIR_TABLE
     n = cfg.n
     dev = torch.device("cuda", local)
-    x0 = torch.tensor(cfg.x, dtype=torch.float64, device=dev)
-    work = torch.empty_like(x0)
     stream = torch.cuda.current_stream()
-    h = fg.FireHandle(n, mass, pot, dt_start=dt)
-    if args.exec == "chunked":
-        h.set_exec_mode(fg.FIRE_EXEC_CHUNKED, 32)
+    pair = args.pair or default_pair(args.form)
+    fp32 = args.form == "fp32pair"
+    is_rgl = not args.config.startswith("lj")
     if args.eval_only:
+        pot, mass, dt, _ = potential_for(args.config, args.form)
+        pot.pair_eval = fg.FIRE_PAIR_ANALYTIC if pair == "analytic" else fg.FIRE_PAIR_TABLE
+        h = fg.FireHandle(n, mass, pot, dt_start=dt)
         t0 = time.perf_counter()
         e, _ = h.energy_forces(cfg.x, cfg.box)
         print(json.dumps({"eval_only": cfg.name, "atoms": n, "energy": e,
@@ -196,27 +277,13 @@ def run_gpu(args):
         h.close()
         return
 
-    def step():
-        work.copy_(x0)
-        return h.minimize_dev(work, cfg.box, ftol, MAXITER, stream)
-
-    for _ in range(args.warmup):
-        r = step()
-    iters_total, launches, results = 0, 0, []
     barrier = (lambda: __import__("torch.distributed").distributed.barrier()) if world > 1 else (lambda: None)
     barrier()
-    torch.cuda.synchronize()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
-        ev0.record(stream)
-        for _ in range(args.steps):
-            r = step()
-            results.append(r.as_dict())
-            iters_total += r.iterations
-        ev1.record(stream)
-        torch.cuda.synchronize()
+    m, h, x_relaxed = relax_form(fg, torch, cfg, args.form, pair, args, dev, stream)
     barrier()
-    ms = ev0.elapsed_time(ev1)
+    pot, ftol, results = m["pot"], m["ftol"], m["results"]
+    ms = m["ms"]
+    iters_total = sum(rr["iterations"] for rr in results)
     if world > 1:
         import torch.distributed as dist
         t = torch.tensor([ms], device=dev)
@@ -228,17 +295,8 @@ def run_gpu(args):
     else:
         iters_total_all = float(iters_total)
     value = n * iters_total_all / (ms * 1e-3)
-    is_rgl = not args.config.startswith("lj")
     rc = pot.rc if is_rgl else pot.rc_lj
-    cell_mode = all(np.floor(np.asarray(cfg.box) / (rc + pot.skin)) >= 3)
-    build_k = 5 if cell_mode else 1
-    fp32 = args.form == "fp32pair"
-    force_k = (2 if fp32 else 3) if is_rgl else 1
-    # kernels per iteration: update, list-build chain (gated), force passes,
-    # reduce, control; per call: prepare + build + forces + reduce + control + finalize
-    per_iter = 1 + build_k + force_k + 2
-    for rr in results:
-        launches += (1 + build_k + force_k + 2 + 1) + per_iter * rr["iterations"]
+    cell_mode = bool(np.all(np.floor(np.asarray(cfg.box) / (rc + pot.skin)) >= 3))
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -247,45 +305,44 @@ def run_gpu(args):
            "config": {"workload": f"{cfg.name} ({n} atoms), FIRE2 + semi-implicit Euler to "
                                   f"max|F_i| < {ftol:g}",
                       "atoms": n, "ftol": ftol, "form": args.form, "skin": pot.skin,
-                      "exec": args.exec, "pair_eval": args.pair,
+                      "exec": args.exec, "pair_eval": pair,
                       "iterations_per_step": [rr["iterations"] for rr in results],
                       "final_fmax_atom": [rr["fmax_atom"] for rr in results],
                       "final_energy_per_atom": [rr["energy"] / n for rr in results],
                       "nbr_builds": [rr["nbr_builds"] for rr in results],
                       "l2": "inputs larger than L2 (working set > 1 GB at 1M atoms)"},
-           "gpu_launches": launches,
-           "clocks": clk.summary()}
+           "gpu_launches": launches_of(results, is_rgl, fp32, cell_mode),
+           "clocks": m["clocks"]}
 
     # per-stage device times (CUDA events) for the roofline of the dominant kernel
     stages = h.profile_stages(cfg.x, cfg.box, reps=5)
-    dom = "density" if is_rgl and stages["density"] >= stages["force"] else "force"
-    pairs = count_pairs(cfg.x, cfg.box, np.sqrt(pot.rc ** 2 if is_rgl else pot.rc_lj ** 2))
-    key = dom if is_rgl else "force_lj"
+    pairs = count_pairs(cfg.x, cfg.box, rc)
+    if is_rgl:
+        dom = "density" if stages["density"] >= stages["force"] else "force"
+        kname, key = STAGE_KERNELS[(args.form, pair)][dom]
+    else:
+        dom, kname, key = "force", "k_force_lj", "force_lj"
     # the FP32-pair form walks a full list: every pair is evaluated from both ends
     evals = pairs * (2 if fp32 else 1)
     flop = ALG_FLOP_PER_PAIR[key] * evals
     achieved = flop / (stages[dom] * 1e-3)
     peak = fg.fire_diag_fma_peak(1 if fp32 else 0)
-    if fp32:
-        kname = {"density": "k_density32", "force": "k_force32"}[dom]
-    else:
-        kname = {"density": "k_density", "force": "k_force_rgl" if is_rgl else "k_force_lj"}[dom]
     out["roofline"] = {"bound": "alu", "kernel": kname, "achieved": achieved / 1e12,
                        "peak": peak / 1e12, "unit": "TFLOP/s",
                        "frac": achieved / peak, "traffic": read_traffic(kname),
-                       "peak_source": ("measured %s FMA issue rate (fire_diag_fma_peak)"
-                                       % ("FP32" if fp32 else "FP64")),
+                       "peak_source": ("measured %s FMA issue rate (fire_diag_fma_peak), "
+                                       "FMA = 2 FLOP" % ("FP32" if fp32 else "FP64")),
+                       "flop_per_pair": ALG_FLOP_PER_PAIR[key],
                        "stage_ms": stages, "pairs_within_rc": pairs, "pair_evaluations": evals}
     # HBM roofline of the whole iteration, as the metric asks
     alg_b = ALG_BYTES_PER_ATOM_ITER["rgl" if is_rgl else "lj"]
-    hbm = None
     try:
-        hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
+        hbm, hsrc = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"], "measured"
     except Exception:
-        hbm = 6800.0
+        hbm, hsrc = 6800.0, "fallback"
     out["hbm_roofline"] = {"alg_bytes_per_atom_iter": alg_b,
                            "achieved_gbs": value * alg_b / 1e9, "peak_gbs": hbm,
-                           "frac": value * alg_b / 1e9 / hbm}
+                           "peak_source": hsrc, "frac": value * alg_b / 1e9 / hbm}
 
     # end to end through the host-pointer API (H2D of positions, D2H of result)
     if not args.no_e2e:
@@ -302,6 +359,32 @@ def run_gpu(args):
                       "h2d_bytes_per_step": int(cfg.x.nbytes) + 1024,
                       "d2h_bytes_per_step": int(cfg.x.nbytes) + 1024}
     h.close()
+
+    # the other form on the same workload, its relaxed state checked in FP64
+    if is_rgl and not args.no_forms and world == 1:
+        other = "fp32pair" if args.form == "fp64" else "fp64"
+        opair = default_pair(other)
+        m2, h2, x2 = relax_form(fg, torch, cfg, other, opair, args, dev, stream, clocks=False)
+        h2.close()
+        ms2 = m2["ms"]
+        it2 = sum(rr["iterations"] for rr in m2["results"])
+        pot64, mass, dt, _ = potential_for(args.config, "fp64")
+        with fg.FireHandle(n, mass, pot64, dt_start=dt) as hv:
+            fv = torch.empty_like(x2)
+            ev = torch.zeros(1, dtype=torch.float64, device=dev)
+            fg.fire_energy_forces_dev(hv.h, x2, cfg.box, fv, ev)
+            f64_fmax = float(torch.linalg.norm(fv, dim=1).max().item())
+            e64 = float(ev.item())
+            fv1 = torch.empty_like(x_relaxed)
+            fg.fire_energy_forces_dev(hv.h, x_relaxed, cfg.box, fv1, ev)
+            e64_head = float(ev.item())
+        out["forms"] = {other: {
+            "value": n * it2 / (ms2 * 1e-3), "unit": UNIT, "ms_per_step": ms2 / args.steps,
+            "pair_eval": opair, "iterations_per_step": [rr["iterations"] for rr in m2["results"]],
+            "final_fmax_atom_own": [rr["fmax_atom"] for rr in m2["results"]],
+            "final_fmax_atom_fp64_check": f64_fmax,
+            "energy_per_atom_fp64_check": e64 / n,
+            "energy_per_atom_diff_vs_headline": (e64 - e64_head) / n}}
     if rank == 0:
         if world == 1 and not args.no_cpu:
             out["cpu_baseline"] = cpu_baseline(cfg, args)

@@ -36,7 +36,7 @@
 extern "C" {
 #endif
 
-#define FIRE2_ABI_VERSION 3
+#define FIRE2_ABI_VERSION 4
 
 typedef enum {
     FIRE_OK = 0,
@@ -143,6 +143,11 @@ typedef struct {
     int32_t norm;               /* fire_norm for the ftol test       (default 0) */
     int32_t variant;            /* fire_variant                      (default 0) */
     int32_t reserved;
+    double dmax;                /* maximum displacement of any atom per step (the
+                                   paper's dmax, Sec. 4 cases 1 and 7), 0 = no cap
+                                   (default 0): the drift x += dt v uses
+                                   min(dt, dmax / max_i |v_i|); the FIRE dt is
+                                   not changed by the cap */
 } fire_params_t;
 
 typedef struct {
@@ -216,6 +221,17 @@ fire_status fire_set_exec_mode(fire_handle_t* h, int32_t mode, int32_t chunk);
  * When exceeded, the loop stops at the next iteration boundary and the call
  * returns FIRE_ERR_TIMEOUT.  Errors: FIRE_ERR_ARG (h NULL or seconds < 0). */
 fire_status fire_set_time_budget(fire_handle_t* h, double seconds);
+
+/* Frozen degrees of freedom for later fire_minimize* calls on h (Sec. 4,
+ * cases 1 and 7: border atoms frozen in x and y).  mask: host, one byte per
+ * atom, bit d (0 = x, 1 = y, 2 = z) set = that component is frozen; the
+ * library copies it.  Frozen force components are set to zero after every
+ * force evaluation of a relaxation, so they enter neither P, the force norms
+ * (ftol test, result norms) nor the motion.  fire_energy_forces* still
+ * return the full forces.  mask = NULL frees every component again.
+ * Errors: FIRE_ERR_ARG (h NULL, a batched handle, a byte above 7),
+ * FIRE_ERR_NOMEM / FIRE_ERR_CUDA. */
+fire_status fire_set_dof_mask(fire_handle_t* h, const uint8_t* mask);
 
 /* Stages timed by fire_profile_stages. */
 typedef enum {
@@ -387,6 +403,45 @@ fire_status fire_rgl_implicit_grad_dev(fire_handle_t* h, const double* d_pos, co
  * paper has no counterpart.  Errors: FIRE_ERR_ARG. */
 fire_status fire_diag_rgl_table(const fire_potential_t* pot, int64_t n, const double* r,
                                 double* out);
+
+/* ---- Nudged elastic band (Sec. 4, cases 7 and 8) ------------------------
+ * FIRE 2.0 relaxation of an ensemble of n_img movable images of one system
+ * between two fixed end states "with modified forces".  The paper cites
+ * Sheppard et al. (2008) and states no formulas; the library uses that
+ * reference's standard forces: the improved tangent of Henkelman and Jonsson
+ * (2000) from the neighbouring images and energies, F - (F.t) t plus the
+ * spring force k (|R_{i+1} - R_i| - |R_i - R_{i-1}|) t, and optionally a
+ * climbing image (the movable image of highest energy: F - 2 (F.t) t).  All
+ * movable images form one system for FIRE (one dt, alpha and P), and the
+ * stopping norm is taken over every image. */
+
+/* Creates a NEB handle for n_img >= 1 movable images of sys->n_atoms atoms
+ * each (n_img x n_atoms <= 2^25 - 1); k_spring >= 0 (energy / length^2);
+ * climb != 0 enables the climbing image.  fire_set_dof_mask takes one
+ * image's mask (n_atoms bytes) and applies it to every image;
+ * fire_set_time_budget and fire_set_exec_mode apply as for single systems.
+ * Errors: FIRE_ERR_ARG, FIRE_ERR_NOMEM, FIRE_ERR_CUDA. */
+fire_status fire_neb_init(fire_handle_t** h, int32_t n_img, const fire_system_t* sys,
+                          const fire_potential_t* pot, const fire_params_t* params,
+                          double k_spring, int32_t climb);
+
+/* Relaxes the band.  path: host, (n_img + 2) x n_atoms x 3 row-major, image 0
+ * and image n_img + 1 are the fixed end states (read only), images 1..n_img
+ * are relaxed in place (updated only on FIRE_OK).  energies: host, n_img + 2
+ * values out (may be NULL); climber: out, the index 1..n_img of the climbing
+ * image at the last evaluation, 0 without climbing (may be NULL).
+ * out->energy is the sum of the movable images' energies, the norms are
+ * those of the NEB forces.  Errors: as fire_minimize, FIRE_ERR_STATE for a
+ * handle not made by fire_neb_init. */
+fire_status fire_neb_minimize(fire_handle_t* h, double* path, const double box[3], double ftol,
+                              int64_t maxiter, fire_result_t* out, double* energies,
+                              int32_t* climber);
+
+/* As fire_neb_minimize with path on the device (same layout), ordered on
+ * `stream` (cudaStream_t); energies and climber are host pointers. */
+fire_status fire_neb_minimize_dev(fire_handle_t* h, double* d_path, const double box[3],
+                                  double ftol, int64_t maxiter, fire_result_t* out,
+                                  double* energies, int32_t* climber, void* stream);
 
 /* Message of the last failed call on h (or of the last failed fire_init when
  * h is NULL).  Never NULL. */

@@ -42,7 +42,8 @@ EXPORTED = ("fire_abi_version", "fire_default_params", "fire_init", "fire_minimi
             "fire_batch_init", "fire_minimize_batch", "fire_minimize_batch_dev",
             "fire_batch_set_tuning", "fire_batch_autotune", "fire_set_rgl_params",
             "fire_rgl_energy_grad_dev", "fire_rgl_hvp_dev", "fire_rgl_implicit_grad_dev",
-            "fire_diag_rgl_table", "fire_last_error", "fire_destroy")
+            "fire_diag_rgl_table", "fire_set_dof_mask", "fire_neb_init", "fire_neb_minimize",
+            "fire_neb_minimize_dev", "fire_last_error", "fire_destroy")
 FIRE_EXEC_GRAPH_WHILE, FIRE_EXEC_CHUNKED = 0, 1
 STAGES = ("build", "density", "embed", "force", "reduce", "control", "update")
 
@@ -66,7 +67,7 @@ class fire_params_t(C.Structure):
                 ("alphashrink", C.c_double), ("delaystep", C.c_int32), ("vdfmax", C.c_int32),
                 ("halfstepback", C.c_int32), ("initialdelay", C.c_int32),
                 ("integrator", C.c_int32), ("norm", C.c_int32), ("variant", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("reserved", C.c_int32), ("dmax", C.c_double)]
 
 
 class fire_batch_tuning_t(C.Structure):
@@ -112,6 +113,16 @@ def load_library(path: str | None = None):
                                            C.c_void_p, C.c_void_p]
     lib.fire_set_time_budget.argtypes = [H, C.c_double]
     lib.fire_set_exec_mode.argtypes = [H, C.c_int32, C.c_int32]
+    lib.fire_set_dof_mask.argtypes = [H, C.c_void_p]
+    lib.fire_neb_init.argtypes = [C.POINTER(H), C.c_int32, C.POINTER(fire_system_t),
+                                  C.POINTER(fire_potential_t), C.POINTER(fire_params_t),
+                                  C.c_double, C.c_int32]
+    lib.fire_neb_minimize.argtypes = [H, C.c_void_p, C.POINTER(C.c_double), C.c_double, C.c_int64,
+                                      C.POINTER(fire_result_t), C.c_void_p,
+                                      C.POINTER(C.c_int32)]
+    lib.fire_neb_minimize_dev.argtypes = [H, C.c_void_p, C.POINTER(C.c_double), C.c_double,
+                                          C.c_int64, C.POINTER(fire_result_t), C.c_void_p,
+                                          C.POINTER(C.c_int32), C.c_void_p]
     lib.fire_diag_exp.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]
     lib.fire_batch_init.argtypes = [C.POINTER(H), C.c_int32, C.c_void_p, C.POINTER(fire_system_t),
                                     C.POINTER(fire_potential_t), C.POINTER(fire_params_t)]
@@ -196,6 +207,16 @@ def fire_destroy(handle) -> None:
 
 def fire_set_time_budget(handle, seconds: float) -> None:
     _check(load_library().fire_set_time_budget(handle, float(seconds)), handle)
+
+
+def fire_set_dof_mask(handle, mask) -> None:
+    """Frozen degrees of freedom of later relaxations: one uint8 per atom,
+    bit d set = component d frozen; None frees them all."""
+    if mask is None:
+        _check(load_library().fire_set_dof_mask(handle, None), handle)
+        return
+    m = np.ascontiguousarray(mask, dtype=np.uint8)
+    _check(load_library().fire_set_dof_mask(handle, m.ctypes.data_as(C.c_void_p)), handle)
 
 
 def fire_set_exec_mode(handle, mode: int, chunk: int = 32) -> None:
@@ -500,6 +521,84 @@ class FireHandle:
 
     def set_time_budget(self, seconds):
         fire_set_time_budget(self.h, seconds)
+
+    def set_dof_mask(self, mask):
+        if mask is not None and np.asarray(mask).shape != (self.n,):
+            raise ValueError("the mask holds one byte per atom")
+        fire_set_dof_mask(self.h, mask)
+
+    def close(self):
+        if getattr(self, "h", None):
+            fire_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class FireNEB:
+    """Nudged elastic band handle (fire_neb_init): n_img movable images of a
+    system of n_atoms atoms, relaxed together with FIRE 2.0."""
+
+    def __init__(self, n_img: int, n_atoms: int, mass: float, pot: Potential, k_spring: float,
+                 climb: bool = True, params=None, periodic=(1, 1, 1),
+                 dt_start: float | None = None, **param_overrides):
+        if params is None:
+            params = fire_default_params(dt_start)
+        for k, v in param_overrides.items():
+            setattr(params, k, int(v) if isinstance(getattr(params, k), int) else float(v))
+        sys = fire_system_t(int(n_atoms), float(mass), (C.c_int32 * 3)(*periodic), 0)
+        self.n_img, self.n = int(n_img), int(n_atoms)
+        h = C.c_void_p()
+        st = load_library().fire_neb_init(C.byref(h), int(n_img), C.byref(sys), C.byref(pot.c()),
+                                          C.byref(params), float(k_spring), int(bool(climb)))
+        _check(st, None)
+        self.h = h
+
+    def _shape_ok(self, path):
+        if tuple(path.shape) != (self.n_img + 2, self.n, 3):
+            raise ValueError(f"path must be ({self.n_img + 2}, {self.n}, 3)")
+
+    def minimize(self, path, box, ftol, maxiter):
+        """path: float64 (n_img + 2, n_atoms, 3), relaxed in place; returns
+        (result, energies (n_img + 2), climbing-image index or 0)."""
+        if not (isinstance(path, np.ndarray) and path.dtype == np.float64
+                and path.flags.c_contiguous):
+            raise ValueError("path must be a C-contiguous float64 array")
+        self._shape_ok(path)
+        out, E, cl = fire_result_t(), np.zeros(self.n_img + 2), C.c_int32(0)
+        _check(load_library().fire_neb_minimize(self.h, path.ctypes.data, _box(box), float(ftol),
+                                                int(maxiter), C.byref(out), E.ctypes.data,
+                                                C.byref(cl)), self.h)
+        return out, E, int(cl.value)
+
+    def minimize_dev(self, d_path, box, ftol, maxiter, stream=None):
+        """d_path: CUDA float64 tensor (n_img + 2, n_atoms, 3), relaxed in place."""
+        _check_dev(d_path)
+        self._shape_ok(d_path)
+        out, E, cl = fire_result_t(), np.zeros(self.n_img + 2), C.c_int32(0)
+        _check(load_library().fire_neb_minimize_dev(self.h, d_path.data_ptr(), _box(box),
+                                                    float(ftol), int(maxiter), C.byref(out),
+                                                    E.ctypes.data, C.byref(cl),
+                                                    _stream(stream)), self.h)
+        return out, E, int(cl.value)
+
+    def set_dof_mask(self, mask):
+        if mask is not None and np.asarray(mask).shape != (self.n,):
+            raise ValueError("the mask holds one byte per atom of an image")
+        fire_set_dof_mask(self.h, mask)
+
+    def set_exec_mode(self, mode, chunk=32):
+        fire_set_exec_mode(self.h, mode, chunk)
 
     def close(self):
         if getattr(self, "h", None):

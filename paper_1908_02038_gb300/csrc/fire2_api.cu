@@ -15,6 +15,7 @@
 #include "fire2.h"
 #include "fire2_device.cuh"
 #include "fire2_grad.cuh"
+#include "fire2_neb.cuh"
 
 using namespace fire2;
 
@@ -37,6 +38,34 @@ struct GradState {
     DevState* st = nullptr;        // status word of the list build
 };
 
+// Nudged elastic band handles (fire_neb_init): the movable images are the
+// handle's atoms, image k = atoms [k img_n, (k + 1) img_n).
+struct NebState {
+    int n_img = 0;
+    double k = 0.0;
+    int climb = 0;
+    int nb = 1;                    // k_neb_sums blocks per image
+    int nb_proj = 1;               // k_neb_project blocks
+    dvec4* end = nullptr;          // 2 x img_n fixed end states
+    double* eatom = nullptr;       // per-atom energies
+    double* part = nullptr;        // kNebSums x n_img x nb
+    double* coef = nullptr;        // 4 x n_img
+    double* E = nullptr;           // n_img + 2
+    int* climber = nullptr;
+    double* d_path = nullptr;      // staging for the host-pointer call, (n_img + 2) x img_n x 3
+    double* d_end_energy = nullptr;   // scratch for the end-state evaluations
+    fire_handle* inner = nullptr;  // one-image handle for the end-state energies
+};
+
+static void neb_free(NebState* q) {
+    if (!q) return;
+    for (void* p : {(void*)q->end, (void*)q->eatom, (void*)q->part, (void*)q->coef, (void*)q->E,
+                    (void*)q->climber, (void*)q->d_path, (void*)q->d_end_energy})
+        if (p) cudaFree(p);
+    if (q->inner) fire_destroy(q->inner);
+    delete q;
+}
+
 struct fire_handle {
     int device = 0;
     fire_system_t sys{};
@@ -48,7 +77,7 @@ struct fire_handle {
     int ncell_alloc = 0;
     Bufs b{};
     cudaStream_t stream = nullptr;   // default stream of host-pointer calls
-    cudaStream_t cap0 = nullptr, cap1 = nullptr;  // private capture streams
+    cudaStream_t cap0 = nullptr, cap1 = nullptr, cap2 = nullptr;  // private capture streams
     DevState* h_state = nullptr;     // pinned
     double* h_pos = nullptr;         // pinned staging, N x 3
     // cached relaxation graph
@@ -67,6 +96,9 @@ struct fire_handle {
     float *tab_d32 = nullptr, *tab_f32 = nullptr;
     size_t smem_d = 0, smem_f = 0;
     int nb_tab_d = 0, nb_tab_f = 0;
+    uint8_t* dofmask = nullptr;      // device copy of the frozen-DOF mask (n bytes)
+    int img_n = 0;                   // atoms per image (n, except for NEB handles)
+    NebState* neb = nullptr;
     std::string err;
 };
 
@@ -134,6 +166,8 @@ GeoC make_geo(const fire_handle* h, const double box[3]) {
     g.full = h->pot.precision == FIRE_PREC_FP32_PAIR ? 1 : 0;
     for (int a = 0; a < 3; ++a)
         g.Lq[a] = (int)(unsigned)(unsigned long long)std::llrint(box[a] * h->b.qscale);
+    g.img_n = h->img_n > 0 ? h->img_n : h->n;
+    g.ncell_img = g.nc[0] * g.nc[1] * g.nc[2];
     return g;
 }
 
@@ -141,7 +175,7 @@ GeoC make_geo(const fire_handle* h, const double box[3]) {
 // density, plus a margin; never more than N - 1.
 int estimate_cap(const fire_handle* h, const GeoC& g) {
     const double vol = g.L[0] * g.L[1] * g.L[2];
-    const double dens = h->n / vol;
+    const double dens = g.img_n / vol;    // atoms of one image
     const double rl = std::sqrt(g.rlist2);
     const double half = 2.0 / 3.0 * M_PI * rl * rl * rl * dens;
     long long cap = (long long)std::ceil(1.5 * half * (g.full ? 2.0 : 1.0)) + 16;
@@ -179,7 +213,7 @@ fire_status ensure_buffers(fire_handle* h, const GeoC& g, int cap) {
         h->cap = cap;
     }
     h->b.cap = h->cap;
-    const int ncell = g.brute ? 1 : g.nc[0] * g.nc[1] * g.nc[2];
+    const int ncell = (h->n / g.img_n) * g.ncell_img;
     if (ncell > h->ncell_alloc) {
         drop_graph(h);
         cudaFree(h->b.cell_count);
@@ -202,6 +236,7 @@ void launch_build(fire_handle* h, const GeoC& g, int force, cudaStream_t s) {
         k_cell_count<<<ceil_div(n, kElemBlock), kElemBlock, 0, s>>>(h->b, g, force);
         k_cell_scan<<<1, 1024, 0, s>>>(h->b, g, force);
         k_cell_fill<<<ceil_div(n, kElemBlock), kElemBlock, 0, s>>>(h->b, g, force);
+        k_cell_sort<<<ceil_div(h->b.ncell, kElemBlock), kElemBlock, 0, s>>>(h->b, g, force);
     }
     k_nbr_build<<<ceil_div(n, kForceBlock), kForceBlock, 0, s>>>(h->b, g, force);
 }
@@ -229,12 +264,77 @@ void launch_forces(fire_handle* h, const GeoC& g, cudaStream_t s) {
     (void)n;
 }
 
-void launch_reduce(fire_handle* h, cudaStream_t s) {
-    k_reduce<<<h->b.nb_red, kElemBlock, 0, s>>>(h->b);
+// The FP32-pair force kernels write whole forces and produce the (F, v)
+// reductions themselves; the atomic-accumulating paths need this pass.
+NebC neb_consts(const fire_handle* h) {
+    const NebState& q = *h->neb;
+    NebC c;
+    c.end = q.end;
+    c.part = q.part;
+    c.coef = q.coef;
+    c.E = q.E;
+    c.climber = q.climber;
+    c.k = q.k;
+    c.climb = q.climb;
+    c.n_img = q.n_img;
+    c.img_n = h->img_n;
+    c.nb = q.nb;
+    return c;
+}
+
+void launch_reduce(fire_handle* h, const GeoC& g, cudaStream_t s) {
+    if (h->neb) {   // nudged elastic band: project, then reduce (F^NEB, v)
+        const NebC c = neb_consts(h);
+        k_neb_sums<<<dim3(c.nb, c.n_img), kNebBlock, 0, s>>>(h->b, g, c);
+        k_neb_scalars<<<1, 256, (size_t)c.n_img * kNebSums * sizeof(double), s>>>(h->b, c);
+        k_neb_project<<<h->neb->nb_proj, kNebBlock, 0, s>>>(h->b, g, c);
+        return;
+    }
+    if (h->b.accum) k_reduce<<<h->b.nb_red, kElemBlock, 0, s>>>(h->b);
 }
 
 int update_grid(int n) { return std::max(1, std::min(ceil_div(n, kElemBlock), 152 * 8)); }
 
+// The element-wise step; with dmax > 0 in two passes (see k_update_pre).
+void launch_update(fire_handle* h, const GeoC& g, cudaStream_t s, cudaGraphConditionalHandle hif,
+                   int has_if) {
+    const bool capped = h->par.dmax > 0.0;
+    if (capped) k_update_pre<<<update_grid(h->n), kElemBlock, 0, s>>>(h->b);
+    k_update<<<update_grid(h->n), kElemBlock, 0, s>>>(h->b, g, hif, has_if, capped ? 1 : 0);
+}
+
+// Appends a conditional node (WHILE or IF, one body) at the capture position
+// of `s` and makes it the stream's only dependency; returns its body graph.
+cudaError_t add_conditional(cudaStream_t s, cudaGraphConditionalHandle hc,
+                            cudaGraphConditionalNodeType type, cudaGraph_t* body) {
+    cudaStreamCaptureStatus cst;
+    cudaGraph_t cg = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    cudaError_t e = cudaStreamGetCaptureInfo(s, &cst, nullptr, &cg, &deps, nullptr, &ndeps);
+    cudaGraphNode_t cnode = nullptr;
+    alignas(cudaGraphNodeParams) unsigned char cp_raw[sizeof(cudaGraphNodeParams)];
+    std::memset(cp_raw, 0, sizeof cp_raw);
+    cudaGraphNodeParams& cp = *reinterpret_cast<cudaGraphNodeParams*>(cp_raw);
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = hc;
+    cp.conditional.type = type;
+    cp.conditional.size = 1;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&cnode, cg, deps, nullptr, ndeps, &cp);
+    if (e == cudaSuccess)
+        e = cudaStreamUpdateCaptureDependencies(s, &cnode, nullptr, 1,
+                                                cudaStreamSetCaptureDependencies);
+    if (e == cudaSuccess) *body = cp.conditional.phGraph_out[0];
+    return e;
+}
+
+// The device loop as one graph:
+//   prepare, build, forces, reductions, control (initial evaluation)
+//   WHILE (not stopped):
+//     update (its last block sets the IF condition: displacement > skin/2)
+//     IF (rebuild): cell binning + neighbour list
+//     forces, reductions, control (sets the WHILE condition)
+//   finalize
 fire_status build_graph(fire_handle* h, const GeoC& g) {
     drop_graph(h);
     cudaGraph_t graph = nullptr;
@@ -255,37 +355,35 @@ fire_status build_graph(fire_handle* h, const GeoC& g) {
     k_prepare<<<ceil_div(n, kElemBlock), kElemBlock, 0, h->cap0>>>(h->b);
     launch_build(h, g, 1, h->cap0);
     launch_forces(h, g, h->cap0);
-    launch_reduce(h, h->cap0);
+    launch_reduce(h, g, h->cap0);
     k_control<<<1, kCtlThreads, 0, h->cap0>>>(h->b, CTL_INITIAL, hw, 1);
 
-    cudaStreamCaptureStatus cst;
-    cudaGraph_t cg = nullptr;
-    const cudaGraphNode_t* deps = nullptr;
-    size_t ndeps = 0;
-    e = cudaStreamGetCaptureInfo(h->cap0, &cst, nullptr, &cg, &deps, nullptr, &ndeps);
-    cudaGraphNode_t cnode = nullptr;
-    alignas(cudaGraphNodeParams) unsigned char cp_raw[sizeof(cudaGraphNodeParams)];
-    std::memset(cp_raw, 0, sizeof cp_raw);
-    cudaGraphNodeParams& cp = *reinterpret_cast<cudaGraphNodeParams*>(cp_raw);
-    cp.type = cudaGraphNodeTypeConditional;
-    cp.conditional.handle = hw;
-    cp.conditional.type = cudaGraphCondTypeWhile;
-    cp.conditional.size = 1;
-    if (e == cudaSuccess) e = cudaGraphAddNode(&cnode, cg, deps, nullptr, ndeps, &cp);
-    if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(h->cap0, &cnode, nullptr, 1,
-                                                                  cudaStreamSetCaptureDependencies);
+    cudaGraph_t body = nullptr;
+    e = add_conditional(h->cap0, hw, cudaGraphCondTypeWhile, &body);
     if (e == cudaSuccess) {
-        cudaGraph_t body = cp.conditional.phGraph_out[0];
-        e = cudaStreamBeginCaptureToGraph(h->cap1, body, nullptr, nullptr, 0,
-                                          cudaStreamCaptureModeRelaxed);
+        cudaGraphConditionalHandle hif;
+        e = cudaGraphConditionalHandleCreate(&hif, body, 0, cudaGraphCondAssignDefault);
+        if (e == cudaSuccess)
+            e = cudaStreamBeginCaptureToGraph(h->cap1, body, nullptr, nullptr, 0,
+                                              cudaStreamCaptureModeRelaxed);
         if (e == cudaSuccess) {
-            k_update<<<update_grid(n), kElemBlock, 0, h->cap1>>>(h->b);
-            launch_build(h, g, 0, h->cap1);
+            launch_update(h, g, h->cap1, hif, 1);
+            cudaGraph_t build_body = nullptr;
+            e = add_conditional(h->cap1, hif, cudaGraphCondTypeIf, &build_body);
+            if (e == cudaSuccess)
+                e = cudaStreamBeginCaptureToGraph(h->cap2, build_body, nullptr, nullptr, 0,
+                                                  cudaStreamCaptureModeRelaxed);
+            if (e == cudaSuccess) {
+                launch_build(h, g, 1, h->cap2);
+                cudaGraph_t bb_out = nullptr;
+                e = cudaStreamEndCapture(h->cap2, &bb_out);
+            }
             launch_forces(h, g, h->cap1);
-            launch_reduce(h, h->cap1);
+            launch_reduce(h, g, h->cap1);
             k_control<<<1, kCtlThreads, 0, h->cap1>>>(h->b, CTL_LOOP, hw, 1);
             cudaGraph_t body_out = nullptr;
-            e = cudaStreamEndCapture(h->cap1, &body_out);
+            const cudaError_t e1 = cudaStreamEndCapture(h->cap1, &body_out);
+            if (e == cudaSuccess) e = e1;
         }
     }
     k_finalize<<<ceil_div(n, kElemBlock), kElemBlock, 0, h->cap0>>>(h->b);
@@ -338,16 +436,16 @@ fire_status build_chunked(fire_handle* h, const GeoC& g) {
         k_prepare<<<ceil_div(n, kElemBlock), kElemBlock, 0, s>>>(h->b);
         launch_build(h, g, 1, s);
         launch_forces(h, g, s);
-        launch_reduce(h, s);
+        launch_reduce(h, g, s);
         k_control<<<1, kCtlThreads, 0, s>>>(h->b, CTL_INITIAL, cudaGraphConditionalHandle{}, 0);
     });
     if (st == FIRE_OK)
         st = capture_plain(h, &h->exec_chunk, [&](cudaStream_t s) {
             for (int c = 0; c < h->chunk; ++c) {
-                k_update<<<update_grid(n), kElemBlock, 0, s>>>(h->b);
+                launch_update(h, g, s, cudaGraphConditionalHandle{}, 0);
                 launch_build(h, g, 0, s);
                 launch_forces(h, g, s);
-                launch_reduce(h, s);
+                launch_reduce(h, g, s);
                 k_control<<<1, kCtlThreads, 0, s>>>(h->b, CTL_LOOP, cudaGraphConditionalHandle{}, 0);
             }
         });
@@ -399,6 +497,7 @@ void init_state(fire_handle* h, double ftol, int64_t maxiter) {
     q.norm = p.norm;
     q.integrator = p.integrator;
     q.variant = p.variant;
+    q.dmax = p.dmax;
     fire_scal_init(q, s.fs);
     s.budget_ns = (unsigned long long)(h->budget_s * 1e9);
 }
@@ -443,11 +542,14 @@ fire_status check_params(fire_handle* h, const fire_params_t& p) {
     if (p.variant != FIRE_VARIANT_FIRE2 && p.variant != FIRE_VARIANT_FIRE1)
         return fail(h, FIRE_ERR_ARG, "unknown variant %d", p.variant);
     if (p.norm < 0 || p.norm > 2) return fail(h, FIRE_ERR_ARG, "unknown norm %d", p.norm);
+    if (!(p.dmax >= 0.0) || !std::isfinite(p.dmax))
+        return fail(h, FIRE_ERR_ARG, "dmax must be finite and >= 0");
     return FIRE_OK;
 }
 
-fire_status prepare_call(fire_handle* h, const double box[3], GeoC* g) {
+fire_status prepare_call(fire_handle* h, const double box[3], GeoC* g, bool neb_call = false) {
     if (h->batch) return fail(h, FIRE_ERR_STATE, "batched handle: use fire_minimize_batch");
+    if (h->neb && !neb_call) return fail(h, FIRE_ERR_STATE, "NEB handle: use fire_neb_minimize");
     fire_status st = check_box(h, box);
     if (st != FIRE_OK) return st;
     CK(h, cudaSetDevice(h->device));
@@ -501,6 +603,7 @@ fire_status fire_default_params(fire_params_t* out, double dt_start) {
     out->norm = FIRE_NORM_MAX_ATOM;
     out->variant = FIRE_VARIANT_FIRE2;
     out->reserved = 0;
+    out->dmax = 0.0;
     return FIRE_OK;
 }
 
@@ -633,6 +736,7 @@ static fire_status init_handle(fire_handle_t** hp, const fire_system_t* sys,
     h->pot = *pot;
     h->par = *params;
     h->n = (int)sys->n_atoms;
+    h->img_n = h->n;
     fire_status st = check_params(h, *params);
     if (st != FIRE_OK) {
         g_init_err = h->err;
@@ -666,6 +770,7 @@ static fire_status init_handle(fire_handle_t** hp, const fire_system_t* sys,
     CKI(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
     CKI(cudaStreamCreateWithFlags(&h->cap0, cudaStreamNonBlocking));
     CKI(cudaStreamCreateWithFlags(&h->cap1, cudaStreamNonBlocking));
+    CKI(cudaStreamCreateWithFlags(&h->cap2, cudaStreamNonBlocking));
     const size_t n = (size_t)h->n;
     Bufs& b = h->b;
     {
@@ -685,9 +790,32 @@ static fire_status init_handle(fire_handle_t** hp, const fire_system_t* sys,
         return FIRE_OK;
     }
     b.n = h->n;
+    int sms = 0;
+    CKI(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+    // Grids.  One-atom-per-thread kernels (FP64 density/force, LJ) use
+    // ceil(n / kForceBlock) blocks; the grid-stride kernels use what fits on
+    // the device at once, which keeps the partial sums the control kernel adds
+    // up few.  nb_force + nb_embed energy partials, nb_red rows of the (F, v)
+    // reductions.
+    b.accum = fp32pair ? 0 : 1;
+    b.fused_red = fp32pair ? 1 : 0;
     b.nb_force = ceil_div(h->n, kForceBlock);
-    b.nb_embed = (pot->kind == FIRE_POT_RGL && !fp32pair) ? ceil_div(h->n, kElemBlock) : 0;
-    b.nb_red = std::max(1, std::min(ceil_div(h->n, kElemBlock), 152 * 4));
+    b.nb_embed = (pot->kind == FIRE_POT_RGL && !fp32pair)
+                     ? std::max(1, std::min(ceil_div(h->n, kElemBlock), sms * 8)) : 0;
+    b.nb_red = std::max(1, std::min(ceil_div(h->n, kElemBlock), sms * 4));
+    if (pot->kind == FIRE_POT_RGL && pot->pair_eval == FIRE_PAIR_TABLE) {
+        fire_status ts = upload_tables(h);
+        if (ts != FIRE_OK) return bail(ts);
+        if (fp32pair) {
+            b.nb_force = h->nb_tab_d;
+            b.nb_red = h->nb_tab_f;
+        }
+    } else if (fp32pair) {
+        int occ = 0;
+        CKI(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_force32, kForceBlock, 0));
+        b.nb_force = std::max(1, std::min(ceil_div(h->n, kForceBlock), sms * std::max(occ, 1)));
+        b.nb_red = b.nb_force;
+    }
     CKI(cudaMalloc(&b.x, n * sizeof(dvec4)));
     CKI(cudaMalloc(&b.v, n * sizeof(dvec4)));
     CKI(cudaMalloc(&b.f, n * sizeof(dvec4)));
@@ -705,12 +833,9 @@ static fire_status init_handle(fire_handle_t** hp, const fire_system_t* sys,
         CKI(cudaMalloc(&b.fp, n * sizeof(double)));
     }
     CKI(cudaMalloc(&b.epart, (size_t)(b.nb_force + b.nb_embed) * sizeof(double)));
-    // table kernels write fewer energy partials than nb_force; the rest stay 0
+    // the FP64 table density kernel writes fewer energy partials than
+    // nb_force; the rest stay 0
     CKI(cudaMemset(b.epart, 0, (size_t)(b.nb_force + b.nb_embed) * sizeof(double)));
-    if (pot->kind == FIRE_POT_RGL && pot->pair_eval == FIRE_PAIR_TABLE) {
-        fire_status ts = upload_tables(h);
-        if (ts != FIRE_OK) return bail(ts);
-    }
     CKI(cudaMalloc(&b.rpart, (size_t)5 * b.nb_red * sizeof(double)));
     CKI(cudaMalloc(&b.st, sizeof(DevState)));
     CKI(cudaMalloc(&b.pos_io, 3 * n * sizeof(double)));
@@ -771,7 +896,9 @@ void fire_destroy(fire_handle_t* h) {
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->batch) fire2_batch_free(h->batch);
-    for (void* p : {(void*)h->tab_d64, (void*)h->tab_f64, (void*)h->tab_d32, (void*)h->tab_f32})
+    if (h->neb) neb_free(h->neb);
+    for (void* p : {(void*)h->tab_d64, (void*)h->tab_f64, (void*)h->tab_d32, (void*)h->tab_f32,
+                    (void*)h->dofmask})
         if (p) cudaFree(p);
     {
         GradState& gs = h->grad;
@@ -785,6 +912,7 @@ void fire_destroy(fire_handle_t* h) {
     if (h->h_pos) cudaFreeHost(h->h_pos);
     if (h->stream) cudaStreamDestroy(h->stream);
     if (h->cap0) cudaStreamDestroy(h->cap0);
+    if (h->cap2) cudaStreamDestroy(h->cap2);
     if (h->cap1) cudaStreamDestroy(h->cap1);
     delete h;
 }
@@ -797,6 +925,38 @@ fire_status fire_set_time_budget(fire_handle_t* h, double seconds) {
     if (!h) return FIRE_ERR_ARG;
     if (!(seconds >= 0.0)) return fail(h, FIRE_ERR_ARG, "time budget must be >= 0");
     h->budget_s = seconds;
+    return FIRE_OK;
+}
+
+fire_status fire_set_dof_mask(fire_handle_t* h, const uint8_t* mask) {
+    if (!h) return FIRE_ERR_ARG;
+    if (h->batch) return fail(h, FIRE_ERR_ARG, "frozen degrees of freedom need a single-system handle");
+    CK(h, cudaSetDevice(h->device));
+    const bool was_on = h->b.dofmask != nullptr;
+    if (mask) {
+        for (int i = 0; i < h->img_n; ++i)
+            if (mask[i] > 7u)
+                return fail(h, FIRE_ERR_ARG, "mask[%d] = %u: only bits 0..2 (x, y, z) exist", i,
+                            (unsigned)mask[i]);
+        if (!h->dofmask) {
+            cudaError_t e = cudaMalloc(&h->dofmask, (size_t)std::max(h->n, 1));
+            if (e != cudaSuccess) {
+                h->dofmask = nullptr;
+                return fail(h, e == cudaErrorMemoryAllocation ? FIRE_ERR_NOMEM : FIRE_ERR_CUDA,
+                            "cudaMalloc(mask): %s", cudaGetErrorString(e));
+            }
+        }
+        CK(h, cudaStreamSynchronize(h->stream));
+        // a NEB handle takes one image's mask and applies it to every image
+        for (int k = 0; k < h->n / h->img_n; ++k)
+            CK(h, cudaMemcpy(h->dofmask + (size_t)k * h->img_n, mask, (size_t)h->img_n,
+                             cudaMemcpyHostToDevice));
+        h->b.dofmask = h->dofmask;
+    } else {
+        h->b.dofmask = nullptr;
+    }
+    // the relaxation graph holds the kernels' arguments: capture again
+    if (was_on != (h->b.dofmask != nullptr)) drop_graph(h);
     return FIRE_OK;
 }
 
@@ -890,14 +1050,24 @@ fire_status fire_minimize(fire_handle_t* h, double* pos, const double box[3], do
     return FIRE_OK;
 }
 
-// Energy and forces at one configuration (plain stream launches).
+// Energy and forces at one configuration (plain stream launches); the
+// frozen-DOF mask belongs to relaxations only.
+static fire_status run_eval_unmasked(fire_handle* h, const GeoC& g, cudaStream_t s);
 static fire_status run_eval(fire_handle* h, const GeoC& g, cudaStream_t s) {
+    const uint8_t* mask = h->b.dofmask;
+    h->b.dofmask = nullptr;
+    const fire_status st = run_eval_unmasked(h, g, s);
+    h->b.dofmask = mask;
+    return st;
+}
+
+static fire_status run_eval_unmasked(fire_handle* h, const GeoC& g, cudaStream_t s) {
     init_state(h, 0.0, 0);
     CK(h, cudaMemcpyAsync(h->b.st, h->h_state, sizeof(DevState), cudaMemcpyHostToDevice, s));
     k_prepare<<<ceil_div(h->n, kElemBlock), kElemBlock, 0, s>>>(h->b);
     launch_build(h, g, 1, s);
     launch_forces(h, g, s);
-    launch_reduce(h, s);
+    launch_reduce(h, g, s);
     k_control<<<1, kCtlThreads, 0, s>>>(h->b, CTL_EVAL, cudaGraphConditionalHandle{}, 0);
     k_export_forces<<<ceil_div(h->n, kElemBlock), kElemBlock, 0, s>>>(h->b);
     CK(h, cudaGetLastError());
@@ -1035,6 +1205,7 @@ static fire_status grad_setup(fire_handle* h, const double* d_pos, const double 
         k_cell_count<<<ceil_div(n, kElemBlock), kElemBlock, 0, s>>>(lb, g, 1);
         k_cell_scan<<<1, 1024, 0, s>>>(lb, g, 1);
         k_cell_fill<<<ceil_div(n, kElemBlock), kElemBlock, 0, s>>>(lb, g, 1);
+        k_cell_sort<<<ceil_div(lb.ncell, kElemBlock), kElemBlock, 0, s>>>(lb, g, 1);
     }
     k_nbr_build<<<ceil_div(n, kForceBlock), kForceBlock, 0, s>>>(lb, g, 1);
     CK(h, cudaGetLastError());
@@ -1307,11 +1478,11 @@ fire_status fire_profile_stages(fire_handle_t* h, const double* pos, const doubl
         else if (rgl) k_force_rgl<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, g);
         else k_force_lj<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
         cudaEventRecord(ev[4], s);
-        launch_reduce(h, s);
+        launch_reduce(h, g, s);
         cudaEventRecord(ev[5], s);
         k_control<<<1, kCtlThreads, 0, s>>>(h->b, CTL_EVAL, cudaGraphConditionalHandle{}, 0);
         cudaEventRecord(ev[6], s);
-        k_update<<<update_grid(h->n), kElemBlock, 0, s>>>(h->b);
+        launch_update(h, g, s, cudaGraphConditionalHandle{}, 0);
         cudaEventRecord(ev[7], s);
         cudaError_t e = cudaEventSynchronize(ev[7]);
         if (e != cudaSuccess) {
@@ -1332,6 +1503,159 @@ fire_status fire_profile_stages(fire_handle_t* h, const double* pos, const doubl
     if (st != FIRE_OK) return st;
     for (int k = 0; k < FIRE_NSTAGES; ++k) stage_ms[k] = acc[k] / reps;
     if (!rgl) stage_ms[FIRE_STAGE_DENSITY] = stage_ms[FIRE_STAGE_EMBED] = 0.0;
+    return FIRE_OK;
+}
+
+
+// ---------------------------------------------------------------------------
+// Nudged elastic band (Sec. 4, cases 7 and 8)
+
+fire_status fire_neb_init(fire_handle_t** hp, int32_t n_img, const fire_system_t* sys,
+                          const fire_potential_t* pot, const fire_params_t* params,
+                          double k_spring, int32_t climb) {
+    if (!hp || !sys || !pot || !params) return fail(nullptr, FIRE_ERR_ARG, "NULL argument to fire_neb_init");
+    *hp = nullptr;
+    if (n_img < 1) return fail(nullptr, FIRE_ERR_ARG, "n_img = %d must be >= 1", n_img);
+    if (!(k_spring >= 0.0) || !std::isfinite(k_spring))
+        return fail(nullptr, FIRE_ERR_ARG, "k_spring must be finite and >= 0");
+    if (sys->n_atoms < 1 || (int64_t)n_img * sys->n_atoms > (int64_t)kIdxMask)
+        return fail(nullptr, FIRE_ERR_ARG, "n_img x n_atoms = %lld outside [1, %u]",
+                    (long long)n_img * (long long)sys->n_atoms, kIdxMask);
+    fire_system_t all = *sys;
+    all.n_atoms = (int64_t)n_img * sys->n_atoms;
+    fire_handle_t* h = nullptr;
+    fire_status st = init_handle(&h, &all, pot, params, true);
+    if (st != FIRE_OK) return st;
+    const int N = (int)sys->n_atoms;
+    h->img_n = N;
+    NebState* q = new (std::nothrow) NebState();
+    if (!q) {
+        fire_destroy(h);
+        return fail(nullptr, FIRE_ERR_NOMEM, "host allocation failed");
+    }
+    h->neb = q;
+    q->n_img = n_img;
+    q->k = k_spring;
+    q->climb = climb ? 1 : 0;
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+    q->nb = std::max(1, std::min(ceil_div(N, kNebBlock), std::max(1, sms * 4 / n_img)));
+    q->nb_proj = std::max(1, std::min(ceil_div(h->n, kNebBlock), sms * 4));
+#define CKN(call)                                                                            \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess) {                                                             \
+            fail(nullptr, e_ == cudaErrorMemoryAllocation ? FIRE_ERR_NOMEM : FIRE_ERR_CUDA,  \
+                 "%s: %s", #call, cudaGetErrorString(e_));                                   \
+            fire_destroy(h);                                                                 \
+            return e_ == cudaErrorMemoryAllocation ? FIRE_ERR_NOMEM : FIRE_ERR_CUDA;         \
+        }                                                                                    \
+    } while (0)
+    CKN(cudaMalloc(&q->end, 2 * (size_t)N * sizeof(dvec4)));
+    CKN(cudaMalloc(&q->eatom, (size_t)h->n * sizeof(double)));
+    CKN(cudaMalloc(&q->part, (size_t)kNebSums * n_img * q->nb * sizeof(double)));
+    CKN(cudaMalloc(&q->coef, (size_t)4 * n_img * sizeof(double)));
+    CKN(cudaMalloc(&q->E, ((size_t)n_img + 2) * sizeof(double)));
+    CKN(cudaMalloc(&q->climber, sizeof(int)));
+    CKN(cudaMalloc(&q->d_end_energy, 2 * sizeof(double)));
+    // the projection kernel writes the (F, v) reductions
+    if (q->nb_proj > h->b.nb_red) {
+        cudaFree(h->b.rpart);
+        h->b.rpart = nullptr;
+        CKN(cudaMalloc(&h->b.rpart, (size_t)5 * q->nb_proj * sizeof(double)));
+    }
+    h->b.nb_red = q->nb_proj;
+    h->b.eatom = q->eatom;
+    h->b.fused_red = 0;
+#undef CKN
+    fire_system_t one = *sys;
+    st = fire_init(&q->inner, &one, pot, params);
+    if (st != FIRE_OK) {
+        fire_destroy(h);
+        return st;
+    }
+    *hp = h;
+    return FIRE_OK;
+}
+
+// The band relaxation on device positions d_path ((n_img + 2) x N x 3).
+static fire_status neb_run(fire_handle* h, double* d_path, const double box[3], double ftol,
+                           int64_t maxiter, fire_result_t* out, double* energies,
+                           int32_t* climber, cudaStream_t s) {
+    NebState& q = *h->neb;
+    const int N = h->img_n, M = q.n_img;
+    GeoC g;
+    fire_status st = prepare_call(h, box, &g, true);
+    if (st != FIRE_OK) return st;
+    const size_t img_bytes = (size_t)3 * N * sizeof(double);
+    const double* p0 = d_path;
+    const double* p1 = d_path + (size_t)3 * N * (M + 1);
+    k_neb_load_ends<<<ceil_div(2 * N, kElemBlock), kElemBlock, 0, s>>>(p0, p1, q.end, N);
+    CK(h, cudaGetLastError());
+    // end-state energies with the one-image handle, written straight into E
+    for (int e = 0; e < 2; ++e) {
+        st = fire_energy_forces_dev(q.inner, e == 0 ? p0 : p1, box, nullptr, q.d_end_energy + e,
+                                    (void*)s);
+        if (st != FIRE_OK) return fail(h, st, "end state %d: %s", e, fire_last_error(q.inner));
+    }
+    CK(h, cudaMemcpyAsync(q.E, q.d_end_energy, sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CK(h, cudaMemcpyAsync(q.E + M + 1, q.d_end_energy + 1, sizeof(double),
+                          cudaMemcpyDeviceToDevice, s));
+    for (int attempt = 0; attempt < 4; ++attempt) {
+        CK(h, cudaMemcpyAsync(h->b.pos_io, d_path + (size_t)3 * N, img_bytes * M,
+                              cudaMemcpyDeviceToDevice, s));
+        st = run_minimize(h, g, ftol, maxiter, s);
+        if (st != FIRE_ERR_NBR_OVERFLOW || h->cap >= N - 1) break;
+        st = ensure_buffers(h, g, std::min(2 * h->cap, std::max(N - 1, 1)));
+        if (st != FIRE_OK) return st;
+    }
+    if (st != FIRE_OK) return st;
+    CK(h, cudaMemcpyAsync(d_path + (size_t)3 * N, h->b.pos_io, img_bytes * M,
+                          cudaMemcpyDeviceToDevice, s));
+    int cl = 0;
+    if (energies)
+        CK(h, cudaMemcpyAsync(energies, q.E, ((size_t)M + 2) * sizeof(double),
+                              cudaMemcpyDeviceToHost, s));
+    CK(h, cudaMemcpyAsync(&cl, q.climber, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(h, cudaStreamSynchronize(s));
+    if (climber) *climber = cl;
+    fill_result(h, out);
+    return FIRE_OK;
+}
+
+static fire_status neb_check(fire_handle_t* h, const void* path, fire_result_t* out, double ftol,
+                             int64_t maxiter) {
+    if (!h) return FIRE_ERR_ARG;
+    if (!h->neb) return fail(h, FIRE_ERR_STATE, "not a NEB handle (use fire_neb_init)");
+    if (!path || !out) return fail(h, FIRE_ERR_ARG, "NULL path or result");
+    if (!(ftol >= 0.0) || maxiter < 0) return fail(h, FIRE_ERR_ARG, "need ftol >= 0 and maxiter >= 0");
+    return FIRE_OK;
+}
+
+fire_status fire_neb_minimize_dev(fire_handle_t* h, double* d_path, const double box[3],
+                                  double ftol, int64_t maxiter, fire_result_t* out,
+                                  double* energies, int32_t* climber, void* stream) {
+    fire_status st = neb_check(h, d_path, out, ftol, maxiter);
+    if (st != FIRE_OK) return st;
+    CK(h, cudaSetDevice(h->device));
+    return neb_run(h, d_path, box, ftol, maxiter, out, energies, climber, (cudaStream_t)stream);
+}
+
+fire_status fire_neb_minimize(fire_handle_t* h, double* path, const double box[3], double ftol,
+                              int64_t maxiter, fire_result_t* out, double* energies,
+                              int32_t* climber) {
+    fire_status st = neb_check(h, path, out, ftol, maxiter);
+    if (st != FIRE_OK) return st;
+    CK(h, cudaSetDevice(h->device));
+    NebState& q = *h->neb;
+    const size_t bytes = (size_t)3 * h->img_n * (q.n_img + 2) * sizeof(double);
+    if (!q.d_path) CK(h, cudaMalloc(&q.d_path, bytes));
+    cudaStream_t s = h->stream;
+    CK(h, cudaMemcpyAsync(q.d_path, path, bytes, cudaMemcpyHostToDevice, s));
+    st = neb_run(h, q.d_path, box, ftol, maxiter, out, energies, climber, s);
+    if (st != FIRE_OK) return st;
+    CK(h, cudaMemcpyAsync(path, q.d_path, bytes, cudaMemcpyDeviceToHost, s));
+    CK(h, cudaStreamSynchronize(s));
     return FIRE_OK;
 }
 

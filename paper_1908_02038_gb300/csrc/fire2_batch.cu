@@ -420,11 +420,29 @@ __global__ void __launch_bounds__(512, 1) k_batch_relax(BArgs a) {
         b_reduce_control(a, I, sh, E, red, true, t0);
         while (!sh.done) {
             const FireScal fs = sh.fs;
+            // maximum displacement per step: the drift waits for max_i |v_i|
+            double dt_drift = fs.dt_cur;
+            if (a.prm.dmax > 0.0) {
+                double vm = 0.0;
+                for (int i = threadIdx.x; i < I.n; i += blockDim.x) {
+                    const long long gi = I.off + i;
+                    dvec4 x = a.x[gi], v = a.v[gi];
+                    fire_update_pre(fs, x, v, a.f[gi]);
+                    if (fs.zero_v) a.x[gi] = x;
+                    a.v[gi] = v;
+                    vm = fmax(vm, v.x * v.x + v.y * v.y + v.z * v.z);
+                }
+                vm = bmax(vm, red);
+                dt_drift = fire_capped_dt(fs.dt_cur, a.prm.dmax, vm);
+            }
             double dmax = 0.0;
             for (int i = threadIdx.x; i < I.n; i += blockDim.x) {
                 const long long gi = I.off + i;
                 dvec4 x = a.x[gi], v = a.v[gi];
-                fire_update_atom(fs, x, v, a.f[gi]);
+                if (a.prm.dmax > 0.0)
+                    fire_update_drift(fs, dt_drift, x, v, a.f[gi]);
+                else
+                    fire_update_atom(fs, x, v, a.f[gi]);
                 a.x[gi] = x;
                 a.v[gi] = v;
                 a.xf[gi] = make_float4((float)x.x, (float)x.y, (float)x.z, 0.f);
@@ -676,6 +694,7 @@ static fire_status batch_launch(fire_handle_t* h, fire_batch_state* b, double ft
     q.norm = p.norm;
     q.integrator = p.integrator;
     q.variant = p.variant;
+    q.dmax = p.dmax;
     a.budget_ns = (unsigned long long)(fire2_budget(h) * 1e9);
     a.P = fire2_potc(h);
     a.exp_table = fire2_exp_table(h);

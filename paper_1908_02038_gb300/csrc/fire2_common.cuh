@@ -204,6 +204,7 @@ struct FireParamsD {
     long long maxiter;
     double dt_start, dtmax, dtmin, dtgrow, dtshrink, alpha0, alphashrink, mass;
     int delaystep, vdfmax, halfstepback, initialdelay, norm, integrator, variant, pad;
+    double dmax;           // maximum displacement per step, 0 = no cap
 };
 
 // Scalar state of Algorithms 1/2 plus the coefficients the next element-wise
@@ -340,8 +341,11 @@ __device__ inline bool fire_control_step(const FireParamsD& p, FireScal& s, doub
 // (Alg. 2, or v = 0 only for Alg. 1), mixing of v(t) (Algs. 1 and 3), the
 // kick before the drift, mixing of the kicked velocity (Algs. 4-6), the
 // drift x += dt v, and the explicit-Euler kick with the force at x(t).
-__device__ __forceinline__ void fire_update_atom(const FireScal& s, dvec4& x, dvec4& v,
-                                                 const dvec4& f) {
+// The part before the drift (everything the maximum-displacement cap needs
+// to know the drift velocity), then the drift with a given dt and the
+// explicit-Euler kick; fire_update_atom chains the two with the FIRE dt.
+__device__ __forceinline__ void fire_update_pre(const FireScal& s, dvec4& x, dvec4& v,
+                                                const dvec4& f) {
     if (s.lf_init) v = make_dvec4(s.lf_c * f.x, s.lf_c * f.y, s.lf_c * f.z, 0.0);
     if (s.zero_v) {
         x.x -= s.halfstep * v.x;
@@ -364,12 +368,32 @@ __device__ __forceinline__ void fire_update_atom(const FireScal& s, dvec4& x, dv
         v.y = (1.0 - a) * v.y + afv * f.y;
         v.z = (1.0 - a) * v.z + afv * f.z;
     }
-    x.x += s.dt_cur * v.x;
-    x.y += s.dt_cur * v.y;
-    x.z += s.dt_cur * v.z;
+}
+
+__device__ __forceinline__ void fire_update_drift(const FireScal& s, double dt, dvec4& x,
+                                                  dvec4& v, const dvec4& f) {
+    x.x += dt * v.x;
+    x.y += dt * v.y;
+    x.z += dt * v.z;
     v.x += s.kick_after * f.x;
     v.y += s.kick_after * f.y;
     v.z += s.kick_after * f.z;
+}
+
+__device__ __forceinline__ void fire_update_atom(const FireScal& s, dvec4& x, dvec4& v,
+                                                 const dvec4& f) {
+    fire_update_pre(s, x, v, f);
+    fire_update_drift(s, s.dt_cur, x, v, f);
+}
+
+// Drift timestep under the maximum-displacement cap: dmax / max_i |v_i| when
+// dt max_i |v_i| exceeds dmax > 0, else dt.
+__host__ __device__ inline double fire_capped_dt(double dt, double dmax, double vmax2) {
+    if (dmax > 0.0) {
+        const double vmax = sqrt(vmax2);
+        if (dt * vmax > dmax) return dmax / vmax;
+    }
+    return dt;
 }
 
 // Velocity Verlet's second half kick with the new force (Algorithm 6).

@@ -3,10 +3,13 @@
 // One relaxation iteration (Algorithm 2 of Guenole et al. with the
 // semi-implicit Euler integrator of Algorithm 4) is the kernel chain
 //
-//   k_update -> [k_cell_* -> k_nbr_build, only when an atom moved > skin/2]
-//            -> k_density -> k_embed -> k_force      (RGL second-moment EAM)
-//               or k_force_lj                        (Lennard-Jones)
-//            -> k_reduce -> k_control
+//   [k_update_pre, with a maximum displacement per step] -> k_update
+//     -> [k_cell_zero/count/scan/fill/sort -> k_nbr_build, only when an atom
+//         moved > skin/2: a graph IF node set by k_update's last block]
+//     -> FP64:  k_density(_tab) -> k_embed -> k_force_rgl -> k_reduce
+//        FP32-pair: k_density32(_tab) -> k_force32(_tab) (reductions fused)
+//        LJ:    k_force_lj -> k_reduce
+//     -> k_control
 //
 // k_control finishes the FP64 reductions of P = F.v, |F|^2, |v|^2 and the
 // stopping norms (Sec. 3.4), runs the scalar dt / alpha / counter logic of
@@ -36,6 +39,11 @@ struct GeoC {
     float rlist2f;         // (rc + skin + margin)^2, margin covers FP32 rounding
     int full;              // 1 = full list (both directions), 0 = half list
     int Lq[3];             // box lengths in fixed-point units, modulo 2^32
+    // several images of one system in the same box (nudged elastic band):
+    // atoms [k img_n, (k + 1) img_n) form image k and interact only among
+    // themselves; one system: img_n = n
+    int img_n;
+    int ncell_img;         // cells per image (1 in all-pairs mode)
 };
 
 // FIRE parameters (Table 1) and call arguments, device resident.
@@ -48,11 +56,19 @@ struct DevState {
     // reductions of the current (F, v)
     double P, F2, V2, fmax2, finf, energy;
     unsigned long long max_disp2;           // bits of max |x - x_ref|^2 (>= 0)
+    unsigned int upd_blocks;                // k_update blocks finished (last-block test)
+    unsigned long long vmax2;               // bits of max |v_i|^2 before the drift (dmax)
 };
 
 struct Bufs {
     int n, cap, ncell;
     int nb_force, nb_embed, nb_red;
+    const uint8_t* dofmask;   // frozen components per atom (bit d = axis d), or NULL
+    double* eatom;         // per-atom energy (images' energies), or NULL
+    int fused_red;         // 1: the FP32-pair force kernels also reduce (F, v)
+    int accum;             // 1: forces and densities accumulate with atomics (cleared
+                           //    by k_update); 0: force kernels write them whole and
+                           //    also produce the (F, v) reductions
     dvec4 *x, *v, *f, *xref;
     float4* xf;            // FP32 copy of x for the list build
     int4* xq;              // FP32-pair form: x in fixed point (qscale units), modulo 2^32
@@ -153,10 +169,11 @@ __global__ void k_cell_count(Bufs b, GeoC g, int force) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= b.n) return;
     const dvec4 x = b.x[i];
+    b.xf[i] = make_float4((float)x.x, (float)x.y, (float)x.z, 0.f);   // list-build copy
     const int cx = cell_coord(x.x, g.Linv[0], g.nc[0]);
     const int cy = cell_coord(x.y, g.Linv[1], g.nc[1]);
     const int cz = cell_coord(x.z, g.Linv[2], g.nc[2]);
-    const int c = (cx * g.nc[1] + cy) * g.nc[2] + cz;
+    const int c = (i / g.img_n) * g.ncell_img + (cx * g.nc[1] + cy) * g.nc[2] + cz;
     b.cell_of[i] = c;
     atomicAdd(&b.cell_count[c], 1);
 }
@@ -197,13 +214,40 @@ __global__ void k_cell_fill(Bufs b, GeoC g, int force) {
     b.cell_atoms[slot] = i;
 }
 
+// The fill above places a cell's atoms in atomic order; sorting each cell by
+// atom index makes the neighbour lists, and with them every sum over a list,
+// the same from run to run (one thread per cell, ~13 atoms per cell).
+__global__ void k_cell_sort(Bufs b, GeoC g, int force) {
+    if (!need_rebuild(b.st, g, force)) return;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= b.ncell) return;
+    int* a = b.cell_atoms + b.cell_start[c];
+    const int m = b.cell_start[c + 1] - b.cell_start[c];
+    for (int k = 1; k < m; ++k) {
+        const int v = a[k];
+        int j = k - 1;
+        while (j >= 0 && a[j] > v) {
+            a[j + 1] = a[j];
+            --j;
+        }
+        a[j + 1] = v;
+    }
+}
+
 // Candidate test in FP32 (the FP64 unit is ~58x slower on this part): the
 // list radius carries a margin larger than the FP32 rounding of the
 // positions, so every pair closer than rc + skin is kept; the force kernels
 // test r < rc again in FP64.
+__device__ __forceinline__ float4 xf_of(const Bufs& b, int j) {
+    const dvec4 x = b.x[j];
+    return make_float4((float)x.x, (float)x.y, (float)x.z, 0.f);
+}
+
+// FP32 positions come from xf (refreshed by k_cell_count) in cell mode and
+// are converted from x in the all-pairs mode (small systems).
 __device__ __forceinline__ void try_add_pair(const Bufs& b, const GeoC& g, int i, float4 xi,
                                              int j, int& cnt) {
-    const float4 xj = b.xf[j];
+    const float4 xj = g.brute ? xf_of(b, j) : b.xf[j];
     float d[3] = {xj.x - xi.x, xj.y - xi.y, xj.z - xi.z};
     int s[3] = {0, 0, 0};
 #pragma unroll
@@ -235,10 +279,11 @@ __global__ void k_nbr_build(Bufs b, GeoC g, int force) {
     if (i == 0) b.st->nbr_builds += 1;
     if (i >= b.n) return;
     const dvec4 xi = b.x[i];
-    const float4 xif = b.xf[i];
+    const float4 xif = g.brute ? xf_of(b, i) : b.xf[i];
     int cnt = 0;
+    const int img = i / g.img_n;
     if (g.brute) {
-        for (int j = 0; j < b.n; ++j)
+        for (int j = img * g.img_n; j < (img + 1) * g.img_n; ++j)
             if (j != i) try_add_pair(b, g, i, xif, j, cnt);
     } else {
         const int cx = cell_coord(xi.x, g.Linv[0], g.nc[0]);
@@ -250,7 +295,7 @@ __global__ void k_nbr_build(Bufs b, GeoC g, int force) {
                 const int ay = (cy + oy + g.nc[1]) % g.nc[1];
                 for (int oz = -1; oz <= 1; ++oz) {
                     const int az = (cz + oz + g.nc[2]) % g.nc[2];
-                    const int c = (ax * g.nc[1] + ay) * g.nc[2] + az;
+                    const int c = img * g.ncell_img + (ax * g.nc[1] + ay) * g.nc[2] + az;
                     for (int k = b.cell_start[c]; k < b.cell_start[c + 1]; ++k) {
                         const int j = b.cell_atoms[k];
                         if (j != i) try_add_pair(b, g, i, xif, j, cnt);
@@ -325,6 +370,7 @@ __global__ void __launch_bounds__(kForceBlock) k_density(Bufs b, PotC P, GeoC g)
             b.cden[slot] = cden;
         }
         atomicAdd(&b.rho[i], rho_i);
+        if (b.eatom) b.eatom[i] = erep;
     }
     const double s = block_sum(erep, red);
     if (threadIdx.x == 0) b.epart[blockIdx.x] = s;
@@ -335,13 +381,13 @@ __global__ void __launch_bounds__(kForceBlock) k_density(Bufs b, PotC P, GeoC g)
 __global__ void k_embed(Bufs b) {
     __shared__ double red[32];
     if (b.st->done) return;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
     double emb = 0.0;
-    if (i < b.n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < b.n; i += gridDim.x * blockDim.x) {
         const double rho = b.rho[i];
         const double sq = sqrt(rho);
         b.fp[i] = rho > 0.0 ? -0.5 / sq : 0.0;
-        emb = -sq;
+        emb -= sq;
+        if (b.eatom) b.eatom[i] -= sq;
     }
     const double s = block_sum(emb, red);
     if (threadIdx.x == 0) b.epart[b.nb_force + blockIdx.x] = s;
@@ -431,6 +477,7 @@ __global__ void __launch_bounds__(kForceBlock) k_force_lj(Bufs b, PotC P, GeoC g
         atomicAdd(&b.f[i].x, fx);
         atomicAdd(&b.f[i].y, fy);
         atomicAdd(&b.f[i].z, fz);
+        if (b.eatom) b.eatom[i] = epair;
     }
     const double s = block_sum(epair, red);
     if (threadIdx.x == 0) b.epart[blockIdx.x] = s;
@@ -475,6 +522,61 @@ __device__ __forceinline__ long long pair_sep_q(const Bufs& b, const int3* qt, i
     return (long long)dx * dx + (long long)dy * dy + (long long)dz * dz;
 }
 
+// ---------------------------------------------------------------------------
+// Per-atom part of the FP64 reductions of (F, v) (see k_reduce), shared by
+// k_reduce and the force kernels that write whole forces.
+
+struct RedAcc {
+    double P = 0.0, F2 = 0.0, V2 = 0.0, fa2 = 0.0, fin = 0.0;
+};
+
+// Zeroes the frozen components of f (if any); true when f changed.
+__device__ __forceinline__ bool mask_force(const Bufs& b, int i, dvec4& f) {
+    if (!b.dofmask) return false;
+    const unsigned m = b.dofmask[i];
+    if (m & 1u) f.x = 0.0;
+    if (m & 2u) f.y = 0.0;
+    if (m & 4u) f.z = 0.0;
+    return m != 0u;
+}
+
+// Reductions of atom i's (F, v); f must be masked already.
+__device__ __forceinline__ void red_atom(const Bufs& b, int i, const dvec4& f, double vv_half,
+                                         RedAcc& a) {
+    dvec4 v = b.v[i];
+    if (vv_half != 0.0) {   // second half kick of velocity Verlet, with the new force
+        v.x += vv_half * f.x;
+        v.y += vv_half * f.y;
+        v.z += vv_half * f.z;
+        b.v[i] = v;
+    }
+    a.P += f.x * v.x + f.y * v.y + f.z * v.z;
+    const double q = f.x * f.x + f.y * f.y + f.z * f.z;
+    a.F2 += q;
+    a.V2 += v.x * v.x + v.y * v.y + v.z * v.z;
+    a.fa2 = fmax(a.fa2, q);
+    a.fin = fmax(a.fin, fmax(fabs(f.x), fmax(fabs(f.y), fabs(f.z))));
+}
+
+__device__ __forceinline__ void red_write(const RedAcc& a, double* red, double* rpart) {
+    const int nb = gridDim.x;
+    double r;
+    r = block_sum(a.P, red);
+    if (threadIdx.x == 0) rpart[0 * nb + blockIdx.x] = r;
+    r = block_sum(a.F2, red);
+    if (threadIdx.x == 0) rpart[1 * nb + blockIdx.x] = r;
+    r = block_sum(a.V2, red);
+    if (threadIdx.x == 0) rpart[2 * nb + blockIdx.x] = r;
+    r = block_max(a.fa2, red);
+    if (threadIdx.x == 0) rpart[3 * nb + blockIdx.x] = r;
+    r = block_max(a.fin, red);
+    if (threadIdx.x == 0) rpart[4 * nb + blockIdx.x] = r;
+}
+
+__device__ __forceinline__ double vv_half_of(const DevState* st) {
+    return st->fs.vv ? st->fs.vv_half : 0.0;
+}
+
 // Pass 1 (FP32-pair): rho_i, F'(rho_i) = -1/(2 sqrt(rho_i)) and the atom's
 // energy sum_j phi - sqrt(rho_i); the full list makes rho_i complete in one
 // thread, so the embedding step is fused here.
@@ -486,9 +588,8 @@ __global__ void __launch_bounds__(kForceBlock) k_density32(Bufs b, PotC P, GeoC 
     fill_qshift_table(qt, g);
     for (int t = threadIdx.x; t < kExp32TableSize; t += blockDim.x) et[t] = b.exp32_table[t];
     __syncthreads();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
     double e_atom = 0.0;
-    if (i < b.n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < b.n; i += gridDim.x * blockDim.x) {
         const int4 qi = b.xq[i];
         const int m = b.nnbr[i];
         Kahan32 rho, erep;
@@ -506,7 +607,9 @@ __global__ void __launch_bounds__(kForceBlock) k_density32(Bufs b, PotC P, GeoC 
         const float sq = sqrtf(rf);
         b.fp32[i] = rf > 0.f ? -0.5f / sq : 0.f;
         b.rho[i] = rho_d;
-        e_atom = erep.value() - (double)sq;
+        const double ei = erep.value() - (double)sq;
+        if (b.eatom) b.eatom[i] = ei;
+        e_atom += ei;
     }
     const double bs = block_sum(e_atom, red);
     if (threadIdx.x == 0) b.epart[blockIdx.x] = bs;
@@ -517,28 +620,35 @@ __global__ void __launch_bounds__(kForceBlock) k_density32(Bufs b, PotC P, GeoC 
 __global__ void __launch_bounds__(kForceBlock) k_force32(Bufs b, PotC P, GeoC g) {
     __shared__ int3 qt[125];
     __shared__ float et[kExp32TableSize];
+    __shared__ double red[32];
     if (b.st->done) return;
     fill_qshift_table(qt, g);
     for (int t = threadIdx.x; t < kExp32TableSize; t += blockDim.x) et[t] = b.exp32_table[t];
     __syncthreads();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= b.n) return;
-    const int4 qi = b.xq[i];
-    const float fpi = b.fp32[i];
-    const int m = b.nnbr[i];
-    Kahan32 fx, fy, fz;
-    for (int k = 0; k < m; ++k) {
-        int dx, dy, dz, j;
-        const long long r2q = pair_sep_q(b, qt, qi, b.nbr[(size_t)k * b.n + i], dx, dy, dz, j);
-        if (r2q >= P.rc2q) continue;
-        float rinv, phi, dphi, gg, dg;
-        rgl_pair32(P, r2q, et, rinv, phi, dphi, gg, dg);
-        const float fs = (2.f * dphi + (fpi + b.fp32[j]) * dg) * rinv * P.qinv;
-        fx.add(fs * (float)dx);
-        fy.add(fs * (float)dy);
-        fz.add(fs * (float)dz);
+    const double vvh = vv_half_of(b.st);
+    RedAcc acc;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < b.n; i += gridDim.x * blockDim.x) {
+        const int4 qi = b.xq[i];
+        const float fpi = b.fp32[i];
+        const int m = b.nnbr[i];
+        Kahan32 fx, fy, fz;
+        for (int k = 0; k < m; ++k) {
+            int dx, dy, dz, j;
+            const long long r2q = pair_sep_q(b, qt, qi, b.nbr[(size_t)k * b.n + i], dx, dy, dz, j);
+            if (r2q >= P.rc2q) continue;
+            float rinv, phi, dphi, gg, dg;
+            rgl_pair32(P, r2q, et, rinv, phi, dphi, gg, dg);
+            const float fs = (2.f * dphi + (fpi + b.fp32[j]) * dg) * rinv * P.qinv;
+            fx.add(fs * (float)dx);
+            fy.add(fs * (float)dy);
+            fz.add(fs * (float)dz);
+        }
+        dvec4 f = make_dvec4(fx.value(), fy.value(), fz.value(), 0.0);
+        mask_force(b, i, f);
+        b.f[i] = f;
+        if (b.fused_red) red_atom(b, i, f, vvh, acc);
     }
-    b.f[i] = make_dvec4(fx.value(), fy.value(), fz.value(), 0.0);
+    if (b.fused_red) red_write(acc, red, b.rpart);
 }
 
 // ---------------------------------------------------------------------------
@@ -571,7 +681,7 @@ __global__ void __launch_bounds__(kTabBlock64) k_density_tab(Bufs b, PotC P, Geo
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < b.n; i += gridDim.x * blockDim.x) {
         const dvec4 xi = b.x[i];
         const int m = b.nnbr[i];
-        double rho_i = 0.0;
+        double rho_i = 0.0, erep_i = 0.0;
         for (int k = 0; k < m; ++k) {
             const size_t slot = (size_t)k * b.n + i;
             const uint32_t e = b.nbr[slot];
@@ -605,12 +715,14 @@ __global__ void __launch_bounds__(kTabBlock64) k_density_tab(Bufs b, PotC P, Geo
                 }
                 rho_i += gg;
                 atomicAdd(&b.rho[j], gg);
-                erep += 2.0 * phi;
+                erep_i += 2.0 * phi;
             }
             b.crep[slot] = crep;
             b.cden[slot] = cden;
         }
         atomicAdd(&b.rho[i], rho_i);
+        erep += erep_i;
+        if (b.eatom) b.eatom[i] = erep_i;
     }
     const double s = block_sum(erep, red);
     if (threadIdx.x == 0) b.epart[blockIdx.x] = s;
@@ -655,7 +767,9 @@ __global__ void __launch_bounds__(kTabBlock) k_density32_tab(Bufs b, PotC P, Geo
         const float sq = sqrtf(rf);
         b.fp32[i] = rf > 0.f ? -0.5f / sq : 0.f;
         b.rho[i] = rho_d;
-        e_sum += erep.value() - (double)sq;
+        const double ei = erep.value() - (double)sq;
+        if (b.eatom) b.eatom[i] = ei;
+        e_sum += ei;
     }
     const double bs = block_sum(e_sum, red);
     if (threadIdx.x == 0) b.epart[blockIdx.x] = bs;
@@ -666,7 +780,10 @@ __global__ void __launch_bounds__(kTabBlock) k_force32_tab(Bufs b, PotC P, GeoC 
     extern __shared__ float tabf32[];
     __shared__ int3 qt[125];
     __shared__ float et[kExp32TableSize];
+    __shared__ double red[32];
     if (b.st->done) return;
+    const double vvh = vv_half_of(b.st);
+    RedAcc acc;
     fill_qshift_table(qt, g);
     load_table(tabf32, b.tab_f32, (P.tab32.nA + P.tab32.nB) * kTabForce);
     load_table(et, b.exp32_table, kExp32TableSize);
@@ -697,8 +814,12 @@ __global__ void __launch_bounds__(kTabBlock) k_force32_tab(Bufs b, PotC P, GeoC 
             fy.add(fs * (float)dy);
             fz.add(fs * (float)dz);
         }
-        b.f[i] = make_dvec4(fx.value(), fy.value(), fz.value(), 0.0);
+        dvec4 f = make_dvec4(fx.value(), fy.value(), fz.value(), 0.0);
+        mask_force(b, i, f);
+        b.f[i] = f;
+        if (b.fused_red) red_atom(b, i, f, vvh, acc);
     }
+    if (b.fused_red) red_write(acc, red, b.rpart);
 }
 
 // ---------------------------------------------------------------------------
@@ -708,35 +829,14 @@ __global__ void __launch_bounds__(kTabBlock) k_force32_tab(Bufs b, PotC P, GeoC 
 __global__ void k_reduce(Bufs b) {
     __shared__ double red[32];
     if (b.st->done) return;
-    const bool vv = b.st->fs.vv != 0;
-    const FireScal fs = b.st->fs;
-    double P = 0.0, F2 = 0.0, V2 = 0.0, fa2 = 0.0, fin = 0.0;
+    const double vvh = vv_half_of(b.st);
+    RedAcc acc;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < b.n; i += gridDim.x * blockDim.x) {
-        const dvec4 f = b.f[i];
-        dvec4 v = b.v[i];
-        if (vv) {   // second half kick of velocity Verlet, with the new force
-            fire_vv_kick(fs, v, f);
-            b.v[i] = v;
-        }
-        P += f.x * v.x + f.y * v.y + f.z * v.z;
-        const double a2 = f.x * f.x + f.y * f.y + f.z * f.z;
-        F2 += a2;
-        V2 += v.x * v.x + v.y * v.y + v.z * v.z;
-        fa2 = fmax(fa2, a2);
-        fin = fmax(fin, fmax(fabs(f.x), fmax(fabs(f.y), fabs(f.z))));
+        dvec4 f = b.f[i];
+        if (mask_force(b, i, f)) b.f[i] = f;
+        red_atom(b, i, f, vvh, acc);
     }
-    const int nb = gridDim.x;
-    double r;
-    r = block_sum(P, red);
-    if (threadIdx.x == 0) b.rpart[0 * nb + blockIdx.x] = r;
-    r = block_sum(F2, red);
-    if (threadIdx.x == 0) b.rpart[1 * nb + blockIdx.x] = r;
-    r = block_sum(V2, red);
-    if (threadIdx.x == 0) b.rpart[2 * nb + blockIdx.x] = r;
-    r = block_max(fa2, red);
-    if (threadIdx.x == 0) b.rpart[3 * nb + blockIdx.x] = r;
-    r = block_max(fin, red);
-    if (threadIdx.x == 0) b.rpart[4 * nb + blockIdx.x] = r;
+    red_write(acc, red, b.rpart);
 }
 
 // Fixed-order reduction of `cnt` partials by one block (deterministic).
@@ -776,6 +876,7 @@ __global__ void k_control(Bufs b, int mode, cudaGraphConditionalHandle h, int ha
     s.finf = fin;
     s.energy = E;
     s.max_disp2 = 0ull;
+    s.vmax2 = 0ull;
     if (mode == CTL_EVAL) {
         if ((!isfinite(E) || !isfinite(F2)) && s.status == ST_OK) s.status = ST_NONFINITE;
         return;
@@ -802,31 +903,75 @@ __global__ void k_control(Bufs b, int mode, cudaGraphConditionalHandle h, int ha
 // Element-wise part of one iteration: optional half step back and v = 0
 // (P <= 0, Alg. 2), then Algorithm 4: v += dt F / m, mixing
 // v = (1 - alpha) v + alpha |v| F / |F| (P > 0), x += dt v.  Clears F and rho
-// for the next force evaluation and tracks max |x - x_ref|^2.
-__global__ void k_update(Bufs b) {
+// for the next force evaluation (accumulating paths) and tracks
+// max |x - x_ref|^2.  With has_if, the last block to finish sets the graph's
+// IF condition to "the neighbour list must be rebuilt" (see need_rebuild).
+__global__ void k_update(Bufs b, GeoC g, cudaGraphConditionalHandle hif, int has_if,
+                         int after_pre) {
     __shared__ double red[32];
-    if (b.st->done) return;
+    if (b.st->done) {
+        if (has_if && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(hif, 0u);
+        return;
+    }
     const FireScal s = b.st->fs;
-    double dmax = 0.0;
+    // after k_update_pre: only the drift is left, with the capped dt
+    const double dt = after_pre ? fire_capped_dt(s.dt_cur, b.st->prm.dmax,
+                                                 __longlong_as_double((long long)b.st->vmax2))
+                                : s.dt_cur;
+    double d2max = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < b.n; i += gridDim.x * blockDim.x) {
         dvec4 x = b.x[i], v = b.v[i];
         const dvec4 f = b.f[i];
-        fire_update_atom(s, x, v, f);
+        if (after_pre)
+            fire_update_drift(s, dt, x, v, f);
+        else
+            fire_update_atom(s, x, v, f);
         b.x[i] = x;
-        b.xf[i] = make_float4((float)x.x, (float)x.y, (float)x.z, 0.f);
         if (b.xq)
             b.xq[i] = make_int4(to_fixed(x.x, b.qscale), to_fixed(x.y, b.qscale),
                                 to_fixed(x.z, b.qscale), 0);
         b.v[i] = v;
-        b.f[i] = make_dvec4(0.0, 0.0, 0.0, 0.0);
-        if (b.rho) b.rho[i] = 0.0;
+        if (b.accum) {
+            b.f[i] = make_dvec4(0.0, 0.0, 0.0, 0.0);
+            if (b.rho) b.rho[i] = 0.0;
+        }
         const dvec4 r = b.xref[i];
         const double ddx = x.x - r.x, ddy = x.y - r.y, ddz = x.z - r.z;
-        dmax = fmax(dmax, ddx * ddx + ddy * ddy + ddz * ddz);
+        d2max = fmax(d2max, ddx * ddx + ddy * ddy + ddz * ddz);
     }
-    const double bm = block_max(dmax, red);
-    if (threadIdx.x == 0)
+    const double bm = block_max(d2max, red);
+    if (threadIdx.x == 0) {
         atomicMax(&b.st->max_disp2, (unsigned long long)__double_as_longlong(bm));
+        if (has_if) {
+            __threadfence();
+            if (atomicAdd(&b.st->upd_blocks, 1u) == gridDim.x - 1) {
+                b.st->upd_blocks = 0u;
+                const unsigned long long d = atomicAdd(&b.st->max_disp2, 0ull);
+                const bool rebuild = __longlong_as_double((long long)d) > g.half_skin2;
+                cudaGraphSetConditional(hif, rebuild ? 1u : 0u);
+            }
+        }
+    }
+}
+
+// With a maximum displacement per step (dmax > 0) the element-wise step runs
+// in two passes: this one applies everything before the drift and takes
+// max_i |v_i|^2 of the drift velocity; k_update(after_pre = 1) then drifts
+// with fire_capped_dt.
+__global__ void k_update_pre(Bufs b) {
+    __shared__ double red[32];
+    if (b.st->done) return;
+    const FireScal s = b.st->fs;
+    double vm = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < b.n; i += gridDim.x * blockDim.x) {
+        dvec4 x = b.x[i], v = b.v[i];
+        fire_update_pre(s, x, v, b.f[i]);
+        if (s.zero_v) b.x[i] = x;      // the half step back moved x
+        b.v[i] = v;
+        vm = fmax(vm, v.x * v.x + v.y * v.y + v.z * v.z);
+    }
+    const double bm = block_max(vm, red);
+    if (threadIdx.x == 0) atomicMax(&b.st->vmax2, (unsigned long long)__double_as_longlong(bm));
 }
 
 }  // namespace fire2

@@ -120,3 +120,19 @@ def test_batch_rejects_single_system_calls():
             b.minimize(xbad, boxes, 1e-6, 100)
         assert e.value.status == fg.FIRE_ERR_NONFINITE
         assert np.isinf(xbad[3, 0])
+
+
+def test_batch_dmax_relaxations_match_oracle():
+    cfgs = small_batch(n_sys=5, seed=53)
+    x, boxes, counts = pack(cfgs)
+    with fg.FireBatch(counts, fi.CU_MASS, rgl_pot(), dt_start=fi.CU_DT, dmax=0.002) as b:
+        res, _ = b.minimize(x, boxes, 1e-6, 100000)
+    for s, c in enumerate(cfgs):
+        _, ro, _ = oracle.fire2(c.x, c.box, ora_rgl(),
+                                oracle.Params(dt_start=fi.CU_DT, dmax=0.002), fi.CU_MASS, 1e-6,
+                                100000)
+        r = res[s]
+        assert ro.stop == oracle.STOP_FTOL and r.stop == fg.FIRE_STOP_FTOL, s
+        assert abs(r.energy - ro.energy) / c.n < 1e-8, s
+        assert abs(r.iterations - ro.iterations) <= max(2, 0.05 * ro.iterations), \
+            (s, r.iterations, ro.iterations)

@@ -316,6 +316,27 @@ def test_chunked_execution_matches_graph_loop():
     assert r3.stop == fg.FIRE_STOP_MAXITER and r3.iterations == 50 and r3.force_evals == 51
 
 
+def test_fp32pair_graph_and_chunked_runs_are_identical():
+    # The FP32-pair passes write whole forces and sum in a fixed order, so the
+    # graph loop (rebuild decided by the update kernel's last block, build
+    # chain under an IF node) and the chunked loop (every build kernel tests
+    # the displacement itself) must follow the same trajectory bit for bit.
+    c = fi.rgl_vacancy_box(ncell=12, seed=14, n_vac=4, sigma=0.1)
+    pot = rgl_pot(precision=fg.FIRE_PREC_FP32_PAIR)
+    with fg.FireHandle(c.n, fi.CU_MASS, pot, dt_start=fi.CU_DT) as h:
+        x1 = c.x.copy()
+        r1 = h.minimize(x1, c.box, 1e-6, 100000)
+        h.set_exec_mode(fg.FIRE_EXEC_CHUNKED, 16)
+        x2 = c.x.copy()
+        r2 = h.minimize(x2, c.box, 1e-6, 100000)
+    assert r1.stop == r2.stop == fg.FIRE_STOP_FTOL
+    assert r1.nbr_builds > 2
+    assert (r1.iterations, r1.nbr_builds, r1.force_evals) == (r2.iterations, r2.nbr_builds,
+                                                               r2.force_evals)
+    assert r1.energy == r2.energy
+    assert np.array_equal(x1, x2)
+
+
 # ----------------------------------------------------------------------------
 # FP32-pair form (pair/embedding math FP32; positions, sums, control FP64)
 
@@ -453,3 +474,86 @@ def test_compressed_pairs_fall_back_to_analytic_terms():
         e, f = h.energy_forces(x, box)
     assert force_rel_err(f, fo) < F_REL
     assert e == pytest.approx(eo, rel=E_REL)
+
+
+# ----------------------------------------------------------------------------
+# maximum displacement per step (dmax) and frozen degrees of freedom
+
+@pytest.mark.parametrize("integ", [fg.FIRE_INT_EULER_IMPLICIT, fg.FIRE_INT_VERLET])
+def test_dmax_state_after_60_iterations_matches_oracle(integ):
+    c = fi.rgl_vacancy_box(ncell=4, seed=91, n_vac=2, sigma=0.1)
+    prm = dict(dt_start=fi.CU_DT, integrator=integ, dmax=0.003)
+    xo, ro, _ = oracle.fire2(c.x, c.box, ora_rgl(), oracle.Params(**prm), fi.CU_MASS, 1e-12, 60)
+    x = c.x.copy()
+    with fg.FireHandle(c.n, fi.CU_MASS, rgl_pot(), **prm) as h:
+        r = h.minimize(x, c.box, 1e-12, 60)
+    assert r.stop == ro.stop == fg.FIRE_STOP_MAXITER
+    assert r.dt_final == pytest.approx(ro.dt_final, rel=1e-12)
+    assert np.abs(x - xo).max() < 1e-9
+    assert r.energy == pytest.approx(ro.energy, rel=1e-12)
+
+
+@pytest.mark.parametrize("mode", [fg.FIRE_EXEC_GRAPH_WHILE, fg.FIRE_EXEC_CHUNKED])
+def test_dmax_relaxation_parity(mode):
+    c = fi.rgl_vacancy_box(ncell=5, seed=92, n_vac=2, sigma=0.1)
+    xo, ro, _ = oracle.fire2(c.x, c.box, ora_rgl(), oracle.Params(dt_start=fi.CU_DT, dmax=0.002),
+                             fi.CU_MASS, 1e-6, 100000)
+    x = c.x.copy()
+    with fg.FireHandle(c.n, fi.CU_MASS, rgl_pot(), dt_start=fi.CU_DT, dmax=0.002) as h:
+        h.set_exec_mode(mode, 16)
+        r = h.minimize(x, c.box, 1e-6, 100000)
+    assert_relax_parity(c, r, ro, 1e-6)
+
+
+def frozen_slab(c):
+    fz = np.zeros(c.n, np.uint8)
+    fz[c.x[:, 0] < 4.0] = 3          # frozen in x and y
+    fz[c.x[:, 0] > c.box[0] - 3.0] = 4   # frozen in z
+    return fz
+
+
+@pytest.mark.parametrize("precision", [fg.FIRE_PREC_FP64, fg.FIRE_PREC_FP32_PAIR])
+def test_frozen_dofs_relaxation_parity(precision):
+    c = fi.rgl_vacancy_box(ncell=6, seed=93, n_vac=3, sigma=0.05)
+    fz = frozen_slab(c)
+    xo, ro, _ = oracle.fire2(c.x, c.box, ora_rgl(), oracle.Params(dt_start=fi.CU_DT), fi.CU_MASS,
+                             1e-6, 100000, frozen=fz)
+    x = c.x.copy()
+    with fg.FireHandle(c.n, fi.CU_MASS, rgl_pot(precision=precision), dt_start=fi.CU_DT) as h:
+        h.set_dof_mask(fz)
+        r = h.minimize(x, c.box, 1e-6, 100000)
+        # forces from an evaluation are the full forces, mask or not
+        e_m, f_m = h.energy_forces(x, c.box)
+        h.set_dof_mask(None)
+        e_u, f_u = h.energy_forces(x, c.box)
+    for d in range(3):
+        sel = (fz >> d) & 1 == 1
+        assert np.array_equal(x[sel, d], c.x[sel, d]), d
+    # (equal up to the order of the FP64 atomic sums)
+    assert np.abs(f_m - f_u).max() <= 1e-12 * np.abs(f_u).max()
+    assert e_m == pytest.approx(e_u, rel=1e-13)
+    if precision == fg.FIRE_PREC_FP64:
+        assert_relax_parity(c, r, ro, 1e-6)
+    else:
+        assert r.stop == fg.FIRE_STOP_FTOL
+        assert abs(r.energy - ro.energy) / c.n < E32_PER_ATOM
+
+
+def test_frozen_mask_changes_take_effect_and_bad_masks_are_rejected():
+    c = fi.rgl_vacancy_box(ncell=4, seed=94, n_vac=1, sigma=0.05)
+    with fg.FireHandle(c.n, fi.CU_MASS, rgl_pot(), dt_start=fi.CU_DT) as h:
+        r0 = h.minimize(c.x.copy(), c.box, 1e-6, 100000)
+        h.set_dof_mask(np.full(c.n, 7, np.uint8))     # everything frozen
+        x = c.x.copy()
+        r1 = h.minimize(x, c.box, 1e-6, 100000)
+        assert r1.iterations == 0 and r1.stop == fg.FIRE_STOP_FTOL and np.array_equal(x, c.x)
+        bad = np.zeros(c.n, np.uint8)
+        bad[5] = 8
+        with pytest.raises(fg.FireError) as e:
+            h.set_dof_mask(bad)
+        assert e.value.status == fg.FIRE_ERR_ARG
+        h.set_dof_mask(None)
+        r2 = h.minimize(c.x.copy(), c.box, 1e-6, 100000)
+    # (FP64 atomics: the two runs may differ in the last bits)
+    assert abs(r2.iterations - r0.iterations) <= 2
+    assert abs(r2.energy - r0.energy) / c.n < 1e-10
