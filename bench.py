@@ -34,6 +34,7 @@ import fire_inputs as fi  # noqa: E402
 METRIC = "FIRE2 atom-iters/s & time-to-ftol, EAM 1M atoms, 1 GB300; HBM roofline fraction"
 UNIT = "atom-iters/s"
 FTOL = 1e-6
+FP32_FORCE_ERR = 1e-7
 MAXITER = 200000
 CONFIGS = {
     "rgl1m": lambda: fi.rgl_void_box(),
@@ -79,6 +80,8 @@ def parse():
                          "tables for fp64, exponentials for fp32pair, the faster of each)")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the second form (FP32-pair next to FP64 and vice versa)")
+    ap.add_argument("--no-neb", action="store_true",
+                    help="skip the nudged-elastic-band line (vacancy hop, 6 images)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--exec", default="graph", choices=["graph", "chunked"],
                     help="graph: one CUDA graph with a WHILE node per relaxation (default); "
@@ -104,8 +107,11 @@ def potential_for(cfg_name, form="fp64"):
         return (fg.Potential(fg.FIRE_POT_LJ, eps=1.0, sigma=1.0, rc_lj=2.5, skin=0.3),
                 fi.LJ_MASS, fi.LJ_DT, 1e-8)
     prec = fg.FIRE_PREC_FP32_PAIR if form == "fp32pair" else fg.FIRE_PREC_FP64
+    # the FP32-pair form stops at ftol less its force error bound (1e-7 eV/A,
+    # tests), so that its structure meets ftol when re-evaluated in FP64
+    ftol = FTOL - FP32_FORCE_ERR if form == "fp32pair" else FTOL
     return (fg.Potential(fg.FIRE_POT_RGL, precision=prec, skin=0.3, **fi.RGL_CU), fi.CU_MASS,
-            fi.CU_DT, FTOL)
+            fi.CU_DT, ftol)
 
 
 def count_pairs(x, box, rc):
@@ -244,6 +250,51 @@ def launches_of(results, is_rgl, fp32, cell_mode):
         total += (1 + force_k + reduce_k + 1) * rr["iterations"]
         total += build_k * max(0, rr["nbr_builds"] - 1)
     return total
+
+
+def neb_block(fg, torch, form, dev):
+    """Nudged elastic band of a vacancy hop in a 12^3-cell Cu box (6,911
+    atoms, the size of the paper's NEB case 7) with 6 movable images and a
+    climbing image, relaxed to 1e-4 eV/A on the NEB forces; end states
+    relaxed first (FP64).  Reports atom-iterations over all images per
+    second and the barrier; the climbing image is checked in FP64."""
+    c = fi.neb_vacancy_hop(ncell=12, seed=6, n_img=6)
+    n, m = c.x.shape[1], 6
+    pot, mass, dt, _ = potential_for("rgl1m", form)
+    pot.pair_eval = fg.FIRE_PAIR_ANALYTIC if default_pair(form) == "analytic" else fg.FIRE_PAIR_TABLE
+    pot64, _, _, _ = potential_for("rgl1m", "fp64")
+    path = c.x.copy()
+    with fg.FireHandle(n, mass, pot64, dt_start=dt) as h:
+        for e in (0, -1):
+            x = np.ascontiguousarray(path[e])
+            r = h.minimize(x, c.box, 1e-8, 100000)
+            path[e] = x
+    t = np.linspace(0.0, 1.0, m + 2)[:, None, None]
+    path = np.ascontiguousarray(path[0][None] + t * (path[-1] - path[0])[None])
+    d0 = torch.tensor(path, dtype=torch.float64, device=dev)
+    d = torch.empty_like(d0)
+    with fg.FireNEB(m, n, mass, pot, 1.0, True, dt_start=dt) as h:
+        for _ in range(2):
+            d.copy_(d0)
+            h.minimize_dev(d, c.box, 1e-4, 100000)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        d.copy_(d0)
+        ev0.record()
+        r, E, cl = h.minimize_dev(d, c.box, 1e-4, 100000)
+        ev1.record()
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    with fg.FireHandle(n, mass, pot64, dt_start=dt) as h:
+        e_cl, f_cl = h.energy_forces(d[cl].cpu().numpy(), c.box)
+        e_0, _ = h.energy_forces(path[0], c.box)
+    return {"workload": f"vacancy hop in Cu 12^3 cells ({n} atoms), {m} images + climbing "
+                        "image, NEB forces < 1e-4 eV/A", "form": form,
+            "value": n * m * r.iterations / (ms * 1e-3), "unit": UNIT, "ms": ms,
+            "iterations": r.iterations, "climbing_image": cl,
+            "barrier_eV": float(E[cl] - E[0]),
+            "barrier_fp64_check_eV": float(e_cl - e_0),
+            "climbing_image_fp64_max_force": float(np.linalg.norm(f_cl, axis=1).max())}
 
 
 def run_gpu(args):
@@ -385,6 +436,8 @@ def run_gpu(args):
             "final_fmax_atom_fp64_check": f64_fmax,
             "energy_per_atom_fp64_check": e64 / n,
             "energy_per_atom_diff_vs_headline": (e64 - e64_head) / n}}
+    if is_rgl and not args.no_neb and world == 1:
+        out["neb"] = neb_block(fg, torch, args.form, dev)
     if rank == 0:
         if world == 1 and not args.no_cpu:
             out["cpu_baseline"] = cpu_baseline(cfg, args)

@@ -92,7 +92,7 @@ struct fire_handle {
     fire_batch_state* batch = nullptr;   // set for handles made by fire_batch_init
     GradState grad;
     // tabulated pair functions: device copies and launch shapes
-    double *tab_d64 = nullptr, *tab_f64 = nullptr;
+    double* tab_s64 = nullptr;
     float *tab_d32 = nullptr, *tab_f32 = nullptr;
     size_t smem_d = 0, smem_f = 0;
     int nb_tab_d = 0, nb_tab_f = 0;
@@ -669,25 +669,23 @@ static fire_status upload_tables(fire_handle* h) {
     const RglTables T32 = build_rgl_tables(p.A, p.xi, p.p, p.q, p.r0, p.rs, p.rc, 0.12);
     h->potc.tab = T.meta;
     h->potc.tab32 = T32.meta;
-    const size_t nd = T.dens64.size(), nf = T.force64.size();
+    const std::vector<double> S = build_split_table(T);
+    const size_t ns = S.size();
     const size_t nd32 = T32.dens32.size(), nf32 = T32.force32.size();
-    if (!h->tab_d64) {
-        CK(h, cudaMalloc(&h->tab_d64, nd * sizeof(double)));
-        CK(h, cudaMalloc(&h->tab_f64, nf * sizeof(double)));
+    if (!h->tab_s64) {
+        CK(h, cudaMalloc(&h->tab_s64, ns * sizeof(double)));
         CK(h, cudaMalloc(&h->tab_d32, nd32 * sizeof(float)));
         CK(h, cudaMalloc(&h->tab_f32, nf32 * sizeof(float)));
     }
-    CK(h, cudaMemcpy(h->tab_d64, T.dens64.data(), nd * sizeof(double), cudaMemcpyHostToDevice));
-    CK(h, cudaMemcpy(h->tab_f64, T.force64.data(), nf * sizeof(double), cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpy(h->tab_s64, S.data(), ns * sizeof(double), cudaMemcpyHostToDevice));
     CK(h, cudaMemcpy(h->tab_d32, T32.dens32.data(), nd32 * sizeof(float), cudaMemcpyHostToDevice));
     CK(h, cudaMemcpy(h->tab_f32, T32.force32.data(), nf32 * sizeof(float), cudaMemcpyHostToDevice));
-    h->b.tab_d64 = h->tab_d64;
-    h->b.tab_f64 = h->tab_f64;
+    h->b.tab_s64 = h->tab_s64;
     h->b.tab_d32 = h->tab_d32;
     h->b.tab_f32 = h->tab_f32;
     const bool f32 = p.precision == FIRE_PREC_FP32_PAIR;
-    // FP64: one kernel holds both tables; FP32: one table per kernel
-    h->smem_d = f32 ? nd32 * sizeof(float) : (nd + nf) * sizeof(double);
+    // FP64: one kernel holds the split rows; FP32: one table per kernel
+    h->smem_d = f32 ? nd32 * sizeof(float) : ns * sizeof(double);
     h->smem_f = f32 ? nf32 * sizeof(float) : 0;
     const int block = f32 ? kTabBlock : kTabBlock64;
     const void* kd = f32 ? (const void*)k_density32_tab : (const void*)k_density_tab;
@@ -811,9 +809,10 @@ static fire_status init_handle(fire_handle_t** hp, const fire_system_t* sys,
             b.nb_red = h->nb_tab_f;
         }
     } else if (fp32pair) {
-        int occ = 0;
-        CKI(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_force32, kForceBlock, 0));
-        b.nb_force = std::max(1, std::min(ceil_div(h->n, kForceBlock), sms * std::max(occ, 1)));
+        // one atom per thread: the hardware block scheduler evens out the
+        // uneven neighbour counts (void surfaces) better than a grid-stride
+        // loop over a device-sized grid
+        b.nb_force = ceil_div(h->n, kForceBlock);
         b.nb_red = b.nb_force;
     }
     CKI(cudaMalloc(&b.x, n * sizeof(dvec4)));
@@ -897,7 +896,7 @@ void fire_destroy(fire_handle_t* h) {
         if (p) cudaFree(p);
     if (h->batch) fire2_batch_free(h->batch);
     if (h->neb) neb_free(h->neb);
-    for (void* p : {(void*)h->tab_d64, (void*)h->tab_f64, (void*)h->tab_d32, (void*)h->tab_f32,
+    for (void* p : {(void*)h->tab_s64, (void*)h->tab_d32, (void*)h->tab_f32,
                     (void*)h->dofmask})
         if (p) cudaFree(p);
     {
@@ -1259,7 +1258,7 @@ fire_status fire_set_rgl_params(fire_handle_t* h, const double theta[4]) {
     h->pot.p = theta[2];
     h->pot.q = theta[3];
     fill_potc(h);
-    if (h->tab_d64) {
+    if (h->tab_s64) {
         st = upload_tables(h);
         if (st != FIRE_OK) return st;
     }
@@ -1415,20 +1414,19 @@ fire_status fire_diag_rgl_table(const fire_potential_t* pot, int64_t n, const do
         return FIRE_ERR_ARG;
     const RglTables T = build_rgl_tables(pot->A, pot->xi, pot->p, pot->q, pot->r0, pot->rs,
                                          pot->rc, 0.04);
+    const std::vector<double> S = build_split_table(T);
     for (int64_t i = 0; i < n; ++i) {
         const double u = r[i] * r[i] - pot->r0 * pot->r0;
-        int k;
-        double t;
+        double v[4];
         double* o = out + 4 * i;
         if (!(r[i] < pot->rc)) {
             o[0] = o[1] = o[2] = o[3] = 0.0;
-        } else if (tab_locate(T.meta, u, k, t)) {
-            const double* cd = T.dens64.data() + (size_t)k * kTabDens;
-            const double* cf = T.force64.data() + (size_t)k * kTabForce;
-            o[0] = poly5(cd, t);
-            o[1] = poly5(cd + 6, t);
-            o[2] = 2.0 * r[i] * poly5(cf, t);
-            o[3] = 2.0 * r[i] * poly5(cf + 6, t);
+        } else if (split_eval(T.meta, S.data(), u, v)) {
+            // the FP64 kernel's arithmetic: (2 phi, g, 2 phi'/r, g'/r)
+            o[0] = 0.5 * v[0];
+            o[1] = v[1];
+            o[2] = 0.5 * r[i] * v[2];
+            o[3] = r[i] * v[3];
         } else {
             double a[8];
             rgl_analytic(pot->A, pot->xi, pot->p, pot->q, pot->r0, pot->rs, pot->rc, r[i], a);

@@ -78,7 +78,7 @@ struct Bufs {
     double *rho, *fp;
     const double* exp_table;  // 2^(j/256), j = 0..255
     // tabulated RGL pair functions (fire2_table.cuh); nullptr when analytic
-    const double *tab_d64, *tab_f64;
+    const double* tab_s64;     // FP64 split table rows (kSplitRow doubles each)
     const float *tab_d32, *tab_f32;
     uint32_t *nbr;
     int *nnbr;
@@ -662,19 +662,17 @@ __device__ __forceinline__ void load_table(T* dst, const T* src, int count) {
 }
 
 // FP64 pass 1 (half list): rho_i, rho_j (atomics), 2 phi per pair, and the
-// pair cache of pass 2 (2 phi'/r = 4 phi_u, g'/r = 2 g_u) from the tables.
+// pair cache of pass 2 (2 phi'/r, g'/r) from the split-precision table rows
+// (split_eval: FP64 where 53 bits matter, FP32 for the high-order terms).
 __global__ void __launch_bounds__(kTabBlock64) k_density_tab(Bufs b, PotC P, GeoC g) {
-    extern __shared__ double tabs[];   // density table, then force table
+    extern __shared__ double tabs[];   // split rows
     __shared__ double3 tbl[125];
     __shared__ double etab[kExpTableSize];
     __shared__ double red[32];
     if (b.st->done) return;
     const int nint = P.tab.nA + P.tab.nB;
-    double* tabd = tabs;
-    double* tabf = tabs + nint * kTabDens;
     fill_shift_table(tbl, g);
-    load_table(tabd, b.tab_d64, nint * kTabDens);
-    load_table(tabf, b.tab_f64, nint * kTabForce);
+    load_table(tabs, b.tab_s64, nint * kSplitRow);
     load_table(etab, b.exp_table, kExpTableSize);
     __syncthreads();
     double erep = 0.0;
@@ -698,24 +696,20 @@ __global__ void __launch_bounds__(kTabBlock64) k_density_tab(Bufs b, PotC P, Geo
             const double r2 = dx * dx + dy * dy + dz * dz;
             double crep = 0.0, cden = 0.0;
             if (r2 < P.rc2) {
-                int ki;
-                double t, phi, gg;
-                if (tab_locate(P.tab, r2 - P.r0sq, ki, t)) {
-                    const double* cd = tabd + ki * kTabDens;
-                    const double* cf = tabf + ki * kTabForce;
-                    phi = poly5(cd, t);
-                    gg = poly5(cd + 6, t);
-                    crep = 4.0 * poly5(cf, t);
-                    cden = 2.0 * poly5(cf + 6, t);
-                } else {
-                    double rinv, dphi, dg;
+                double v[4];
+                if (!split_eval(P.tab, tabs, r2 - P.r0sq, v)) {
+                    double rinv, phi, dphi, gg, dg;
                     rgl_pair64(P, r2, etab, rinv, phi, dphi, gg, dg);
-                    crep = 2.0 * dphi * rinv;
-                    cden = dg * rinv;
+                    v[0] = 2.0 * phi;
+                    v[1] = gg;
+                    v[2] = 2.0 * dphi * rinv;
+                    v[3] = dg * rinv;
                 }
-                rho_i += gg;
-                atomicAdd(&b.rho[j], gg);
-                erep_i += 2.0 * phi;
+                rho_i += v[1];
+                atomicAdd(&b.rho[j], v[1]);
+                erep_i += v[0];
+                crep = v[2];
+                cden = v[3];
             }
             b.crep[slot] = crep;
             b.cden[slot] = cden;

@@ -27,6 +27,7 @@
 #pragma once
 
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 #include "fire2_common.cuh"
@@ -223,6 +224,152 @@ __host__ __device__ __forceinline__ T poly5(const T* c, T t) {
 template <typename T>
 __host__ __device__ __forceinline__ T poly4(const T* c, T t) {
     return (((c[4] * t + c[3]) * t + c[2]) * t + c[1]) * t + c[0];
+}
+
+}  // namespace fire2
+
+namespace fire2 {
+
+// ---------------------------------------------------------------------------
+// FP64 table rows with few FP64 instructions.
+//
+// FP64 instructions issue at 1/58 of the FP32 rate on this part, so the FP64
+// density pass spends FP64 only where 53 bits are needed.  With s = u - u_k
+// the offset from the interval start, each quintic is evaluated as
+//   f = c0 + s (c1 + s (c2 + s q)),   q = c3 + s (c4 + s c5)
+// where q is computed in FP32 from float copies of c3..c5 and a float copy
+// of s.  On these tables |s c_{j+1} / c_j| < ~0.07, so s^3 q is < ~1e-4 of f
+// and its FP32 rounding (~1e-7 relative) enters f at ~1e-11 relative or
+// less; c0..c2, s and the three FMAs stay FP64.  The float copies of s and
+// q cross between the formats by integer operations on the IEEE-754 fields
+// (no FP64 conversion instruction).  Interval indices come from an FP32 copy
+// of u; an index one off at an interval edge only moves s by ~1e-6 of the
+// interval outside [0, h], where the quintic is still accurate.
+//
+// Row layout (kSplitRow doubles = 160 bytes): [0] u_k; [1 + 3p + j] = c_j
+// of polynomial p (j = 0..2); [13] unused; then 12 floats at double offset
+// 14: c3, c4, c5 of p = 0..3.  Polynomials (in s, coefficients divided by
+// h^j): p = 0: 2 phi, 1: g, 2: 4 phi_u = 2 phi'/r, 3: 2 g_u = g'/r.
+
+constexpr int kSplitRow = 20;
+
+__host__ __device__ __forceinline__ void dbl_words(double d, unsigned& hi, unsigned& lo) {
+#ifdef __CUDA_ARCH__
+    hi = (unsigned)__double2hiint(d);
+    lo = (unsigned)__double2loint(d);
+#else
+    unsigned long long b;
+    std::memcpy(&b, &d, sizeof b);
+    hi = (unsigned)(b >> 32);
+    lo = (unsigned)b;
+#endif
+}
+
+__host__ __device__ __forceinline__ double dbl_from_words(unsigned hi, unsigned lo) {
+#ifdef __CUDA_ARCH__
+    return __hiloint2double((int)hi, (int)lo);
+#else
+    const unsigned long long b = ((unsigned long long)hi << 32) | lo;
+    double d;
+    std::memcpy(&d, &b, sizeof d);
+    return d;
+#endif
+}
+
+__host__ __device__ __forceinline__ float flt_from_bits(unsigned b) {
+#ifdef __CUDA_ARCH__
+    return __uint_as_float(b);
+#else
+    float f;
+    std::memcpy(&f, &b, sizeof f);
+    return f;
+#endif
+}
+
+__host__ __device__ __forceinline__ unsigned flt_bits(float f) {
+#ifdef __CUDA_ARCH__
+    return __float_as_uint(f);
+#else
+    unsigned b;
+    std::memcpy(&b, &f, sizeof b);
+    return b;
+#endif
+}
+
+// double -> float by truncating the significand (exponent rebiased by
+// 1023 - 127 = 896); magnitudes below 2^-126 give +-0, none here exceed 2^127.
+__host__ __device__ __forceinline__ float f64_to_f32_trunc(double d) {
+    unsigned hi, lo;
+    dbl_words(d, hi, lo);
+    const unsigned sgn = hi & 0x80000000u, ahi = hi & 0x7fffffffu;
+    if (ahi < (897u << 20)) return flt_from_bits(sgn);
+    return flt_from_bits(sgn | ((ahi - (896u << 20)) << 3) | (lo >> 29));
+}
+
+// float -> double, exact for normal floats (zero and subnormals give +-0).
+__host__ __device__ __forceinline__ double f32_to_f64(float f) {
+    const unsigned b = flt_bits(f), a = b & 0x7fffffffu;
+    if (a < 0x00800000u) return dbl_from_words(b & 0x80000000u, 0u);
+    return dbl_from_words((b & 0x80000000u) | ((a >> 3) + (896u << 20)), a << 29);
+}
+
+__host__ __device__ __forceinline__ double split_poly(const double* c, const float* cf, double s,
+                                                      float sf) {
+    const float q = fmaf(fmaf(cf[2], sf, cf[1]), sf, cf[0]);
+    double r = fma(s, f32_to_f64(q), c[2]);
+    r = fma(s, r, c[1]);
+    return fma(s, r, c[0]);
+}
+
+// Interval of u (from its FP32 copy uf), clamped to the table.
+__host__ __device__ __forceinline__ int split_index(const TabMeta& m, float uf) {
+    int k = uf < m.u_rs_f ? m.nA0 + (int)floorf(uf * m.hA_inv_f)
+                          : m.nA + (int)floorf((uf - m.u_rs_f) * m.hB_inv_f);
+    const int last = m.nA + m.nB - 1;
+    return k < 0 ? 0 : (k > last ? last : k);
+}
+
+// out = (2 phi, g, 2 phi'/r, g'/r) at u = r^2 - r0^2; false below the table
+// (u < u_lo: the caller uses the analytic functions).
+__host__ __device__ __forceinline__ bool split_eval(const TabMeta& m, const double* tab, double u,
+                                                    double out[4]) {
+    const float uf = f64_to_f32_trunc(u);
+    if (uf < m.u_lo_f) return false;
+    const double* row = tab + (size_t)split_index(m, uf) * kSplitRow;
+    const float* rf = reinterpret_cast<const float*>(row + 14);
+    const double s = u - row[0];
+    const float sf = f64_to_f32_trunc(s);
+    for (int p = 0; p < 4; ++p) out[p] = split_poly(row + 1 + 3 * p, rf + 3 * p, s, sf);
+    return true;
+}
+
+// Rows from the Hermite coefficients of build_rgl_tables (in t = s / h).
+inline std::vector<double> build_split_table(const RglTables& T) {
+    const TabMeta& m = T.meta;
+    const int nint = m.nA + m.nB;
+    std::vector<double> out((size_t)nint * kSplitRow, 0.0);
+    const double hA = 1.0 / m.hA_inv, hB = 1.0 / m.hB_inv;
+    const double scale[4] = {2.0, 1.0, 4.0, 2.0};
+    for (int i = 0; i < nint; ++i) {
+        const double h = i < m.nA ? hA : hB;
+        const double uk = i < m.nA ? (i - m.nA0) * hA : m.u_rs + (i - m.nA) * hB;
+        double* row = out.data() + (size_t)i * kSplitRow;
+        float* rf = reinterpret_cast<float*>(row + 14);
+        row[0] = uk;
+        for (int p = 0; p < 4; ++p) {
+            const double* c = (p < 2 ? T.dens64.data() + (size_t)i * kTabDens + 6 * p
+                                     : T.force64.data() + (size_t)i * kTabForce + 6 * (p - 2));
+            double hp = 1.0;
+            double cs[6];
+            for (int j = 0; j < 6; ++j) {
+                cs[j] = scale[p] * c[j] / hp;
+                hp *= h;
+            }
+            for (int j = 0; j < 3; ++j) row[1 + 3 * p + j] = cs[j];
+            for (int j = 0; j < 3; ++j) rf[3 * p + j] = (float)cs[3 + j];
+        }
+    }
+    return out;
 }
 
 }  // namespace fire2

@@ -126,5 +126,5 @@ def test_neb_rejects_wrong_calls():
         with pytest.raises(ValueError):
             h.minimize(path[:3].copy(), c.box, 1e-6, 10)
     with pytest.raises(fg.FireError) as e:
-        fg.FireNEB(0, 10, fi.CU_MASS, rgl_pot(), 1.0)
+        fg.FireNEB(0, 10, fi.CU_MASS, rgl_pot(), 1.0, dt_start=fi.CU_DT)
     assert e.value.status == fg.FIRE_ERR_ARG
