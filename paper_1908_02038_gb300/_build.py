@@ -37,7 +37,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(LIB_DIR, exist_ok=True)
     cuda = os.environ.get("CUDA_HOME", "/usr/local/cuda")
     tmp = LIB_PATH + f".tmp{os.getpid()}"
-    cmd = [_nvcc(), ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
+    # host code: no FMA contraction, so host-side evaluations of the device
+    # arithmetic (table diagnostics) round the same way on x86 and Arm hosts
+    cmd = [_nvcc(), ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC",
+           "-Xcompiler", "-ffp-contract=off", "-shared",
            "-cudart", "shared", f"-I{INCLUDE}", *_sources(), "-o", tmp,
            "-Xlinker", f"-rpath,{os.path.join(cuda, 'lib64')}"]
     if verbose:

@@ -282,6 +282,8 @@ NebC neb_consts(const fire_handle* h) {
     return c;
 }
 
+// The FP64 reductions of (F, v); for NEB handles the projection that ends
+// with them.
 void launch_reduce(fire_handle* h, const GeoC& g, cudaStream_t s) {
     if (h->neb) {   // nudged elastic band: project, then reduce (F^NEB, v)
         const NebC c = neb_consts(h);
@@ -290,7 +292,7 @@ void launch_reduce(fire_handle* h, const GeoC& g, cudaStream_t s) {
         k_neb_project<<<h->neb->nb_proj, kNebBlock, 0, s>>>(h->b, g, c);
         return;
     }
-    if (h->b.accum) k_reduce<<<h->b.nb_red, kElemBlock, 0, s>>>(h->b);
+    k_reduce<<<h->b.nb_red, kElemBlock, 0, s>>>(h->b);
 }
 
 int update_grid(int n) { return std::max(1, std::min(ceil_div(n, kElemBlock), 152 * 8)); }
@@ -623,6 +625,8 @@ static bool fill_potc(fire_handle* h) {
     }
     c.rc2 = pot->rc * pot->rc;
     c.r0sq = pot->r0 * pot->r0;
+    c.r0sq_f = (float)c.r0sq;
+    c.rc2_f = (float)c.rc2;
     c.A = pot->A;
     c.xi2 = pot->xi * pot->xi;
     c.xi_inv = 1.0 / pot->xi;
@@ -669,7 +673,7 @@ static fire_status upload_tables(fire_handle* h) {
     const RglTables T32 = build_rgl_tables(p.A, p.xi, p.p, p.q, p.r0, p.rs, p.rc, 0.12);
     h->potc.tab = T.meta;
     h->potc.tab32 = T32.meta;
-    const std::vector<double> S = build_split_table(T);
+    const std::vector<double> S = build_split_table(T, p.r0);
     const size_t ns = S.size();
     const size_t nd32 = T32.dens32.size(), nf32 = T32.force32.size();
     if (!h->tab_s64) {
@@ -790,13 +794,14 @@ static fire_status init_handle(fire_handle_t** hp, const fire_system_t* sys,
     b.n = h->n;
     int sms = 0;
     CKI(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
-    // Grids.  One-atom-per-thread kernels (FP64 density/force, LJ) use
-    // ceil(n / kForceBlock) blocks; the grid-stride kernels use what fits on
-    // the device at once, which keeps the partial sums the control kernel adds
-    // up few.  nb_force + nb_embed energy partials, nb_red rows of the (F, v)
-    // reductions.
+    // Grids.  The pair kernels run one atom per thread on ceil(n / kForceBlock)
+    // blocks (the block scheduler evens out uneven neighbour counts), except
+    // the table kernels, which hold their tables in shared memory and loop
+    // over atoms on a device-sized grid (upload_tables); the element-wise
+    // kernels use device-sized grids too, which keeps the partial sums the
+    // control kernel adds up few.  nb_force + nb_embed energy partials,
+    // nb_red rows of the (F, v) reductions.
     b.accum = fp32pair ? 0 : 1;
-    b.fused_red = fp32pair ? 1 : 0;
     b.nb_force = ceil_div(h->n, kForceBlock);
     b.nb_embed = (pot->kind == FIRE_POT_RGL && !fp32pair)
                      ? std::max(1, std::min(ceil_div(h->n, kElemBlock), sms * 8)) : 0;
@@ -804,16 +809,7 @@ static fire_status init_handle(fire_handle_t** hp, const fire_system_t* sys,
     if (pot->kind == FIRE_POT_RGL && pot->pair_eval == FIRE_PAIR_TABLE) {
         fire_status ts = upload_tables(h);
         if (ts != FIRE_OK) return bail(ts);
-        if (fp32pair) {
-            b.nb_force = h->nb_tab_d;
-            b.nb_red = h->nb_tab_f;
-        }
-    } else if (fp32pair) {
-        // one atom per thread: the hardware block scheduler evens out the
-        // uneven neighbour counts (void surfaces) better than a grid-stride
-        // loop over a device-sized grid
-        b.nb_force = ceil_div(h->n, kForceBlock);
-        b.nb_red = b.nb_force;
+        if (fp32pair) b.nb_force = h->nb_tab_d;
     }
     CKI(cudaMalloc(&b.x, n * sizeof(dvec4)));
     CKI(cudaMalloc(&b.v, n * sizeof(dvec4)));
@@ -1414,14 +1410,14 @@ fire_status fire_diag_rgl_table(const fire_potential_t* pot, int64_t n, const do
         return FIRE_ERR_ARG;
     const RglTables T = build_rgl_tables(pot->A, pot->xi, pot->p, pot->q, pot->r0, pot->rs,
                                          pot->rc, 0.04);
-    const std::vector<double> S = build_split_table(T);
+    const std::vector<double> S = build_split_table(T, pot->r0);
+    const double r0sq = pot->r0 * pot->r0;
     for (int64_t i = 0; i < n; ++i) {
-        const double u = r[i] * r[i] - pot->r0 * pot->r0;
         double v[4];
         double* o = out + 4 * i;
         if (!(r[i] < pot->rc)) {
             o[0] = o[1] = o[2] = o[3] = 0.0;
-        } else if (split_eval(T.meta, S.data(), u, v)) {
+        } else if (split_eval(T.meta, S.data(), r[i] * r[i], r0sq, (float)r0sq, v)) {
             // the FP64 kernel's arithmetic: (2 phi, g, 2 phi'/r, g'/r)
             o[0] = 0.5 * v[0];
             o[1] = v[1];
@@ -1564,7 +1560,6 @@ fire_status fire_neb_init(fire_handle_t** hp, int32_t n_img, const fire_system_t
     }
     h->b.nb_red = q->nb_proj;
     h->b.eatom = q->eatom;
-    h->b.fused_red = 0;
 #undef CKN
     fire_system_t one = *sys;
     st = fire_init(&q->inner, &one, pot, params);

@@ -61,6 +61,7 @@ struct PotC {
     float qinv, qinv2;        // 1 / qscale, 1 / qscale^2
     double xi_inv;            // 1 / xi (theta-derivatives)
     double r0sq;              // r0^2 (table variable u = r^2 - r0^2)
+    float r0sq_f, rc2_f;      // FP32 copies (table index and cut-off test of the FP64 pass)
     TabMeta tab;              // knots of the tabulated pair functions (FP64)
     TabMeta tab32;            // knots of the FP32 tables
 };
@@ -122,8 +123,30 @@ __device__ __forceinline__ int cell_coord(double x, double Linv, int nc) {
 // such values, taken in 32-bit wrap-around arithmetic, are exact whenever the
 // true separation is below 2^31 / qscale (qscale is chosen so that every list
 // pair qualifies), whatever periodic image the raw coordinates sit in.
+// round(x qscale) modulo 2^32 for qscale = 2^k, rounding half to even, with
+// integer operations on the IEEE-754 fields (FP64 conversions issue at 1/58
+// of the FP32 rate on this part): x = M 2^(E - 1075) with the 53-bit
+// significand M, so x qscale = M 2^-sh with sh = 1075 - k - E.
 __device__ __forceinline__ int to_fixed(double x, double qscale) {
-    return (int)(unsigned)(unsigned long long)__double2ll_rn(x * qscale);
+    const unsigned long long bx = (unsigned long long)__double_as_longlong(x);
+    const int k = (int)(((unsigned long long)__double_as_longlong(qscale) >> 52) & 0x7ffull) - 1023;
+    const int E = (int)((bx >> 52) & 0x7ffull);
+    if (E == 0) return 0;                       // zero (positions are never subnormal)
+    const unsigned long long M = (bx & 0xfffffffffffffull) | (1ull << 52);
+    const int sh = 1075 - k - E;
+    unsigned long long q;
+    if (sh <= 0) {
+        q = M << (-sh < 63 ? -sh : 63);         // |x qscale| >= 2^52: wraps
+    } else if (sh >= 64) {
+        q = 0ull;
+    } else {
+        q = M >> sh;
+        const unsigned long long rem = M & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+        if (rem > half || (rem == half && (q & 1ull))) ++q;
+    }
+    unsigned r = (unsigned)q;
+    if ((long long)bx < 0) r = 0u - r;
+    return (int)r;
 }
 
 __device__ __forceinline__ int wrap_sub(int a, int b) { return (int)((unsigned)a - (unsigned)b); }
@@ -375,9 +398,11 @@ __device__ __forceinline__ void fire_update_drift(const FireScal& s, double dt, 
     x.x += dt * v.x;
     x.y += dt * v.y;
     x.z += dt * v.z;
-    v.x += s.kick_after * f.x;
-    v.y += s.kick_after * f.y;
-    v.z += s.kick_after * f.z;
+    if (s.kick_after != 0.0) {   // explicit Euler only
+        v.x += s.kick_after * f.x;
+        v.y += s.kick_after * f.y;
+        v.z += s.kick_after * f.z;
+    }
 }
 
 __device__ __forceinline__ void fire_update_atom(const FireScal& s, dvec4& x, dvec4& v,

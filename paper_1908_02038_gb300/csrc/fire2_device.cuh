@@ -65,7 +65,6 @@ struct Bufs {
     int nb_force, nb_embed, nb_red;
     const uint8_t* dofmask;   // frozen components per atom (bit d = axis d), or NULL
     double* eatom;         // per-atom energy (images' energies), or NULL
-    int fused_red;         // 1: the FP32-pair force kernels also reduce (F, v)
     int accum;             // 1: forces and densities accumulate with atomics (cleared
                            //    by k_update); 0: force kernels write them whole and
                            //    also produce the (F, v) reductions
@@ -620,13 +619,10 @@ __global__ void __launch_bounds__(kForceBlock) k_density32(Bufs b, PotC P, GeoC 
 __global__ void __launch_bounds__(kForceBlock) k_force32(Bufs b, PotC P, GeoC g) {
     __shared__ int3 qt[125];
     __shared__ float et[kExp32TableSize];
-    __shared__ double red[32];
     if (b.st->done) return;
     fill_qshift_table(qt, g);
     for (int t = threadIdx.x; t < kExp32TableSize; t += blockDim.x) et[t] = b.exp32_table[t];
     __syncthreads();
-    const double vvh = vv_half_of(b.st);
-    RedAcc acc;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < b.n; i += gridDim.x * blockDim.x) {
         const int4 qi = b.xq[i];
         const float fpi = b.fp32[i];
@@ -646,9 +642,7 @@ __global__ void __launch_bounds__(kForceBlock) k_force32(Bufs b, PotC P, GeoC g)
         dvec4 f = make_dvec4(fx.value(), fy.value(), fz.value(), 0.0);
         mask_force(b, i, f);
         b.f[i] = f;
-        if (b.fused_red) red_atom(b, i, f, vvh, acc);
     }
-    if (b.fused_red) red_write(acc, red, b.rpart);
 }
 
 // ---------------------------------------------------------------------------
@@ -662,8 +656,8 @@ __device__ __forceinline__ void load_table(T* dst, const T* src, int count) {
 }
 
 // FP64 pass 1 (half list): rho_i, rho_j (atomics), 2 phi per pair, and the
-// pair cache of pass 2 (2 phi'/r, g'/r) from the split-precision table rows
-// (split_eval: FP64 where 53 bits matter, FP32 for the high-order terms).
+// pair cache of pass 2 (2 phi'/r, g'/r) from the table rows: geometry in
+// FP64, quintics and per-atom sums in double-float (see fire2_table.cuh).
 __global__ void __launch_bounds__(kTabBlock64) k_density_tab(Bufs b, PotC P, GeoC g) {
     extern __shared__ double tabs[];   // split rows
     __shared__ double3 tbl[125];
@@ -679,7 +673,7 @@ __global__ void __launch_bounds__(kTabBlock64) k_density_tab(Bufs b, PotC P, Geo
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < b.n; i += gridDim.x * blockDim.x) {
         const dvec4 xi = b.x[i];
         const int m = b.nnbr[i];
-        double rho_i = 0.0, erep_i = 0.0;
+        ffloat rho_i = {0.f, 0.f}, erep_i = {0.f, 0.f};   // double-float sums
         for (int k = 0; k < m; ++k) {
             const size_t slot = (size_t)k * b.n + i;
             const uint32_t e = b.nbr[slot];
@@ -694,29 +688,40 @@ __global__ void __launch_bounds__(kTabBlock64) k_density_tab(Bufs b, PotC P, Geo
                 dz -= sh.z;
             }
             const double r2 = dx * dx + dy * dy + dz * dz;
+            // cut-off and table index in FP32: the taper makes phi, g and
+            // their first two derivatives vanish at rc, so a pair within
+            // FP32 rounding of rc contributes nothing either way
+            const float r2f = f64_to_f32_trunc(r2);
             double crep = 0.0, cden = 0.0;
-            if (r2 < P.rc2) {
-                double v[4];
-                if (!split_eval(P.tab, tabs, r2 - P.r0sq, v)) {
+            if (r2f < P.rc2_f) {
+                const double* row = split_row(P.tab, tabs, r2f - P.r0sq_f);
+                if (row) {
+                    const ffloat s = f64_to_ff(r2 - row[0]);
+                    const float* c = reinterpret_cast<const float*>(row + 1);
+                    const ffloat gg = ff_poly(c + 9, s);
+                    const double g64 = ff_to_f64(gg);
+                    rho_i = ff_add(rho_i, gg);
+                    atomicAdd(&b.rho[j], g64);
+                    erep_i = ff_add(erep_i, ff_poly(c, s));
+                    crep = ff_to_f64(ff_poly(c + 18, s));
+                    cden = ff_to_f64(ff_poly(c + 27, s));
+                } else {   // compressed below r0/2: exponentials
                     double rinv, phi, dphi, gg, dg;
                     rgl_pair64(P, r2, etab, rinv, phi, dphi, gg, dg);
-                    v[0] = 2.0 * phi;
-                    v[1] = gg;
-                    v[2] = 2.0 * dphi * rinv;
-                    v[3] = dg * rinv;
+                    rho_i = ff_add(rho_i, f64_to_ff(gg));
+                    atomicAdd(&b.rho[j], gg);
+                    erep_i = ff_add(erep_i, f64_to_ff(2.0 * phi));
+                    crep = 2.0 * dphi * rinv;
+                    cden = dg * rinv;
                 }
-                rho_i += v[1];
-                atomicAdd(&b.rho[j], v[1]);
-                erep_i += v[0];
-                crep = v[2];
-                cden = v[3];
             }
             b.crep[slot] = crep;
             b.cden[slot] = cden;
         }
-        atomicAdd(&b.rho[i], rho_i);
-        erep += erep_i;
-        if (b.eatom) b.eatom[i] = erep_i;
+        const double e_i = ff_to_f64(erep_i);
+        atomicAdd(&b.rho[i], ff_to_f64(rho_i));
+        erep += e_i;
+        if (b.eatom) b.eatom[i] = e_i;
     }
     const double s = block_sum(erep, red);
     if (threadIdx.x == 0) b.epart[blockIdx.x] = s;
@@ -774,10 +779,7 @@ __global__ void __launch_bounds__(kTabBlock) k_force32_tab(Bufs b, PotC P, GeoC 
     extern __shared__ float tabf32[];
     __shared__ int3 qt[125];
     __shared__ float et[kExp32TableSize];
-    __shared__ double red[32];
     if (b.st->done) return;
-    const double vvh = vv_half_of(b.st);
-    RedAcc acc;
     fill_qshift_table(qt, g);
     load_table(tabf32, b.tab_f32, (P.tab32.nA + P.tab32.nB) * kTabForce);
     load_table(et, b.exp32_table, kExp32TableSize);
@@ -811,9 +813,7 @@ __global__ void __launch_bounds__(kTabBlock) k_force32_tab(Bufs b, PotC P, GeoC 
         dvec4 f = make_dvec4(fx.value(), fy.value(), fz.value(), 0.0);
         mask_force(b, i, f);
         b.f[i] = f;
-        if (b.fused_red) red_atom(b, i, f, vvh, acc);
     }
-    if (b.fused_red) red_write(acc, red, b.rpart);
 }
 
 // ---------------------------------------------------------------------------
@@ -912,7 +912,9 @@ __global__ void k_update(Bufs b, GeoC g, cudaGraphConditionalHandle hif, int has
     const double dt = after_pre ? fire_capped_dt(s.dt_cur, b.st->prm.dmax,
                                                  __longlong_as_double((long long)b.st->vmax2))
                                 : s.dt_cur;
-    double d2max = 0.0;
+    // displacement since the last build in FP32 (truncated copies): off by
+    // < 1e-4 A at most, far inside the list build's FP32 margin
+    float d2max = 0.f;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < b.n; i += gridDim.x * blockDim.x) {
         dvec4 x = b.x[i], v = b.v[i];
         const dvec4 f = b.f[i];
@@ -930,10 +932,12 @@ __global__ void k_update(Bufs b, GeoC g, cudaGraphConditionalHandle hif, int has
             if (b.rho) b.rho[i] = 0.0;
         }
         const dvec4 r = b.xref[i];
-        const double ddx = x.x - r.x, ddy = x.y - r.y, ddz = x.z - r.z;
-        d2max = fmax(d2max, ddx * ddx + ddy * ddy + ddz * ddz);
+        const float ddx = f64_to_f32_trunc(x.x) - f64_to_f32_trunc(r.x);
+        const float ddy = f64_to_f32_trunc(x.y) - f64_to_f32_trunc(r.y);
+        const float ddz = f64_to_f32_trunc(x.z) - f64_to_f32_trunc(r.z);
+        d2max = fmaxf(d2max, ddx * ddx + ddy * ddy + ddz * ddz);
     }
-    const double bm = block_max(d2max, red);
+    const double bm = block_max(f32_to_f64(d2max), red);
     if (threadIdx.x == 0) {
         atomicMax(&b.st->max_disp2, (unsigned long long)__double_as_longlong(bm));
         if (has_if) {

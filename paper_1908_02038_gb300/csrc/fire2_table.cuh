@@ -231,25 +231,30 @@ __host__ __device__ __forceinline__ T poly4(const T* c, T t) {
 namespace fire2 {
 
 // ---------------------------------------------------------------------------
-// FP64 table rows with few FP64 instructions.
+// FP64-accurate table rows with few FP64 instructions.
 //
 // FP64 instructions issue at 1/58 of the FP32 rate on this part, so the FP64
-// density pass spends FP64 only where 53 bits are needed.  With s = u - u_k
-// the offset from the interval start, each quintic is evaluated as
+// density pass keeps FP64 for the geometry (differences, r^2, the offset
+// s = u - u_k from the interval start) and evaluates the quintics in
+// double-float arithmetic: every value is an unevaluated sum hi + lo of two
+// floats (Dekker 1971; Knuth's TwoSum), good to ~2^-44 relative, with
+// FP32 instructions only:
 //   f = c0 + s (c1 + s (c2 + s q)),   q = c3 + s (c4 + s c5)
-// where q is computed in FP32 from float copies of c3..c5 and a float copy
-// of s.  On these tables |s c_{j+1} / c_j| < ~0.07, so s^3 q is < ~1e-4 of f
-// and its FP32 rounding (~1e-7 relative) enters f at ~1e-11 relative or
-// less; c0..c2, s and the three FMAs stay FP64.  The float copies of s and
-// q cross between the formats by integer operations on the IEEE-754 fields
-// (no FP64 conversion instruction).  Interval indices come from an FP32 copy
-// of u; an index one off at an interval edge only moves s by ~1e-6 of the
+// c0..c2 and s as float pairs, q in plain FP32: on these tables
+// |s c_{j+1} / c_j| < ~0.07, so s^3 q is < ~1e-4 of f and its FP32 rounding
+// enters at ~1e-11 relative or less.  Float/double crossings are integer
+// operations on the IEEE-754 fields; the only FP64 instructions left per
+// pair are the geometry, the low part of s and the conversions of the
+// values that leave as doubles (rho_j for the atomic sum, the two cache
+// entries of the force pass).  Interval indices come from an FP32 copy of
+// u; an index one off at an interval edge only moves s by ~1e-6 of the
 // interval outside [0, h], where the quintic is still accurate.
 //
-// Row layout (kSplitRow doubles = 160 bytes): [0] u_k; [1 + 3p + j] = c_j
-// of polynomial p (j = 0..2); [13] unused; then 12 floats at double offset
-// 14: c3, c4, c5 of p = 0..3.  Polynomials (in s, coefficients divided by
-// h^j): p = 0: 2 phi, 1: g, 2: 4 phi_u = 2 phi'/r, 3: 2 g_u = g'/r.
+// Row layout (kSplitRow doubles = 160 bytes): [0] u_k + r0^2 (so that
+// s = r^2 - row[0]); then 36 floats at double offset 1, 9 per polynomial:
+// c0 hi, c0 lo, c1 hi, c1 lo, c2 hi, c2 lo, c3, c4, c5 (coefficients in s,
+// i.e. divided by h^j); 2 floats unused.  Polynomials: p = 0: 2 phi, 1: g,
+// 2: 4 phi_u = 2 phi'/r, 3: 2 g_u = g'/r.
 
 constexpr int kSplitRow = 20;
 
@@ -313,12 +318,69 @@ __host__ __device__ __forceinline__ double f32_to_f64(float f) {
     return dbl_from_words((b & 0x80000000u) | ((a >> 3) + (896u << 20)), a << 29);
 }
 
-__host__ __device__ __forceinline__ double split_poly(const double* c, const float* cf, double s,
-                                                      float sf) {
-    const float q = fmaf(fmaf(cf[2], sf, cf[1]), sf, cf[0]);
-    double r = fma(s, f32_to_f64(q), c[2]);
-    r = fma(s, r, c[1]);
-    return fma(s, r, c[0]);
+// Rounded FP32 operations the compiler may not fuse into FMAs (the error
+// terms below depend on the exact rounding of each step).
+__host__ __device__ __forceinline__ float mul_rn(float a, float b) {
+#ifdef __CUDA_ARCH__
+    return __fmul_rn(a, b);
+#else
+    return a * b;
+#endif
+}
+__host__ __device__ __forceinline__ float add_rn(float a, float b) {
+#ifdef __CUDA_ARCH__
+    return __fadd_rn(a, b);
+#else
+    return a + b;
+#endif
+}
+
+struct ffloat {
+    float hi, lo;
+};
+
+// a + b = s + e exactly (Knuth's TwoSum)
+__host__ __device__ __forceinline__ ffloat two_sum(float a, float b) {
+    const float s = add_rn(a, b);
+    const float bb = add_rn(s, -a);
+    const float e = add_rn(add_rn(a, -add_rn(s, -bb)), add_rn(b, -bb));
+    return {s, e};
+}
+// a + b = s + e exactly when |a| >= |b| (Dekker's Fast2Sum)
+__host__ __device__ __forceinline__ ffloat fast_two_sum(float a, float b) {
+    const float s = add_rn(a, b);
+    return {s, add_rn(b, -add_rn(s, -a))};
+}
+__host__ __device__ __forceinline__ ffloat ff_add(ffloat a, ffloat b) {
+    const ffloat s = two_sum(a.hi, b.hi);
+    return fast_two_sum(s.hi, add_rn(s.lo, add_rn(a.lo, b.lo)));
+}
+// (a.hi + a.lo)(b.hi + b.lo) without the lo*lo term
+__host__ __device__ __forceinline__ ffloat ff_mul(ffloat a, ffloat b) {
+    const float p = mul_rn(a.hi, b.hi);
+    const float e = fmaf(a.hi, b.hi, -p);
+    return fast_two_sum(p, fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e)));
+}
+__host__ __device__ __forceinline__ ffloat ff_mul_f(ffloat a, float b) {
+    const float p = mul_rn(a.hi, b);
+    const float e = fmaf(a.hi, b, -p);
+    return fast_two_sum(p, fmaf(a.lo, b, e));
+}
+__host__ __device__ __forceinline__ double ff_to_f64(ffloat a) {
+    return f32_to_f64(a.hi) + f32_to_f64(a.lo);
+}
+// d (|d| < 2^127) as hi + lo, both truncated: |d - hi - lo| < 2^-46 |d|
+__host__ __device__ __forceinline__ ffloat f64_to_ff(double d) {
+    const float hi = f64_to_f32_trunc(d);
+    return {hi, f64_to_f32_trunc(d - f32_to_f64(hi))};
+}
+
+// One quintic of a row: c = 9 floats (see the layout above), s as a float pair.
+__host__ __device__ __forceinline__ ffloat ff_poly(const float* c, ffloat s) {
+    const float q = fmaf(fmaf(c[8], s.hi, c[7]), s.hi, c[6]);
+    ffloat r = ff_add({c[4], c[5]}, ff_mul_f(s, q));
+    r = ff_add({c[2], c[3]}, ff_mul(s, r));
+    return ff_add({c[0], c[1]}, ff_mul(s, r));
 }
 
 // Interval of u (from its FP32 copy uf), clamped to the table.
@@ -329,22 +391,30 @@ __host__ __device__ __forceinline__ int split_index(const TabMeta& m, float uf) 
     return k < 0 ? 0 : (k > last ? last : k);
 }
 
-// out = (2 phi, g, 2 phi'/r, g'/r) at u = r^2 - r0^2; false below the table
-// (u < u_lo: the caller uses the analytic functions).
-__host__ __device__ __forceinline__ bool split_eval(const TabMeta& m, const double* tab, double u,
-                                                    double out[4]) {
-    const float uf = f64_to_f32_trunc(u);
-    if (uf < m.u_lo_f) return false;
-    const double* row = tab + (size_t)split_index(m, uf) * kSplitRow;
-    const float* rf = reinterpret_cast<const float*>(row + 14);
-    const double s = u - row[0];
-    const float sf = f64_to_f32_trunc(s);
-    for (int p = 0; p < 4; ++p) out[p] = split_poly(row + 1 + 3 * p, rf + 3 * p, s, sf);
+// Row of r^2 (FP32 copy of u = r^2 - r0^2 in uf) and s = r^2 - row[0];
+// NULL below the table (u < u_lo: the caller uses the analytic functions).
+__host__ __device__ __forceinline__ const double* split_row(const TabMeta& m, const double* tab,
+                                                            float uf) {
+    if (uf < m.u_lo_f) return nullptr;
+    return tab + (size_t)split_index(m, uf) * kSplitRow;
+}
+
+// out = (2 phi, g, 2 phi'/r, g'/r) at r^2 (host diagnostic; the kernel
+// inlines the same steps)
+__host__ __device__ __forceinline__ bool split_eval(const TabMeta& m, const double* tab, double r2,
+                                                    double r0sq, float r0sq_f, double out[4]) {
+    const float uf = f64_to_f32_trunc(r2) - r0sq_f;
+    const double* row = split_row(m, tab, uf);
+    if (!row) return false;
+    const ffloat s = f64_to_ff(r2 - row[0]);
+    const float* c = reinterpret_cast<const float*>(row + 1);
+    for (int p = 0; p < 4; ++p) out[p] = ff_to_f64(ff_poly(c + 9 * p, s));
+    (void)r0sq;
     return true;
 }
 
 // Rows from the Hermite coefficients of build_rgl_tables (in t = s / h).
-inline std::vector<double> build_split_table(const RglTables& T) {
+inline std::vector<double> build_split_table(const RglTables& T, double r0) {
     const TabMeta& m = T.meta;
     const int nint = m.nA + m.nB;
     std::vector<double> out((size_t)nint * kSplitRow, 0.0);
@@ -354,19 +424,24 @@ inline std::vector<double> build_split_table(const RglTables& T) {
         const double h = i < m.nA ? hA : hB;
         const double uk = i < m.nA ? (i - m.nA0) * hA : m.u_rs + (i - m.nA) * hB;
         double* row = out.data() + (size_t)i * kSplitRow;
-        float* rf = reinterpret_cast<float*>(row + 14);
-        row[0] = uk;
+        float* c = reinterpret_cast<float*>(row + 1);
+        row[0] = uk + r0 * r0;
         for (int p = 0; p < 4; ++p) {
-            const double* c = (p < 2 ? T.dens64.data() + (size_t)i * kTabDens + 6 * p
-                                     : T.force64.data() + (size_t)i * kTabForce + 6 * (p - 2));
+            const double* src = (p < 2 ? T.dens64.data() + (size_t)i * kTabDens + 6 * p
+                                       : T.force64.data() + (size_t)i * kTabForce + 6 * (p - 2));
             double hp = 1.0;
             double cs[6];
             for (int j = 0; j < 6; ++j) {
-                cs[j] = scale[p] * c[j] / hp;
+                cs[j] = scale[p] * src[j] / hp;
                 hp *= h;
             }
-            for (int j = 0; j < 3; ++j) row[1 + 3 * p + j] = cs[j];
-            for (int j = 0; j < 3; ++j) rf[3 * p + j] = (float)cs[3 + j];
+            float* o = c + 9 * p;
+            for (int j = 0; j < 3; ++j) {
+                const float hi = (float)cs[j];
+                o[2 * j] = hi;
+                o[2 * j + 1] = (float)(cs[j] - (double)hi);
+            }
+            for (int j = 0; j < 3; ++j) o[6 + j] = (float)cs[3 + j];
         }
     }
     return out;
