@@ -41,27 +41,36 @@ CONFIGS = {
     "rgl32k": lambda: fi.rgl_vacancy_box(ncell=20, seed=2),
     "lj256": lambda: fi.lj_fcc_vacancy(seed=1),
 }
-# Algorithmic floating-point operations per pair inside the cut-off (an FMA
-# counts 2, a transcendental 1), counted from the formulas each pass
-# evaluates:
-#   density (exponentials)     32   k_density, k_density32 (FP32)
-#   density_tab (quintic tables, phi, g, phi_u, g_u: 4 x 5 FMA + 18) 58
-#   force (cached 2 phi'/r, g'/r, both atoms)                       18
-#   force32 (exponentials, one atom of the pair, full list)         30
-#   force_lj                   24
-ALG_FLOP_PER_PAIR = {"density": 32, "density_tab": 58, "force": 18, "force32": 30,
+# Algorithmic floating-point operations per unordered pair inside the
+# cut-off (an FMA counts 2, a transcendental 1), counted from the formulas
+# each pass must evaluate once per pair (recomputing a pair from both ends,
+# as the full-list kernels do, is implementation work and not counted):
+#   density, exponentials: distance 8, sqrt 1, s 2, exps 2 + 2, prefactors 2,
+#     terms and derivatives 8, rho sums 2, energy 2, cache 3           32
+#   density, tables: distance 8, u 1, offset 1, two quintics 2 x 10,
+#     rho sums 2, energy 2                                            34
+#   force, cached or exponential derivatives: d 3, fs 3, F_i 6, F_j 6   18
+#   force, tables: distance 8, u 1, offset 1, two quintics 20, fs 3,
+#     F_i 6, F_j 6                                                     45
+#   force, LJ                                                          24
+ALG_FLOP_PER_PAIR = {"density": 32, "density_tab": 34, "force": 18, "force_tab": 45,
                      "force_lj": 24}
-# the kernel each stage runs, per (form, pair evaluation)
+# the kernel each stage runs, per (form, pair evaluation), and its unit
+# ("fp64": FP64 pipe, "ff": double-float on the FP32 pipe, "fp32")
 STAGE_KERNELS = {
-    ("fp64", "table"): {"density": ("k_density_tab", "density_tab"),
-                        "force": ("k_force_rgl", "force")},
-    ("fp64", "analytic"): {"density": ("k_density", "density"),
-                           "force": ("k_force_rgl", "force")},
-    ("fp32pair", "analytic"): {"density": ("k_density32", "density"),
-                               "force": ("k_force32", "force32")},
-    ("fp32pair", "table"): {"density": ("k_density32_tab", "density_tab"),
-                            "force": ("k_force32_tab", "force")},
+    ("fp64", "table"): {"density": ("k_density_ff", "density_tab", "ff"),
+                        "force": ("k_force_ff", "force_tab", "ff")},
+    ("fp64", "analytic"): {"density": ("k_density", "density", "fp64"),
+                           "force": ("k_force_rgl", "force", "fp64")},
+    ("fp32pair", "analytic"): {"density": ("k_density32", "density", "fp32"),
+                               "force": ("k_force32", "force", "fp32")},
+    ("fp32pair", "table"): {"density": ("k_density32_tab", "density_tab", "fp32"),
+                            "force": ("k_force32_tab", "force_tab", "fp32")},
 }
+# FP32 instructions of one double-float multiply-add (ff_mul 7 + ff_add 11,
+# counted from fire2_table.cuh): the double-float ALU peak is the measured
+# FP32 FMA rate / 18 in FP64-equivalent FLOP/s (2 per multiply-add)
+FF_FP32_PER_FMA = 18
 # Algorithmic HBM bytes per atom and iteration (x, v read+write, F'(rho)
 # write+read): 112 for RGL, 96 for LJ.
 ALG_BYTES_PER_ATOM_ITER = {"rgl": 112, "lj": 96}
@@ -352,7 +361,10 @@ def run_gpu(args):
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None,
-           "dtype": "f32-pair/f64" if fp32 else "f64", "data": "synthetic",
+           "dtype": ("f32-pair/f64" if fp32 else
+                     ("f64 (pair terms: int64 fixed point + double-float)" if is_rgl and pair == "table"
+                      else "f64")),
+           "data": "synthetic",
            "config": {"workload": f"{cfg.name} ({n} atoms), FIRE2 + semi-implicit Euler to "
                                   f"max|F_i| < {ftol:g}",
                       "atoms": n, "ftol": ftol, "form": args.form, "skin": pot.skin,
@@ -370,21 +382,26 @@ def run_gpu(args):
     pairs = count_pairs(cfg.x, cfg.box, rc)
     if is_rgl:
         dom = "density" if stages["density"] >= stages["force"] else "force"
-        kname, key = STAGE_KERNELS[(args.form, pair)][dom]
+        kname, key, unit = STAGE_KERNELS[(args.form, pair)][dom]
     else:
-        dom, kname, key = "force", "k_force_lj", "force_lj"
-    # the FP32-pair form walks a full list: every pair is evaluated from both ends
-    evals = pairs * (2 if fp32 else 1)
-    flop = ALG_FLOP_PER_PAIR[key] * evals
+        dom, kname, key, unit = "force", "k_force_lj", "force_lj", "fp64"
+    flop = ALG_FLOP_PER_PAIR[key] * pairs
     achieved = flop / (stages[dom] * 1e-3)
-    peak = fg.fire_diag_fma_peak(1 if fp32 else 0)
+    if unit == "fp64":
+        peak = fg.fire_diag_fma_peak(0)
+        src = "measured FP64 FMA rate (fire_diag_fma_peak), FMA = 2 FLOP"
+    elif unit == "fp32":
+        peak = fg.fire_diag_fma_peak(1)
+        src = "measured FP32 FMA rate (fire_diag_fma_peak), FMA = 2 FLOP"
+    else:
+        peak = fg.fire_diag_fma_peak(1) / FF_FP32_PER_FMA
+        src = ("double-float ALU peak: measured FP32 FMA rate / %d (FP32 instructions per "
+               "double-float multiply-add), in FP64-equivalent FLOP/s" % FF_FP32_PER_FMA)
     out["roofline"] = {"bound": "alu", "kernel": kname, "achieved": achieved / 1e12,
                        "peak": peak / 1e12, "unit": "TFLOP/s",
                        "frac": achieved / peak, "traffic": read_traffic(kname),
-                       "peak_source": ("measured %s FMA issue rate (fire_diag_fma_peak), "
-                                       "FMA = 2 FLOP" % ("FP32" if fp32 else "FP64")),
-                       "flop_per_pair": ALG_FLOP_PER_PAIR[key],
-                       "stage_ms": stages, "pairs_within_rc": pairs, "pair_evaluations": evals}
+                       "peak_source": src, "flop_per_pair": ALG_FLOP_PER_PAIR[key],
+                       "stage_ms": stages, "pairs_within_rc": pairs}
     # HBM roofline of the whole iteration, as the metric asks
     alg_b = ALG_BYTES_PER_ATOM_ITER["rgl" if is_rgl else "lj"]
     try:
@@ -411,31 +428,37 @@ def run_gpu(args):
                       "d2h_bytes_per_step": int(cfg.x.nbytes) + 1024}
     h.close()
 
-    # the other form on the same workload, its relaxed state checked in FP64
+    # the other forms on the same workload, each relaxed state re-evaluated
+    # with the IEEE FP64 exponential pair terms (k_density / k_force_rgl)
     if is_rgl and not args.no_forms and world == 1:
-        other = "fp32pair" if args.form == "fp64" else "fp64"
-        opair = default_pair(other)
-        m2, h2, x2 = relax_form(fg, torch, cfg, other, opair, args, dev, stream, clocks=False)
-        h2.close()
-        ms2 = m2["ms"]
-        it2 = sum(rr["iterations"] for rr in m2["results"])
+        others = [f for f in (("fp32pair", "analytic"), ("fp64", "analytic"), ("fp64", "table"))
+                  if f != (args.form, pair)][:2]
         pot64, mass, dt, _ = potential_for(args.config, "fp64")
+        pot64.pair_eval = fg.FIRE_PAIR_ANALYTIC
+        out["forms"] = {}
         with fg.FireHandle(n, mass, pot64, dt_start=dt) as hv:
-            fv = torch.empty_like(x2)
-            ev = torch.zeros(1, dtype=torch.float64, device=dev)
-            fg.fire_energy_forces_dev(hv.h, x2, cfg.box, fv, ev)
-            f64_fmax = float(torch.linalg.norm(fv, dim=1).max().item())
-            e64 = float(ev.item())
-            fv1 = torch.empty_like(x_relaxed)
-            fg.fire_energy_forces_dev(hv.h, x_relaxed, cfg.box, fv1, ev)
-            e64_head = float(ev.item())
-        out["forms"] = {other: {
-            "value": n * it2 / (ms2 * 1e-3), "unit": UNIT, "ms_per_step": ms2 / args.steps,
-            "pair_eval": opair, "iterations_per_step": [rr["iterations"] for rr in m2["results"]],
-            "final_fmax_atom_own": [rr["fmax_atom"] for rr in m2["results"]],
-            "final_fmax_atom_fp64_check": f64_fmax,
-            "energy_per_atom_fp64_check": e64 / n,
-            "energy_per_atom_diff_vs_headline": (e64 - e64_head) / n}}
+            def check(x):
+                fv = torch.empty_like(x)
+                ev = torch.zeros(1, dtype=torch.float64, device=dev)
+                fg.fire_energy_forces_dev(hv.h, x, cfg.box, fv, ev)
+                return float(torch.linalg.norm(fv, dim=1).max().item()), float(ev.item())
+            fmax_head, e_head = check(x_relaxed)
+            out["config"]["final_fmax_atom_ieee_fp64_check"] = fmax_head
+            for oform, opair in others:
+                m2, h2, x2 = relax_form(fg, torch, cfg, oform, opair, args, dev, stream,
+                                        clocks=False)
+                h2.close()
+                ms2 = m2["ms"]
+                it2 = sum(rr["iterations"] for rr in m2["results"])
+                f64_fmax, e64 = check(x2)
+                out["forms"][f"{oform}_{opair}"] = {
+                    "value": n * it2 / (ms2 * 1e-3), "unit": UNIT,
+                    "ms_per_step": ms2 / args.steps, "ftol": m2["ftol"],
+                    "iterations_per_step": [rr["iterations"] for rr in m2["results"]],
+                    "final_fmax_atom_own": [rr["fmax_atom"] for rr in m2["results"]],
+                    "final_fmax_atom_ieee_fp64_check": f64_fmax,
+                    "energy_per_atom_ieee_fp64_check": e64 / n,
+                    "energy_per_atom_diff_vs_headline": (e64 - e_head) / n}
     if is_rgl and not args.no_neb and world == 1:
         out["neb"] = neb_block(fg, torch, args.form, dev)
     if rank == 0:

@@ -92,7 +92,7 @@ struct fire_handle {
     fire_batch_state* batch = nullptr;   // set for handles made by fire_batch_init
     GradState grad;
     // tabulated pair functions: device copies and launch shapes
-    double* tab_s64 = nullptr;
+    float *tab_ffd = nullptr, *tab_fff = nullptr;
     float *tab_d32 = nullptr, *tab_f32 = nullptr;
     size_t smem_d = 0, smem_f = 0;
     int nb_tab_d = 0, nb_tab_f = 0;
@@ -131,6 +131,12 @@ double cutoff(const fire_potential_t& p) { return p.kind == FIRE_POT_LJ ? p.rc_l
 
 // Neighbour geometry for a box.  The list radius is rc + skin, with the skin
 // reduced where a periodic axis is shorter than 2 (rc + skin) so that the
+// The FP64 form's tabulated RGL passes (fixed-point separations, double-float
+// pair terms, full list, k_density_ff / k_force_ff).
+bool fixed64_form(const fire_potential_t& p) {
+    return p.kind == FIRE_POT_RGL && p.precision == FIRE_PREC_FP64 && p.pair_eval == FIRE_PAIR_TABLE;
+}
+
 // minimum image stays unique within the list radius.
 GeoC make_geo(const fire_handle* h, const double box[3]) {
     GeoC g{};
@@ -163,9 +169,11 @@ GeoC make_geo(const fire_handle* h, const double box[3]) {
     // magnitude (positions stay within about one box length of the box)
     const double margin = 1e-3 * rc + 8.0 * 1.2e-7 * (2.0 * lmax);
     g.rlist2f = (float)((rl + margin) * (rl + margin));
-    g.full = h->pot.precision == FIRE_PREC_FP32_PAIR ? 1 : 0;
-    for (int a = 0; a < 3; ++a)
+    g.full = (h->pot.precision == FIRE_PREC_FP32_PAIR || fixed64_form(h->pot)) ? 1 : 0;
+    for (int a = 0; a < 3; ++a) {
         g.Lq[a] = (int)(unsigned)(unsigned long long)std::llrint(box[a] * h->b.qscale);
+        g.Lq64[a] = std::llrint(std::ldexp(box[a], kFixedBits64));
+    }
     g.img_n = h->img_n > 0 ? h->img_n : h->n;
     g.ncell_img = g.nc[0] * g.nc[1] * g.nc[2];
     return g;
@@ -206,7 +214,8 @@ fire_status ensure_buffers(fire_handle* h, const GeoC& g, int cap) {
         h->b.crep = h->b.cden = nullptr;
         const size_t slots = (size_t)cap * h->n;
         CK(h, cudaMalloc(&h->b.nbr, slots * sizeof(uint32_t)));
-        if (h->pot.kind == FIRE_POT_RGL && h->pot.precision == FIRE_PREC_FP64) {
+        if (h->pot.kind == FIRE_POT_RGL && h->pot.precision == FIRE_PREC_FP64 &&
+            !fixed64_form(h->pot)) {
             CK(h, cudaMalloc(&h->b.crep, slots * sizeof(double)));
             CK(h, cudaMalloc(&h->b.cden, slots * sizeof(double)));
         }
@@ -248,9 +257,8 @@ void launch_forces(fire_handle* h, const GeoC& g, cudaStream_t s) {
         k_density32_tab<<<h->nb_tab_d, kTabBlock, h->smem_d, s>>>(h->b, h->potc, g);
         k_force32_tab<<<h->nb_tab_f, kTabBlock, h->smem_f, s>>>(h->b, h->potc, g);
     } else if (tab) {
-        k_density_tab<<<h->nb_tab_d, kTabBlock64, h->smem_d, s>>>(h->b, h->potc, g);
-        k_embed<<<h->b.nb_embed, kElemBlock, 0, s>>>(h->b);
-        k_force_rgl<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, g);
+        k_density_ff<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
+        k_force_ff<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
     } else if (h->pot.kind == FIRE_POT_RGL && h->pot.precision == FIRE_PREC_FP32_PAIR) {
         k_density32<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
         k_force32<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
@@ -673,35 +681,37 @@ static fire_status upload_tables(fire_handle* h) {
     const RglTables T32 = build_rgl_tables(p.A, p.xi, p.p, p.q, p.r0, p.rs, p.rc, 0.12);
     h->potc.tab = T.meta;
     h->potc.tab32 = T32.meta;
-    const std::vector<double> S = build_split_table(T, p.r0);
-    const size_t ns = S.size();
+    std::vector<float> ffd, fff;
+    build_ff_tables(T, p.r0, ffd, fff);
+    const size_t nff = ffd.size();
     const size_t nd32 = T32.dens32.size(), nf32 = T32.force32.size();
-    if (!h->tab_s64) {
-        CK(h, cudaMalloc(&h->tab_s64, ns * sizeof(double)));
+    if (!h->tab_ffd) {
+        CK(h, cudaMalloc(&h->tab_ffd, nff * sizeof(float)));
+        CK(h, cudaMalloc(&h->tab_fff, nff * sizeof(float)));
         CK(h, cudaMalloc(&h->tab_d32, nd32 * sizeof(float)));
         CK(h, cudaMalloc(&h->tab_f32, nf32 * sizeof(float)));
     }
-    CK(h, cudaMemcpy(h->tab_s64, S.data(), ns * sizeof(double), cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpy(h->tab_ffd, ffd.data(), nff * sizeof(float), cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpy(h->tab_fff, fff.data(), nff * sizeof(float), cudaMemcpyHostToDevice));
     CK(h, cudaMemcpy(h->tab_d32, T32.dens32.data(), nd32 * sizeof(float), cudaMemcpyHostToDevice));
     CK(h, cudaMemcpy(h->tab_f32, T32.force32.data(), nf32 * sizeof(float), cudaMemcpyHostToDevice));
-    h->b.tab_s64 = h->tab_s64;
+    h->b.tab_ffd = h->tab_ffd;
+    h->b.tab_fff = h->tab_fff;
     h->b.tab_d32 = h->tab_d32;
     h->b.tab_f32 = h->tab_f32;
-    const bool f32 = p.precision == FIRE_PREC_FP32_PAIR;
-    // FP64: one kernel holds the split rows; FP32: one table per kernel
-    h->smem_d = f32 ? nd32 * sizeof(float) : ns * sizeof(double);
-    h->smem_f = f32 ? nf32 * sizeof(float) : 0;
-    const int block = f32 ? kTabBlock : kTabBlock64;
-    const void* kd = f32 ? (const void*)k_density32_tab : (const void*)k_density_tab;
+    // FP32-pair tables sit in shared memory (one per kernel, grid-stride
+    // launches); the FP64 form reads its rows through the L1 cache
+    h->smem_d = nd32 * sizeof(float);
+    h->smem_f = nf32 * sizeof(float);
+    const int block = kTabBlock;
+    const void* kd = (const void*)k_density32_tab;
+    const void* kf = (const void*)k_force32_tab;
     CK(h, cudaFuncSetAttribute(kd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->smem_d));
-    int sms = 0, occ_d = 0, occ_f = 1;
+    CK(h, cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->smem_f));
+    int sms = 0, occ_d = 0, occ_f = 0;
     CK(h, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
     CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_d, kd, block, h->smem_d));
-    if (f32) {
-        const void* kf = (const void*)k_force32_tab;
-        CK(h, cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->smem_f));
-        CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_f, kf, block, h->smem_f));
-    }
+    CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_f, kf, block, h->smem_f));
     const int need = ceil_div(h->n, block);
     h->nb_tab_d = std::max(1, std::min(need, sms * std::max(occ_d, 1)));
     h->nb_tab_f = std::max(1, std::min(need, sms * std::max(occ_f, 1)));
@@ -801,9 +811,10 @@ static fire_status init_handle(fire_handle_t** hp, const fire_system_t* sys,
     // kernels use device-sized grids too, which keeps the partial sums the
     // control kernel adds up few.  nb_force + nb_embed energy partials,
     // nb_red rows of the (F, v) reductions.
-    b.accum = fp32pair ? 0 : 1;
+    const bool fixed64 = fixed64_form(*pot);
+    b.accum = (fp32pair || fixed64) ? 0 : 1;
     b.nb_force = ceil_div(h->n, kForceBlock);
-    b.nb_embed = (pot->kind == FIRE_POT_RGL && !fp32pair)
+    b.nb_embed = (pot->kind == FIRE_POT_RGL && !fp32pair && !fixed64)
                      ? std::max(1, std::min(ceil_div(h->n, kElemBlock), sms * 8)) : 0;
     b.nb_red = std::max(1, std::min(ceil_div(h->n, kElemBlock), sms * 4));
     if (pot->kind == FIRE_POT_RGL && pot->pair_eval == FIRE_PAIR_TABLE) {
@@ -820,6 +831,10 @@ static fire_status init_handle(fire_handle_t** hp, const fire_system_t* sys,
         CKI(cudaMalloc(&b.xq, n * sizeof(int4)));
         CKI(cudaMalloc(&b.fp32, n * sizeof(float)));
     }
+    if (fixed64) {
+        CKI(cudaMalloc(&b.xq64, n * sizeof(lvec4)));
+        CKI(cudaMalloc(&b.fpff, n * sizeof(float2)));
+    }
     CKI(cudaMalloc(&b.nnbr, n * sizeof(int)));
     CKI(cudaMalloc(&b.cell_of, n * sizeof(int)));
     CKI(cudaMalloc(&b.cell_atoms, n * sizeof(int)));
@@ -828,8 +843,8 @@ static fire_status init_handle(fire_handle_t** hp, const fire_system_t* sys,
         CKI(cudaMalloc(&b.fp, n * sizeof(double)));
     }
     CKI(cudaMalloc(&b.epart, (size_t)(b.nb_force + b.nb_embed) * sizeof(double)));
-    // the FP64 table density kernel writes fewer energy partials than
-    // nb_force; the rest stay 0
+    // the FP32-pair table kernels write fewer energy partials than nb_force;
+    // the rest stay 0
     CKI(cudaMemset(b.epart, 0, (size_t)(b.nb_force + b.nb_embed) * sizeof(double)));
     CKI(cudaMalloc(&b.rpart, (size_t)5 * b.nb_red * sizeof(double)));
     CKI(cudaMalloc(&b.st, sizeof(DevState)));
@@ -884,7 +899,7 @@ void fire_destroy(fire_handle_t* h) {
     if (h->stream) cudaStreamSynchronize(h->stream);
     drop_graph(h);
     Bufs& b = h->b;
-    void* ptrs[] = {b.x, b.v, b.f, b.xref, b.xf, b.xq, b.fp32, (void*)b.exp32_table,
+    void* ptrs[] = {b.x, b.v, b.f, b.xref, b.xf, b.xq, b.xq64, b.fpff, b.fp32, (void*)b.exp32_table,
                     (void*)b.exp_table, b.rho, b.fp, b.nbr, b.nnbr, b.crep, b.cden,
                     b.cell_of, b.cell_count, b.cell_start, b.cell_atoms, b.epart, b.rpart,
                     b.st, b.pos_io};
@@ -892,7 +907,7 @@ void fire_destroy(fire_handle_t* h) {
         if (p) cudaFree(p);
     if (h->batch) fire2_batch_free(h->batch);
     if (h->neb) neb_free(h->neb);
-    for (void* p : {(void*)h->tab_s64, (void*)h->tab_d32, (void*)h->tab_f32,
+    for (void* p : {(void*)h->tab_ffd, (void*)h->tab_fff, (void*)h->tab_d32, (void*)h->tab_f32,
                     (void*)h->dofmask})
         if (p) cudaFree(p);
     {
@@ -1254,7 +1269,7 @@ fire_status fire_set_rgl_params(fire_handle_t* h, const double theta[4]) {
     h->pot.p = theta[2];
     h->pot.q = theta[3];
     fill_potc(h);
-    if (h->tab_s64) {
+    if (h->tab_ffd) {
         st = upload_tables(h);
         if (st != FIRE_OK) return st;
     }
@@ -1410,19 +1425,25 @@ fire_status fire_diag_rgl_table(const fire_potential_t* pot, int64_t n, const do
         return FIRE_ERR_ARG;
     const RglTables T = build_rgl_tables(pot->A, pot->xi, pot->p, pot->q, pot->r0, pot->rs,
                                          pot->rc, 0.04);
-    const std::vector<double> S = build_split_table(T, pot->r0);
-    const double r0sq = pot->r0 * pot->r0;
+    std::vector<float> ffd, fff;
+    build_ff_tables(T, pot->r0, ffd, fff);
+    const float r0sq_f = (float)(pot->r0 * pot->r0), rc2_f = (float)(pot->rc * pot->rc);
     for (int64_t i = 0; i < n; ++i) {
-        double v[4];
         double* o = out + 4 * i;
-        if (!(r[i] < pot->rc)) {
+        // the FP64 kernels' arithmetic from r^2 on (r^2 as a float pair)
+        const ffloat r2 = f64_to_ff(r[i] * r[i]);
+        const float* rd = ff_row(T.meta, ffd, r2.hi - r0sq_f);
+        const float* rf = ff_row(T.meta, fff, r2.hi - r0sq_f);
+        if (!(r2.hi < rc2_f)) {
             o[0] = o[1] = o[2] = o[3] = 0.0;
-        } else if (split_eval(T.meta, S.data(), r[i] * r[i], r0sq, (float)r0sq, v)) {
-            // the FP64 kernel's arithmetic: (2 phi, g, 2 phi'/r, g'/r)
-            o[0] = 0.5 * v[0];
-            o[1] = v[1];
-            o[2] = 0.5 * r[i] * v[2];
-            o[3] = r[i] * v[3];
+        } else if (rd) {
+            ffloat d[2], f[2];
+            ff_row_eval(rd, r2, d);
+            ff_row_eval(rf, r2, f);
+            o[0] = ff_to_f64(d[0]);                 // phi
+            o[1] = ff_to_f64(d[1]);                 // g
+            o[2] = 0.5 * r[i] * ff_to_f64(f[0]);    // phi' = r (2 phi'/r) / 2
+            o[3] = r[i] * ff_to_f64(f[1]);          // g' = r (g'/r)
         } else {
             double a[8];
             rgl_analytic(pot->A, pot->xi, pot->p, pot->q, pot->r0, pot->rs, pot->rc, r[i], a);
@@ -1461,13 +1482,14 @@ fire_status fire_profile_stages(fire_handle_t* h, const double* pos, const doubl
         cudaEventRecord(ev[1], s);
         const bool tab = rgl && h->pot.pair_eval == FIRE_PAIR_TABLE;
         if (tab && f32) k_density32_tab<<<h->nb_tab_d, kTabBlock, h->smem_d, s>>>(h->b, h->potc, g);
-        else if (tab) k_density_tab<<<h->nb_tab_d, kTabBlock64, h->smem_d, s>>>(h->b, h->potc, g);
+        else if (tab) k_density_ff<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
         else if (rgl && f32) k_density32<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
         else if (rgl) k_density<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
         cudaEventRecord(ev[2], s);
-        if (rgl && !f32) k_embed<<<h->b.nb_embed, kElemBlock, 0, s>>>(h->b);
+        if (rgl && !f32 && !tab) k_embed<<<h->b.nb_embed, kElemBlock, 0, s>>>(h->b);
         cudaEventRecord(ev[3], s);
         if (tab && f32) k_force32_tab<<<h->nb_tab_f, kTabBlock, h->smem_f, s>>>(h->b, h->potc, g);
+        else if (tab) k_force_ff<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
         else if (rgl && f32) k_force32<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
         else if (rgl) k_force_rgl<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, g);
         else k_force_lj<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);

@@ -149,6 +149,31 @@ __device__ __forceinline__ int to_fixed(double x, double qscale) {
     return (int)r;
 }
 
+// round(x 2^k) as a 64-bit integer (|x 2^k| < 2^62), half to even, by the
+// same integer operations as to_fixed.
+__device__ __forceinline__ long long to_fixed64(double x, int k) {
+    const unsigned long long bx = (unsigned long long)__double_as_longlong(x);
+    const int E = (int)((bx >> 52) & 0x7ffull);
+    if (E == 0) return 0ll;
+    const unsigned long long M = (bx & 0xfffffffffffffull) | (1ull << 52);
+    const int sh = 1075 - k - E;
+    unsigned long long q;
+    if (sh <= 0) {
+        q = M << (-sh < 63 ? -sh : 63);
+    } else if (sh >= 64) {
+        q = 0ull;
+    } else {
+        q = M >> sh;
+        const unsigned long long rem = M & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+        if (rem > half || (rem == half && (q & 1ull))) ++q;
+    }
+    return (long long)bx < 0 ? -(long long)q : (long long)q;
+}
+
+struct __align__(32) lvec4 {   // fixed-point position (x, y, z, unused)
+    long long x, y, z, w;
+};
+
 __device__ __forceinline__ int wrap_sub(int a, int b) { return (int)((unsigned)a - (unsigned)b); }
 
 // Upper half-space test on the minimum-image vector d = x_j - x_i: exactly

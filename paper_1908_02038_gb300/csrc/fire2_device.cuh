@@ -39,6 +39,7 @@ struct GeoC {
     float rlist2f;         // (rc + skin + margin)^2, margin covers FP32 rounding
     int full;              // 1 = full list (both directions), 0 = half list
     int Lq[3];             // box lengths in fixed-point units, modulo 2^32
+    long long Lq64[3];     // box lengths in 2^-44 A units (FP64 form)
     // several images of one system in the same box (nudged elastic band):
     // atoms [k img_n, (k + 1) img_n) form image k and interact only among
     // themselves; one system: img_n = n
@@ -77,7 +78,9 @@ struct Bufs {
     double *rho, *fp;
     const double* exp_table;  // 2^(j/256), j = 0..255
     // tabulated RGL pair functions (fire2_table.cuh); nullptr when analytic
-    const double* tab_s64;     // FP64 split table rows (kSplitRow doubles each)
+    const float *tab_ffd, *tab_fff;   // FP64 form: density / force rows (kFFRow floats)
+    lvec4* xq64;               // FP64 form: positions in 2^-44 A units
+    float2* fpff;              // FP64 form: F'(rho) as a float pair
     const float *tab_d32, *tab_f32;
     uint32_t *nbr;
     int *nnbr;
@@ -128,6 +131,9 @@ __global__ void k_prepare(Bufs b) {
     if (b.xq)
         b.xq[i] = make_int4(to_fixed(p[0], b.qscale), to_fixed(p[1], b.qscale),
                             to_fixed(p[2], b.qscale), 0);
+    if (b.xq64)
+        b.xq64[i] = {to_fixed64(p[0], kFixedBits64), to_fixed64(p[1], kFixedBits64),
+                     to_fixed64(p[2], kFixedBits64), 0ll};
     b.v[i] = make_dvec4(0.0, 0.0, 0.0, 0.0);
     b.f[i] = make_dvec4(0.0, 0.0, 0.0, 0.0);
     if (b.rho) b.rho[i] = 0.0;
@@ -655,76 +661,145 @@ __device__ __forceinline__ void load_table(T* dst, const T* src, int count) {
     for (int t = threadIdx.x; t < count; t += blockDim.x) dst[t] = src[t];
 }
 
-// FP64 pass 1 (half list): rho_i, rho_j (atomics), 2 phi per pair, and the
-// pair cache of pass 2 (2 phi'/r, g'/r) from the table rows: geometry in
-// FP64, quintics and per-atom sums in double-float (see fire2_table.cuh).
-__global__ void __launch_bounds__(kTabBlock64) k_density_tab(Bufs b, PotC P, GeoC g) {
-    extern __shared__ double tabs[];   // split rows
-    __shared__ double3 tbl[125];
+// ---------------------------------------------------------------------------
+// FP64 form, tabulated RGL on the full list with no FP64 instruction per
+// pair (fire2_table.cuh): exact fixed-point separations, double-float r^2,
+// interval offsets, quintics and per-atom sums.  One atom per thread, no
+// atomics: every atom's sums are complete in its own thread.
+
+__device__ __forceinline__ void fill_qshift64_table(long long* qt, const GeoC& g) {
+    for (int t = threadIdx.x; t < 125; t += blockDim.x) {
+        const int sx = t % 5 - 2, sy = (t / 5) % 5 - 2, sz = t / 25 - 2;
+        qt[3 * t] = sx * g.Lq64[0];
+        qt[3 * t + 1] = sy * g.Lq64[1];
+        qt[3 * t + 2] = sz * g.Lq64[2];
+    }
+}
+
+// Separation x_j - x_i - shift of list slot e as float pairs (exact), r^2.
+__device__ __forceinline__ ffloat pair_sep_ff(const Bufs& b, const long long* qt, const lvec4& qi,
+                                              uint32_t e, ffloat& dx, ffloat& dy, ffloat& dz,
+                                              int& j) {
+    j = (int)(e & kIdxMask);
+    const int code = (int)(e >> kIdxBits);
+    const lvec4 qj = b.xq64[j];
+    long long ix = qj.x - qi.x, iy = qj.y - qi.y, iz = qj.z - qi.z;
+    if (code != kCodeZero) {
+        ix -= qt[3 * code];
+        iy -= qt[3 * code + 1];
+        iz -= qt[3 * code + 2];
+    }
+    dx = fixed_to_ff(ix);
+    dy = fixed_to_ff(iy);
+    dz = fixed_to_ff(iz);
+    return ff_add(ff_add(ff_mul(dx, dx), ff_mul(dy, dy)), ff_mul(dz, dz));
+}
+
+__device__ __forceinline__ void load_row(const float* tab, int k, float row[kFFRow]) {
+    const float4* src = reinterpret_cast<const float4*>(tab + (size_t)k * kFFRow);
+#pragma unroll
+    for (int q = 0; q < kFFRow / 4; ++q) {
+        const float4 v = __ldg(src + q);
+        row[4 * q] = v.x;
+        row[4 * q + 1] = v.y;
+        row[4 * q + 2] = v.z;
+        row[4 * q + 3] = v.w;
+    }
+}
+
+// Pass 1: rho_i, F'(rho_i) (FP64 per atom) and the atom's energy
+// sum_j phi - sqrt(rho_i).  Pairs compressed below r0/2 fall back to the
+// FP64 exponentials.
+__global__ void __launch_bounds__(kForceBlock) k_density_ff(Bufs b, PotC P, GeoC g) {
+    __shared__ long long qt[375];
     __shared__ double etab[kExpTableSize];
     __shared__ double red[32];
     if (b.st->done) return;
-    const int nint = P.tab.nA + P.tab.nB;
-    fill_shift_table(tbl, g);
-    load_table(tabs, b.tab_s64, nint * kSplitRow);
-    load_table(etab, b.exp_table, kExpTableSize);
+    fill_qshift64_table(qt, g);
+    for (int t = threadIdx.x; t < kExpTableSize; t += blockDim.x) etab[t] = b.exp_table[t];
     __syncthreads();
-    double erep = 0.0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < b.n; i += gridDim.x * blockDim.x) {
-        const dvec4 xi = b.x[i];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double e_atom = 0.0;
+    if (i < b.n) {
+        const lvec4 qi = b.xq64[i];
         const int m = b.nnbr[i];
-        ffloat rho_i = {0.f, 0.f}, erep_i = {0.f, 0.f};   // double-float sums
+        ffloat rho = {0.f, 0.f}, erep = {0.f, 0.f};
         for (int k = 0; k < m; ++k) {
-            const size_t slot = (size_t)k * b.n + i;
-            const uint32_t e = b.nbr[slot];
-            const int j = (int)(e & kIdxMask);
-            const int code = (int)(e >> kIdxBits);
-            const dvec4 xj = b.x[j];
-            double dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
-            if (code != kCodeZero) {
-                const double3 sh = tbl[code];
-                dx -= sh.x;
-                dy -= sh.y;
-                dz -= sh.z;
+            ffloat dx, dy, dz;
+            int j;
+            const ffloat r2 = pair_sep_ff(b, qt, qi, b.nbr[(size_t)k * b.n + i], dx, dy, dz, j);
+            if (!(r2.hi < P.rc2_f)) continue;
+            const float uf = r2.hi - P.r0sq_f;
+            if (uf >= P.tab.u_lo_f) {
+                float row[kFFRow];
+                load_row(b.tab_ffd, ff_index(P.tab, uf), row);
+                ffloat v[2];
+                ff_row_eval(row, r2, v);
+                erep = ff_add(erep, v[0]);
+                rho = ff_add(rho, v[1]);
+            } else {
+                double rinv, phi, dphi, gg, dg;
+                rgl_pair64(P, ff_to_f64(r2), etab, rinv, phi, dphi, gg, dg);
+                erep = ff_add(erep, f64_to_ff(phi));
+                rho = ff_add(rho, f64_to_ff(gg));
             }
-            const double r2 = dx * dx + dy * dy + dz * dz;
-            // cut-off and table index in FP32: the taper makes phi, g and
-            // their first two derivatives vanish at rc, so a pair within
-            // FP32 rounding of rc contributes nothing either way
-            const float r2f = f64_to_f32_trunc(r2);
-            double crep = 0.0, cden = 0.0;
-            if (r2f < P.rc2_f) {
-                const double* row = split_row(P.tab, tabs, r2f - P.r0sq_f);
-                if (row) {
-                    const ffloat s = f64_to_ff(r2 - row[0]);
-                    const float* c = reinterpret_cast<const float*>(row + 1);
-                    const ffloat gg = ff_poly(c + 9, s);
-                    const double g64 = ff_to_f64(gg);
-                    rho_i = ff_add(rho_i, gg);
-                    atomicAdd(&b.rho[j], g64);
-                    erep_i = ff_add(erep_i, ff_poly(c, s));
-                    crep = ff_to_f64(ff_poly(c + 18, s));
-                    cden = ff_to_f64(ff_poly(c + 27, s));
-                } else {   // compressed below r0/2: exponentials
-                    double rinv, phi, dphi, gg, dg;
-                    rgl_pair64(P, r2, etab, rinv, phi, dphi, gg, dg);
-                    rho_i = ff_add(rho_i, f64_to_ff(gg));
-                    atomicAdd(&b.rho[j], gg);
-                    erep_i = ff_add(erep_i, f64_to_ff(2.0 * phi));
-                    crep = 2.0 * dphi * rinv;
-                    cden = dg * rinv;
-                }
-            }
-            b.crep[slot] = crep;
-            b.cden[slot] = cden;
         }
-        const double e_i = ff_to_f64(erep_i);
-        atomicAdd(&b.rho[i], ff_to_f64(rho_i));
-        erep += e_i;
-        if (b.eatom) b.eatom[i] = e_i;
+        const double rho_d = ff_to_f64(rho);
+        const double sq = sqrt(rho_d);
+        const double fp = rho_d > 0.0 ? -0.5 / sq : 0.0;
+        b.rho[i] = rho_d;
+        b.fp[i] = fp;
+        const ffloat fpf = f64_to_ff(fp);
+        b.fpff[i] = make_float2(fpf.hi, fpf.lo);
+        e_atom = ff_to_f64(erep) - sq;
+        if (b.eatom) b.eatom[i] = e_atom;
     }
-    const double s = block_sum(erep, red);
+    const double s = block_sum(e_atom, red);
     if (threadIdx.x == 0) b.epart[blockIdx.x] = s;
+}
+
+// Pass 2: F_i = sum_j [2 phi'/r + (F'_i + F'_j) g'/r] (x_j - x_i), written
+// whole (F = -grad E, Sec. 2.1).
+__global__ void __launch_bounds__(kForceBlock) k_force_ff(Bufs b, PotC P, GeoC g) {
+    __shared__ long long qt[375];
+    __shared__ double etab[kExpTableSize];
+    if (b.st->done) return;
+    fill_qshift64_table(qt, g);
+    for (int t = threadIdx.x; t < kExpTableSize; t += blockDim.x) etab[t] = b.exp_table[t];
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= b.n) return;
+    const lvec4 qi = b.xq64[i];
+    const float2 fpi2 = b.fpff[i];
+    const ffloat fpi = {fpi2.x, fpi2.y};
+    const int m = b.nnbr[i];
+    ffloat fx = {0.f, 0.f}, fy = {0.f, 0.f}, fz = {0.f, 0.f};
+    for (int k = 0; k < m; ++k) {
+        ffloat dx, dy, dz;
+        int j;
+        const ffloat r2 = pair_sep_ff(b, qt, qi, b.nbr[(size_t)k * b.n + i], dx, dy, dz, j);
+        if (!(r2.hi < P.rc2_f)) continue;
+        const float uf = r2.hi - P.r0sq_f;
+        ffloat c[2];
+        if (uf >= P.tab.u_lo_f) {
+            float row[kFFRow];
+            load_row(b.tab_fff, ff_index(P.tab, uf), row);
+            ff_row_eval(row, r2, c);
+        } else {
+            double rinv, phi, dphi, gg, dg;
+            rgl_pair64(P, ff_to_f64(r2), etab, rinv, phi, dphi, gg, dg);
+            c[0] = f64_to_ff(2.0 * dphi * rinv);
+            c[1] = f64_to_ff(dg * rinv);
+        }
+        const float2 fpj2 = b.fpff[j];
+        const ffloat fs = ff_add(c[0], ff_mul(ff_add(fpi, {fpj2.x, fpj2.y}), c[1]));
+        fx = ff_add(fx, ff_mul(fs, dx));
+        fy = ff_add(fy, ff_mul(fs, dy));
+        fz = ff_add(fz, ff_mul(fs, dz));
+    }
+    dvec4 f = make_dvec4(ff_to_f64(fx), ff_to_f64(fy), ff_to_f64(fz), 0.0);
+    mask_force(b, i, f);
+    b.f[i] = f;
 }
 
 // FP32-pair pass 1 (full list, tables): u = r^2 - r0^2 exact in fixed point,
@@ -926,6 +1001,9 @@ __global__ void k_update(Bufs b, GeoC g, cudaGraphConditionalHandle hif, int has
         if (b.xq)
             b.xq[i] = make_int4(to_fixed(x.x, b.qscale), to_fixed(x.y, b.qscale),
                                 to_fixed(x.z, b.qscale), 0);
+        if (b.xq64)
+            b.xq64[i] = {to_fixed64(x.x, kFixedBits64), to_fixed64(x.y, kFixedBits64),
+                         to_fixed64(x.z, kFixedBits64), 0ll};
         b.v[i] = v;
         if (b.accum) {
             b.f[i] = make_dvec4(0.0, 0.0, 0.0, 0.0);

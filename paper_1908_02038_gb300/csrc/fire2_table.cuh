@@ -231,32 +231,37 @@ __host__ __device__ __forceinline__ T poly4(const T* c, T t) {
 namespace fire2 {
 
 // ---------------------------------------------------------------------------
-// FP64-accurate table rows with few FP64 instructions.
+// FP64-accurate pair terms without FP64 instructions.
 //
 // FP64 instructions issue at 1/58 of the FP32 rate on this part, so the FP64
-// density pass keeps FP64 for the geometry (differences, r^2, the offset
-// s = u - u_k from the interval start) and evaluates the quintics in
-// double-float arithmetic: every value is an unevaluated sum hi + lo of two
-// floats (Dekker 1971; Knuth's TwoSum), good to ~2^-44 relative, with
-// FP32 instructions only:
-//   f = c0 + s (c1 + s (c2 + s q)),   q = c3 + s (c4 + s c5)
-// c0..c2 and s as float pairs, q in plain FP32: on these tables
-// |s c_{j+1} / c_j| < ~0.07, so s^3 q is < ~1e-4 of f and its FP32 rounding
-// enters at ~1e-11 relative or less.  Float/double crossings are integer
-// operations on the IEEE-754 fields; the only FP64 instructions left per
-// pair are the geometry, the low part of s and the conversions of the
-// values that leave as doubles (rho_j for the atomic sum, the two cache
-// entries of the force pass).  Interval indices come from an FP32 copy of
-// u; an index one off at an interval edge only moves s by ~1e-6 of the
-// interval outside [0, h], where the quintic is still accurate.
+// form's pair passes use no FP64 instruction per pair:
+//   * separations are exact: positions in 64-bit fixed point (2^44 units per
+//     A, i.e. a grid finer than the last bit of a double coordinate beyond
+//     ~2 A), differences in integers, then split exactly into two floats;
+//   * everything else is double-float arithmetic: each value is an
+//     unevaluated sum hi + lo of two floats (Dekker 1971; Knuth's TwoSum),
+//     good to ~2^-44 relative, in FP32 instructions only:
+//       r^2 = dx^2 + dy^2 + dz^2,  s = r^2 - (u_k + r0^2),
+//       f = c0 + s (c1 + s (c2 + s q)),   q = c3 + s (c4 + s c5)
+//     with c0..c2 and s as float pairs and q in plain FP32: on these tables
+//     |s c_{j+1} / c_j| < ~0.07, so s^3 q is < ~1e-4 of f and its FP32
+//     rounding enters at ~1e-11 relative or less;
+//   * the cut-off test and the interval index use the FP32 high part of r^2:
+//     the taper makes phi, g and their first two derivatives vanish at rc,
+//     so a pair within FP32 rounding of rc contributes nothing either way,
+//     and an index one off at an interval edge only moves s by ~1e-6 of the
+//     interval outside [0, h], where the quintic is still accurate.
+// Float/double crossings (per atom only) are integer operations on the
+// IEEE-754 fields.
 //
-// Row layout (kSplitRow doubles = 160 bytes): [0] u_k + r0^2 (so that
-// s = r^2 - row[0]); then 36 floats at double offset 1, 9 per polynomial:
-// c0 hi, c0 lo, c1 hi, c1 lo, c2 hi, c2 lo, c3, c4, c5 (coefficients in s,
-// i.e. divided by h^j); 2 floats unused.  Polynomials: p = 0: 2 phi, 1: g,
-// 2: 4 phi_u = 2 phi'/r, 3: 2 g_u = g'/r.
+// Rows (kFFRow floats = 80 bytes, 16-byte aligned): [0], [1] u_k + r0^2 as
+// hi, lo; then two polynomials of 9 floats each: c0 hi, c0 lo, c1 hi, c1 lo,
+// c2 hi, c2 lo, c3, c4, c5 (coefficients in s, i.e. divided by h^j).
+// Density rows: phi, g.  Force rows: 4 phi_u = 2 phi'/r, 2 g_u = g'/r.
 
-constexpr int kSplitRow = 20;
+constexpr int kFFRow = 20;
+constexpr int kFixedBits64 = 44;   // fixed-point positions of the FP64 form: 2^44 per A
+
 
 __host__ __device__ __forceinline__ void dbl_words(double d, unsigned& hi, unsigned& lo) {
 #ifdef __CUDA_ARCH__
@@ -383,49 +388,65 @@ __host__ __device__ __forceinline__ ffloat ff_poly(const float* c, ffloat s) {
     return ff_add({c[0], c[1]}, ff_mul(s, r));
 }
 
+__host__ __device__ __forceinline__ ffloat ff_neg(ffloat a) { return {-a.hi, -a.lo}; }
+__host__ __device__ __forceinline__ ffloat ff_scale2(ffloat a, float p2) {   // p2 a power of 2
+    return {a.hi * p2, a.lo * p2};
+}
+
 // Interval of u (from its FP32 copy uf), clamped to the table.
-__host__ __device__ __forceinline__ int split_index(const TabMeta& m, float uf) {
+__host__ __device__ __forceinline__ int ff_index(const TabMeta& m, float uf) {
     int k = uf < m.u_rs_f ? m.nA0 + (int)floorf(uf * m.hA_inv_f)
                           : m.nA + (int)floorf((uf - m.u_rs_f) * m.hB_inv_f);
     const int last = m.nA + m.nB - 1;
     return k < 0 ? 0 : (k > last ? last : k);
 }
 
-// Row of r^2 (FP32 copy of u = r^2 - r0^2 in uf) and s = r^2 - row[0];
-// NULL below the table (u < u_lo: the caller uses the analytic functions).
-__host__ __device__ __forceinline__ const double* split_row(const TabMeta& m, const double* tab,
-                                                            float uf) {
+// The two polynomials of `row` at r^2 (float pair): out[0], out[1].
+__host__ __device__ __forceinline__ void ff_row_eval(const float* row, ffloat r2, ffloat out[2]) {
+    const ffloat s = ff_add(r2, ff_neg({row[0], row[1]}));
+    out[0] = ff_poly(row + 2, s);
+    out[1] = ff_poly(row + 11, s);
+}
+
+// Exact split of a 64-bit integer |n| < 2^47 times 2^-kFixedBits64 into a
+// float pair (both parts exact: 24 + 23 bits).
+__host__ __device__ __forceinline__ ffloat fixed_to_ff(long long n) {
+    const long long a = n >> 23;                          // floor(n / 2^23)
+    const int b = (int)(n - (a << 23));                   // 0 <= b < 2^23
+    const float hi = (float)(int)a * 0x1p-21f;            // 2^(23 - 44)
+    const float lo = (float)b * 0x1p-44f;
+    return two_sum(hi, lo);
+}
+
+// Host evaluation with the kernels' arithmetic (diagnostic): row of the
+// table of u = r^2 - r0^2, or NULL below the table (u < u_lo, where the
+// kernels use the exponentials).
+inline const float* ff_row(const TabMeta& m, const std::vector<float>& tab, float uf) {
     if (uf < m.u_lo_f) return nullptr;
-    return tab + (size_t)split_index(m, uf) * kSplitRow;
+    return tab.data() + (size_t)ff_index(m, uf) * kFFRow;
 }
 
-// out = (2 phi, g, 2 phi'/r, g'/r) at r^2 (host diagnostic; the kernel
-// inlines the same steps)
-__host__ __device__ __forceinline__ bool split_eval(const TabMeta& m, const double* tab, double r2,
-                                                    double r0sq, float r0sq_f, double out[4]) {
-    const float uf = f64_to_f32_trunc(r2) - r0sq_f;
-    const double* row = split_row(m, tab, uf);
-    if (!row) return false;
-    const ffloat s = f64_to_ff(r2 - row[0]);
-    const float* c = reinterpret_cast<const float*>(row + 1);
-    for (int p = 0; p < 4; ++p) out[p] = ff_to_f64(ff_poly(c + 9 * p, s));
-    (void)r0sq;
-    return true;
-}
-
-// Rows from the Hermite coefficients of build_rgl_tables (in t = s / h).
-inline std::vector<double> build_split_table(const RglTables& T, double r0) {
+// Density rows (phi, g) and force rows (2 phi'/r, g'/r) from the Hermite
+// coefficients of build_rgl_tables (in t = s / h).
+inline void build_ff_tables(const RglTables& T, double r0, std::vector<float>& dens,
+                            std::vector<float>& force) {
     const TabMeta& m = T.meta;
     const int nint = m.nA + m.nB;
-    std::vector<double> out((size_t)nint * kSplitRow, 0.0);
+    dens.assign((size_t)nint * kFFRow, 0.f);
+    force.assign((size_t)nint * kFFRow, 0.f);
     const double hA = 1.0 / m.hA_inv, hB = 1.0 / m.hB_inv;
-    const double scale[4] = {2.0, 1.0, 4.0, 2.0};
+    const double scale[4] = {1.0, 1.0, 4.0, 2.0};
+    auto split = [](double v, float* o) {
+        const float hi = (float)v;
+        o[0] = hi;
+        o[1] = (float)(v - (double)hi);
+    };
     for (int i = 0; i < nint; ++i) {
         const double h = i < m.nA ? hA : hB;
         const double uk = i < m.nA ? (i - m.nA0) * hA : m.u_rs + (i - m.nA) * hB;
-        double* row = out.data() + (size_t)i * kSplitRow;
-        float* c = reinterpret_cast<float*>(row + 1);
-        row[0] = uk + r0 * r0;
+        float* rows[2] = {dens.data() + (size_t)i * kFFRow, force.data() + (size_t)i * kFFRow};
+        split(uk + r0 * r0, rows[0]);
+        split(uk + r0 * r0, rows[1]);
         for (int p = 0; p < 4; ++p) {
             const double* src = (p < 2 ? T.dens64.data() + (size_t)i * kTabDens + 6 * p
                                        : T.force64.data() + (size_t)i * kTabForce + 6 * (p - 2));
@@ -435,16 +456,11 @@ inline std::vector<double> build_split_table(const RglTables& T, double r0) {
                 cs[j] = scale[p] * src[j] / hp;
                 hp *= h;
             }
-            float* o = c + 9 * p;
-            for (int j = 0; j < 3; ++j) {
-                const float hi = (float)cs[j];
-                o[2 * j] = hi;
-                o[2 * j + 1] = (float)(cs[j] - (double)hi);
-            }
+            float* o = rows[p / 2] + 2 + 9 * (p % 2);
+            for (int j = 0; j < 3; ++j) split(cs[j], o + 2 * j);
             for (int j = 0; j < 3; ++j) o[6 + j] = (float)cs[3 + j];
         }
     }
-    return out;
 }
 
 }  // namespace fire2
