@@ -9,7 +9,11 @@ builds, both RGL force passes, the FP64 reductions, the dt/alpha control and
 the integration -- runs inside one CUDA graph launch (fire_minimize_dev).
 
 metric: atom-iterations per second (N x FIRE iterations / wall time), higher is
-better; ms_per_step is the time-to-ftol of one relaxation.
+better; ms_per_step is the time-to-ftol of one relaxation.  The line also
+carries the other precision forms on the same workload (`forms`, each
+relaxed structure re-checked with the IEEE-FP64 kernels), a nudged-elastic-
+band run (`neb`), the roofline of the dominant kernel and the oracle timed on
+the host cores (`cpu_baseline`).
 
 `--impl reference` times the FP64 CPU oracle (plain C, OpenMP) on a bounded
 sample of the same workload (a few FIRE iterations of the same box).
@@ -87,6 +91,8 @@ def parse():
     ap.add_argument("--pair", default=None, choices=["table", "analytic"],
                     help="RGL pair functions: quintic tables or exponentials (default: "
                          "tables for fp64, exponentials for fp32pair, the faster of each)")
+    ap.add_argument("--newton", default="auto", choices=["auto", "on", "off"],
+                    help="FP64 tabulated form: half list + atomics (on) or full list (off)")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the second form (FP32-pair next to FP64 and vice versa)")
     ap.add_argument("--no-neb", action="store_true",
@@ -209,6 +215,8 @@ def relax_form(fg, torch, cfg, form, pair, args, dev, stream, clocks=True):
     relaxed positions of the last step."""
     pot, mass, dt, ftol = potential_for(args.config, form)
     pot.pair_eval = fg.FIRE_PAIR_ANALYTIC if pair == "analytic" else fg.FIRE_PAIR_TABLE
+    pot.newton = {"auto": fg.FIRE_NEWTON_AUTO, "on": fg.FIRE_NEWTON_ON,
+                  "off": fg.FIRE_NEWTON_OFF}[args.newton]
     x0 = torch.tensor(cfg.x, dtype=torch.float64, device=dev)
     work = torch.empty_like(x0)
     h = fg.FireHandle(cfg.n, mass, pot, dt_start=dt)
@@ -368,7 +376,7 @@ def run_gpu(args):
            "config": {"workload": f"{cfg.name} ({n} atoms), FIRE2 + semi-implicit Euler to "
                                   f"max|F_i| < {ftol:g}",
                       "atoms": n, "ftol": ftol, "form": args.form, "skin": pot.skin,
-                      "exec": args.exec, "pair_eval": pair,
+                      "exec": args.exec, "pair_eval": pair, "newton": args.newton,
                       "iterations_per_step": [rr["iterations"] for rr in results],
                       "final_fmax_atom": [rr["fmax_atom"] for rr in results],
                       "final_energy_per_atom": [rr["energy"] / n for rr in results],

@@ -36,7 +36,7 @@
 extern "C" {
 #endif
 
-#define FIRE2_ABI_VERSION 4
+#define FIRE2_ABI_VERSION 5
 
 typedef enum {
     FIRE_OK = 0,
@@ -73,12 +73,27 @@ typedef enum {
  * u = r^2 - r0^2 (knots every ~0.04 A^2, on rs and rc, matching value, first
  * and second derivative at every knot; interpolation error ~1e-13 relative
  * for values, ~1e-11 for derivatives), no square root or exponential per
- * pair; pairs closer than r0/2 use the analytic functions.
- * FIRE_PAIR_ANALYTIC: the exponentials and the taper per pair. */
+ * pair; pairs closer than r0/2 use the analytic functions.  In the FP64
+ * precision the table terms are computed from exact fixed-point separations
+ * (2^-44 A) in double-float arithmetic (float pairs, ~2^-44 relative), with
+ * FP64 sums, reductions and integration.
+ * FIRE_PAIR_ANALYTIC: the exponentials and the taper per pair, IEEE FP64 in
+ * the FP64 precision. */
 typedef enum {
     FIRE_PAIR_TABLE = 0,
     FIRE_PAIR_ANALYTIC = 1
 } fire_pair_eval;
+
+/* Neighbour lists of the FP64 tabulated form (other forms ignore it).
+ * FIRE_NEWTON_ON: each pair once (half list), its terms added to both atoms
+ * by FP64 atomics.  FIRE_NEWTON_OFF: full list, every pair from both ends,
+ * no atomics (results reproducible bit for bit).  FIRE_NEWTON_AUTO: the
+ * library's default for this part (FIRE_NEWTON_ON). */
+typedef enum {
+    FIRE_NEWTON_AUTO = 0,
+    FIRE_NEWTON_ON = 1,
+    FIRE_NEWTON_OFF = 2
+} fire_newton;
 
 typedef enum {
     FIRE_PREC_FP64 = 0,         /* all arithmetic in FP64 */
@@ -123,7 +138,7 @@ typedef struct {
                                    any atom moved more than skin/2 */
     int32_t pair_eval;          /* fire_pair_eval (RGL): FIRE_PAIR_TABLE (default) or
                                    FIRE_PAIR_ANALYTIC */
-    int32_t reserved;
+    int32_t newton;             /* fire_newton (FP64 tabulated RGL only) */
 } fire_potential_t;
 
 /* FIRE 2.0 parameters: Table 1 names; dt_start is the MD timestep. */

@@ -27,6 +27,7 @@ FIRE_NORM_MAX_ATOM, FIRE_NORM_TWO, FIRE_NORM_INF = 0, 1, 2
 FIRE_POT_LJ, FIRE_POT_RGL = 0, 1
 FIRE_PREC_FP64, FIRE_PREC_FP32_PAIR = 0, 1
 FIRE_PAIR_TABLE, FIRE_PAIR_ANALYTIC = 0, 1
+FIRE_NEWTON_AUTO, FIRE_NEWTON_ON, FIRE_NEWTON_OFF = 0, 1, 2
 FIRE_INT_EULER_IMPLICIT, FIRE_INT_EULER_EXPLICIT, FIRE_INT_VERLET, FIRE_INT_LEAPFROG = 0, 1, 2, 3
 FIRE_VARIANT_FIRE2, FIRE_VARIANT_FIRE1 = 0, 1
 
@@ -58,7 +59,7 @@ class fire_potential_t(C.Structure):
                 ("eps", C.c_double), ("sigma", C.c_double), ("rc_lj", C.c_double),
                 ("A", C.c_double), ("xi", C.c_double), ("p", C.c_double), ("q", C.c_double),
                 ("r0", C.c_double), ("rs", C.c_double), ("rc", C.c_double),
-                ("skin", C.c_double), ("pair_eval", C.c_int32), ("reserved", C.c_int32)]
+                ("skin", C.c_double), ("pair_eval", C.c_int32), ("newton", C.c_int32)]
 
 
 class fire_params_t(C.Structure):
@@ -435,11 +436,12 @@ class Potential:
     rc: float = 0.0
     skin: float = 0.3
     pair_eval: int = FIRE_PAIR_TABLE
+    newton: int = FIRE_NEWTON_AUTO
 
     def c(self) -> fire_potential_t:
         return fire_potential_t(self.kind, self.precision, self.eps, self.sigma, self.rc_lj,
                                 self.A, self.xi, self.p, self.q, self.r0, self.rs, self.rc,
-                                self.skin, self.pair_eval, 0)
+                                self.skin, self.pair_eval, self.newton)
 
 
 class FireBatch:

@@ -136,6 +136,10 @@ double cutoff(const fire_potential_t& p) { return p.kind == FIRE_POT_LJ ? p.rc_l
 bool fixed64_form(const fire_potential_t& p) {
     return p.kind == FIRE_POT_RGL && p.precision == FIRE_PREC_FP64 && p.pair_eval == FIRE_PAIR_TABLE;
 }
+// ... on a half list with FP64 atomics (Newton's third law) or a full list.
+bool fixed64_half(const fire_potential_t& p) {
+    return fixed64_form(p) && p.newton != FIRE_NEWTON_OFF;
+}
 
 // minimum image stays unique within the list radius.
 GeoC make_geo(const fire_handle* h, const double box[3]) {
@@ -169,7 +173,8 @@ GeoC make_geo(const fire_handle* h, const double box[3]) {
     // magnitude (positions stay within about one box length of the box)
     const double margin = 1e-3 * rc + 8.0 * 1.2e-7 * (2.0 * lmax);
     g.rlist2f = (float)((rl + margin) * (rl + margin));
-    g.full = (h->pot.precision == FIRE_PREC_FP32_PAIR || fixed64_form(h->pot)) ? 1 : 0;
+    g.full = (h->pot.precision == FIRE_PREC_FP32_PAIR ||
+              (fixed64_form(h->pot) && !fixed64_half(h->pot))) ? 1 : 0;
     for (int a = 0; a < 3; ++a) {
         g.Lq[a] = (int)(unsigned)(unsigned long long)std::llrint(box[a] * h->b.qscale);
         g.Lq64[a] = std::llrint(std::ldexp(box[a], kFixedBits64));
@@ -256,9 +261,13 @@ void launch_forces(fire_handle* h, const GeoC& g, cudaStream_t s) {
     if (tab && h->pot.precision == FIRE_PREC_FP32_PAIR) {
         k_density32_tab<<<h->nb_tab_d, kTabBlock, h->smem_d, s>>>(h->b, h->potc, g);
         k_force32_tab<<<h->nb_tab_f, kTabBlock, h->smem_f, s>>>(h->b, h->potc, g);
+    } else if (tab && fixed64_half(h->pot)) {
+        k_density_ff<true><<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
+        k_embed<<<h->b.nb_embed, kElemBlock, 0, s>>>(h->b);
+        k_force_ff<true><<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
     } else if (tab) {
-        k_density_ff<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
-        k_force_ff<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
+        k_density_ff<false><<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
+        k_force_ff<false><<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
     } else if (h->pot.kind == FIRE_POT_RGL && h->pot.precision == FIRE_PREC_FP32_PAIR) {
         k_density32<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
         k_force32<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
@@ -728,6 +737,8 @@ static fire_status init_handle(fire_handle_t** hp, const fire_system_t* sys,
     if (!(sys->mass > 0.0) || !std::isfinite(sys->mass)) return fail(nullptr, FIRE_ERR_ARG, "mass must be > 0");
     if (pot->kind != FIRE_POT_LJ && pot->kind != FIRE_POT_RGL)
         return fail(nullptr, FIRE_ERR_ARG, "unknown potential kind %d", pot->kind);
+    if (pot->newton < FIRE_NEWTON_AUTO || pot->newton > FIRE_NEWTON_OFF)
+        return fail(nullptr, FIRE_ERR_ARG, "unknown newton setting %d", pot->newton);
     if (pot->pair_eval != FIRE_PAIR_TABLE && pot->pair_eval != FIRE_PAIR_ANALYTIC)
         return fail(nullptr, FIRE_ERR_ARG, "unknown pair_eval %d", pot->pair_eval);
     if (pot->precision != FIRE_PREC_FP64 &&
@@ -812,9 +823,10 @@ static fire_status init_handle(fire_handle_t** hp, const fire_system_t* sys,
     // control kernel adds up few.  nb_force + nb_embed energy partials,
     // nb_red rows of the (F, v) reductions.
     const bool fixed64 = fixed64_form(*pot);
-    b.accum = (fp32pair || fixed64) ? 0 : 1;
+    const bool whole = fp32pair || (fixed64 && !fixed64_half(*pot));   // no atomics
+    b.accum = whole ? 0 : 1;
     b.nb_force = ceil_div(h->n, kForceBlock);
-    b.nb_embed = (pot->kind == FIRE_POT_RGL && !fp32pair && !fixed64)
+    b.nb_embed = (pot->kind == FIRE_POT_RGL && !whole)
                      ? std::max(1, std::min(ceil_div(h->n, kElemBlock), sms * 8)) : 0;
     b.nb_red = std::max(1, std::min(ceil_div(h->n, kElemBlock), sms * 4));
     if (pot->kind == FIRE_POT_RGL && pot->pair_eval == FIRE_PAIR_TABLE) {
@@ -1482,14 +1494,18 @@ fire_status fire_profile_stages(fire_handle_t* h, const double* pos, const doubl
         cudaEventRecord(ev[1], s);
         const bool tab = rgl && h->pot.pair_eval == FIRE_PAIR_TABLE;
         if (tab && f32) k_density32_tab<<<h->nb_tab_d, kTabBlock, h->smem_d, s>>>(h->b, h->potc, g);
-        else if (tab) k_density_ff<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
+        else if (tab && fixed64_half(h->pot))
+            k_density_ff<true><<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
+        else if (tab) k_density_ff<false><<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
         else if (rgl && f32) k_density32<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
         else if (rgl) k_density<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
         cudaEventRecord(ev[2], s);
-        if (rgl && !f32 && !tab) k_embed<<<h->b.nb_embed, kElemBlock, 0, s>>>(h->b);
+        if (h->b.nb_embed > 0) k_embed<<<h->b.nb_embed, kElemBlock, 0, s>>>(h->b);
         cudaEventRecord(ev[3], s);
         if (tab && f32) k_force32_tab<<<h->nb_tab_f, kTabBlock, h->smem_f, s>>>(h->b, h->potc, g);
-        else if (tab) k_force_ff<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
+        else if (tab && fixed64_half(h->pot))
+            k_force_ff<true><<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
+        else if (tab) k_force_ff<false><<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
         else if (rgl && f32) k_force32<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
         else if (rgl) k_force_rgl<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, g);
         else k_force_lj<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);

@@ -390,7 +390,12 @@ __global__ void k_embed(Bufs b) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < b.n; i += gridDim.x * blockDim.x) {
         const double rho = b.rho[i];
         const double sq = sqrt(rho);
-        b.fp[i] = rho > 0.0 ? -0.5 / sq : 0.0;
+        const double fp = rho > 0.0 ? -0.5 / sq : 0.0;
+        b.fp[i] = fp;
+        if (b.fpff) {   // FP64 form: F' as a float pair for the force pass
+            const ffloat q = f64_to_ff(fp);
+            b.fpff[i] = make_float2(q.hi, q.lo);
+        }
         emb -= sq;
         if (b.eatom) b.eatom[i] -= sq;
     }
@@ -692,7 +697,7 @@ __device__ __forceinline__ ffloat pair_sep_ff(const Bufs& b, const long long* qt
     dx = fixed_to_ff(ix);
     dy = fixed_to_ff(iy);
     dz = fixed_to_ff(iz);
-    return ff_add(ff_add(ff_mul(dx, dx), ff_mul(dy, dy)), ff_mul(dz, dz));
+    return ff_norm2(dx, dy, dz);
 }
 
 __device__ __forceinline__ void load_row(const float* tab, int k, float row[kFFRow]) {
@@ -707,9 +712,12 @@ __device__ __forceinline__ void load_row(const float* tab, int k, float row[kFFR
     }
 }
 
-// Pass 1: rho_i, F'(rho_i) (FP64 per atom) and the atom's energy
-// sum_j phi - sqrt(rho_i).  Pairs compressed below r0/2 fall back to the
-// FP64 exponentials.
+// Pass 1.  Full list (HALF = false): rho_i, F'(rho_i) (FP64 per atom) and the
+// atom's energy sum_j phi - sqrt(rho_i), all in the atom's thread.  Half
+// list (HALF = true): rho_i and rho_j (FP64 atomics), 2 phi per pair credited
+// to i; k_embed then forms F'(rho) and the embedding energy.  Pairs
+// compressed below r0/2 fall back to the FP64 exponentials.
+template <bool HALF>
 __global__ void __launch_bounds__(kForceBlock) k_density_ff(Bufs b, PotC P, GeoC g) {
     __shared__ long long qt[375];
     __shared__ double etab[kExpTableSize];
@@ -735,31 +743,40 @@ __global__ void __launch_bounds__(kForceBlock) k_density_ff(Bufs b, PotC P, GeoC
                 load_row(b.tab_ffd, ff_index(P.tab, uf), row);
                 ffloat v[2];
                 ff_row_eval(row, r2, v);
-                erep = ff_add(erep, v[0]);
+                erep = ff_add(erep, HALF ? ff_scale2(v[0], 2.f) : v[0]);
                 rho = ff_add(rho, v[1]);
+                if (HALF) atomicAdd(&b.rho[j], ff_to_f64(v[1]));
             } else {
                 double rinv, phi, dphi, gg, dg;
                 rgl_pair64(P, ff_to_f64(r2), etab, rinv, phi, dphi, gg, dg);
-                erep = ff_add(erep, f64_to_ff(phi));
+                erep = ff_add(erep, f64_to_ff(HALF ? 2.0 * phi : phi));
                 rho = ff_add(rho, f64_to_ff(gg));
+                if (HALF) atomicAdd(&b.rho[j], gg);
             }
         }
-        const double rho_d = ff_to_f64(rho);
-        const double sq = sqrt(rho_d);
-        const double fp = rho_d > 0.0 ? -0.5 / sq : 0.0;
-        b.rho[i] = rho_d;
-        b.fp[i] = fp;
-        const ffloat fpf = f64_to_ff(fp);
-        b.fpff[i] = make_float2(fpf.hi, fpf.lo);
-        e_atom = ff_to_f64(erep) - sq;
-        if (b.eatom) b.eatom[i] = e_atom;
+        if (HALF) {
+            atomicAdd(&b.rho[i], ff_to_f64(rho));
+            e_atom = ff_to_f64(erep);
+            if (b.eatom) b.eatom[i] = e_atom;
+        } else {
+            const double rho_d = ff_to_f64(rho);
+            const double sq = sqrt(rho_d);
+            const double fp = rho_d > 0.0 ? -0.5 / sq : 0.0;
+            b.rho[i] = rho_d;
+            b.fp[i] = fp;
+            const ffloat fpf = f64_to_ff(fp);
+            b.fpff[i] = make_float2(fpf.hi, fpf.lo);
+            e_atom = ff_to_f64(erep) - sq;
+            if (b.eatom) b.eatom[i] = e_atom;
+        }
     }
     const double s = block_sum(e_atom, red);
     if (threadIdx.x == 0) b.epart[blockIdx.x] = s;
 }
 
-// Pass 2: F_i = sum_j [2 phi'/r + (F'_i + F'_j) g'/r] (x_j - x_i), written
-// whole (F = -grad E, Sec. 2.1).
+// Pass 2: F_i = sum_j [2 phi'/r + (F'_i + F'_j) g'/r] (x_j - x_i) (F = -grad E,
+// Sec. 2.1); full list: written whole; half list: F_i and F_j by FP64 atomics.
+template <bool HALF>
 __global__ void __launch_bounds__(kForceBlock) k_force_ff(Bufs b, PotC P, GeoC g) {
     __shared__ long long qt[375];
     __shared__ double etab[kExpTableSize];
@@ -793,13 +810,25 @@ __global__ void __launch_bounds__(kForceBlock) k_force_ff(Bufs b, PotC P, GeoC g
         }
         const float2 fpj2 = b.fpff[j];
         const ffloat fs = ff_add(c[0], ff_mul(ff_add(fpi, {fpj2.x, fpj2.y}), c[1]));
-        fx = ff_add(fx, ff_mul(fs, dx));
-        fy = ff_add(fy, ff_mul(fs, dy));
-        fz = ff_add(fz, ff_mul(fs, dz));
+        const ffloat tx = ff_mul(fs, dx), ty = ff_mul(fs, dy), tz = ff_mul(fs, dz);
+        fx = ff_add(fx, tx);
+        fy = ff_add(fy, ty);
+        fz = ff_add(fz, tz);
+        if (HALF) {
+            atomicAdd(&b.f[j].x, -ff_to_f64(tx));
+            atomicAdd(&b.f[j].y, -ff_to_f64(ty));
+            atomicAdd(&b.f[j].z, -ff_to_f64(tz));
+        }
     }
-    dvec4 f = make_dvec4(ff_to_f64(fx), ff_to_f64(fy), ff_to_f64(fz), 0.0);
-    mask_force(b, i, f);
-    b.f[i] = f;
+    if (HALF) {   // k_reduce applies the frozen-DOF mask
+        atomicAdd(&b.f[i].x, ff_to_f64(fx));
+        atomicAdd(&b.f[i].y, ff_to_f64(fy));
+        atomicAdd(&b.f[i].z, ff_to_f64(fz));
+    } else {
+        dvec4 f = make_dvec4(ff_to_f64(fx), ff_to_f64(fy), ff_to_f64(fz), 0.0);
+        mask_force(b, i, f);
+        b.f[i] = f;
+    }
 }
 
 // FP32-pair pass 1 (full list, tables): u = r^2 - r0^2 exact in fixed point,

@@ -415,7 +415,20 @@ __host__ __device__ __forceinline__ ffloat fixed_to_ff(long long n) {
     const int b = (int)(n - (a << 23));                   // 0 <= b < 2^23
     const float hi = (float)(int)a * 0x1p-21f;            // 2^(23 - 44)
     const float lo = (float)b * 0x1p-44f;
-    return two_sum(hi, lo);
+    return fast_two_sum(hi, lo);   // |hi| >= 2^-21 > lo >= 0, or hi = 0
+}
+
+// x^2 + y^2 + z^2 of normalised float pairs: exact products of the high
+// parts, the cross terms 2 hi lo added to their errors (lo^2 < 2^-48 hi^2 is
+// dropped), one renormalisation at the end.
+__host__ __device__ __forceinline__ ffloat ff_norm2(ffloat x, ffloat y, ffloat z) {
+    const float px = mul_rn(x.hi, x.hi), py = mul_rn(y.hi, y.hi), pz = mul_rn(z.hi, z.hi);
+    const float ex = fmaf(2.f * x.hi, x.lo, fmaf(x.hi, x.hi, -px));
+    const float ey = fmaf(2.f * y.hi, y.lo, fmaf(y.hi, y.hi, -py));
+    const float ez = fmaf(2.f * z.hi, z.lo, fmaf(z.hi, z.hi, -pz));
+    const ffloat s1 = two_sum(px, py);
+    const ffloat s2 = two_sum(s1.hi, pz);
+    return fast_two_sum(s2.hi, add_rn(add_rn(s1.lo, s2.lo), add_rn(add_rn(ex, ey), ez)));
 }
 
 // Host evaluation with the kernels' arithmetic (diagnostic): row of the

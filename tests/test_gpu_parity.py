@@ -557,3 +557,27 @@ def test_frozen_mask_changes_take_effect_and_bad_masks_are_rejected():
     # (FP64 atomics: the two runs may differ in the last bits)
     assert abs(r2.iterations - r0.iterations) <= 2
     assert abs(r2.energy - r0.energy) / c.n < 1e-10
+
+
+# ----------------------------------------------------------------------------
+# FP64 tabulated form: half list with atomics (Newton's third law) or full list
+
+@pytest.mark.parametrize("newton", [fg.FIRE_NEWTON_ON, fg.FIRE_NEWTON_OFF])
+def test_fp64_table_newton_settings_match_oracle(newton):
+    c = fi.rgl_vacancy_box(ncell=7, seed=95, n_vac=4, sigma=0.08)
+    eo, fo = oracle.energy_forces(c.x, c.box, ora_rgl(), mode=oracle.FORCE_CELLS)
+    pot = rgl_pot()
+    pot.newton = newton
+    with fg.FireHandle(c.n, fi.CU_MASS, pot, dt_start=fi.CU_DT) as h:
+        e, f = h.energy_forces(c.x, c.box)
+        x1 = c.x.copy()
+        r1 = h.minimize(x1, c.box, 1e-6, 100000)
+        x2 = c.x.copy()
+        r2 = h.minimize(x2, c.box, 1e-6, 100000)
+    assert np.abs(f - fo).max() / np.abs(fo).max() < 1e-10
+    assert e == pytest.approx(eo, rel=1e-12)
+    _, ro, _ = oracle.fire2(c.x, c.box, ora_rgl(), oracle.Params(dt_start=fi.CU_DT), fi.CU_MASS,
+                            1e-6, 100000, mode=oracle.FORCE_CELLS)
+    assert_relax_parity(c, r1, ro, 1e-6)
+    if newton == fg.FIRE_NEWTON_OFF:   # no atomics: the same run twice, bit for bit
+        assert np.array_equal(x1, x2) and r1.energy == r2.energy
