@@ -38,6 +38,17 @@ EV_PER_A_AMU_TO_A_PS2 = 1.602176634e-19 / (1e-10 * 1.66053906660e-27) * 1e-14
 CU_MASS = CU_MASS_AMU / EV_PER_A_AMU_TO_A_PS2   # eV ps^2 / A^2, so that a = F / m
 CU_DT = 0.001          # ps
 
+# Stillinger-Weber silicon (Stillinger and Weber, Phys. Rev. B 31, 5262
+# (1985)): eps [eV], sigma [A] and the dimensionless A, B, p, q, a, lambda,
+# gamma of the published parameter set.
+SW_SI = dict(eps=2.1683, sigma=2.0951, sw_A=7.049556277, sw_B=0.6022245584, sw_p=4.0,
+             sw_q=0.0, sw_a=1.80, sw_lambda=21.0, sw_gamma=1.20)
+# diamond lattice constant of the pair minimum: nearest neighbours at 2^(1/6) sigma
+SI_A = 4.0 * 2.0 ** (1.0 / 6.0) * SW_SI["sigma"] / np.sqrt(3.0)
+SI_MASS_AMU = 28.0855
+SI_MASS = SI_MASS_AMU / 9648.533212331001   # eV ps^2 / A^2 (see CU_MASS)
+SI_DT = 0.001          # ps
+
 FIRE_TABLE1 = dict(tmax=10.0, tmin=0.02, dtgrow=1.1, dtshrink=0.5, alpha0=0.25,
                    alphashrink=0.99, delaystep=20, vdfmax=2000, halfstepback=True,
                    initialdelay=True)
@@ -159,3 +170,31 @@ def neb_vacancy_hop(ncell: int = 3, seed: int = 6, n_img: int = 5, sigma: float 
     return Config(f"neb_cu{ncell}_hop", path, box,
                   meta=dict(vacancy_site=sites[v], target_site=sites[w], hopper=k, ncell=ncell,
                             n_img=n_img))
+
+
+_DIAMOND_BASIS = np.array([[0.0, 0.0, 0.0], [0.5, 0.5, 0.0], [0.5, 0.0, 0.5], [0.0, 0.5, 0.5],
+                           [0.25, 0.25, 0.25], [0.75, 0.75, 0.25], [0.75, 0.25, 0.75],
+                           [0.25, 0.75, 0.75]])
+
+
+def diamond_sites(n: int, a: float) -> np.ndarray:
+    """Diamond-lattice sites of an n x n x n block of cubic cells (8 per cell)."""
+    ix, iy, iz = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    corners = np.stack([ix, iy, iz], axis=-1).reshape(-1, 1, 3).astype(np.float64)
+    return ((corners + _DIAMOND_BASIS[None]) * a).reshape(-1, 3)
+
+
+def sw_si_vacancy_box(ncell: int = 8, seed: int = 7, n_vac: int = 1, sigma: float = 0.05,
+                      a: float | None = None) -> Config:
+    """Periodic diamond Si box (Stillinger-Weber workload, the paper's
+    three-body case): n_vac seeded vacancies, Gaussian noise per component."""
+    a = SI_A if a is None else a
+    rng = np.random.Generator(np.random.PCG64(seed))
+    sites = diamond_sites(ncell, a)
+    vac = np.sort(rng.choice(len(sites), size=n_vac, replace=False)) if n_vac > 0 else np.zeros(0, int)
+    keep = np.ones(len(sites), bool)
+    keep[vac] = False
+    lattice = sites[keep]
+    x = lattice + rng.normal(0.0, sigma, size=lattice.shape)
+    return Config(f"sw_si{ncell}_vac{n_vac}", x, np.full(3, ncell * a),
+                  meta=dict(vacancies=vac.tolist(), lattice=lattice, ncell=ncell))

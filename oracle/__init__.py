@@ -27,7 +27,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "fire_oracle.c")
 _LIB = os.path.join(_HERE, "_build", "libfire_oracle.so")
 
-POT_LJ, POT_RGL, POT_QUAD, POT_DWELL = 0, 1, 2, 3
+POT_LJ, POT_RGL, POT_QUAD, POT_DWELL, POT_SW = 0, 1, 2, 3, 4
 FORCE_BRUTE, FORCE_CELLS = 0, 1
 STOP_FTOL, STOP_MAXITER, STOP_MAXVDOTF = 0, 1, 2
 NORM_MAX_ATOM, NORM_TWO, NORM_INF = 0, 1, 2
@@ -46,7 +46,10 @@ class _Pot(C.Structure):
                 ("A", C.c_double), ("xi", C.c_double), ("p", C.c_double), ("q", C.c_double),
                 ("r0", C.c_double), ("rs", C.c_double), ("rc", C.c_double),
                 ("quad_k", C.POINTER(C.c_double)), ("quad_x0", C.POINTER(C.c_double)),
-                ("dwell", C.POINTER(C.c_double))]
+                ("dwell", C.POINTER(C.c_double)),
+                ("sw_A", C.c_double), ("sw_B", C.c_double), ("sw_p", C.c_double),
+                ("sw_q", C.c_double), ("sw_a", C.c_double), ("sw_lambda", C.c_double),
+                ("sw_gamma", C.c_double)]
 
 
 class _Params(C.Structure):
@@ -134,8 +137,9 @@ def max_threads() -> int:
 
 @dataclass
 class Potential:
-    """Potential description.  kind: 'lj', 'rgl', 'quad' (test well) or 'dwell'
-    (double-well test surface, dwell = (h, a, c, ky, kz))."""
+    """Potential description.  kind: 'lj', 'rgl', 'sw' (Stillinger-Weber with
+    eps, sigma and the sw_* fields), 'quad' (test well) or 'dwell' (double-well
+    test surface, dwell = (h, a, c, ky, kz))."""
     kind: str
     eps: float = 1.0
     sigma: float = 1.0
@@ -150,6 +154,13 @@ class Potential:
     quad_k: np.ndarray | None = None
     quad_x0: np.ndarray | None = None
     dwell: tuple | None = None
+    sw_A: float = 0.0
+    sw_B: float = 0.0
+    sw_p: float = 0.0
+    sw_q: float = 0.0
+    sw_a: float = 0.0
+    sw_lambda: float = 0.0
+    sw_gamma: float = 0.0
 
 
 @dataclass
@@ -197,10 +208,11 @@ def _sys(n, box, periodic, mass):
 
 
 def _pot(pot: Potential, keep: list):
-    kinds = {"lj": POT_LJ, "rgl": POT_RGL, "quad": POT_QUAD, "dwell": POT_DWELL}
+    kinds = {"lj": POT_LJ, "rgl": POT_RGL, "quad": POT_QUAD, "dwell": POT_DWELL, "sw": POT_SW}
     p = _Pot()
     p.kind = kinds[pot.kind]
-    for name in ("eps", "sigma", "rc_lj", "A", "xi", "p", "q", "r0", "rs", "rc"):
+    for name in ("eps", "sigma", "rc_lj", "A", "xi", "p", "q", "r0", "rs", "rc", "sw_A", "sw_B",
+                 "sw_p", "sw_q", "sw_a", "sw_lambda", "sw_gamma"):
         setattr(p, name, float(getattr(pot, name)))
     if pot.kind == "quad":
         k = np.ascontiguousarray(pot.quad_k, dtype=np.float64)

@@ -66,7 +66,7 @@
 #include <omp.h>
 #endif
 
-enum { POT_LJ = 0, POT_RGL = 1, POT_QUAD = 2, POT_DWELL = 3 };
+enum { POT_LJ = 0, POT_RGL = 1, POT_QUAD = 2, POT_DWELL = 3, POT_SW = 4 };
 enum { FORCE_BRUTE = 0, FORCE_CELLS = 1 };
 enum { STOP_FTOL = 0, STOP_MAXITER = 1, STOP_MAXVDOTF = 2 };
 enum { NORM_MAX_ATOM = 0, NORM_TWO = 1, NORM_INF = 2 };
@@ -92,6 +92,13 @@ typedef struct {
      * E = h ((x/a)^2 - 1)^2 + ky (y - c x^2)^2 + kz z^2; minima (+-a, c a^2, 0)
      * with E = 0, first-order saddle (0, 0, 0) with E = h. */
     const double *dwell;
+    /* Stillinger-Weber (the paper's three-body family, Sec. 4 case 5), with
+     * eps and sigma above: E = sum_{i<j} phi2(r_ij) + sum_i sum_{j<k} phi3,
+     * phi2 = A eps [B (sigma/r)^p - (sigma/r)^q] exp(sigma / (r - a sigma)),
+     * phi3 = lambda eps (cos theta_jik + 1/3)^2
+     *        exp(gamma sigma / (r_ij - a sigma)) exp(gamma sigma / (r_ik - a sigma)),
+     * every term zero beyond r = a sigma. */
+    double sw_A, sw_B, sw_p, sw_q, sw_a, sw_lambda, sw_gamma;
 } ora_pot;
 
 typedef struct {
@@ -132,6 +139,7 @@ static double min_image(double d, double L, int periodic) {
 }
 
 static double pot_cutoff(const ora_pot *pot) {
+    if (pot->kind == POT_SW) return pot->sw_a * pot->sigma;
     return pot->kind == POT_LJ ? pot->rc_lj : pot->rc;
 }
 
@@ -291,6 +299,94 @@ static int check_box(const ora_sys *sys, const ora_pot *pot) {
     return 0;
 }
 
+/* Stillinger-Weber energy and forces (all atoms), written plainly: the pair
+ * sum over j > i, then for every centre i every pair j < k of its neighbours
+ * within a sigma, with the gradient of each term added to i, j and k.
+ * F = -grad E (Sec. 2.1). */
+static void sw_phi2(const ora_pot *pot, double r, double *e, double *de) {
+    const double s = pot->sigma, rc = pot->sw_a * s;
+    const double sr = s / r, bp = pot->sw_B * pow(sr, pot->sw_p), bq = pow(sr, pot->sw_q);
+    const double ex = exp(s / (r - rc));
+    *e = pot->sw_A * pot->eps * (bp - bq) * ex;
+    /* d/dr: A eps ex [(-p bp + q bq) / r - (bp - bq) s / (r - rc)^2] */
+    *de = pot->sw_A * pot->eps * ex *
+          ((-pot->sw_p * bp + pot->sw_q * bq) / r - (bp - bq) * s / ((r - rc) * (r - rc)));
+}
+
+static int sw_energy_forces(const ora_sys *sys, const ora_pot *pot, const double *x, double *f,
+                            double *energy, int mode) {
+    const int64_t n = sys->n;
+    const double rc = pot_cutoff(pot), rc2 = rc * rc, s = pot->sigma;
+    ora_grid g;
+    grid_build(&g, sys, x, rc, mode);
+    const int64_t cap = grid_max_candidates(&g) + 1;
+    int64_t *cand = (int64_t *)malloc((size_t)cap * sizeof(int64_t));
+    int64_t *nb = (int64_t *)malloc((size_t)cap * sizeof(int64_t));
+    double *dv = (double *)malloc((size_t)cap * 3 * sizeof(double));
+    double *rv = (double *)malloc((size_t)cap * sizeof(double));
+    if (f)
+        for (int64_t k = 0; k < 3 * n; ++k) f[k] = 0.0;
+    double etot = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        const int64_t m = grid_candidates(&g, sys, x, i, cand);
+        int64_t cnt = 0;
+        for (int64_t c = 0; c < m; ++c) {
+            const int64_t j = cand[c];
+            double d[3];
+            for (int a = 0; a < 3; ++a)
+                d[a] = min_image(x[3 * j + a] - x[3 * i + a], sys->box[a], sys->periodic[a]);
+            const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            if (r2 >= rc2) continue;
+            const double r = sqrt(r2);
+            nb[cnt] = j;
+            rv[cnt] = r;
+            for (int a = 0; a < 3; ++a) dv[3 * cnt + a] = d[a];
+            ++cnt;
+            if (j > i) {   /* pair term once per pair */
+                double e2, de2;
+                sw_phi2(pot, r, &e2, &de2);
+                etot += e2;
+                if (f)
+                    for (int a = 0; a < 3; ++a) {   /* dE/dx_j = de2 d/r */
+                        f[3 * j + a] -= de2 * d[a] / r;
+                        f[3 * i + a] += de2 * d[a] / r;
+                    }
+            }
+        }
+        /* three-body terms centred on i */
+        for (int64_t p = 0; p < cnt; ++p)
+            for (int64_t q = p + 1; q < cnt; ++q) {
+                const double rj = rv[p], rk = rv[q];
+                const double *dj = dv + 3 * p, *dk = dv + 3 * q;
+                const double cs = (dj[0] * dk[0] + dj[1] * dk[1] + dj[2] * dk[2]) / (rj * rk);
+                const double ej = exp(pot->sw_gamma * s / (rj - rc));
+                const double ek = exp(pot->sw_gamma * s / (rk - rc));
+                const double w = cs + 1.0 / 3.0;
+                const double h = pot->sw_lambda * pot->eps * w * w * ej * ek;
+                etot += h;
+                if (!f) continue;
+                const double dh_dc = 2.0 * pot->sw_lambda * pot->eps * w * ej * ek;
+                const double dh_drj = -h * pot->sw_gamma * s / ((rj - rc) * (rj - rc));
+                const double dh_drk = -h * pot->sw_gamma * s / ((rk - rc) * (rk - rc));
+                for (int a = 0; a < 3; ++a) {
+                    const double uj = dj[a] / rj, uk = dk[a] / rk;
+                    const double gj = dh_drj * uj + dh_dc * (uk - cs * uj) / rj;   /* dh/dx_j */
+                    const double gk = dh_drk * uk + dh_dc * (uj - cs * uk) / rk;   /* dh/dx_k */
+                    f[3 * nb[p] + a] -= gj;
+                    f[3 * nb[q] + a] -= gk;
+                    f[3 * i + a] += gj + gk;
+                }
+            }
+    }
+    free(cand);
+    free(nb);
+    free(dv);
+    free(rv);
+    grid_free(&g);
+    *energy = etot;
+    return 0;
+}
+
 /* Evaluates E and (if f != NULL) F for the atoms listed in `which` (or all
  * atoms when which == NULL).  E is always the total energy. */
 static int energy_forces_impl(const ora_sys *sys, const ora_pot *pot, const double *x,
@@ -325,6 +421,10 @@ static int energy_forces_impl(const ora_sys *sys, const ora_pot *pot, const doub
         }
         *energy = e;
         return 0;
+    }
+    if (pot->kind == POT_SW) {
+        if (which) return -1;   /* all atoms only */
+        return sw_energy_forces(sys, pot, x, f, energy, mode);
     }
     const double rc = pot_cutoff(pot), rc2 = rc * rc;
     ora_grid g;

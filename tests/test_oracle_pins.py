@@ -486,3 +486,68 @@ def test_frozen_slab_stays_put_and_the_rest_relaxes():
     fm[sel, :2] = 0.0
     assert np.linalg.norm(fm, axis=1).max() < 1e-6
     assert np.abs(f[sel, :2]).max() > 1e-4
+
+
+# ----------------------------------------------------------------------------
+# Stillinger-Weber (the paper's three-body family, Sec. 4 case 5)
+
+def sw():
+    return oracle.Potential("sw", **fi.SW_SI)
+
+
+@pytest.mark.parametrize("ncell", [3, 4])
+def test_sw_diamond_cohesive_energy_closed_form(ncell):
+    # Nearest neighbours at the pair minimum 2^(1/6) sigma, where the
+    # published A, B give phi2 = -eps; second neighbours (1.633 r) lie beyond
+    # a sigma and every bond angle is tetrahedral (cos = -1/3, phi3 = 0):
+    # E/atom = 4/2 (-eps) = -2 eps = -4.3366 eV, with zero force.
+    x = fi.diamond_sites(ncell, fi.SI_A)
+    e, f = oracle.energy_forces(x, [ncell * fi.SI_A] * 3, sw())
+    assert e / len(x) == pytest.approx(-2.0 * fi.SW_SI["eps"], rel=1e-9)
+    assert np.abs(f).max() < 1e-12
+
+
+def test_sw_dimer_minimum_and_trimer_angle_shape():
+    box = [100.0] * 3
+    r = 2.0 ** (1.0 / 6.0) * fi.SW_SI["sigma"]
+    dimer = np.array([[0.0, 0.0, 0.0], [r, 0.0, 0.0]])
+    e2, _ = oracle.energy_forces(dimer, box, sw(), periodic=(0, 0, 0))
+    assert e2 == pytest.approx(-fi.SW_SI["eps"], rel=1e-9)
+    # trimer j-i-k with both bonds r and the j-k distance beyond the cut-off:
+    # E(theta) - 2 E_dimer is the three-body term alone, proportional to
+    # (cos theta + 1/3)^2 at fixed bond lengths (zero at the tetrahedral angle)
+    def trimer(theta):
+        x = np.array([[0.0, 0.0, 0.0], [r, 0.0, 0.0], [r * np.cos(theta), r * np.sin(theta), 0.0]])
+        e, _ = oracle.energy_forces(x, box, sw(), periodic=(0, 0, 0))
+        return e - 2.0 * e2
+    tet = np.arccos(-1.0 / 3.0)
+    assert abs(trimer(tet)) < 1e-13
+    t1, t2 = 2.2, 2.6
+    ratio = trimer(t1) / trimer(t2)
+    assert ratio == pytest.approx((np.cos(t1) + 1 / 3) ** 2 / (np.cos(t2) + 1 / 3) ** 2, rel=1e-12)
+
+
+def test_sw_forces_finite_difference_and_sum():
+    c = fi.sw_si_vacancy_box(ncell=3, seed=3, n_vac=1, sigma=0.08)
+    e, f = oracle.energy_forces(c.x, c.box, sw())
+    assert np.abs(f.sum(0)).max() < 1e-11
+    h = 1e-5
+    for i, d in [(0, 0), (5, 1), (17, 2), (40, 0), (100, 1)]:
+        xp, xm = c.x.copy(), c.x.copy()
+        xp[i, d] += h
+        xm[i, d] -= h
+        ep, _ = oracle.energy_forces(xp, c.box, sw())
+        em, _ = oracle.energy_forces(xm, c.box, sw())
+        assert f[i, d] == pytest.approx(-(ep - em) / (2 * h), rel=1e-7, abs=1e-8)
+
+
+def test_sw_cell_grid_matches_all_pairs_and_relaxation_converges():
+    c = fi.sw_si_vacancy_box(ncell=4, seed=4, n_vac=1, sigma=0.05)
+    e1, f1 = oracle.energy_forces(c.x, c.box, sw(), mode=oracle.FORCE_BRUTE)
+    e2, f2 = oracle.energy_forces(c.x, c.box, sw(), mode=oracle.FORCE_CELLS)
+    assert e1 == e2 and np.array_equal(f1, f2)
+    xf, res, _ = oracle.fire2(c.x, c.box, sw(), oracle.Params(dt_start=fi.SI_DT), fi.SI_MASS,
+                              1e-6, 100000, mode=oracle.FORCE_CELLS)
+    assert res.stop == oracle.STOP_FTOL
+    # a vacancy costs energy relative to the perfect crystal
+    assert res.energy - (-2.0 * fi.SW_SI["eps"]) * c.n > 1.0
