@@ -36,7 +36,7 @@
 extern "C" {
 #endif
 
-#define FIRE2_ABI_VERSION 5
+#define FIRE2_ABI_VERSION 6
 
 typedef enum {
     FIRE_OK = 0,
@@ -65,7 +65,8 @@ typedef enum {
 
 typedef enum {
     FIRE_POT_LJ = 0,            /* 12-6 Lennard-Jones, energy shifted to 0 at rc */
-    FIRE_POT_RGL = 1            /* second-moment (RGL) EAM, quintic taper on [rs, rc) */
+    FIRE_POT_RGL = 1,           /* second-moment (RGL) EAM, quintic taper on [rs, rc) */
+    FIRE_POT_SW = 2             /* Stillinger-Weber three-body (Sec. 4 case 5 family), FP64 */
 } fire_pot_kind;
 
 /* How the RGL pair functions phi(r), g(r) and their derivatives are
@@ -139,6 +140,11 @@ typedef struct {
     int32_t pair_eval;          /* fire_pair_eval (RGL): FIRE_PAIR_TABLE (default) or
                                    FIRE_PAIR_ANALYTIC */
     int32_t newton;             /* fire_newton (FP64 tabulated RGL only) */
+    /* SW (with eps, sigma above): E = sum_{i<j} phi2(r_ij) + sum_i sum_{j<k} phi3,
+     * phi2 = sw_A eps [sw_B (sigma/r)^sw_p - (sigma/r)^sw_q] exp(sigma / (r - sw_a sigma)),
+     * phi3 = sw_lambda eps (cos theta_jik + 1/3)^2 exp(sw_gamma sigma / (r_ij - sw_a sigma))
+     *        exp(sw_gamma sigma / (r_ik - sw_a sigma)); cut-off sw_a sigma.  FP64 only. */
+    double sw_A, sw_B, sw_p, sw_q, sw_a, sw_lambda, sw_gamma;
 } fire_potential_t;
 
 /* FIRE 2.0 parameters: Table 1 names; dt_start is the MD timestep. */

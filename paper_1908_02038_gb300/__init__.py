@@ -24,7 +24,7 @@ FIRE_OK, FIRE_ERR_ARG, FIRE_ERR_CUDA, FIRE_ERR_NOMEM = 0, 1, 2, 3
 FIRE_ERR_NONFINITE, FIRE_ERR_NBR_OVERFLOW, FIRE_ERR_TIMEOUT, FIRE_ERR_STATE = 4, 5, 6, 7
 FIRE_STOP_FTOL, FIRE_STOP_MAXITER, FIRE_STOP_MAXVDOTF = 0, 1, 2
 FIRE_NORM_MAX_ATOM, FIRE_NORM_TWO, FIRE_NORM_INF = 0, 1, 2
-FIRE_POT_LJ, FIRE_POT_RGL = 0, 1
+FIRE_POT_LJ, FIRE_POT_RGL, FIRE_POT_SW = 0, 1, 2
 FIRE_PREC_FP64, FIRE_PREC_FP32_PAIR = 0, 1
 FIRE_PAIR_TABLE, FIRE_PAIR_ANALYTIC = 0, 1
 FIRE_NEWTON_AUTO, FIRE_NEWTON_ON, FIRE_NEWTON_OFF = 0, 1, 2
@@ -59,7 +59,10 @@ class fire_potential_t(C.Structure):
                 ("eps", C.c_double), ("sigma", C.c_double), ("rc_lj", C.c_double),
                 ("A", C.c_double), ("xi", C.c_double), ("p", C.c_double), ("q", C.c_double),
                 ("r0", C.c_double), ("rs", C.c_double), ("rc", C.c_double),
-                ("skin", C.c_double), ("pair_eval", C.c_int32), ("newton", C.c_int32)]
+                ("skin", C.c_double), ("pair_eval", C.c_int32), ("newton", C.c_int32),
+                ("sw_A", C.c_double), ("sw_B", C.c_double), ("sw_p", C.c_double),
+                ("sw_q", C.c_double), ("sw_a", C.c_double), ("sw_lambda", C.c_double),
+                ("sw_gamma", C.c_double)]
 
 
 class fire_params_t(C.Structure):
@@ -437,11 +440,19 @@ class Potential:
     skin: float = 0.3
     pair_eval: int = FIRE_PAIR_TABLE
     newton: int = FIRE_NEWTON_AUTO
+    sw_A: float = 0.0
+    sw_B: float = 0.0
+    sw_p: float = 0.0
+    sw_q: float = 0.0
+    sw_a: float = 0.0
+    sw_lambda: float = 0.0
+    sw_gamma: float = 0.0
 
     def c(self) -> fire_potential_t:
         return fire_potential_t(self.kind, self.precision, self.eps, self.sigma, self.rc_lj,
                                 self.A, self.xi, self.p, self.q, self.r0, self.rs, self.rc,
-                                self.skin, self.pair_eval, self.newton)
+                                self.skin, self.pair_eval, self.newton, self.sw_A, self.sw_B,
+                                self.sw_p, self.sw_q, self.sw_a, self.sw_lambda, self.sw_gamma)
 
 
 class FireBatch:

@@ -127,7 +127,10 @@ fire_status fail(fire_handle* h, fire_status code, const char* fmt, ...) {
 
 inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 
-double cutoff(const fire_potential_t& p) { return p.kind == FIRE_POT_LJ ? p.rc_lj : p.rc; }
+double cutoff(const fire_potential_t& p) {
+    if (p.kind == FIRE_POT_SW) return p.sw_a * p.sigma;
+    return p.kind == FIRE_POT_LJ ? p.rc_lj : p.rc;
+}
 
 // Neighbour geometry for a box.  The list radius is rc + skin, with the skin
 // reduced where a periodic axis is shorter than 2 (rc + skin) so that the
@@ -173,7 +176,7 @@ GeoC make_geo(const fire_handle* h, const double box[3]) {
     // magnitude (positions stay within about one box length of the box)
     const double margin = 1e-3 * rc + 8.0 * 1.2e-7 * (2.0 * lmax);
     g.rlist2f = (float)((rl + margin) * (rl + margin));
-    g.full = (h->pot.precision == FIRE_PREC_FP32_PAIR ||
+    g.full = (h->pot.precision == FIRE_PREC_FP32_PAIR || h->pot.kind == FIRE_POT_SW ||
               (fixed64_form(h->pot) && !fixed64_half(h->pot))) ? 1 : 0;
     for (int a = 0; a < 3; ++a) {
         g.Lq[a] = (int)(unsigned)(unsigned long long)std::llrint(box[a] * h->b.qscale);
@@ -275,6 +278,8 @@ void launch_forces(fire_handle* h, const GeoC& g, cudaStream_t s) {
         k_density<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
         k_embed<<<h->b.nb_embed, kElemBlock, 0, s>>>(h->b);
         k_force_rgl<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, g);
+    } else if (h->pot.kind == FIRE_POT_SW) {
+        k_force_sw<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
     } else {
         k_force_lj<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
     }
@@ -529,6 +534,9 @@ fire_status status_to_error(fire_handle* h, int st) {
         case ST_TIMEOUT: return fail(h, FIRE_ERR_TIMEOUT, "device loop exceeded its time budget");
         case ST_RANGE:
             return fail(h, FIRE_ERR_ARG, "positions lie more than one box length outside the box");
+        case ST_CROWDED:
+            return fail(h, FIRE_ERR_ARG,
+                        "more than %d atoms within the Stillinger-Weber cut-off of one atom", kSwMax);
         default: return fail(h, FIRE_ERR_CUDA, "unknown device status %d", st);
     }
 }
@@ -632,6 +640,19 @@ static bool fill_potc(fire_handle* h) {
     const fire_potential_t* pot = &h->pot;
     PotC& c = h->potc;
     c.kind = pot->kind;
+    if (pot->kind == FIRE_POT_SW) {
+        c.eps = pot->eps;
+        c.sw_sigma = pot->sigma;
+        c.sw_rc = pot->sw_a * pot->sigma;
+        c.rc2 = c.sw_rc * c.sw_rc;
+        c.sw_A = pot->sw_A;
+        c.sw_B = pot->sw_B;
+        c.sw_p = pot->sw_p;
+        c.sw_q = pot->sw_q;
+        c.sw_lambda = pot->sw_lambda;
+        c.sw_gamma = pot->sw_gamma;
+        return true;
+    }
     if (pot->kind == FIRE_POT_LJ) {
         c.rc2 = pot->rc_lj * pot->rc_lj;
         c.eps = pot->eps;
@@ -735,7 +756,7 @@ static fire_status init_handle(fire_handle_t** hp, const fire_system_t* sys,
     if (sys->n_atoms < 1 || sys->n_atoms > (int64_t)kIdxMask)
         return fail(nullptr, FIRE_ERR_ARG, "n_atoms = %lld outside [1, %u]", (long long)sys->n_atoms, kIdxMask);
     if (!(sys->mass > 0.0) || !std::isfinite(sys->mass)) return fail(nullptr, FIRE_ERR_ARG, "mass must be > 0");
-    if (pot->kind != FIRE_POT_LJ && pot->kind != FIRE_POT_RGL)
+    if (pot->kind != FIRE_POT_LJ && pot->kind != FIRE_POT_RGL && pot->kind != FIRE_POT_SW)
         return fail(nullptr, FIRE_ERR_ARG, "unknown potential kind %d", pot->kind);
     if (pot->newton < FIRE_NEWTON_AUTO || pot->newton > FIRE_NEWTON_OFF)
         return fail(nullptr, FIRE_ERR_ARG, "unknown newton setting %d", pot->newton);
@@ -747,6 +768,10 @@ static fire_status init_handle(fire_handle_t** hp, const fire_system_t* sys,
                     "precision %d not available for this potential (FP32-pair is RGL only)",
                     pot->precision);
     if (!(pot->skin >= 0.0)) return fail(nullptr, FIRE_ERR_ARG, "skin must be >= 0");
+    if (pot->kind == FIRE_POT_SW &&
+        !(pot->eps > 0.0 && pot->sigma > 0.0 && pot->sw_a > 0.0 && pot->sw_gamma >= 0.0 &&
+          std::isfinite(pot->sw_A + pot->sw_B + pot->sw_p + pot->sw_q + pot->sw_lambda)))
+        return fail(nullptr, FIRE_ERR_ARG, "SW needs eps, sigma, sw_a > 0 and finite parameters");
     if (pot->kind == FIRE_POT_LJ && !(pot->rc_lj > 0.0 && pot->sigma > 0.0 && pot->eps > 0.0))
         return fail(nullptr, FIRE_ERR_ARG, "LJ needs eps, sigma, rc_lj > 0");
     if (pot->kind == FIRE_POT_RGL &&
@@ -1508,6 +1533,7 @@ fire_status fire_profile_stages(fire_handle_t* h, const double* pos, const doubl
         else if (tab) k_force_ff<false><<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
         else if (rgl && f32) k_force32<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
         else if (rgl) k_force_rgl<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, g);
+        else if (h->pot.kind == FIRE_POT_SW) k_force_sw<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
         else k_force_lj<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
         cudaEventRecord(ev[4], s);
         launch_reduce(h, g, s);

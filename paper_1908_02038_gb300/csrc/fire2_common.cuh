@@ -28,7 +28,8 @@ constexpr int kTabBlock64 = 512;  // FP64 table kernel (both tables, ~112 KB, in
 constexpr int kElemBlock = 256;
 constexpr int kCtlThreads = 512;
 
-enum { ST_OK = 0, ST_NONFINITE = 4, ST_NBR_OVERFLOW = 5, ST_TIMEOUT = 6, ST_RANGE = 8 };
+enum { ST_OK = 0, ST_NONFINITE = 4, ST_NBR_OVERFLOW = 5, ST_TIMEOUT = 6, ST_RANGE = 8,
+       ST_CROWDED = 9 };
 enum { STOP_FTOL = 0, STOP_MAXITER = 1, STOP_MAXVDOTF = 2 };
 enum { POT_LJ = 0, POT_RGL = 1 };
 enum { CTL_INITIAL = 0, CTL_LOOP = 1, CTL_EVAL = 2 };
@@ -51,6 +52,8 @@ struct PotC {
     double rc2;            // interaction cut-off squared
     // LJ
     double eps, sigma2, lj_shift;
+    // SW (eps above): sigma, a sigma, and the published dimensionless set
+    double sw_sigma, sw_rc, sw_A, sw_B, sw_p, sw_q, sw_lambda, sw_gamma;
     // RGL
     double A, xi2, p, q2, r0inv, p_r0, q2_r0, rs, rc, winv;
     ExpC ex;               // constants of the table-driven exponential

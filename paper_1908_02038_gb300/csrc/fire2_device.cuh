@@ -445,6 +445,112 @@ __global__ void __launch_bounds__(kForceBlock) k_force_rgl(Bufs b, GeoC g) {
     atomicAdd(&b.f[i].z, fz);
 }
 
+// Stillinger-Weber, one pass over the full list (IEEE FP64): the pair term
+// from both ends (half its energy to each atom, its force on i), then the
+// three-body terms centred on i for every pair j < k of neighbours within
+// a sigma, their gradients added to i here and to j and k by FP64 atomics:
+//   h = lambda eps (c + 1/3)^2 e_j e_k,  e = exp(gamma sigma / (r - a sigma)),
+//   dh/dx_j = dh/dr_j u_j + dh/dc (u_k - c u_j) / r_j   (u = unit vectors).
+constexpr int kSwMax = 32;   // neighbours within a sigma per atom (a solid has 4)
+
+__device__ __forceinline__ void sw_pair(const PotC& P, double r, double& e2, double& de2) {
+    const double s = P.sw_sigma, rc = P.sw_rc;
+    const double sr = s / r, bp = P.sw_B * pow(sr, P.sw_p), bq = pow(sr, P.sw_q);
+    const double ex = exp(s / (r - rc));
+    e2 = P.sw_A * P.eps * (bp - bq) * ex;
+    de2 = P.sw_A * P.eps * ex * ((-P.sw_p * bp + P.sw_q * bq) / r - (bp - bq) * s / ((r - rc) * (r - rc)));
+}
+
+__global__ void __launch_bounds__(kForceBlock) k_force_sw(Bufs b, PotC P, GeoC g) {
+    __shared__ double3 tbl[125];
+    __shared__ double red[32];
+    if (b.st->done) return;
+    fill_shift_table(tbl, g);
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double e_i = 0.0;
+    if (i < b.n) {
+        const dvec4 xi = b.x[i];
+        const int m = b.nnbr[i];
+        int nj[kSwMax];
+        double ddx[kSwMax], ddy[kSwMax], ddz[kSwMax], rr[kSwMax], eg[kSwMax];
+        int cnt = 0;
+        double fx = 0.0, fy = 0.0, fz = 0.0;
+        const double s = P.sw_sigma, rc = P.sw_rc;
+        for (int k = 0; k < m; ++k) {
+            const uint32_t e = b.nbr[(size_t)k * b.n + i];
+            const int j = (int)(e & kIdxMask);
+            const int code = (int)(e >> kIdxBits);
+            const dvec4 xj = b.x[j];
+            double dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
+            if (code != kCodeZero) {
+                const double3 sh = tbl[code];
+                dx -= sh.x;
+                dy -= sh.y;
+                dz -= sh.z;
+            }
+            const double r2 = dx * dx + dy * dy + dz * dz;
+            if (!(r2 < P.rc2)) continue;
+            const double r = sqrt(r2);
+            double e2, de2;
+            sw_pair(P, r, e2, de2);
+            e_i += 0.5 * e2;
+            const double w = de2 / r;   // force on i from the pair: +phi2'(r) d / r
+            fx += w * dx;
+            fy += w * dy;
+            fz += w * dz;
+            if (cnt < kSwMax) {
+                nj[cnt] = j;
+                ddx[cnt] = dx;
+                ddy[cnt] = dy;
+                ddz[cnt] = dz;
+                rr[cnt] = r;
+                eg[cnt] = exp(P.sw_gamma * s / (r - rc));
+            }
+            ++cnt;
+        }
+        if (cnt > kSwMax) {
+            set_status(b.st, ST_CROWDED);
+            cnt = kSwMax;
+        }
+        for (int p = 0; p < cnt; ++p)
+            for (int q = p + 1; q < cnt; ++q) {
+                const double rj = rr[p], rk = rr[q];
+                const double cs = (ddx[p] * ddx[q] + ddy[p] * ddy[q] + ddz[p] * ddz[q]) / (rj * rk);
+                const double wv = cs + 1.0 / 3.0;
+                const double ee = eg[p] * eg[q];
+                const double h = P.sw_lambda * P.eps * wv * wv * ee;
+                e_i += h;
+                const double dh_dc = 2.0 * P.sw_lambda * P.eps * wv * ee;
+                const double dj = -h * P.sw_gamma * s / ((rj - rc) * (rj - rc));
+                const double dk = -h * P.sw_gamma * s / ((rk - rc) * (rk - rc));
+                const double ujx = ddx[p] / rj, ujy = ddy[p] / rj, ujz = ddz[p] / rj;
+                const double ukx = ddx[q] / rk, uky = ddy[q] / rk, ukz = ddz[q] / rk;
+                const double gjx = dj * ujx + dh_dc * (ukx - cs * ujx) / rj;
+                const double gjy = dj * ujy + dh_dc * (uky - cs * ujy) / rj;
+                const double gjz = dj * ujz + dh_dc * (ukz - cs * ujz) / rj;
+                const double gkx = dk * ukx + dh_dc * (ujx - cs * ukx) / rk;
+                const double gky = dk * uky + dh_dc * (ujy - cs * uky) / rk;
+                const double gkz = dk * ukz + dh_dc * (ujz - cs * ukz) / rk;
+                fx += gjx + gkx;
+                fy += gjy + gky;
+                fz += gjz + gkz;
+                atomicAdd(&b.f[nj[p]].x, -gjx);
+                atomicAdd(&b.f[nj[p]].y, -gjy);
+                atomicAdd(&b.f[nj[p]].z, -gjz);
+                atomicAdd(&b.f[nj[q]].x, -gkx);
+                atomicAdd(&b.f[nj[q]].y, -gky);
+                atomicAdd(&b.f[nj[q]].z, -gkz);
+            }
+        atomicAdd(&b.f[i].x, fx);
+        atomicAdd(&b.f[i].y, fy);
+        atomicAdd(&b.f[i].z, fz);
+        if (b.eatom) b.eatom[i] = e_i;
+    }
+    const double bs = block_sum(e_i, red);
+    if (threadIdx.x == 0) b.epart[blockIdx.x] = bs;
+}
+
 // Lennard-Jones, one pass: w = 24 eps [2 (s/r)^12 - (s/r)^6] / r^2,
 // F_i -= w d, F_j += w d; pair energy 4 eps [(s/r)^12 - (s/r)^6] - phi(rc).
 __global__ void __launch_bounds__(kForceBlock) k_force_lj(Bufs b, PotC P, GeoC g) {

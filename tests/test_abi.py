@@ -37,7 +37,7 @@ def test_library_exports_every_header_symbol(lib):
 
 
 def test_abi_version_and_defaults(lib):
-    assert fg.fire_abi_version() == 5
+    assert fg.fire_abi_version() == 6
     p = fg.fire_default_params(0.001)
     assert (p.tmax, p.tmin, p.dtgrow, p.dtshrink, p.alpha0, p.alphashrink) == \
         (10.0, 0.02, 1.1, 0.5, 0.25, 0.99)
@@ -51,7 +51,7 @@ def test_abi_version_and_defaults(lib):
 def test_struct_layouts_match_header(lib):
     # sizes of the C structs as the header lays them out on LP64
     assert ctypes.sizeof(fg.fire_system_t) == 8 + 8 + 12 + 4
-    assert ctypes.sizeof(fg.fire_potential_t) == 4 + 4 + 8 * 11 + 8
+    assert ctypes.sizeof(fg.fire_potential_t) == 4 + 4 + 8 * 11 + 8 + 8 * 7
     assert ctypes.sizeof(fg.fire_params_t) == 7 * 8 + 8 * 4 + 8
     assert ctypes.sizeof(fg.fire_result_t) == 8 + 8 * 3 + 4 + 4 + 8 * 5
 

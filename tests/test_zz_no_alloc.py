@@ -69,4 +69,4 @@ def test_noalloc_rejects_too_many_atoms(torch):
         fg.fire_energy_forces_noalloc(pot.c(), d_pos, [200.0] * 3, (1, 1, 1), None, None)
     assert e.value.status == fg.FIRE_ERR_ARG
     assert "32768" in str(e.value)
-    assert ctypes.sizeof(fg.fire_potential_t) == 104
+    assert ctypes.sizeof(fg.fire_potential_t) == 160
