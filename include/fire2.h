@@ -36,7 +36,7 @@
 extern "C" {
 #endif
 
-#define FIRE2_ABI_VERSION 6
+#define FIRE2_ABI_VERSION 7
 
 typedef enum {
     FIRE_OK = 0,
@@ -333,7 +333,11 @@ fire_status fire_diag_exp(int64_t n, const double* d_x, double* d_out, void* str
 typedef struct {
     int32_t threads_per_block;  /* multiple of 32 in [32, 512] (default 256) */
     int32_t ctas_per_sm;        /* resident CTAs per SM, 1..32 (default 2) */
-    int32_t reserved0, reserved1;
+    int32_t cluster_size;       /* CTAs per thread-block cluster sharing each system:
+                                   1 (or 0): one CTA per system; 2, 4 or 8: the
+                                   cluster splits every system's atoms and combines
+                                   its reductions through distributed shared memory */
+    int32_t reserved;
 } fire_batch_tuning_t;
 
 /* Creates a batched handle for n_sys systems; system s owns atoms
@@ -369,7 +373,8 @@ fire_status fire_minimize_batch_dev(fire_handle_t* h, double* d_pos, const doubl
 fire_status fire_batch_set_tuning(fire_handle_t* h, const fire_batch_tuning_t* tuning);
 
 /* Autotuner: times every candidate launch shape (threads per CTA 64..512,
- * CTAs per SM 1..8, at most 2048 threads per SM) on this batch -- positions
+ * CTAs per SM 1..8, at most 2048 threads per SM, clusters of 1, 2 or 4 CTAs
+ * where the device can co-schedule them) on this batch -- positions
  * pos and boxes as for fire_minimize_batch, `iters` FIRE iterations of every
  * system from the same start -- keeps the fastest for later calls and
  * returns it in *chosen (may be NULL).  pos is not modified.

@@ -76,7 +76,7 @@ class fire_params_t(C.Structure):
 
 class fire_batch_tuning_t(C.Structure):
     _fields_ = [("threads_per_block", C.c_int32), ("ctas_per_sm", C.c_int32),
-                ("reserved0", C.c_int32), ("reserved1", C.c_int32)]
+                ("cluster_size", C.c_int32), ("reserved", C.c_int32)]
 
 
 class fire_result_t(C.Structure):
@@ -341,8 +341,9 @@ def fire_minimize_batch_dev(handle, d_pos, boxes, ftol: float, maxiter: int, d_f
     return list(out)
 
 
-def fire_batch_set_tuning(handle, threads_per_block: int, ctas_per_sm: int) -> None:
-    t = fire_batch_tuning_t(int(threads_per_block), int(ctas_per_sm), 0, 0)
+def fire_batch_set_tuning(handle, threads_per_block: int, ctas_per_sm: int,
+                          cluster_size: int = 1) -> None:
+    t = fire_batch_tuning_t(int(threads_per_block), int(ctas_per_sm), int(cluster_size), 0)
     _check(load_library().fire_batch_set_tuning(handle, C.byref(t)), handle)
 
 
@@ -352,7 +353,8 @@ def fire_batch_autotune(handle, pos: np.ndarray, boxes, iters: int = 20):
     t = fire_batch_tuning_t()
     _check(load_library().fire_batch_autotune(handle, pos.ctypes.data, bx.ctypes.data,
                                               int(iters), C.byref(t)), handle)
-    return {"threads_per_block": t.threads_per_block, "ctas_per_sm": t.ctas_per_sm}
+    return {"threads_per_block": t.threads_per_block, "ctas_per_sm": t.ctas_per_sm,
+            "cluster_size": max(1, t.cluster_size)}
 
 
 def _theta(theta):
@@ -474,8 +476,8 @@ class FireBatch:
     def minimize_dev(self, d_pos, boxes, ftol, maxiter, d_forces=None, stream=None):
         return fire_minimize_batch_dev(self.h, d_pos, boxes, ftol, maxiter, d_forces, stream)
 
-    def set_tuning(self, threads_per_block, ctas_per_sm):
-        fire_batch_set_tuning(self.h, threads_per_block, ctas_per_sm)
+    def set_tuning(self, threads_per_block, ctas_per_sm, cluster_size=1):
+        fire_batch_set_tuning(self.h, threads_per_block, ctas_per_sm, cluster_size)
 
     def autotune(self, pos, boxes, iters=20):
         return fire_batch_autotune(self.h, pos, boxes, iters)

@@ -13,6 +13,7 @@
 // The launch shape (threads per CTA, CTAs per SM) is chosen by the autotuner
 // in fire_batch_autotune: it times every candidate shape on the caller's
 // batch for a fixed number of iterations and keeps the fastest.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -123,10 +124,12 @@ __device__ __forceinline__ void b_try_pair(const BArgs& a, const BInst& I, int i
     ++cnt;
 }
 
-// Full neighbour list of one system; cell-sorted atoms in shared memory when
-// the box holds at least 3 cells per axis, all pairs otherwise.
-__device__ __forceinline__ void b_build(const BArgs& a, const BInst& I, int* s_count, int* s_start, int* s_atoms,
-                        BShared& sh, double* red) {
+// Full neighbour list of atoms [lo, hi) of one system; cell-sorted atoms of
+// the whole system in shared memory when the box holds at least 3 cells per
+// axis, all pairs otherwise.  Returns the CTA's error status (0, ST_RANGE or
+// ST_NBR_OVERFLOW), the same in every thread.
+__device__ __forceinline__ int b_build(const BArgs& a, const BInst& I, int lo, int hi, int* s_count,
+                                       int* s_start, int* s_atoms, double* red) {
     const int T = blockDim.x, t = threadIdx.x;
     const bool cells = I.nc[0] > 0;
     const int ncell = cells ? I.nc[0] * I.nc[1] * I.nc[2] : 0;
@@ -161,7 +164,7 @@ __device__ __forceinline__ void b_build(const BArgs& a, const BInst& I, int* s_c
         __syncthreads();
     }
     int bad = ST_OK, over = 0;
-    for (int i = t; i < I.n; i += T) {
+    for (int i = lo + t; i < hi; i += T) {
         const float4 xi = a.xf[I.off + i];
         int cnt = 0;
         if (!cells) {
@@ -194,23 +197,21 @@ __device__ __forceinline__ void b_build(const BArgs& a, const BInst& I, int* s_c
         a.nnbr[I.off + i] = cnt;
         a.xref[I.off + i] = a.x[I.off + i];
     }
-    const double flag = bmax((double)(bad != ST_OK ? bad : (over ? ST_NBR_OVERFLOW : 0)), red);
-    if (t == 0) {
-        if (flag > 0.0 && sh.status == ST_OK) sh.status = (int)flag;
-        sh.builds += 1;
-    }
-    __syncthreads();
+    return (int)bmax((double)(bad != ST_OK ? bad : (over ? ST_NBR_OVERFLOW : 0)), red);
 }
 
-// Energy and forces of one system (full list, no atomics); returns E.
-template <bool F32>
-__device__ __forceinline__ double b_forces(const BArgs& a, const BInst& I, const double* etab, const float* et32,
-                           double* red) {
+// Energy and forces of atoms [lo, hi) of one system (full list, no
+// atomics); returns their energy.  With CL, the CTAs of a thread-block
+// cluster share the system: the cluster barrier between the passes makes
+// every CTA's F'(rho) visible to the others.
+template <bool F32, bool CL>
+__device__ __forceinline__ double b_forces(const BArgs& a, const BInst& I, int lo, int hi,
+                                           const double* etab, const float* et32, double* red) {
     const PotC& P = a.P;
     const int T = blockDim.x, t = threadIdx.x;
     double e_sum = 0.0;
     // pass 1: densities, embedding derivative, atom energies
-    for (int i = t; i < I.n; i += T) {
+    for (int i = lo + t; i < hi; i += T) {
         const long long gi = I.off + i;
         const int m = a.nnbr[gi];
         if (F32) {
@@ -262,9 +263,10 @@ __device__ __forceinline__ double b_forces(const BArgs& a, const BInst& I, const
             e_sum += erep - sq;
         }
     }
-    const double E = bsum(e_sum, red);  // also orders pass 1 before pass 2
+    const double E = bsum(e_sum, red);  // also orders pass 1 before pass 2 in the CTA
+    if (CL) cooperative_groups::this_cluster().sync();   // ... and across the cluster
     // pass 2: forces
-    for (int i = t; i < I.n; i += T) {
+    for (int i = lo + t; i < hi; i += T) {
         const long long gi = I.off + i;
         const int m = a.nnbr[gi];
         if (F32) {
@@ -320,12 +322,56 @@ __device__ __forceinline__ double b_forces(const BArgs& a, const BInst& I, const
     return E;
 }
 
-// FP64 reductions of (F, v) of one system into sh, then Algorithm 2.
-__device__ __forceinline__ void b_reduce_control(const BArgs& a, const BInst& I, BShared& sh, double E,
-                                 double* red, bool first, unsigned long long t0) {
+// Exchange of per-CTA scalars inside a thread-block cluster (distributed
+// shared memory): thread 0 of every CTA stores its values, one cluster
+// barrier, then thread 0 of every CTA reads all ranks' values in rank order
+// and combines them -- sums for the first nsum entries, maxima for the rest
+// -- so every CTA holds bit-identical results without a second barrier.  Two
+// buffers alternate: the barrier of the next exchange orders the reads of
+// this one before any later overwrite.  Without a cluster the values pass
+// through unchanged.
+struct ClX {
+    double buf[2][8];
+    double res[8];
+    int parity;
+};
+
+template <bool CL>
+__device__ __forceinline__ void cl_combine(ClX& x, const double* v, int nsum, int nval) {
+    if (!CL) {
+        if (threadIdx.x == 0)
+            for (int k = 0; k < nval; ++k) x.res[k] = v[k];
+        __syncthreads();
+        return;
+    }
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    const int par = x.parity;
+    if (threadIdx.x == 0)
+        for (int k = 0; k < nval; ++k) x.buf[par][k] = v[k];
+    cl.sync();
+    if (threadIdx.x == 0) {
+        double acc[8];
+        for (int r = 0; r < (int)cl.num_blocks(); ++r) {
+            const double* rv = cl.map_shared_rank(&x.buf[par][0], r);
+            for (int k = 0; k < nval; ++k)
+                acc[k] = r == 0 ? rv[k] : (k < nsum ? acc[k] + rv[k] : fmax(acc[k], rv[k]));
+        }
+        for (int k = 0; k < nval; ++k) x.res[k] = acc[k];
+        x.parity = par ^ 1;
+    }
+    __syncthreads();
+}
+
+// FP64 reductions of (F, v) of atoms [lo, hi) (combined over the cluster),
+// then Algorithm 2 in thread 0 of every CTA on identical inputs.
+template <bool CL>
+__device__ __forceinline__ void b_reduce_control(const BArgs& a, const BInst& I, int lo, int hi,
+                                                 BShared& sh, ClX& X, double E, double* red,
+                                                 unsigned long long t0) {
     double P = 0.0, F2 = 0.0, V2 = 0.0, fa2 = 0.0, fin = 0.0;
     const FireScal fs = sh.fs;
-    for (int i = threadIdx.x; i < I.n; i += blockDim.x) {
+    for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
         const dvec4 f = a.f[I.off + i];
         dvec4 v = a.v[I.off + i];
         if (fs.vv) {   // second half kick of velocity Verlet (Alg. 6)
@@ -339,64 +385,97 @@ __device__ __forceinline__ void b_reduce_control(const BArgs& a, const BInst& I,
         fa2 = fmax(fa2, q);
         fin = fmax(fin, fmax(fabs(f.x), fmax(fabs(f.y), fabs(f.z))));
     }
-    P = bsum(P, red);
-    F2 = bsum(F2, red);
-    V2 = bsum(V2, red);
-    fa2 = bmax(fa2, red);
-    fin = bmax(fin, red);
+    double v[8];
+    v[0] = bsum(P, red);
+    v[1] = bsum(F2, red);
+    v[2] = bsum(V2, red);
+    v[3] = E;
+    v[4] = bmax(fa2, red);
+    v[5] = bmax(fin, red);
+    v[6] = (double)sh.status;
+    v[7] = (double)(globaltimer_ns() - t0);   // the cluster takes the largest
+    cl_combine<CL>(X, v, 4, 8);
     if (threadIdx.x == 0) {
-        sh.P = P;
-        sh.F2 = F2;
-        sh.V2 = V2;
-        sh.fa2 = fa2;
-        sh.fin = fin;
-        sh.E = E;
+        const double* r = X.res;
+        sh.P = r[0];
+        sh.F2 = r[1];
+        sh.V2 = r[2];
+        sh.E = r[3];
+        sh.fa2 = r[4];
+        sh.fin = r[5];
+        sh.status = (int)r[6];
         bool stop;
         if (sh.status != ST_OK) {
             sh.fs.evals += 1;
             stop = true;
-        } else if (!isfinite(E) || !isfinite(F2) || !isfinite(V2)) {
+        } else if (!isfinite(sh.E) || !isfinite(sh.F2) || !isfinite(sh.V2)) {
             sh.fs.evals += 1;
             sh.status = ST_NONFINITE;
             stop = true;
-        } else if (a.budget_ns && globaltimer_ns() - t0 > a.budget_ns) {
+        } else if (a.budget_ns && r[7] > (double)a.budget_ns) {
             sh.fs.evals += 1;
             sh.status = ST_TIMEOUT;
             stop = true;
         } else {
-            stop = fire_control_step(a.prm, sh.fs, P, F2, V2, fa2, fin);
+            stop = fire_control_step(a.prm, sh.fs, sh.P, sh.F2, sh.V2, sh.fa2, sh.fin);
         }
         sh.done = stop ? 1 : 0;
     }
     __syncthreads();
-    (void)first;
 }
 
-template <bool F32>
+// The batched relaxation.  CL = false: one CTA per system.  CL = true: the
+// CTAs of a thread-block cluster share each system -- rank r owns atoms
+// [r n / C, (r + 1) n / C) -- with cluster barriers where one CTA reads what
+// another wrote (positions before a list build or force pass, F'(rho)
+// between the passes) and the cluster exchange for every reduction; every
+// decision (stop, rebuild, drift cap) is taken on bit-identical values in
+// all CTAs, so they run through the same barriers.
+template <bool F32, bool CL>
 __global__ void __launch_bounds__(512, 1) k_batch_relax(BArgs a) {
+    namespace cg = cooperative_groups;
     extern __shared__ int smem[];
     __shared__ double etab[kExpTableSize];
     __shared__ float et32[kExp32TableSize];
     __shared__ double red[32];
     __shared__ BShared sh;
+    __shared__ ClX X;
     int* s_count = smem;
     int* s_start = smem + a.max_cells;
     int* s_atoms = smem + 2 * a.max_cells + 1;
+    int rank = 0, C = 1;
+    if (CL) {
+        rank = (int)cg::this_cluster().block_rank();
+        C = (int)cg::this_cluster().num_blocks();
+    }
     for (int t = threadIdx.x; t < kExpTableSize; t += blockDim.x) etab[t] = a.exp_table[t];
     for (int t = threadIdx.x; t < kExp32TableSize; t += blockDim.x) et32[t] = a.exp32_table[t];
+    if (threadIdx.x == 0) X.parity = 0;
+    // every CTA of the cluster must be running before any distributed
+    // shared memory access
+    if (CL) cg::this_cluster().sync();
     for (;;) {
-        if (threadIdx.x == 0) {
+        // the next system: rank 0 takes it from the queue and hands it to the cluster
+        if (rank == 0 && threadIdx.x == 0) {
             const int k = atomicAdd(a.queue, 1);
-            sh.sys = k < a.n_sys ? a.order[k] : -1;
+            const int next = k < a.n_sys ? a.order[k] : -1;
+            if (CL) {
+                cg::cluster_group cl = cg::this_cluster();
+                for (int r = 0; r < C; ++r) cl.map_shared_rank(&sh, r)->sys = next;
+            } else {
+                sh.sys = next;
+            }
         }
-        __syncthreads();
+        if (CL) cg::this_cluster().sync();
+        else __syncthreads();
         const int sys = sh.sys;
         if (sys < 0) return;
         const BInst I = a.inst[sys];
+        const int lo = (int)((long long)I.n * rank / C), hi = (int)((long long)I.n * (rank + 1) / C);
         const unsigned long long t0 = globaltimer_ns();
         // set-up: positions in, v = 0, FIRE state (Algorithm 2 initialisation)
         int bad = 0;
-        for (int i = threadIdx.x; i < I.n; i += blockDim.x) {
+        for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
             const long long gi = I.off + i;
             const double* p = a.pos_io + 3 * gi;
             if (!isfinite(p[0]) || !isfinite(p[1]) || !isfinite(p[2])) bad = 1;
@@ -414,17 +493,22 @@ __global__ void __launch_bounds__(512, 1) k_batch_relax(BArgs a) {
             sh.builds = 0;
             sh.done = 0;
         }
-        __syncthreads();
-        b_build(a, I, s_count, s_start, s_atoms, sh, red);
-        double E = b_forces<F32>(a, I, etab, et32, red);
-        b_reduce_control(a, I, sh, E, red, true, t0);
+        if (CL) cg::this_cluster().sync();   // every CTA's positions before the list build
+        else __syncthreads();
+        int bst = b_build(a, I, lo, hi, s_count, s_start, s_atoms, red);
+        if (threadIdx.x == 0) {
+            if (bst != ST_OK && sh.status == ST_OK) sh.status = bst;
+            sh.builds += 1;
+        }
+        double E = b_forces<F32, CL>(a, I, lo, hi, etab, et32, red);
+        b_reduce_control<CL>(a, I, lo, hi, sh, X, E, red, t0);
         while (!sh.done) {
             const FireScal fs = sh.fs;
             // maximum displacement per step: the drift waits for max_i |v_i|
             double dt_drift = fs.dt_cur;
             if (a.prm.dmax > 0.0) {
                 double vm = 0.0;
-                for (int i = threadIdx.x; i < I.n; i += blockDim.x) {
+                for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
                     const long long gi = I.off + i;
                     dvec4 x = a.x[gi], v = a.v[gi];
                     fire_update_pre(fs, x, v, a.f[gi]);
@@ -432,11 +516,12 @@ __global__ void __launch_bounds__(512, 1) k_batch_relax(BArgs a) {
                     a.v[gi] = v;
                     vm = fmax(vm, v.x * v.x + v.y * v.y + v.z * v.z);
                 }
-                vm = bmax(vm, red);
-                dt_drift = fire_capped_dt(fs.dt_cur, a.prm.dmax, vm);
+                const double vb = bmax(vm, red);
+                cl_combine<CL>(X, &vb, 0, 1);
+                dt_drift = fire_capped_dt(fs.dt_cur, a.prm.dmax, X.res[0]);
             }
             double dmax = 0.0;
-            for (int i = threadIdx.x; i < I.n; i += blockDim.x) {
+            for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
                 const long long gi = I.off + i;
                 dvec4 x = a.x[gi], v = a.v[gi];
                 if (a.prm.dmax > 0.0)
@@ -453,13 +538,21 @@ __global__ void __launch_bounds__(512, 1) k_batch_relax(BArgs a) {
                 const double ddx = x.x - r.x, ddy = x.y - r.y, ddz = x.z - r.z;
                 dmax = fmax(dmax, ddx * ddx + ddy * ddy + ddz * ddz);
             }
-            dmax = bmax(dmax, red);
-            if (dmax > I.half_skin2) b_build(a, I, s_count, s_start, s_atoms, sh, red);
-            E = b_forces<F32>(a, I, etab, et32, red);
-            b_reduce_control(a, I, sh, E, red, false, t0);
+            // the exchange's barrier also publishes every CTA's new positions
+            const double db = bmax(dmax, red);
+            cl_combine<CL>(X, &db, 0, 1);
+            if (X.res[0] > I.half_skin2) {
+                bst = b_build(a, I, lo, hi, s_count, s_start, s_atoms, red);
+                if (threadIdx.x == 0) {
+                    if (bst != ST_OK && sh.status == ST_OK) sh.status = bst;
+                    sh.builds += 1;
+                }
+            }
+            E = b_forces<F32, CL>(a, I, lo, hi, etab, et32, red);
+            b_reduce_control<CL>(a, I, lo, hi, sh, X, E, red, t0);
         }
         // write back
-        for (int i = threadIdx.x; i < I.n; i += blockDim.x) {
+        for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
             const long long gi = I.off + i;
             const dvec4 x = a.x[gi];
             double* p = a.pos_io + 3 * gi;
@@ -474,7 +567,7 @@ __global__ void __launch_bounds__(512, 1) k_batch_relax(BArgs a) {
                 q[2] = f.z;
             }
         }
-        if (threadIdx.x == 0) {
+        if (rank == 0 && threadIdx.x == 0) {
             BRes& r = a.res[sys];
             r.energy = sh.E;
             r.fmax2 = sh.fa2;
@@ -664,6 +757,72 @@ FIRE2_HIDDEN fire_status fire2_batch_create(fire_handle_t* h, int32_t n_sys,
     return FIRE_OK;
 }
 
+// Cluster size of a tuning (0 means 1).
+static int cluster_of(const fire_batch_tuning_t& t) { return t.cluster_size > 1 ? t.cluster_size : 1; }
+
+// Launches the batched kernel with b->tune: plain launch, or cluster launch
+// with the grid a multiple of the cluster size.
+template <bool F32>
+static fire_status launch_shape(fire_handle_t* h, fire_batch_state* b, cudaStream_t s) {
+    const int threads = b->tune.threads_per_block;
+    const int C = cluster_of(b->tune);
+    const BArgs& a = b->args;
+    if (C == 1) {
+        const int grid = std::max(1, std::min(b->n_sys, b->sms * b->tune.ctas_per_sm));
+        BCK(cudaFuncSetAttribute(k_batch_relax<F32, false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem_bytes));
+        k_batch_relax<F32, false><<<grid, threads, b->smem_bytes, s>>>(a);
+        BCK(cudaGetLastError());
+        return FIRE_OK;
+    }
+    const int clusters = std::max(1, std::min(b->n_sys, b->sms * b->tune.ctas_per_sm / C));
+    BCK(cudaFuncSetAttribute(k_batch_relax<F32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)b->smem_bytes));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(clusters * C), 1, 1);
+    cfg.blockDim = dim3((unsigned)threads, 1, 1);
+    cfg.dynamicSmemBytes = b->smem_bytes;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    BCK(cudaLaunchKernelEx(&cfg, k_batch_relax<F32, true>, a));
+    return FIRE_OK;
+}
+
+// Whether clusters of the tuning's size and shape can be co-scheduled.
+template <bool F32>
+static bool cluster_fits(const fire_batch_state* b, const fire_batch_tuning_t& t) {
+    const int C = cluster_of(t);
+    if (C == 1) return true;
+    if (cudaFuncSetAttribute(k_batch_relax<F32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)b->smem_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)C, 1, 1);
+    cfg.blockDim = dim3((unsigned)t.threads_per_block, 1, 1);
+    cfg.dynamicSmemBytes = b->smem_bytes;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k_batch_relax<F32, true>, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return n > 0;
+}
+
 // Launches one batched relaxation with the current tuning (asynchronous).
 static fire_status batch_launch(fire_handle_t* h, fire_batch_state* b, double ftol,
                                 int64_t maxiter, double* d_fout, cudaStream_t s) {
@@ -701,22 +860,11 @@ static fire_status batch_launch(fire_handle_t* h, fire_batch_state* b, double ft
     a.exp32_table = fire2_exp32_table(h);
     a.qscale = fire2_qscale(h);
     const bool f32 = fire2_pot(h).precision == FIRE_PREC_FP32_PAIR;
-    const int threads = b->tune.threads_per_block;
-    const int grid = std::max(1, std::min(b->n_sys, b->sms * b->tune.ctas_per_sm));
     BCK(cudaMemcpyAsync(b->d_inst, b->inst.data(), (size_t)b->n_sys * sizeof(BInst),
                         cudaMemcpyHostToDevice, s));
     BCK(cudaMemsetAsync(b->d_queue, 0, sizeof(int), s));
-    if (f32) {
-        BCK(cudaFuncSetAttribute(k_batch_relax<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)b->smem_bytes));
-        k_batch_relax<true><<<grid, threads, b->smem_bytes, s>>>(a);
-    } else {
-        BCK(cudaFuncSetAttribute(k_batch_relax<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)b->smem_bytes));
-        k_batch_relax<false><<<grid, threads, b->smem_bytes, s>>>(a);
-    }
-    BCK(cudaGetLastError());
-    return FIRE_OK;
+    if (f32) return launch_shape<true>(h, b, s);
+    return launch_shape<false>(h, b, s);
 }
 
 static fire_status batch_collect(fire_handle_t* h, fire_batch_state* b, fire_result_t* out,
@@ -813,6 +961,13 @@ fire_status fire_batch_set_tuning(fire_handle_t* h, const fire_batch_tuning_t* t
         t->threads_per_block % 32 != 0 || t->ctas_per_sm < 1 || t->ctas_per_sm > 32)
         return fire2_batch_fail(h, FIRE_ERR_ARG, "threads_per_block must be a multiple of 32 in "
                                                  "[32, 512] and ctas_per_sm in [1, 32]");
+    const int C = cluster_of(*t);
+    if (C != 1 && C != 2 && C != 4 && C != 8)
+        return fire2_batch_fail(h, FIRE_ERR_ARG, "cluster_size must be 0, 1, 2, 4 or 8");
+    const bool f32 = fire2_pot(h).precision == FIRE_PREC_FP32_PAIR;
+    if (!(f32 ? cluster_fits<true>(b, *t) : cluster_fits<false>(b, *t)))
+        return fire2_batch_fail(h, FIRE_ERR_ARG, "clusters of this size and shape cannot be "
+                                                 "co-scheduled on this device");
     b->tune = *t;
     return FIRE_OK;
 }
@@ -832,6 +987,8 @@ fire_status fire_batch_autotune(fire_handle_t* h, const double* pos, const doubl
     BCK(cudaMemcpy(d_src, pos, bytes, cudaMemcpyHostToDevice));
     const int threads_c[] = {64, 128, 256, 512};
     const int ctas_c[] = {1, 2, 4, 8};
+    const int cl_c[] = {1, 2, 4};
+    const bool f32 = fire2_pot(h).precision == FIRE_PREC_FP32_PAIR;
     const fire_batch_tuning_t saved = b->tune;
     double best = 1e300;
     fire_batch_tuning_t best_t = saved;
@@ -839,10 +996,13 @@ fire_status fire_batch_autotune(fire_handle_t* h, const double* pos, const doubl
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     for (int th : threads_c) {
-        for (int c : ctas_c) {
+        for (int cc = 0; cc < 12; ++cc) {
+            const int c = ctas_c[cc % 4], C = cl_c[cc / 4];
             if (th * c > 2048) continue;   // more threads than an SM holds
             b->tune.threads_per_block = th;
             b->tune.ctas_per_sm = c;
+            b->tune.cluster_size = C;
+            if (!(f32 ? cluster_fits<true>(b, b->tune) : cluster_fits<false>(b, b->tune))) continue;
             cudaMemcpyAsync(b->args.pos_io, d_src, bytes, cudaMemcpyDeviceToDevice, s);
             cudaEventRecord(e0, s);
             st = batch_launch(h, b, 0.0, iters, nullptr, s);   // ftol = 0: every system runs `iters`

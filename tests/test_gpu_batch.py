@@ -136,3 +136,40 @@ def test_batch_dmax_relaxations_match_oracle():
         assert abs(r.energy - ro.energy) / c.n < 1e-8, s
         assert abs(r.iterations - ro.iterations) <= max(2, 0.05 * ro.iterations), \
             (s, r.iterations, ro.iterations)
+
+
+@pytest.mark.parametrize("cluster", [2, 4])
+def test_batch_clusters_share_systems_and_match_oracle(cluster):
+    # clusters of CTAs split every system's atoms and combine the reductions
+    # through distributed shared memory; FP64 parity per system as for one CTA
+    cfgs = small_batch(n_sys=7, seed=54)
+    x, boxes, counts = pack(cfgs)
+    with fg.FireBatch(counts, fi.CU_MASS, rgl_pot(), dt_start=fi.CU_DT) as b:
+        b.set_tuning(256, 2, cluster)
+        res, f = b.minimize(x.copy(), boxes, 1e-6, 100000, want_forces=True)
+        r0, f0 = b.minimize(x.copy(), boxes, 1e-6, 0, want_forces=True)
+    off = np.concatenate([[0], np.cumsum(counts)])
+    for s, c in enumerate(cfgs):
+        eo, fo = oracle.energy_forces(c.x, c.box, ora_rgl())
+        assert np.abs(f0[off[s]:off[s + 1]] - fo).max() / np.abs(fo).max() < 1e-10, s
+        assert r0[s].energy == pytest.approx(eo, rel=1e-12)
+        _, ro, _ = oracle.fire2(c.x, c.box, ora_rgl(), oracle.Params(dt_start=fi.CU_DT),
+                                fi.CU_MASS, 1e-6, 100000)
+        r = res[s]
+        assert r.stop == fg.FIRE_STOP_FTOL and r.fmax_atom < 1e-6, s
+        assert abs(r.energy - ro.energy) / c.n < 1e-8, s
+        assert abs(r.iterations - ro.iterations) <= max(2, 0.05 * ro.iterations), \
+            (s, r.iterations, ro.iterations)
+
+
+def test_batch_512_fp32_with_clusters_converges():
+    cfgs = fi.rgl_batch()
+    x, boxes, counts = pack(cfgs)
+    with fg.FireBatch(counts, fi.CU_MASS, rgl_pot(fg.FIRE_PREC_FP32_PAIR),
+                      dt_start=fi.CU_DT) as b:
+        b.set_tuning(512, 1, 2)
+        res, _ = b.minimize(x, boxes, 0.9e-6, 200000)
+    assert all(r.stop == fg.FIRE_STOP_FTOL for r in res)
+    with pytest.raises(fg.FireError):
+        with fg.FireBatch(counts[:4], fi.CU_MASS, rgl_pot(), dt_start=fi.CU_DT) as b:
+            b.set_tuning(256, 1, 3)
