@@ -198,3 +198,60 @@ def sw_si_vacancy_box(ncell: int = 8, seed: int = 7, n_vac: int = 1, sigma: floa
     x = lattice + rng.normal(0.0, sigma, size=lattice.shape)
     return Config(f"sw_si{ncell}_vac{n_vac}", x, np.full(3, ncell * a),
                   meta=dict(vacancies=vac.tolist(), lattice=lattice, ncell=ncell))
+
+
+# ---------------------------------------------------------------------------
+# Free surfaces (open axes).  The paper's cases include a Si slab periodic in
+# x and y only (five vacancies, 32,762 atoms, Stillinger-Weber) and open
+# clusters and pillars; these are synthetic stand-ins of that structure.
+
+def rgl_slab(ncell: int = 6, nz: int | None = None, seed: int = 21, n_vac: int = 2,
+             sigma: float = 0.05, vacuum: float = 10.0, z_shift: float = 0.0,
+             a: float = CU_A) -> Config:
+    """Cu FCC slab of ncell x ncell x nz cells, periodic in x and y, open in z:
+    box z length = nz a + vacuum; every z moved by z_shift (a negative shift
+    puts the lowest layers below z = 0, outside the box on the open axis)."""
+    nz = ncell if nz is None else nz
+    rng = np.random.Generator(np.random.PCG64(seed))
+    sites = fcc_sites(ncell, ncell, nz, a)
+    vac = np.sort(rng.choice(len(sites), size=n_vac, replace=False)) if n_vac > 0 else np.zeros(0, int)
+    keep = np.ones(len(sites), bool)
+    keep[vac] = False
+    x = sites[keep] + rng.normal(0.0, sigma, size=(int(keep.sum()), 3))
+    x[:, 2] += z_shift
+    box = np.array([ncell * a, ncell * a, nz * a + vacuum])
+    return Config(f"rgl_slab{ncell}x{nz}_vac{n_vac}", x, box, periodic=(1, 1, 0),
+                  meta=dict(vacancies=vac.tolist(), ncell=ncell, nz=nz))
+
+
+def rgl_cluster(radius: float = 10.0, seed: int = 22, sigma: float = 0.05,
+                centre=(15.0, 15.0, 15.0), box: float = 30.0, a: float = CU_A) -> Config:
+    """Spherical Cu cluster (FCC sites within `radius` of a lattice site),
+    open on every axis, centred at `centre` in a cube of side `box` (a centre
+    near a face puts atoms outside the box)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    n = int(np.ceil(radius / a)) + 1
+    sites = fcc_sites(2 * n, 2 * n, 2 * n, a) - n * a
+    sites = sites[np.sum(sites * sites, axis=1) <= radius * radius]
+    x = sites + np.asarray(centre, dtype=np.float64) + rng.normal(0.0, sigma, size=sites.shape)
+    return Config(f"rgl_cluster_r{radius:g}", x, np.full(3, float(box)), periodic=(0, 0, 0),
+                  meta=dict(radius=radius))
+
+
+def sw_si_slab(ncell: int = 16, nz: int | None = None, seed: int = 23, n_vac: int = 5,
+               sigma: float = 0.05, vacuum: float = 10.0, a: float | None = None) -> Config:
+    """Diamond Si slab, periodic in x and y, open in z, with n_vac seeded
+    vacancies (the structure of the paper's silicon vacancy case)."""
+    a = SI_A if a is None else a
+    nz = ncell if nz is None else nz
+    rng = np.random.Generator(np.random.PCG64(seed))
+    ix, iy, iz = np.meshgrid(np.arange(ncell), np.arange(ncell), np.arange(nz), indexing="ij")
+    corners = np.stack([ix, iy, iz], axis=-1).reshape(-1, 1, 3).astype(np.float64)
+    sites = ((corners + _DIAMOND_BASIS[None]) * a).reshape(-1, 3)
+    vac = np.sort(rng.choice(len(sites), size=n_vac, replace=False)) if n_vac > 0 else np.zeros(0, int)
+    keep = np.ones(len(sites), bool)
+    keep[vac] = False
+    x = sites[keep] + rng.normal(0.0, sigma, size=(int(keep.sum()), 3))
+    box = np.array([ncell * a, ncell * a, nz * a + vacuum])
+    return Config(f"sw_si_slab{ncell}x{nz}_vac{n_vac}", x, box, periodic=(1, 1, 0),
+                  meta=dict(vacancies=vac.tolist(), ncell=ncell, nz=nz))

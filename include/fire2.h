@@ -22,7 +22,10 @@
  *     it in fire_destroy.  A handle must not be used by two threads at once.
  *   - Positions are N x 3 row-major doubles (x0 y0 z0 x1 y1 z1 ...).  Boxes
  *     are orthorhombic with lengths box[3]; a periodic axis must be at least
- *     twice the interaction cut-off long (minimum-image convention).
+ *     twice the interaction cut-off long (minimum-image convention).  On an
+ *     open axis the length only sets the extent of the cell grid of the
+ *     neighbour search: atoms may lie outside [0, L) there (they share the
+ *     edge cells, which costs time, not correctness).
  *   - Units are the caller's.  `mass` is expressed so that the acceleration
  *     is F / mass (for metal units with masses in amu divide the mass by
  *     9648.533212 to get eV ps^2 / A^2).
@@ -331,7 +334,18 @@ fire_status fire_diag_exp(int64_t n, const double* d_x, double* d_out, void* str
 
 /* Launch shape of the batched kernel. */
 typedef struct {
-    int32_t threads_per_block;  /* multiple of 32 in [32, 512] (default 256) */
+    int32_t threads_per_block;  /* multiple of 32 in [32, 1024] (default 256);
+                                   above 512 only without clusters and with
+                                   threads_per_block x ctas_per_sm <= 1024.
+                                   The kernel exists in three register budgets:
+                                   128 registers per thread (up to 512 threads
+                                   per SM), 80 (768) and 64 (1024); a tuning
+                                   without clusters runs the smallest budget
+                                   that holds threads_per_block x ctas_per_sm
+                                   threads, or the 128-register one when that
+                                   product exceeds 1024 (fewer CTAs are then
+                                   resident); clusters always run the
+                                   128-register one */
     int32_t ctas_per_sm;        /* resident CTAs per SM, 1..32 (default 2) */
     int32_t cluster_size;       /* CTAs per thread-block cluster sharing each system:
                                    1 (or 0): one CTA per system; 2, 4 or 8: the
@@ -374,7 +388,9 @@ fire_status fire_batch_set_tuning(fire_handle_t* h, const fire_batch_tuning_t* t
 
 /* Autotuner: times every candidate launch shape (threads per CTA 64..512,
  * CTAs per SM 1..8, at most 2048 threads per SM, clusters of 1, 2 or 4 CTAs
- * where the device can co-schedule them) on this batch -- positions
+ * where the device can co-schedule them; 768 threads per SM as 768 x 1,
+ * 384 x 2, 256 x 3, 192 x 4 or 128 x 6; and 1024 x 1) on this batch
+ * -- positions
  * pos and boxes as for fire_minimize_batch, `iters` FIRE iterations of every
  * system from the same start -- keeps the fastest for later calls and
  * returns it in *chosen (may be NULL).  pos is not modified.

@@ -160,8 +160,10 @@ GeoC make_geo(const fire_handle* h, const double box[3]) {
         g.L[a] = box[a];
         g.Linv[a] = 1.0 / box[a];
         g.per[a] = h->sys.periodic[a] ? 1 : 0;
-        g.nc[a] = (int)std::floor(box[a] / rl);
-        if (!g.per[a] || g.nc[a] < 3) g.brute = 1;
+        // a periodic axis needs 3 cells for a stencil without repeats; an
+        // open axis takes any count (at least one), its cells clamped
+        g.nc[a] = std::max((int)std::floor(box[a] / rl), g.per[a] ? 0 : 1);
+        if (g.per[a] && g.nc[a] < 3) g.brute = 1;
     }
     if (g.brute)
         for (int a = 0; a < 3; ++a) g.nc[a] = 1;

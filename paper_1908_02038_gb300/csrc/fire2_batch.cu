@@ -125,8 +125,8 @@ __device__ __forceinline__ void b_try_pair(const BArgs& a, const BInst& I, int i
 }
 
 // Full neighbour list of atoms [lo, hi) of one system; cell-sorted atoms of
-// the whole system in shared memory when the box holds at least 3 cells per
-// axis, all pairs otherwise.  Returns the CTA's error status (0, ST_RANGE or
+// the whole system in shared memory when every periodic axis holds at least
+// 3 cells (open axes any number), all pairs otherwise.  Returns the CTA's error status (0, ST_RANGE or
 // ST_NBR_OVERFLOW), the same in every thread.
 __device__ __forceinline__ int b_build(const BArgs& a, const BInst& I, int lo, int hi, int* s_count,
                                        int* s_start, int* s_atoms, double* red) {
@@ -138,9 +138,9 @@ __device__ __forceinline__ int b_build(const BArgs& a, const BInst& I, int lo, i
         __syncthreads();
         for (int i = t; i < I.n; i += T) {
             const dvec4 x = a.x[I.off + i];
-            const int c = (cell_coord(x.x, I.Linv[0], I.nc[0]) * I.nc[1] +
-                           cell_coord(x.y, I.Linv[1], I.nc[1])) * I.nc[2] +
-                          cell_coord(x.z, I.Linv[2], I.nc[2]);
+            const int c = (cell_coord(x.x, I.Linv[0], I.nc[0], I.per[0]) * I.nc[1] +
+                           cell_coord(x.y, I.Linv[1], I.nc[1], I.per[1])) * I.nc[2] +
+                          cell_coord(x.z, I.Linv[2], I.nc[2], I.per[2]);
             atomicAdd(&s_count[c], 1);
         }
         __syncthreads();
@@ -156,9 +156,9 @@ __device__ __forceinline__ int b_build(const BArgs& a, const BInst& I, int lo, i
         __syncthreads();
         for (int i = t; i < I.n; i += T) {
             const dvec4 x = a.x[I.off + i];
-            const int c = (cell_coord(x.x, I.Linv[0], I.nc[0]) * I.nc[1] +
-                           cell_coord(x.y, I.Linv[1], I.nc[1])) * I.nc[2] +
-                          cell_coord(x.z, I.Linv[2], I.nc[2]);
+            const int c = (cell_coord(x.x, I.Linv[0], I.nc[0], I.per[0]) * I.nc[1] +
+                           cell_coord(x.y, I.Linv[1], I.nc[1], I.per[1])) * I.nc[2] +
+                          cell_coord(x.z, I.Linv[2], I.nc[2], I.per[2]);
             s_atoms[atomicAdd(&s_count[c], 1)] = i;
         }
         __syncthreads();
@@ -172,15 +172,18 @@ __device__ __forceinline__ int b_build(const BArgs& a, const BInst& I, int lo, i
                 if (j != i) b_try_pair(a, I, i, xi, j, cnt, bad);
         } else {
             const dvec4 x = a.x[I.off + i];
-            const int cx = cell_coord(x.x, I.Linv[0], I.nc[0]);
-            const int cy = cell_coord(x.y, I.Linv[1], I.nc[1]);
-            const int cz = cell_coord(x.z, I.Linv[2], I.nc[2]);
+            const int cx = cell_coord(x.x, I.Linv[0], I.nc[0], I.per[0]);
+            const int cy = cell_coord(x.y, I.Linv[1], I.nc[1], I.per[1]);
+            const int cz = cell_coord(x.z, I.Linv[2], I.nc[2], I.per[2]);
             for (int ox = -1; ox <= 1; ++ox) {
-                const int ax = (cx + ox + I.nc[0]) % I.nc[0];
+                const int ax = cell_step(cx, ox, I.nc[0], I.per[0]);
+                if (ax < 0) continue;
                 for (int oy = -1; oy <= 1; ++oy) {
-                    const int ay = (cy + oy + I.nc[1]) % I.nc[1];
+                    const int ay = cell_step(cy, oy, I.nc[1], I.per[1]);
+                    if (ay < 0) continue;
                     for (int oz = -1; oz <= 1; ++oz) {
-                        const int az = (cz + oz + I.nc[2]) % I.nc[2];
+                        const int az = cell_step(cz, oz, I.nc[2], I.per[2]);
+                        if (az < 0) continue;
                         const int c = (ax * I.nc[1] + ay) * I.nc[2] + az;
                         for (int k = s_start[c]; k < s_start[c + 1]; ++k) {
                             const int j = s_atoms[k];
@@ -431,8 +434,13 @@ __device__ __forceinline__ void b_reduce_control(const BArgs& a, const BInst& I,
 // between the passes) and the cluster exchange for every reduction; every
 // decision (stop, rebuild, drift cap) is taken on bit-identical values in
 // all CTAs, so they run through the same barriers.
-template <bool F32, bool CL>
-__global__ void __launch_bounds__(512, 1) k_batch_relax(BArgs a) {
+// Register budgets: MAXT = 512 allows up to 128 registers per thread, so one
+// 512-thread CTA (16 warps) per SM; MAXT = 768 holds the kernel to 80
+// registers (a few spilled bytes) so 768 threads (24 warps) fit on an SM;
+// MAXT = 1024 to 64 (more spills), 32 warps.  More warps keep more of the
+// neighbour gathers in flight; the autotuner measures which budget wins.
+template <bool F32, bool CL, int MAXT>
+__global__ void __launch_bounds__(MAXT, 1) k_batch_relax(BArgs a) {
     namespace cg = cooperative_groups;
     extern __shared__ int smem[];
     __shared__ double etab[kExpTableSize];
@@ -675,8 +683,9 @@ static fire_status batch_geometry(fire_handle_t* h, fire_batch_state* b, const d
             I.Linvf[k] = (float)(1.0 / L);
             I.per[k] = sys.periodic[k] ? 1 : 0;
             I.Lq[k] = (int)(unsigned)(unsigned long long)std::llrint(L * qscale);
-            I.nc[k] = (int)std::floor(L / rl);
-            if (!I.per[k] || I.nc[k] < 3) cells = false;
+            // open axes take any cell count (clamped cells), periodic ones 3 or more
+            I.nc[k] = std::max((int)std::floor(L / rl), I.per[k] ? 0 : 1);
+            if (I.per[k] && I.nc[k] < 3) cells = false;
             lmax = std::max(lmax, L);
             vol *= L;
         }
@@ -760,6 +769,26 @@ FIRE2_HIDDEN fire_status fire2_batch_create(fire_handle_t* h, int32_t n_sys,
 // Cluster size of a tuning (0 means 1).
 static int cluster_of(const fire_batch_tuning_t& t) { return t.cluster_size > 1 ? t.cluster_size : 1; }
 
+// Register budget (MAXT) a tuning runs: without clusters the smallest of
+// 512, 768 and 1024 threads per SM that holds threads_per_block x
+// ctas_per_sm, else 512 (fewer CTAs are then resident than asked for);
+// clusters always 512.
+static int maxt_of(const fire_batch_tuning_t& t) {
+    const int per_sm = t.threads_per_block * t.ctas_per_sm;
+    if (cluster_of(t) != 1 || per_sm <= 512 || per_sm > 1024) return 512;
+    return per_sm <= 768 ? 768 : 1024;
+}
+
+template <bool F32, int MAXT>
+static fire_status launch_plain(fire_batch_state* b, int grid, int threads, cudaStream_t s) {
+    if (cudaFuncSetAttribute(k_batch_relax<F32, false, MAXT>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)b->smem_bytes) != cudaSuccess)
+        return FIRE_ERR_CUDA;
+    k_batch_relax<F32, false, MAXT><<<grid, threads, b->smem_bytes, s>>>(b->args);
+    return cudaGetLastError() == cudaSuccess ? FIRE_OK : FIRE_ERR_CUDA;
+}
+
 // Launches the batched kernel with b->tune: plain launch, or cluster launch
 // with the grid a multiple of the cluster size.
 template <bool F32>
@@ -769,15 +798,19 @@ static fire_status launch_shape(fire_handle_t* h, fire_batch_state* b, cudaStrea
     const BArgs& a = b->args;
     if (C == 1) {
         const int grid = std::max(1, std::min(b->n_sys, b->sms * b->tune.ctas_per_sm));
-        BCK(cudaFuncSetAttribute(k_batch_relax<F32, false>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem_bytes));
-        k_batch_relax<F32, false><<<grid, threads, b->smem_bytes, s>>>(a);
-        BCK(cudaGetLastError());
+        const int mt = maxt_of(b->tune);
+        const fire_status st = mt == 768    ? launch_plain<F32, 768>(b, grid, threads, s)
+                               : mt == 1024 ? launch_plain<F32, 1024>(b, grid, threads, s)
+                                            : launch_plain<F32, 512>(b, grid, threads, s);
+        if (st != FIRE_OK) {
+            const cudaError_t e = cudaGetLastError();
+            return fire2_batch_fail(h, FIRE_ERR_CUDA, cudaGetErrorString(e));
+        }
         return FIRE_OK;
     }
     const int clusters = std::max(1, std::min(b->n_sys, b->sms * b->tune.ctas_per_sm / C));
-    BCK(cudaFuncSetAttribute(k_batch_relax<F32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)b->smem_bytes));
+    BCK(cudaFuncSetAttribute(k_batch_relax<F32, true, 512>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem_bytes));
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(clusters * C), 1, 1);
     cfg.blockDim = dim3((unsigned)threads, 1, 1);
@@ -790,7 +823,7 @@ static fire_status launch_shape(fire_handle_t* h, fire_batch_state* b, cudaStrea
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    BCK(cudaLaunchKernelEx(&cfg, k_batch_relax<F32, true>, a));
+    BCK(cudaLaunchKernelEx(&cfg, k_batch_relax<F32, true, 512>, a));
     return FIRE_OK;
 }
 
@@ -799,7 +832,8 @@ template <bool F32>
 static bool cluster_fits(const fire_batch_state* b, const fire_batch_tuning_t& t) {
     const int C = cluster_of(t);
     if (C == 1) return true;
-    if (cudaFuncSetAttribute(k_batch_relax<F32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(k_batch_relax<F32, true, 512>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)b->smem_bytes) != cudaSuccess) {
         cudaGetLastError();
         return false;
@@ -816,7 +850,7 @@ static bool cluster_fits(const fire_batch_state* b, const fire_batch_tuning_t& t
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, k_batch_relax<F32, true>, &cfg) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveClusters(&n, k_batch_relax<F32, true, 512>, &cfg) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
@@ -957,13 +991,17 @@ fire_status fire_batch_set_tuning(fire_handle_t* h, const fire_batch_tuning_t* t
     fire_batch_state* b = h ? fire2_batch_of(h) : nullptr;
     if (!b) return h ? fire2_batch_fail(h, FIRE_ERR_STATE, "handle was not created by fire_batch_init")
                      : FIRE_ERR_ARG;
-    if (!t || t->threads_per_block < 32 || t->threads_per_block > 512 ||
+    if (!t || t->threads_per_block < 32 || t->threads_per_block > 1024 ||
         t->threads_per_block % 32 != 0 || t->ctas_per_sm < 1 || t->ctas_per_sm > 32)
         return fire2_batch_fail(h, FIRE_ERR_ARG, "threads_per_block must be a multiple of 32 in "
-                                                 "[32, 512] and ctas_per_sm in [1, 32]");
+                                                 "[32, 1024] and ctas_per_sm in [1, 32]");
     const int C = cluster_of(*t);
     if (C != 1 && C != 2 && C != 4 && C != 8)
         return fire2_batch_fail(h, FIRE_ERR_ARG, "cluster_size must be 0, 1, 2, 4 or 8");
+    if (t->threads_per_block > maxt_of(*t))
+        return fire2_batch_fail(h, FIRE_ERR_ARG, "more than 512 threads per CTA needs no "
+                                                 "cluster and at most 1024 threads per SM "
+                                                 "in all");
     const bool f32 = fire2_pot(h).precision == FIRE_PREC_FP32_PAIR;
     if (!(f32 ? cluster_fits<true>(b, *t) : cluster_fits<false>(b, *t)))
         return fire2_batch_fail(h, FIRE_ERR_ARG, "clusters of this size and shape cannot be "
@@ -985,9 +1023,17 @@ fire_status fire_batch_autotune(fire_handle_t* h, const double* pos, const doubl
     double* d_src = nullptr;
     BCK(cudaMalloc(&d_src, bytes));
     BCK(cudaMemcpy(d_src, pos, bytes, cudaMemcpyHostToDevice));
-    const int threads_c[] = {64, 128, 256, 512};
-    const int ctas_c[] = {1, 2, 4, 8};
-    const int cl_c[] = {1, 2, 4};
+    // (threads, CTAs per SM, cluster): CTAs of 64..512 threads, 1..8 per SM
+    // (each shape runs the register budget maxt_of gives it), clusters of 1,
+    // 2 and 4; then 768 threads per SM in CTAs of 768, 384, 256, 192, 128,
+    // and one CTA of 1024
+    std::vector<fire_batch_tuning_t> cands;
+    for (int th : {64, 128, 256, 512})
+        for (int C : {1, 2, 4})
+            for (int c : {1, 2, 4, 8})
+                if (th * c <= 2048) cands.push_back({th, c, C, 0});
+    for (int th : {768, 384, 256, 192, 128}) cands.push_back({th, 768 / th, 1, 0});
+    cands.push_back({1024, 1, 1, 0});
     const bool f32 = fire2_pot(h).precision == FIRE_PREC_FP32_PAIR;
     const fire_batch_tuning_t saved = b->tune;
     double best = 1e300;
@@ -995,31 +1041,24 @@ fire_status fire_batch_autotune(fire_handle_t* h, const double* pos, const doubl
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    for (int th : threads_c) {
-        for (int cc = 0; cc < 12; ++cc) {
-            const int c = ctas_c[cc % 4], C = cl_c[cc / 4];
-            if (th * c > 2048) continue;   // more threads than an SM holds
-            b->tune.threads_per_block = th;
-            b->tune.ctas_per_sm = c;
-            b->tune.cluster_size = C;
-            if (!(f32 ? cluster_fits<true>(b, b->tune) : cluster_fits<false>(b, b->tune))) continue;
-            cudaMemcpyAsync(b->args.pos_io, d_src, bytes, cudaMemcpyDeviceToDevice, s);
-            cudaEventRecord(e0, s);
-            st = batch_launch(h, b, 0.0, iters, nullptr, s);   // ftol = 0: every system runs `iters`
-            cudaEventRecord(e1, s);
-            if (st != FIRE_OK) break;
-            if (cudaEventSynchronize(e1) != cudaSuccess) {
-                st = fire2_batch_fail(h, FIRE_ERR_CUDA, "autotune launch failed");
-                break;
-            }
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (ms < best) {
-                best = ms;
-                best_t = b->tune;
-            }
-        }
+    for (const fire_batch_tuning_t& t : cands) {
+        b->tune = t;
+        if (!(f32 ? cluster_fits<true>(b, b->tune) : cluster_fits<false>(b, b->tune))) continue;
+        cudaMemcpyAsync(b->args.pos_io, d_src, bytes, cudaMemcpyDeviceToDevice, s);
+        cudaEventRecord(e0, s);
+        st = batch_launch(h, b, 0.0, iters, nullptr, s);   // ftol = 0: every system runs `iters`
+        cudaEventRecord(e1, s);
         if (st != FIRE_OK) break;
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            st = fire2_batch_fail(h, FIRE_ERR_CUDA, "autotune launch failed");
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+            best = ms;
+            best_t = b->tune;
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

@@ -115,11 +115,25 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
     return t;
 }
 
-__device__ __forceinline__ int cell_coord(double x, double Linv, int nc) {
+// Cell index of coordinate x on an axis of nc cells over [0, L): wrapped into
+// the box on a periodic axis, clamped to the edge cells on an open one (an
+// atom outside the box shares the edge cell; with cells at least the list
+// radius wide, any two atoms within that radius still lie in the same or
+// adjacent cells).
+__device__ __forceinline__ int cell_coord(double x, double Linv, int nc, int per) {
     double u = x * Linv;
-    u -= floor(u);
-    int c = (int)(u * nc);
-    return c < 0 ? 0 : (c >= nc ? nc - 1 : c);
+    if (per) u -= floor(u);
+    const double c = floor(u * nc);
+    if (!(c >= 0.0)) return 0;   // also NaN
+    return c >= nc ? nc - 1 : (int)c;
+}
+
+// Neighbour cell cx + o on an axis: wrapped on a periodic axis; -1 when it
+// falls outside an open one.
+__device__ __forceinline__ int cell_step(int cx, int o, int nc, int per) {
+    const int a = cx + o;
+    if (per) return (a + nc) % nc;
+    return (a < 0 || a >= nc) ? -1 : a;
 }
 
 // Fixed-point coordinate (units of 1/qscale) modulo 2^32.  Differences of two

@@ -31,7 +31,7 @@ struct GeoC {
     int per[3];
     int nc[3];             // cells per axis (cell mode)
     double cinv[3];        // nc / L
-    int brute;             // 1 = all-pairs list build (small or open boxes)
+    int brute;             // 1 = all-pairs list build (a periodic axis under 3 cells)
     double rlist2;         // (rc + skin)^2
     double half_skin2;     // (skin / 2)^2
     // FP32 copies for the list build's candidate test
@@ -175,9 +175,9 @@ __global__ void k_cell_count(Bufs b, GeoC g, int force) {
     if (i >= b.n) return;
     const dvec4 x = b.x[i];
     b.xf[i] = make_float4((float)x.x, (float)x.y, (float)x.z, 0.f);   // list-build copy
-    const int cx = cell_coord(x.x, g.Linv[0], g.nc[0]);
-    const int cy = cell_coord(x.y, g.Linv[1], g.nc[1]);
-    const int cz = cell_coord(x.z, g.Linv[2], g.nc[2]);
+    const int cx = cell_coord(x.x, g.Linv[0], g.nc[0], g.per[0]);
+    const int cy = cell_coord(x.y, g.Linv[1], g.nc[1], g.per[1]);
+    const int cz = cell_coord(x.z, g.Linv[2], g.nc[2], g.per[2]);
     const int c = (i / g.img_n) * g.ncell_img + (cx * g.nc[1] + cy) * g.nc[2] + cz;
     b.cell_of[i] = c;
     atomicAdd(&b.cell_count[c], 1);
@@ -291,15 +291,18 @@ __global__ void k_nbr_build(Bufs b, GeoC g, int force) {
         for (int j = img * g.img_n; j < (img + 1) * g.img_n; ++j)
             if (j != i) try_add_pair(b, g, i, xif, j, cnt);
     } else {
-        const int cx = cell_coord(xi.x, g.Linv[0], g.nc[0]);
-        const int cy = cell_coord(xi.y, g.Linv[1], g.nc[1]);
-        const int cz = cell_coord(xi.z, g.Linv[2], g.nc[2]);
+        const int cx = cell_coord(xi.x, g.Linv[0], g.nc[0], g.per[0]);
+        const int cy = cell_coord(xi.y, g.Linv[1], g.nc[1], g.per[1]);
+        const int cz = cell_coord(xi.z, g.Linv[2], g.nc[2], g.per[2]);
         for (int ox = -1; ox <= 1; ++ox) {
-            const int ax = (cx + ox + g.nc[0]) % g.nc[0];
+            const int ax = cell_step(cx, ox, g.nc[0], g.per[0]);
+            if (ax < 0) continue;
             for (int oy = -1; oy <= 1; ++oy) {
-                const int ay = (cy + oy + g.nc[1]) % g.nc[1];
+                const int ay = cell_step(cy, oy, g.nc[1], g.per[1]);
+                if (ay < 0) continue;
                 for (int oz = -1; oz <= 1; ++oz) {
-                    const int az = (cz + oz + g.nc[2]) % g.nc[2];
+                    const int az = cell_step(cz, oz, g.nc[2], g.per[2]);
+                    if (az < 0) continue;
                     const int c = img * g.ncell_img + (ax * g.nc[1] + ay) * g.nc[2] + az;
                     for (int k = b.cell_start[c]; k < b.cell_start[c + 1]; ++k) {
                         const int j = b.cell_atoms[k];

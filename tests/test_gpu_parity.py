@@ -342,6 +342,7 @@ def test_fp32pair_graph_and_chunked_runs_are_identical():
 
 F32_ABS = 3e-6      # eV/A, max-abs force difference against the FP64 oracle
 E32_PER_ATOM = 1e-6  # eV/atom
+F32_MARGIN = 6e-7    # eV/A, FP32-pair force error bound at relaxed structures
 
 
 @pytest.mark.parametrize("ncell,nvac", [(3, 2), (5, 3), (7, 10)])
@@ -375,14 +376,18 @@ def test_fp32pair_relaxation_reaches_fp64_converged_state():
             fg.FireHandle(c.n, fi.CU_MASS, rgl_pot(precision=fg.FIRE_PREC_FP32_PAIR),
                           dt_start=fi.CU_DT) as h32:
         r64 = h64.minimize(x64, c.box, 1e-6, 100000)
-        r32 = h32.minimize(x32, c.box, 1e-6, 100000)
+        # stop the FP32-pair form at ftol less its force error at relaxed
+        # structures (<= 5.6e-7 eV/A measured, margin 6e-7)
+        r32 = h32.minimize(x32, c.box, 1e-6 - F32_MARGIN, 100000)
         # the FP32 solution judged by FP64 forces
         e_chk, f_chk = h64.energy_forces(x32, c.box)
+        _, f32_at32 = h32.energy_forces(x32, c.box)
     fmax64_at32 = np.sqrt((f_chk ** 2).sum(1)).max()
+    assert np.sqrt(((f32_at32 - f_chk) ** 2).sum(1)).max() < F32_MARGIN
     print(f"iterations FP64 {r64.iterations}, FP32-pair {r32.iterations}; FP64 max|F| at the "
           f"FP32-pair minimum {fmax64_at32:.3e}; dE/N {abs(e_chk - r64.energy) / c.n:.3e}")
-    assert r32.stop == fg.FIRE_STOP_FTOL and r32.fmax_atom < 1e-6
-    assert fmax64_at32 < 2e-6
+    assert r32.stop == fg.FIRE_STOP_FTOL and r32.fmax_atom < 1e-6 - F32_MARGIN
+    assert fmax64_at32 < 1e-6
     assert abs(e_chk - r64.energy) / c.n < 1e-8
 
 
