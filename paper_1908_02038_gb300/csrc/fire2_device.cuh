@@ -790,13 +790,13 @@ __device__ __forceinline__ void fill_qshift64_table(long long* qt, const GeoC& g
     }
 }
 
-// Separation x_j - x_i - shift of list slot e as float pairs (exact), r^2.
-__device__ __forceinline__ ffloat pair_sep_ff(const Bufs& b, const long long* qt, const lvec4& qi,
-                                              uint32_t e, ffloat& dx, ffloat& dy, ffloat& dz,
-                                              int& j) {
+// Separation x_j - x_i - shift of list slot e (atom j at fixed-point position
+// qj) as float pairs (exact), and r^2.
+__device__ __forceinline__ ffloat pair_sep_ff_q(const long long* qt, const lvec4& qi,
+                                                const lvec4& qj, uint32_t e, ffloat& dx,
+                                                ffloat& dy, ffloat& dz, int& j) {
     j = (int)(e & kIdxMask);
     const int code = (int)(e >> kIdxBits);
-    const lvec4 qj = b.xq64[j];
     long long ix = qj.x - qi.x, iy = qj.y - qi.y, iz = qj.z - qi.z;
     if (code != kCodeZero) {
         ix -= qt[3 * code];
@@ -807,6 +807,13 @@ __device__ __forceinline__ ffloat pair_sep_ff(const Bufs& b, const long long* qt
     dy = fixed_to_ff(iy);
     dz = fixed_to_ff(iz);
     return ff_norm2(dx, dy, dz);
+}
+
+// The same, loading atom j's position.
+__device__ __forceinline__ ffloat pair_sep_ff(const Bufs& b, const long long* qt, const lvec4& qi,
+                                              uint32_t e, ffloat& dx, ffloat& dy, ffloat& dz,
+                                              int& j) {
+    return pair_sep_ff_q(qt, qi, b.xq64[e & kIdxMask], e, dx, dy, dz, j);
 }
 
 __device__ __forceinline__ void load_row(const float* tab, int k, float row[kFFRow]) {
@@ -900,10 +907,23 @@ __global__ void __launch_bounds__(kForceBlock) k_force_ff(Bufs b, PotC P, GeoC g
     const ffloat fpi = {fpi2.x, fpi2.y};
     const int m = b.nnbr[i];
     ffloat fx = {0.f, 0.f}, fy = {0.f, 0.f}, fz = {0.f, 0.f};
+    // software pipeline: the next list entry, and the position and F' of its
+    // atom, load while this pair is evaluated
+    uint32_t e_nx = m > 0 ? b.nbr[i] : 0u;
+    lvec4 q_nx = b.xq64[m > 0 ? (int)(e_nx & kIdxMask) : i];
+    float2 p_nx = b.fpff[m > 0 ? (int)(e_nx & kIdxMask) : i];
     for (int k = 0; k < m; ++k) {
+        const uint32_t e = e_nx;
+        const lvec4 qj = q_nx;
+        const float2 fpj2 = p_nx;
+        if (k + 1 < m) {
+            e_nx = b.nbr[(size_t)(k + 1) * b.n + i];
+            q_nx = b.xq64[e_nx & kIdxMask];
+            p_nx = b.fpff[e_nx & kIdxMask];
+        }
         ffloat dx, dy, dz;
         int j;
-        const ffloat r2 = pair_sep_ff(b, qt, qi, b.nbr[(size_t)k * b.n + i], dx, dy, dz, j);
+        const ffloat r2 = pair_sep_ff_q(qt, qi, qj, e, dx, dy, dz, j);
         if (!(r2.hi < P.rc2_f)) continue;
         const float uf = r2.hi - P.r0sq_f;
         ffloat c[2];
@@ -917,7 +937,6 @@ __global__ void __launch_bounds__(kForceBlock) k_force_ff(Bufs b, PotC P, GeoC g
             c[0] = f64_to_ff(2.0 * dphi * rinv);
             c[1] = f64_to_ff(dg * rinv);
         }
-        const float2 fpj2 = b.fpff[j];
         const ffloat fs = ff_add(c[0], ff_mul(ff_add(fpi, {fpj2.x, fpj2.y}), c[1]));
         const ffloat tx = ff_mul(fs, dx), ty = ff_mul(fs, dy), tz = ff_mul(fs, dz);
         fx = ff_add(fx, tx);
