@@ -653,6 +653,13 @@ static bool fill_potc(fire_handle* h) {
         c.sw_q = pot->sw_q;
         c.sw_lambda = pot->sw_lambda;
         c.sw_gamma = pot->sw_gamma;
+        // integer exponents (p = 4, q = 0 in the original set) are evaluated
+        // by multiplication instead of pow()
+        auto small_int = [](double e) {
+            return (e >= 0.0 && e <= 32.0 && e == std::floor(e)) ? (int)e : -1;
+        };
+        c.sw_pi = small_int(pot->sw_p);
+        c.sw_qi = small_int(pot->sw_q);
         return true;
     }
     if (pot->kind == FIRE_POT_LJ) {

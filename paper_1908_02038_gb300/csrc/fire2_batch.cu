@@ -261,8 +261,9 @@ __device__ __forceinline__ double b_forces(const BArgs& a, const BInst& I, int l
                 rho += g;
                 erep += phi;
             }
-            const double sq = sqrt(rho);
-            a.fp64[gi] = rho > 0.0 ? -0.5 / sq : 0.0;
+            double sq, fp;
+            rgl_embed(rho, sq, fp);
+            a.fp64[gi] = fp;
             e_sum += erep - sq;
         }
     }

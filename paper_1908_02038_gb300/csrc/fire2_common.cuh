@@ -54,6 +54,7 @@ struct PotC {
     double eps, sigma2, lj_shift;
     // SW (eps above): sigma, a sigma, and the published dimensionless set
     double sw_sigma, sw_rc, sw_A, sw_B, sw_p, sw_q, sw_lambda, sw_gamma;
+    int sw_pi, sw_qi;      // sw_p, sw_q as small non-negative integers, or -1
     // RGL
     double A, xi2, p, q2, r0inv, p_r0, q2_r0, rs, rc, winv;
     ExpC ex;               // constants of the table-driven exponential

@@ -392,8 +392,8 @@ __global__ void k_embed(Bufs b) {
     double emb = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < b.n; i += gridDim.x * blockDim.x) {
         const double rho = b.rho[i];
-        const double sq = sqrt(rho);
-        const double fp = rho > 0.0 ? -0.5 / sq : 0.0;
+        double sq, fp;
+        rgl_embed(rho, sq, fp);
         b.fp[i] = fp;
         if (b.fpff) {   // FP64 form: F' as a float pair for the force pass
             const ffloat q = f64_to_ff(fp);
@@ -454,14 +454,32 @@ __global__ void __launch_bounds__(kForceBlock) k_force_rgl(Bufs b, GeoC g) {
 // a sigma, their gradients added to i here and to j and k by FP64 atomics:
 //   h = lambda eps (c + 1/3)^2 e_j e_k,  e = exp(gamma sigma / (r - a sigma)),
 //   dh/dx_j = dh/dr_j u_j + dh/dc (u_k - c u_j) / r_j   (u = unit vectors).
+// Everything that depends on one neighbour only (u, 1/r, e, and
+// gamma sigma / (r - a sigma)^2 = -d ln e / dr) is computed once per
+// neighbour, so the triplet loop has no division or exponential.
 constexpr int kSwMax = 32;   // neighbours within a sigma per atom (a solid has 4)
 
-__device__ __forceinline__ void sw_pair(const PotC& P, double r, double& e2, double& de2) {
-    const double s = P.sw_sigma, rc = P.sw_rc;
-    const double sr = s / r, bp = P.sw_B * pow(sr, P.sw_p), bq = pow(sr, P.sw_q);
-    const double ex = exp(s / (r - rc));
+// x^e for the SW exponents: repeated squaring when e is a small non-negative
+// integer (ei >= 0), pow() otherwise.
+__device__ __forceinline__ double sw_pow(double x, double e, int ei) {
+    if (ei < 0) return pow(x, e);
+    double r = 1.0, b = x;
+    for (int n = ei; n > 0; n >>= 1) {
+        if (n & 1) r *= b;
+        b *= b;
+    }
+    return r;
+}
+
+// Pair term phi2(r) and phi2'(r) from invr = 1/r and t = 1/(r - a sigma).
+__device__ __forceinline__ void sw_pair(const PotC& P, double invr, double t, double& e2,
+                                        double& de2) {
+    const double s = P.sw_sigma;
+    const double sr = s * invr;
+    const double bp = P.sw_B * sw_pow(sr, P.sw_p, P.sw_pi), bq = sw_pow(sr, P.sw_q, P.sw_qi);
+    const double ex = exp(s * t);
     e2 = P.sw_A * P.eps * (bp - bq) * ex;
-    de2 = P.sw_A * P.eps * ex * ((-P.sw_p * bp + P.sw_q * bq) / r - (bp - bq) * s / ((r - rc) * (r - rc)));
+    de2 = P.sw_A * P.eps * ex * ((-P.sw_p * bp + P.sw_q * bq) * invr - (bp - bq) * s * t * t);
 }
 
 __global__ void __launch_bounds__(kForceBlock) k_force_sw(Bufs b, PotC P, GeoC g) {
@@ -475,11 +493,14 @@ __global__ void __launch_bounds__(kForceBlock) k_force_sw(Bufs b, PotC P, GeoC g
     if (i < b.n) {
         const dvec4 xi = b.x[i];
         const int m = b.nnbr[i];
+        // per neighbour: unit vector, 1/r, exp(gamma sigma / (r - a sigma)) and
+        // gamma sigma / (r - a sigma)^2, so the triplet loop only multiplies
         int nj[kSwMax];
-        double ddx[kSwMax], ddy[kSwMax], ddz[kSwMax], rr[kSwMax], eg[kSwMax];
+        double ux[kSwMax], uy[kSwMax], uz[kSwMax], ir[kSwMax], eg[kSwMax], gd[kSwMax];
         int cnt = 0;
         double fx = 0.0, fy = 0.0, fz = 0.0;
-        const double s = P.sw_sigma, rc = P.sw_rc;
+        const double gs = P.sw_gamma * P.sw_sigma, rc = P.sw_rc;
+        const double le = P.sw_lambda * P.eps;
         for (int k = 0; k < m; ++k) {
             const uint32_t e = b.nbr[(size_t)k * b.n + i];
             const int j = (int)(e & kIdxMask);
@@ -494,21 +515,24 @@ __global__ void __launch_bounds__(kForceBlock) k_force_sw(Bufs b, PotC P, GeoC g
             }
             const double r2 = dx * dx + dy * dy + dz * dz;
             if (!(r2 < P.rc2)) continue;
-            const double r = sqrt(r2);
+            const double invr = rsqrt_newton(r2);   // r2 > 0: list pairs are distinct atoms
+            const double r = r2 * invr;
+            const double t = 1.0 / (r - rc);
             double e2, de2;
-            sw_pair(P, r, e2, de2);
+            sw_pair(P, invr, t, e2, de2);
             e_i += 0.5 * e2;
-            const double w = de2 / r;   // force on i from the pair: +phi2'(r) d / r
+            const double w = de2 * invr;   // force on i from the pair: +phi2'(r) d / r
             fx += w * dx;
             fy += w * dy;
             fz += w * dz;
             if (cnt < kSwMax) {
                 nj[cnt] = j;
-                ddx[cnt] = dx;
-                ddy[cnt] = dy;
-                ddz[cnt] = dz;
-                rr[cnt] = r;
-                eg[cnt] = exp(P.sw_gamma * s / (r - rc));
+                ux[cnt] = dx * invr;
+                uy[cnt] = dy * invr;
+                uz[cnt] = dz * invr;
+                ir[cnt] = invr;
+                eg[cnt] = exp(gs * t);
+                gd[cnt] = gs * t * t;
             }
             ++cnt;
         }
@@ -518,23 +542,22 @@ __global__ void __launch_bounds__(kForceBlock) k_force_sw(Bufs b, PotC P, GeoC g
         }
         for (int p = 0; p < cnt; ++p)
             for (int q = p + 1; q < cnt; ++q) {
-                const double rj = rr[p], rk = rr[q];
-                const double cs = (ddx[p] * ddx[q] + ddy[p] * ddy[q] + ddz[p] * ddz[q]) / (rj * rk);
+                const double ujx = ux[p], ujy = uy[p], ujz = uz[p];
+                const double ukx = ux[q], uky = uy[q], ukz = uz[q];
+                const double cs = ujx * ukx + ujy * uky + ujz * ukz;   // cos theta_jik
                 const double wv = cs + 1.0 / 3.0;
                 const double ee = eg[p] * eg[q];
-                const double h = P.sw_lambda * P.eps * wv * wv * ee;
+                const double h = le * wv * wv * ee;
                 e_i += h;
-                const double dh_dc = 2.0 * P.sw_lambda * P.eps * wv * ee;
-                const double dj = -h * P.sw_gamma * s / ((rj - rc) * (rj - rc));
-                const double dk = -h * P.sw_gamma * s / ((rk - rc) * (rk - rc));
-                const double ujx = ddx[p] / rj, ujy = ddy[p] / rj, ujz = ddz[p] / rj;
-                const double ukx = ddx[q] / rk, uky = ddy[q] / rk, ukz = ddz[q] / rk;
-                const double gjx = dj * ujx + dh_dc * (ukx - cs * ujx) / rj;
-                const double gjy = dj * ujy + dh_dc * (uky - cs * ujy) / rj;
-                const double gjz = dj * ujz + dh_dc * (ukz - cs * ujz) / rj;
-                const double gkx = dk * ukx + dh_dc * (ujx - cs * ukx) / rk;
-                const double gky = dk * uky + dh_dc * (ujy - cs * uky) / rk;
-                const double gkz = dk * ukz + dh_dc * (ujz - cs * ukz) / rk;
+                const double dh_dc = 2.0 * le * wv * ee;
+                const double dj = -h * gd[p], dk = -h * gd[q];
+                const double cj = dh_dc * ir[p], ck = dh_dc * ir[q];
+                const double gjx = dj * ujx + cj * (ukx - cs * ujx);
+                const double gjy = dj * ujy + cj * (uky - cs * ujy);
+                const double gjz = dj * ujz + cj * (ukz - cs * ujz);
+                const double gkx = dk * ukx + ck * (ujx - cs * ukx);
+                const double gky = dk * uky + ck * (ujy - cs * uky);
+                const double gkz = dk * ukz + ck * (ujz - cs * ukz);
                 fx += gjx + gkx;
                 fy += gjy + gky;
                 fz += gjz + gkz;
@@ -859,25 +882,25 @@ __global__ void __launch_bounds__(kForceBlock) k_density_ff(Bufs b, PotC P, GeoC
                 load_row(b.tab_ffd, ff_index(P.tab, uf), row);
                 ffloat v[2];
                 ff_row_eval(row, r2, v);
-                erep = ff_add(erep, HALF ? ff_scale2(v[0], 2.f) : v[0]);
+                erep = ff_add(erep, v[0]);   // doubled at the end on the half list
                 rho = ff_add(rho, v[1]);
                 if (HALF) atomicAdd(&b.rho[j], ff_to_f64(v[1]));
             } else {
                 double rinv, phi, dphi, gg, dg;
                 rgl_pair64(P, ff_to_f64(r2), etab, rinv, phi, dphi, gg, dg);
-                erep = ff_add(erep, f64_to_ff(HALF ? 2.0 * phi : phi));
+                erep = ff_add(erep, f64_to_ff(phi));
                 rho = ff_add(rho, f64_to_ff(gg));
                 if (HALF) atomicAdd(&b.rho[j], gg);
             }
         }
         if (HALF) {
             atomicAdd(&b.rho[i], ff_to_f64(rho));
-            e_atom = ff_to_f64(erep);
+            e_atom = 2.0 * ff_to_f64(erep);   // each pair's 2 phi credited to i
             if (b.eatom) b.eatom[i] = e_atom;
         } else {
             const double rho_d = ff_to_f64(rho);
-            const double sq = sqrt(rho_d);
-            const double fp = rho_d > 0.0 ? -0.5 / sq : 0.0;
+            double sq, fp;
+            rgl_embed(rho_d, sq, fp);
             b.rho[i] = rho_d;
             b.fp[i] = fp;
             const ffloat fpf = f64_to_ff(fp);

@@ -112,6 +112,35 @@ __device__ __forceinline__ float exp32_tang(float x, const Exp32C& c, const floa
     return __int_as_float(__float_as_int(y) + (m << 23));
 }
 
+// RGL embedding F(rho) = -sqrt(rho) at density rho: sqrt(rho) and
+// F'(rho) = -1/(2 sqrt(rho)) from one reciprocal square root y.  Newton's
+// method on f(y) = 1/y^2 - rho gives y <- y + y (1 - rho y^2) / 2, which
+// squares the relative error of y at each step: from the FP32 estimate
+// (~2e-7) two steps land below the FP64 rounding, so sqrt(rho) = rho y and
+// F' = -y/2 are within a few FP64 ulps -- about ten FP64 instructions in
+// place of an IEEE square root and an IEEE division (FP64 issues at 1/58 of
+// FP32 on this part).  Densities outside the FP32 range take the IEEE
+// operations; rho <= 0 (no pair inside rc) gives sqrt = 0, F' = 0.
+__device__ __forceinline__ double rsqrt_newton(double x) {
+    double y = (double)rsqrtf((float)x);
+    for (int k = 0; k < 2; ++k) {
+        const double e = fma(-x * y, y, 1.0);
+        y = fma(0.5 * y, e, y);
+    }
+    return y;
+}
+
+__device__ __forceinline__ void rgl_embed(double rho, double& sq, double& fp) {
+    if (rho > 1e-30 && rho < 1e30) {
+        const double y = rsqrt_newton(rho);
+        sq = rho * y;
+        fp = -0.5 * y;
+    } else {
+        sq = sqrt(rho);
+        fp = rho > 0.0 ? -0.5 / sq : 0.0;
+    }
+}
+
 // Compensated (Kahan) accumulation in FP32: sum + c carries the running
 // total to about one float ulp of the sum.
 struct Kahan32 {
