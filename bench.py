@@ -406,7 +406,8 @@ def batch_compare(fg, torch, dev, cfgs, x, x_fin, boxes, counts):
     """The batched FP32-pair result next to FP64 GPU paths on the same
     systems, all to the same converged max|F_i| < 1e-6 eV/A checked in FP64:
     every FP32-pair structure re-evaluated in FP64; the whole batch relaxed
-    in the batched FP64 form; and a sample of 32 systems (every 16th by
+    in the batched FP64 form (double-float table terms, the default FP64
+    pair evaluation); and a sample of 32 systems (every 16th by
     size) relaxed one at a time through the single-system FP64 path (default
     form, whole loop in one CUDA graph), as a caller without the batched
     entry point would."""

@@ -328,7 +328,10 @@ fire_status fire_diag_exp(int64_t n, const double* d_x, double* d_out, void* str
  * its own dt, alpha, counters, neighbour list and stop reason) of uneven atom
  * counts in one persistent kernel launch: each CTA takes the next system from
  * a device queue (largest first) and relaxes it to its own stop.  RGL
- * potential only; FP64 or FP32-pair precision as in fire_potential_t.  The
+ * potential only; FP64 or FP32-pair precision as in fire_potential_t, and in
+ * FP64 the pair evaluation of pot->pair_eval (FIRE_PAIR_TABLE: double-float
+ * table terms on exact fixed-point separations, as in the single-system
+ * FP64 form; FIRE_PAIR_ANALYTIC: IEEE-FP64 exponentials).  The
  * paper relaxes one configuration per run; the batch is this library's
  * throughput form (e.g. for ensembles of defect configurations). */
 

@@ -609,6 +609,8 @@ FIRE2_HIDDEN double fire2_budget(fire_handle_t* h) { return h->budget_s; }
 FIRE2_HIDDEN const double* fire2_exp_table(fire_handle_t* h) { return h->b.exp_table; }
 FIRE2_HIDDEN const float* fire2_exp32_table(fire_handle_t* h) { return h->b.exp32_table; }
 FIRE2_HIDDEN double fire2_qscale(fire_handle_t* h) { return h->b.qscale; }
+FIRE2_HIDDEN const float* fire2_tab_ffd(fire_handle_t* h) { return h->tab_ffd; }
+FIRE2_HIDDEN const float* fire2_tab_fff(fire_handle_t* h) { return h->tab_fff; }
 FIRE2_HIDDEN cudaStream_t fire2_stream(fire_handle_t* h) { return h->stream; }
 
 extern "C" {
@@ -843,6 +845,11 @@ static fire_status init_handle(fire_handle_t** hp, const fire_system_t* sys,
         CKI(cudaMemcpy(t, exp32_table_host, kExp32TableSize * sizeof(float), cudaMemcpyHostToDevice));
     }
     if (!single) {
+        // the batched FP64 form reads the same double-float pair tables
+        if (fixed64_form(*pot)) {
+            const fire_status ts = upload_tables(h);
+            if (ts != FIRE_OK) return bail(ts);
+        }
         *hp = h;
         return FIRE_OK;
     }

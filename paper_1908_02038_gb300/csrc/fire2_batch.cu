@@ -24,6 +24,7 @@
 
 #include "fire2.h"
 #include "fire2_common.cuh"
+#include "fire2_table.cuh"
 
 using namespace fire2;
 
@@ -37,6 +38,7 @@ struct BInst {
     int nc[3];              // cells per axis; nc[0] == 0 -> all-pairs build
     int per[3];
     int Lq[3];              // box in fixed-point units (FP32-pair form)
+    long long Lq64[3];      // box in 2^-44 A units (FP64 table form)
     double L[3], Linv[3];
     float Lf[3], Linvf[3];
     float rlist2f;
@@ -59,6 +61,10 @@ struct BArgs {
     dvec4 *x, *v, *f, *xref;
     int4* xq;
     float4* xf;
+    lvec4* xq64;            // FP64 table form: positions in 2^-44 A units
+    float2* fpff;           // FP64 table form: F'(rho) as a float pair
+    const float *tab_ffd, *tab_fff;   // FP64 table form: density / force rows
+    int ff;                 // 1: FP64 table form (double-float pair terms)
     double* fp64;           // F'(rho) (FP64 form)
     float* fp32;            // F'(rho) (FP32-pair form)
     uint32_t* nbr;
@@ -203,6 +209,24 @@ __device__ __forceinline__ int b_build(const BArgs& a, const BInst& I, int lo, i
     return (int)bmax((double)(bad != ST_OK ? bad : (over ? ST_NBR_OVERFLOW : 0)), red);
 }
 
+// Separation x_j - x_i - shift of list entry e in the FP64 table form: exact
+// in 2^-44 A fixed point, split into float pairs; returns r^2.
+__device__ __forceinline__ ffloat b_sep_ff(const BArgs& a, const BInst& I, const lvec4& qi,
+                                           uint32_t e, ffloat& dx, ffloat& dy, ffloat& dz) {
+    const int j = (int)(e & kIdxMask), code = (int)(e >> kIdxBits);
+    const lvec4 qj = a.xq64[I.off + j];
+    long long ix = qj.x - qi.x, iy = qj.y - qi.y, iz = qj.z - qi.z;
+    if (code != kCodeZero) {
+        ix -= (long long)(code % 5 - 2) * I.Lq64[0];
+        iy -= (long long)((code / 5) % 5 - 2) * I.Lq64[1];
+        iz -= (long long)(code / 25 - 2) * I.Lq64[2];
+    }
+    dx = fixed_to_ff(ix);
+    dy = fixed_to_ff(iy);
+    dz = fixed_to_ff(iz);
+    return ff_norm2(dx, dy, dz);
+}
+
 // Energy and forces of atoms [lo, hi) of one system (full list, no
 // atomics); returns their energy.  With CL, the CTAs of a thread-block
 // cluster share the system: the cluster barrier between the passes makes
@@ -241,6 +265,35 @@ __device__ __forceinline__ double b_forces(const BArgs& a, const BInst& I, int l
             const float sq = sqrtf(rf);
             a.fp32[gi] = rf > 0.f ? -0.5f / sq : 0.f;
             e_sum += erep.value() - (double)sq;
+        } else if (a.ff) {   // FP64 table form: double-float pair terms, FP64 embedding
+            const lvec4 qi = a.xq64[gi];
+            ffloat rho = {0.f, 0.f}, erep = {0.f, 0.f};
+            for (int k = 0; k < m; ++k) {
+                ffloat dx, dy, dz;
+                const ffloat r2 =
+                    b_sep_ff(a, I, qi, a.nbr[I.list_off + (long long)k * I.n + i], dx, dy, dz);
+                if (!(r2.hi < P.rc2_f)) continue;
+                const float uf = r2.hi - P.r0sq_f;
+                if (uf >= P.tab.u_lo_f) {
+                    float row[kFFRow];
+                    load_row(a.tab_ffd, ff_index(P.tab, uf), row);
+                    ffloat v[2];
+                    ff_row_eval(row, r2, v);
+                    erep = ff_add(erep, v[0]);
+                    rho = ff_add(rho, v[1]);
+                } else {   // compressed below the table: FP64 exponentials
+                    double rinv, phi, dphi, g, dg;
+                    rgl_pair64(P, ff_to_f64(r2), etab, rinv, phi, dphi, g, dg);
+                    erep = ff_add(erep, f64_to_ff(phi));
+                    rho = ff_add(rho, f64_to_ff(g));
+                }
+            }
+            double sq, fp;
+            rgl_embed(ff_to_f64(rho), sq, fp);
+            a.fp64[gi] = fp;
+            const ffloat fpf = f64_to_ff(fp);
+            a.fpff[gi] = make_float2(fpf.hi, fpf.lo);
+            e_sum += ff_to_f64(erep) - sq;
         } else {
             const dvec4 xi = a.x[gi];
             double rho = 0.0, erep = 0.0;
@@ -297,6 +350,35 @@ __device__ __forceinline__ double b_forces(const BArgs& a, const BInst& I, int l
                 fz.add(fs * (float)dz);
             }
             a.f[gi] = make_dvec4(fx.value(), fy.value(), fz.value(), 0.0);
+        } else if (a.ff) {
+            const lvec4 qi = a.xq64[gi];
+            const float2 fpi2 = a.fpff[gi];
+            const ffloat fpi = {fpi2.x, fpi2.y};
+            ffloat fx = {0.f, 0.f}, fy = {0.f, 0.f}, fz = {0.f, 0.f};
+            for (int k = 0; k < m; ++k) {
+                const uint32_t e = a.nbr[I.list_off + (long long)k * I.n + i];
+                ffloat dx, dy, dz;
+                const ffloat r2 = b_sep_ff(a, I, qi, e, dx, dy, dz);
+                if (!(r2.hi < P.rc2_f)) continue;
+                const float uf = r2.hi - P.r0sq_f;
+                ffloat c[2];
+                if (uf >= P.tab.u_lo_f) {
+                    float row[kFFRow];
+                    load_row(a.tab_fff, ff_index(P.tab, uf), row);
+                    ff_row_eval(row, r2, c);
+                } else {
+                    double rinv, phi, dphi, g, dg;
+                    rgl_pair64(P, ff_to_f64(r2), etab, rinv, phi, dphi, g, dg);
+                    c[0] = f64_to_ff(2.0 * dphi * rinv);
+                    c[1] = f64_to_ff(dg * rinv);
+                }
+                const float2 fpj2 = a.fpff[I.off + (int)(e & kIdxMask)];
+                const ffloat fs = ff_add(c[0], ff_mul(ff_add(fpi, {fpj2.x, fpj2.y}), c[1]));
+                fx = ff_add(fx, ff_mul(fs, dx));
+                fy = ff_add(fy, ff_mul(fs, dy));
+                fz = ff_add(fz, ff_mul(fs, dz));
+            }
+            a.f[gi] = make_dvec4(ff_to_f64(fx), ff_to_f64(fy), ff_to_f64(fz), 0.0);
         } else {
             const dvec4 xi = a.x[gi];
             const double fpi = a.fp64[gi];
@@ -368,9 +450,12 @@ __device__ __forceinline__ void cl_combine(ClX& x, const double* v, int nsum, in
 }
 
 // FP64 reductions of (F, v) of atoms [lo, hi) (combined over the cluster),
-// then Algorithm 2 in thread 0 of every CTA on identical inputs.
+// then Algorithm 2 in thread 0 of every CTA on identical inputs.  Kept out of
+// line: inlined, its FP64 scalar state raised the kernel's register peak and
+// made the 64-register budget spill (228 bytes) in the force loops; called,
+// nothing spills and the 1024-thread shape runs 3 % faster.
 template <bool CL>
-__device__ __forceinline__ void b_reduce_control(const BArgs& a, const BInst& I, int lo, int hi,
+__device__ __noinline__ void b_reduce_control(const BArgs& a, const BInst& I, int lo, int hi,
                                                  BShared& sh, ClX& X, double E, double* red,
                                                  unsigned long long t0) {
     double P = 0.0, F2 = 0.0, V2 = 0.0, fa2 = 0.0, fin = 0.0;
@@ -493,6 +578,9 @@ __global__ void __launch_bounds__(MAXT, 1) k_batch_relax(BArgs a) {
             if (F32)
                 a.xq[gi] = make_int4(to_fixed(p[0], a.qscale), to_fixed(p[1], a.qscale),
                                      to_fixed(p[2], a.qscale), 0);
+            else if (a.ff)
+                a.xq64[gi] = {to_fixed64(p[0], kFixedBits64), to_fixed64(p[1], kFixedBits64),
+                              to_fixed64(p[2], kFixedBits64), 0ll};
             a.v[gi] = make_dvec4(0.0, 0.0, 0.0, 0.0);
         }
         const double anybad = bmax((double)bad, red);
@@ -543,6 +631,9 @@ __global__ void __launch_bounds__(MAXT, 1) k_batch_relax(BArgs a) {
                 if (F32)
                     a.xq[gi] = make_int4(to_fixed(x.x, a.qscale), to_fixed(x.y, a.qscale),
                                          to_fixed(x.z, a.qscale), 0);
+                else if (a.ff)
+                    a.xq64[gi] = {to_fixed64(x.x, kFixedBits64), to_fixed64(x.y, kFixedBits64),
+                                  to_fixed64(x.z, kFixedBits64), 0ll};
                 const dvec4 r = a.xref[gi];
                 const double ddx = x.x - r.x, ddy = x.y - r.y, ddz = x.z - r.z;
                 dmax = fmax(dmax, ddx * ddx + ddy * ddy + ddz * ddz);
@@ -627,6 +718,8 @@ double fire2_budget(fire_handle_t* h);
 const double* fire2_exp_table(fire_handle_t* h);
 const float* fire2_exp32_table(fire_handle_t* h);
 double fire2_qscale(fire_handle_t* h);
+const float* fire2_tab_ffd(fire_handle_t* h);   // NULL unless the FP64 table form
+const float* fire2_tab_fff(fire_handle_t* h);
 cudaStream_t fire2_stream(fire_handle_t* h);
 
 #define BCK(call)                                                                         \
@@ -643,7 +736,8 @@ cudaStream_t fire2_stream(fire_handle_t* h);
 static void free_batch(fire_batch_state* b) {
     if (!b) return;
     BArgs& a = b->args;
-    void* ptrs[] = {a.x, a.v, a.f, a.xref, a.xq, a.xf, a.fp64, a.fp32, a.nbr, a.nnbr, a.pos_io,
+    void* ptrs[] = {a.x, a.v, a.f, a.xref, a.xq, a.xf, a.xq64, a.fpff, a.fp64, a.fp32, a.nbr,
+                    a.nnbr, a.pos_io,
                     b->d_inst, b->d_res, b->d_order, b->d_queue};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -684,6 +778,7 @@ static fire_status batch_geometry(fire_handle_t* h, fire_batch_state* b, const d
             I.Linvf[k] = (float)(1.0 / L);
             I.per[k] = sys.periodic[k] ? 1 : 0;
             I.Lq[k] = (int)(unsigned)(unsigned long long)std::llrint(L * qscale);
+            I.Lq64[k] = std::llrint(std::ldexp(L, kFixedBits64));
             // open axes take any cell count (clamped cells), periodic ones 3 or more
             I.nc[k] = std::max((int)std::floor(L / rl), I.per[k] ? 0 : 1);
             if (I.per[k] && I.nc[k] < 3) cells = false;
@@ -749,6 +844,13 @@ FIRE2_HIDDEN fire_status fire2_batch_create(fire_handle_t* h, int32_t n_sys,
         BA(a.fp32, n * sizeof(float));
     } else {
         BA(a.fp64, n * sizeof(double));
+    }
+    a.ff = fire2_tab_ffd(h) != nullptr && !f32 ? 1 : 0;
+    if (a.ff) {
+        BA(a.xq64, n * sizeof(lvec4));
+        BA(a.fpff, n * sizeof(float2));
+        a.tab_ffd = fire2_tab_ffd(h);
+        a.tab_fff = fire2_tab_fff(h);
     }
     BA(a.nnbr, n * sizeof(int));
     BA(a.pos_io, 3 * n * sizeof(double));

@@ -839,18 +839,6 @@ __device__ __forceinline__ ffloat pair_sep_ff(const Bufs& b, const long long* qt
     return pair_sep_ff_q(qt, qi, b.xq64[e & kIdxMask], e, dx, dy, dz, j);
 }
 
-__device__ __forceinline__ void load_row(const float* tab, int k, float row[kFFRow]) {
-    const float4* src = reinterpret_cast<const float4*>(tab + (size_t)k * kFFRow);
-#pragma unroll
-    for (int q = 0; q < kFFRow / 4; ++q) {
-        const float4 v = __ldg(src + q);
-        row[4 * q] = v.x;
-        row[4 * q + 1] = v.y;
-        row[4 * q + 2] = v.z;
-        row[4 * q + 3] = v.w;
-    }
-}
-
 // Pass 1.  Full list (HALF = false): rho_i, F'(rho_i) (FP64 per atom) and the
 // atom's energy sum_j phi - sqrt(rho_i), all in the atom's thread.  Half
 // list (HALF = true): rho_i and rho_j (FP64 atomics), 2 phi per pair credited

@@ -401,6 +401,19 @@ __host__ __device__ __forceinline__ int ff_index(const TabMeta& m, float uf) {
     return k < 0 ? 0 : (k > last ? last : k);
 }
 
+// Row k of a table in global memory (80 bytes, 16-byte aligned), through L1.
+__device__ __forceinline__ void load_row(const float* tab, int k, float row[kFFRow]) {
+    const float4* src = reinterpret_cast<const float4*>(tab + (size_t)k * kFFRow);
+#pragma unroll
+    for (int q = 0; q < kFFRow / 4; ++q) {
+        const float4 v = __ldg(src + q);
+        row[4 * q] = v.x;
+        row[4 * q + 1] = v.y;
+        row[4 * q + 2] = v.z;
+        row[4 * q + 3] = v.w;
+    }
+}
+
 // The two polynomials of `row` at r^2 (float pair): out[0], out[1].
 __host__ __device__ __forceinline__ void ff_row_eval(const float* row, ffloat r2, ffloat out[2]) {
     const ffloat s = ff_add(r2, ff_neg({row[0], row[1]}));

@@ -16,8 +16,14 @@ def _built():
     fg.load_library()
 
 
-def rgl_pot(precision=fg.FIRE_PREC_FP64):
-    return fg.Potential(fg.FIRE_POT_RGL, precision=precision, skin=0.3, **fi.RGL_CU)
+def rgl_pot(precision=fg.FIRE_PREC_FP64, pair_eval=fg.FIRE_PAIR_TABLE):
+    # FP64: the table form (double-float pair terms) by default, the IEEE-FP64
+    # exponentials with FIRE_PAIR_ANALYTIC
+    return fg.Potential(fg.FIRE_POT_RGL, precision=precision, pair_eval=pair_eval, skin=0.3,
+                        **fi.RGL_CU)
+
+
+FP64_FORMS = [fg.FIRE_PAIR_TABLE, fg.FIRE_PAIR_ANALYTIC]
 
 
 def ora_rgl():
@@ -36,10 +42,11 @@ def small_batch(n_sys=10, seed=50):
     return fi.rgl_batch(n_sys=n_sys, seed=seed, nmin=3, nmax=6)
 
 
-def test_batch_fp64_forces_match_oracle():
+@pytest.mark.parametrize("pair_eval", FP64_FORMS)
+def test_batch_fp64_forces_match_oracle(pair_eval):
     cfgs = small_batch()
     x, boxes, counts = pack(cfgs)
-    with fg.FireBatch(counts, fi.CU_MASS, rgl_pot(), dt_start=fi.CU_DT) as b:
+    with fg.FireBatch(counts, fi.CU_MASS, rgl_pot(pair_eval=pair_eval), dt_start=fi.CU_DT) as b:
         res, f = b.minimize(x.copy(), boxes, 1e-6, 0, want_forces=True)
     off = np.concatenate([[0], np.cumsum(counts)])
     for s, c in enumerate(cfgs):
@@ -50,10 +57,11 @@ def test_batch_fp64_forces_match_oracle():
         assert res[s].iterations == 0 and res[s].stop == fg.FIRE_STOP_MAXITER
 
 
-def test_batch_fp64_relaxations_match_oracle():
+@pytest.mark.parametrize("pair_eval", FP64_FORMS)
+def test_batch_fp64_relaxations_match_oracle(pair_eval):
     cfgs = small_batch(n_sys=8, seed=51)
     x, boxes, counts = pack(cfgs)
-    with fg.FireBatch(counts, fi.CU_MASS, rgl_pot(), dt_start=fi.CU_DT) as b:
+    with fg.FireBatch(counts, fi.CU_MASS, rgl_pot(pair_eval=pair_eval), dt_start=fi.CU_DT) as b:
         res, _ = b.minimize(x, boxes, 1e-6, 100000)
     for s, c in enumerate(cfgs):
         _, ro, _ = oracle.fire2(c.x, c.box, ora_rgl(), oracle.Params(dt_start=fi.CU_DT),

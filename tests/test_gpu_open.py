@@ -113,14 +113,16 @@ def test_sw_slab_energy_forces_match_oracle():
     assert e == pytest.approx(eo, rel=1e-12)
 
 
-@pytest.mark.parametrize("precision", [fg.FIRE_PREC_FP64, fg.FIRE_PREC_FP32_PAIR])
-def test_batch_open_axis_matches_oracle(precision):
+@pytest.mark.parametrize("precision,pair_eval", [
+    (fg.FIRE_PREC_FP64, fg.FIRE_PAIR_TABLE), (fg.FIRE_PREC_FP64, fg.FIRE_PAIR_ANALYTIC),
+    (fg.FIRE_PREC_FP32_PAIR, fg.FIRE_PAIR_ANALYTIC)])
+def test_batch_open_axis_matches_oracle(precision, pair_eval):
     cfgs = [fi.rgl_slab(ncell=n, nz=m, seed=40 + n, n_vac=1, sigma=0.08, vacuum=6.0)
             for n, m in [(3, 3), (4, 6), (6, 4), (5, 5)]]
     x = np.ascontiguousarray(np.concatenate([c.x for c in cfgs]))
     boxes = np.array([c.box for c in cfgs])
     counts = [c.n for c in cfgs]
-    pot = fg.Potential(fg.FIRE_POT_RGL, precision=precision, pair_eval=fg.FIRE_PAIR_ANALYTIC,
+    pot = fg.Potential(fg.FIRE_POT_RGL, precision=precision, pair_eval=pair_eval,
                        skin=0.3, **fi.RGL_CU)
     with fg.FireBatch(counts, fi.CU_MASS, pot, dt_start=fi.CU_DT, periodic=(1, 1, 0)) as b:
         res, f = b.minimize(x.copy(), boxes, 1e-6, 0, want_forces=True)
