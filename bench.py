@@ -41,8 +41,9 @@ FTOL = 1e-6
 # Largest FP32-pair force error (|F_32 - F_64| per atom) at relaxed Cu
 # structures, measured on GB300 over the 1M box and the 512-system batch
 # (2.3 M atoms; max 5.6e-7 eV/A, 99.99th percentile 4.4e-7), rounded up: the
-# FP32-pair forms stop at ftol less this, so that their structures meet ftol
-# when re-evaluated in FP64 (which every FP32-pair result in the line is).
+# batched FP32-pair form stops at ftol less this, so that its structures meet
+# ftol when re-evaluated in FP64 (which every FP32-pair result in the line
+# is); the single-system FP32-pair form confirms its stop in FP64 instead.
 FP32_FORCE_ERR = 6e-7
 MAXITER = 200000
 CONFIGS = {
@@ -135,9 +136,10 @@ def potential_for(cfg_name, form="fp64"):
         return (fg.Potential(fg.FIRE_POT_LJ, eps=1.0, sigma=1.0, rc_lj=2.5, skin=0.3),
                 fi.LJ_MASS, fi.LJ_DT, 1e-8)
     prec = fg.FIRE_PREC_FP32_PAIR if form == "fp32pair" else fg.FIRE_PREC_FP64
-    # the FP32-pair form stops at ftol less its force error (FP32_FORCE_ERR),
-    # so that its structure meets ftol when re-evaluated in FP64
-    ftol = FTOL - FP32_FORCE_ERR if form == "fp32pair" else FTOL
+    # the FP32-pair form stops at ftol: the library confirms such a stop with
+    # one FP64 evaluation (fire_params_t.confirm64), so its structure meets
+    # ftol in FP64 (which the line checks again)
+    ftol = FTOL
     return (fg.Potential(fg.FIRE_POT_RGL, precision=prec, skin=0.3, **fi.RGL_CU), fi.CU_MASS,
             fi.CU_DT, ftol)
 
@@ -268,16 +270,18 @@ class _NoClock:
 
 def launches_of(results, is_rgl, fp32, cell_mode):
     """Kernels one relaxation launches: prepare, list build, forces, reduce,
-    control, finalize once; per iteration update, forces, reduce (FP64 forms:
-    the FP32-pair force pass fuses it), control; the build chain (binning +
-    list) once per rebuild."""
+    control, finalize once; per loop pass update, forces, reduce, control;
+    the build chain (binning + list) once per rebuild.  The FP32-pair form
+    also launches the two FP64 confirming passes with every evaluation (they
+    return at once unless a stop is being confirmed), and each confirmation
+    is one more loop pass (force evaluations - iterations - 1)."""
     build_k = 6 if cell_mode else 1
-    force_k = (2 if fp32 else 3) if is_rgl else 1
-    reduce_k = 0 if fp32 else 1
+    force_k = (2 + 2 if fp32 else 3) if is_rgl else 1
     total = 0
     for rr in results:
-        total += (1 + build_k + force_k + reduce_k + 1 + 1)
-        total += (1 + force_k + reduce_k + 1) * rr["iterations"]
+        passes = rr["iterations"] + max(0, rr["force_evals"] - rr["iterations"] - 1)
+        total += (1 + build_k + force_k + 1 + 1 + 1)
+        total += (1 + force_k + 1 + 1) * passes
         total += build_k * max(0, rr["nbr_builds"] - 1)
     return total
 
@@ -658,6 +662,7 @@ def run_gpu(args):
                     "value": n * it2 / (ms2 * 1e-3), "unit": UNIT,
                     "ms_per_step": ms2 / args.steps, "ftol": m2["ftol"],
                     "iterations_per_step": [rr["iterations"] for rr in m2["results"]],
+                    "force_evals_per_step": [rr["force_evals"] for rr in m2["results"]],
                     "final_fmax_atom_own": [rr["fmax_atom"] for rr in m2["results"]],
                     "final_fmax_atom_ieee_fp64_check": f64_fmax,
                     "energy_per_atom_ieee_fp64_check": e64 / n,

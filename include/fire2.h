@@ -166,7 +166,15 @@ typedef struct {
     int32_t integrator;         /* fire_integrator                   (default 0) */
     int32_t norm;               /* fire_norm for the ftol test       (default 0) */
     int32_t variant;            /* fire_variant                      (default 0) */
-    int32_t reserved;
+    int32_t confirm64;          /* FP32-pair form (default 1): when the FP32-pair forces
+                                   meet ftol, the same configuration is evaluated once
+                                   more in FP64 (double-float table terms, full list)
+                                   and the relaxation stops only if those forces meet
+                                   ftol too; otherwise it tightens its FP32 threshold
+                                   by the FP32-FP64 difference seen there and goes on.
+                                   Each confirmation is one force evaluation that is not
+                                   an iteration.  0: stop on the FP32-pair forces.
+                                   Other forms ignore it. */
     double dmax;                /* maximum displacement of any atom per step (the
                                    paper's dmax, Sec. 4 cases 1 and 7), 0 = no cap
                                    (default 0): the drift x += dt v uses

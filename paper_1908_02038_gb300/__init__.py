@@ -71,7 +71,7 @@ class fire_params_t(C.Structure):
                 ("alphashrink", C.c_double), ("delaystep", C.c_int32), ("vdfmax", C.c_int32),
                 ("halfstepback", C.c_int32), ("initialdelay", C.c_int32),
                 ("integrator", C.c_int32), ("norm", C.c_int32), ("variant", C.c_int32),
-                ("reserved", C.c_int32), ("dmax", C.c_double)]
+                ("confirm64", C.c_int32), ("dmax", C.c_double)]
 
 
 class fire_batch_tuning_t(C.Structure):

@@ -98,6 +98,7 @@ struct fire_handle {
     int nb_tab_d = 0, nb_tab_f = 0;
     uint8_t* dofmask = nullptr;      // device copy of the frozen-DOF mask (n bytes)
     int img_n = 0;                   // atoms per image (n, except for NEB handles)
+    bool verify = false;             // FP32-pair: stops on ftol confirmed in FP64
     NebState* neb = nullptr;
     std::string err;
 };
@@ -284,6 +285,12 @@ void launch_forces(fire_handle* h, const GeoC& g, cudaStream_t s) {
         k_force_sw<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
     } else {
         k_force_lj<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
+    }
+    if (h->verify) {   // FP64 passes on the same full list; they run only to confirm a stop
+        Bufs bv = h->b;
+        bv.pass_role = 2;
+        k_density_ff<false><<<h->b.nb_verify, kForceBlock, 0, s>>>(bv, h->potc, g);
+        k_force_ff<false><<<h->b.nb_verify, kForceBlock, 0, s>>>(bv, h->potc, g);
     }
     (void)n;
 }
@@ -526,6 +533,8 @@ void init_state(fire_handle* h, double ftol, int64_t maxiter) {
     q.dmax = p.dmax;
     fire_scal_init(q, s.fs);
     s.budget_ns = (unsigned long long)(h->budget_s * 1e9);
+    s.ftol_user = ftol;
+    s.vstate = h->verify ? 1 : 0;
 }
 
 fire_status status_to_error(fire_handle* h, int st) {
@@ -633,7 +642,7 @@ fire_status fire_default_params(fire_params_t* out, double dt_start) {
     out->integrator = FIRE_INT_EULER_IMPLICIT;
     out->norm = FIRE_NORM_MAX_ATOM;
     out->variant = FIRE_VARIANT_FIRE2;
-    out->reserved = 0;
+    out->confirm64 = 1;
     out->dmax = 0.0;
     return FIRE_OK;
 }
@@ -870,11 +879,15 @@ static fire_status init_handle(fire_handle_t** hp, const fire_system_t* sys,
     b.nb_embed = (pot->kind == FIRE_POT_RGL && !whole)
                      ? std::max(1, std::min(ceil_div(h->n, kElemBlock), sms * 8)) : 0;
     b.nb_red = std::max(1, std::min(ceil_div(h->n, kElemBlock), sms * 4));
-    if (pot->kind == FIRE_POT_RGL && pot->pair_eval == FIRE_PAIR_TABLE) {
+    // an FP32-pair stop on ftol is confirmed with the FP64 table passes
+    h->verify = fp32pair && pot->kind == FIRE_POT_RGL && params->confirm64 != 0;
+    if (pot->kind == FIRE_POT_RGL && (pot->pair_eval == FIRE_PAIR_TABLE || h->verify)) {
         fire_status ts = upload_tables(h);
         if (ts != FIRE_OK) return bail(ts);
-        if (fp32pair) b.nb_force = h->nb_tab_d;
+        if (fp32pair && pot->pair_eval == FIRE_PAIR_TABLE) b.nb_force = h->nb_tab_d;
     }
+    b.nb_verify = h->verify ? ceil_div(h->n, kForceBlock) : 0;
+    b.pass_role = h->verify ? 1 : 0;
     CKI(cudaMalloc(&b.x, n * sizeof(dvec4)));
     CKI(cudaMalloc(&b.v, n * sizeof(dvec4)));
     CKI(cudaMalloc(&b.f, n * sizeof(dvec4)));
@@ -884,7 +897,7 @@ static fire_status init_handle(fire_handle_t** hp, const fire_system_t* sys,
         CKI(cudaMalloc(&b.xq, n * sizeof(int4)));
         CKI(cudaMalloc(&b.fp32, n * sizeof(float)));
     }
-    if (fixed64) {
+    if (fixed64 || h->verify) {
         CKI(cudaMalloc(&b.xq64, n * sizeof(lvec4)));
         CKI(cudaMalloc(&b.fpff, n * sizeof(float2)));
     }
@@ -895,10 +908,11 @@ static fire_status init_handle(fire_handle_t** hp, const fire_system_t* sys,
         CKI(cudaMalloc(&b.rho, n * sizeof(double)));
         CKI(cudaMalloc(&b.fp, n * sizeof(double)));
     }
-    CKI(cudaMalloc(&b.epart, (size_t)(b.nb_force + b.nb_embed) * sizeof(double)));
+    const size_t n_epart = (size_t)std::max(b.nb_force + b.nb_embed, b.nb_verify);
+    CKI(cudaMalloc(&b.epart, n_epart * sizeof(double)));
     // the FP32-pair table kernels write fewer energy partials than nb_force;
     // the rest stay 0
-    CKI(cudaMemset(b.epart, 0, (size_t)(b.nb_force + b.nb_embed) * sizeof(double)));
+    CKI(cudaMemset(b.epart, 0, n_epart * sizeof(double)));
     CKI(cudaMalloc(&b.rpart, (size_t)5 * b.nb_red * sizeof(double)));
     CKI(cudaMalloc(&b.st, sizeof(DevState)));
     CKI(cudaMalloc(&b.pos_io, 3 * n * sizeof(double)));

@@ -315,10 +315,15 @@ __host__ __device__ inline void fire_scal_init(const FireParamsD& p, FireScal& s
 //    Leapfrog initialisation v(-dt/2) = -dt/2 F / m at the first iteration.
 // Norms of mixed velocities come from the reductions:
 // |v + c F|^2 = |v|^2 + 2 c P + c^2 |F|^2.  Returns true to stop.
+// The stopping norm of Sec. 3.4 (fire_norm) from the reductions.
+__device__ __forceinline__ double force_norm(int norm, double F2, double fa2, double fin) {
+    return norm == 1 ? sqrt(F2) : (norm == 2 ? fin : sqrt(fa2));
+}
+
 __device__ inline bool fire_control_step(const FireParamsD& p, FireScal& s, double P, double F2,
                                          double V2, double fa2, double fin) {
     s.evals += 1;
-    const double fn = p.norm == 1 ? sqrt(F2) : (p.norm == 2 ? fin : sqrt(fa2));
+    const double fn = force_norm(p.norm, F2, fa2, fin);
     if (fn < p.ftol) {
         s.stop = STOP_FTOL;
         return true;

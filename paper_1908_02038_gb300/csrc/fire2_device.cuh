@@ -59,6 +59,12 @@ struct DevState {
     unsigned long long max_disp2;           // bits of max |x - x_ref|^2 (>= 0)
     unsigned int upd_blocks;                // k_update blocks finished (last-block test)
     unsigned long long vmax2;               // bits of max |v_i|^2 before the drift (dmax)
+    // FP64 confirmation of an FP32-pair stop on ftol: vstate 0 = off, 1 = FP32
+    // phase, 2 = the current evaluation confirms in FP64; prm.ftol is the
+    // (possibly tightened) FP32 threshold, ftol_user the caller's, fn32 the
+    // FP32 norm at the configuration being confirmed
+    int vstate, vcount;
+    double ftol_user, fn32;
 };
 
 struct Bufs {
@@ -81,6 +87,9 @@ struct Bufs {
     const float *tab_ffd, *tab_fff;   // FP64 form: density / force rows (kFFRow floats)
     lvec4* xq64;               // FP64 form: positions in 2^-44 A units
     float2* fpff;              // FP64 form: F'(rho) as a float pair
+    int pass_role;             // 0: always run; 1: FP32-pair pass that sits out the FP64
+                               //    confirmation; 2: FP64 pass that runs only for it
+    int nb_verify;             // blocks of the FP64 confirming passes
     const float *tab_d32, *tab_f32;
     uint32_t *nbr;
     int *nnbr;
@@ -92,6 +101,15 @@ struct Bufs {
     double* f_out;         // N x 3 row-major forces (evaluation only)
     double* e_out;         // energy (evaluation only)
 };
+
+// Whether a force pass sits this evaluation out (pass_role above; the state
+// says whether the evaluation confirms an FP32-pair stop in FP64).
+__device__ __forceinline__ bool pass_skipped(const Bufs& b) {
+    if (b.st->done) return true;
+    if (b.pass_role == 0) return false;
+    const bool confirming = b.st->vstate == 2;
+    return b.pass_role == 1 ? confirming : !confirming;
+}
 
 // Image-shift table: code = (sx+2) + 5 (sy+2) + 25 (sz+2), shift = s * L.
 __device__ __forceinline__ void fill_shift_table(double3* tbl, const GeoC& g) {
@@ -726,7 +744,7 @@ __global__ void __launch_bounds__(kForceBlock) k_density32(Bufs b, PotC P, GeoC 
     __shared__ int3 qt[125];
     __shared__ float et[kExp32TableSize];
     __shared__ double red[32];
-    if (b.st->done) return;
+    if (pass_skipped(b)) return;
     fill_qshift_table(qt, g);
     for (int t = threadIdx.x; t < kExp32TableSize; t += blockDim.x) et[t] = b.exp32_table[t];
     __syncthreads();
@@ -762,7 +780,7 @@ __global__ void __launch_bounds__(kForceBlock) k_density32(Bufs b, PotC P, GeoC 
 __global__ void __launch_bounds__(kForceBlock) k_force32(Bufs b, PotC P, GeoC g) {
     __shared__ int3 qt[125];
     __shared__ float et[kExp32TableSize];
-    if (b.st->done) return;
+    if (pass_skipped(b)) return;
     fill_qshift_table(qt, g);
     for (int t = threadIdx.x; t < kExp32TableSize; t += blockDim.x) et[t] = b.exp32_table[t];
     __syncthreads();
@@ -849,7 +867,7 @@ __global__ void __launch_bounds__(kForceBlock) k_density_ff(Bufs b, PotC P, GeoC
     __shared__ long long qt[375];
     __shared__ double etab[kExpTableSize];
     __shared__ double red[32];
-    if (b.st->done) return;
+    if (pass_skipped(b)) return;
     fill_qshift64_table(qt, g);
     for (int t = threadIdx.x; t < kExpTableSize; t += blockDim.x) etab[t] = b.exp_table[t];
     __syncthreads();
@@ -907,7 +925,7 @@ template <bool HALF>
 __global__ void __launch_bounds__(kForceBlock) k_force_ff(Bufs b, PotC P, GeoC g) {
     __shared__ long long qt[375];
     __shared__ double etab[kExpTableSize];
-    if (b.st->done) return;
+    if (pass_skipped(b)) return;
     fill_qshift64_table(qt, g);
     for (int t = threadIdx.x; t < kExpTableSize; t += blockDim.x) etab[t] = b.exp_table[t];
     __syncthreads();
@@ -977,7 +995,7 @@ __global__ void __launch_bounds__(kTabBlock) k_density32_tab(Bufs b, PotC P, Geo
     __shared__ int3 qt[125];
     __shared__ float et[kExp32TableSize];
     __shared__ double red[32];
-    if (b.st->done) return;
+    if (pass_skipped(b)) return;
     fill_qshift_table(qt, g);
     load_table(tabd32, b.tab_d32, (P.tab32.nA + P.tab32.nB) * kTabDens);
     load_table(et, b.exp32_table, kExp32TableSize);
@@ -1022,7 +1040,7 @@ __global__ void __launch_bounds__(kTabBlock) k_force32_tab(Bufs b, PotC P, GeoC 
     extern __shared__ float tabf32[];
     __shared__ int3 qt[125];
     __shared__ float et[kExp32TableSize];
-    if (b.st->done) return;
+    if (pass_skipped(b)) return;
     fill_qshift_table(qt, g);
     load_table(tabf32, b.tab_f32, (P.tab32.nA + P.tab32.nB) * kTabForce);
     load_table(et, b.exp32_table, kExp32TableSize);
@@ -1103,7 +1121,8 @@ __global__ void k_control(Bufs b, int mode, cudaGraphConditionalHandle h, int ha
     const double V2 = ctl_sum(b.rpart + 2 * b.nb_red, b.nb_red, sh);
     const double fa2 = ctl_max(b.rpart + 3 * b.nb_red, b.nb_red, sh);
     const double fin = ctl_max(b.rpart + 4 * b.nb_red, b.nb_red, sh);
-    const double E = ctl_sum(b.epart, b.nb_force + b.nb_embed, sh);
+    const int ne = b.st->vstate == 2 ? b.nb_verify : b.nb_force + b.nb_embed;
+    const double E = ctl_sum(b.epart, ne, sh);
     if (threadIdx.x != 0) return;
     DevState& s = *b.st;
     s.P = P;
@@ -1130,8 +1149,29 @@ __global__ void k_control(Bufs b, int mode, cudaGraphConditionalHandle h, int ha
         s.fs.evals += 1;
         s.status = ST_TIMEOUT;
         stop = true;
+    } else if (s.vstate == 2) {
+        // this evaluation used FP64 forces at the configuration where the
+        // FP32-pair forces met the threshold
+        const double fn = force_norm(s.prm.norm, F2, fa2, fin);
+        if (fn < s.ftol_user) {
+            s.fs.evals += 1;
+            s.fs.stop = STOP_FTOL;
+            stop = true;
+        } else {
+            // not converged in FP64: tighten the FP32 threshold by the FP32 to
+            // FP64 difference seen here and take the step with these forces
+            s.prm.ftol = fmax(s.prm.ftol - 1.5 * (fn - s.fn32), 0.4 * s.ftol_user);
+            s.vstate = 1;
+            stop = fire_control_step(s.prm, s.fs, P, F2, V2, fa2, fin);
+        }
     } else {
         stop = fire_control_step(s.prm, s.fs, P, F2, V2, fa2, fin);
+        if (stop && s.vstate == 1 && s.fs.stop == STOP_FTOL && s.status == ST_OK) {
+            s.fn32 = force_norm(s.prm.norm, F2, fa2, fin);
+            s.vstate = 2;
+            s.vcount += 1;
+            stop = false;
+        }
     }
     s.done = stop ? 1 : 0;
     if (has_handle) cudaGraphSetConditional(h, stop ? 0u : 1u);
@@ -1146,7 +1186,9 @@ __global__ void k_control(Bufs b, int mode, cudaGraphConditionalHandle h, int ha
 __global__ void k_update(Bufs b, GeoC g, cudaGraphConditionalHandle hif, int has_if,
                          int after_pre) {
     __shared__ double red[32];
-    if (b.st->done) {
+    // no step when stopped, nor while an FP32-pair stop is confirmed in FP64
+    // (the next evaluation is at the same positions)
+    if (b.st->done || b.st->vstate == 2) {
         if (has_if && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(hif, 0u);
         return;
     }
@@ -1204,7 +1246,7 @@ __global__ void k_update(Bufs b, GeoC g, cudaGraphConditionalHandle hif, int has
 // with fire_capped_dt.
 __global__ void k_update_pre(Bufs b) {
     __shared__ double red[32];
-    if (b.st->done) return;
+    if (b.st->done || b.st->vstate == 2) return;   // no step while confirming
     const FireScal s = b.st->fs;
     double vm = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < b.n; i += gridDim.x * blockDim.x) {

@@ -370,25 +370,46 @@ def test_fp32pair_1m_sampled_forces_vs_oracle():
 
 
 def test_fp32pair_relaxation_reaches_fp64_converged_state():
+    # default: a stop on the FP32-pair forces is confirmed by one FP64
+    # evaluation at the same positions, so the result meets ftol in FP64
     c = fi.rgl_vacancy_box(ncell=20, seed=2)
     x64, x32 = c.x.copy(), c.x.copy()
     with fg.FireHandle(c.n, fi.CU_MASS, rgl_pot(), dt_start=fi.CU_DT) as h64, \
             fg.FireHandle(c.n, fi.CU_MASS, rgl_pot(precision=fg.FIRE_PREC_FP32_PAIR),
                           dt_start=fi.CU_DT) as h32:
         r64 = h64.minimize(x64, c.box, 1e-6, 100000)
-        # stop the FP32-pair form at ftol less its force error at relaxed
-        # structures (<= 5.6e-7 eV/A measured, margin 6e-7)
-        r32 = h32.minimize(x32, c.box, 1e-6 - F32_MARGIN, 100000)
+        r32 = h32.minimize(x32, c.box, 1e-6, 100000)
         # the FP32 solution judged by FP64 forces
         e_chk, f_chk = h64.energy_forces(x32, c.box)
         _, f32_at32 = h32.energy_forces(x32, c.box)
     fmax64_at32 = np.sqrt((f_chk ** 2).sum(1)).max()
-    assert np.sqrt(((f32_at32 - f_chk) ** 2).sum(1)).max() < F32_MARGIN
-    print(f"iterations FP64 {r64.iterations}, FP32-pair {r32.iterations}; FP64 max|F| at the "
-          f"FP32-pair minimum {fmax64_at32:.3e}; dE/N {abs(e_chk - r64.energy) / c.n:.3e}")
-    assert r32.stop == fg.FIRE_STOP_FTOL and r32.fmax_atom < 1e-6 - F32_MARGIN
+    confirmations = r32.force_evals - r32.iterations - 1
+    print(f"iterations FP64 {r64.iterations}, FP32-pair {r32.iterations} "
+          f"({confirmations} FP64 confirmations); FP64 max|F| at the FP32-pair minimum "
+          f"{fmax64_at32:.3e}; dE/N {abs(e_chk - r64.energy) / c.n:.3e}")
+    assert r32.stop == fg.FIRE_STOP_FTOL and confirmations >= 1
+    # the reported norm and energy are those of the confirming FP64 evaluation
+    assert abs(r32.fmax_atom - fmax64_at32) < 1e-12 and r32.fmax_atom < 1e-6
+    assert r32.energy == pytest.approx(e_chk, rel=1e-13)
     assert fmax64_at32 < 1e-6
     assert abs(e_chk - r64.energy) / c.n < 1e-8
+    # FP32-pair force error at the relaxed structure
+    assert np.sqrt(((f32_at32 - f_chk) ** 2).sum(1)).max() < F32_MARGIN
+
+
+def test_fp32pair_without_confirmation_stops_on_fp32_forces():
+    # confirm64 = 0: stop on the FP32-pair forces alone; at ftol less their
+    # error bound the structure still meets ftol in FP64
+    c = fi.rgl_vacancy_box(ncell=8, seed=15, n_vac=3)
+    x = c.x.copy()
+    with fg.FireHandle(c.n, fi.CU_MASS, rgl_pot(), dt_start=fi.CU_DT) as h64, \
+            fg.FireHandle(c.n, fi.CU_MASS, rgl_pot(precision=fg.FIRE_PREC_FP32_PAIR),
+                          dt_start=fi.CU_DT, confirm64=0) as h32:
+        r = h32.minimize(x, c.box, 1e-6 - F32_MARGIN, 100000)
+        _, f_chk = h64.energy_forces(x, c.box)
+    assert r.stop == fg.FIRE_STOP_FTOL and r.force_evals == r.iterations + 1
+    assert r.fmax_atom < 1e-6 - F32_MARGIN
+    assert np.sqrt((f_chk ** 2).sum(1)).max() < 1e-6
 
 
 # ----------------------------------------------------------------------------
