@@ -173,8 +173,9 @@ typedef struct {
                                    ftol too; otherwise it tightens its FP32 threshold
                                    by the FP32-FP64 difference seen there and goes on.
                                    Each confirmation is one force evaluation that is not
-                                   an iteration.  0: stop on the FP32-pair forces.
-                                   Other forms ignore it. */
+                                   an iteration.  The batched form confirms per system.
+                                   0: stop on the FP32-pair forces.  Other forms
+                                   ignore it. */
     double dmax;                /* maximum displacement of any atom per step (the
                                    paper's dmax, Sec. 4 cases 1 and 7), 0 = no cap
                                    (default 0): the drift x += dt v uses

@@ -854,8 +854,9 @@ static fire_status init_handle(fire_handle_t** hp, const fire_system_t* sys,
         CKI(cudaMemcpy(t, exp32_table_host, kExp32TableSize * sizeof(float), cudaMemcpyHostToDevice));
     }
     if (!single) {
-        // the batched FP64 form reads the same double-float pair tables
-        if (fixed64_form(*pot)) {
+        // the batched FP64 form, and the FP32-pair form confirming its stops,
+        // read the same double-float pair tables
+        if (fixed64_form(*pot) || (fp32pair && pot->kind == FIRE_POT_RGL && params->confirm64 != 0)) {
             const fire_status ts = upload_tables(h);
             if (ts != FIRE_OK) return bail(ts);
         }

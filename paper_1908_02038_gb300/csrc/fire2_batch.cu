@@ -64,7 +64,9 @@ struct BArgs {
     lvec4* xq64;            // FP64 table form: positions in 2^-44 A units
     float2* fpff;           // FP64 table form: F'(rho) as a float pair
     const float *tab_ffd, *tab_fff;   // FP64 table form: density / force rows
-    int ff;                 // 1: FP64 table form (double-float pair terms)
+    int ff;                 // 1: FP64 table passes available (FP64 table form, or the
+                            //    FP32-pair form confirming its stops)
+    int confirm;            // FP32-pair form: confirm stops on ftol in FP64
     double* fp64;           // F'(rho) (FP64 form)
     float* fp32;            // F'(rho) (FP32-pair form)
     uint32_t* nbr;
@@ -86,6 +88,10 @@ struct BShared {            // per-CTA scalars
     int sys, done, status, rebuild;
     long long builds;
     double P, F2, V2, fa2, fin, E, dmax;
+    // FP64 confirmation of FP32-pair stops (as fire2_device.cuh's DevState):
+    // vstate 0 off, 1 FP32 phase, 2 the next evaluation confirms in FP64
+    int vstate;
+    double ftol_work, fn32;
 };
 
 // Block reductions into shared scalars (all threads must call).
@@ -506,11 +512,41 @@ __device__ __noinline__ void b_reduce_control(const BArgs& a, const BInst& I, in
             sh.status = ST_TIMEOUT;
             stop = true;
         } else {
-            stop = fire_control_step(a.prm, sh.fs, sh.P, sh.F2, sh.V2, sh.fa2, sh.fin);
+            FireParamsD p = a.prm;
+            p.ftol = sh.ftol_work;
+            if (sh.vstate == 2) {   // these forces confirm an FP32-pair stop in FP64
+                const double fn = force_norm(p.norm, sh.F2, sh.fa2, sh.fin);
+                if (fn < a.prm.ftol) {
+                    sh.fs.evals += 1;
+                    sh.fs.stop = STOP_FTOL;
+                    stop = true;
+                } else {   // tighten the FP32 threshold, step with these forces
+                    sh.ftol_work = fmax(sh.ftol_work - 1.5 * (fn - sh.fn32), 0.4 * a.prm.ftol);
+                    p.ftol = sh.ftol_work;
+                    sh.vstate = 1;
+                    stop = fire_control_step(p, sh.fs, sh.P, sh.F2, sh.V2, sh.fa2, sh.fin);
+                }
+            } else {
+                stop = fire_control_step(p, sh.fs, sh.P, sh.F2, sh.V2, sh.fa2, sh.fin);
+                if (stop && sh.vstate == 1 && sh.fs.stop == STOP_FTOL) {
+                    sh.fn32 = force_norm(p.norm, sh.F2, sh.fa2, sh.fin);
+                    sh.vstate = 2;
+                    stop = false;
+                }
+            }
         }
         sh.done = stop ? 1 : 0;
     }
     __syncthreads();
+}
+
+// The FP64 table passes of one system, out of line so that the FP32-pair
+// kernel that calls them to confirm a stop keeps its own register budget.
+template <bool CL>
+__device__ __noinline__ double b_forces_confirm(const BArgs& a, const BInst& I, int lo, int hi,
+                                                const double* etab, const float* et32,
+                                                double* red) {
+    return b_forces<false, CL>(a, I, lo, hi, etab, et32, red);
 }
 
 // The batched relaxation.  CL = false: one CTA per system.  CL = true: the
@@ -586,6 +622,8 @@ __global__ void __launch_bounds__(MAXT, 1) k_batch_relax(BArgs a) {
         const double anybad = bmax((double)bad, red);
         if (threadIdx.x == 0) {
             fire_scal_init(a.prm, sh.fs);
+            sh.vstate = (F32 && a.confirm) ? 1 : 0;
+            sh.ftol_work = a.prm.ftol;
             sh.status = anybad > 0.0 ? ST_NONFINITE : ST_OK;
             sh.builds = 0;
             sh.done = 0;
@@ -600,6 +638,20 @@ __global__ void __launch_bounds__(MAXT, 1) k_batch_relax(BArgs a) {
         double E = b_forces<F32, CL>(a, I, lo, hi, etab, et32, red);
         b_reduce_control<CL>(a, I, lo, hi, sh, X, E, red, t0);
         while (!sh.done) {
+            if (F32 && sh.vstate == 2) {
+                // confirm the FP32-pair stop: FP64 forces at the same positions
+                for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+                    const dvec4 x = a.x[I.off + i];
+                    a.xq64[I.off + i] = {to_fixed64(x.x, kFixedBits64),
+                                         to_fixed64(x.y, kFixedBits64),
+                                         to_fixed64(x.z, kFixedBits64), 0ll};
+                }
+                if (CL) cg::this_cluster().sync();
+                else __syncthreads();
+                E = b_forces_confirm<CL>(a, I, lo, hi, etab, et32, red);
+                b_reduce_control<CL>(a, I, lo, hi, sh, X, E, red, t0);
+                continue;
+            }
             const FireScal fs = sh.fs;
             // maximum displacement per step: the drift waits for max_i |v_i|
             double dt_drift = fs.dt_cur;
@@ -845,7 +897,9 @@ FIRE2_HIDDEN fire_status fire2_batch_create(fire_handle_t* h, int32_t n_sys,
     } else {
         BA(a.fp64, n * sizeof(double));
     }
-    a.ff = fire2_tab_ffd(h) != nullptr && !f32 ? 1 : 0;
+    a.confirm = f32 && fire2_params(h).confirm64 != 0 ? 1 : 0;
+    a.ff = fire2_tab_ffd(h) != nullptr && (!f32 || a.confirm) ? 1 : 0;
+    if (a.ff && f32) BA(a.fp64, n * sizeof(double));
     if (a.ff) {
         BA(a.xq64, n * sizeof(lvec4));
         BA(a.fpff, n * sizeof(float2));
