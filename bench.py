@@ -261,20 +261,25 @@ class _NoClock:
         return None
 
 
-def launches_of(results, is_rgl, fp32, cell_mode):
+def launches_of(results, is_rgl, fp32, cell_mode, chunked=False):
     """Kernels one relaxation launches: prepare, list build, forces, reduce,
     control, finalize once; per loop pass update, forces, reduce, control;
     the build chain (binning + list) once per rebuild.  The FP32-pair form
-    also launches the two FP64 confirming passes with every evaluation (they
-    return at once unless a stop is being confirmed), and each confirmation
-    is one more loop pass (force evaluations - iterations - 1)."""
+    also has the two FP64 confirming passes: launched once in the set-up,
+    then in the graph loop only in the passes that confirm a stop (an IF
+    node), in the chunked loop with every pass (they return at once unless
+    a stop is being confirmed).  Each confirmation is one more loop pass
+    (force evaluations - iterations - 1)."""
     build_k = 6 if cell_mode else 1
-    force_k = (2 + 2 if fp32 else 3) if is_rgl else 1
+    force_k = (2 if fp32 else 3) if is_rgl else 1
     total = 0
     for rr in results:
-        passes = rr["iterations"] + max(0, rr["force_evals"] - rr["iterations"] - 1)
-        total += (1 + build_k + force_k + 1 + 1 + 1)
+        conf = max(0, rr["force_evals"] - rr["iterations"] - 1) if fp32 else 0
+        passes = rr["iterations"] + conf
+        total += (1 + build_k + force_k + 1 + 1 + 1) + (2 if fp32 else 0)
         total += (1 + force_k + 1 + 1) * passes
+        if fp32:
+            total += 2 * (passes if chunked else conf)
         total += build_k * max(0, rr["nbr_builds"] - 1)
     return total
 
@@ -577,7 +582,7 @@ def run_gpu(args):
                       "final_energy_per_atom": [rr["energy"] / n for rr in results],
                       "nbr_builds": [rr["nbr_builds"] for rr in results],
                       "l2": "inputs larger than L2 (working set > 1 GB at 1M atoms)"},
-           "gpu_launches": launches_of(results, is_rgl, fp32, cell_mode),
+           "gpu_launches": launches_of(results, is_rgl, fp32, cell_mode, args.exec == "chunked"),
            "clocks": m["clocks"]}
 
     # per-stage device times (CUDA events) for the roofline of the dominant kernel

@@ -261,7 +261,19 @@ void launch_build(fire_handle* h, const GeoC& g, int force, cudaStream_t s) {
     k_nbr_build<<<ceil_div(n, kForceBlock), kForceBlock, 0, s>>>(h->b, g, force);
 }
 
-void launch_forces(fire_handle* h, const GeoC& g, cudaStream_t s) {
+// FP32-pair handles that confirm their stops: the FP64 passes on the same
+// full list (they return at once unless a stop is being confirmed).
+void launch_confirm(fire_handle* h, const GeoC& g, cudaStream_t s) {
+    Bufs bv = h->b;
+    bv.pass_role = 2;
+    k_density_ff<false><<<h->b.nb_verify, kForceBlock, 0, s>>>(bv, h->potc, g);
+    k_force_ff<false><<<h->b.nb_verify, kForceBlock, 0, s>>>(bv, h->potc, g);
+}
+
+// The force passes of one evaluation; with confirm_passes, also the FP64
+// confirming passes of FP32-pair handles (the graph loop puts those under
+// an IF node instead).
+void launch_forces(fire_handle* h, const GeoC& g, cudaStream_t s, bool confirm_passes = true) {
     const int n = h->n;
     const bool tab = h->pot.kind == FIRE_POT_RGL && h->pot.pair_eval == FIRE_PAIR_TABLE;
     if (tab && h->pot.precision == FIRE_PREC_FP32_PAIR) {
@@ -286,12 +298,7 @@ void launch_forces(fire_handle* h, const GeoC& g, cudaStream_t s) {
     } else {
         k_force_lj<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
     }
-    if (h->verify) {   // FP64 passes on the same full list; they run only to confirm a stop
-        Bufs bv = h->b;
-        bv.pass_role = 2;
-        k_density_ff<false><<<h->b.nb_verify, kForceBlock, 0, s>>>(bv, h->potc, g);
-        k_force_ff<false><<<h->b.nb_verify, kForceBlock, 0, s>>>(bv, h->potc, g);
-    }
+    if (h->verify && confirm_passes) launch_confirm(h, g, s);
     (void)n;
 }
 
@@ -330,10 +337,11 @@ int update_grid(int n) { return std::max(1, std::min(ceil_div(n, kElemBlock), 15
 
 // The element-wise step; with dmax > 0 in two passes (see k_update_pre).
 void launch_update(fire_handle* h, const GeoC& g, cudaStream_t s, cudaGraphConditionalHandle hif,
-                   int has_if) {
+                   int has_if, cudaGraphConditionalHandle hconf = {}, int has_conf = 0) {
     const bool capped = h->par.dmax > 0.0;
     if (capped) k_update_pre<<<update_grid(h->n), kElemBlock, 0, s>>>(h->b);
-    k_update<<<update_grid(h->n), kElemBlock, 0, s>>>(h->b, g, hif, has_if, capped ? 1 : 0);
+    k_update<<<update_grid(h->n), kElemBlock, 0, s>>>(h->b, g, hif, has_if, capped ? 1 : 0,
+                                                      hconf, has_conf);
 }
 
 // Appends a conditional node (WHILE or IF, one body) at the capture position
@@ -394,13 +402,15 @@ fire_status build_graph(fire_handle* h, const GeoC& g) {
     cudaGraph_t body = nullptr;
     e = add_conditional(h->cap0, hw, cudaGraphCondTypeWhile, &body);
     if (e == cudaSuccess) {
-        cudaGraphConditionalHandle hif;
+        cudaGraphConditionalHandle hif, hconf{};
         e = cudaGraphConditionalHandleCreate(&hif, body, 0, cudaGraphCondAssignDefault);
+        if (e == cudaSuccess && h->verify)
+            e = cudaGraphConditionalHandleCreate(&hconf, body, 0, cudaGraphCondAssignDefault);
         if (e == cudaSuccess)
             e = cudaStreamBeginCaptureToGraph(h->cap1, body, nullptr, nullptr, 0,
                                               cudaStreamCaptureModeRelaxed);
         if (e == cudaSuccess) {
-            launch_update(h, g, h->cap1, hif, 1);
+            launch_update(h, g, h->cap1, hif, 1, hconf, h->verify ? 1 : 0);
             cudaGraph_t build_body = nullptr;
             e = add_conditional(h->cap1, hif, cudaGraphCondTypeIf, &build_body);
             if (e == cudaSuccess)
@@ -411,7 +421,19 @@ fire_status build_graph(fire_handle* h, const GeoC& g) {
                 cudaGraph_t bb_out = nullptr;
                 e = cudaStreamEndCapture(h->cap2, &bb_out);
             }
-            launch_forces(h, g, h->cap1);
+            launch_forces(h, g, h->cap1, false);
+            if (e == cudaSuccess && h->verify) {   // the confirming passes, only when due
+                cudaGraph_t conf_body = nullptr;
+                e = add_conditional(h->cap1, hconf, cudaGraphCondTypeIf, &conf_body);
+                if (e == cudaSuccess)
+                    e = cudaStreamBeginCaptureToGraph(h->cap2, conf_body, nullptr, nullptr, 0,
+                                                      cudaStreamCaptureModeRelaxed);
+                if (e == cudaSuccess) {
+                    launch_confirm(h, g, h->cap2);
+                    cudaGraph_t cb_out = nullptr;
+                    e = cudaStreamEndCapture(h->cap2, &cb_out);
+                }
+            }
             launch_reduce(h, g, h->cap1);
             k_control<<<1, kCtlThreads, 0, h->cap1>>>(h->b, CTL_LOOP, hw, 1);
             cudaGraph_t body_out = nullptr;

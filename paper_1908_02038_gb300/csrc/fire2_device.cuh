@@ -1184,8 +1184,12 @@ __global__ void k_control(Bufs b, int mode, cudaGraphConditionalHandle h, int ha
 // max |x - x_ref|^2.  With has_if, the last block to finish sets the graph's
 // IF condition to "the neighbour list must be rebuilt" (see need_rebuild).
 __global__ void k_update(Bufs b, GeoC g, cudaGraphConditionalHandle hif, int has_if,
-                         int after_pre) {
+                         int after_pre, cudaGraphConditionalHandle hconf, int has_conf) {
     __shared__ double red[32];
+    // graph loop: the IF node of the FP64 confirming passes runs this pass
+    // only when an FP32-pair stop is being confirmed
+    if (has_conf && blockIdx.x == 0 && threadIdx.x == 0)
+        cudaGraphSetConditional(hconf, b.st->vstate == 2 ? 1u : 0u);
     // no step when stopped, nor while an FP32-pair stop is confirmed in FP64
     // (the next evaluation is at the same positions)
     if (b.st->done || b.st->vstate == 2) {
