@@ -507,6 +507,24 @@ def test_sw_diamond_cohesive_energy_closed_form(ncell):
     assert np.abs(f).max() < 1e-12
 
 
+@pytest.mark.parametrize("n,nz", [(3, 3), (4, 2)])
+def test_sw_diamond_slab_open_axis_closed_form(n, nz):
+    # A perfect diamond slab, periodic in x and y, open in z (the structure
+    # of the paper's silicon vacancy case without the vacancies): every bond
+    # still sits at the pair minimum with tetrahedral angles, so E = -eps per
+    # bond and F = 0; the two outer (001) layers (2 n^2 atoms each) have two
+    # bonds less per atom: bonds = (4 N - 2 (4 n^2)) / 2 = 16 n^2 nz - 4 n^2.
+    c = fi.sw_si_slab(ncell=n, nz=nz, n_vac=0, sigma=0.0)
+    assert c.n == 8 * n * n * nz
+    e, f = oracle.energy_forces(c.x, c.box, sw(), periodic=c.periodic)
+    bonds = 16 * n * n * nz - 4 * n * n
+    assert e == pytest.approx(-bonds * fi.SW_SI["eps"], rel=1e-9)
+    assert np.abs(f).max() < 1e-8
+    # the same atoms periodic in z are the bulk: -2 eps per atom
+    e_bulk, _ = oracle.energy_forces(c.x, [n * fi.SI_A, n * fi.SI_A, nz * fi.SI_A], sw())
+    assert e_bulk / c.n == pytest.approx(-2.0 * fi.SW_SI["eps"], rel=1e-9)
+
+
 def test_sw_dimer_minimum_and_trimer_angle_shape():
     box = [100.0] * 3
     r = 2.0 ** (1.0 / 6.0) * fi.SW_SI["sigma"]
