@@ -456,6 +456,59 @@ def batch_compare(fg, torch, dev, cfgs, x, x_fin, boxes, counts):
                                                   "one fire_minimize each", "converged": conv1}}
 
 
+def grad_block(fg, torch, dev):
+    """The differentiable form on its workload, the 20^3-cell Cu box with one
+    vacancy (31,999 atoms): the structure relaxed to max|F_i| < 1e-10 eV/A,
+    then the hand-written backward (E, F and dE/dtheta in one call), the
+    Hessian-vector product, and the implicit gradient dL/dtheta of the
+    vacancy loss (sum over the atoms whose lattice site lies within 6 A of
+    the vacancy of |x - x_lattice|^2) by CG to a relative residual 1e-10;
+    milliseconds per call (the calls synchronise their stream; CUDA events
+    around them)."""
+    c = fi.rgl_vacancy_box(ncell=20, seed=5, n_vac=1)
+    theta = [fi.RGL_CU[k] for k in ("A", "xi", "p", "q")]
+    pot = fg.Potential(fg.FIRE_POT_RGL, skin=0.3, **fi.RGL_CU)
+    x = torch.tensor(c.x, dtype=torch.float64, device=dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        ev0.record()
+        for _ in range(reps):
+            out = fn()
+        ev1.record()
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1) / reps, out
+
+    with fg.FireHandle(c.n, fi.CU_MASS, pot, dt_start=fi.CU_DT) as h:
+        r = h.minimize_dev(x, c.box, 1e-10, 400000)
+        f = torch.empty_like(x)
+        ms_eg, (e, de) = timed(lambda: fg.fire_rgl_energy_grad_dev(h.h, x, c.box, theta, f), 10)
+        u = torch.randn(x.shape, dtype=torch.float64, device=dev,
+                        generator=torch.Generator(device=dev).manual_seed(7))
+        hu = torch.empty_like(x)
+        ms_hvp, _ = timed(lambda: fg.fire_rgl_hvp_dev(h.h, x, c.box, theta, u, hu), 20)
+        site = c.meta["vacancy_sites"][0]
+        d = c.meta["lattice"] - site
+        d -= c.box * np.rint(d / c.box)
+        sel = np.flatnonzero(np.sum(d * d, 1) < 36.0)
+        dd = x.cpu().numpy()[sel] - c.meta["lattice"][sel]
+        dd -= c.box * np.rint(dd / c.box)
+        g = np.zeros((c.n, 3))
+        g[sel] = 2.0 * dd
+        gd = torch.tensor(g, dtype=torch.float64, device=dev)
+        ms_ig, (dl, cg_it) = timed(
+            lambda: fg.fire_rgl_implicit_grad_dev(h.h, x, c.box, theta, gd, 1e-10), 3)
+    return {"workload": f"Cu 20^3 cells, 1 vacancy ({c.n} atoms), FP64, relaxed to "
+                        f"max|F_i| < 1e-10 eV/A ({r.iterations} iterations)",
+            "energy_grad_ms": ms_eg, "hvp_ms": ms_hvp,
+            "hvp_atoms_per_s": c.n / (ms_hvp * 1e-3),
+            "implicit_grad_ms": ms_ig, "cg_iterations": cg_it,
+            "dL_dtheta": {k: float(v) for k, v in zip(("A", "xi", "p", "q"), dl)},
+            "dE_dtheta": {k: float(v) for k, v in zip(("A", "xi", "p", "q"), de)}}
+
+
 INTEGRATORS = {"semi_implicit_euler": 0, "explicit_euler": 1, "velocity_verlet": 2, "leapfrog": 3}
 
 
@@ -672,6 +725,7 @@ def run_gpu(args):
         out["neb"] = neb_block(fg, torch, args.form, dev)
         out["sw"] = sw_block(fg, torch, dev)
         out["batched"] = batch_block(fg, torch, dev)
+        out["grad"] = grad_block(fg, torch, dev)
     if rank == 0:
         if world == 1 and not args.no_cpu:
             out["cpu_baseline"] = cpu_baseline(cfg, args)
