@@ -34,6 +34,8 @@ struct GradState {
     double *rho = nullptr, *F1 = nullptr, *F2 = nullptr, *drho = nullptr, *dq = nullptr;
     double* part = nullptr;        // 9 x nb block partials
     double* vec = nullptr;         // 4 work vectors of 3N (r, p, Ap, lambda)
+    double* pcache = nullptr;      // HVP pair coefficients, 3 x cap x N (implicit gradient)
+    size_t pcache_slots = 0;
     double* h_part = nullptr;      // pinned copy of part
     DevState* st = nullptr;        // status word of the list build
 };
@@ -1003,7 +1005,7 @@ void fire_destroy(fire_handle_t* h) {
     {
         GradState& gs = h->grad;
         void* gp[] = {gs.x, gs.xref, gs.xf, gs.nbr, gs.nnbr, gs.rho, gs.F1, gs.F2, gs.drho,
-                      gs.dq, gs.part, gs.vec, gs.st};
+                      gs.dq, gs.part, gs.vec, gs.pcache, gs.st};
         for (void* p : gp)
             if (p) cudaFree(p);
         if (gs.h_part) cudaFreeHost(gs.h_part);
@@ -1396,6 +1398,11 @@ fire_status fire_rgl_energy_grad_dev(fire_handle_t* h, const double* d_pos, cons
 static void launch_hvp(fire_handle* h, const GradBufs& b, const PotC& pc, const double box[3],
                        const double* u, double* hu, cudaStream_t s) {
     GeoL L{{box[0], box[1], box[2]}};
+    if (b.w1) {   // pair coefficients cached for this solve
+        k_g_hvp1c<<<h->grad.nb, kForceBlock, 0, s>>>(b, L, u);
+        k_g_hvp2c<<<h->grad.nb, kForceBlock, 0, s>>>(b, L, u, hu);
+        return;
+    }
     k_g_hvp1<<<h->grad.nb, kForceBlock, 0, s>>>(b, pc, L, h->b.exp_table, u);
     k_g_hvp2<<<h->grad.nb, kForceBlock, 0, s>>>(b, pc, L, h->b.exp_table, u, hu);
 }
@@ -1466,6 +1473,28 @@ fire_status fire_rgl_implicit_grad_dev(fire_handle_t* h, const double* d_pos, co
     fire_status st = grad_setup(h, d_pos, box, theta, s, &g, &pc, &b);
     if (st != FIRE_OK) return st;
     const int n = h->n, m = 3 * n;
+    // the positions are fixed for the whole solve: cache the pair
+    // coefficients of the HVP once (3 doubles per list slot)
+    {
+        GradState& gs = h->grad;
+        const size_t slots = (size_t)gs.cap * n;
+        if (slots > gs.pcache_slots) {
+            cudaFree(gs.pcache);
+            gs.pcache = nullptr;
+            gs.pcache_slots = 0;
+            CK(h, cudaMalloc(&gs.pcache, 3 * slots * sizeof(double)));
+            gs.pcache_slots = slots;
+        }
+        double* w1 = gs.pcache;
+        double* fsc = w1 + slots;
+        double* a2 = fsc + slots;
+        GeoL L{{box[0], box[1], box[2]}};
+        k_g_pair_cache<<<gs.nb, kForceBlock, 0, s>>>(b, pc, L, h->b.exp_table, w1, fsc, a2);
+        CK(h, cudaGetLastError());
+        b.w1 = w1;
+        b.fsc = fsc;
+        b.a2 = a2;
+    }
     const size_t bytes = (size_t)m * sizeof(double);
     double* r = h->grad.vec;
     double* p = r + m;

@@ -28,6 +28,9 @@ struct GradBufs {
     const int* nnbr;
     double *rho, *F1, *F2, *drho, *dq;
     double* part;          // block partials
+    // pair coefficients of the HVP at fixed positions (k_g_pair_cache), one
+    // per list slot [k * n + i]; NULL when not computed
+    const double *w1, *fsc, *a2;
 };
 
 struct Pair2 {
@@ -275,6 +278,109 @@ __global__ void __launch_bounds__(kForceBlock) k_g_hvp2(GradBufs g, PotC P, GeoL
         const double dr = (d[0] * du[0] + d[1] * du[1] + d[2] * du[2]) * q.rinv;
         const double dc = dci + g.F2[j] * g.drho[j];
         const double dfs = ((2.0 * q.d2phi + c * q.d2g) * q.rinv - fs * q.rinv) * dr + dc * q.dg * q.rinv;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) dF[a] += dfs * d[a] + fs * du[a];
+    }
+    double* h = hu + 3 * (size_t)i;
+    h[0] = -dF[0];
+    h[1] = -dF[1];
+    h[2] = -dF[2];
+}
+
+// Pair coefficients of the HVP at the current positions, for the many
+// products of one conjugate-gradient solve (the positions do not change):
+// per list slot w1 = g'/r, fs = [2 phi' + (F'_i + F'_j) g'] / r and
+// a2 = [2 phi'' + (F'_i + F'_j) g'' - fs] / r^2, zero beyond rc.  With them
+// dfs = a2 d.(u_j - u_i) + (F''_i drho_i + F''_j drho_j) w1 (HVP pass 2) and
+// drho_i = sum_j w1 d.(u_j - u_i) (pass 1) need no pair function.
+__global__ void __launch_bounds__(kForceBlock) k_g_pair_cache(GradBufs g, PotC P, GeoL L,
+                                                              const double* exp_table,
+                                                              double* w1, double* fsc,
+                                                              double* a2) {
+    __shared__ double3 tbl[125];
+    __shared__ double etab[kExpTableSize];
+    grad_tables(tbl, etab, exp_table, L.L);
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.n) return;
+    const dvec4 xi = g.x[i];
+    const double f1i = g.F1[i];
+    const int m = g.nnbr[i];
+    for (int k = 0; k < m; ++k) {
+        const size_t slot = (size_t)k * g.n + i;
+        int j;
+        double dx, dy, dz;
+        const double r2 = grad_pair_vec(g, tbl, xi, g.nbr[slot], j, dx, dy, dz);
+        if (!(r2 < P.rc2)) {
+            w1[slot] = 0.0;
+            fsc[slot] = 0.0;
+            a2[slot] = 0.0;
+            continue;
+        }
+        Pair2 q;
+        rgl_pair_d2(P, r2, etab, q);
+        const double c = f1i + g.F1[j];
+        const double fs = (2.0 * q.dphi + c * q.dg) * q.rinv;
+        w1[slot] = q.dg * q.rinv;
+        fsc[slot] = fs;
+        a2[slot] = (2.0 * q.d2phi + c * q.d2g - fs) * q.rinv * q.rinv;
+    }
+}
+
+// HVP pass 1 from the pair cache.
+__global__ void __launch_bounds__(kForceBlock) k_g_hvp1c(GradBufs g, GeoL L, const double* u) {
+    __shared__ double3 tbl[125];
+    for (int t = threadIdx.x; t < 125; t += blockDim.x) {
+        const int sx = t % 5 - 2, sy = (t / 5) % 5 - 2, sz = t / 25 - 2;
+        tbl[t] = make_double3(sx * L.L[0], sy * L.L[1], sz * L.L[2]);
+    }
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.n) return;
+    const dvec4 xi = g.x[i];
+    const double* ui = u + 3 * (size_t)i;
+    double acc = 0.0;
+    const int m = g.nnbr[i];
+    for (int k = 0; k < m; ++k) {
+        const size_t slot = (size_t)k * g.n + i;
+        const double w = g.w1[slot];
+        if (w == 0.0) continue;
+        int j;
+        double dx, dy, dz;
+        grad_pair_vec(g, tbl, xi, g.nbr[slot], j, dx, dy, dz);
+        const double* uj = u + 3 * (size_t)j;
+        acc += w * (dx * (uj[0] - ui[0]) + dy * (uj[1] - ui[1]) + dz * (uj[2] - ui[2]));
+    }
+    g.drho[i] = acc;
+}
+
+// HVP pass 2 from the pair cache: (H u)_i = -dF_i.
+__global__ void __launch_bounds__(kForceBlock) k_g_hvp2c(GradBufs g, GeoL L, const double* u,
+                                                         double* hu) {
+    __shared__ double3 tbl[125];
+    for (int t = threadIdx.x; t < 125; t += blockDim.x) {
+        const int sx = t % 5 - 2, sy = (t / 5) % 5 - 2, sz = t / 25 - 2;
+        tbl[t] = make_double3(sx * L.L[0], sy * L.L[1], sz * L.L[2]);
+    }
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.n) return;
+    const dvec4 xi = g.x[i];
+    const double* ui = u + 3 * (size_t)i;
+    const double dci = g.F2[i] * g.drho[i];
+    double dF[3] = {0, 0, 0};
+    const int m = g.nnbr[i];
+    for (int k = 0; k < m; ++k) {
+        const size_t slot = (size_t)k * g.n + i;
+        const double fs = g.fsc[slot];
+        if (fs == 0.0 && g.w1[slot] == 0.0) continue;
+        int j;
+        double d[3];
+        grad_pair_vec(g, tbl, xi, g.nbr[slot], j, d[0], d[1], d[2]);
+        const double* uj = u + 3 * (size_t)j;
+        const double du[3] = {uj[0] - ui[0], uj[1] - ui[1], uj[2] - ui[2]};
+        const double dd = d[0] * du[0] + d[1] * du[1] + d[2] * du[2];
+        const double dfs = g.a2[slot] * dd + (dci + g.F2[j] * g.drho[j]) * g.w1[slot];
 #pragma unroll
         for (int a = 0; a < 3; ++a) dF[a] += dfs * d[a] + fs * du[a];
     }
