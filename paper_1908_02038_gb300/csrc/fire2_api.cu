@@ -36,6 +36,8 @@ struct GradState {
     double* vec = nullptr;         // 4 work vectors of 3N (r, p, Ap, lambda)
     double* pcache = nullptr;      // HVP pair coefficients, 3 x cap x N (implicit gradient)
     size_t pcache_slots = 0;
+    CgState* cs = nullptr;         // device scalars of the CG solve
+    CgState* h_cs = nullptr;       // pinned copy
     double* h_part = nullptr;      // pinned copy of part
     DevState* st = nullptr;        // status word of the list build
 };
@@ -1005,10 +1007,11 @@ void fire_destroy(fire_handle_t* h) {
     {
         GradState& gs = h->grad;
         void* gp[] = {gs.x, gs.xref, gs.xf, gs.nbr, gs.nnbr, gs.rho, gs.F1, gs.F2, gs.drho,
-                      gs.dq, gs.part, gs.vec, gs.pcache, gs.st};
+                      gs.dq, gs.part, gs.vec, gs.pcache, gs.cs, gs.st};
         for (void* p : gp)
             if (p) cudaFree(p);
         if (gs.h_part) cudaFreeHost(gs.h_part);
+        if (gs.h_cs) cudaFreeHost(gs.h_cs);
     }
     if (h->h_state) cudaFreeHost(h->h_state);
     if (h->h_pos) cudaFreeHost(h->h_pos);
@@ -1399,8 +1402,8 @@ static void launch_hvp(fire_handle* h, const GradBufs& b, const PotC& pc, const 
                        const double* u, double* hu, cudaStream_t s) {
     GeoL L{{box[0], box[1], box[2]}};
     if (b.w1) {   // pair coefficients cached for this solve
-        k_g_hvp1c<<<h->grad.nb, kForceBlock, 0, s>>>(b, L, u);
-        k_g_hvp2c<<<h->grad.nb, kForceBlock, 0, s>>>(b, L, u, hu);
+        k_g_hvp1c<<<h->grad.nb, kForceBlock, 0, s>>>(b, L, u, nullptr);
+        k_g_hvp2c<<<h->grad.nb, kForceBlock, 0, s>>>(b, L, u, hu, nullptr);
         return;
     }
     k_g_hvp1<<<h->grad.nb, kForceBlock, 0, s>>>(b, pc, L, h->b.exp_table, u);
@@ -1507,25 +1510,43 @@ fire_status fire_rgl_implicit_grad_dev(fire_handle_t* h, const double* d_pos, co
     CK(h, cudaMemcpyAsync(p, r, bytes, cudaMemcpyDeviceToDevice, s));
     double rr = 0.0;
     if ((st = dev_dot(h, r, r, &rr, s)) != FIRE_OK) return st;
-    const double stop2 = tol * tol * rr;
-    int64_t it = 0;
-    while (it < maxit && rr > stop2 && rr > 0.0) {
-        launch_hvp(h, b, pc, box, p, Ap, s);
-        CK(h, cudaGetLastError());
-        if ((st = project_out_translations(h, Ap, s)) != FIRE_OK) return st;
-        double pAp = 0.0;
-        if ((st = dev_dot(h, p, Ap, &pAp, s)) != FIRE_OK) return st;
-        if (!(pAp > 0.0)) break;   // not positive definite along p
-        const double alpha = rr / pAp;
-        k_g_cg_step<<<nb, kElemBlock, 0, s>>>(m, alpha, p, Ap, lam, r);
-        double rr_new = 0.0;
-        if ((st = dev_dot(h, r, r, &rr_new, s)) != FIRE_OK) return st;
-        k_g_cg_dir<<<nb, kElemBlock, 0, s>>>(m, rr_new / rr, r, p);
-        CK(h, cudaGetLastError());
-        rr = rr_new;
-        ++it;
+    // the iterations run on device scalars (CgState): the host queues
+    // kCgBatch of them at a time and reads the state once per batch; the
+    // kernels of iterations after the stop return at once
+    GradState& gs = h->grad;
+    if (!gs.cs) {
+        CK(h, cudaMalloc(&gs.cs, sizeof(CgState)));
+        CK(h, cudaMallocHost(&gs.h_cs, sizeof(CgState)));
     }
+    CgState c0{};
+    c0.rr = rr;
+    c0.stop2 = tol * tol * rr;
+    c0.maxit = maxit;
+    c0.done = (rr > c0.stop2 && rr > 0.0) ? 0 : 1;
+    *gs.h_cs = c0;
+    CK(h, cudaMemcpyAsync(gs.cs, gs.h_cs, sizeof(CgState), cudaMemcpyHostToDevice, s));
     GeoL L{{box[0], box[1], box[2]}};
+    const int* skip = &gs.cs->done;
+    constexpr int kCgBatch = 16;
+    int done = c0.done;
+    while (!done) {
+        for (int c = 0; c < kCgBatch; ++c) {
+            k_g_hvp1c<<<gs.nb, kForceBlock, 0, s>>>(b, L, p, skip);
+            k_g_hvp2c<<<gs.nb, kForceBlock, 0, s>>>(b, L, p, Ap, skip);
+            k_cg_colsum<<<nb, kElemBlock, 0, s>>>(n, gs.cs, Ap, gs.part);
+            k_cg_means<<<1, kElemBlock, 0, s>>>(gs.cs, gs.part, nb, n);
+            k_cg_project_dot<<<nb, kElemBlock, 0, s>>>(n, gs.cs, Ap, p, gs.part);
+            k_cg_alpha<<<1, kElemBlock, 0, s>>>(gs.cs, gs.part, nb);
+            k_cg_step<<<nb, kElemBlock, 0, s>>>(m, gs.cs, p, Ap, lam, r, gs.part);
+            k_cg_beta<<<1, kElemBlock, 0, s>>>(gs.cs, gs.part, nb);
+            k_cg_dir<<<nb, kElemBlock, 0, s>>>(m, gs.cs, r, p);
+        }
+        CK(h, cudaGetLastError());
+        CK(h, cudaMemcpyAsync(gs.h_cs, gs.cs, sizeof(CgState), cudaMemcpyDeviceToHost, s));
+        CK(h, cudaStreamSynchronize(s));
+        done = gs.h_cs->done;
+    }
+    const int64_t it = gs.h_cs->it;
     k_g_force<<<h->grad.nb, kForceBlock, 0, s>>>(b, pc, L, h->b.exp_table, nullptr, nullptr, lam);
     CK(h, cudaGetLastError());
     double sums[4];

@@ -328,8 +328,10 @@ __global__ void __launch_bounds__(kForceBlock) k_g_pair_cache(GradBufs g, PotC P
 }
 
 // HVP pass 1 from the pair cache.
-__global__ void __launch_bounds__(kForceBlock) k_g_hvp1c(GradBufs g, GeoL L, const double* u) {
+__global__ void __launch_bounds__(kForceBlock) k_g_hvp1c(GradBufs g, GeoL L, const double* u,
+                                                         const int* skip) {
     __shared__ double3 tbl[125];
+    if (skip && *skip) return;   // a finished conjugate-gradient solve
     for (int t = threadIdx.x; t < 125; t += blockDim.x) {
         const int sx = t % 5 - 2, sy = (t / 5) % 5 - 2, sz = t / 25 - 2;
         tbl[t] = make_double3(sx * L.L[0], sy * L.L[1], sz * L.L[2]);
@@ -356,8 +358,9 @@ __global__ void __launch_bounds__(kForceBlock) k_g_hvp1c(GradBufs g, GeoL L, con
 
 // HVP pass 2 from the pair cache: (H u)_i = -dF_i.
 __global__ void __launch_bounds__(kForceBlock) k_g_hvp2c(GradBufs g, GeoL L, const double* u,
-                                                         double* hu) {
+                                                         double* hu, const int* skip) {
     __shared__ double3 tbl[125];
+    if (skip && *skip) return;
     for (int t = threadIdx.x; t < 125; t += blockDim.x) {
         const int sx = t % 5 - 2, sy = (t / 5) % 5 - 2, sz = t / 25 - 2;
         tbl[t] = make_double3(sx * L.L[0], sy * L.L[1], sz * L.L[2]);
@@ -433,17 +436,115 @@ __global__ void k_g_sub_mean(int n, double* a, double m0, double m1, double m2) 
     }
 }
 
-// lam += alpha p; r -= alpha Ap
-__global__ void k_g_cg_step(int m, double alpha, const double* p, const double* Ap, double* lam,
-                            double* r) {
+// Scalars of the conjugate-gradient solve, kept on the device so that the
+// iterations run without a host round trip; every kernel of an iteration
+// returns at once when the solve is done (done = 1), so the host can queue
+// several iterations and look at the state once per batch.
+struct CgState {
+    double rr, stop2, alpha, beta, m[3];
+    long long it, maxit;
+    int done;
+};
+
+// Fixed-order sum of cnt partials by one block (result in thread 0).
+__device__ __forceinline__ double cg_sum(const double* a, int cnt, double* red) {
+    double s = 0.0;
+    for (int k = threadIdx.x; k < cnt; k += blockDim.x) s += a[k];
+    return block_sum(s, red);
+}
+
+// Column sums of Ap, as partials (k_g_colsum), unless the solve is done.
+__global__ void k_cg_colsum(int n, const CgState* cs, const double* a, double* part) {
+    __shared__ double red[32];
+    if (cs->done) return;
+    double c[3] = {0.0, 0.0, 0.0};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        c[0] += a[3 * (size_t)i];
+        c[1] += a[3 * (size_t)i + 1];
+        c[2] += a[3 * (size_t)i + 2];
+    }
+    for (int k = 0; k < 3; ++k) {
+        const double s = block_sum(c[k], red);
+        if (threadIdx.x == 0) part[k * gridDim.x + blockIdx.x] = s;
+    }
+}
+
+// One block: the mean of each Cartesian column of Ap (the translations that
+// are projected out, H being singular along them).
+__global__ void k_cg_means(CgState* cs, const double* part, int nb, int n) {
+    __shared__ double red[32];
+    if (cs->done) return;
+    for (int k = 0; k < 3; ++k) {
+        const double s = cg_sum(part + (size_t)k * nb, nb, red);
+        if (threadIdx.x == 0) cs->m[k] = s / n;
+    }
+}
+
+// Ap -= its column means; partials of p.Ap.
+__global__ void k_cg_project_dot(int n, const CgState* cs, double* ap, const double* p,
+                                 double* part) {
+    __shared__ double red[32];
+    if (cs->done) return;
+    const double m0 = cs->m[0], m1 = cs->m[1], m2 = cs->m[2];
+    double acc = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const size_t k = 3 * (size_t)i;
+        const double a0 = ap[k] - m0, a1 = ap[k + 1] - m1, a2 = ap[k + 2] - m2;
+        ap[k] = a0;
+        ap[k + 1] = a1;
+        ap[k + 2] = a2;
+        acc += p[k] * a0 + p[k + 1] * a1 + p[k + 2] * a2;
+    }
+    acc = block_sum(acc, red);
+    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+// One block: alpha = r.r / p.Ap; stops when H is not positive definite
+// along p.
+__global__ void k_cg_alpha(CgState* cs, const double* part, int nb) {
+    __shared__ double red[32];
+    if (cs->done) return;
+    const double pAp = cg_sum(part, nb, red);
+    if (threadIdx.x == 0) {
+        if (!(pAp > 0.0)) cs->done = 1;
+        else cs->alpha = cs->rr / pAp;
+    }
+}
+
+// lam += alpha p; r -= alpha Ap; partials of r.r.
+__global__ void k_cg_step(int m, const CgState* cs, const double* p, const double* Ap,
+                          double* lam, double* r, double* part) {
+    __shared__ double red[32];
+    if (cs->done) return;
+    const double alpha = cs->alpha;
+    double acc = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
         lam[i] += alpha * p[i];
-        r[i] -= alpha * Ap[i];
+        const double ri = r[i] - alpha * Ap[i];
+        r[i] = ri;
+        acc += ri * ri;
+    }
+    acc = block_sum(acc, red);
+    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+// One block: the new r.r, beta, the iteration count and the stopping test.
+__global__ void k_cg_beta(CgState* cs, const double* part, int nb) {
+    __shared__ double red[32];
+    if (cs->done) return;
+    const double rr = cg_sum(part, nb, red);
+    if (threadIdx.x == 0) {
+        cs->beta = rr / cs->rr;
+        cs->rr = rr;
+        cs->it += 1;
+        if (!(rr > cs->stop2) || cs->it >= cs->maxit) cs->done = 1;
     }
 }
 
 // p = r + beta p
-__global__ void k_g_cg_dir(int m, double beta, const double* r, double* p) {
+__global__ void k_cg_dir(int m, const CgState* cs, const double* r, double* p) {
+    if (cs->done) return;
+    const double beta = cs->beta;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x)
         p[i] = r[i] + beta * p[i];
 }
