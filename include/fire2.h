@@ -114,6 +114,27 @@ typedef enum {
                                     v(-dt/2) = -dt/2 F / m in place of v = 0 */
 } fire_integrator;
 
+/* How an FP32-pair relaxation reaches an FP64-checked ftol
+ * (fire_params_t.confirm64; the paper's stopping test at tight ftol is what
+ * FP32 pair terms cannot settle alone: their force error, ~5e-7 eV/A at
+ * relaxed Cu structures, is comparable to ftol = 1e-6).
+ * FIRE_FP64_CHECK_OFF: stop on the FP32-pair forces.
+ * FIRE_FP64_CHECK_CONFIRM: when the FP32-pair forces meet ftol, the same
+ *   configuration is evaluated once more in FP64 (double-float table terms,
+ *   full list) and the relaxation stops only if those forces meet ftol too;
+ *   otherwise it tightens its FP32 threshold by the FP32-FP64 difference seen
+ *   there and goes on.  Each confirmation is one force evaluation that is not
+ *   an iteration.  The batched form confirms per system.
+ * FIRE_FP64_CHECK_FINISH: FP32-pair forces while the force norm is at least
+ *   3 ftol, FP64 forces (double-float table terms, full list) from the first
+ *   evaluation below it to the end; a precision schedule (single-system
+ *   handles; the batched form confirms instead). */
+typedef enum {
+    FIRE_FP64_CHECK_OFF = 0,
+    FIRE_FP64_CHECK_CONFIRM = 1,
+    FIRE_FP64_CHECK_FINISH = 2
+} fire_fp64_check;
+
 /* Minimizer variant. */
 typedef enum {
     FIRE_VARIANT_FIRE2 = 0,      /* FIRE 2.0, Algorithm 2 (default) */
@@ -166,16 +187,8 @@ typedef struct {
     int32_t integrator;         /* fire_integrator                   (default 0) */
     int32_t norm;               /* fire_norm for the ftol test       (default 0) */
     int32_t variant;            /* fire_variant                      (default 0) */
-    int32_t confirm64;          /* FP32-pair form (default 1): when the FP32-pair forces
-                                   meet ftol, the same configuration is evaluated once
-                                   more in FP64 (double-float table terms, full list)
-                                   and the relaxation stops only if those forces meet
-                                   ftol too; otherwise it tightens its FP32 threshold
-                                   by the FP32-FP64 difference seen there and goes on.
-                                   Each confirmation is one force evaluation that is not
-                                   an iteration.  The batched form confirms per system.
-                                   0: stop on the FP32-pair forces.  Other forms
-                                   ignore it. */
+    int32_t confirm64;          /* fire_fp64_check, FP32-pair form only (default
+                                   FIRE_FP64_CHECK_CONFIRM) */
     double dmax;                /* maximum displacement of any atom per step (the
                                    paper's dmax, Sec. 4 cases 1 and 7), 0 = no cap
                                    (default 0): the drift x += dt v uses

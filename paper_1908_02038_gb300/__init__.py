@@ -30,6 +30,7 @@ FIRE_PAIR_TABLE, FIRE_PAIR_ANALYTIC = 0, 1
 FIRE_NEWTON_AUTO, FIRE_NEWTON_ON, FIRE_NEWTON_OFF = 0, 1, 2
 FIRE_INT_EULER_IMPLICIT, FIRE_INT_EULER_EXPLICIT, FIRE_INT_VERLET, FIRE_INT_LEAPFROG = 0, 1, 2, 3
 FIRE_VARIANT_FIRE2, FIRE_VARIANT_FIRE1 = 0, 1
+FIRE_FP64_CHECK_OFF, FIRE_FP64_CHECK_CONFIRM, FIRE_FP64_CHECK_FINISH = 0, 1, 2
 
 STATUS_NAMES = {0: "FIRE_OK", 1: "FIRE_ERR_ARG", 2: "FIRE_ERR_CUDA", 3: "FIRE_ERR_NOMEM",
                 4: "FIRE_ERR_NONFINITE", 5: "FIRE_ERR_NBR_OVERFLOW", 6: "FIRE_ERR_TIMEOUT",

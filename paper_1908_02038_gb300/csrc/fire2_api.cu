@@ -561,6 +561,8 @@ void init_state(fire_handle* h, double ftol, int64_t maxiter) {
     s.budget_ns = (unsigned long long)(h->budget_s * 1e9);
     s.ftol_user = ftol;
     s.vstate = h->verify ? 1 : 0;
+    s.vmode = h->verify ? h->par.confirm64 : 0;
+    s.fsw = 3.0 * ftol;   // mode 2: the FP64 phase starts below 3 ftol
 }
 
 fire_status status_to_error(fire_handle* h, int st) {
@@ -606,6 +608,8 @@ fire_status check_params(fire_handle* h, const fire_params_t& p) {
     if (p.variant != FIRE_VARIANT_FIRE2 && p.variant != FIRE_VARIANT_FIRE1)
         return fail(h, FIRE_ERR_ARG, "unknown variant %d", p.variant);
     if (p.norm < 0 || p.norm > 2) return fail(h, FIRE_ERR_ARG, "unknown norm %d", p.norm);
+    if (p.confirm64 < FIRE_FP64_CHECK_OFF || p.confirm64 > FIRE_FP64_CHECK_FINISH)
+        return fail(h, FIRE_ERR_ARG, "unknown confirm64 setting %d", p.confirm64);
     if (!(p.dmax >= 0.0) || !std::isfinite(p.dmax))
         return fail(h, FIRE_ERR_ARG, "dmax must be finite and >= 0");
     return FIRE_OK;
@@ -668,7 +672,7 @@ fire_status fire_default_params(fire_params_t* out, double dt_start) {
     out->integrator = FIRE_INT_EULER_IMPLICIT;
     out->norm = FIRE_NORM_MAX_ATOM;
     out->variant = FIRE_VARIANT_FIRE2;
-    out->confirm64 = 1;
+    out->confirm64 = FIRE_FP64_CHECK_CONFIRM;
     out->dmax = 0.0;
     return FIRE_OK;
 }

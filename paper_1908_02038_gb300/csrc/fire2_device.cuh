@@ -59,12 +59,13 @@ struct DevState {
     unsigned long long max_disp2;           // bits of max |x - x_ref|^2 (>= 0)
     unsigned int upd_blocks;                // k_update blocks finished (last-block test)
     unsigned long long vmax2;               // bits of max |v_i|^2 before the drift (dmax)
-    // FP64 confirmation of an FP32-pair stop on ftol: vstate 0 = off, 1 = FP32
-    // phase, 2 = the current evaluation confirms in FP64; prm.ftol is the
-    // (possibly tightened) FP32 threshold, ftol_user the caller's, fn32 the
-    // FP32 norm at the configuration being confirmed
-    int vstate, vcount;
-    double ftol_user, fn32;
+    // FP64 check of FP32-pair relaxations (fire_params_t.confirm64): vstate
+    // 0 = off, 1 = FP32 phase, 2 = the current evaluation confirms an FP32
+    // stop in FP64, 3 = FP64 phase to the end (mode 2, below fsw); prm.ftol is
+    // the (possibly tightened) FP32 threshold, ftol_user the caller's, fn32
+    // the FP32 norm at the configuration being confirmed
+    int vstate, vcount, vmode;
+    double ftol_user, fn32, fsw;
 };
 
 struct Bufs {
@@ -107,7 +108,7 @@ struct Bufs {
 __device__ __forceinline__ bool pass_skipped(const Bufs& b) {
     if (b.st->done) return true;
     if (b.pass_role == 0) return false;
-    const bool confirming = b.st->vstate == 2;
+    const bool confirming = b.st->vstate >= 2;   // confirming, or the FP64 phase
     return b.pass_role == 1 ? confirming : !confirming;
 }
 
@@ -1121,7 +1122,7 @@ __global__ void k_control(Bufs b, int mode, cudaGraphConditionalHandle h, int ha
     const double V2 = ctl_sum(b.rpart + 2 * b.nb_red, b.nb_red, sh);
     const double fa2 = ctl_max(b.rpart + 3 * b.nb_red, b.nb_red, sh);
     const double fin = ctl_max(b.rpart + 4 * b.nb_red, b.nb_red, sh);
-    const int ne = b.st->vstate == 2 ? b.nb_verify : b.nb_force + b.nb_embed;
+    const int ne = b.st->vstate >= 2 ? b.nb_verify : b.nb_force + b.nb_embed;
     const double E = ctl_sum(b.epart, ne, sh);
     if (threadIdx.x != 0) return;
     DevState& s = *b.st;
@@ -1157,6 +1158,10 @@ __global__ void k_control(Bufs b, int mode, cudaGraphConditionalHandle h, int ha
             s.fs.evals += 1;
             s.fs.stop = STOP_FTOL;
             stop = true;
+        } else if (s.vmode == 2) {   // finish in FP64 from here
+            s.prm.ftol = s.ftol_user;
+            s.vstate = 3;
+            stop = fire_control_step(s.prm, s.fs, P, F2, V2, fa2, fin);
         } else {
             // not converged in FP64: tighten the FP32 threshold by the FP32 to
             // FP64 difference seen here and take the step with these forces
@@ -1171,6 +1176,9 @@ __global__ void k_control(Bufs b, int mode, cudaGraphConditionalHandle h, int ha
             s.vstate = 2;
             s.vcount += 1;
             stop = false;
+        } else if (!stop && s.vstate == 1 && s.vmode == 2 &&
+                   force_norm(s.prm.norm, F2, fa2, fin) < s.fsw) {
+            s.vstate = 3;   // the FP32-pair forces have done their part: FP64 from the next
         }
     }
     s.done = stop ? 1 : 0;
@@ -1189,7 +1197,7 @@ __global__ void k_update(Bufs b, GeoC g, cudaGraphConditionalHandle hif, int has
     // graph loop: the IF node of the FP64 confirming passes runs this pass
     // only when an FP32-pair stop is being confirmed
     if (has_conf && blockIdx.x == 0 && threadIdx.x == 0)
-        cudaGraphSetConditional(hconf, b.st->vstate == 2 ? 1u : 0u);
+        cudaGraphSetConditional(hconf, b.st->vstate >= 2 ? 1u : 0u);
     // no step when stopped, nor while an FP32-pair stop is confirmed in FP64
     // (the next evaluation is at the same positions)
     if (b.st->done || b.st->vstate == 2) {

@@ -7,6 +7,7 @@ import subprocess
 
 import pytest
 
+import fire_inputs as fi
 import paper_1908_02038_gb300 as fg
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -43,6 +44,7 @@ def test_abi_version_and_defaults(lib):
         (10.0, 0.02, 1.1, 0.5, 0.25, 0.99)
     assert (p.delaystep, p.vdfmax, p.halfstepback, p.initialdelay, p.integrator, p.norm) == \
         (20, 2000, 1, 1, 0, 0)
+    assert p.confirm64 == fg.FIRE_FP64_CHECK_CONFIRM
     with pytest.raises(fg.FireError) as e:
         fg.fire_default_params(0.0)
     assert e.value.status == fg.FIRE_ERR_ARG
@@ -66,6 +68,16 @@ def test_init_rejects_bad_arguments_before_touching_the_gpu(lib):
     sys = fg.fire_system_t(10, -1.0, (ctypes.c_int32 * 3)(1, 1, 1), 0)
     with pytest.raises(fg.FireError):
         fg.fire_init(sys, pot, par)
+
+
+def test_init_rejects_unknown_fp64_check_setting(lib):
+    pot = fg.Potential(fg.FIRE_POT_RGL, precision=fg.FIRE_PREC_FP32_PAIR, **fi.RGL_CU).c()
+    sys = fg.fire_system_t(10, 1.0, (ctypes.c_int32 * 3)(1, 1, 1), 0)
+    par = fg.fire_default_params(0.001)
+    par.confirm64 = 3
+    with pytest.raises(fg.FireError) as e:
+        fg.fire_init(sys, pot, par)
+    assert e.value.status == fg.FIRE_ERR_ARG and "confirm64" in str(e.value)
 
 
 def test_fp32pair_rejected_for_lj(lib):

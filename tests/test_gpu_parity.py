@@ -316,14 +316,15 @@ def test_chunked_execution_matches_graph_loop():
     assert r3.stop == fg.FIRE_STOP_MAXITER and r3.iterations == 50 and r3.force_evals == 51
 
 
-def test_fp32pair_graph_and_chunked_runs_are_identical():
+@pytest.mark.parametrize("check", [fg.FIRE_FP64_CHECK_CONFIRM, fg.FIRE_FP64_CHECK_FINISH])
+def test_fp32pair_graph_and_chunked_runs_are_identical(check):
     # The FP32-pair passes write whole forces and sum in a fixed order, so the
     # graph loop (rebuild decided by the update kernel's last block, build
     # chain under an IF node) and the chunked loop (every build kernel tests
     # the displacement itself) must follow the same trajectory bit for bit.
     c = fi.rgl_vacancy_box(ncell=12, seed=14, n_vac=4, sigma=0.1)
     pot = rgl_pot(precision=fg.FIRE_PREC_FP32_PAIR)
-    with fg.FireHandle(c.n, fi.CU_MASS, pot, dt_start=fi.CU_DT) as h:
+    with fg.FireHandle(c.n, fi.CU_MASS, pot, dt_start=fi.CU_DT, confirm64=check) as h:
         x1 = c.x.copy()
         r1 = h.minimize(x1, c.box, 1e-6, 100000)
         h.set_exec_mode(fg.FIRE_EXEC_CHUNKED, 16)
@@ -395,6 +396,25 @@ def test_fp32pair_relaxation_reaches_fp64_converged_state():
     assert abs(e_chk - r64.energy) / c.n < 1e-8
     # FP32-pair force error at the relaxed structure
     assert np.sqrt(((f32_at32 - f_chk) ** 2).sum(1)).max() < F32_MARGIN
+
+
+def test_fp32pair_finishing_in_fp64_converges_in_fp64():
+    # FIRE_FP64_CHECK_FINISH: FP32-pair forces while the norm is >= 3 ftol,
+    # FP64 forces from there on; the stop is on FP64 forces
+    c = fi.rgl_vacancy_box(ncell=20, seed=2)
+    x = c.x.copy()
+    with fg.FireHandle(c.n, fi.CU_MASS, rgl_pot(), dt_start=fi.CU_DT) as h64, \
+            fg.FireHandle(c.n, fi.CU_MASS, rgl_pot(precision=fg.FIRE_PREC_FP32_PAIR),
+                          dt_start=fi.CU_DT, confirm64=fg.FIRE_FP64_CHECK_FINISH) as h32:
+        r64 = h64.minimize(c.x.copy(), c.box, 1e-6, 100000)
+        r = h32.minimize(x, c.box, 1e-6, 100000)
+        e_chk, f_chk = h64.energy_forces(x, c.box)
+    fmax64 = np.sqrt((f_chk ** 2).sum(1)).max()
+    print(f"FP64 {r64.iterations} iterations; FP32-pair then FP64 {r.iterations}")
+    assert r.stop == fg.FIRE_STOP_FTOL and r.force_evals == r.iterations + 1
+    assert fmax64 < 1e-6 and abs(r.fmax_atom - fmax64) < 1e-12
+    assert r.energy == pytest.approx(e_chk, rel=1e-13)
+    assert abs(e_chk - r64.energy) / c.n < 1e-8
 
 
 def test_fp32pair_without_confirmation_stops_on_fp32_forces():
