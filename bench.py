@@ -403,6 +403,27 @@ def batch_block(fg, torch, dev, steps=3, tuning=None, compare=True):
            "converged": int(sum(r.stop == fg.FIRE_STOP_FTOL for r in res)),
            "max_iterations": int(max(r.iterations for r in res))}
     if compare:
+        # the same batch finishing in FP64 below 3 ftol (a precision schedule,
+        # per system), at the same launch shape
+        with fg.FireBatch(counts, fi.CU_MASS, pot, dt_start=fi.CU_DT,
+                          confirm64=fg.FIRE_FP64_CHECK_FINISH) as bf:
+            bf.set_tuning(tune["threads_per_block"], tune["ctas_per_sm"],
+                          tune.get("cluster_size", 1) or 1)
+            w.copy_(x0)
+            bf.minimize_dev(w, boxes, FTOL, MAXITER)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            w.copy_(x0)
+            e0.record()
+            rf = bf.minimize_dev(w, boxes, FTOL, MAXITER)
+            e1.record()
+            torch.cuda.synchronize()
+        msf = e0.elapsed_time(e1)
+        out["finish64"] = {"ms_per_step": msf,
+                           "value": sum(int(r.iterations) * int(n) for r, n in zip(rf, counts))
+                           / (msf * 1e-3), "unit": UNIT,
+                           "converged": int(sum(r.stop == fg.FIRE_STOP_FTOL for r in rf)),
+                           "max_iterations": int(max(r.iterations for r in rf))}
         out.update(batch_compare(fg, torch, dev, cfgs, x, x_fin, boxes, counts))
     return out
 

@@ -127,8 +127,8 @@ typedef enum {
  *   an iteration.  The batched form confirms per system.
  * FIRE_FP64_CHECK_FINISH: FP32-pair forces while the force norm is at least
  *   3 ftol, FP64 forces (double-float table terms, full list) from the first
- *   evaluation below it to the end; a precision schedule (single-system
- *   handles; the batched form confirms instead). */
+ *   evaluation below it to the end; a precision schedule (per system in the
+ *   batched form). */
 typedef enum {
     FIRE_FP64_CHECK_OFF = 0,
     FIRE_FP64_CHECK_CONFIRM = 1,

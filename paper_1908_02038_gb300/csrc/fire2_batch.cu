@@ -66,7 +66,8 @@ struct BArgs {
     const float *tab_ffd, *tab_fff;   // FP64 table form: density / force rows
     int ff;                 // 1: FP64 table passes available (FP64 table form, or the
                             //    FP32-pair form confirming its stops)
-    int confirm;            // FP32-pair form: confirm stops on ftol in FP64
+    int confirm;            // FP32-pair form: FP64 check of its stops (confirm64 != 0)
+    int vmode;              // fire_fp64_check: 1 confirm, 2 finish in FP64 below 3 ftol
     double* fp64;           // F'(rho) (FP64 form)
     float* fp32;            // F'(rho) (FP32-pair form)
     uint32_t* nbr;
@@ -88,8 +89,9 @@ struct BShared {            // per-CTA scalars
     int sys, done, status, rebuild;
     long long builds;
     double P, F2, V2, fa2, fin, E, dmax;
-    // FP64 confirmation of FP32-pair stops (as fire2_device.cuh's DevState):
-    // vstate 0 off, 1 FP32 phase, 2 the next evaluation confirms in FP64
+    // FP64 check of FP32-pair stops (as fire2_device.cuh's DevState): vstate
+    // 0 off, 1 FP32 phase, 2 the next evaluation confirms in FP64, 3 FP64
+    // passes to the end (vmode 2)
     int vstate;
     double ftol_work, fn32;
 };
@@ -520,6 +522,9 @@ __device__ __noinline__ void b_reduce_control(const BArgs& a, const BInst& I, in
                     sh.fs.evals += 1;
                     sh.fs.stop = STOP_FTOL;
                     stop = true;
+                } else if (a.vmode == 2) {   // finish in FP64 from here
+                    sh.vstate = 3;
+                    stop = fire_control_step(p, sh.fs, sh.P, sh.F2, sh.V2, sh.fa2, sh.fin);
                 } else {   // tighten the FP32 threshold, step with these forces
                     sh.ftol_work = fmax(sh.ftol_work - 1.5 * (fn - sh.fn32), 0.4 * a.prm.ftol);
                     p.ftol = sh.ftol_work;
@@ -532,6 +537,9 @@ __device__ __noinline__ void b_reduce_control(const BArgs& a, const BInst& I, in
                     sh.fn32 = force_norm(p.norm, sh.F2, sh.fa2, sh.fin);
                     sh.vstate = 2;
                     stop = false;
+                } else if (!stop && sh.vstate == 1 && a.vmode == 2 &&
+                           force_norm(p.norm, sh.F2, sh.fa2, sh.fin) < 3.0 * a.prm.ftol) {
+                    sh.vstate = 3;   // FP64 passes from the next evaluation on
                 }
             }
         }
@@ -653,6 +661,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_batch_relax(BArgs a) {
                 continue;
             }
             const FireScal fs = sh.fs;
+            const bool fp64_phase = F32 && sh.vstate == 3;   // finishing in FP64
             // maximum displacement per step: the drift waits for max_i |v_i|
             double dt_drift = fs.dt_cur;
             if (a.prm.dmax > 0.0) {
@@ -683,7 +692,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_batch_relax(BArgs a) {
                 if (F32)
                     a.xq[gi] = make_int4(to_fixed(x.x, a.qscale), to_fixed(x.y, a.qscale),
                                          to_fixed(x.z, a.qscale), 0);
-                else if (a.ff)
+                if (a.ff && (!F32 || fp64_phase))
                     a.xq64[gi] = {to_fixed64(x.x, kFixedBits64), to_fixed64(x.y, kFixedBits64),
                                   to_fixed64(x.z, kFixedBits64), 0ll};
                 const dvec4 r = a.xref[gi];
@@ -700,7 +709,8 @@ __global__ void __launch_bounds__(MAXT, 1) k_batch_relax(BArgs a) {
                     sh.builds += 1;
                 }
             }
-            E = b_forces<F32, CL>(a, I, lo, hi, etab, et32, red);
+            E = fp64_phase ? b_forces_confirm<CL>(a, I, lo, hi, etab, et32, red)
+                           : b_forces<F32, CL>(a, I, lo, hi, etab, et32, red);
             b_reduce_control<CL>(a, I, lo, hi, sh, X, E, red, t0);
         }
         // write back
@@ -898,6 +908,7 @@ FIRE2_HIDDEN fire_status fire2_batch_create(fire_handle_t* h, int32_t n_sys,
         BA(a.fp64, n * sizeof(double));
     }
     a.confirm = f32 && fire2_params(h).confirm64 != 0 ? 1 : 0;
+    a.vmode = a.confirm ? fire2_params(h).confirm64 : 0;
     a.ff = fire2_tab_ffd(h) != nullptr && (!f32 || a.confirm) ? 1 : 0;
     if (a.ff && f32) BA(a.fp64, n * sizeof(double));
     if (a.ff) {

@@ -95,6 +95,25 @@ def test_batch_matches_single_system_path_and_tuning_does_not_change_results():
             assert abs(r.energy - rs.energy) / c.n < 1e-7
 
 
+@pytest.mark.parametrize("check", [fg.FIRE_FP64_CHECK_CONFIRM, fg.FIRE_FP64_CHECK_FINISH])
+def test_batch_fp32pair_stops_meet_ftol_in_fp64(check):
+    # every system's stop is checked in FP64 (confirmation, or the FP64
+    # finish below 3 ftol): the structures meet ftol with FP64 forces
+    cfgs = fi.rgl_batch(n_sys=24, seed=57, nmin=3, nmax=8)
+    x, boxes, counts = pack(cfgs)
+    with fg.FireBatch(counts, fi.CU_MASS, rgl_pot(fg.FIRE_PREC_FP32_PAIR),
+                      dt_start=fi.CU_DT, confirm64=check) as b:
+        res, _ = b.minimize(x, boxes, 1e-6, 100000)
+    assert all(r.stop == fg.FIRE_STOP_FTOL for r in res)
+    with fg.FireBatch(counts, fi.CU_MASS, rgl_pot(), dt_start=fi.CU_DT) as b64:
+        chk, _ = b64.minimize(x.copy(), boxes, 1e-6, 0)
+    for s, (r, rc) in enumerate(zip(res, chk)):
+        assert rc.fmax_atom < 1e-6, (s, rc.fmax_atom)
+        # the reported norm and energy come from the FP64 evaluation
+        assert abs(r.fmax_atom - rc.fmax_atom) < 1e-10, s
+        assert abs(r.energy - rc.energy) / counts[s] < 1e-12, s
+
+
 def test_batch_512_fp32_all_converge_and_sample_matches_oracle():
     cfgs = fi.rgl_batch()           # 512 systems, 3^3..12^3 cells, 1-3 vacancies
     x, boxes, counts = pack(cfgs)
