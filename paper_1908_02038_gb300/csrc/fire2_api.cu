@@ -1405,11 +1405,6 @@ fire_status fire_rgl_energy_grad_dev(fire_handle_t* h, const double* d_pos, cons
 static void launch_hvp(fire_handle* h, const GradBufs& b, const PotC& pc, const double box[3],
                        const double* u, double* hu, cudaStream_t s) {
     GeoL L{{box[0], box[1], box[2]}};
-    if (b.w1) {   // pair coefficients cached for this solve
-        k_g_hvp1c<<<h->grad.nb, kForceBlock, 0, s>>>(b, L, u, nullptr);
-        k_g_hvp2c<<<h->grad.nb, kForceBlock, 0, s>>>(b, L, u, hu, nullptr);
-        return;
-    }
     k_g_hvp1<<<h->grad.nb, kForceBlock, 0, s>>>(b, pc, L, h->b.exp_table, u);
     k_g_hvp2<<<h->grad.nb, kForceBlock, 0, s>>>(b, pc, L, h->b.exp_table, u, hu);
 }

@@ -389,9 +389,6 @@ __host__ __device__ __forceinline__ ffloat ff_poly(const float* c, ffloat s) {
 }
 
 __host__ __device__ __forceinline__ ffloat ff_neg(ffloat a) { return {-a.hi, -a.lo}; }
-__host__ __device__ __forceinline__ ffloat ff_scale2(ffloat a, float p2) {   // p2 a power of 2
-    return {a.hi * p2, a.lo * p2};
-}
 
 // Interval of u (from its FP32 copy uf), clamped to the table.
 __host__ __device__ __forceinline__ int ff_index(const TabMeta& m, float uf) {
