@@ -196,9 +196,13 @@ typedef struct {
                                    not changed by the cap */
 } fire_params_t;
 
+/* Result of a relaxation.  Energy and norms are those of the last force
+ * evaluation, which for an FP32-pair relaxation stopped on ftol with an FP64
+ * check (confirm64) is the FP64 one. */
 typedef struct {
     double energy;              /* E at the returned positions */
-    int64_t iterations;         /* completed FIRE iterations (= force evaluations - 1) */
+    int64_t iterations;         /* completed FIRE iterations (= force evaluations - 1,
+                                   less the FP64 confirmations of FP32-pair stops) */
     int64_t force_evals;        /* force evaluations including the initial one */
     int64_t nbr_builds;         /* neighbour-list builds during the call */
     int32_t stop;               /* fire_stop */
