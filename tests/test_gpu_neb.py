@@ -99,13 +99,14 @@ def test_neb_device_path_and_frozen_layer():
     assert np.array_equal(p[:, sel], path[:, sel])
 
 
-def test_neb_fp32pair_reaches_the_fp64_barrier():
+@pytest.mark.parametrize("check", [fg.FIRE_FP64_CHECK_CONFIRM, fg.FIRE_FP64_CHECK_FINISH])
+def test_neb_fp32pair_reaches_the_fp64_barrier(check):
     c, path = hop_path(6, 5, seed=10, mode=oracle.FORCE_CELLS)
     res = {}
     for prec in (fg.FIRE_PREC_FP64, fg.FIRE_PREC_FP32_PAIR):
         p = path.copy()
         with fg.FireNEB(5, path.shape[1], fi.CU_MASS, rgl_pot(prec, fg.FIRE_PAIR_ANALYTIC), 1.0,
-                        True, dt_start=fi.CU_DT) as h:
+                        True, dt_start=fi.CU_DT, confirm64=check) as h:
             r, E, cl = h.minimize(p, c.box, 1e-5, 100000)
         assert r.stop == fg.FIRE_STOP_FTOL and cl == 3
         res[prec] = (E[cl] - E[0], p)
