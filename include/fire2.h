@@ -39,7 +39,7 @@
 extern "C" {
 #endif
 
-#define FIRE2_ABI_VERSION 7
+#define FIRE2_ABI_VERSION 8
 
 typedef enum {
     FIRE_OK = 0,
@@ -266,6 +266,22 @@ typedef enum {
  * counterpart (it describes the loop of Algorithm 2, not how it is driven).
  * Errors: FIRE_ERR_ARG. */
 fire_status fire_set_exec_mode(fire_handle_t* h, int32_t mode, int32_t chunk);
+
+/* Threads per atom in the RGL pair passes of the FP64 table form and of the
+ * FP32-pair form with exponentials: tpa = 1, 2, 4 or 8, or 0 for the
+ * automatic choice, which handles start with (the fewest that give a pass at
+ * least 1024 threads per SM in the FP64 form, 512 in the FP32-pair form: on a
+ * 152-SM device one thread per atom from about 155,000 and 78,000 atoms, 8
+ * below about 39,000 and 19,000).  The threads of an atom
+ * take every tpa-th entry of its neighbour list and their partial sums are
+ * added in FP64, so results change only in the rounding of the per-atom sums
+ * (far below the FP64 form's 1e-10 relative force error).  Other forms run
+ * one thread per atom and report 1.  *chosen (may be NULL) receives the value
+ * in effect.  Applies to later calls on h; the paper has no counterpart (it
+ * does not say how force evaluation is parallelised).
+ * Errors: FIRE_ERR_ARG (another tpa; batched handles, which take their launch
+ * shape from fire_batch_set_tuning). */
+fire_status fire_set_threads_per_atom(fire_handle_t* h, int32_t tpa, int32_t* chosen);
 
 /* Wall-clock budget of one device relaxation loop (default 3600 s, 0 = none).
  * When exceeded, the loop stops at the next iteration boundary and the call

@@ -40,7 +40,8 @@ STATUS_NAMES = {0: "FIRE_OK", 1: "FIRE_ERR_ARG", 2: "FIRE_ERR_CUDA", 3: "FIRE_ER
 EXPORTED = ("fire_abi_version", "fire_default_params", "fire_init", "fire_minimize",
             "fire_minimize_dev", "fire_energy_forces", "fire_energy_forces_dev",
             "fire_set_time_budget", "fire_profile_stages", "fire_diag_fma_peak",
-            "fire_energy_forces_noalloc", "fire_set_exec_mode", "fire_diag_exp",
+            "fire_energy_forces_noalloc", "fire_set_exec_mode", "fire_set_threads_per_atom",
+            "fire_diag_exp",
             "fire_batch_init", "fire_minimize_batch", "fire_minimize_batch_dev",
             "fire_batch_set_tuning", "fire_batch_autotune", "fire_set_rgl_params",
             "fire_rgl_energy_grad_dev", "fire_rgl_hvp_dev", "fire_rgl_implicit_grad_dev",
@@ -118,6 +119,7 @@ def load_library(path: str | None = None):
                                            C.c_void_p, C.c_void_p]
     lib.fire_set_time_budget.argtypes = [H, C.c_double]
     lib.fire_set_exec_mode.argtypes = [H, C.c_int32, C.c_int32]
+    lib.fire_set_threads_per_atom.argtypes = [H, C.c_int32, C.POINTER(C.c_int32)]
     lib.fire_set_dof_mask.argtypes = [H, C.c_void_p]
     lib.fire_neb_init.argtypes = [C.POINTER(H), C.c_int32, C.POINTER(fire_system_t),
                                   C.POINTER(fire_potential_t), C.POINTER(fire_params_t),
@@ -226,6 +228,14 @@ def fire_set_dof_mask(handle, mask) -> None:
 
 def fire_set_exec_mode(handle, mode: int, chunk: int = 32) -> None:
     _check(load_library().fire_set_exec_mode(handle, int(mode), int(chunk)), handle)
+
+
+def fire_set_threads_per_atom(handle, tpa: int = 0) -> int:
+    """Threads per atom of the splitting RGL pair passes (0 = automatic);
+    returns the value in effect."""
+    out = C.c_int32(0)
+    _check(load_library().fire_set_threads_per_atom(handle, int(tpa), C.byref(out)), handle)
+    return out.value
 
 
 def fire_minimize(handle, pos: np.ndarray, box, ftol: float, maxiter: int) -> fire_result_t:
@@ -535,6 +545,9 @@ class FireHandle:
     def set_exec_mode(self, mode, chunk=32):
         fire_set_exec_mode(self.h, mode, chunk)
 
+    def set_threads_per_atom(self, tpa=0):
+        return fire_set_threads_per_atom(self.h, tpa)
+
     def set_time_budget(self, seconds):
         fire_set_time_budget(self.h, seconds)
 
@@ -615,6 +628,9 @@ class FireNEB:
 
     def set_exec_mode(self, mode, chunk=32):
         fire_set_exec_mode(self.h, mode, chunk)
+
+    def set_threads_per_atom(self, tpa=0):
+        return fire_set_threads_per_atom(self.h, tpa)
 
     def close(self):
         if getattr(self, "h", None):

@@ -103,6 +103,7 @@ struct fire_handle {
     uint8_t* dofmask = nullptr;      // device copy of the frozen-DOF mask (n bytes)
     int img_n = 0;                   // atoms per image (n, except for NEB handles)
     bool verify = false;             // FP32-pair: stops on ftol confirmed in FP64
+    int sms = 0;                     // SM count of the device
     NebState* neb = nullptr;
     std::string err;
 };
@@ -137,10 +138,8 @@ double cutoff(const fire_potential_t& p) {
     return p.kind == FIRE_POT_LJ ? p.rc_lj : p.rc;
 }
 
-// Neighbour geometry for a box.  The list radius is rc + skin, with the skin
-// reduced where a periodic axis is shorter than 2 (rc + skin) so that the
 // The FP64 form's tabulated RGL passes (fixed-point separations, double-float
-// pair terms, full list, k_density_ff / k_force_ff).
+// pair terms, k_density_ff / k_force_ff) ...
 bool fixed64_form(const fire_potential_t& p) {
     return p.kind == FIRE_POT_RGL && p.precision == FIRE_PREC_FP64 && p.pair_eval == FIRE_PAIR_TABLE;
 }
@@ -149,6 +148,32 @@ bool fixed64_half(const fire_potential_t& p) {
     return fixed64_form(p) && p.newton != FIRE_NEWTON_OFF;
 }
 
+// The pair passes that can split an atom's list over several threads: the
+// FP64 table form and the FP32-pair form with exponentials.
+bool tpa_form(const fire_potential_t& p) {
+    return fixed64_form(p) || (p.kind == FIRE_POT_RGL && p.precision == FIRE_PREC_FP32_PAIR &&
+                               p.pair_eval == FIRE_PAIR_ANALYTIC);
+}
+
+constexpr int kMaxTpa = 8;
+
+// Threads per atom chosen when the caller sets none: the fewest (1, 2, 4 or
+// 8) that give a pair pass at least 1024 threads per SM in the FP64 table
+// form, 512 in the FP32-pair form.  Measured on GB300 (152 SMs, us per
+// iteration at 1 / 2 / 4 / 8 threads per atom): FP64 form 3,751 atoms
+// 110 / 94 / 78 / 57, 29,931 atoms 116 / 104 / 93 / 90, 59,762 atoms
+// 135 / 126 / 119 / 122, 128,277 atoms 187 / 194 / 189 / 204, 997,450 atoms
+// 986 / 1031 / 1090 / 1307; FP32-pair form 29,931 atoms 108 / 81 / 73 / 78,
+// 59,762 atoms 115 / 92 / 92 / 102, 997,450 atoms 652 / 680 / 753 / 963.
+int auto_tpa(const fire_potential_t& p, long long n, int sms) {
+    const long long want = (long long)sms * (p.precision == FIRE_PREC_FP32_PAIR ? 512 : 1024);
+    int t = 1;
+    while (t < kMaxTpa && n * t < want) t *= 2;
+    return t;
+}
+
+// Neighbour geometry for a box.  The list radius is rc + skin, with the skin
+// reduced where a periodic axis is shorter than 2 (rc + skin) so that the
 // minimum image stays unique within the list radius.
 GeoC make_geo(const fire_handle* h, const double box[3]) {
     GeoC g{};
@@ -265,13 +290,49 @@ void launch_build(fire_handle* h, const GeoC& g, int force, cudaStream_t s) {
     k_nbr_build<<<ceil_div(n, kForceBlock), kForceBlock, 0, s>>>(h->b, g, force);
 }
 
+// The pair passes for the handle's threads per atom (b.tpa).
+template <bool HALF>
+void density_ff(const Bufs& b, const PotC& P, const GeoC& g, int nb, cudaStream_t s) {
+    switch (b.tpa) {
+    case 8: k_density_ff<HALF, 8><<<nb, kForceBlock, 0, s>>>(b, P, g); break;
+    case 4: k_density_ff<HALF, 4><<<nb, kForceBlock, 0, s>>>(b, P, g); break;
+    case 2: k_density_ff<HALF, 2><<<nb, kForceBlock, 0, s>>>(b, P, g); break;
+    default: k_density_ff<HALF, 1><<<nb, kForceBlock, 0, s>>>(b, P, g);
+    }
+}
+template <bool HALF>
+void force_ff(const Bufs& b, const PotC& P, const GeoC& g, int nb, cudaStream_t s) {
+    switch (b.tpa) {
+    case 8: k_force_ff<HALF, 8><<<nb, kForceBlock, 0, s>>>(b, P, g); break;
+    case 4: k_force_ff<HALF, 4><<<nb, kForceBlock, 0, s>>>(b, P, g); break;
+    case 2: k_force_ff<HALF, 2><<<nb, kForceBlock, 0, s>>>(b, P, g); break;
+    default: k_force_ff<HALF, 1><<<nb, kForceBlock, 0, s>>>(b, P, g);
+    }
+}
+void density32(const Bufs& b, const PotC& P, const GeoC& g, cudaStream_t s) {
+    switch (b.tpa) {
+    case 8: k_density32<8><<<b.nb_force, kForceBlock, 0, s>>>(b, P, g); break;
+    case 4: k_density32<4><<<b.nb_force, kForceBlock, 0, s>>>(b, P, g); break;
+    case 2: k_density32<2><<<b.nb_force, kForceBlock, 0, s>>>(b, P, g); break;
+    default: k_density32<1><<<b.nb_force, kForceBlock, 0, s>>>(b, P, g);
+    }
+}
+void force32(const Bufs& b, const PotC& P, const GeoC& g, cudaStream_t s) {
+    switch (b.tpa) {
+    case 8: k_force32<8><<<b.nb_force, kForceBlock, 0, s>>>(b, P, g); break;
+    case 4: k_force32<4><<<b.nb_force, kForceBlock, 0, s>>>(b, P, g); break;
+    case 2: k_force32<2><<<b.nb_force, kForceBlock, 0, s>>>(b, P, g); break;
+    default: k_force32<1><<<b.nb_force, kForceBlock, 0, s>>>(b, P, g);
+    }
+}
+
 // FP32-pair handles that confirm their stops: the FP64 passes on the same
 // full list (they return at once unless a stop is being confirmed).
 void launch_confirm(fire_handle* h, const GeoC& g, cudaStream_t s) {
     Bufs bv = h->b;
     bv.pass_role = 2;
-    k_density_ff<false><<<h->b.nb_verify, kForceBlock, 0, s>>>(bv, h->potc, g);
-    k_force_ff<false><<<h->b.nb_verify, kForceBlock, 0, s>>>(bv, h->potc, g);
+    density_ff<false>(bv, h->potc, g, h->b.nb_verify, s);
+    force_ff<false>(bv, h->potc, g, h->b.nb_verify, s);
 }
 
 // The force passes of one evaluation; with confirm_passes, also the FP64
@@ -284,15 +345,15 @@ void launch_forces(fire_handle* h, const GeoC& g, cudaStream_t s, bool confirm_p
         k_density32_tab<<<h->nb_tab_d, kTabBlock, h->smem_d, s>>>(h->b, h->potc, g);
         k_force32_tab<<<h->nb_tab_f, kTabBlock, h->smem_f, s>>>(h->b, h->potc, g);
     } else if (tab && fixed64_half(h->pot)) {
-        k_density_ff<true><<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
+        density_ff<true>(h->b, h->potc, g, h->b.nb_force, s);
         k_embed<<<h->b.nb_embed, kElemBlock, 0, s>>>(h->b);
-        k_force_ff<true><<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
+        force_ff<true>(h->b, h->potc, g, h->b.nb_force, s);
     } else if (tab) {
-        k_density_ff<false><<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
-        k_force_ff<false><<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
+        density_ff<false>(h->b, h->potc, g, h->b.nb_force, s);
+        force_ff<false>(h->b, h->potc, g, h->b.nb_force, s);
     } else if (h->pot.kind == FIRE_POT_RGL && h->pot.precision == FIRE_PREC_FP32_PAIR) {
-        k_density32<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
-        k_force32<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
+        density32(h->b, h->potc, g, s);
+        force32(h->b, h->potc, g, s);
     } else if (h->pot.kind == FIRE_POT_RGL) {
         k_density<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
         k_embed<<<h->b.nb_embed, kElemBlock, 0, s>>>(h->b);
@@ -906,7 +967,11 @@ static fire_status init_handle(fire_handle_t** hp, const fire_system_t* sys,
     const bool fixed64 = fixed64_form(*pot);
     const bool whole = fp32pair || (fixed64 && !fixed64_half(*pot));   // no atomics
     b.accum = whole ? 0 : 1;
-    b.nb_force = ceil_div(h->n, kForceBlock);
+    // pair passes that split an atom's list: enough threads per atom to fill
+    // the device on small systems (auto_tpa)
+    h->sms = sms;
+    b.tpa = tpa_form(*pot) ? auto_tpa(*pot, h->n, sms) : 1;
+    b.nb_force = ceil_div((long long)h->n * b.tpa, kForceBlock);
     // the embedding and the reductions run best on two blocks per SM (1M
     // atoms, measured: embed 37 / 39 / 41 us at 2 / 4 / 8 blocks per SM;
     // reduce 51 / 49 / 55 / 62 us at 1 / 2 / 4 / 8)
@@ -920,7 +985,7 @@ static fire_status init_handle(fire_handle_t** hp, const fire_system_t* sys,
         if (ts != FIRE_OK) return bail(ts);
         if (fp32pair && pot->pair_eval == FIRE_PAIR_TABLE) b.nb_force = h->nb_tab_d;
     }
-    b.nb_verify = h->verify ? ceil_div(h->n, kForceBlock) : 0;
+    b.nb_verify = h->verify ? ceil_div((long long)h->n * b.tpa, kForceBlock) : 0;
     b.pass_role = h->verify ? 1 : 0;
     CKI(cudaMalloc(&b.x, n * sizeof(dvec4)));
     CKI(cudaMalloc(&b.v, n * sizeof(dvec4)));
@@ -942,7 +1007,10 @@ static fire_status init_handle(fire_handle_t** hp, const fire_system_t* sys,
         CKI(cudaMalloc(&b.rho, n * sizeof(double)));
         CKI(cudaMalloc(&b.fp, n * sizeof(double)));
     }
-    const size_t n_epart = (size_t)std::max(b.nb_force + b.nb_embed, b.nb_verify);
+    // room for the energy partials at the largest threads per atom
+    // (fire_set_threads_per_atom)
+    const int nb_max = ceil_div((long long)h->n * kMaxTpa, kForceBlock);
+    const size_t n_epart = (size_t)std::max(std::max(b.nb_force, nb_max) + b.nb_embed, nb_max);
     CKI(cudaMalloc(&b.epart, n_epart * sizeof(double)));
     // the FP32-pair table kernels write fewer energy partials than nb_force;
     // the rest stay 0
@@ -1099,6 +1167,23 @@ static fire_status run_minimize(fire_handle* h, const GeoC& g, double ftol, int6
     CK(h, cudaMemcpyAsync(h->h_state, h->b.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
     CK(h, cudaStreamSynchronize(s));
     return status_to_error(h, h->h_state->status);
+}
+
+fire_status fire_set_threads_per_atom(fire_handle_t* h, int32_t tpa, int32_t* chosen) {
+    if (!h) return FIRE_ERR_ARG;
+    if (h->batch) return fail(h, FIRE_ERR_ARG, "batched handle: use fire_batch_set_tuning");
+    if (tpa != 0 && tpa != 1 && tpa != 2 && tpa != 4 && tpa != kMaxTpa)
+        return fail(h, FIRE_ERR_ARG, "threads per atom must be 0 (automatic), 1, 2, 4 or 8");
+    const int t = !tpa_form(h->pot) ? 1 : tpa == 0 ? auto_tpa(h->pot, h->n, h->sms) : tpa;
+    if (t != h->b.tpa) {
+        drop_graph(h);
+        h->b.tpa = t;
+        if (!(h->pot.precision == FIRE_PREC_FP32_PAIR && h->pot.pair_eval == FIRE_PAIR_TABLE))
+            h->b.nb_force = ceil_div((long long)h->n * t, kForceBlock);
+        if (h->verify) h->b.nb_verify = ceil_div((long long)h->n * t, kForceBlock);
+    }
+    if (chosen) *chosen = t;
+    return FIRE_OK;
 }
 
 fire_status fire_set_exec_mode(fire_handle_t* h, int32_t mode, int32_t chunk) {
@@ -1624,19 +1709,17 @@ fire_status fire_profile_stages(fire_handle_t* h, const double* pos, const doubl
         cudaEventRecord(ev[1], s);
         const bool tab = rgl && h->pot.pair_eval == FIRE_PAIR_TABLE;
         if (tab && f32) k_density32_tab<<<h->nb_tab_d, kTabBlock, h->smem_d, s>>>(h->b, h->potc, g);
-        else if (tab && fixed64_half(h->pot))
-            k_density_ff<true><<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
-        else if (tab) k_density_ff<false><<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
-        else if (rgl && f32) k_density32<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
+        else if (tab && fixed64_half(h->pot)) density_ff<true>(h->b, h->potc, g, h->b.nb_force, s);
+        else if (tab) density_ff<false>(h->b, h->potc, g, h->b.nb_force, s);
+        else if (rgl && f32) density32(h->b, h->potc, g, s);
         else if (rgl) k_density<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
         cudaEventRecord(ev[2], s);
         if (h->b.nb_embed > 0) k_embed<<<h->b.nb_embed, kElemBlock, 0, s>>>(h->b);
         cudaEventRecord(ev[3], s);
         if (tab && f32) k_force32_tab<<<h->nb_tab_f, kTabBlock, h->smem_f, s>>>(h->b, h->potc, g);
-        else if (tab && fixed64_half(h->pot))
-            k_force_ff<true><<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
-        else if (tab) k_force_ff<false><<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
-        else if (rgl && f32) k_force32<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
+        else if (tab && fixed64_half(h->pot)) force_ff<true>(h->b, h->potc, g, h->b.nb_force, s);
+        else if (tab) force_ff<false>(h->b, h->potc, g, h->b.nb_force, s);
+        else if (rgl && f32) force32(h->b, h->potc, g, s);
         else if (rgl) k_force_rgl<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, g);
         else if (h->pot.kind == FIRE_POT_SW) k_force_sw<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
         else k_force_lj<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);

@@ -82,6 +82,22 @@ __device__ __forceinline__ double warp_max(double v) {
     return v;
 }
 
+// Sum over the TPA consecutive lanes that share one atom in the pair passes
+// (TPA = 1, 2, 4 or 8 threads per atom); every lane of the group receives
+// the total.  Only the group's own lanes are named in the mask, so groups
+// whose atom index is past the end may have left the kernel.
+template <int TPA>
+__device__ __forceinline__ double group_sum(double v) {
+    static_assert(TPA == 1 || TPA == 2 || TPA == 4 || TPA == 8, "threads per atom");
+    if (TPA > 1) {
+        const unsigned lane = threadIdx.x & 31u;
+        const unsigned gmask = ((1u << TPA) - 1u) << (lane & ~(unsigned)(TPA - 1));
+#pragma unroll
+        for (int o = TPA / 2; o > 0; o >>= 1) v += __shfl_xor_sync(gmask, v, o, TPA);
+    }
+    return v;
+}
+
 // Block-wide sum; result valid in thread 0.  `sh` holds >= 32 doubles.
 __device__ __forceinline__ double block_sum(double v, double* sh) {
     v = warp_sum(v);

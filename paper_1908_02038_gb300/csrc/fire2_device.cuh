@@ -71,6 +71,8 @@ struct DevState {
 struct Bufs {
     int n, cap, ncell;
     int nb_force, nb_embed, nb_red;
+    int tpa;               // threads per atom of the RGL pair passes that split an
+                           // atom's list (FP64 table form, FP32-pair analytic form)
     const uint8_t* dofmask;   // frozen components per atom (bit d = axis d), or NULL
     double* eatom;         // per-atom energy (images' energies), or NULL
     int accum;             // 1: forces and densities accumulate with atomics (cleared
@@ -740,7 +742,9 @@ __device__ __forceinline__ double vv_half_of(const DevState* st) {
 
 // Pass 1 (FP32-pair): rho_i, F'(rho_i) = -1/(2 sqrt(rho_i)) and the atom's
 // energy sum_j phi - sqrt(rho_i); the full list makes rho_i complete in one
-// thread, so the embedding step is fused here.
+// group of TPA threads (lane sums added in FP64), so the embedding step is
+// fused here.
+template <int TPA = 1>
 __global__ void __launch_bounds__(kForceBlock) k_density32(Bufs b, PotC P, GeoC g) {
     __shared__ int3 qt[125];
     __shared__ float et[kExp32TableSize];
@@ -750,11 +754,13 @@ __global__ void __launch_bounds__(kForceBlock) k_density32(Bufs b, PotC P, GeoC 
     for (int t = threadIdx.x; t < kExp32TableSize; t += blockDim.x) et[t] = b.exp32_table[t];
     __syncthreads();
     double e_atom = 0.0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < b.n; i += gridDim.x * blockDim.x) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t / TPA < b.n;
+         t += gridDim.x * blockDim.x) {
+        const int i = t / TPA, lane = t % TPA;
         const int4 qi = b.xq[i];
         const int m = b.nnbr[i];
         Kahan32 rho, erep;
-        for (int k = 0; k < m; ++k) {
+        for (int k = lane; k < m; k += TPA) {
             int dx, dy, dz, j;
             const long long r2q = pair_sep_q(b, qt, qi, b.nbr[(size_t)k * b.n + i], dx, dy, dz, j);
             if (r2q >= P.rc2q) continue;
@@ -763,12 +769,14 @@ __global__ void __launch_bounds__(kForceBlock) k_density32(Bufs b, PotC P, GeoC 
             rho.add(gg);
             erep.add(phi);
         }
-        const double rho_d = rho.value();
+        const double rho_d = group_sum<TPA>(rho.value());
+        const double erep_d = group_sum<TPA>(erep.value());
+        if (lane != 0) continue;
         const float rf = (float)rho_d;
         const float sq = sqrtf(rf);
         b.fp32[i] = rf > 0.f ? -0.5f / sq : 0.f;
         b.rho[i] = rho_d;
-        const double ei = erep.value() - (double)sq;
+        const double ei = erep_d - (double)sq;
         if (b.eatom) b.eatom[i] = ei;
         e_atom += ei;
     }
@@ -777,7 +785,9 @@ __global__ void __launch_bounds__(kForceBlock) k_density32(Bufs b, PotC P, GeoC 
 }
 
 // Pass 2 (FP32-pair): F_i = sum_j [2 phi' + (F'_i + F'_j) g'] (x_j - x_i) / r,
-// Kahan-compensated per component, written as FP64 (no atomics).
+// Kahan-compensated per component, written as FP64 (no atomics); TPA
+// threads per atom as in k_density32.
+template <int TPA = 1>
 __global__ void __launch_bounds__(kForceBlock) k_force32(Bufs b, PotC P, GeoC g) {
     __shared__ int3 qt[125];
     __shared__ float et[kExp32TableSize];
@@ -785,12 +795,14 @@ __global__ void __launch_bounds__(kForceBlock) k_force32(Bufs b, PotC P, GeoC g)
     fill_qshift_table(qt, g);
     for (int t = threadIdx.x; t < kExp32TableSize; t += blockDim.x) et[t] = b.exp32_table[t];
     __syncthreads();
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < b.n; i += gridDim.x * blockDim.x) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t / TPA < b.n;
+         t += gridDim.x * blockDim.x) {
+        const int i = t / TPA, lane = t % TPA;
         const int4 qi = b.xq[i];
         const float fpi = b.fp32[i];
         const int m = b.nnbr[i];
         Kahan32 fx, fy, fz;
-        for (int k = 0; k < m; ++k) {
+        for (int k = lane; k < m; k += TPA) {
             int dx, dy, dz, j;
             const long long r2q = pair_sep_q(b, qt, qi, b.nbr[(size_t)k * b.n + i], dx, dy, dz, j);
             if (r2q >= P.rc2q) continue;
@@ -801,7 +813,11 @@ __global__ void __launch_bounds__(kForceBlock) k_force32(Bufs b, PotC P, GeoC g)
             fy.add(fs * (float)dy);
             fz.add(fs * (float)dz);
         }
-        dvec4 f = make_dvec4(fx.value(), fy.value(), fz.value(), 0.0);
+        const double sx = group_sum<TPA>(fx.value());
+        const double sy = group_sum<TPA>(fy.value());
+        const double sz = group_sum<TPA>(fz.value());
+        if (lane != 0) continue;
+        dvec4 f = make_dvec4(sx, sy, sz, 0.0);
         mask_force(b, i, f);
         b.f[i] = f;
     }
@@ -862,8 +878,10 @@ __device__ __forceinline__ ffloat pair_sep_ff(const Bufs& b, const long long* qt
 // atom's energy sum_j phi - sqrt(rho_i), all in the atom's thread.  Half
 // list (HALF = true): rho_i and rho_j (FP64 atomics), 2 phi per pair credited
 // to i; k_embed then forms F'(rho) and the embedding energy.  Pairs
-// compressed below r0/2 fall back to the FP64 exponentials.
-template <bool HALF>
+// compressed below r0/2 fall back to the FP64 exponentials.  TPA threads
+// share an atom: lane l takes list slots l, l + TPA, ..., and the lanes'
+// sums are added in FP64 (group_sum) before lane 0 finishes the atom.
+template <bool HALF, int TPA = 1>
 __global__ void __launch_bounds__(kForceBlock) k_density_ff(Bufs b, PotC P, GeoC g) {
     __shared__ long long qt[375];
     __shared__ double etab[kExpTableSize];
@@ -872,13 +890,14 @@ __global__ void __launch_bounds__(kForceBlock) k_density_ff(Bufs b, PotC P, GeoC
     fill_qshift64_table(qt, g);
     for (int t = threadIdx.x; t < kExpTableSize; t += blockDim.x) etab[t] = b.exp_table[t];
     __syncthreads();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = t / TPA, lane = t % TPA;
     double e_atom = 0.0;
     if (i < b.n) {
         const lvec4 qi = b.xq64[i];
         const int m = b.nnbr[i];
         ffloat rho = {0.f, 0.f}, erep = {0.f, 0.f};
-        for (int k = 0; k < m; ++k) {
+        for (int k = lane; k < m; k += TPA) {
             ffloat dx, dy, dz;
             int j;
             const ffloat r2 = pair_sep_ff(b, qt, qi, b.nbr[(size_t)k * b.n + i], dx, dy, dz, j);
@@ -900,19 +919,20 @@ __global__ void __launch_bounds__(kForceBlock) k_density_ff(Bufs b, PotC P, GeoC
                 if (HALF) atomicAdd(&b.rho[j], gg);
             }
         }
-        if (HALF) {
-            atomicAdd(&b.rho[i], ff_to_f64(rho));
-            e_atom = 2.0 * ff_to_f64(erep);   // each pair's 2 phi credited to i
+        const double rho_d = group_sum<TPA>(ff_to_f64(rho));
+        const double erep_d = group_sum<TPA>(ff_to_f64(erep));
+        if (lane == 0 && HALF) {
+            atomicAdd(&b.rho[i], rho_d);
+            e_atom = 2.0 * erep_d;   // each pair's 2 phi credited to i
             if (b.eatom) b.eatom[i] = e_atom;
-        } else {
-            const double rho_d = ff_to_f64(rho);
+        } else if (lane == 0) {
             double sq, fp;
             rgl_embed(rho_d, sq, fp);
             b.rho[i] = rho_d;
             b.fp[i] = fp;
             const ffloat fpf = f64_to_ff(fp);
             b.fpff[i] = make_float2(fpf.hi, fpf.lo);
-            e_atom = ff_to_f64(erep) - sq;
+            e_atom = erep_d - sq;
             if (b.eatom) b.eatom[i] = e_atom;
         }
     }
@@ -922,7 +942,8 @@ __global__ void __launch_bounds__(kForceBlock) k_density_ff(Bufs b, PotC P, GeoC
 
 // Pass 2: F_i = sum_j [2 phi'/r + (F'_i + F'_j) g'/r] (x_j - x_i) (F = -grad E,
 // Sec. 2.1); full list: written whole; half list: F_i and F_j by FP64 atomics.
-template <bool HALF>
+// TPA threads per atom as in k_density_ff.
+template <bool HALF, int TPA = 1>
 __global__ void __launch_bounds__(kForceBlock) k_force_ff(Bufs b, PotC P, GeoC g) {
     __shared__ long long qt[375];
     __shared__ double etab[kExpTableSize];
@@ -930,8 +951,9 @@ __global__ void __launch_bounds__(kForceBlock) k_force_ff(Bufs b, PotC P, GeoC g
     fill_qshift64_table(qt, g);
     for (int t = threadIdx.x; t < kExpTableSize; t += blockDim.x) etab[t] = b.exp_table[t];
     __syncthreads();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= b.n) return;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = t / TPA, lane = t % TPA;
+    if (i >= b.n) return;   // the whole group leaves
     const lvec4 qi = b.xq64[i];
     const float2 fpi2 = b.fpff[i];
     const ffloat fpi = {fpi2.x, fpi2.y};
@@ -939,15 +961,15 @@ __global__ void __launch_bounds__(kForceBlock) k_force_ff(Bufs b, PotC P, GeoC g
     ffloat fx = {0.f, 0.f}, fy = {0.f, 0.f}, fz = {0.f, 0.f};
     // software pipeline: the next list entry, and the position and F' of its
     // atom, load while this pair is evaluated
-    uint32_t e_nx = m > 0 ? b.nbr[i] : 0u;
-    lvec4 q_nx = b.xq64[m > 0 ? (int)(e_nx & kIdxMask) : i];
-    float2 p_nx = b.fpff[m > 0 ? (int)(e_nx & kIdxMask) : i];
-    for (int k = 0; k < m; ++k) {
+    uint32_t e_nx = lane < m ? b.nbr[(size_t)lane * b.n + i] : 0u;
+    lvec4 q_nx = b.xq64[lane < m ? (int)(e_nx & kIdxMask) : i];
+    float2 p_nx = b.fpff[lane < m ? (int)(e_nx & kIdxMask) : i];
+    for (int k = lane; k < m; k += TPA) {
         const uint32_t e = e_nx;
         const lvec4 qj = q_nx;
         const float2 fpj2 = p_nx;
-        if (k + 1 < m) {
-            e_nx = b.nbr[(size_t)(k + 1) * b.n + i];
+        if (k + TPA < m) {
+            e_nx = b.nbr[(size_t)(k + TPA) * b.n + i];
             q_nx = b.xq64[e_nx & kIdxMask];
             p_nx = b.fpff[e_nx & kIdxMask];
         }
@@ -978,12 +1000,16 @@ __global__ void __launch_bounds__(kForceBlock) k_force_ff(Bufs b, PotC P, GeoC g
             atomicAdd(&b.f[j].z, -ff_to_f64(tz));
         }
     }
+    const double sx = group_sum<TPA>(ff_to_f64(fx));
+    const double sy = group_sum<TPA>(ff_to_f64(fy));
+    const double sz = group_sum<TPA>(ff_to_f64(fz));
+    if (lane != 0) return;
     if (HALF) {   // k_reduce applies the frozen-DOF mask
-        atomicAdd(&b.f[i].x, ff_to_f64(fx));
-        atomicAdd(&b.f[i].y, ff_to_f64(fy));
-        atomicAdd(&b.f[i].z, ff_to_f64(fz));
+        atomicAdd(&b.f[i].x, sx);
+        atomicAdd(&b.f[i].y, sy);
+        atomicAdd(&b.f[i].z, sz);
     } else {
-        dvec4 f = make_dvec4(ff_to_f64(fx), ff_to_f64(fy), ff_to_f64(fz), 0.0);
+        dvec4 f = make_dvec4(sx, sy, sz, 0.0);
         mask_force(b, i, f);
         b.f[i] = f;
     }
@@ -1095,36 +1121,66 @@ __global__ void k_reduce(Bufs b) {
     red_write(acc, red, b.rpart);
 }
 
-// Fixed-order reduction of `cnt` partials by one block (deterministic).
-__device__ double ctl_sum(const double* a, int cnt, double* sh) {
-    double s = 0.0;
-    for (int k = threadIdx.x; k < cnt; k += blockDim.x) s += a[k];
-    return block_sum(s, sh);
-}
-__device__ double ctl_max(const double* a, int cnt, double* sh) {
-    double s = 0.0;
-    for (int k = threadIdx.x; k < cnt; k += blockDim.x) s = fmax(s, a[k]);
-    return block_max(s, sh);
+// Fixed-order final reductions of the partials by one block (deterministic):
+// the sums of P, |F|^2, |v|^2 and E and the maxima of |F_i|^2 and |F_i,d|,
+// all six in one sweep so that their loads are in flight together.  Each
+// quantity is added up in the order of a block_sum / block_max of its own.
+struct CtlSums {
+    double P, F2, V2, fa2, fin, E;
+};
+__device__ __forceinline__ CtlSums ctl_reduce(const Bufs& b, int ne, double* sh /* 6 x 32 */) {
+    double a[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    const int nr = b.nb_red;
+    for (int k = threadIdx.x; k < nr; k += blockDim.x) {
+        a[0] += b.rpart[k];
+        a[1] += b.rpart[nr + k];
+        a[2] += b.rpart[2 * nr + k];
+        a[3] = fmax(a[3], b.rpart[3 * nr + k]);
+        a[4] = fmax(a[4], b.rpart[4 * nr + k]);
+    }
+    for (int k = threadIdx.x; k < ne; k += blockDim.x) a[5] += b.epart[k];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            const double t = __shfl_down_sync(0xffffffffu, a[q], o);
+            a[q] = (q == 3 || q == 4) ? fmax(a[q], t) : a[q] + t;
+        }
+    }
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < 6; ++q) sh[q * 32 + w] = a[q];
+    __syncthreads();
+    if (w == 0) {
+#pragma unroll
+        for (int q = 0; q < 6; ++q) a[q] = lane < (int)(blockDim.x >> 5) ? sh[q * 32 + lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+            for (int q = 0; q < 6; ++q) {
+                const double t = __shfl_down_sync(0xffffffffu, a[q], o);
+                a[q] = (q == 3 || q == 4) ? fmax(a[q], t) : a[q] + t;
+            }
+        }
+    }
+    return {a[0], a[1], a[2], a[3], a[4], a[5]};   // valid in thread 0
 }
 
 // Scalar FIRE 2.0 control (Algorithm 2, fire_control_step), one block: the
 // fixed-order final reductions, the error checks, then the convergence test
 // and the preparation of the next iteration; sets the WHILE condition.
 __global__ void k_control(Bufs b, int mode, cudaGraphConditionalHandle h, int has_handle) {
-    __shared__ double sh[32];
+    __shared__ double sh[6 * 32];
     // chunked execution runs loop bodies past the stop; they must not count
     if (mode == CTL_LOOP && b.st->done) {
         if (has_handle && threadIdx.x == 0) cudaGraphSetConditional(h, 0u);
         return;
     }
-    const double P = ctl_sum(b.rpart + 0 * b.nb_red, b.nb_red, sh);
-    const double F2 = ctl_sum(b.rpart + 1 * b.nb_red, b.nb_red, sh);
-    const double V2 = ctl_sum(b.rpart + 2 * b.nb_red, b.nb_red, sh);
-    const double fa2 = ctl_max(b.rpart + 3 * b.nb_red, b.nb_red, sh);
-    const double fin = ctl_max(b.rpart + 4 * b.nb_red, b.nb_red, sh);
     const int ne = b.st->vstate >= 2 ? b.nb_verify : b.nb_force + b.nb_embed;
-    const double E = ctl_sum(b.epart, ne, sh);
+    const CtlSums r = ctl_reduce(b, ne, sh);
     if (threadIdx.x != 0) return;
+    const double P = r.P, F2 = r.F2, V2 = r.V2, fa2 = r.fa2, fin = r.fin, E = r.E;
     DevState& s = *b.st;
     s.P = P;
     s.F2 = F2;

@@ -38,7 +38,7 @@ def test_library_exports_every_header_symbol(lib):
 
 
 def test_abi_version_and_defaults(lib):
-    assert fg.fire_abi_version() == 7
+    assert fg.fire_abi_version() == 8
     p = fg.fire_default_params(0.001)
     assert (p.tmax, p.tmin, p.dtgrow, p.dtshrink, p.alpha0, p.alphashrink) == \
         (10.0, 0.02, 1.1, 0.5, 0.25, 0.99)
