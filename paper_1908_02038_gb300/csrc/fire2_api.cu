@@ -367,8 +367,7 @@ void launch_forces(fire_handle* h, const GeoC& g, cudaStream_t s, bool confirm_p
     (void)n;
 }
 
-// The FP32-pair force kernels write whole forces and produce the (F, v)
-// reductions themselves; the atomic-accumulating paths need this pass.
+// Device constants of a NEB handle's projection and reduction kernels.
 NebC neb_consts(const fire_handle* h) {
     const NebState& q = *h->neb;
     NebC c;

@@ -7,7 +7,7 @@
 //     -> [k_cell_zero/count/scan/fill/sort -> k_nbr_build, only when an atom
 //         moved > skin/2: a graph IF node set by k_update's last block]
 //     -> FP64:  k_density(_tab) -> k_embed -> k_force_rgl -> k_reduce
-//        FP32-pair: k_density32(_tab) -> k_force32(_tab) (reductions fused)
+//        FP32-pair: k_density32(_tab) -> k_force32(_tab) -> k_reduce
 //        LJ:    k_force_lj -> k_reduce
 //     -> k_control
 //
@@ -76,8 +76,7 @@ struct Bufs {
     const uint8_t* dofmask;   // frozen components per atom (bit d = axis d), or NULL
     double* eatom;         // per-atom energy (images' energies), or NULL
     int accum;             // 1: forces and densities accumulate with atomics (cleared
-                           //    by k_update); 0: force kernels write them whole and
-                           //    also produce the (F, v) reductions
+                           //    by k_update); 0: force kernels write them whole
     dvec4 *x, *v, *f, *xref;
     float4* xf;            // FP32 copy of x for the list build
     int4* xq;              // FP32-pair form: x in fixed point (qscale units), modulo 2^32
@@ -693,6 +692,15 @@ struct RedAcc {
     double P = 0.0, F2 = 0.0, V2 = 0.0, fa2 = 0.0, fin = 0.0;
 };
 
+// max(a, b) of non-negative doubles (NaN propagates: its pattern is larger
+// than that of +inf) and |x|, both on the integer pipes.
+__device__ __forceinline__ double max_nonneg(double a, double b) {
+    return __longlong_as_double(max(__double_as_longlong(a), __double_as_longlong(b)));
+}
+__device__ __forceinline__ double abs_bits(double x) {
+    return __longlong_as_double(__double_as_longlong(x) & 0x7fffffffffffffffll);
+}
+
 // Zeroes the frozen components of f (if any); true when f changed.
 __device__ __forceinline__ bool mask_force(const Bufs& b, int i, dvec4& f) {
     if (!b.dofmask) return false;
@@ -704,21 +712,24 @@ __device__ __forceinline__ bool mask_force(const Bufs& b, int i, dvec4& f) {
 }
 
 // Reductions of atom i's (F, v); f must be masked already.
-__device__ __forceinline__ void red_atom(const Bufs& b, int i, const dvec4& f, double vv_half,
-                                         RedAcc& a) {
-    dvec4 v = b.v[i];
+__device__ __forceinline__ void red_atom(const Bufs& b, int i, const dvec4& f, dvec4 v,
+                                         double vv_half, RedAcc& a) {
     if (vv_half != 0.0) {   // second half kick of velocity Verlet, with the new force
         v.x += vv_half * f.x;
         v.y += vv_half * f.y;
         v.z += vv_half * f.z;
         b.v[i] = v;
     }
-    a.P += f.x * v.x + f.y * v.y + f.z * v.z;
-    const double q = f.x * f.x + f.y * f.y + f.z * f.z;
+    // FP64 arithmetic runs at 1/58 of the FP32 rate on this part and bounds
+    // this pass: the sums P and |v|^2 chain their products into the running
+    // sum (3 FMAs each), and the maxima of non-negative values compare the
+    // IEEE bit patterns as integers, which order the same way
+    a.P = fma(f.z, v.z, fma(f.y, v.y, fma(f.x, v.x, a.P)));
+    const double q = fma(f.z, f.z, fma(f.y, f.y, f.x * f.x));
     a.F2 += q;
-    a.V2 += v.x * v.x + v.y * v.y + v.z * v.z;
-    a.fa2 = fmax(a.fa2, q);
-    a.fin = fmax(a.fin, fmax(fabs(f.x), fmax(fabs(f.y), fabs(f.z))));
+    a.V2 = fma(v.z, v.z, fma(v.y, v.y, fma(v.x, v.x, a.V2)));
+    a.fa2 = max_nonneg(a.fa2, q);
+    a.fin = max_nonneg(a.fin, max_nonneg(abs_bits(f.x), max_nonneg(abs_bits(f.y), abs_bits(f.z))));
 }
 
 __device__ __forceinline__ void red_write(const RedAcc& a, double* red, double* rpart) {
@@ -1116,7 +1127,7 @@ __global__ void k_reduce(Bufs b) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < b.n; i += gridDim.x * blockDim.x) {
         dvec4 f = b.f[i];
         if (mask_force(b, i, f)) b.f[i] = f;
-        red_atom(b, i, f, vvh, acc);
+        red_atom(b, i, f, b.v[i], vvh, acc);
     }
     red_write(acc, red, b.rpart);
 }
@@ -1271,6 +1282,7 @@ __global__ void k_update(Bufs b, GeoC g, cudaGraphConditionalHandle hif, int has
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < b.n; i += gridDim.x * blockDim.x) {
         dvec4 x = b.x[i], v = b.v[i];
         const dvec4 f = b.f[i];
+        const dvec4 r = b.xref[i];   // loaded with the rest, before the stores
         if (after_pre)
             fire_update_drift(s, dt, x, v, f);
         else
@@ -1287,7 +1299,6 @@ __global__ void k_update(Bufs b, GeoC g, cudaGraphConditionalHandle hif, int has
             b.f[i] = make_dvec4(0.0, 0.0, 0.0, 0.0);
             if (b.rho) b.rho[i] = 0.0;
         }
-        const dvec4 r = b.xref[i];
         const float ddx = f64_to_f32_trunc(x.x) - f64_to_f32_trunc(r.x);
         const float ddy = f64_to_f32_trunc(x.y) - f64_to_f32_trunc(r.y);
         const float ddz = f64_to_f32_trunc(x.z) - f64_to_f32_trunc(r.z);

@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(kNebBlock) k_neb_project(Bufs b, GeoC g, NebC 
         f.z += o[2] * (o[0] * tp[2] + o[1] * tm[2]);
         mask_force(b, gi, f);
         b.f[gi] = f;
-        red_atom(b, gi, f, vvh, acc);
+        red_atom(b, gi, f, b.v[gi], vvh, acc);
     }
     red_write(acc, red, b.rpart);
 }
