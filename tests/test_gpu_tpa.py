@@ -121,3 +121,49 @@ def test_threads_per_atom_choice_and_errors():
                       dt_start=fi.CU_DT) as b:
         with pytest.raises(fg.FireError):
             fg.fire_set_threads_per_atom(b.h, 2)
+
+
+@pytest.mark.parametrize("check", [fg.FIRE_FP64_CHECK_CONFIRM, fg.FIRE_FP64_CHECK_FINISH])
+def test_fp32pair_split_lists_graph_and_chunked_runs_are_identical(check):
+    # full lists, fixed per-atom sum order: the graph loop and the chunked
+    # loop follow the same trajectory bit for bit at 4 threads per atom,
+    # through the FP64 confirmations (full-list FP64 passes, also split)
+    c = fi.rgl_vacancy_box(ncell=8, seed=36, n_vac=4, sigma=0.1)
+    with fg.FireHandle(c.n, fi.CU_MASS, rgl_pot("fp32pair"), dt_start=fi.CU_DT,
+                       confirm64=check) as h:
+        assert h.set_threads_per_atom(4) == 4
+        x1 = c.x.copy()
+        r1 = h.minimize(x1, c.box, 1e-6, 100000)
+        h.set_exec_mode(fg.FIRE_EXEC_CHUNKED, 16)
+        x2 = c.x.copy()
+        r2 = h.minimize(x2, c.box, 1e-6, 100000)
+    assert r1.stop == r2.stop == fg.FIRE_STOP_FTOL
+    assert (r1.iterations, r1.nbr_builds, r1.force_evals) == (r2.iterations, r2.nbr_builds,
+                                                               r2.force_evals)
+    if check == fg.FIRE_FP64_CHECK_CONFIRM:   # the stop was confirmed in FP64
+        assert r1.force_evals > r1.iterations + 1
+    assert r1.energy == r2.energy and np.array_equal(x1, x2)
+
+
+@pytest.mark.parametrize("form", ["fp64_half", "fp32pair"])
+def test_frozen_components_with_split_lists(form):
+    c = fi.rgl_vacancy_box(ncell=6, seed=37, n_vac=3, sigma=0.05)
+    fz = np.zeros(c.n, np.uint8)
+    fz[c.x[:, 0] < 4.0] = 3               # frozen in x and y
+    fz[c.x[:, 0] > c.box[0] - 3.0] = 4    # frozen in z
+    xo, ro, _ = oracle.fire2(c.x, c.box, ora_rgl(), oracle.Params(dt_start=fi.CU_DT), fi.CU_MASS,
+                             1e-6, 100000, frozen=fz)
+    x = c.x.copy()
+    with fg.FireHandle(c.n, fi.CU_MASS, rgl_pot(form), dt_start=fi.CU_DT) as h:
+        assert h.set_threads_per_atom(2) == 2
+        h.set_dof_mask(fz)
+        r = h.minimize(x, c.box, 1e-6, 100000)
+    for d in range(3):
+        sel = (fz >> d) & 1 == 1
+        assert np.array_equal(x[sel, d], c.x[sel, d]), d
+    assert r.stop == fg.FIRE_STOP_FTOL and ro.stop == oracle.STOP_FTOL
+    if form == "fp32pair":
+        assert abs(r.energy - ro.energy) / c.n < E32_PER_ATOM
+    else:
+        assert abs(r.energy - ro.energy) / c.n < 1e-8
+        assert abs(r.iterations - ro.iterations) <= max(2, 0.05 * ro.iterations)
