@@ -165,11 +165,13 @@ constexpr int kMaxTpa = 8;
 // 135 / 126 / 119 / 122, 128,277 atoms 187 / 194 / 189 / 204, 997,450 atoms
 // 986 / 1031 / 1090 / 1307; FP32-pair form 29,931 atoms 108 / 81 / 73 / 78,
 // 59,762 atoms 115 / 92 / 92 / 102, 997,450 atoms 652 / 680 / 753 / 963.
-int auto_tpa(const fire_potential_t& p, long long n, int sms) {
-    const long long want = (long long)sms * (p.precision == FIRE_PREC_FP32_PAIR ? 512 : 1024);
+int tpa_for(long long n, int sms, int per_sm) {
     int t = 1;
-    while (t < kMaxTpa && n * t < want) t *= 2;
+    while (t < kMaxTpa && n * t < (long long)sms * per_sm) t *= 2;
     return t;
+}
+int auto_tpa(const fire_potential_t& p, long long n, int sms) {
+    return tpa_for(n, sms, p.precision == FIRE_PREC_FP32_PAIR ? 512 : 1024);
 }
 
 // Neighbour geometry for a box.  The list radius is rc + skin, with the skin
@@ -323,6 +325,24 @@ void force32(const Bufs& b, const PotC& P, const GeoC& g, cudaStream_t s) {
     case 4: k_force32<4><<<b.nb_force, kForceBlock, 0, s>>>(b, P, g); break;
     case 2: k_force32<2><<<b.nb_force, kForceBlock, 0, s>>>(b, P, g); break;
     default: k_force32<1><<<b.nb_force, kForceBlock, 0, s>>>(b, P, g);
+    }
+}
+
+// The two passes of the cached Hessian-vector product, TPA threads per atom.
+template <int TPA>
+void hvp_cached_t(const GradBufs& b, const GeoL& L, const double* u, double* hu, const int* skip,
+                  int n, cudaStream_t s) {
+    const int nb = ceil_div((long long)n * TPA, kForceBlock);
+    k_g_hvp1c<TPA><<<nb, kForceBlock, 0, s>>>(b, L, u, skip);
+    k_g_hvp2c<TPA><<<nb, kForceBlock, 0, s>>>(b, L, u, hu, skip);
+}
+void hvp_cached(const GradBufs& b, const GeoL& L, const double* u, double* hu, const int* skip,
+                int tpa, int n, cudaStream_t s) {
+    switch (tpa) {
+    case 8: hvp_cached_t<8>(b, L, u, hu, skip, n, s); break;
+    case 4: hvp_cached_t<4>(b, L, u, hu, skip, n, s); break;
+    case 2: hvp_cached_t<2>(b, L, u, hu, skip, n, s); break;
+    default: hvp_cached_t<1>(b, L, u, hu, skip, n, s);
     }
 }
 
@@ -1613,12 +1633,14 @@ fire_status fire_rgl_implicit_grad_dev(fire_handle_t* h, const double* d_pos, co
     CK(h, cudaMemcpyAsync(gs.cs, gs.h_cs, sizeof(CgState), cudaMemcpyHostToDevice, s));
     GeoL L{{box[0], box[1], box[2]}};
     const int* skip = &gs.cs->done;
+    // the cached HVP passes are FP64 pair loops like the force passes: split
+    // each atom's list over several threads on small systems
+    const int tpa = tpa_for(n, h->sms, 1024);
     constexpr int kCgBatch = 16;
     int done = c0.done;
     while (!done) {
         for (int c = 0; c < kCgBatch; ++c) {
-            k_g_hvp1c<<<gs.nb, kForceBlock, 0, s>>>(b, L, p, skip);
-            k_g_hvp2c<<<gs.nb, kForceBlock, 0, s>>>(b, L, p, Ap, skip);
+            hvp_cached(b, L, p, Ap, skip, tpa, n, s);
             k_cg_colsum<<<nb, kElemBlock, 0, s>>>(n, gs.cs, Ap, gs.part);
             k_cg_means<<<1, kElemBlock, 0, s>>>(gs.cs, gs.part, nb, n);
             k_cg_project_dot<<<nb, kElemBlock, 0, s>>>(n, gs.cs, Ap, p, gs.part);

@@ -328,6 +328,7 @@ __global__ void __launch_bounds__(kForceBlock) k_g_pair_cache(GradBufs g, PotC P
 }
 
 // HVP pass 1 from the pair cache.
+template <int TPA>
 __global__ void __launch_bounds__(kForceBlock) k_g_hvp1c(GradBufs g, GeoL L, const double* u,
                                                          const int* skip) {
     __shared__ double3 tbl[125];
@@ -337,13 +338,14 @@ __global__ void __launch_bounds__(kForceBlock) k_g_hvp1c(GradBufs g, GeoL L, con
         tbl[t] = make_double3(sx * L.L[0], sy * L.L[1], sz * L.L[2]);
     }
     __syncthreads();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = t / TPA, lane = t % TPA;   // TPA threads per atom (group_sum)
     if (i >= g.n) return;
     const dvec4 xi = g.x[i];
     const double* ui = u + 3 * (size_t)i;
     double acc = 0.0;
     const int m = g.nnbr[i];
-    for (int k = 0; k < m; ++k) {
+    for (int k = lane; k < m; k += TPA) {
         const size_t slot = (size_t)k * g.n + i;
         const double w = g.w1[slot];
         if (w == 0.0) continue;
@@ -353,10 +355,12 @@ __global__ void __launch_bounds__(kForceBlock) k_g_hvp1c(GradBufs g, GeoL L, con
         const double* uj = u + 3 * (size_t)j;
         acc += w * (dx * (uj[0] - ui[0]) + dy * (uj[1] - ui[1]) + dz * (uj[2] - ui[2]));
     }
-    g.drho[i] = acc;
+    acc = group_sum<TPA>(acc);
+    if (lane == 0) g.drho[i] = acc;
 }
 
 // HVP pass 2 from the pair cache: (H u)_i = -dF_i.
+template <int TPA>
 __global__ void __launch_bounds__(kForceBlock) k_g_hvp2c(GradBufs g, GeoL L, const double* u,
                                                          double* hu, const int* skip) {
     __shared__ double3 tbl[125];
@@ -366,14 +370,15 @@ __global__ void __launch_bounds__(kForceBlock) k_g_hvp2c(GradBufs g, GeoL L, con
         tbl[t] = make_double3(sx * L.L[0], sy * L.L[1], sz * L.L[2]);
     }
     __syncthreads();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = t / TPA, lane = t % TPA;
     if (i >= g.n) return;
     const dvec4 xi = g.x[i];
     const double* ui = u + 3 * (size_t)i;
     const double dci = g.F2[i] * g.drho[i];
     double dF[3] = {0, 0, 0};
     const int m = g.nnbr[i];
-    for (int k = 0; k < m; ++k) {
+    for (int k = lane; k < m; k += TPA) {
         const size_t slot = (size_t)k * g.n + i;
         const double fs = g.fsc[slot];
         if (fs == 0.0 && g.w1[slot] == 0.0) continue;
@@ -387,6 +392,9 @@ __global__ void __launch_bounds__(kForceBlock) k_g_hvp2c(GradBufs g, GeoL L, con
 #pragma unroll
         for (int a = 0; a < 3; ++a) dF[a] += dfs * d[a] + fs * du[a];
     }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) dF[a] = group_sum<TPA>(dF[a]);
+    if (lane != 0) return;
     double* h = hu + 3 * (size_t)i;
     h[0] = -dF[0];
     h[1] = -dF[1];
