@@ -1638,22 +1638,37 @@ fire_status fire_rgl_implicit_grad_dev(fire_handle_t* h, const double* d_pos, co
     const int tpa = tpa_for(n, h->sms, 1024);
     constexpr int kCgBatch = 16;
     int done = c0.done;
+    // the kCgBatch iterations between two reads of the state form one CUDA
+    // graph (the pointers stay fixed for the whole solve), launched on s
+    cudaGraphExec_t batch = nullptr;
+    if (!done) {
+        CK(h, cudaStreamSynchronize(s));   // the set-up above is complete before the graph runs
+        st = capture_plain(h, &batch, [&](cudaStream_t cs) {
+            for (int c = 0; c < kCgBatch; ++c) {
+                hvp_cached(b, L, p, Ap, skip, tpa, n, cs);
+                k_cg_colsum<<<nb, kElemBlock, 0, cs>>>(n, gs.cs, Ap, gs.part);
+                k_cg_means<<<1, kElemBlock, 0, cs>>>(gs.cs, gs.part, nb, n);
+                k_cg_project_dot<<<nb, kElemBlock, 0, cs>>>(n, gs.cs, Ap, p, gs.part);
+                k_cg_alpha<<<1, kElemBlock, 0, cs>>>(gs.cs, gs.part, nb);
+                k_cg_step<<<nb, kElemBlock, 0, cs>>>(m, gs.cs, p, Ap, lam, r, gs.part);
+                k_cg_beta<<<1, kElemBlock, 0, cs>>>(gs.cs, gs.part, nb);
+                k_cg_dir<<<nb, kElemBlock, 0, cs>>>(m, gs.cs, r, p);
+            }
+        });
+        if (st != FIRE_OK) return st;
+    }
     while (!done) {
-        for (int c = 0; c < kCgBatch; ++c) {
-            hvp_cached(b, L, p, Ap, skip, tpa, n, s);
-            k_cg_colsum<<<nb, kElemBlock, 0, s>>>(n, gs.cs, Ap, gs.part);
-            k_cg_means<<<1, kElemBlock, 0, s>>>(gs.cs, gs.part, nb, n);
-            k_cg_project_dot<<<nb, kElemBlock, 0, s>>>(n, gs.cs, Ap, p, gs.part);
-            k_cg_alpha<<<1, kElemBlock, 0, s>>>(gs.cs, gs.part, nb);
-            k_cg_step<<<nb, kElemBlock, 0, s>>>(m, gs.cs, p, Ap, lam, r, gs.part);
-            k_cg_beta<<<1, kElemBlock, 0, s>>>(gs.cs, gs.part, nb);
-            k_cg_dir<<<nb, kElemBlock, 0, s>>>(m, gs.cs, r, p);
+        cudaError_t e = cudaGraphLaunch(batch, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(gs.h_cs, gs.cs, sizeof(CgState), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            cudaGraphExecDestroy(batch);
+            return fail(h, FIRE_ERR_CUDA, "conjugate-gradient batch: %s", cudaGetErrorString(e));
         }
-        CK(h, cudaGetLastError());
-        CK(h, cudaMemcpyAsync(gs.h_cs, gs.cs, sizeof(CgState), cudaMemcpyDeviceToHost, s));
-        CK(h, cudaStreamSynchronize(s));
         done = gs.h_cs->done;
     }
+    if (batch) cudaGraphExecDestroy(batch);
     const int64_t it = gs.h_cs->it;
     k_g_force<<<h->grad.nb, kForceBlock, 0, s>>>(b, pc, L, h->b.exp_table, nullptr, nullptr, lam);
     CK(h, cudaGetLastError());
