@@ -330,19 +330,19 @@ void force32(const Bufs& b, const PotC& P, const GeoC& g, cudaStream_t s) {
 
 // The two passes of the cached Hessian-vector product, TPA threads per atom.
 template <int TPA>
-void hvp_cached_t(const GradBufs& b, const GeoL& L, const double* u, double* hu, const int* skip,
-                  int n, cudaStream_t s) {
+void hvp_cached_t(const GradBufs& b, const double* u, double* hu, const int* skip, int n,
+                  cudaStream_t s) {
     const int nb = ceil_div((long long)n * TPA, kForceBlock);
-    k_g_hvp1c<TPA><<<nb, kForceBlock, 0, s>>>(b, L, u, skip);
-    k_g_hvp2c<TPA><<<nb, kForceBlock, 0, s>>>(b, L, u, hu, skip);
+    k_g_hvp1c<TPA><<<nb, kForceBlock, 0, s>>>(b, u, skip);
+    k_g_hvp2c<TPA><<<nb, kForceBlock, 0, s>>>(b, u, hu, skip);
 }
-void hvp_cached(const GradBufs& b, const GeoL& L, const double* u, double* hu, const int* skip,
-                int tpa, int n, cudaStream_t s) {
+void hvp_cached(const GradBufs& b, const double* u, double* hu, const int* skip, int tpa, int n,
+                cudaStream_t s) {
     switch (tpa) {
-    case 8: hvp_cached_t<8>(b, L, u, hu, skip, n, s); break;
-    case 4: hvp_cached_t<4>(b, L, u, hu, skip, n, s); break;
-    case 2: hvp_cached_t<2>(b, L, u, hu, skip, n, s); break;
-    default: hvp_cached_t<1>(b, L, u, hu, skip, n, s);
+    case 8: hvp_cached_t<8>(b, u, hu, skip, n, s); break;
+    case 4: hvp_cached_t<4>(b, u, hu, skip, n, s); break;
+    case 2: hvp_cached_t<2>(b, u, hu, skip, n, s); break;
+    default: hvp_cached_t<1>(b, u, hu, skip, n, s);
     }
 }
 
@@ -1583,7 +1583,7 @@ fire_status fire_rgl_implicit_grad_dev(fire_handle_t* h, const double* d_pos, co
     if (st != FIRE_OK) return st;
     const int n = h->n, m = 3 * n;
     // the positions are fixed for the whole solve: cache the pair
-    // coefficients of the HVP once (3 doubles per list slot)
+    // coefficients of the HVP and the separations once (6 doubles per slot)
     {
         GradState& gs = h->grad;
         const size_t slots = (size_t)gs.cap * n;
@@ -1591,18 +1591,25 @@ fire_status fire_rgl_implicit_grad_dev(fire_handle_t* h, const double* d_pos, co
             cudaFree(gs.pcache);
             gs.pcache = nullptr;
             gs.pcache_slots = 0;
-            CK(h, cudaMalloc(&gs.pcache, 3 * slots * sizeof(double)));
+            CK(h, cudaMalloc(&gs.pcache, 6 * slots * sizeof(double)));
             gs.pcache_slots = slots;
         }
         double* w1 = gs.pcache;
         double* fsc = w1 + slots;
         double* a2 = fsc + slots;
+        double* dcx = a2 + slots;
+        double* dcy = dcx + slots;
+        double* dcz = dcy + slots;
         GeoL L{{box[0], box[1], box[2]}};
-        k_g_pair_cache<<<gs.nb, kForceBlock, 0, s>>>(b, pc, L, h->b.exp_table, w1, fsc, a2);
+        k_g_pair_cache<<<gs.nb, kForceBlock, 0, s>>>(b, pc, L, h->b.exp_table, w1, fsc, a2,
+                                                      dcx, dcy, dcz);
         CK(h, cudaGetLastError());
         b.w1 = w1;
         b.fsc = fsc;
         b.a2 = a2;
+        b.dcx = dcx;
+        b.dcy = dcy;
+        b.dcz = dcz;
     }
     const size_t bytes = (size_t)m * sizeof(double);
     double* r = h->grad.vec;
@@ -1645,7 +1652,7 @@ fire_status fire_rgl_implicit_grad_dev(fire_handle_t* h, const double* d_pos, co
         CK(h, cudaStreamSynchronize(s));   // the set-up above is complete before the graph runs
         st = capture_plain(h, &batch, [&](cudaStream_t cs) {
             for (int c = 0; c < kCgBatch; ++c) {
-                hvp_cached(b, L, p, Ap, skip, tpa, n, cs);
+                hvp_cached(b, p, Ap, skip, tpa, n, cs);
                 k_cg_colsum<<<nb, kElemBlock, 0, cs>>>(n, gs.cs, Ap, gs.part);
                 k_cg_means<<<1, kElemBlock, 0, cs>>>(gs.cs, gs.part, nb, n);
                 k_cg_project_dot<<<nb, kElemBlock, 0, cs>>>(n, gs.cs, Ap, p, gs.part);

@@ -31,6 +31,7 @@ struct GradBufs {
     // pair coefficients of the HVP at fixed positions (k_g_pair_cache), one
     // per list slot [k * n + i]; NULL when not computed
     const double *w1, *fsc, *a2;
+    const double *dcx, *dcy, *dcz;   // cached separation x_j - x_i per list slot
 };
 
 struct Pair2 {
@@ -292,11 +293,15 @@ __global__ void __launch_bounds__(kForceBlock) k_g_hvp2(GradBufs g, PotC P, GeoL
 // per list slot w1 = g'/r, fs = [2 phi' + (F'_i + F'_j) g'] / r and
 // a2 = [2 phi'' + (F'_i + F'_j) g'' - fs] / r^2, zero beyond rc.  With them
 // dfs = a2 d.(u_j - u_i) + (F''_i drho_i + F''_j drho_j) w1 (HVP pass 2) and
-// drho_i = sum_j w1 d.(u_j - u_i) (pass 1) need no pair function.
+// drho_i = sum_j w1 d.(u_j - u_i) (pass 1) need no pair function.  The
+// separation d = x_j - x_i of each slot is cached too: the HVP passes then
+// stream it instead of gathering x_j and redoing the minimum image (six FP64
+// instructions per pair and pass at 1/58 of the FP32 rate).
 __global__ void __launch_bounds__(kForceBlock) k_g_pair_cache(GradBufs g, PotC P, GeoL L,
                                                               const double* exp_table,
                                                               double* w1, double* fsc,
-                                                              double* a2) {
+                                                              double* a2, double* dcx,
+                                                              double* dcy, double* dcz) {
     __shared__ double3 tbl[125];
     __shared__ double etab[kExpTableSize];
     grad_tables(tbl, etab, exp_table, L.L);
@@ -311,6 +316,9 @@ __global__ void __launch_bounds__(kForceBlock) k_g_pair_cache(GradBufs g, PotC P
         int j;
         double dx, dy, dz;
         const double r2 = grad_pair_vec(g, tbl, xi, g.nbr[slot], j, dx, dy, dz);
+        dcx[slot] = dx;
+        dcy[slot] = dy;
+        dcz[slot] = dz;
         if (!(r2 < P.rc2)) {
             w1[slot] = 0.0;
             fsc[slot] = 0.0;
@@ -329,19 +337,12 @@ __global__ void __launch_bounds__(kForceBlock) k_g_pair_cache(GradBufs g, PotC P
 
 // HVP pass 1 from the pair cache.
 template <int TPA>
-__global__ void __launch_bounds__(kForceBlock) k_g_hvp1c(GradBufs g, GeoL L, const double* u,
+__global__ void __launch_bounds__(kForceBlock) k_g_hvp1c(GradBufs g, const double* u,
                                                          const int* skip) {
-    __shared__ double3 tbl[125];
     if (skip && *skip) return;   // a finished conjugate-gradient solve
-    for (int t = threadIdx.x; t < 125; t += blockDim.x) {
-        const int sx = t % 5 - 2, sy = (t / 5) % 5 - 2, sz = t / 25 - 2;
-        tbl[t] = make_double3(sx * L.L[0], sy * L.L[1], sz * L.L[2]);
-    }
-    __syncthreads();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = t / TPA, lane = t % TPA;   // TPA threads per atom (group_sum)
     if (i >= g.n) return;
-    const dvec4 xi = g.x[i];
     const double* ui = u + 3 * (size_t)i;
     double acc = 0.0;
     const int m = g.nnbr[i];
@@ -349,9 +350,8 @@ __global__ void __launch_bounds__(kForceBlock) k_g_hvp1c(GradBufs g, GeoL L, con
         const size_t slot = (size_t)k * g.n + i;
         const double w = g.w1[slot];
         if (w == 0.0) continue;
-        int j;
-        double dx, dy, dz;
-        grad_pair_vec(g, tbl, xi, g.nbr[slot], j, dx, dy, dz);
+        const int j = (int)(g.nbr[slot] & kIdxMask);
+        const double dx = g.dcx[slot], dy = g.dcy[slot], dz = g.dcz[slot];
         const double* uj = u + 3 * (size_t)j;
         acc += w * (dx * (uj[0] - ui[0]) + dy * (uj[1] - ui[1]) + dz * (uj[2] - ui[2]));
     }
@@ -361,19 +361,12 @@ __global__ void __launch_bounds__(kForceBlock) k_g_hvp1c(GradBufs g, GeoL L, con
 
 // HVP pass 2 from the pair cache: (H u)_i = -dF_i.
 template <int TPA>
-__global__ void __launch_bounds__(kForceBlock) k_g_hvp2c(GradBufs g, GeoL L, const double* u,
-                                                         double* hu, const int* skip) {
-    __shared__ double3 tbl[125];
+__global__ void __launch_bounds__(kForceBlock) k_g_hvp2c(GradBufs g, const double* u, double* hu,
+                                                         const int* skip) {
     if (skip && *skip) return;
-    for (int t = threadIdx.x; t < 125; t += blockDim.x) {
-        const int sx = t % 5 - 2, sy = (t / 5) % 5 - 2, sz = t / 25 - 2;
-        tbl[t] = make_double3(sx * L.L[0], sy * L.L[1], sz * L.L[2]);
-    }
-    __syncthreads();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = t / TPA, lane = t % TPA;
     if (i >= g.n) return;
-    const dvec4 xi = g.x[i];
     const double* ui = u + 3 * (size_t)i;
     const double dci = g.F2[i] * g.drho[i];
     double dF[3] = {0, 0, 0};
@@ -382,9 +375,8 @@ __global__ void __launch_bounds__(kForceBlock) k_g_hvp2c(GradBufs g, GeoL L, con
         const size_t slot = (size_t)k * g.n + i;
         const double fs = g.fsc[slot];
         if (fs == 0.0 && g.w1[slot] == 0.0) continue;
-        int j;
-        double d[3];
-        grad_pair_vec(g, tbl, xi, g.nbr[slot], j, d[0], d[1], d[2]);
+        const int j = (int)(g.nbr[slot] & kIdxMask);
+        const double d[3] = {g.dcx[slot], g.dcy[slot], g.dcz[slot]};
         const double* uj = u + 3 * (size_t)j;
         const double du[3] = {uj[0] - ui[0], uj[1] - ui[1], uj[2] - ui[2]};
         const double dd = d[0] * du[0] + d[1] * du[1] + d[2] * du[2];
