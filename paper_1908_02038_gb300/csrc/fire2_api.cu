@@ -1512,8 +1512,26 @@ fire_status fire_rgl_energy_grad_dev(fire_handle_t* h, const double* d_pos, cons
 static void launch_hvp(fire_handle* h, const GradBufs& b, const PotC& pc, const double box[3],
                        const double* u, double* hu, cudaStream_t s) {
     GeoL L{{box[0], box[1], box[2]}};
-    k_g_hvp1<<<h->grad.nb, kForceBlock, 0, s>>>(b, pc, L, h->b.exp_table, u);
-    k_g_hvp2<<<h->grad.nb, kForceBlock, 0, s>>>(b, pc, L, h->b.exp_table, u, hu);
+    const int tpa = tpa_for(h->n, h->sms, 1024);   // small systems: split the lists
+    const int nb = ceil_div((long long)h->n * tpa, kForceBlock);
+    const double* et = h->b.exp_table;
+    switch (tpa) {
+    case 8:
+        k_g_hvp1<8><<<nb, kForceBlock, 0, s>>>(b, pc, L, et, u);
+        k_g_hvp2<8><<<nb, kForceBlock, 0, s>>>(b, pc, L, et, u, hu);
+        break;
+    case 4:
+        k_g_hvp1<4><<<nb, kForceBlock, 0, s>>>(b, pc, L, et, u);
+        k_g_hvp2<4><<<nb, kForceBlock, 0, s>>>(b, pc, L, et, u, hu);
+        break;
+    case 2:
+        k_g_hvp1<2><<<nb, kForceBlock, 0, s>>>(b, pc, L, et, u);
+        k_g_hvp2<2><<<nb, kForceBlock, 0, s>>>(b, pc, L, et, u, hu);
+        break;
+    default:
+        k_g_hvp1<1><<<nb, kForceBlock, 0, s>>>(b, pc, L, et, u);
+        k_g_hvp2<1><<<nb, kForceBlock, 0, s>>>(b, pc, L, et, u, hu);
+    }
 }
 
 fire_status fire_rgl_hvp_dev(fire_handle_t* h, const double* d_pos, const double box[3],

@@ -221,20 +221,23 @@ __global__ void __launch_bounds__(kForceBlock) k_g_force(GradBufs g, PotC P, Geo
     }
 }
 
-// HVP pass 1: drho_i = sum_j g'(r) d.(u_j - u_i) / r.
+// HVP pass 1: drho_i = sum_j g'(r) d.(u_j - u_i) / r; TPA threads per atom
+// (group_sum), as in the cached passes.
+template <int TPA>
 __global__ void __launch_bounds__(kForceBlock) k_g_hvp1(GradBufs g, PotC P, GeoL L,
                                                         const double* exp_table, const double* u) {
     __shared__ double3 tbl[125];
     __shared__ double etab[kExpTableSize];
     grad_tables(tbl, etab, exp_table, L.L);
     __syncthreads();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = t / TPA, lane = t % TPA;
     if (i >= g.n) return;
     const dvec4 xi = g.x[i];
     const double* ui = u + 3 * (size_t)i;
     double acc = 0.0;
     const int m = g.nnbr[i];
-    for (int k = 0; k < m; ++k) {
+    for (int k = lane; k < m; k += TPA) {
         int j;
         double dx, dy, dz;
         const double r2 = grad_pair_vec(g, tbl, xi, g.nbr[(size_t)k * g.n + i], j, dx, dy, dz);
@@ -245,12 +248,14 @@ __global__ void __launch_bounds__(kForceBlock) k_g_hvp1(GradBufs g, PotC P, GeoL
         const double dr = (dx * (uj[0] - ui[0]) + dy * (uj[1] - ui[1]) + dz * (uj[2] - ui[2])) * q.rinv;
         acc += q.dg * dr;
     }
-    g.drho[i] = acc;
+    acc = group_sum<TPA>(acc);
+    if (lane == 0) g.drho[i] = acc;
 }
 
 // HVP pass 2: (H u)_i = -dF_i with
 // dF_i = sum_j [dfs d + fs (u_j - u_i)],
 // dfs = [(2 phi'' + c g'')/r - fs/r] dr + (F''_i drho_i + F''_j drho_j) g'/r.
+template <int TPA>
 __global__ void __launch_bounds__(kForceBlock) k_g_hvp2(GradBufs g, PotC P, GeoL L,
                                                         const double* exp_table, const double* u,
                                                         double* hu) {
@@ -258,14 +263,15 @@ __global__ void __launch_bounds__(kForceBlock) k_g_hvp2(GradBufs g, PotC P, GeoL
     __shared__ double etab[kExpTableSize];
     grad_tables(tbl, etab, exp_table, L.L);
     __syncthreads();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = t / TPA, lane = t % TPA;
     if (i >= g.n) return;
     const dvec4 xi = g.x[i];
     const double* ui = u + 3 * (size_t)i;
     const double f1i = g.F1[i], dci = g.F2[i] * g.drho[i];
     double dF[3] = {0, 0, 0};
     const int m = g.nnbr[i];
-    for (int k = 0; k < m; ++k) {
+    for (int k = lane; k < m; k += TPA) {
         int j;
         double d[3];
         const double r2 = grad_pair_vec(g, tbl, xi, g.nbr[(size_t)k * g.n + i], j, d[0], d[1], d[2]);
@@ -282,6 +288,9 @@ __global__ void __launch_bounds__(kForceBlock) k_g_hvp2(GradBufs g, PotC P, GeoL
 #pragma unroll
         for (int a = 0; a < 3; ++a) dF[a] += dfs * d[a] + fs * du[a];
     }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) dF[a] = group_sum<TPA>(dF[a]);
+    if (lane != 0) return;
     double* h = hu + 3 * (size_t)i;
     h[0] = -dF[0];
     h[1] = -dF[1];
