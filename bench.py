@@ -145,25 +145,51 @@ def count_pairs(x, box, rc):
     return int((t.count_neighbors(t, rc) - len(x)) // 2)
 
 
+def gpu_smi_id(dev_index):
+    """An id nvidia-smi resolves to the same physical GPU as torch's device
+    dev_index: nvidia-smi ignores CUDA_VISIBLE_DEVICES, so a logical index
+    could name another GPU of a shared machine.  The UUID, else the PCI bus
+    id, else the index."""
+    try:
+        import torch
+        props = torch.cuda.get_device_properties(dev_index)
+        u = str(getattr(props, "uuid", "") or "")
+        if u:
+            return u if u.startswith("GPU-") else "GPU-" + u
+        if hasattr(props, "pci_bus_id"):
+            return "%08X:%02X:%02X.0" % (getattr(props, "pci_domain_id", 0), props.pci_bus_id,
+                                         getattr(props, "pci_device_id", 0))
+    except Exception:
+        pass
+    return str(dev_index)
+
+
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index=0):
-        self.index = index
+        self.smi_id = gpu_smi_id(index)
         self.proc = None
-        # raw nvidia-smi samples (FIRE2_CLOCKS_DIR keeps them; the JSON line
-        # carries their summary)
-        out_dir = os.environ.get("FIRE2_CLOCKS_DIR") or tempfile.gettempdir()
-        self.path = os.path.join(out_dir, f"clocks_bench_{os.getpid()}.csv")
+        self.lines = []
+        # raw nvidia-smi samples go to a temporary file that is removed once
+        # read, unless FIRE2_CLOCKS_DIR names a folder to keep them in (the
+        # JSON line carries their summary)
+        self.keep_dir = os.environ.get("FIRE2_CLOCKS_DIR")
+        self.path = None
 
     def __enter__(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
-            self.fh = open(self.path, "w")
+            if self.keep_dir:
+                os.makedirs(self.keep_dir, exist_ok=True)
+                self.path = os.path.join(self.keep_dir, f"clocks_bench_{os.getpid()}.csv")
+                self.fh = open(self.path, "w")
+            else:
+                fd, self.path = tempfile.mkstemp(prefix="clocks_bench_", suffix=".csv")
+                self.fh = os.fdopen(fd, "w")
             self.proc = subprocess.Popen(
-                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                ["nvidia-smi", f"--id={self.smi_id}", f"--query-gpu={self.FIELDS}",
                  "--format=csv,noheader,nounits", "-lms", "200"],
                 stdout=self.fh, stderr=subprocess.DEVNULL)
         except Exception:
@@ -177,14 +203,23 @@ class ClockSampler:
                 self.proc.wait(timeout=5)
             except Exception:
                 self.proc.kill()
-            self.fh.close()
+        if self.path:
+            try:
+                self.fh.close()
+                with open(self.path) as fh:
+                    self.lines = fh.readlines()
+                if not self.keep_dir:
+                    os.remove(self.path)
+            except Exception:
+                pass
 
     def summary(self):
         if not self.proc:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"],
+                    "sampled_gpu": self.smi_id}
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
+        for line in self.lines:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 9:
                 continue
@@ -198,7 +233,7 @@ class ClockSampler:
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "sampled_gpu": self.smi_id}
 
 
 def read_traffic(kernel):

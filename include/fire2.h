@@ -39,7 +39,7 @@
 extern "C" {
 #endif
 
-#define FIRE2_ABI_VERSION 8
+#define FIRE2_ABI_VERSION 9
 
 typedef enum {
     FIRE_OK = 0,
@@ -49,7 +49,8 @@ typedef enum {
     FIRE_ERR_NONFINITE = 4,     /* a force, energy or position became NaN/Inf */
     FIRE_ERR_NBR_OVERFLOW = 5,  /* a neighbour list or cell exceeded its capacity */
     FIRE_ERR_TIMEOUT = 6,       /* the device loop exceeded its wall-clock budget */
-    FIRE_ERR_STATE = 7          /* call not valid for this handle (e.g. wrong size) */
+    FIRE_ERR_STATE = 7,         /* call not valid for this handle (e.g. wrong size) */
+    FIRE_ERR_NOT_CONVERGED = 8  /* an inner iterative solve stopped before its tolerance */
 } fire_status;
 
 /* Stop reasons (Algorithm 2 and Sec. 3.4). */
@@ -100,7 +101,13 @@ typedef enum {
 } fire_newton;
 
 typedef enum {
-    FIRE_PREC_FP64 = 0,         /* all arithmetic in FP64 */
+    FIRE_PREC_FP64 = 0,         /* FP64 results: positions, densities, forces, energies,
+                                   reductions, control and integration in FP64.  The
+                                   pair terms follow pot.pair_eval: with the default
+                                   FIRE_PAIR_TABLE they are double-float (float pairs,
+                                   ~2^-44 relative) from table interpolation on exact
+                                   fixed-point separations; FIRE_PAIR_ANALYTIC computes
+                                   them with IEEE-FP64 exponentials */
     FIRE_PREC_FP32_PAIR = 1     /* pair/embedding math in FP32; positions, sums, control FP64 */
 } fire_precision;
 
@@ -331,10 +338,10 @@ fire_status fire_diag_fma_peak(int32_t which, double* flops_per_s);
 
 /* Energy and forces of one configuration without allocating device memory.
  * The paper has no counterpart: this entry point exists for callers that
- * cannot call cudaMalloc when they need forces -- code running while a stream
- * is captured into a CUDA graph (allocation is not capturable), plug-ins
- * whose host program's memory pool owns all device memory, and
- * latency-critical loops where an allocation could synchronise the device.
+ * cannot call cudaMalloc when they need forces -- plug-ins whose host
+ * program's memory pool owns all device memory and forbids stray
+ * allocations, and latency-critical loops where an allocation could
+ * synchronise the device or fail under memory pressure.
  * It needs no handle: the caller passes the potential, the periodic flags,
  * device buffers d_pos (n_atoms x 3 doubles, row-major, read) and d_forces
  * (n_atoms x 3, written; may be NULL) and d_energy (one double, written; may
@@ -347,8 +354,10 @@ fire_status fire_diag_fma_peak(int32_t which, double* flops_per_s);
  * contents; every value a call reads is written earlier in the same call, so
  * nothing needs clearing between calls, but calls that overlap on the GPU
  * race on it and must be serialised by the caller.  The first call on each
- * device looks up the array's device address (cudaGetSymbolAddress); make
- * that first call before any stream capture on that device.
+ * device, and the first after a device reset (a new context), looks up the
+ * array's device address (cudaGetSymbolAddress); make that first call
+ * before any stream capture on that device.  A CUDA error left pending by
+ * the caller's earlier work is neither reported as this call's nor cleared.
  * Errors (message in fire_last_error(NULL)): FIRE_ERR_ARG for NULL
  * arguments, n_atoms outside [1, 32768], precision other than FP64, bad
  * potential parameters or a periodic box shorter than twice the cut-off;
@@ -477,8 +486,14 @@ fire_status fire_rgl_hvp_dev(fire_handle_t* h, const double* d_pos, const double
 /* Implicit gradient at a relaxed d_pos: d_g = dL/dx (device, N x 3),
  * CG until |r| <= tol |g| or maxit iterations; dL_dtheta (host, 4) receives
  * lambda . dF/dtheta, d_lambda (device, N x 3, may be NULL) the solution,
- * *cg_iters (may be NULL) the iteration count.
- * Errors: FIRE_ERR_ARG (tol <= 0, maxit < 1, NULL), FIRE_ERR_NBR_OVERFLOW, FIRE_ERR_CUDA. */
+ * *cg_iters (may be NULL) the iteration count.  Returns FIRE_OK only when
+ * the residual met tol.  FIRE_ERR_NOT_CONVERGED when CG stopped first:
+ * either maxit iterations left |r| > tol |g|, or CG broke down (p.Hp <= 0
+ * or not finite along a search direction, i.e. d_pos is not at a minimum).
+ * In both cases the outputs hold the last iterate, and fire_last_error(h)
+ * names the cause and the final relative residual.
+ * Errors: FIRE_ERR_ARG (tol <= 0, maxit < 1, NULL), FIRE_ERR_NONFINITE (d_g),
+ * FIRE_ERR_NOT_CONVERGED, FIRE_ERR_NBR_OVERFLOW, FIRE_ERR_CUDA. */
 fire_status fire_rgl_implicit_grad_dev(fire_handle_t* h, const double* d_pos, const double box[3],
                                        const double theta[4], const double* d_g, double tol,
                                        int64_t maxit, double dL_dtheta[4], double* d_lambda,

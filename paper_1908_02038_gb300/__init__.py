@@ -22,6 +22,7 @@ from ._build import LIB_PATH, build  # noqa: F401
 
 FIRE_OK, FIRE_ERR_ARG, FIRE_ERR_CUDA, FIRE_ERR_NOMEM = 0, 1, 2, 3
 FIRE_ERR_NONFINITE, FIRE_ERR_NBR_OVERFLOW, FIRE_ERR_TIMEOUT, FIRE_ERR_STATE = 4, 5, 6, 7
+FIRE_ERR_NOT_CONVERGED = 8
 FIRE_STOP_FTOL, FIRE_STOP_MAXITER, FIRE_STOP_MAXVDOTF = 0, 1, 2
 FIRE_NORM_MAX_ATOM, FIRE_NORM_TWO, FIRE_NORM_INF = 0, 1, 2
 FIRE_POT_LJ, FIRE_POT_RGL, FIRE_POT_SW = 0, 1, 2
@@ -34,7 +35,7 @@ FIRE_FP64_CHECK_OFF, FIRE_FP64_CHECK_CONFIRM, FIRE_FP64_CHECK_FINISH = 0, 1, 2
 
 STATUS_NAMES = {0: "FIRE_OK", 1: "FIRE_ERR_ARG", 2: "FIRE_ERR_CUDA", 3: "FIRE_ERR_NOMEM",
                 4: "FIRE_ERR_NONFINITE", 5: "FIRE_ERR_NBR_OVERFLOW", 6: "FIRE_ERR_TIMEOUT",
-                7: "FIRE_ERR_STATE"}
+                7: "FIRE_ERR_STATE", 8: "FIRE_ERR_NOT_CONVERGED"}
 
 # Every symbol include/fire2.h declares (checked by the ABI test).
 EXPORTED = ("fire_abi_version", "fire_default_params", "fire_init", "fire_minimize",
@@ -251,7 +252,7 @@ def fire_minimize(handle, pos: np.ndarray, box, ftol: float, maxiter: int) -> fi
 
 def fire_minimize_dev(handle, d_pos, box, ftol: float, maxiter: int, stream=None) -> fire_result_t:
     """d_pos: CUDA float64 tensor (N x 3, contiguous), relaxed in place."""
-    _check_dev(d_pos)
+    _check_dev(d_pos, "d_pos", rows3=True)
     res = fire_result_t()
     st = load_library().fire_minimize_dev(handle, d_pos.data_ptr(), _box(box), float(ftol),
                                           int(maxiter), C.byref(res), _stream(stream))
@@ -270,7 +271,7 @@ def fire_energy_forces(handle, pos: np.ndarray, box, want_forces: bool = True):
 
 
 def fire_energy_forces_dev(handle, d_pos, box, d_forces=None, d_energy=None, stream=None):
-    _check_dev(d_pos)
+    _check_outputs(d_pos, d_forces, d_energy)
     st = load_library().fire_energy_forces_dev(
         handle, d_pos.data_ptr(), _box(box),
         d_forces.data_ptr() if d_forces is not None else None,
@@ -298,7 +299,7 @@ def fire_energy_forces_noalloc(pot: fire_potential_t, d_pos, box, periodic=(1, 1
                                d_forces=None, d_energy=None, stream=None) -> None:
     """Allocation-free evaluation into caller-owned CUDA tensors (enqueued on
     `stream`; synchronise before reading the results)."""
-    _check_dev(d_pos)
+    _check_outputs(d_pos, d_forces, d_energy)
     per = (C.c_int32 * 3)(*[int(bool(p)) for p in periodic])
     st = load_library().fire_energy_forces_noalloc(
         C.byref(pot), int(d_pos.shape[0]), per, d_pos.data_ptr(), _box(box),
@@ -309,8 +310,8 @@ def fire_energy_forces_noalloc(pot: fire_potential_t, d_pos, box, periodic=(1, 1
 
 def fire_diag_exp(d_x, d_out, stream=None) -> None:
     """The library's FP64 exponential at the points of d_x (CUDA float64)."""
-    _check_dev(d_x)
-    _check_dev(d_out)
+    _check_dev(d_x, "d_x")
+    _check_dev(d_out, "d_out", like=d_x)
     _check(load_library().fire_diag_exp(int(d_x.numel()), d_x.data_ptr(), d_out.data_ptr(),
                                         _stream(stream)), None)
 
@@ -341,7 +342,9 @@ def fire_minimize_batch(handle, pos: np.ndarray, boxes, ftol: float, maxiter: in
 
 def fire_minimize_batch_dev(handle, d_pos, boxes, ftol: float, maxiter: int, d_forces=None,
                             stream=None):
-    _check_dev(d_pos)
+    _check_dev(d_pos, "d_pos", rows3=True)
+    if d_forces is not None:
+        _check_dev(d_forces, "d_forces", like=d_pos)
     bx = np.ascontiguousarray(boxes, dtype=np.float64).reshape(-1, 3)
     out = (fire_result_t * len(bx))()
     st = load_library().fire_minimize_batch_dev(
@@ -378,7 +381,7 @@ def fire_set_rgl_params(handle, theta) -> None:
 
 def fire_rgl_energy_grad_dev(handle, d_pos, box, theta, d_forces=None, stream=None):
     """Returns (E, dE/dtheta as a numpy (4,)); fills d_forces if given."""
-    _check_dev(d_pos)
+    _check_outputs(d_pos, d_forces, None)
     e = C.c_double(0.0)
     de = (C.c_double * 4)()
     st = load_library().fire_rgl_energy_grad_dev(
@@ -389,8 +392,10 @@ def fire_rgl_energy_grad_dev(handle, d_pos, box, theta, d_forces=None, stream=No
 
 
 def fire_rgl_hvp_dev(handle, d_pos, box, theta, d_u, d_hu, stream=None) -> None:
-    for t in (d_pos, d_u, d_hu):
-        _check_dev(t)
+    for cuda in (False, True):
+        _check_dev(d_pos, "d_pos", rows3=True, cuda=cuda)
+        _check_dev(d_u, "d_u", like=d_pos, cuda=cuda)
+        _check_dev(d_hu, "d_hu", like=d_pos, cuda=cuda)
     st = load_library().fire_rgl_hvp_dev(handle, d_pos.data_ptr(), _box(box), _theta(theta),
                                          d_u.data_ptr(), d_hu.data_ptr(), _stream(stream))
     _check(st, handle)
@@ -398,9 +403,14 @@ def fire_rgl_hvp_dev(handle, d_pos, box, theta, d_u, d_hu, stream=None) -> None:
 
 def fire_rgl_implicit_grad_dev(handle, d_pos, box, theta, d_g, tol=1e-10, maxit=20000,
                                d_lambda=None, stream=None):
-    """Returns (dL/dtheta as numpy (4,), CG iterations)."""
-    _check_dev(d_pos)
-    _check_dev(d_g)
+    """Returns (dL/dtheta as numpy (4,), CG iterations).  Raises FireError
+    with status FIRE_ERR_NOT_CONVERGED when CG stopped before tol (maxit
+    reached, or a breakdown away from a minimum)."""
+    for cuda in (False, True):
+        _check_dev(d_pos, "d_pos", rows3=True, cuda=cuda)
+        _check_dev(d_g, "d_g", like=d_pos, cuda=cuda)
+        if d_lambda is not None:
+            _check_dev(d_lambda, "d_lambda", like=d_pos, cuda=cuda)
     out = (C.c_double * 4)()
     it = C.c_int64(0)
     st = load_library().fire_rgl_implicit_grad_dev(
@@ -420,11 +430,41 @@ def fire_diag_rgl_table(pot: fire_potential_t, r) -> np.ndarray:
     return out
 
 
-def _check_dev(t):
+def _check_dev(t, name="tensor", rows3=False, like=None, min_numel=1, cuda=True):
+    """Raises ValueError unless t is a contiguous float64 CUDA tensor; with
+    rows3 it must be shaped (n, 3); with like, it must have like's shape and
+    device; it must hold at least min_numel elements.  The checks that need
+    no GPU come first (cuda=False: only those)."""
     import torch
-    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64
-            and t.is_contiguous()):
-        raise ValueError("expected a contiguous float64 CUDA tensor")
+    if not isinstance(t, torch.Tensor):
+        raise ValueError(f"{name}: expected a torch tensor, got {type(t).__name__}")
+    if t.dtype != torch.float64 or not t.is_contiguous():
+        raise ValueError(f"{name}: expected a contiguous float64 tensor")
+    if rows3 and (t.dim() != 2 or t.shape[1] != 3):
+        raise ValueError(f"{name}: expected shape (n, 3), got {tuple(t.shape)}")
+    if like is not None and t.shape != like.shape:
+        raise ValueError(f"{name}: expected shape {tuple(like.shape)}, got {tuple(t.shape)}")
+    if t.numel() < min_numel:
+        raise ValueError(f"{name}: expected at least {min_numel} element(s)")
+    if not cuda:
+        return
+    if not t.is_cuda:
+        raise ValueError(f"{name}: expected a CUDA tensor")
+    if like is not None and t.device != like.device:
+        raise ValueError(f"{name}: on {t.device}, expected {like.device}")
+
+
+def _check_outputs(d_pos, d_forces, d_energy):
+    """Positions (n, 3); forces, if given, shaped like them on the same
+    device; energy, if given, one double or more on the same device."""
+    for cuda in (False, True):   # every layout check before the device checks
+        _check_dev(d_pos, "d_pos", rows3=True, cuda=cuda)
+        if d_forces is not None:
+            _check_dev(d_forces, "d_forces", like=d_pos, cuda=cuda)
+        if d_energy is not None:
+            _check_dev(d_energy, "d_energy", cuda=cuda)
+    if d_energy is not None and d_energy.device != d_pos.device:
+        raise ValueError(f"d_energy: on {d_energy.device}, expected {d_pos.device}")
 
 
 def _stream(stream):

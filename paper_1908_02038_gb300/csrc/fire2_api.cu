@@ -1653,7 +1653,10 @@ fire_status fire_rgl_implicit_grad_dev(fire_handle_t* h, const double* d_pos, co
     c0.rr = rr;
     c0.stop2 = tol * tol * rr;
     c0.maxit = maxit;
+    if (!std::isfinite(rr))
+        return fail(h, FIRE_ERR_NONFINITE, "implicit gradient: dL/dx has a non-finite entry");
     c0.done = (rr > c0.stop2 && rr > 0.0) ? 0 : 1;
+    c0.reason = c0.done ? CG_CONVERGED : CG_RUNNING;   // a zero right-hand side is solved
     *gs.h_cs = c0;
     CK(h, cudaMemcpyAsync(gs.cs, gs.h_cs, sizeof(CgState), cudaMemcpyHostToDevice, s));
     GeoL L{{box[0], box[1], box[2]}};
@@ -1695,6 +1698,8 @@ fire_status fire_rgl_implicit_grad_dev(fire_handle_t* h, const double* d_pos, co
     }
     if (batch) cudaGraphExecDestroy(batch);
     const int64_t it = gs.h_cs->it;
+    const int reason = gs.h_cs->reason;
+    const double rel_res = rr > 0.0 ? std::sqrt(gs.h_cs->rr / rr) : 0.0;
     k_g_force<<<h->grad.nb, kForceBlock, 0, s>>>(b, pc, L, h->b.exp_table, nullptr, nullptr, lam);
     CK(h, cudaGetLastError());
     double sums[4];
@@ -1703,6 +1708,17 @@ fire_status fire_rgl_implicit_grad_dev(fire_handle_t* h, const double* d_pos, co
     if (d_lambda) CK(h, cudaMemcpyAsync(d_lambda, lam, bytes, cudaMemcpyDeviceToDevice, s));
     CK(h, cudaStreamSynchronize(s));
     if (cg_iters) *cg_iters = it;
+    // the outputs above hold the last iterate in every case; a solve that did
+    // not reach tol says so in its status
+    if (reason == CG_BREAKDOWN)
+        return fail(h, FIRE_ERR_NOT_CONVERGED,
+                    "implicit gradient: conjugate gradient broke down after %lld iterations "
+                    "(p.Hp <= 0 or not finite: the configuration is not at a minimum), "
+                    "relative residual %.3e", (long long)it, rel_res);
+    if (reason != CG_CONVERGED)
+        return fail(h, FIRE_ERR_NOT_CONVERGED,
+                    "implicit gradient: conjugate gradient reached maxit = %lld with relative "
+                    "residual %.3e > tol = %.3e", (long long)maxit, rel_res, tol);
     return FIRE_OK;
 }
 

@@ -449,10 +449,14 @@ __global__ void k_g_sub_mean(int n, double* a, double m0, double m1, double m2) 
 // iterations run without a host round trip; every kernel of an iteration
 // returns at once when the solve is done (done = 1), so the host can queue
 // several iterations and look at the state once per batch.
+// Why the solve stopped (CgState::reason).
+enum CgReason { CG_RUNNING = 0, CG_CONVERGED = 1, CG_BREAKDOWN = 2, CG_MAXIT = 3 };
+
 struct CgState {
     double rr, stop2, alpha, beta, m[3];
     long long it, maxit;
     int done;
+    int reason;            // CgReason
 };
 
 // Fixed-order sum of cnt partials by one block (result in thread 0).
@@ -508,15 +512,19 @@ __global__ void k_cg_project_dot(int n, const CgState* cs, double* ap, const dou
     if (threadIdx.x == 0) part[blockIdx.x] = acc;
 }
 
-// One block: alpha = r.r / p.Ap; stops when H is not positive definite
-// along p.
+// One block: alpha = r.r / p.Ap; stops (CG_BREAKDOWN) when H is not
+// positive definite along p or p.Ap is not finite.
 __global__ void k_cg_alpha(CgState* cs, const double* part, int nb) {
     __shared__ double red[32];
     if (cs->done) return;
     const double pAp = cg_sum(part, nb, red);
     if (threadIdx.x == 0) {
-        if (!(pAp > 0.0)) cs->done = 1;
-        else cs->alpha = cs->rr / pAp;
+        if (!(pAp > 0.0) || !isfinite(pAp)) {
+            cs->done = 1;
+            cs->reason = CG_BREAKDOWN;
+        } else {
+            cs->alpha = cs->rr / pAp;
+        }
     }
 }
 
@@ -546,7 +554,16 @@ __global__ void k_cg_beta(CgState* cs, const double* part, int nb) {
         cs->beta = rr / cs->rr;
         cs->rr = rr;
         cs->it += 1;
-        if (!(rr > cs->stop2) || cs->it >= cs->maxit) cs->done = 1;
+        if (!isfinite(rr)) {
+            cs->done = 1;
+            cs->reason = CG_BREAKDOWN;
+        } else if (!(rr > cs->stop2)) {
+            cs->done = 1;
+            cs->reason = CG_CONVERGED;
+        } else if (cs->it >= cs->maxit) {
+            cs->done = 1;
+            cs->reason = CG_MAXIT;
+        }
     }
 }
 

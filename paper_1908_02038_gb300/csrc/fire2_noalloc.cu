@@ -1,11 +1,10 @@
 // Allocation-free energy/force evaluation (fire_energy_forces_noalloc).
 //
 // Some callers cannot call cudaMalloc at the point where they need forces:
-// code that runs while a stream is being captured into a CUDA graph
-// (allocation is not a capturable operation), plug-ins of host programs whose
-// memory pool owns all device memory and forbids stray allocations, and
-// latency-critical loops where an allocation could synchronise the device.
-// This entry point serves them: the caller passes device buffers for the
+// plug-ins of host programs whose memory pool owns all device memory and
+// forbids stray allocations, and latency-critical loops where an allocation
+// could synchronise the device or fail under memory pressure.  This entry
+// point serves them: the caller passes device buffers for the
 // positions and the results, and the only scratch the kernels need (per-atom
 // densities, embedding derivatives and per-block energy partials) lives in the
 // file-scope device array `g_scratch` below, sized for at most
@@ -17,6 +16,7 @@
 // blocks: every scratch value read in a call is written earlier in the same
 // call.  Calls that overlap on the GPU (two streams, or two host threads) race
 // on g_scratch and must be serialised by the caller.
+#include <cuda.h>   // CUcontext and the driver function types (entry points, no link)
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -204,22 +204,64 @@ __global__ void k_na_energy(const double* scratch, int nblocks, double* energy) 
 }
 
 std::mutex g_mu;
-double* g_scratch_ptr[128] = {nullptr};
 
-// Device address of g_scratch on the current device (looked up once per device).
+// The scratch array's device address is looked up once per device context:
+// cudaDeviceReset (or a reset of the primary context) gives the device a new
+// context and reloads the module, so the cache is keyed on the context's
+// unique id (cuCtxGetId, through the runtime's driver entry points).
+struct ScratchAddr {
+    unsigned long long ctx_id = 0;   // 0 = none cached
+    double* ptr = nullptr;
+};
+ScratchAddr g_addr[128];
+
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+
+// Unique id of the current context, or 0 when it cannot be had (then the
+// address is looked up on every call).
+unsigned long long current_context_id() {
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static bool resolved = false;
+    if (!resolved) {   // under g_mu
+        cudaDriverEntryPointQueryResult q1, q2;
+        void* f1 = nullptr;
+        void* f2 = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault,
+                                             &q1) == cudaSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault,
+                                             &q2) == cudaSuccess &&
+            q1 == cudaDriverEntryPointSuccess && q2 == cudaDriverEntryPointSuccess) {
+            get_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+            get_id = reinterpret_cast<CtxGetIdFn>(f2);
+        }
+        resolved = true;
+    }
+    if (!get_current || !get_id) return 0;
+    CUcontext c = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&c) != CUDA_SUCCESS || !c || get_id(c, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
+
+// Device address of g_scratch in the current device's context.
 cudaError_t scratch_address(double** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 128) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_ptr[dev]) {
+    const unsigned long long id = current_context_id();
+    ScratchAddr& a = g_addr[dev];
+    if (id == 0 || a.ctx_id != id || !a.ptr) {
         void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_scratch);
+        e = cudaGetSymbolAddress(&p, g_scratch);   // also makes the context current
         if (e != cudaSuccess) return e;
-        g_scratch_ptr[dev] = static_cast<double*>(p);
+        a.ptr = static_cast<double*>(p);
+        a.ctx_id = current_context_id();
     }
-    *out = g_scratch_ptr[dev];
+    *out = a.ptr;
     return cudaSuccess;
 }
 
@@ -286,13 +328,22 @@ extern "C" fire_status fire_energy_forces_noalloc(const fire_potential_t* pot, i
     double* scratch = nullptr;
     cudaError_t e = scratch_address(&scratch);
     if (e != cudaSuccess) return na_fail(FIRE_ERR_CUDA, cudaGetErrorString(e));
-    const int n = (int)n_atoms;
-    const int blocks = (n + kBlock - 1) / kBlock;
+    int n = (int)n_atoms;
+    int blocks = (n + kBlock - 1) / kBlock;
     cudaStream_t s = (cudaStream_t)stream;
-    k_na_pass1<<<blocks, kBlock, 0, s>>>(d_pos, n, P, scratch, d_forces);
-    if (P.kind == FIRE_POT_RGL) k_na_pass2<<<blocks, kBlock, 0, s>>>(d_pos, n, P, scratch, d_forces);
-    k_na_energy<<<1, 256, 0, s>>>(scratch, blocks, d_energy);
-    e = cudaGetLastError();
+    // cudaLaunchKernel returns the status of its own launch, so an error left
+    // pending by the caller's earlier work is neither reported as this call's
+    // nor cleared
+    const double* pos = d_pos;
+    double* fout = d_forces;
+    double* eout = d_energy;
+    void* args12[] = {(void*)&pos, (void*)&n, (void*)&P, (void*)&scratch, (void*)&fout};
+    e = cudaLaunchKernel((const void*)k_na_pass1, dim3(blocks), dim3(kBlock), args12, 0, s);
+    if (e == cudaSuccess && P.kind == FIRE_POT_RGL)
+        e = cudaLaunchKernel((const void*)k_na_pass2, dim3(blocks), dim3(kBlock), args12, 0, s);
+    void* args3[] = {(void*)&scratch, (void*)&blocks, (void*)&eout};
+    if (e == cudaSuccess)
+        e = cudaLaunchKernel((const void*)k_na_energy, dim3(1), dim3(256), args3, 0, s);
     if (e != cudaSuccess) return na_fail(FIRE_ERR_CUDA, cudaGetErrorString(e));
     return FIRE_OK;
 }

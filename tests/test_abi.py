@@ -38,7 +38,7 @@ def test_library_exports_every_header_symbol(lib):
 
 
 def test_abi_version_and_defaults(lib):
-    assert fg.fire_abi_version() == 8
+    assert fg.fire_abi_version() == 9
     p = fg.fire_default_params(0.001)
     assert (p.tmax, p.tmin, p.dtgrow, p.dtshrink, p.alpha0, p.alphashrink) == \
         (10.0, 0.02, 1.1, 0.5, 0.25, 0.99)
@@ -121,3 +121,39 @@ def test_pair_function_table_matches_oracle(lib):
         assert err[near].max() / np.abs(ref[near, k]).max() < 5e-12, k
     # beyond rc everything vanishes
     assert np.all(fg.fire_diag_rgl_table(pot, np.array([5.0, 6.0])) == 0.0)
+
+
+def test_device_wrappers_reject_bad_shapes_on_the_host():
+    """The *_dev wrappers check shapes and dtypes before any library call, so
+    a flat 3N position tensor or a mis-shaped output never reaches a kernel
+    (which would read or write past the tensors)."""
+    import torch
+    pot = fg.Potential(fg.FIRE_POT_RGL, **fi.RGL_CU).c()
+    flat = torch.zeros(30, dtype=torch.float64)
+    pos = torch.zeros((10, 3), dtype=torch.float64)
+    box = [20.0] * 3
+    cases = [
+        (lambda: fg.fire_energy_forces_noalloc(pot, flat, box), "shape (n, 3)"),
+        (lambda: fg.fire_energy_forces_noalloc(pot, pos, box, d_forces=torch.zeros(
+            (9, 3), dtype=torch.float64)), "d_forces"),
+        (lambda: fg.fire_energy_forces_noalloc(pot, pos, box, d_forces=torch.zeros(
+            (10, 3), dtype=torch.float32)), "d_forces"),
+        (lambda: fg.fire_energy_forces_noalloc(pot, pos, box, d_energy=torch.zeros(
+            0, dtype=torch.float64)), "d_energy"),
+        (lambda: fg.fire_energy_forces_dev(None, flat, box), "shape (n, 3)"),
+        (lambda: fg.fire_minimize_dev(None, flat, box, 1e-6, 10), "shape (n, 3)"),
+        (lambda: fg.fire_rgl_hvp_dev(None, pos, box, [1, 1, 1, 1], pos, flat), "d_hu"),
+        (lambda: fg.fire_rgl_implicit_grad_dev(None, pos, box, [1, 1, 1, 1], flat), "d_g"),
+        (lambda: fg.fire_energy_forces_noalloc(pot, pos, box), "CUDA"),
+    ]
+    for call, what in cases:
+        with pytest.raises(ValueError) as e:
+            call()
+        assert what in str(e.value), (what, str(e.value))
+
+
+def test_not_converged_status_is_named():
+    assert fg.FIRE_ERR_NOT_CONVERGED == 8
+    assert fg.STATUS_NAMES[8] == "FIRE_ERR_NOT_CONVERGED"
+    txt = open(os.path.join(ROOT, "include", "fire2.h")).read()
+    assert "FIRE_ERR_NOT_CONVERGED = 8" in txt

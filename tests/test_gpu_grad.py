@@ -141,3 +141,50 @@ def test_autograd_energy_backward(torch):
     assert e.item() == pytest.approx(eo, rel=1e-12)
     assert np.abs(pos.grad.cpu().numpy() + fo).max() < 1e-10 * np.abs(fo).max()
     np.testing.assert_allclose(theta.grad.numpy(), dEo, rtol=1e-10)
+
+
+def test_implicit_gradient_reports_unconverged_solve(torch):
+    """A CG solve cut off by maxit returns FIRE_ERR_NOT_CONVERGED (with the
+    residual in the message), not FIRE_OK; a zero right-hand side is solved
+    in 0 iterations."""
+    c = fi.rgl_vacancy_box(ncell=5, seed=75, n_vac=1, sigma=0.05)
+    d_pos = torch.tensor(c.x, dtype=torch.float64, device="cuda")
+    with handle(c.n) as h:
+        fg.fire_minimize_dev(h.h, d_pos, c.box, 1e-10, 100000)
+        g = torch.zeros_like(d_pos)
+        g[0, 0] = 1.0
+        with pytest.raises(fg.FireError) as e:
+            fg.fire_rgl_implicit_grad_dev(h.h, d_pos, c.box, THETA0, g, tol=1e-12, maxit=1)
+        assert e.value.status == fg.FIRE_ERR_NOT_CONVERGED
+        assert "maxit" in str(e.value) and "residual" in str(e.value)
+        grad, it = fg.fire_rgl_implicit_grad_dev(h.h, d_pos, c.box, THETA0,
+                                                 torch.zeros_like(d_pos), tol=1e-12)
+        assert it == 0 and np.all(grad == 0.0)
+
+
+def test_implicit_gradient_32k_matches_oracle_golden(torch):
+    """The differentiation workload itself (31,999-atom vacancy box, seed 5):
+    the GPU relaxes to max|F_i| < 1e-12 eV/A and solves for dL/dtheta; the
+    oracle's gradient of the same workload (relaxed by the oracle to the same
+    ftol, its own CG to 1e-12) is stored in tests/golden, written by
+    tests/golden/make_implicit_grad_rgl32k.py from oracle/ alone."""
+    import json
+    import os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden",
+                                       "implicit_grad_rgl32k.json")))
+    c = fi.rgl_vacancy_box(ncell=20, seed=5, n_vac=1)
+    assert c.n == gold["n_atoms"] == 31999
+    sel, loss_grad = vacancy_loss(c, gold["radius_A"])
+    assert len(sel) == gold["loss_atoms"]
+    d_pos = torch.tensor(c.x, dtype=torch.float64, device="cuda")
+    with handle(c.n) as h:
+        r = fg.fire_minimize_dev(h.h, d_pos, c.box, gold["ftol"], 400000)
+        assert r.stop == fg.FIRE_STOP_FTOL
+        loss, g = loss_grad(d_pos.cpu().numpy())
+        d_g = torch.tensor(g, dtype=torch.float64, device="cuda")
+        grad, it = fg.fire_rgl_implicit_grad_dev(h.h, d_pos, c.box, THETA0, d_g,
+                                                 tol=gold["cg_tol"])
+    print(f"GPU {r.iterations} FIRE iterations, {it} CG iterations; oracle "
+          f"{gold['oracle_fire_iterations']} / {gold['oracle_cg_iterations']}")
+    assert loss == pytest.approx(gold["loss"], rel=1e-8)
+    np.testing.assert_allclose(grad, gold["dL_dtheta"], rtol=1e-6)
