@@ -46,34 +46,36 @@ CONFIGS = {
     "lj256": lambda: fi.lj_fcc_vacancy(seed=1),
 }
 # Algorithmic floating-point operations per unordered pair inside the
-# cut-off (an FMA counts 2, a transcendental 1), counted from the formulas
-# each pass must evaluate once per pair (recomputing a pair from both ends,
-# as the full-list kernels do, is implementation work and not counted):
-#   density, exponentials: distance 8, sqrt 1, s 2, exps 2 + 2, prefactors 2,
-#     terms and derivatives 8, rho sums 2, energy 2, cache 3           32
-#   density, tables: distance 8, u 1, offset 1, two quintics 2 x 10,
-#     rho sums 2, energy 2                                            34
-#   force, cached or exponential derivatives: d 3, fs 3, F_i 6, F_j 6   18
-#   force, tables: distance 8, u 1, offset 1, two quintics 20, fs 3,
-#     F_i 6, F_j 6                                                     45
-#   force, LJ                                                          24
-ALG_FLOP_PER_PAIR = {"density": 32, "density_tab": 34, "force": 18, "force_tab": 45,
-                     "force_lj": 24}
-# the kernel each stage runs, per (form, pair evaluation), and its unit
-# ("fp64": FP64 pipe, "ff": double-float on the FP32 pipe, "fp32")
+# cut-off: the method's own work for one pass (an FMA counts 2, a square
+# root, division or exponential 1), whatever the kernel does to get there
+# (table interpolation, double-float arithmetic and evaluating a pair from
+# both ends are implementation work and not counted):
+#   density pass (rho_i = sum_j g(r_ij), E_rep = sum_j phi(r_ij), Sec. 4 /
+#   the RGL form): separation 3 + r^2 5 = 8; r 1; s = r/r0 - 1: 2;
+#   exp(-p s), exp(-2q s): 2 + 2; prefactors A, xi^2: 2; taper t 2,
+#   S and S' 16 (Horner, also for pairs below rs: per-pair average rounded
+#   up); phi = e S, g = e S: 2; rho_i, rho_j sums 2; energy 2        39
+#   force pass (F = -grad E, Sec. 2.1): separation 8, r 1, s 2, exps 4,
+#   prefactors 2, taper 18; phi', g' (e (-a S + S')) 6; fs = (2 phi' +
+#   (F'_i + F'_j) g') / r: 5; F_i and F_j: 6 + 6                     56
+#   LJ force pass: separation 8; 1/r^2 1; (s/r)^6, ^12: 3; w = 24 eps
+#   (2 s12 - s6) / r^2: 4; pair energy 3; F_i and F_j 12              31
+METHOD_FLOP_PER_PAIR = {"density": 39, "force": 56, "force_lj": 31}
+# the kernel each stage runs, per (form, pair evaluation), and the unit it
+# issues on ("fp64": FP64 pipe; "ff": double-float arithmetic on the FP32
+# pipe; "fp32")
 STAGE_KERNELS = {
-    ("fp64", "table"): {"density": ("k_density_ff", "density_tab", "ff"),
-                        "force": ("k_force_ff", "force_tab", "ff")},
-    ("fp64", "analytic"): {"density": ("k_density", "density", "fp64"),
-                           "force": ("k_force_rgl", "force", "fp64")},
-    ("fp32pair", "analytic"): {"density": ("k_density32", "density", "fp32"),
-                               "force": ("k_force32", "force", "fp32")},
-    ("fp32pair", "table"): {"density": ("k_density32_tab", "density_tab", "fp32"),
-                            "force": ("k_force32_tab", "force_tab", "fp32")},
+    ("fp64", "table"): {"density": ("k_density_ff", "ff"), "force": ("k_force_ff", "ff")},
+    ("fp64", "analytic"): {"density": ("k_density", "fp64"), "force": ("k_force_rgl", "fp64")},
+    ("fp32pair", "analytic"): {"density": ("k_density32", "fp32"),
+                               "force": ("k_force32", "fp32")},
+    ("fp32pair", "table"): {"density": ("k_density32_tab", "fp32"),
+                            "force": ("k_force32_tab", "fp32")},
 }
 # FP32 instructions of one double-float multiply-add (ff_mul 7 + ff_add 11,
-# counted from fire2_table.cuh): the double-float ALU peak is the measured
-# FP32 FMA rate / 18 in FP64-equivalent FLOP/s (2 per multiply-add)
+# counted from fire2_table.cuh): the emulation's own ceiling is the FP32 FMA
+# rate / 18 in FP64-equivalent FLOP/s (reported as emulation_efficiency,
+# not as the roofline)
 FF_FP32_PER_FMA = 18
 # Algorithmic HBM bytes per atom and iteration (x, v read+write, F'(rho)
 # write+read): 112 for RGL, 96 for LJ.
@@ -114,6 +116,11 @@ def parse():
                     help="one energy/force evaluation of the config (profiling aid)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="target CPU time of the oracle sample")
+    ap.add_argument("--cpu-full", action="store_true",
+                    help="time the oracle's one-thread runs of the small configurations in "
+                         "full instead of as bounded samples (several minutes)")
+    ap.add_argument("--no-small", action="store_true",
+                    help="skip the LJ and 32k-atom configuration blocks")
     return ap.parse_args()
 
 
@@ -236,20 +243,62 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm), "sampled_gpu": self.smi_id}
 
 
-def read_traffic(kernel):
-    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if its
-    recorded source hash matches the current kernel sources; else None."""
+def _device_src_hash():
     import hashlib
-    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    h = hashlib.sha256()
+    for f in ("fire2_device.cuh", "fire2_tile.cuh"):
+        path = os.path.join(ROOT, "paper_1908_02038_gb300", "csrc", f)
+        if os.path.exists(path):
+            h.update(open(path, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def read_ncu(kernel, workload="rgl1m"):
+    """ncu figures of `kernel` on `workload` from the committed summary
+    profiles/ncu_counters.txt (one line per kernel: name, source hash,
+    workload, then key=value pairs), if its recorded source hash matches the
+    current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", "ncu_counters.txt")
     if not os.path.exists(path):
         return None
-    src = os.path.join(ROOT, "paper_1908_02038_gb300", "csrc", "fire2_device.cuh")
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    h = _device_src_hash()
     for line in open(path):
         parts = line.split()
-        if len(parts) >= 4 and parts[0] == kernel and parts[1] == h:
-            return float(parts[3])
+        if len(parts) >= 4 and parts[0] == kernel and parts[1] == h and parts[2] == workload:
+            out = {}
+            for kv in parts[3:]:
+                k, _, v = kv.partition("=")
+                try:
+                    out[k] = float(v)
+                except ValueError:
+                    out[k] = v
+            return out
     return None
+
+
+def host_cpu():
+    """CPU model and core counts of the host the oracle runs on."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            key, _, val = line.partition(":")
+            if key.strip() == "Model name" and val.strip():
+                model = val.strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    import platform
+    return {"model": model or platform.processor() or "unknown", "arch": platform.machine(),
+            "nproc": os.cpu_count(), "affinity": len(os.sched_getaffinity(0))}
 
 
 def default_pair(form):
@@ -571,6 +620,246 @@ def grad_block(fg, torch, dev):
             "dE_dtheta": {k: float(v) for k, v in zip(("A", "xi", "p", "q"), de)}}
 
 
+def relax_timed(fg, torch, dev, stream, cfg, pot, mass, dt, ftol, steps=5, warmup=3, **hkw):
+    """Median time-to-ftol of `steps` relaxations of cfg from its initial
+    configuration (after `warmup` untimed ones): CUDA events on the launching
+    stream around each fire_minimize_dev call (which synchronises its stream),
+    and the host wall time of the same calls.  Returns (result dict, the
+    relaxed positions of the last step)."""
+    x0 = torch.tensor(cfg.x, dtype=torch.float64, device=dev)
+    work = torch.empty_like(x0)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    dev_ms, host_ms, res = [], [], None
+    with fg.FireHandle(cfg.n, mass, pot, dt_start=dt, **hkw) as h:
+        for k in range(warmup + steps):
+            work.copy_(x0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ev0.record(stream)
+            r = h.minimize_dev(work, cfg.box, ftol, MAXITER, stream)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            if k >= warmup:
+                dev_ms.append(ev0.elapsed_time(ev1))
+                host_ms.append(1e3 * (t1 - t0))
+                res = r
+    med = statistics.median(dev_ms)
+    return ({"value": cfg.n * res.iterations / (med * 1e-3), "unit": UNIT,
+             "time_to_ftol_ms": med, "time_to_ftol_host_ms": statistics.median(host_ms),
+             "times_ms": [round(t, 4) for t in dev_ms], "iterations": int(res.iterations),
+             "force_evals": int(res.force_evals), "stop": int(res.stop),
+             "final_fmax_atom": res.fmax_atom, "energy_per_atom": res.energy / cfg.n},
+            work)
+
+
+def ieee_check(fg, torch, dev, cfg, x):
+    """max_i |F_i| and E/N of positions x (CUDA) with the IEEE-FP64 kernels."""
+    pot = fg.Potential(fg.FIRE_POT_RGL, skin=0.3, pair_eval=fg.FIRE_PAIR_ANALYTIC, **fi.RGL_CU)
+    with fg.FireHandle(cfg.n, fi.CU_MASS, pot, dt_start=fi.CU_DT) as hv:
+        fv = torch.empty_like(x)
+        ev = torch.zeros(1, dtype=torch.float64, device=dev)
+        fg.fire_energy_forces_dev(hv.h, x, cfg.box, fv, ev)
+        torch.cuda.synchronize()
+    return float(torch.linalg.norm(fv, dim=1).max().item()), float(ev.item()) / cfg.n
+
+
+def lj_block(fg, torch, dev, stream):
+    """Config 1: the LJ FCC 4^3-cell box with one vacancy (255 atoms, uniform
+    +-0.1 sigma noise, seed 1), FP64, Table 1 parameters with dt_start =
+    0.005 tau, relaxed to max_i |F_i| < 1e-8: time-to-ftol (median of 5 after
+    3 warm-up relaxations), iterations and atom-iterations per second."""
+    cfg = CONFIGS["lj256"]()
+    pot, mass, dt, ftol = potential_for("lj256")
+    r, _ = relax_timed(fg, torch, dev, stream, cfg, pot, mass, dt, ftol)
+    r.update({"workload": f"{cfg.name} ({cfg.n} atoms), LJ shifted rc = 2.5 sigma, FP64, "
+                          f"max|F_i| < {ftol:g}", "atoms": cfg.n, "ftol": ftol})
+    return r
+
+
+def rgl32k_block(fg, torch, dev, stream):
+    """Config 2: the RGL-Cu FCC 20^3-cell box with 1 % vacancies (31,680
+    atoms, Gaussian 0.05 A noise, seed 2) relaxed to max_i |F_i| < 1e-6 eV/A
+    in the FP64 form (double-float table terms, the library default) and the
+    FP32-pair form (each stop confirmed in FP64 by the library); each relaxed
+    structure re-evaluated with the IEEE-FP64 kernels."""
+    cfg = CONFIGS["rgl32k"]()
+    out = {"workload": f"{cfg.name} ({cfg.n} atoms), RGL Cu, max|F_i| < {FTOL:g} eV/A",
+           "atoms": cfg.n, "ftol": FTOL}
+    for form, pair in (("fp64", "table"), ("fp32pair", "analytic")):
+        pot, mass, dt, ftol = potential_for("rgl32k", form)
+        pot.pair_eval = fg.FIRE_PAIR_ANALYTIC if pair == "analytic" else fg.FIRE_PAIR_TABLE
+        r, x = relax_timed(fg, torch, dev, stream, cfg, pot, mass, dt, ftol)
+        r["pair_eval"] = pair
+        r["final_fmax_atom_ieee_fp64_check"], r["energy_per_atom_ieee_fp64_check"] = \
+            ieee_check(fg, torch, dev, cfg, x)
+        out[form] = r
+    return out
+
+
+def _timed_oracle(fn, threads):
+    import oracle
+    oracle.set_threads(threads)
+    t0 = time.perf_counter()
+    out = fn()
+    return out, time.perf_counter() - t0
+
+
+def cpu_oracle_block(gpu, full_single=False):
+    """The FP64 CPU oracle as it stands, timed on this host's cores for the
+    small configurations: on all cores and on one thread.  `gpu` carries the
+    GPU iteration counts used where a single-thread run is a bounded sample
+    (per-iteration time x iterations, marked "estimate").  The oracle runs
+    all-pairs forces for boxes under 3 cells per axis, else its cell grid
+    (bit-identical to all-pairs, tested)."""
+    import oracle
+    oracle.build()
+    allc = oracle.max_threads()
+    out = {"host": host_cpu(), "threads_all": allc}
+    lj = oracle.Potential("lj", eps=1.0, sigma=1.0, rc_lj=2.5)
+    cu = oracle.Potential("rgl", **fi.RGL_CU)
+    plj, pcu = oracle.Params(dt_start=fi.LJ_DT), oracle.Params(dt_start=fi.CU_DT)
+
+    def mode(c, rc):
+        return (oracle.FORCE_CELLS if np.all(np.floor(np.asarray(c.box) / rc) >= 3)
+                else oracle.FORCE_BRUTE)
+
+    def entry(n, iters, secs, kind, note):
+        return {"seconds": round(secs, 3), "iterations": int(iters), "kind": kind,
+                "value": n * iters / secs, "unit": UNIT, "note": note}
+
+    try:
+        # config 1: both in full
+        c = CONFIGS["lj256"]()
+        blk = {"atoms": c.n}
+        for th, key in ((allc, "all_cores"), (1, "one_thread")):
+            (x, r, _), t = _timed_oracle(lambda: oracle.fire2(
+                c.x, c.box, lj, plj, fi.LJ_MASS, 1e-8, MAXITER, mode=oracle.FORCE_BRUTE), th)
+            blk[key] = entry(c.n, r.iterations, t, "full",
+                             f"whole relaxation to max|F_i| < 1e-8, {th} thread(s)")
+            blk["energy_per_atom"] = r.energy / c.n
+        out["lj256"] = blk
+
+        # config 2: all cores in full; one thread in full or as a sample
+        c = CONFIGS["rgl32k"]()
+        blk = {"atoms": c.n}
+        (x, r, _), t = _timed_oracle(lambda: oracle.fire2(
+            c.x, c.box, cu, pcu, fi.CU_MASS, FTOL, MAXITER, mode=oracle.FORCE_CELLS), allc)
+        blk["all_cores"] = entry(c.n, r.iterations, t, "full",
+                                 f"whole relaxation to max|F_i| < {FTOL:g} eV/A, {allc} threads")
+        blk["energy_per_atom"] = r.energy / c.n
+        its_full = r.iterations
+        if full_single:
+            (x, r1, _), t = _timed_oracle(lambda: oracle.fire2(
+                c.x, c.box, cu, pcu, fi.CU_MASS, FTOL, MAXITER, mode=oracle.FORCE_CELLS), 1)
+            blk["one_thread"] = entry(c.n, r1.iterations, t, "full",
+                                      "whole relaxation, 1 thread")
+        else:
+            k = 8
+            (_, r1, _), t = _timed_oracle(lambda: oracle.fire2(
+                c.x, c.box, cu, pcu, fi.CU_MASS, 0.0, k, mode=oracle.FORCE_CELLS), 1)
+            per_eval = t / (k + 1)
+            blk["one_thread"] = entry(c.n, its_full, per_eval * (its_full + 1), "estimate",
+                                      f"{k} FIRE iterations (+1 initial evaluation) timed on 1 "
+                                      f"thread ({t:.1f} s); the remaining "
+                                      f"{its_full - k} of the oracle's {its_full} iterations "
+                                      "extrapolated at the same time per evaluation")
+        out["rgl32k"] = blk
+
+        # config 5: relaxation to 1e-10 eV/A + implicit gradient (CG to 1e-10)
+        c = fi.rgl_vacancy_box(ncell=20, seed=5, n_vac=1)
+        blk = {"atoms": c.n}
+        site = c.meta["vacancy_sites"][0]
+        d = c.meta["lattice"] - site
+        d -= c.box * np.rint(d / c.box)
+        sel = np.flatnonzero(np.sum(d * d, 1) < 36.0)
+
+        def grad_pipeline(ftol_relax, maxiter, cg_maxit):
+            xr, rr, _ = oracle.fire2(c.x, c.box, cu, pcu, fi.CU_MASS, ftol_relax, maxiter,
+                                     mode=oracle.FORCE_CELLS)
+            t_relax = time.perf_counter()
+            dd = xr[sel] - c.meta["lattice"][sel]
+            dd -= c.box * np.rint(dd / c.box)
+            g = np.zeros_like(xr)
+            g[sel] = 2.0 * dd
+            try:
+                lam, it = oracle.rgl_cg(xr, c.box, cu, g, 1e-10, cg_maxit, mode=oracle.FORCE_CELLS)
+            except RuntimeError:
+                it = cg_maxit
+            _ = oracle.rgl_param_derivs(xr, c.box, cu, mode=oracle.FORCE_CELLS)
+            return rr, it, t_relax
+
+        t0 = time.perf_counter()
+        oracle.set_threads(allc)
+        rr, cg_it, t_mid = grad_pipeline(1e-10, MAXITER, 20000)
+        t1 = time.perf_counter()
+        blk["all_cores"] = {"seconds": round(t1 - t0, 3), "relax_seconds": round(t_mid - t0, 3),
+                            "fire_iterations": int(rr.iterations), "cg_iterations": int(cg_it),
+                            "kind": "full", "note": f"relaxation to max|F_i| < 1e-10 eV/A, CG "
+                                                    f"to 1e-10, dF/dtheta; {allc} threads"}
+        if full_single:
+            oracle.set_threads(1)
+            t0 = time.perf_counter()
+            rr1, cg1, t_mid = grad_pipeline(1e-10, MAXITER, 20000)
+            blk["one_thread"] = {"seconds": round(time.perf_counter() - t0, 3), "kind": "full",
+                                 "fire_iterations": int(rr1.iterations),
+                                 "cg_iterations": int(cg1)}
+        else:
+            oracle.set_threads(1)
+            k, kc = 4, 4
+            t0 = time.perf_counter()
+            rr1, _, t_mid = grad_pipeline(0.0, k, kc)
+            t1 = time.perf_counter()
+            per_eval = (t_mid - t0) / (k + 1)
+            per_cg = (t1 - t_mid) / kc      # includes dF/dtheta once (small)
+            est = per_eval * (rr.iterations + 1) + per_cg * cg_it
+            blk["one_thread"] = {"seconds": round(est, 3), "kind": "estimate",
+                                 "note": f"{k} FIRE iterations ({t_mid - t0:.1f} s) and {kc} CG "
+                                         f"iterations ({t1 - t_mid:.1f} s) timed on 1 thread, "
+                                         f"extrapolated to the all-core run's "
+                                         f"{rr.iterations} FIRE and {cg_it} CG iterations"}
+        out["grad32k"] = blk
+
+        # config 4: 16 of the 512 boxes (every 32nd by size) relaxed in full
+        cfgs = fi.rgl_batch(n_sys=512, seed=4)
+        sizes = np.array([cc.n for cc in cfgs])
+        pick = np.argsort(sizes, kind="stable")[16::32]
+        oracle.set_threads(allc)
+        t0 = time.perf_counter()
+        ai = 0
+        for sidx in pick:
+            cc = cfgs[sidx]
+            _, rb, _ = oracle.fire2(cc.x, cc.box, cu, pcu, fi.CU_MASS, FTOL, MAXITER,
+                                    mode=mode(cc, fi.RGL_CU["rc"] + 0.3))
+            ai += cc.n * rb.iterations
+        t = time.perf_counter() - t0
+        rate = ai / t
+        blk = {"systems_sampled": len(pick), "atoms_sampled": int(sizes[pick].sum()),
+               "all_cores": {"value": rate, "unit": UNIT, "seconds": round(t, 3),
+                             "kind": "sample",
+                             "note": f"16 of the 512 boxes (every 32nd by size) relaxed in full "
+                                     f"on {allc} threads"}}
+        if gpu.get("batch_atom_iters"):
+            blk["all_cores"]["estimate_512_seconds"] = gpu["batch_atom_iters"] / rate
+        med = cfgs[pick[len(pick) // 2]]
+        oracle.set_threads(1)
+        t0 = time.perf_counter()
+        _, rb, _ = oracle.fire2(med.x, med.box, cu, pcu, fi.CU_MASS, FTOL, MAXITER,
+                                mode=mode(med, fi.RGL_CU["rc"] + 0.3))
+        t = time.perf_counter() - t0
+        blk["one_thread"] = {"value": med.n * rb.iterations / t, "unit": UNIT,
+                             "seconds": round(t, 3), "kind": "sample",
+                             "note": f"the median-size sampled box ({med.n} atoms) relaxed in "
+                                     "full on 1 thread"}
+        if gpu.get("batch_atom_iters"):
+            blk["one_thread"]["estimate_512_seconds"] = \
+                gpu["batch_atom_iters"] / blk["one_thread"]["value"]
+        out["batch512"] = blk
+    finally:
+        oracle.set_threads(allc)
+    return out
+
+
 INTEGRATORS = {"semi_implicit_euler": 0, "explicit_euler": 1, "velocity_verlet": 2, "leapfrog": 3}
 
 
@@ -619,6 +908,45 @@ def study_block(fg, torch, dev):
         f"{d * 1e3:g}fs/{tm:g}": run(c, pot, mass, ftol, dt_start=d, alpha0=0.15,
                                      tmax=tm)["force_evals"]
         for d in (0.0005, 0.001, 0.002, 0.004) for tm in tmaxs}
+    return out
+
+
+def roofline_block(fg, args, is_rgl, pair, stages, pairs, workload="rgl1m"):
+    """Roofline of the dominant pair kernel against a measured hardware peak.
+    No pass is HBM-bound (DRAM 5-15 % in every ncu capture), so the bound is
+    the arithmetic unit the kernel issues on: the measured FP32 FMA rate for
+    the double-float and FP32-pair kernels, the measured FP64 FMA rate for
+    the IEEE-FP64 ones.  achieved = the method's FLOPs per pair (exponentials,
+    taper, sums; METHOD_FLOP_PER_PAIR) x pairs within rc / the kernel's mean
+    CUDA-event time."""
+    if is_rgl:
+        dom = "density" if stages["density"] >= stages["force"] else "force"
+        kname, unit = STAGE_KERNELS[(args.form, pair)][dom]
+        key = dom
+    else:
+        dom, kname, unit, key = "force", "k_force_lj", "fp64", "force_lj"
+    flop = METHOD_FLOP_PER_PAIR[key] * pairs
+    achieved = flop / (stages[dom] * 1e-3)
+    fp32 = fg.fire_diag_fma_peak(1)
+    fp64 = fg.fire_diag_fma_peak(0)
+    peak = fp64 if unit == "fp64" else fp32
+    src = ("measured %s FMA issue rate on this GPU (fire_diag_fma_peak, FMA = 2 FLOP)"
+           % ("FP64" if unit == "fp64" else "FP32"))
+    out = {"bound": "alu", "kernel": kname, "achieved": achieved / 1e12, "peak": peak / 1e12,
+           "unit": "TFLOP/s", "frac": achieved / peak, "peak_source": src,
+           "pipe": {"ff": "FP32 (double-float arithmetic)", "fp32": "FP32",
+                    "fp64": "FP64"}[unit],
+           "flop_per_pair": METHOD_FLOP_PER_PAIR[key], "flop_count": "method (per pass)",
+           "pairs_within_rc": pairs, "stage_ms": stages,
+           "fp64_peak": fp64 / 1e12, "fp32_peak": fp32 / 1e12,
+           "vs_fp64_peak": achieved / fp64}
+    if unit == "ff":
+        # the emulation's own ceiling: one double-float multiply-add is 18 FP32
+        # instructions; not a hardware roof
+        out["emulation_efficiency"] = achieved / (fp32 / FF_FP32_PER_FMA)
+    ncu = read_ncu(kname, workload)
+    out["traffic"] = (ncu or {}).get("dram_bytes")
+    out["ncu"] = ncu
     return out
 
 
@@ -703,28 +1031,7 @@ def run_gpu(args):
     # per-stage device times (CUDA events) for the roofline of the dominant kernel
     stages = h.profile_stages(cfg.x, cfg.box, reps=5)
     pairs = count_pairs(cfg.x, cfg.box, rc)
-    if is_rgl:
-        dom = "density" if stages["density"] >= stages["force"] else "force"
-        kname, key, unit = STAGE_KERNELS[(args.form, pair)][dom]
-    else:
-        dom, kname, key, unit = "force", "k_force_lj", "force_lj", "fp64"
-    flop = ALG_FLOP_PER_PAIR[key] * pairs
-    achieved = flop / (stages[dom] * 1e-3)
-    if unit == "fp64":
-        peak = fg.fire_diag_fma_peak(0)
-        src = "measured FP64 FMA rate (fire_diag_fma_peak), FMA = 2 FLOP"
-    elif unit == "fp32":
-        peak = fg.fire_diag_fma_peak(1)
-        src = "measured FP32 FMA rate (fire_diag_fma_peak), FMA = 2 FLOP"
-    else:
-        peak = fg.fire_diag_fma_peak(1) / FF_FP32_PER_FMA
-        src = ("double-float ALU peak: measured FP32 FMA rate / %d (FP32 instructions per "
-               "double-float multiply-add), in FP64-equivalent FLOP/s" % FF_FP32_PER_FMA)
-    out["roofline"] = {"bound": "alu", "kernel": kname, "achieved": achieved / 1e12,
-                       "peak": peak / 1e12, "unit": "TFLOP/s",
-                       "frac": achieved / peak, "traffic": read_traffic(kname),
-                       "peak_source": src, "flop_per_pair": ALG_FLOP_PER_PAIR[key],
-                       "stage_ms": stages, "pairs_within_rc": pairs}
+    out["roofline"] = roofline_block(fg, args, is_rgl, pair, stages, pairs)
     # HBM roofline of the whole iteration, as the metric asks
     alg_b = ALG_BYTES_PER_ATOM_ITER["rgl" if is_rgl else "lj"]
     try:
@@ -790,6 +1097,9 @@ def run_gpu(args):
                     "final_fmax_atom_ieee_fp64_check": f64_fmax,
                     "energy_per_atom_ieee_fp64_check": e64 / n,
                     "energy_per_atom_diff_vs_headline": (e64 - e_head) / n}
+    if is_rgl and not args.no_small and world == 1:
+        out["lj"] = lj_block(fg, torch, dev, stream)
+        out["rgl32k"] = rgl32k_block(fg, torch, dev, stream)
     if is_rgl and not args.no_neb and world == 1:
         out["neb"] = neb_block(fg, torch, args.form, dev)
         out["sw"] = sw_block(fg, torch, dev)
@@ -797,7 +1107,24 @@ def run_gpu(args):
         out["grad"] = grad_block(fg, torch, dev)
     if rank == 0:
         if world == 1 and not args.no_cpu:
-            out["cpu_baseline"] = cpu_baseline(cfg, args)
+            cb = cpu_baseline(cfg, args)
+            if is_rgl and not args.no_small:
+                gpu = {}
+                if "batched" in out:
+                    gpu["batch_atom_iters"] = (out["batched"]["value"] *
+                                               out["batched"]["ms_per_step"] * 1e-3)
+                cb["configs"] = cpu_oracle_block(gpu, args.cpu_full)
+                co = cb["configs"]
+                # energy of each GPU relaxation against the oracle's own
+                # relaxation of the same box (same ftol)
+                out["lj"]["energy_err_vs_oracle_per_atom"] = \
+                    out["lj"]["energy_per_atom"] - co["lj256"]["energy_per_atom"]
+                out["lj"]["oracle_iterations"] = co["lj256"]["all_cores"]["iterations"]
+                for form in ("fp64", "fp32pair"):
+                    out["rgl32k"][form]["energy_err_vs_oracle_per_atom"] = \
+                        out["rgl32k"][form]["energy_per_atom"] - co["rgl32k"]["energy_per_atom"]
+                out["rgl32k"]["oracle_iterations"] = co["rgl32k"]["all_cores"]["iterations"]
+            out["cpu_baseline"] = cb
         print(json.dumps(out), flush=True)
     if world > 1:
         import torch.distributed as dist
@@ -834,7 +1161,9 @@ def cpu_sample(cfg, k):
     return {"value": cfg.n * r.iterations / t, "unit": UNIT, "cores": oracle.max_threads(),
             "kind": "oracle", "seconds": t,
             "sample": f"{r.iterations} FIRE iterations (+1 initial force evaluation) of the same "
-                      f"{cfg.n}-atom box, oracle cell-grid forces, {t:.1f} s"}
+                      f"{cfg.n}-atom box timed ({t:.1f} s), oracle cell-grid forces; the "
+                      "metric divides the atom-iterations of that sample by its time, so no "
+                      "whole relaxation is extrapolated"}
 
 
 def cpu_baseline(cfg, args):

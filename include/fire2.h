@@ -290,6 +290,32 @@ fire_status fire_set_exec_mode(fire_handle_t* h, int32_t mode, int32_t chunk);
  * shape from fire_batch_set_tuning). */
 fire_status fire_set_threads_per_atom(fire_handle_t* h, int32_t tpa, int32_t* chosen);
 
+/* Shared-memory tiles of the FP64 form's half-list passes (pot.precision =
+ * FIRE_PREC_FP64, pair_eval = FIRE_PAIR_TABLE, newton on; other forms ignore
+ * the setting).  F = -grad E (Sec. 2.1) on a half list owes each pair's term
+ * to both atoms.  With tiles the atoms are taken brick of cells by brick of
+ * cells (4 x 4 x 2 list cells): a brick's atoms and every neighbour their
+ * lists name are staged in shared memory, the neighbours' terms are summed
+ * there exactly (two 32-bit fixed-point words per component, 2^-40 units),
+ * and each staged atom's sum goes to global memory with one FP64 atomic per
+ * component, in place of one per pair.  Neighbours beyond stage_cap distinct
+ * atoms per brick, and terms of 15 or more (eV/A) per component, take the
+ * per-pair FP64 atomics.  Forces and densities agree with the untiled
+ * passes to the rounding of their sums (well inside the 1e-10 relative
+ * force bar).  mode: FIRE_TILES_AUTO (default: tiles from 200,000 atoms of
+ * a single periodic-or-open system in cell mode), FIRE_TILES_ON (whenever
+ * the list is in cell mode), FIRE_TILES_OFF.  stage_cap: 0 for the largest
+ * stage (1920 atoms), else 64..1920 (smaller stages send more pairs down
+ * the per-pair path; a testing aid).  Applies to later calls on h; the
+ * paper has no counterpart.  Errors: FIRE_ERR_ARG (mode, stage_cap, batched
+ * handle). */
+typedef enum {
+    FIRE_TILES_AUTO = 0,
+    FIRE_TILES_ON = 1,
+    FIRE_TILES_OFF = 2
+} fire_tiles;
+fire_status fire_set_pair_tiles(fire_handle_t* h, int32_t mode, int32_t stage_cap);
+
 /* Wall-clock budget of one device relaxation loop (default 3600 s, 0 = none).
  * When exceeded, the loop stops at the next iteration boundary and the call
  * returns FIRE_ERR_TIMEOUT.  Errors: FIRE_ERR_ARG (h NULL or seconds < 0). */

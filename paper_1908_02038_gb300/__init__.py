@@ -40,6 +40,7 @@ STATUS_NAMES = {0: "FIRE_OK", 1: "FIRE_ERR_ARG", 2: "FIRE_ERR_CUDA", 3: "FIRE_ER
 # Every symbol include/fire2.h declares (checked by the ABI test).
 EXPORTED = ("fire_abi_version", "fire_default_params", "fire_init", "fire_minimize",
             "fire_minimize_dev", "fire_energy_forces", "fire_energy_forces_dev",
+            "fire_set_pair_tiles",
             "fire_set_time_budget", "fire_profile_stages", "fire_diag_fma_peak",
             "fire_energy_forces_noalloc", "fire_set_exec_mode", "fire_set_threads_per_atom",
             "fire_diag_exp",
@@ -49,6 +50,7 @@ EXPORTED = ("fire_abi_version", "fire_default_params", "fire_init", "fire_minimi
             "fire_diag_rgl_table", "fire_set_dof_mask", "fire_neb_init", "fire_neb_minimize",
             "fire_neb_minimize_dev", "fire_last_error", "fire_destroy")
 FIRE_EXEC_GRAPH_WHILE, FIRE_EXEC_CHUNKED = 0, 1
+FIRE_TILES_AUTO, FIRE_TILES_ON, FIRE_TILES_OFF = 0, 1, 2
 STAGES = ("build", "density", "embed", "force", "reduce", "control", "update")
 
 
@@ -121,6 +123,7 @@ def load_library(path: str | None = None):
     lib.fire_set_time_budget.argtypes = [H, C.c_double]
     lib.fire_set_exec_mode.argtypes = [H, C.c_int32, C.c_int32]
     lib.fire_set_threads_per_atom.argtypes = [H, C.c_int32, C.POINTER(C.c_int32)]
+    lib.fire_set_pair_tiles.argtypes = [H, C.c_int32, C.c_int32]
     lib.fire_set_dof_mask.argtypes = [H, C.c_void_p]
     lib.fire_neb_init.argtypes = [C.POINTER(H), C.c_int32, C.POINTER(fire_system_t),
                                   C.POINTER(fire_potential_t), C.POINTER(fire_params_t),
@@ -237,6 +240,12 @@ def fire_set_threads_per_atom(handle, tpa: int = 0) -> int:
     out = C.c_int32(0)
     _check(load_library().fire_set_threads_per_atom(handle, int(tpa), C.byref(out)), handle)
     return out.value
+
+
+def fire_set_pair_tiles(handle, mode: int = FIRE_TILES_AUTO, stage_cap: int = 0) -> None:
+    """Shared-memory tiles of the FP64 half-list passes: FIRE_TILES_AUTO,
+    FIRE_TILES_ON or FIRE_TILES_OFF; stage_cap 0 = the largest stage."""
+    _check(load_library().fire_set_pair_tiles(handle, int(mode), int(stage_cap)), handle)
 
 
 def fire_minimize(handle, pos: np.ndarray, box, ftol: float, maxiter: int) -> fire_result_t:
@@ -587,6 +596,9 @@ class FireHandle:
 
     def set_threads_per_atom(self, tpa=0):
         return fire_set_threads_per_atom(self.h, tpa)
+
+    def set_pair_tiles(self, mode=FIRE_TILES_AUTO, stage_cap=0):
+        fire_set_pair_tiles(self.h, mode, stage_cap)
 
     def set_time_budget(self, seconds):
         fire_set_time_budget(self.h, seconds)

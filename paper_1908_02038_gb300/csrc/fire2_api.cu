@@ -16,6 +16,7 @@
 #include "fire2_device.cuh"
 #include "fire2_grad.cuh"
 #include "fire2_neb.cuh"
+#include "fire2_tile.cuh"
 
 using namespace fire2;
 
@@ -104,6 +105,11 @@ struct fire_handle {
     int img_n = 0;                   // atoms per image (n, except for NEB handles)
     bool verify = false;             // FP32-pair: stops on ftol confirmed in FP64
     int sms = 0;                     // SM count of the device
+    int tile_mode = FIRE_TILES_AUTO; // shared-memory tiles of the FP64 half-list passes
+    int stage_cap = 0;               // staged atoms per tile (0 = kStageMax)
+    size_t loc_slots = 0;            // allocated nbr_loc entries
+    int tile_alloc = 0;              // allocated tiles (tile_key, tile_ns)
+    bool tile_attr = false;          // dynamic shared-memory limits of the tile kernels set
     NebState* neb = nullptr;
     std::string err;
 };
@@ -174,6 +180,18 @@ int auto_tpa(const fire_potential_t& p, long long n, int sms) {
     return tpa_for(n, sms, p.precision == FIRE_PREC_FP32_PAIR ? 512 : 1024);
 }
 
+// Atoms from which the FP64 half-list passes run on shared-memory tiles by
+// default (FIRE_TILES_AUTO).
+constexpr long long kTileAutoAtoms = 200000;
+
+// Whether the FP64 half-list passes of this geometry run on tiles: the FP64
+// table form on a half list, cell mode, one system.
+bool tiles_wanted(const fire_handle* h, const GeoC& g) {
+    if (!fixed64_half(h->pot) || g.brute || h->neb || g.img_n != h->n) return false;
+    if (h->tile_mode == FIRE_TILES_OFF) return false;
+    return h->tile_mode == FIRE_TILES_ON || (long long)h->n >= kTileAutoAtoms;
+}
+
 // Neighbour geometry for a box.  The list radius is rc + skin, with the skin
 // reduced where a periodic axis is shorter than 2 (rc + skin) so that the
 // minimum image stays unique within the list radius.
@@ -217,7 +235,24 @@ GeoC make_geo(const fire_handle* h, const double box[3]) {
         g.Lq64[a] = std::llrint(std::ldexp(box[a], kFixedBits64));
     }
     g.img_n = h->img_n > 0 ? h->img_n : h->n;
-    g.ncell_img = g.nc[0] * g.nc[1] * g.nc[2];
+    // bricks of cells: the tiles of the FP64 half-list passes (fire2_tile.cuh);
+    // flat in z, the axis the half list cuts (a tile's stage then holds about
+    // twice its own atoms); bricks of one cell, the plain cell order, otherwise
+    for (int a = 0; a < 3; ++a) {
+        g.bk[a] = 1;
+        g.nbk[a] = g.nc[a];
+    }
+    if (tiles_wanted(h, g)) {
+        const int want[3] = {4, 4, 2};
+        for (int a = 0; a < 3; ++a) {
+            g.bk[a] = std::min(want[a], g.nc[a]);
+            g.nbk[a] = ceil_div(g.nc[a], g.bk[a]);
+        }
+        g.tiled = 1;
+        g.ntile = g.nbk[0] * g.nbk[1] * g.nbk[2];
+        g.stage_cap = h->stage_cap > 0 ? h->stage_cap : kStageMax;
+    }
+    g.ncell_img = g.nbk[0] * g.nbk[1] * g.nbk[2] * g.bk[0] * g.bk[1] * g.bk[2];
     return g;
 }
 
@@ -244,6 +279,14 @@ void drop_graph(fire_handle* h) {
     h->exec = nullptr;
     h->graph = nullptr;
     h->has_graph = false;
+}
+
+// Blocks of the tile passes: two per SM (the force pass stages 105 KB per
+// block), looping over the tiles; never more than the energy partials
+// allocated for the density pass.
+int tile_grid(const fire_handle* h, const GeoC& g) {
+    const int nb_max = ceil_div((long long)h->n * kMaxTpa, kForceBlock);
+    return std::max(1, std::min(std::min(g.ntile, 2 * h->sms), nb_max));
 }
 
 fire_status ensure_buffers(fire_handle* h, const GeoC& g, int cap) {
@@ -275,6 +318,37 @@ fire_status ensure_buffers(fire_handle* h, const GeoC& g, int cap) {
         h->ncell_alloc = ncell;
     }
     h->b.ncell = ncell;
+    if (g.tiled) {
+        const size_t slots = (size_t)h->cap * h->n;
+        if (slots > h->loc_slots) {
+            drop_graph(h);
+            cudaFree(h->b.nbr_loc);
+            h->b.nbr_loc = nullptr;
+            h->loc_slots = 0;
+            CK(h, cudaMalloc(&h->b.nbr_loc, slots * sizeof(uint16_t)));
+            h->loc_slots = slots;
+        }
+        if (g.ntile > h->tile_alloc) {
+            drop_graph(h);
+            cudaFree(h->b.tile_key);
+            cudaFree(h->b.tile_ns);
+            h->b.tile_key = nullptr;
+            h->b.tile_ns = nullptr;
+            h->tile_alloc = 0;
+            CK(h, cudaMalloc(&h->b.tile_key, (size_t)g.ntile * kStageMax * sizeof(uint32_t)));
+            CK(h, cudaMalloc(&h->b.tile_ns, (size_t)g.ntile * sizeof(int)));
+            h->tile_alloc = g.ntile;
+        }
+        if (!h->tile_attr) {
+            CK(h, cudaFuncSetAttribute(k_density_tile, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kDensTileSmem));
+            CK(h, cudaFuncSetAttribute(k_force_tile, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kForceTileSmem));
+            h->tile_attr = true;
+        }
+    }
+    // energy partials of the density (or only) pass, then the embedding's
+    h->b.ne_dens = g.tiled ? tile_grid(h, g) : h->b.nb_force;
     return FIRE_OK;
 }
 
@@ -290,6 +364,9 @@ void launch_build(fire_handle* h, const GeoC& g, int force, cudaStream_t s) {
         k_cell_sort<<<ceil_div(h->b.ncell, kElemBlock), kElemBlock, 0, s>>>(h->b, g, force);
     }
     k_nbr_build<<<ceil_div(n, kForceBlock), kForceBlock, 0, s>>>(h->b, g, force);
+    if (g.tiled)
+        k_tile_build<<<std::max(1, std::min(g.ntile, 4 * h->sms)), kTileThreads, 0, s>>>(h->b, g,
+                                                                                         force);
 }
 
 // The pair passes for the handle's threads per atom (b.tpa).
@@ -364,6 +441,11 @@ void launch_forces(fire_handle* h, const GeoC& g, cudaStream_t s, bool confirm_p
     if (tab && h->pot.precision == FIRE_PREC_FP32_PAIR) {
         k_density32_tab<<<h->nb_tab_d, kTabBlock, h->smem_d, s>>>(h->b, h->potc, g);
         k_force32_tab<<<h->nb_tab_f, kTabBlock, h->smem_f, s>>>(h->b, h->potc, g);
+    } else if (tab && fixed64_half(h->pot) && g.tiled) {
+        const int nt = tile_grid(h, g);
+        k_density_tile<<<nt, kTileThreads, kDensTileSmem, s>>>(h->b, h->potc, g);
+        k_embed<<<h->b.nb_embed, kElemBlock, 0, s>>>(h->b);
+        k_force_tile<<<nt, kTileThreads, kForceTileSmem, s>>>(h->b, h->potc, g);
     } else if (tab && fixed64_half(h->pot)) {
         density_ff<true>(h->b, h->potc, g, h->b.nb_force, s);
         k_embed<<<h->b.nb_embed, kElemBlock, 0, s>>>(h->b);
@@ -1006,6 +1088,7 @@ static fire_status init_handle(fire_handle_t** hp, const fire_system_t* sys,
     }
     b.nb_verify = h->verify ? ceil_div((long long)h->n * b.tpa, kForceBlock) : 0;
     b.pass_role = h->verify ? 1 : 0;
+    b.ne_dens = b.nb_force;
     CKI(cudaMalloc(&b.x, n * sizeof(dvec4)));
     CKI(cudaMalloc(&b.v, n * sizeof(dvec4)));
     CKI(cudaMalloc(&b.f, n * sizeof(dvec4)));
@@ -1090,7 +1173,7 @@ void fire_destroy(fire_handle_t* h) {
     void* ptrs[] = {b.x, b.v, b.f, b.xref, b.xf, b.xq, b.xq64, b.fpff, b.fp32, (void*)b.exp32_table,
                     (void*)b.exp_table, b.rho, b.fp, b.nbr, b.nnbr, b.crep, b.cden,
                     b.cell_of, b.cell_count, b.cell_start, b.cell_atoms, b.epart, b.rpart,
-                    b.st, b.pos_io};
+                    b.st, b.pos_io, b.nbr_loc, b.tile_key, b.tile_ns};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->batch) fire2_batch_free(h->batch);
@@ -1202,6 +1285,19 @@ fire_status fire_set_threads_per_atom(fire_handle_t* h, int32_t tpa, int32_t* ch
         if (h->verify) h->b.nb_verify = ceil_div((long long)h->n * t, kForceBlock);
     }
     if (chosen) *chosen = t;
+    return FIRE_OK;
+}
+
+fire_status fire_set_pair_tiles(fire_handle_t* h, int32_t mode, int32_t stage_cap) {
+    if (!h) return FIRE_ERR_ARG;
+    if (h->batch) return fail(h, FIRE_ERR_ARG, "batched handle: tiles are per single system");
+    if (mode != FIRE_TILES_AUTO && mode != FIRE_TILES_ON && mode != FIRE_TILES_OFF)
+        return fail(h, FIRE_ERR_ARG, "unknown tile mode %d", mode);
+    if (stage_cap != 0 && (stage_cap < 64 || stage_cap > kStageMax))
+        return fail(h, FIRE_ERR_ARG, "stage_cap must be 0 or in [64, %d]", kStageMax);
+    drop_graph(h);
+    h->tile_mode = mode;
+    h->stage_cap = stage_cap;
     return FIRE_OK;
 }
 
@@ -1786,6 +1882,8 @@ fire_status fire_profile_stages(fire_handle_t* h, const double* pos, const doubl
         cudaEventRecord(ev[1], s);
         const bool tab = rgl && h->pot.pair_eval == FIRE_PAIR_TABLE;
         if (tab && f32) k_density32_tab<<<h->nb_tab_d, kTabBlock, h->smem_d, s>>>(h->b, h->potc, g);
+        else if (tab && fixed64_half(h->pot) && g.tiled)
+            k_density_tile<<<tile_grid(h, g), kTileThreads, kDensTileSmem, s>>>(h->b, h->potc, g);
         else if (tab && fixed64_half(h->pot)) density_ff<true>(h->b, h->potc, g, h->b.nb_force, s);
         else if (tab) density_ff<false>(h->b, h->potc, g, h->b.nb_force, s);
         else if (rgl && f32) density32(h->b, h->potc, g, s);
@@ -1794,6 +1892,8 @@ fire_status fire_profile_stages(fire_handle_t* h, const double* pos, const doubl
         if (h->b.nb_embed > 0) k_embed<<<h->b.nb_embed, kElemBlock, 0, s>>>(h->b);
         cudaEventRecord(ev[3], s);
         if (tab && f32) k_force32_tab<<<h->nb_tab_f, kTabBlock, h->smem_f, s>>>(h->b, h->potc, g);
+        else if (tab && fixed64_half(h->pot) && g.tiled)
+            k_force_tile<<<tile_grid(h, g), kTileThreads, kForceTileSmem, s>>>(h->b, h->potc, g);
         else if (tab && fixed64_half(h->pot)) force_ff<true>(h->b, h->potc, g, h->b.nb_force, s);
         else if (tab) force_ff<false>(h->b, h->potc, g, h->b.nb_force, s);
         else if (rgl && f32) force32(h->b, h->potc, g, s);

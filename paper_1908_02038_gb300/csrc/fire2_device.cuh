@@ -44,8 +44,23 @@ struct GeoC {
     // atoms [k img_n, (k + 1) img_n) form image k and interact only among
     // themselves; one system: img_n = n
     int img_n;
-    int ncell_img;         // cells per image (1 in all-pairs mode)
+    int ncell_img;         // cells per image (1 in all-pairs mode), bricks padded
+    // cells are numbered brick by brick: bricks of bk[0] x bk[1] x bk[2] cells,
+    // nbk[a] bricks per axis (the last ones padded with empty cells), cells
+    // inside a brick in (x, y, z) order; bk = 1 gives the plain (x, y, z) order
+    int bk[3], nbk[3];
+    int tiled;             // 1: the FP64 half-list passes run on shared-memory tiles
+    int ntile;             // tiles (bricks of one image) when tiled
+    int stage_cap;         // staged atoms per tile used by the tile build (<= kStageMax)
 };
+
+// Linear index of cell (cx, cy, cz) of image img (brick-major numbering).
+__host__ __device__ __forceinline__ int cell_index(const GeoC& g, int img, int cx, int cy, int cz) {
+    const int bx = cx / g.bk[0], by = cy / g.bk[1], bz = cz / g.bk[2];
+    const int lx = cx - bx * g.bk[0], ly = cy - by * g.bk[1], lz = cz - bz * g.bk[2];
+    return img * g.ncell_img + ((bx * g.nbk[1] + by) * g.nbk[2] + bz) * (g.bk[0] * g.bk[1] * g.bk[2]) +
+           (lx * g.bk[1] + ly) * g.bk[2] + lz;
+}
 
 // FIRE parameters (Table 1) and call arguments, device resident.
 struct DevState {
@@ -66,11 +81,13 @@ struct DevState {
     // the FP32 norm at the configuration being confirmed
     int vstate, vcount, vmode;
     double ftol_user, fn32, fsw;
+    int tile_over;         // tile builds whose stage overflowed (pairs then use global atomics)
 };
 
 struct Bufs {
     int n, cap, ncell;
     int nb_force, nb_embed, nb_red;
+    int ne_dens;           // energy partials written by the density (or only) pass
     int tpa;               // threads per atom of the RGL pair passes that split an
                            // atom's list (FP64 table form, FP32-pair analytic form)
     const uint8_t* dofmask;   // frozen components per atom (bit d = axis d), or NULL
@@ -95,6 +112,13 @@ struct Bufs {
     const float *tab_d32, *tab_f32;
     uint32_t *nbr;
     int *nnbr;
+    // shared-memory tiles of the FP64 half-list passes (fire2_tile.cuh):
+    // nbr_loc[k n + p] = stage slot of the k-th neighbour of the atom at
+    // cell-sorted position p; tile_key[T kStageMax + s] = list entry (atom |
+    // image code) of slot s of tile T; tile_ns[T] = slots in use
+    uint16_t* nbr_loc;
+    uint32_t* tile_key;
+    int* tile_ns;
     double *crep, *cden;
     int *cell_of, *cell_count, *cell_start, *cell_atoms;
     double *epart, *rpart;
@@ -198,7 +222,7 @@ __global__ void k_cell_count(Bufs b, GeoC g, int force) {
     const int cx = cell_coord(x.x, g.Linv[0], g.nc[0], g.per[0]);
     const int cy = cell_coord(x.y, g.Linv[1], g.nc[1], g.per[1]);
     const int cz = cell_coord(x.z, g.Linv[2], g.nc[2], g.per[2]);
-    const int c = (i / g.img_n) * g.ncell_img + (cx * g.nc[1] + cy) * g.nc[2] + cz;
+    const int c = cell_index(g, i / g.img_n, cx, cy, cz);
     b.cell_of[i] = c;
     atomicAdd(&b.cell_count[c], 1);
 }
@@ -323,7 +347,7 @@ __global__ void k_nbr_build(Bufs b, GeoC g, int force) {
                 for (int oz = -1; oz <= 1; ++oz) {
                     const int az = cell_step(cz, oz, g.nc[2], g.per[2]);
                     if (az < 0) continue;
-                    const int c = img * g.ncell_img + (ax * g.nc[1] + ay) * g.nc[2] + az;
+                    const int c = cell_index(g, img, ax, ay, az);
                     for (int k = b.cell_start[c]; k < b.cell_start[c + 1]; ++k) {
                         const int j = b.cell_atoms[k];
                         if (j != i) try_add_pair(b, g, i, xif, j, cnt);
@@ -423,7 +447,7 @@ __global__ void k_embed(Bufs b) {
         if (b.eatom) b.eatom[i] -= sq;
     }
     const double s = block_sum(emb, red);
-    if (threadIdx.x == 0) b.epart[b.nb_force + blockIdx.x] = s;
+    if (threadIdx.x == 0) b.epart[b.ne_dens + blockIdx.x] = s;
 }
 
 // Pass 2: F_i += fs d, F_j -= fs d with fs = [2 phi' + (F'_i + F'_j) g'] / r
@@ -1188,7 +1212,7 @@ __global__ void k_control(Bufs b, int mode, cudaGraphConditionalHandle h, int ha
         if (has_handle && threadIdx.x == 0) cudaGraphSetConditional(h, 0u);
         return;
     }
-    const int ne = b.st->vstate >= 2 ? b.nb_verify : b.nb_force + b.nb_embed;
+    const int ne = b.st->vstate >= 2 ? b.nb_verify : b.ne_dens + b.nb_embed;
     const CtlSums r = ctl_reduce(b, ne, sh);
     if (threadIdx.x != 0) return;
     const double P = r.P, F2 = r.F2, V2 = r.V2, fa2 = r.fa2, fin = r.fin, E = r.E;
