@@ -72,6 +72,9 @@ STAGE_KERNELS = {
     ("fp32pair", "table"): {"density": ("k_density32_tab", "fp32"),
                             "force": ("k_force32_tab", "fp32")},
 }
+# the FP64 table form on a half list runs its pair passes on shared-memory
+# tiles when asked (--tiles on); the library's automatic choice is untiled
+TILED_KERNELS = {"density": ("k_density_tile", "ff"), "force": ("k_force_tile", "ff")}
 # FP32 instructions of one double-float multiply-add (ff_mul 7 + ff_add 11,
 # counted from fire2_table.cuh): the emulation's own ceiling is the FP32 FMA
 # rate / 18 in FP64-equivalent FLOP/s (reported as emulation_efficiency,
@@ -95,6 +98,9 @@ def parse():
                          "tables for fp64, exponentials for fp32pair, the faster of each)")
     ap.add_argument("--newton", default="auto", choices=["auto", "on", "off"],
                     help="FP64 tabulated form: half list + atomics (on) or full list (off)")
+    ap.add_argument("--tiles", default="auto", choices=["auto", "on", "off"],
+                    help="FP64 half-list passes on shared-memory tiles (auto: the "
+                         "library's choice, untiled)")
     ap.add_argument("--batch-only", action="store_true",
                     help="only the batched block (512 systems), one timed batch (profiling aid)")
     ap.add_argument("--batch-tuning", default=None,
@@ -301,6 +307,16 @@ def host_cpu():
             "nproc": os.cpu_count(), "affinity": len(os.sched_getaffinity(0))}
 
 
+TILE_MODES = {"auto": 0, "on": 1, "off": 2}   # FIRE_TILES_AUTO / ON / OFF
+
+
+def tiles_active(args, form, pair, n):
+    """Whether the library runs the FP64 half-list passes on tiles."""
+    if form != "fp64" or pair != "table" or args.newton == "off":
+        return False
+    return args.tiles == "on"
+
+
 def default_pair(form):
     return "analytic" if form == "fp32pair" else "table"
 
@@ -318,6 +334,7 @@ def relax_form(fg, torch, cfg, form, pair, args, dev, stream, clocks=True, confi
     work = torch.empty_like(x0)
     extra = {} if confirm64 is None else {"confirm64": confirm64}
     h = fg.FireHandle(cfg.n, mass, pot, dt_start=dt, **extra)
+    h.set_pair_tiles(TILE_MODES[args.tiles])
     if args.exec == "chunked":
         h.set_exec_mode(fg.FIRE_EXEC_CHUNKED, 32)
 
@@ -351,23 +368,26 @@ class _NoClock:
         return None
 
 
-def launches_of(results, is_rgl, fp32, cell_mode, chunked=False):
-    """Kernels one relaxation launches: prepare, list build, forces, reduce,
-    control, finalize once; per loop pass update, forces, reduce, control;
+def launches_of(results, is_rgl, fp32, cell_mode, chunked=False, tiled=False):
+    """Kernels one relaxation launches: prepare, list build, forces and
+    finalize once; then per loop pass one cooperative launch of the
+    reductions, the control step and the update (k_step), and the forces
+    (one more pass than iterations: the pass whose control step stops the
+    loop also launches its forces, which return at once);
     the build chain (binning + list) once per rebuild.  The FP32-pair form
     also has the two FP64 confirming passes: launched once in the set-up,
     then in the graph loop only in the passes that confirm a stop (an IF
     node), in the chunked loop with every pass (they return at once unless
     a stop is being confirmed).  Each confirmation is one more loop pass
     (force evaluations - iterations - 1)."""
-    build_k = 6 if cell_mode else 1
+    build_k = (6 + (1 if tiled else 0)) if cell_mode else 1
     force_k = (2 if fp32 else 3) if is_rgl else 1
     total = 0
     for rr in results:
         conf = max(0, rr["force_evals"] - rr["iterations"] - 1) if fp32 else 0
         passes = rr["iterations"] + conf
-        total += (1 + build_k + force_k + 1 + 1 + 1) + (2 if fp32 else 0)
-        total += (1 + force_k + 1 + 1) * passes
+        total += (1 + build_k + force_k + 1) + (2 if fp32 else 0)
+        total += (1 + force_k) * (passes + 1)
         if fp32:
             total += 2 * (passes if chunked else conf)
         total += build_k * max(0, rr["nbr_builds"] - 1)
@@ -911,7 +931,7 @@ def study_block(fg, torch, dev):
     return out
 
 
-def roofline_block(fg, args, is_rgl, pair, stages, pairs, workload="rgl1m"):
+def roofline_block(fg, args, is_rgl, pair, stages, pairs, workload="rgl1m", n=0):
     """Roofline of the dominant pair kernel against a measured hardware peak.
     No pass is HBM-bound (DRAM 5-15 % in every ncu capture), so the bound is
     the arithmetic unit the kernel issues on: the measured FP32 FMA rate for
@@ -921,7 +941,9 @@ def roofline_block(fg, args, is_rgl, pair, stages, pairs, workload="rgl1m"):
     CUDA-event time."""
     if is_rgl:
         dom = "density" if stages["density"] >= stages["force"] else "force"
-        kname, unit = STAGE_KERNELS[(args.form, pair)][dom]
+        kernels = (TILED_KERNELS if tiles_active(args, args.form, pair, n)
+                   else STAGE_KERNELS[(args.form, pair)])
+        kname, unit = kernels[dom]
         key = dom
     else:
         dom, kname, unit, key = "force", "k_force_lj", "fp64", "force_lj"
@@ -981,6 +1003,7 @@ def run_gpu(args):
         pot, mass, dt, _ = potential_for(args.config, args.form)
         pot.pair_eval = fg.FIRE_PAIR_ANALYTIC if pair == "analytic" else fg.FIRE_PAIR_TABLE
         h = fg.FireHandle(n, mass, pot, dt_start=dt)
+        h.set_pair_tiles(TILE_MODES[args.tiles])
         t0 = time.perf_counter()
         e, _ = h.energy_forces(cfg.x, cfg.box)
         print(json.dumps({"eval_only": cfg.name, "atoms": n, "energy": e,
@@ -1020,18 +1043,20 @@ def run_gpu(args):
                                   f"max|F_i| < {ftol:g}",
                       "atoms": n, "ftol": ftol, "form": args.form, "skin": pot.skin,
                       "exec": args.exec, "pair_eval": pair, "newton": args.newton,
+                      "tiles": tiles_active(args, args.form, pair, n),
                       "iterations_per_step": [rr["iterations"] for rr in results],
                       "final_fmax_atom": [rr["fmax_atom"] for rr in results],
                       "final_energy_per_atom": [rr["energy"] / n for rr in results],
                       "nbr_builds": [rr["nbr_builds"] for rr in results],
                       "l2": "inputs larger than L2 (working set > 1 GB at 1M atoms)"},
-           "gpu_launches": launches_of(results, is_rgl, fp32, cell_mode, args.exec == "chunked"),
+           "gpu_launches": launches_of(results, is_rgl, fp32, cell_mode, args.exec == "chunked",
+                                       tiles_active(args, args.form, pair, n)),
            "clocks": m["clocks"]}
 
     # per-stage device times (CUDA events) for the roofline of the dominant kernel
     stages = h.profile_stages(cfg.x, cfg.box, reps=5)
     pairs = count_pairs(cfg.x, cfg.box, rc)
-    out["roofline"] = roofline_block(fg, args, is_rgl, pair, stages, pairs)
+    out["roofline"] = roofline_block(fg, args, is_rgl, pair, stages, pairs, n=n)
     # HBM roofline of the whole iteration, as the metric asks
     alg_b = ALG_BYTES_PER_ATOM_ITER["rgl" if is_rgl else "lj"]
     try:

@@ -275,7 +275,8 @@ typedef enum {
 fire_status fire_set_exec_mode(fire_handle_t* h, int32_t mode, int32_t chunk);
 
 /* Threads per atom in the RGL pair passes of the FP64 table form and of the
- * FP32-pair form with exponentials: tpa = 1, 2, 4 or 8, or 0 for the
+ * FP32-pair form with exponentials, and in the LJ force pass: tpa = 1, 2, 4
+ * or 8, or 0 for the
  * automatic choice, which handles start with (the fewest that give a pass at
  * least 1024 threads per SM in the FP64 form, 512 in the FP32-pair form: on a
  * 152-SM device one thread per atom from about 155,000 and 78,000 atoms, 8
@@ -302,9 +303,13 @@ fire_status fire_set_threads_per_atom(fire_handle_t* h, int32_t tpa, int32_t* ch
  * atoms per brick, and terms of 15 or more (eV/A) per component, take the
  * per-pair FP64 atomics.  Forces and densities agree with the untiled
  * passes to the rounding of their sums (well inside the 1e-10 relative
- * force bar).  mode: FIRE_TILES_AUTO (default: tiles from 200,000 atoms of
- * a single periodic-or-open system in cell mode), FIRE_TILES_ON (whenever
- * the list is in cell mode), FIRE_TILES_OFF.  stage_cap: 0 for the largest
+ * force bar).  mode: FIRE_TILES_ON (whenever the list is in cell mode and
+ * the handle holds one system), FIRE_TILES_OFF, or FIRE_TILES_AUTO (the
+ * default: the library's choice, which is the untiled passes -- on GB300
+ * both passes are bound by the issue of their double-float arithmetic, and
+ * the tiles' staging and fixed-point splits cost more issue than the FP64
+ * additions and atomics they remove: 0.60 against 0.51 ms for the force
+ * pass of the 1M-atom box).  stage_cap: 0 for the largest
  * stage (1920 atoms), else 64..1920 (smaller stages send more pairs down
  * the per-pair path; a testing aid).  Applies to later calls on h; the
  * paper has no counterpart.  Errors: FIRE_ERR_ARG (mode, stage_cap, batched
@@ -338,9 +343,14 @@ typedef enum {
     FIRE_STAGE_DENSITY = 1,     /* RGL density pass (0 for LJ) */
     FIRE_STAGE_EMBED = 2,       /* RGL embedding derivative (0 for LJ) */
     FIRE_STAGE_FORCE = 3,       /* force pass (RGL pass 2, or LJ) */
-    FIRE_STAGE_REDUCE = 4,      /* FP64 reductions of P, |F|^2, |v|^2, max|F_i| */
-    FIRE_STAGE_CONTROL = 5,     /* scalar FIRE control (Algorithm 2) */
-    FIRE_STAGE_UPDATE = 6,      /* element-wise half step back / kick / mix / drift */
+    FIRE_STAGE_REDUCE = 4,      /* FP64 reductions of P, |F|^2, |v|^2, max|F_i|, with the
+                                   scalar FIRE control (Algorithm 2) in the same launch;
+                                   without a displacement cap and outside NEB also the
+                                   element-wise update (one cooperative launch) */
+    FIRE_STAGE_CONTROL = 5,     /* the control as a launch of its own: NEB handles only
+                                   (otherwise ~0, its work is in FIRE_STAGE_REDUCE) */
+    FIRE_STAGE_UPDATE = 6,      /* element-wise half step back / kick / mix / drift, where
+                                   it is a launch of its own (otherwise ~0) */
     FIRE_NSTAGES = 7
 } fire_stage;
 

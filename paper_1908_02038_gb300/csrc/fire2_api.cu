@@ -157,8 +157,9 @@ bool fixed64_half(const fire_potential_t& p) {
 // The pair passes that can split an atom's list over several threads: the
 // FP64 table form and the FP32-pair form with exponentials.
 bool tpa_form(const fire_potential_t& p) {
-    return fixed64_form(p) || (p.kind == FIRE_POT_RGL && p.precision == FIRE_PREC_FP32_PAIR &&
-                               p.pair_eval == FIRE_PAIR_ANALYTIC);
+    return fixed64_form(p) || p.kind == FIRE_POT_LJ ||
+           (p.kind == FIRE_POT_RGL && p.precision == FIRE_PREC_FP32_PAIR &&
+            p.pair_eval == FIRE_PAIR_ANALYTIC);
 }
 
 constexpr int kMaxTpa = 8;
@@ -180,16 +181,17 @@ int auto_tpa(const fire_potential_t& p, long long n, int sms) {
     return tpa_for(n, sms, p.precision == FIRE_PREC_FP32_PAIR ? 512 : 1024);
 }
 
-// Atoms from which the FP64 half-list passes run on shared-memory tiles by
-// default (FIRE_TILES_AUTO).
-constexpr long long kTileAutoAtoms = 200000;
-
 // Whether the FP64 half-list passes of this geometry run on tiles: the FP64
-// table form on a half list, cell mode, one system.
+// table form on a half list, cell mode, one system, and tiles asked for.
+// FIRE_TILES_AUTO takes the untiled passes: on GB300 the tiled ones remove
+// the FP64 additions and L2 atomics of the neighbour terms (FP64 pipe 64 % ->
+// 2 %, L2 56 % -> 7 % in the force pass) but both passes are bound by the
+// issue of their double-float arithmetic, and the tiles' staging, barriers
+// and fixed-point splits cost more issue than they save (1M-atom box: force
+// 0.60-0.62 ms against 0.51, density 0.44 against 0.34 over four tile shapes).
 bool tiles_wanted(const fire_handle* h, const GeoC& g) {
     if (!fixed64_half(h->pot) || g.brute || h->neb || g.img_n != h->n) return false;
-    if (h->tile_mode == FIRE_TILES_OFF) return false;
-    return h->tile_mode == FIRE_TILES_ON || (long long)h->n >= kTileAutoAtoms;
+    return h->tile_mode == FIRE_TILES_ON;
 }
 
 // Neighbour geometry for a box.  The list radius is rc + skin, with the skin
@@ -243,9 +245,8 @@ GeoC make_geo(const fire_handle* h, const double box[3]) {
         g.nbk[a] = g.nc[a];
     }
     if (tiles_wanted(h, g)) {
-        const int want[3] = {4, 4, 2};
         for (int a = 0; a < 3; ++a) {
-            g.bk[a] = std::min(want[a], g.nc[a]);
+            g.bk[a] = std::min(kTileBrick[a], g.nc[a]);
             g.nbk[a] = ceil_div(g.nc[a], g.bk[a]);
         }
         g.tiled = 1;
@@ -281,12 +282,12 @@ void drop_graph(fire_handle* h) {
     h->has_graph = false;
 }
 
-// Blocks of the tile passes: two per SM (the force pass stages 105 KB per
-// block), looping over the tiles; never more than the energy partials
-// allocated for the density pass.
+// Blocks of the tile passes: kTileMinBlocks per SM (as many as the force
+// pass's stage and registers allow), looping over the tiles; never more than
+// the energy partials allocated for the density pass.
 int tile_grid(const fire_handle* h, const GeoC& g) {
     const int nb_max = ceil_div((long long)h->n * kMaxTpa, kForceBlock);
-    return std::max(1, std::min(std::min(g.ntile, 2 * h->sms), nb_max));
+    return std::max(1, std::min(std::min(g.ntile, kTileMinBlocks * h->sms), nb_max));
 }
 
 fire_status ensure_buffers(fire_handle* h, const GeoC& g, int cap) {
@@ -344,6 +345,12 @@ fire_status ensure_buffers(fire_handle* h, const GeoC& g, int cap) {
                                        (int)kDensTileSmem));
             CK(h, cudaFuncSetAttribute(k_force_tile, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)kForceTileSmem));
+            // all of the unified L1 / shared storage as shared memory: the
+            // resident blocks' stages need it
+            CK(h, cudaFuncSetAttribute(k_density_tile,
+                                       cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+            CK(h, cudaFuncSetAttribute(k_force_tile,
+                                       cudaFuncAttributePreferredSharedMemoryCarveout, 100));
             h->tile_attr = true;
         }
     }
@@ -386,6 +393,14 @@ void force_ff(const Bufs& b, const PotC& P, const GeoC& g, int nb, cudaStream_t 
     case 4: k_force_ff<HALF, 4><<<nb, kForceBlock, 0, s>>>(b, P, g); break;
     case 2: k_force_ff<HALF, 2><<<nb, kForceBlock, 0, s>>>(b, P, g); break;
     default: k_force_ff<HALF, 1><<<nb, kForceBlock, 0, s>>>(b, P, g);
+    }
+}
+void force_lj(const Bufs& b, const PotC& P, const GeoC& g, cudaStream_t s) {
+    switch (b.tpa) {
+    case 8: k_force_lj<8><<<b.nb_force, kForceBlock, 0, s>>>(b, P, g); break;
+    case 4: k_force_lj<4><<<b.nb_force, kForceBlock, 0, s>>>(b, P, g); break;
+    case 2: k_force_lj<2><<<b.nb_force, kForceBlock, 0, s>>>(b, P, g); break;
+    default: k_force_lj<1><<<b.nb_force, kForceBlock, 0, s>>>(b, P, g);
     }
 }
 void density32(const Bufs& b, const PotC& P, const GeoC& g, cudaStream_t s) {
@@ -463,7 +478,7 @@ void launch_forces(fire_handle* h, const GeoC& g, cudaStream_t s, bool confirm_p
     } else if (h->pot.kind == FIRE_POT_SW) {
         k_force_sw<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
     } else {
-        k_force_lj<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
+        force_lj(h->b, h->potc, g, s);
     }
     if (h->verify && confirm_passes) launch_confirm(h, g, s);
     (void)n;
@@ -499,7 +514,45 @@ void launch_reduce(fire_handle* h, const GeoC& g, cudaStream_t s) {
     k_reduce<<<h->b.nb_red, kElemBlock, 0, s>>>(h->b);
 }
 
+// The reductions and the control step (Algorithm 2) of one evaluation: one
+// launch (k_reduce_ctl, whose last block runs the control), or for NEB
+// handles the projection chain followed by k_control.
+void launch_reduce_control(fire_handle* h, const GeoC& g, cudaStream_t s, int mode,
+                           cudaGraphConditionalHandle hc, int has_handle) {
+    if (h->neb) {
+        launch_reduce(h, g, s);
+        k_control<<<1, kCtlThreads, 0, s>>>(h->b, mode, hc, has_handle);
+        return;
+    }
+    k_reduce_ctl<<<h->b.nb_red, kElemBlock, 0, s>>>(h->b, mode, hc, has_handle);
+}
+
 int update_grid(int n) { return std::max(1, std::min(ceil_div(n, kElemBlock), 152 * 8)); }
+
+// Whether a loop pass runs its reductions, control step and update as one
+// cooperative launch (k_step): not with a displacement cap (two update
+// passes around a maximum) nor for NEB handles (a projection chain between
+// the reductions and the control).
+bool fused_step(const fire_handle* h) { return !h->neb && !(h->par.dmax > 0.0); }
+
+// k_step on nb_red blocks as a cooperative launch (every block resident,
+// which its release wait needs).
+cudaError_t launch_step(fire_handle* h, const GeoC& g, cudaStream_t s, int mode,
+                        cudaGraphConditionalHandle hw, int has_w, cudaGraphConditionalHandle hif,
+                        int has_if, cudaGraphConditionalHandle hconf, int has_conf) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(h->b.nb_red);
+    cfg.blockDim = dim3(kElemBlock);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_step, h->b, g, mode, hw, has_w, hif, has_if, hconf,
+                              has_conf);
+}
 
 // The element-wise step; with dmax > 0 in two passes (see k_update_pre).
 void launch_update(fire_handle* h, const GeoC& g, cudaStream_t s, cudaGraphConditionalHandle hif,
@@ -547,7 +600,11 @@ fire_status build_graph(fire_handle* h, const GeoC& g) {
     cudaGraph_t graph = nullptr;
     CK(h, cudaGraphCreate(&graph, 0));
     cudaGraphConditionalHandle hw;
-    cudaError_t e = cudaGraphConditionalHandleCreate(&hw, graph, 0, cudaGraphCondAssignDefault);
+    // with the fused step the first control step runs inside the loop, which
+    // is therefore entered (the WHILE condition starts at 1)
+    const bool fused = fused_step(h);
+    cudaError_t e = cudaGraphConditionalHandleCreate(&hw, graph, fused ? 1u : 0u,
+                                                     cudaGraphCondAssignDefault);
     if (e != cudaSuccess) {
         cudaGraphDestroy(graph);
         return fail(h, FIRE_ERR_CUDA, "cudaGraphConditionalHandleCreate: %s", cudaGetErrorString(e));
@@ -562,8 +619,7 @@ fire_status build_graph(fire_handle* h, const GeoC& g) {
     k_prepare<<<ceil_div(n, kElemBlock), kElemBlock, 0, h->cap0>>>(h->b);
     launch_build(h, g, 1, h->cap0);
     launch_forces(h, g, h->cap0);
-    launch_reduce(h, g, h->cap0);
-    k_control<<<1, kCtlThreads, 0, h->cap0>>>(h->b, CTL_INITIAL, hw, 1);
+    if (!fused) launch_reduce_control(h, g, h->cap0, CTL_INITIAL, hw, 1);
 
     cudaGraph_t body = nullptr;
     e = add_conditional(h->cap0, hw, cudaGraphCondTypeWhile, &body);
@@ -576,9 +632,12 @@ fire_status build_graph(fire_handle* h, const GeoC& g) {
             e = cudaStreamBeginCaptureToGraph(h->cap1, body, nullptr, nullptr, 0,
                                               cudaStreamCaptureModeRelaxed);
         if (e == cudaSuccess) {
-            launch_update(h, g, h->cap1, hif, 1, hconf, h->verify ? 1 : 0);
+            if (fused)   // reductions, control (sets WHILE), update (sets the IFs)
+                e = launch_step(h, g, h->cap1, CTL_LOOP, hw, 1, hif, 1, hconf, h->verify ? 1 : 0);
+            else
+                launch_update(h, g, h->cap1, hif, 1, hconf, h->verify ? 1 : 0);
             cudaGraph_t build_body = nullptr;
-            e = add_conditional(h->cap1, hif, cudaGraphCondTypeIf, &build_body);
+            if (e == cudaSuccess) e = add_conditional(h->cap1, hif, cudaGraphCondTypeIf, &build_body);
             if (e == cudaSuccess)
                 e = cudaStreamBeginCaptureToGraph(h->cap2, build_body, nullptr, nullptr, 0,
                                                   cudaStreamCaptureModeRelaxed);
@@ -600,8 +659,7 @@ fire_status build_graph(fire_handle* h, const GeoC& g) {
                     e = cudaStreamEndCapture(h->cap2, &cb_out);
                 }
             }
-            launch_reduce(h, g, h->cap1);
-            k_control<<<1, kCtlThreads, 0, h->cap1>>>(h->b, CTL_LOOP, hw, 1);
+            if (!fused) launch_reduce_control(h, g, h->cap1, CTL_LOOP, hw, 1);
             cudaGraph_t body_out = nullptr;
             const cudaError_t e1 = cudaStreamEndCapture(h->cap1, &body_out);
             if (e == cudaSuccess) e = e1;
@@ -653,23 +711,31 @@ fire_status capture_plain(fire_handle* h, cudaGraphExec_t* out, Fn fn) {
 fire_status build_chunked(fire_handle* h, const GeoC& g) {
     drop_graph(h);
     const int n = h->n;
+    const bool fused = fused_step(h);
+    const cudaGraphConditionalHandle none{};
+    cudaError_t le = cudaSuccess;
     fire_status st = capture_plain(h, &h->exec_init, [&](cudaStream_t s) {
         k_prepare<<<ceil_div(n, kElemBlock), kElemBlock, 0, s>>>(h->b);
         launch_build(h, g, 1, s);
         launch_forces(h, g, s);
-        launch_reduce(h, g, s);
-        k_control<<<1, kCtlThreads, 0, s>>>(h->b, CTL_INITIAL, cudaGraphConditionalHandle{}, 0);
+        if (!fused) launch_reduce_control(h, g, s, CTL_INITIAL, none, 0);
     });
     if (st == FIRE_OK)
         st = capture_plain(h, &h->exec_chunk, [&](cudaStream_t s) {
             for (int c = 0; c < h->chunk; ++c) {
-                launch_update(h, g, s, cudaGraphConditionalHandle{}, 0);
+                if (fused) {   // reductions, control and update of one pass, then forces
+                    const cudaError_t e1 = launch_step(h, g, s, CTL_LOOP, none, 0, none, 0, none, 0);
+                    if (le == cudaSuccess) le = e1;
+                } else {
+                    launch_update(h, g, s, none, 0);
+                }
                 launch_build(h, g, 0, s);
                 launch_forces(h, g, s);
-                launch_reduce(h, g, s);
-                k_control<<<1, kCtlThreads, 0, s>>>(h->b, CTL_LOOP, cudaGraphConditionalHandle{}, 0);
+                if (!fused) launch_reduce_control(h, g, s, CTL_LOOP, none, 0);
             }
         });
+    if (st == FIRE_OK && le != cudaSuccess)
+        st = fail(h, FIRE_ERR_CUDA, "cooperative step launch: %s", cudaGetErrorString(le));
     if (st == FIRE_OK)
         st = capture_plain(h, &h->exec_final, [&](cudaStream_t s) {
             k_finalize<<<ceil_div(n, kElemBlock), kElemBlock, 0, s>>>(h->b);
@@ -1379,8 +1445,7 @@ static fire_status run_eval_unmasked(fire_handle* h, const GeoC& g, cudaStream_t
     k_prepare<<<ceil_div(h->n, kElemBlock), kElemBlock, 0, s>>>(h->b);
     launch_build(h, g, 1, s);
     launch_forces(h, g, s);
-    launch_reduce(h, g, s);
-    k_control<<<1, kCtlThreads, 0, s>>>(h->b, CTL_EVAL, cudaGraphConditionalHandle{}, 0);
+    launch_reduce_control(h, g, s, CTL_EVAL, cudaGraphConditionalHandle{}, 0);
     k_export_forces<<<ceil_div(h->n, kElemBlock), kElemBlock, 0, s>>>(h->b);
     CK(h, cudaGetLastError());
     CK(h, cudaMemcpyAsync(h->h_state, h->b.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
@@ -1899,14 +1964,30 @@ fire_status fire_profile_stages(fire_handle_t* h, const double* pos, const doubl
         else if (rgl && f32) force32(h->b, h->potc, g, s);
         else if (rgl) k_force_rgl<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, g);
         else if (h->pot.kind == FIRE_POT_SW) k_force_sw<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
-        else k_force_lj<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
+        else force_lj(h->b, h->potc, g, s);
         cudaEventRecord(ev[4], s);
-        launch_reduce(h, g, s);
-        cudaEventRecord(ev[5], s);
-        k_control<<<1, kCtlThreads, 0, s>>>(h->b, CTL_EVAL, cudaGraphConditionalHandle{}, 0);
-        cudaEventRecord(ev[6], s);
-        launch_update(h, g, s, cudaGraphConditionalHandle{}, 0);
-        cudaEventRecord(ev[7], s);
+        const cudaGraphConditionalHandle none{};
+        if (fused_step(h)) {
+            // reductions, control step and update in one cooperative launch
+            // (k_step; the control in CTL_EVAL mode leaves dt = 0, so the
+            // update does not move the atoms): all of it under FIRE_STAGE_REDUCE
+            const cudaError_t le = launch_step(h, g, s, CTL_EVAL, none, 0, none, 0, none, 0);
+            if (le != cudaSuccess) {
+                for (auto& x : ev) cudaEventDestroy(x);
+                return fail(h, FIRE_ERR_CUDA, "cooperative step launch: %s", cudaGetErrorString(le));
+            }
+            cudaEventRecord(ev[5], s);
+            cudaEventRecord(ev[6], s);
+            cudaEventRecord(ev[7], s);
+        } else {
+            // the control step runs in the last block of the reductions'
+            // launch (k_reduce_ctl); NEB handles run it as a kernel of its own
+            launch_reduce_control(h, g, s, CTL_EVAL, none, 0);
+            cudaEventRecord(ev[5], s);
+            cudaEventRecord(ev[6], s);
+            launch_update(h, g, s, none, 0);
+            cudaEventRecord(ev[7], s);
+        }
         cudaError_t e = cudaEventSynchronize(ev[7]);
         if (e != cudaSuccess) {
             for (auto& x : ev) cudaEventDestroy(x);

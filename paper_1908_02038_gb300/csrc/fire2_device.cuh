@@ -82,6 +82,8 @@ struct DevState {
     int vstate, vcount, vmode;
     double ftol_user, fn32, fsw;
     int tile_over;         // tile builds whose stage overflowed (pairs then use global atomics)
+    unsigned int red_blocks;   // k_reduce_ctl / k_step blocks arrived (last-block test)
+    unsigned int step_gen;     // k_step: bumped by the block that ran the control step
 };
 
 struct Bufs {
@@ -623,19 +625,23 @@ __global__ void __launch_bounds__(kForceBlock) k_force_sw(Bufs b, PotC P, GeoC g
 
 // Lennard-Jones, one pass: w = 24 eps [2 (s/r)^12 - (s/r)^6] / r^2,
 // F_i -= w d, F_j += w d; pair energy 4 eps [(s/r)^12 - (s/r)^6] - phi(rc).
+template <int TPA = 1>
 __global__ void __launch_bounds__(kForceBlock) k_force_lj(Bufs b, PotC P, GeoC g) {
     __shared__ double3 tbl[125];
     __shared__ double red[32];
     if (b.st->done) return;
     fill_shift_table(tbl, g);
     __syncthreads();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    // TPA threads share an atom (small systems): lane l takes list slots
+    // l, l + TPA, ...; their sums meet in FP64 before lane 0 adds F_i
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = t / TPA, lane = t % TPA;
     double epair = 0.0;
     if (i < b.n) {
         const dvec4 xi = b.x[i];
         const int m = b.nnbr[i];
         double fx = 0.0, fy = 0.0, fz = 0.0;
-        for (int k = 0; k < m; ++k) {
+        for (int k = lane; k < m; k += TPA) {
             const uint32_t e = b.nbr[(size_t)k * b.n + i];
             const int j = (int)(e & kIdxMask);
             const int code = (int)(e >> kIdxBits);
@@ -649,10 +655,14 @@ __global__ void __launch_bounds__(kForceBlock) k_force_lj(Bufs b, PotC P, GeoC g
             }
             const double r2 = dx * dx + dy * dy + dz * dz;
             if (!(r2 < P.rc2)) continue;
-            const double sr2 = P.sigma2 / r2;
+            // one correctly rounded reciprocal in place of two FP64 divisions
+            // (each a long FP64 sequence on a part where FP64 issues at 1/64
+            // of the FP32 rate)
+            const double ir2 = __drcp_rn(r2);
+            const double sr2 = P.sigma2 * ir2;
             const double sr6 = sr2 * sr2 * sr2;
             epair += 4.0 * P.eps * (sr6 * sr6 - sr6) - P.lj_shift;
-            const double w = 24.0 * P.eps * (2.0 * sr6 * sr6 - sr6) / r2;
+            const double w = 24.0 * P.eps * (2.0 * sr6 * sr6 - sr6) * ir2;
             fx -= w * dx;
             fy -= w * dy;
             fz -= w * dz;
@@ -660,10 +670,16 @@ __global__ void __launch_bounds__(kForceBlock) k_force_lj(Bufs b, PotC P, GeoC g
             atomicAdd(&b.f[j].y, w * dy);
             atomicAdd(&b.f[j].z, w * dz);
         }
-        atomicAdd(&b.f[i].x, fx);
-        atomicAdd(&b.f[i].y, fy);
-        atomicAdd(&b.f[i].z, fz);
-        if (b.eatom) b.eatom[i] = epair;
+        fx = group_sum<TPA>(fx);
+        fy = group_sum<TPA>(fy);
+        fz = group_sum<TPA>(fz);
+        const double ep = group_sum<TPA>(epair);
+        if (lane == 0) {
+            atomicAdd(&b.f[i].x, fx);
+            atomicAdd(&b.f[i].y, fy);
+            atomicAdd(&b.f[i].z, fz);
+            if (b.eatom) b.eatom[i] = ep;
+        }
     }
     const double s = block_sum(epair, red);
     if (threadIdx.x == 0) b.epart[blockIdx.x] = s;
@@ -1205,13 +1221,10 @@ __device__ __forceinline__ CtlSums ctl_reduce(const Bufs& b, int ne, double* sh 
 // Scalar FIRE 2.0 control (Algorithm 2, fire_control_step), one block: the
 // fixed-order final reductions, the error checks, then the convergence test
 // and the preparation of the next iteration; sets the WHILE condition.
-__global__ void k_control(Bufs b, int mode, cudaGraphConditionalHandle h, int has_handle) {
-    __shared__ double sh[6 * 32];
-    // chunked execution runs loop bodies past the stop; they must not count
-    if (mode == CTL_LOOP && b.st->done) {
-        if (has_handle && threadIdx.x == 0) cudaGraphSetConditional(h, 0u);
-        return;
-    }
+// The control step proper: every thread of one block enters (the final
+// reductions), thread 0 runs the scalar part.
+__device__ void control_body(const Bufs& b, int mode, cudaGraphConditionalHandle h,
+                             int has_handle, double* sh) {
     const int ne = b.st->vstate >= 2 ? b.nb_verify : b.ne_dens + b.nb_embed;
     const CtlSums r = ctl_reduce(b, ne, sh);
     if (threadIdx.x != 0) return;
@@ -1276,30 +1289,69 @@ __global__ void k_control(Bufs b, int mode, cudaGraphConditionalHandle h, int ha
     if (has_handle) cudaGraphSetConditional(h, stop ? 0u : 1u);
 }
 
+__global__ void k_control(Bufs b, int mode, cudaGraphConditionalHandle h, int has_handle) {
+    __shared__ double sh[6 * 32];
+    // chunked execution runs loop bodies past the stop; they must not count
+    if (mode == CTL_LOOP && b.st->done) {
+        if (has_handle && threadIdx.x == 0) cudaGraphSetConditional(h, 0u);
+        return;
+    }
+    control_body(b, mode, h, has_handle, sh);
+}
+
+// The reductions of k_reduce and the control step of k_control in one
+// launch (nb_red blocks): every block writes its partials, and the last
+// block to finish (a ticket counter, reset by that block) runs the control
+// step on all of them.  No block waits for another.
+__global__ void k_reduce_ctl(Bufs b, int mode, cudaGraphConditionalHandle h, int has_handle) {
+    __shared__ double red[32];
+    __shared__ double sh[6 * 32];
+    __shared__ int last;
+    if (b.st->done) {   // chunked loop bodies past the stop
+        if (mode == CTL_LOOP && has_handle && blockIdx.x == 0 && threadIdx.x == 0)
+            cudaGraphSetConditional(h, 0u);
+        return;
+    }
+    const double vvh = vv_half_of(b.st);
+    RedAcc acc;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < b.n; i += gridDim.x * blockDim.x) {
+        dvec4 f = b.f[i];
+        if (mask_force(b, i, f)) b.f[i] = f;
+        red_atom(b, i, f, b.v[i], vvh, acc);
+    }
+    red_write(acc, red, b.rpart);
+    if (threadIdx.x == 0) {
+        __threadfence();   // this block's partials before its ticket
+        last = atomicAdd(&b.st->red_blocks, 1u) == gridDim.x - 1 ? 1 : 0;
+    }
+    __syncthreads();
+    if (!last) return;
+    if (threadIdx.x == 0) b.st->red_blocks = 0u;
+    __threadfence();       // every other block's partials are visible from here
+    control_body(b, mode, h, has_handle, sh);
+}
+
 // Element-wise part of one iteration: optional half step back and v = 0
 // (P <= 0, Alg. 2), then Algorithm 4: v += dt F / m, mixing
 // v = (1 - alpha) v + alpha |v| F / |F| (P > 0), x += dt v.  Clears F and rho
 // for the next force evaluation (accumulating paths) and tracks
 // max |x - x_ref|^2.  With has_if, the last block to finish sets the graph's
 // IF condition to "the neighbour list must be rebuilt" (see need_rebuild).
-__global__ void k_update(Bufs b, GeoC g, cudaGraphConditionalHandle hif, int has_if,
-                         int after_pre, cudaGraphConditionalHandle hconf, int has_conf) {
-    __shared__ double red[32];
+// The element-wise step of k_update and k_step, given the state the control
+// step left (s, done, vstate) and the drift dt.
+__device__ void update_body(const Bufs& b, const GeoC& g, const FireScal& s, int done, int vstate,
+                            double dt, int after_pre, cudaGraphConditionalHandle hif, int has_if,
+                            cudaGraphConditionalHandle hconf, int has_conf, double* red) {
     // graph loop: the IF node of the FP64 confirming passes runs this pass
     // only when an FP32-pair stop is being confirmed
     if (has_conf && blockIdx.x == 0 && threadIdx.x == 0)
-        cudaGraphSetConditional(hconf, b.st->vstate >= 2 ? 1u : 0u);
+        cudaGraphSetConditional(hconf, vstate >= 2 ? 1u : 0u);
     // no step when stopped, nor while an FP32-pair stop is confirmed in FP64
     // (the next evaluation is at the same positions)
-    if (b.st->done || b.st->vstate == 2) {
+    if (done || vstate == 2) {
         if (has_if && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(hif, 0u);
         return;
     }
-    const FireScal s = b.st->fs;
-    // after k_update_pre: only the drift is left, with the capped dt
-    const double dt = after_pre ? fire_capped_dt(s.dt_cur, b.st->prm.dmax,
-                                                 __longlong_as_double((long long)b.st->vmax2))
-                                : s.dt_cur;
     // displacement since the last build in FP32 (truncated copies): off by
     // < 1e-4 A at most, far inside the list build's FP32 margin
     float d2max = 0.f;
@@ -1341,6 +1393,105 @@ __global__ void k_update(Bufs b, GeoC g, cudaGraphConditionalHandle hif, int has
             }
         }
     }
+}
+
+__global__ void k_update(Bufs b, GeoC g, cudaGraphConditionalHandle hif, int has_if,
+                         int after_pre, cudaGraphConditionalHandle hconf, int has_conf) {
+    __shared__ double red[32];
+    const FireScal s = b.st->fs;
+    // after k_update_pre: only the drift is left, with the capped dt
+    const double dt = after_pre ? fire_capped_dt(s.dt_cur, b.st->prm.dmax,
+                                                 __longlong_as_double((long long)b.st->vmax2))
+                                : s.dt_cur;
+    update_body(b, g, s, b.st->done, b.st->vstate, dt, after_pre, hif, has_if, hconf, has_conf,
+                red);
+}
+
+// A struct written by another block of the same launch, read past L1.
+template <typename T>
+__device__ __forceinline__ T load_cg(const T* p) {
+    static_assert(sizeof(T) % 8 == 0, "8-byte words");
+    T out;
+    const unsigned long long* src = reinterpret_cast<const unsigned long long*>(p);
+    unsigned long long* dst = reinterpret_cast<unsigned long long*>(&out);
+#pragma unroll
+    for (int k = 0; k < (int)(sizeof(T) / 8); ++k) dst[k] = __ldcg(src + k);
+    return out;
+}
+
+constexpr unsigned long long kStepWaitNs = 2000000000ull;   // release wait limit of k_step
+
+// One loop pass's reductions, control step (Algorithm 2) and element-wise
+// step (Algorithm 4) in one cooperative launch of nb_red blocks, all
+// resident: every block writes its partials and takes a ticket; the last
+// block runs the control step and bumps step_gen; the others wait for that
+// (at most kStepWaitNs, then the call ends with ST_TIMEOUT) and all apply
+// the update.  Replaces k_reduce_ctl + k_update where no displacement cap
+// and no NEB projection sit between them.
+__global__ void k_step(Bufs b, GeoC g, int mode, cudaGraphConditionalHandle hw, int has_w,
+                       cudaGraphConditionalHandle hif, int has_if,
+                       cudaGraphConditionalHandle hconf, int has_conf) {
+    __shared__ double red[32];
+    __shared__ double sh[6 * 32];
+    __shared__ int last, ok;
+    if (b.st->done) {   // chunked loop bodies past the stop
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            if (has_w) cudaGraphSetConditional(hw, 0u);
+            if (has_if) cudaGraphSetConditional(hif, 0u);
+            if (has_conf) cudaGraphSetConditional(hconf, 0u);
+        }
+        return;
+    }
+    const double vvh = vv_half_of(b.st);
+    RedAcc acc;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < b.n; i += gridDim.x * blockDim.x) {
+        dvec4 f = b.f[i];
+        if (mask_force(b, i, f)) b.f[i] = f;
+        red_atom(b, i, f, b.v[i], vvh, acc);
+    }
+    red_write(acc, red, b.rpart);
+    unsigned g0 = 0u;
+    if (threadIdx.x == 0) {
+        g0 = *(volatile unsigned int*)&b.st->step_gen;   // before the ticket
+        __threadfence();
+        last = atomicAdd(&b.st->red_blocks, 1u) == gridDim.x - 1 ? 1 : 0;
+        ok = 1;
+    }
+    __syncthreads();
+    if (last) {
+        if (threadIdx.x == 0) b.st->red_blocks = 0u;
+        __threadfence();
+        control_body(b, mode, hw, has_w, sh);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicAdd(&b.st->step_gen, 1u);   // release
+        }
+    } else if (threadIdx.x == 0) {
+        const volatile unsigned int* gen = &b.st->step_gen;
+        const unsigned long long t0 = globaltimer_ns();
+        while (*gen == g0) {
+            if (globaltimer_ns() - t0 > kStepWaitNs) {
+                ok = 0;
+                break;
+            }
+            __nanosleep(64);
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    if (!ok) {   // never with every block resident; ends the call instead of waiting on
+        if (threadIdx.x == 0) {
+            set_status(b.st, ST_TIMEOUT);
+            atomicExch(&b.st->done, 1);
+            if (has_w) cudaGraphSetConditional(hw, 0u);
+            if (has_if) cudaGraphSetConditional(hif, 0u);
+        }
+        return;
+    }
+    const FireScal s = load_cg(&b.st->fs);
+    const int done = __ldcg(&b.st->done), vstate = __ldcg(&b.st->vstate);
+    update_body(b, g, s, done, vstate, s.dt_cur, 0, hif, has_if, hconf, has_conf, red);
 }
 
 // With a maximum displacement per step (dmax > 0) the element-wise step runs

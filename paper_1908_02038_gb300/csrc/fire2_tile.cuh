@@ -27,10 +27,30 @@
 
 namespace fire2 {
 
-constexpr int kTileThreads = 512;
-constexpr int kStageMax = 1920;          // staged atoms per tile (force pass: 56 B each)
+// Launch shape of the tile passes and the brick of cells a tile covers
+// (compile-time; the defaults are the measured choice on GB300).
+#ifndef FIRE_TILE_THREADS
+#define FIRE_TILE_THREADS 512
+#endif
+#ifndef FIRE_TILE_STAGE
+#define FIRE_TILE_STAGE 1920
+#endif
+#ifndef FIRE_TILE_MINB
+#define FIRE_TILE_MINB 2
+#endif
+#ifndef FIRE_TILE_BRICK_X
+#define FIRE_TILE_BRICK_X 4
+#define FIRE_TILE_BRICK_Y 4
+#define FIRE_TILE_BRICK_Z 2
+#endif
+constexpr int kTileThreads = FIRE_TILE_THREADS;
+constexpr int kTileMinBlocks = FIRE_TILE_MINB;   // resident blocks per SM (registers)
+constexpr int kStageMax = FIRE_TILE_STAGE;       // staged atoms per tile (force pass: 56 B each)
+constexpr int kTileBrick[3] = {FIRE_TILE_BRICK_X, FIRE_TILE_BRICK_Y, FIRE_TILE_BRICK_Z};
 constexpr int kTileHash = 4096;          // hash table of the stage build (power of 2)
 constexpr int kTileHashBits = 12;
+static_assert(kTileHash >= 2 * kStageMax, "hash table at most half full");
+static_assert(kTileThreads % 32 == 0 && kTileThreads <= 1024, "tile block size");
 constexpr uint16_t kSlotNone = 0xffffu;  // not staged: global path
 constexpr uint16_t kSlotOwnOver = 0xfffeu;   // own atom beyond the stage (build only)
 constexpr uint32_t kKeyEmpty = 0xffffffffu;  // never a list entry (image codes <= 124)
@@ -190,18 +210,19 @@ __global__ void __launch_bounds__(kTileThreads) k_tile_build(Bufs b, GeoC g, int
                 if (tile_insert(keys, b.nbr[(size_t)k * b.n + i]) < 0) fail = 1;
         }
         __syncthreads();
-        constexpr int kPer = kTileHash / kTileThreads;
+        constexpr int kPer = (kTileHash + kTileThreads - 1) / kTileThreads;
         const int h0 = threadIdx.x * kPer;
         int cnt = 0;
 #pragma unroll
         for (int q = 0; q < kPer; ++q)
-            cnt += (keys[h0 + q] != kKeyEmpty && slot_of[h0 + q] == kSlotNone) ? 1 : 0;
+            cnt += (h0 + q < kTileHash && keys[h0 + q] != kKeyEmpty &&
+                    slot_of[h0 + q] == kSlotNone) ? 1 : 0;
         int nhalo = 0;
         int s = min(nown, cap) + block_exscan(cnt, ws, &nhalo);
 #pragma unroll
         for (int q = 0; q < kPer; ++q) {
             const int h = h0 + q;
-            if (keys[h] != kKeyEmpty && slot_of[h] == kSlotNone) {
+            if (h < kTileHash && keys[h] != kKeyEmpty && slot_of[h] == kSlotNone) {
                 if (s < cap) {
                     slot_of[h] = (uint16_t)s;
                     tkey[s] = keys[h];
@@ -265,7 +286,7 @@ __device__ __forceinline__ ffloat tile_sep(long long ix, long long iy, long long
 // Pass 1 on tiles: rho_i (own atoms' sums plus the j-side terms of the
 // tile, flushed per staged atom) and 2 phi per pair credited to i; k_embed
 // then forms F'(rho) and the embedding energy.
-__global__ void __launch_bounds__(kTileThreads, 2) k_density_tile(Bufs b, PotC P, GeoC g) {
+__global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) k_density_tile(Bufs b, PotC P, GeoC g) {
     extern __shared__ __align__(16) unsigned char smem[];
     long long* sx = reinterpret_cast<long long*>(smem);
     long long* sy = sx + kStageMax;
@@ -373,7 +394,7 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_density_tile(Bufs b, PotC P
 // Pass 2 on tiles: F_i = sum_j [2 phi'/r + (F'_i + F'_j) g'/r] (x_j - x_i),
 // the j-side terms accumulated per staged atom and flushed (F = -grad E,
 // Sec. 2.1).  k_reduce applies the frozen-DOF mask afterwards.
-__global__ void __launch_bounds__(kTileThreads, 2) k_force_tile(Bufs b, PotC P, GeoC g) {
+__global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) k_force_tile(Bufs b, PotC P, GeoC g) {
     extern __shared__ __align__(16) unsigned char smem[];
     long long* sx = reinterpret_cast<long long*>(smem);
     long long* sy = sx + kStageMax;

@@ -130,3 +130,16 @@ def test_tile_setting_rejects_bad_arguments():
             with pytest.raises(fg.FireError) as e:
                 h.set_pair_tiles(mode, cap)
             assert e.value.status == fg.FIRE_ERR_ARG
+
+
+def test_tiled_forces_1m_sampled_match_oracle():
+    """The 997,450-atom void box (2,541 tiles) on tiles: 2,048 sampled atoms
+    against the oracle's forces, the energy against the oracle's total."""
+    c = fi.rgl_void_box()
+    rng = np.random.default_rng(9)
+    which = np.sort(rng.choice(c.n, size=2048, replace=False))
+    eo, fo = oracle.energy_forces_subset(c.x, c.box, ora_rgl(), which, mode=oracle.FORCE_CELLS)
+    e, f = tiled_eval(c)
+    assert rel(f[which], fo) < F_REL
+    assert e == pytest.approx(eo, rel=E_REL)
+    assert np.abs(f.sum(0)).max() < 1e-9 * np.abs(f).max() * np.sqrt(c.n)

@@ -112,9 +112,9 @@ def test_threads_per_atom_choice_and_errors():
                 h.set_threads_per_atom(bad)
         assert h.set_threads_per_atom(2) == 2
     # forms that do not split the list report one thread per atom
-    lj = fg.Potential(fg.FIRE_POT_LJ, eps=1.0, sigma=1.0, rc_lj=2.5, skin=0.3)
-    cl = fi.lj_fcc_vacancy(seed=1)
-    with fg.FireHandle(cl.n, fi.LJ_MASS, lj, dt_start=fi.LJ_DT) as h:
+    sw = fg.Potential(fg.FIRE_POT_SW, skin=0.3, **fi.SW_SI)
+    cs = fi.sw_si_vacancy_box(ncell=4, seed=7, n_vac=1, sigma=0.05)
+    with fg.FireHandle(cs.n, fi.SI_MASS, sw, dt_start=fi.SI_DT) as h:
         assert h.set_threads_per_atom(4) == 1
     cfgs = [fi.rgl_vacancy_box(ncell=3, seed=35 + k, n_vac=1) for k in range(2)]
     with fg.FireBatch([q.n for q in cfgs], fi.CU_MASS, rgl_pot("fp32pair"),
@@ -167,3 +167,19 @@ def test_frozen_components_with_split_lists(form):
     else:
         assert abs(r.energy - ro.energy) / c.n < 1e-8
         assert abs(r.iterations - ro.iterations) <= max(2, 0.05 * ro.iterations)
+
+
+def test_lj_every_threads_per_atom_matches_oracle():
+    """The LJ force pass splits an atom's list the same way (small boxes
+    spread their FP64 pair work over more SMs)."""
+    c = fi.lj_fcc_vacancy(seed=2)
+    opot = oracle.Potential("lj", eps=1.0, sigma=1.0, rc_lj=2.5)
+    eo, fo = oracle.energy_forces(c.x, c.box, opot)
+    pot = fg.Potential(fg.FIRE_POT_LJ, eps=1.0, sigma=1.0, rc_lj=2.5, skin=0.3)
+    with fg.FireHandle(c.n, fi.LJ_MASS, pot, dt_start=fi.LJ_DT) as h:
+        assert h.set_threads_per_atom(0) == 8   # 255 atoms: the automatic choice
+        for t in TPAS:
+            assert h.set_threads_per_atom(t) == t
+            e, f = h.energy_forces(c.x, c.box)
+            assert np.abs(f - fo).max() / np.abs(fo).max() < F_REL, t
+            assert e == pytest.approx(eo, rel=1e-12), t
