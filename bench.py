@@ -369,11 +369,9 @@ class _NoClock:
 
 
 def launches_of(results, is_rgl, fp32, cell_mode, chunked=False, tiled=False):
-    """Kernels one relaxation launches: prepare, list build, forces and
-    finalize once; then per loop pass one cooperative launch of the
-    reductions, the control step and the update (k_step), and the forces
-    (one more pass than iterations: the pass whose control step stops the
-    loop also launches its forces, which return at once);
+    """Kernels one relaxation launches: prepare, list build, forces, the
+    reductions with the control step (one launch), finalize once; per loop
+    pass update, forces, reductions + control;
     the build chain (binning + list) once per rebuild.  The FP32-pair form
     also has the two FP64 confirming passes: launched once in the set-up,
     then in the graph loop only in the passes that confirm a stop (an IF
@@ -386,8 +384,8 @@ def launches_of(results, is_rgl, fp32, cell_mode, chunked=False, tiled=False):
     for rr in results:
         conf = max(0, rr["force_evals"] - rr["iterations"] - 1) if fp32 else 0
         passes = rr["iterations"] + conf
-        total += (1 + build_k + force_k + 1) + (2 if fp32 else 0)
-        total += (1 + force_k) * (passes + 1)
+        total += (1 + build_k + force_k + 1 + 1) + (2 if fp32 else 0)
+        total += (1 + force_k + 1) * passes
         if fp32:
             total += 2 * (passes if chunked else conf)
         total += build_k * max(0, rr["nbr_builds"] - 1)

@@ -529,31 +529,6 @@ void launch_reduce_control(fire_handle* h, const GeoC& g, cudaStream_t s, int mo
 
 int update_grid(int n) { return std::max(1, std::min(ceil_div(n, kElemBlock), 152 * 8)); }
 
-// Whether a loop pass runs its reductions, control step and update as one
-// cooperative launch (k_step): not with a displacement cap (two update
-// passes around a maximum) nor for NEB handles (a projection chain between
-// the reductions and the control).
-bool fused_step(const fire_handle* h) { return !h->neb && !(h->par.dmax > 0.0); }
-
-// k_step on nb_red blocks as a cooperative launch (every block resident,
-// which its release wait needs).
-cudaError_t launch_step(fire_handle* h, const GeoC& g, cudaStream_t s, int mode,
-                        cudaGraphConditionalHandle hw, int has_w, cudaGraphConditionalHandle hif,
-                        int has_if, cudaGraphConditionalHandle hconf, int has_conf) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(h->b.nb_red);
-    cfg.blockDim = dim3(kElemBlock);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_step, h->b, g, mode, hw, has_w, hif, has_if, hconf,
-                              has_conf);
-}
-
 // The element-wise step; with dmax > 0 in two passes (see k_update_pre).
 void launch_update(fire_handle* h, const GeoC& g, cudaStream_t s, cudaGraphConditionalHandle hif,
                    int has_if, cudaGraphConditionalHandle hconf = {}, int has_conf = 0) {
@@ -600,11 +575,7 @@ fire_status build_graph(fire_handle* h, const GeoC& g) {
     cudaGraph_t graph = nullptr;
     CK(h, cudaGraphCreate(&graph, 0));
     cudaGraphConditionalHandle hw;
-    // with the fused step the first control step runs inside the loop, which
-    // is therefore entered (the WHILE condition starts at 1)
-    const bool fused = fused_step(h);
-    cudaError_t e = cudaGraphConditionalHandleCreate(&hw, graph, fused ? 1u : 0u,
-                                                     cudaGraphCondAssignDefault);
+    cudaError_t e = cudaGraphConditionalHandleCreate(&hw, graph, 0, cudaGraphCondAssignDefault);
     if (e != cudaSuccess) {
         cudaGraphDestroy(graph);
         return fail(h, FIRE_ERR_CUDA, "cudaGraphConditionalHandleCreate: %s", cudaGetErrorString(e));
@@ -619,7 +590,7 @@ fire_status build_graph(fire_handle* h, const GeoC& g) {
     k_prepare<<<ceil_div(n, kElemBlock), kElemBlock, 0, h->cap0>>>(h->b);
     launch_build(h, g, 1, h->cap0);
     launch_forces(h, g, h->cap0);
-    if (!fused) launch_reduce_control(h, g, h->cap0, CTL_INITIAL, hw, 1);
+    launch_reduce_control(h, g, h->cap0, CTL_INITIAL, hw, 1);
 
     cudaGraph_t body = nullptr;
     e = add_conditional(h->cap0, hw, cudaGraphCondTypeWhile, &body);
@@ -632,12 +603,9 @@ fire_status build_graph(fire_handle* h, const GeoC& g) {
             e = cudaStreamBeginCaptureToGraph(h->cap1, body, nullptr, nullptr, 0,
                                               cudaStreamCaptureModeRelaxed);
         if (e == cudaSuccess) {
-            if (fused)   // reductions, control (sets WHILE), update (sets the IFs)
-                e = launch_step(h, g, h->cap1, CTL_LOOP, hw, 1, hif, 1, hconf, h->verify ? 1 : 0);
-            else
-                launch_update(h, g, h->cap1, hif, 1, hconf, h->verify ? 1 : 0);
+            launch_update(h, g, h->cap1, hif, 1, hconf, h->verify ? 1 : 0);
             cudaGraph_t build_body = nullptr;
-            if (e == cudaSuccess) e = add_conditional(h->cap1, hif, cudaGraphCondTypeIf, &build_body);
+            e = add_conditional(h->cap1, hif, cudaGraphCondTypeIf, &build_body);
             if (e == cudaSuccess)
                 e = cudaStreamBeginCaptureToGraph(h->cap2, build_body, nullptr, nullptr, 0,
                                                   cudaStreamCaptureModeRelaxed);
@@ -659,7 +627,7 @@ fire_status build_graph(fire_handle* h, const GeoC& g) {
                     e = cudaStreamEndCapture(h->cap2, &cb_out);
                 }
             }
-            if (!fused) launch_reduce_control(h, g, h->cap1, CTL_LOOP, hw, 1);
+            launch_reduce_control(h, g, h->cap1, CTL_LOOP, hw, 1);
             cudaGraph_t body_out = nullptr;
             const cudaError_t e1 = cudaStreamEndCapture(h->cap1, &body_out);
             if (e == cudaSuccess) e = e1;
@@ -711,31 +679,22 @@ fire_status capture_plain(fire_handle* h, cudaGraphExec_t* out, Fn fn) {
 fire_status build_chunked(fire_handle* h, const GeoC& g) {
     drop_graph(h);
     const int n = h->n;
-    const bool fused = fused_step(h);
     const cudaGraphConditionalHandle none{};
-    cudaError_t le = cudaSuccess;
     fire_status st = capture_plain(h, &h->exec_init, [&](cudaStream_t s) {
         k_prepare<<<ceil_div(n, kElemBlock), kElemBlock, 0, s>>>(h->b);
         launch_build(h, g, 1, s);
         launch_forces(h, g, s);
-        if (!fused) launch_reduce_control(h, g, s, CTL_INITIAL, none, 0);
+        launch_reduce_control(h, g, s, CTL_INITIAL, none, 0);
     });
     if (st == FIRE_OK)
         st = capture_plain(h, &h->exec_chunk, [&](cudaStream_t s) {
             for (int c = 0; c < h->chunk; ++c) {
-                if (fused) {   // reductions, control and update of one pass, then forces
-                    const cudaError_t e1 = launch_step(h, g, s, CTL_LOOP, none, 0, none, 0, none, 0);
-                    if (le == cudaSuccess) le = e1;
-                } else {
-                    launch_update(h, g, s, none, 0);
-                }
+                launch_update(h, g, s, none, 0);
                 launch_build(h, g, 0, s);
                 launch_forces(h, g, s);
-                if (!fused) launch_reduce_control(h, g, s, CTL_LOOP, none, 0);
+                launch_reduce_control(h, g, s, CTL_LOOP, none, 0);
             }
         });
-    if (st == FIRE_OK && le != cudaSuccess)
-        st = fail(h, FIRE_ERR_CUDA, "cooperative step launch: %s", cudaGetErrorString(le));
     if (st == FIRE_OK)
         st = capture_plain(h, &h->exec_final, [&](cudaStream_t s) {
             k_finalize<<<ceil_div(n, kElemBlock), kElemBlock, 0, s>>>(h->b);
@@ -1966,28 +1925,14 @@ fire_status fire_profile_stages(fire_handle_t* h, const double* pos, const doubl
         else if (h->pot.kind == FIRE_POT_SW) k_force_sw<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
         else force_lj(h->b, h->potc, g, s);
         cudaEventRecord(ev[4], s);
+        // the control step runs in the last block of the reductions' launch
+        // (k_reduce_ctl); NEB handles run it as a kernel of its own
         const cudaGraphConditionalHandle none{};
-        if (fused_step(h)) {
-            // reductions, control step and update in one cooperative launch
-            // (k_step; the control in CTL_EVAL mode leaves dt = 0, so the
-            // update does not move the atoms): all of it under FIRE_STAGE_REDUCE
-            const cudaError_t le = launch_step(h, g, s, CTL_EVAL, none, 0, none, 0, none, 0);
-            if (le != cudaSuccess) {
-                for (auto& x : ev) cudaEventDestroy(x);
-                return fail(h, FIRE_ERR_CUDA, "cooperative step launch: %s", cudaGetErrorString(le));
-            }
-            cudaEventRecord(ev[5], s);
-            cudaEventRecord(ev[6], s);
-            cudaEventRecord(ev[7], s);
-        } else {
-            // the control step runs in the last block of the reductions'
-            // launch (k_reduce_ctl); NEB handles run it as a kernel of its own
-            launch_reduce_control(h, g, s, CTL_EVAL, none, 0);
-            cudaEventRecord(ev[5], s);
-            cudaEventRecord(ev[6], s);
-            launch_update(h, g, s, none, 0);
-            cudaEventRecord(ev[7], s);
-        }
+        launch_reduce_control(h, g, s, CTL_EVAL, none, 0);
+        cudaEventRecord(ev[5], s);
+        cudaEventRecord(ev[6], s);
+        launch_update(h, g, s, none, 0);
+        cudaEventRecord(ev[7], s);
         cudaError_t e = cudaEventSynchronize(ev[7]);
         if (e != cudaSuccess) {
             for (auto& x : ev) cudaEventDestroy(x);

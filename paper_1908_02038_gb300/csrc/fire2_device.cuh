@@ -82,8 +82,7 @@ struct DevState {
     int vstate, vcount, vmode;
     double ftol_user, fn32, fsw;
     int tile_over;         // tile builds whose stage overflowed (pairs then use global atomics)
-    unsigned int red_blocks;   // k_reduce_ctl / k_step blocks arrived (last-block test)
-    unsigned int step_gen;     // k_step: bumped by the block that ran the control step
+    unsigned int red_blocks;   // k_reduce_ctl blocks finished (last-block test)
 };
 
 struct Bufs {
@@ -1337,7 +1336,7 @@ __global__ void k_reduce_ctl(Bufs b, int mode, cudaGraphConditionalHandle h, int
 // for the next force evaluation (accumulating paths) and tracks
 // max |x - x_ref|^2.  With has_if, the last block to finish sets the graph's
 // IF condition to "the neighbour list must be rebuilt" (see need_rebuild).
-// The element-wise step of k_update and k_step, given the state the control
+// The element-wise step of k_update, given the state the control
 // step left (s, done, vstate) and the drift dt.
 __device__ void update_body(const Bufs& b, const GeoC& g, const FireScal& s, int done, int vstate,
                             double dt, int after_pre, cudaGraphConditionalHandle hif, int has_if,
@@ -1405,93 +1404,6 @@ __global__ void k_update(Bufs b, GeoC g, cudaGraphConditionalHandle hif, int has
                                 : s.dt_cur;
     update_body(b, g, s, b.st->done, b.st->vstate, dt, after_pre, hif, has_if, hconf, has_conf,
                 red);
-}
-
-// A struct written by another block of the same launch, read past L1.
-template <typename T>
-__device__ __forceinline__ T load_cg(const T* p) {
-    static_assert(sizeof(T) % 8 == 0, "8-byte words");
-    T out;
-    const unsigned long long* src = reinterpret_cast<const unsigned long long*>(p);
-    unsigned long long* dst = reinterpret_cast<unsigned long long*>(&out);
-#pragma unroll
-    for (int k = 0; k < (int)(sizeof(T) / 8); ++k) dst[k] = __ldcg(src + k);
-    return out;
-}
-
-constexpr unsigned long long kStepWaitNs = 2000000000ull;   // release wait limit of k_step
-
-// One loop pass's reductions, control step (Algorithm 2) and element-wise
-// step (Algorithm 4) in one cooperative launch of nb_red blocks, all
-// resident: every block writes its partials and takes a ticket; the last
-// block runs the control step and bumps step_gen; the others wait for that
-// (at most kStepWaitNs, then the call ends with ST_TIMEOUT) and all apply
-// the update.  Replaces k_reduce_ctl + k_update where no displacement cap
-// and no NEB projection sit between them.
-__global__ void k_step(Bufs b, GeoC g, int mode, cudaGraphConditionalHandle hw, int has_w,
-                       cudaGraphConditionalHandle hif, int has_if,
-                       cudaGraphConditionalHandle hconf, int has_conf) {
-    __shared__ double red[32];
-    __shared__ double sh[6 * 32];
-    __shared__ int last, ok;
-    if (b.st->done) {   // chunked loop bodies past the stop
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
-            if (has_w) cudaGraphSetConditional(hw, 0u);
-            if (has_if) cudaGraphSetConditional(hif, 0u);
-            if (has_conf) cudaGraphSetConditional(hconf, 0u);
-        }
-        return;
-    }
-    const double vvh = vv_half_of(b.st);
-    RedAcc acc;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < b.n; i += gridDim.x * blockDim.x) {
-        dvec4 f = b.f[i];
-        if (mask_force(b, i, f)) b.f[i] = f;
-        red_atom(b, i, f, b.v[i], vvh, acc);
-    }
-    red_write(acc, red, b.rpart);
-    unsigned g0 = 0u;
-    if (threadIdx.x == 0) {
-        g0 = *(volatile unsigned int*)&b.st->step_gen;   // before the ticket
-        __threadfence();
-        last = atomicAdd(&b.st->red_blocks, 1u) == gridDim.x - 1 ? 1 : 0;
-        ok = 1;
-    }
-    __syncthreads();
-    if (last) {
-        if (threadIdx.x == 0) b.st->red_blocks = 0u;
-        __threadfence();
-        control_body(b, mode, hw, has_w, sh);
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            __threadfence();
-            atomicAdd(&b.st->step_gen, 1u);   // release
-        }
-    } else if (threadIdx.x == 0) {
-        const volatile unsigned int* gen = &b.st->step_gen;
-        const unsigned long long t0 = globaltimer_ns();
-        while (*gen == g0) {
-            if (globaltimer_ns() - t0 > kStepWaitNs) {
-                ok = 0;
-                break;
-            }
-            __nanosleep(64);
-        }
-        __threadfence();
-    }
-    __syncthreads();
-    if (!ok) {   // never with every block resident; ends the call instead of waiting on
-        if (threadIdx.x == 0) {
-            set_status(b.st, ST_TIMEOUT);
-            atomicExch(&b.st->done, 1);
-            if (has_w) cudaGraphSetConditional(hw, 0u);
-            if (has_if) cudaGraphSetConditional(hif, 0u);
-        }
-        return;
-    }
-    const FireScal s = load_cg(&b.st->fs);
-    const int done = __ldcg(&b.st->done), vstate = __ldcg(&b.st->vstate);
-    update_body(b, g, s, done, vstate, s.dt_cur, 0, hif, has_if, hconf, has_conf, red);
 }
 
 // With a maximum displacement per step (dmax > 0) the element-wise step runs
