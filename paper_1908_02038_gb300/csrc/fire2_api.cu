@@ -207,6 +207,7 @@ GeoC make_geo(const fire_handle* h, const double box[3]) {
     const double rl = rc + skin;
     g.rlist2 = rl * rl;
     g.half_skin2 = 0.25 * skin * skin;
+    g.rc2f = (float)(rc * rc);
     g.brute = 0;
     for (int a = 0; a < 3; ++a) {
         g.L[a] = box[a];

@@ -287,19 +287,19 @@ __device__ __forceinline__ double b_forces(const BArgs& a, const BInst& I, int l
                     load_row(a.tab_ffd, ff_index(P.tab, uf), row);
                     ffloat v[2];
                     ff_row_eval(row, r2, v);
-                    erep = ff_add(erep, v[0]);
-                    rho = ff_add(rho, v[1]);
+                    erep = ff_acc(erep, v[0]);
+                    rho = ff_acc(rho, v[1]);
                 } else {   // compressed below the table: FP64 exponentials
                     double rinv, phi, dphi, g, dg;
                     rgl_pair64(P, ff_to_f64(r2), etab, rinv, phi, dphi, g, dg);
-                    erep = ff_add(erep, f64_to_ff(phi));
-                    rho = ff_add(rho, f64_to_ff(g));
+                    erep = ff_acc(erep, f64_to_ff(phi));
+                    rho = ff_acc(rho, f64_to_ff(g));
                 }
             }
             double sq, fp;
-            rgl_embed(ff_to_f64(rho), sq, fp);
+            ffloat fpf;
+            rgl_embed_dd(ff_to_f64(rho), sq, fp, fpf);
             a.fp64[gi] = fp;
-            const ffloat fpf = f64_to_ff(fp);
             a.fpff[gi] = make_float2(fpf.hi, fpf.lo);
             e_sum += ff_to_f64(erep) - sq;
         } else {
@@ -382,9 +382,9 @@ __device__ __forceinline__ double b_forces(const BArgs& a, const BInst& I, int l
                 }
                 const float2 fpj2 = a.fpff[I.off + (int)(e & kIdxMask)];
                 const ffloat fs = ff_add(c[0], ff_mul(ff_add(fpi, {fpj2.x, fpj2.y}), c[1]));
-                fx = ff_add(fx, ff_mul(fs, dx));
-                fy = ff_add(fy, ff_mul(fs, dy));
-                fz = ff_add(fz, ff_mul(fs, dz));
+                fx = ff_acc(fx, ff_mul(fs, dx));
+                fy = ff_acc(fy, ff_mul(fs, dy));
+                fz = ff_acc(fz, ff_mul(fs, dz));
             }
             a.f[gi] = make_dvec4(ff_to_f64(fx), ff_to_f64(fy), ff_to_f64(fz), 0.0);
         } else {

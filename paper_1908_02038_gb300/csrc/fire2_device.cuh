@@ -34,6 +34,7 @@ struct GeoC {
     int brute;             // 1 = all-pairs list build (a periodic axis under 3 cells)
     double rlist2;         // (rc + skin)^2
     double half_skin2;     // (skin / 2)^2
+    float rc2f;            // rc^2 in FP32: the list puts the pairs inside rc first
     // FP32 copies for the list build's candidate test
     float Lf[3], Linvf[3];
     float rlist2f;         // (rc + skin + margin)^2, margin covers FP32 rounding
@@ -293,10 +294,23 @@ __device__ __forceinline__ float4 xf_of(const Bufs& b, int j) {
     return make_float4((float)x.x, (float)x.y, (float)x.z, 0.f);
 }
 
+// List order: the pairs inside rc come first and the skin pairs (rc up to
+// rc + skin, which the force kernels test and skip) after them, so that
+// the lanes of a warp evaluate their in-range pairs together and skip their
+// skin pairs together; a warp otherwise issues the whole pair evaluation
+// whenever any of its lanes has an in-range pair at that list position.
+// Skin pairs wait in a small per-thread buffer and are appended at the end
+// (beyond kSkinBuf of them the rest are written in the order found).
+constexpr int kSkinBuf = 24;
+struct SkinBuf {
+    uint32_t e[kSkinBuf];
+    int n;
+};
+
 // FP32 positions come from xf (refreshed by k_cell_count) in cell mode and
 // are converted from x in the all-pairs mode (small systems).
 __device__ __forceinline__ void try_add_pair(const Bufs& b, const GeoC& g, int i, float4 xi,
-                                             int j, int& cnt) {
+                                             int j, int& cnt, SkinBuf& sk) {
     const float4 xj = g.brute ? xf_of(b, j) : b.xf[j];
     float d[3] = {xj.x - xi.x, xj.y - xi.y, xj.z - xi.z};
     int s[3] = {0, 0, 0};
@@ -316,10 +330,13 @@ __device__ __forceinline__ void try_add_pair(const Bufs& b, const GeoC& g, int i
         set_status(b.st, ST_RANGE);
         return;
     }
-    if (cnt < b.cap) {
-        const uint32_t code = (uint32_t)((s[0] + 2) + 5 * (s[1] + 2) + 25 * (s[2] + 2));
-        b.nbr[(size_t)cnt * b.n + i] = (code << kIdxBits) | (uint32_t)j;
+    const uint32_t code = (uint32_t)((s[0] + 2) + 5 * (s[1] + 2) + 25 * (s[2] + 2));
+    const uint32_t e = (code << kIdxBits) | (uint32_t)j;
+    if (!(r2 < g.rc2f) && sk.n < kSkinBuf) {
+        sk.e[sk.n++] = e;
+        return;
     }
+    if (cnt < b.cap) b.nbr[(size_t)cnt * b.n + i] = e;
     ++cnt;
 }
 
@@ -331,10 +348,12 @@ __global__ void k_nbr_build(Bufs b, GeoC g, int force) {
     const dvec4 xi = b.x[i];
     const float4 xif = g.brute ? xf_of(b, i) : b.xf[i];
     int cnt = 0;
+    SkinBuf sk;
+    sk.n = 0;
     const int img = i / g.img_n;
     if (g.brute) {
         for (int j = img * g.img_n; j < (img + 1) * g.img_n; ++j)
-            if (j != i) try_add_pair(b, g, i, xif, j, cnt);
+            if (j != i) try_add_pair(b, g, i, xif, j, cnt, sk);
     } else {
         const int cx = cell_coord(xi.x, g.Linv[0], g.nc[0], g.per[0]);
         const int cy = cell_coord(xi.y, g.Linv[1], g.nc[1], g.per[1]);
@@ -351,11 +370,15 @@ __global__ void k_nbr_build(Bufs b, GeoC g, int force) {
                     const int c = cell_index(g, img, ax, ay, az);
                     for (int k = b.cell_start[c]; k < b.cell_start[c + 1]; ++k) {
                         const int j = b.cell_atoms[k];
-                        if (j != i) try_add_pair(b, g, i, xif, j, cnt);
+                        if (j != i) try_add_pair(b, g, i, xif, j, cnt, sk);
                     }
                 }
             }
         }
+    }
+    for (int q = 0; q < sk.n; ++q) {   // the skin pairs after the in-range ones
+        if (cnt < b.cap) b.nbr[(size_t)cnt * b.n + i] = sk.e[q];
+        ++cnt;
     }
     if (cnt > b.cap) {
         set_status(b.st, ST_NBR_OVERFLOW);
@@ -438,12 +461,16 @@ __global__ void k_embed(Bufs b) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < b.n; i += gridDim.x * blockDim.x) {
         const double rho = b.rho[i];
         double sq, fp;
-        rgl_embed(rho, sq, fp);
-        b.fp[i] = fp;
-        if (b.fpff) {   // FP64 form: F' as a float pair for the force pass
-            const ffloat q = f64_to_ff(fp);
-            b.fpff[i] = make_float2(q.hi, q.lo);
+        if (b.fpff) {
+            // FP64 form with double-float pair terms: the embedding in float
+            // pairs too, F' as a float pair for the force pass
+            ffloat fpf;
+            rgl_embed_dd(rho, sq, fp, fpf);
+            b.fpff[i] = make_float2(fpf.hi, fpf.lo);
+        } else {
+            rgl_embed(rho, sq, fp);
         }
+        b.fp[i] = fp;
         emb -= sq;
         if (b.eatom) b.eatom[i] -= sq;
     }
@@ -958,14 +985,14 @@ __global__ void __launch_bounds__(kForceBlock) k_density_ff(Bufs b, PotC P, GeoC
                 load_row(b.tab_ffd, ff_index(P.tab, uf), row);
                 ffloat v[2];
                 ff_row_eval(row, r2, v);
-                erep = ff_add(erep, v[0]);   // doubled at the end on the half list
-                rho = ff_add(rho, v[1]);
+                erep = ff_acc(erep, v[0]);   // doubled at the end on the half list
+                rho = ff_acc(rho, v[1]);
                 if (HALF) atomicAdd(&b.rho[j], ff_to_f64(v[1]));
             } else {
                 double rinv, phi, dphi, gg, dg;
                 rgl_pair64(P, ff_to_f64(r2), etab, rinv, phi, dphi, gg, dg);
-                erep = ff_add(erep, f64_to_ff(phi));
-                rho = ff_add(rho, f64_to_ff(gg));
+                erep = ff_acc(erep, f64_to_ff(phi));
+                rho = ff_acc(rho, f64_to_ff(gg));
                 if (HALF) atomicAdd(&b.rho[j], gg);
             }
         }
@@ -977,10 +1004,10 @@ __global__ void __launch_bounds__(kForceBlock) k_density_ff(Bufs b, PotC P, GeoC
             if (b.eatom) b.eatom[i] = e_atom;
         } else if (lane == 0) {
             double sq, fp;
-            rgl_embed(rho_d, sq, fp);
+            ffloat fpf;
+            rgl_embed_dd(rho_d, sq, fp, fpf);
             b.rho[i] = rho_d;
             b.fp[i] = fp;
-            const ffloat fpf = f64_to_ff(fp);
             b.fpff[i] = make_float2(fpf.hi, fpf.lo);
             e_atom = erep_d - sq;
             if (b.eatom) b.eatom[i] = e_atom;
@@ -1041,9 +1068,9 @@ __global__ void __launch_bounds__(kForceBlock) k_force_ff(Bufs b, PotC P, GeoC g
         }
         const ffloat fs = ff_add(c[0], ff_mul(ff_add(fpi, {fpj2.x, fpj2.y}), c[1]));
         const ffloat tx = ff_mul(fs, dx), ty = ff_mul(fs, dy), tz = ff_mul(fs, dz);
-        fx = ff_add(fx, tx);
-        fy = ff_add(fy, ty);
-        fz = ff_add(fz, tz);
+        fx = ff_acc(fx, tx);
+        fy = ff_acc(fy, ty);
+        fz = ff_acc(fz, tz);
         if (HALF) {
             atomicAdd(&b.f[j].x, -ff_to_f64(tx));
             atomicAdd(&b.f[j].y, -ff_to_f64(ty));
@@ -1181,6 +1208,9 @@ struct CtlSums {
 __device__ __forceinline__ CtlSums ctl_reduce(const Bufs& b, int ne, double* sh /* 6 x 32 */) {
     double a[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     const int nr = b.nb_red;
+    // unrolled so that a thread's loads are in flight together (the sums
+    // keep their order; one partial per density block, ~7,800 at 1M atoms)
+#pragma unroll 4
     for (int k = threadIdx.x; k < nr; k += blockDim.x) {
         a[0] += b.rpart[k];
         a[1] += b.rpart[nr + k];
@@ -1188,7 +1218,19 @@ __device__ __forceinline__ CtlSums ctl_reduce(const Bufs& b, int ne, double* sh 
         a[3] = fmax(a[3], b.rpart[3 * nr + k]);
         a[4] = fmax(a[4], b.rpart[4 * nr + k]);
     }
-    for (int k = threadIdx.x; k < ne; k += blockDim.x) a[5] += b.epart[k];
+    {   // four independent sums per thread, so that its loads overlap
+        const int bd = blockDim.x;
+        double e0 = 0.0, e1 = 0.0, e2 = 0.0, e3 = 0.0;
+        int k = threadIdx.x;
+        for (; k + 3 * bd < ne; k += 4 * bd) {
+            e0 += b.epart[k];
+            e1 += b.epart[k + bd];
+            e2 += b.epart[k + 2 * bd];
+            e3 += b.epart[k + 3 * bd];
+        }
+        for (; k < ne; k += bd) e0 += b.epart[k];
+        a[5] = (e0 + e1) + (e2 + e3);
+    }
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {

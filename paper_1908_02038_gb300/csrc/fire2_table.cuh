@@ -374,10 +374,51 @@ __host__ __device__ __forceinline__ ffloat ff_mul_f(ffloat a, float b) {
 __host__ __device__ __forceinline__ double ff_to_f64(ffloat a) {
     return f32_to_f64(a.hi) + f32_to_f64(a.lo);
 }
+// Running sum of double-float terms: TwoSum on the high parts, the low
+// parts and the TwoSum errors added in plain FP32, no renormalisation
+// (ff_to_f64 takes the pair as it is).  Over the few dozen terms of one
+// atom's list the low sum stays below ~2^-48 of the largest term.
+__host__ __device__ __forceinline__ ffloat ff_acc(ffloat acc, ffloat t) {
+    const ffloat s = two_sum(acc.hi, t.hi);
+    return {s.hi, add_rn(acc.lo, add_rn(s.lo, t.lo))};
+}
 // d (|d| < 2^127) as hi + lo, both truncated: |d - hi - lo| < 2^-46 |d|
 __host__ __device__ __forceinline__ ffloat f64_to_ff(double d) {
     const float hi = f64_to_f32_trunc(d);
     return {hi, f64_to_f32_trunc(d - f32_to_f64(hi))};
+}
+
+// RGL embedding of the double-float form: sqrt(rho) and F'(rho) =
+// -1/(2 sqrt(rho)) as float pairs from one reciprocal square root y.  The
+// FP32 estimate y0 (relative error e0 ~ 2^-22) takes one Newton step on
+// 1/y^2 - rho, y1 = y0 + y0 (1 - rho y0^2) / 2, with 1 - rho y0^2 formed in
+// float pairs; y1 is then off by 1.5 e0^2 ~ 1e-13 (relative, from below),
+// the precision of the pair terms.  FP32 and integer instructions only (FP64
+// issues at 1/64 of the FP32 rate on this part).  Valid for rho in the
+// normal FP32 range; the caller takes the FP64 routine outside it.
+__device__ __forceinline__ void rgl_embed_ff(ffloat r, ffloat& sq, ffloat& fp) {
+    const float y0 = rsqrtf(r.hi);
+    const float p = y0 * y0;
+    const ffloat y0sq = {p, fmaf(y0, y0, -p)};              // exact square
+    const ffloat t = ff_mul(r, y0sq);                       // rho y0^2 ~ 1
+    const ffloat e = ff_add({1.f, 0.f}, {-t.hi, -t.lo});     // ~2^-22
+    const ffloat y1 = fast_two_sum(y0, 0.5f * y0 * e.hi);
+    sq = ff_mul(r, y1);
+    fp = {-0.5f * y1.hi, -0.5f * y1.lo};                    // exact scaling
+}
+
+// The embedding of the double-float form at an FP64 density: sqrt(rho) and
+// F'(rho) in FP64, and F' as the float pair the force pass reads.
+__device__ __forceinline__ void rgl_embed_dd(double rho, double& sq, double& fp, ffloat& fpf) {
+    if (rho > 1e-30 && rho < 1e30) {
+        ffloat sqf;
+        rgl_embed_ff(f64_to_ff(rho), sqf, fpf);
+        sq = ff_to_f64(sqf);
+        fp = ff_to_f64(fpf);
+    } else {
+        rgl_embed(rho, sq, fp);
+        fpf = f64_to_ff(fp);
+    }
 }
 
 // One quintic of a row: c = 9 floats (see the layout above), s as a float pair.
@@ -413,7 +454,13 @@ __device__ __forceinline__ void load_row(const float* tab, int k, float row[kFFR
 
 // The two polynomials of `row` at r^2 (float pair): out[0], out[1].
 __host__ __device__ __forceinline__ void ff_row_eval(const float* row, ffloat r2, ffloat out[2]) {
-    const ffloat s = ff_add(r2, ff_neg({row[0], row[1]}));
+    // s = r^2 - (u_k + r0^2): r2.hi and the knot's high part row[0] lie
+    // within a factor 2 of each other (r^2 falls in the knot's interval,
+    // ~0.04 A^2 wide, above 0.25 r0^2), so their difference is exact
+    // (Sterbenz); the low parts' difference joins it in one Fast2Sum (where
+    // that difference exceeds the first, both are below 2^-20 A^2 and the
+    // pair is off by far less than 2^-40 A^2)
+    const ffloat s = fast_two_sum(add_rn(r2.hi, -row[0]), add_rn(r2.lo, -row[1]));
     out[0] = ff_poly(row + 2, s);
     out[1] = ff_poly(row + 11, s);
 }

@@ -358,8 +358,8 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) k_density_tile(B
                     v[0] = f64_to_ff(phi);
                     v[1] = f64_to_ff(gg);
                 }
-                erep = ff_add(erep, v[0]);
-                rho = ff_add(rho, v[1]);
+                erep = ff_acc(erep, v[0]);
+                rho = ff_acc(rho, v[1]);
                 int H, L;
                 if (sl != kSlotNone && fx_split_pair(v[1].hi, v[1].lo, H, L)) {
                     atomicAdd(&aH[sl], H);
@@ -479,9 +479,9 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) k_force_tile(Buf
                 }
                 const ffloat fs = ff_add(c[0], ff_mul(ff_add(fpi, {fpj2.x, fpj2.y}), c[1]));
                 const ffloat t[3] = {ff_mul(fs, dx), ff_mul(fs, dy), ff_mul(fs, dz)};
-                fx = ff_add(fx, t[0]);
-                fy = ff_add(fy, t[1]);
-                fz = ff_add(fz, t[2]);
+                fx = ff_acc(fx, t[0]);
+                fy = ff_acc(fy, t[1]);
+                fz = ff_acc(fz, t[2]);
 #pragma unroll
                 for (int cc = 0; cc < 3; ++cc) {
                     int H, L;
