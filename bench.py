@@ -250,12 +250,14 @@ class ClockSampler:
 
 
 def _device_src_hash():
+    """Hash of every kernel source (csrc/*.cu, *.cuh): ncu figures recorded
+    under another hash describe other code."""
+    import glob
     import hashlib
     h = hashlib.sha256()
-    for f in ("fire2_device.cuh", "fire2_tile.cuh"):
-        path = os.path.join(ROOT, "paper_1908_02038_gb300", "csrc", f)
-        if os.path.exists(path):
-            h.update(open(path, "rb").read())
+    for path in sorted(glob.glob(os.path.join(ROOT, "paper_1908_02038_gb300", "csrc", "*.cu*"))):
+        h.update(os.path.basename(path).encode())
+        h.update(open(path, "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -273,6 +275,8 @@ def read_ncu(kernel, workload="rgl1m"):
         if len(parts) >= 4 and parts[0] == kernel and parts[1] == h and parts[2] == workload:
             out = {}
             for kv in parts[3:]:
+                if kv.startswith("#"):   # the command the line came from
+                    break
                 k, _, v = kv.partition("=")
                 try:
                     out[k] = float(v)
