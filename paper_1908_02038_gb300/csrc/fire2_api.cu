@@ -384,7 +384,7 @@ void density_ff(const Bufs& b, const PotC& P, const GeoC& g, int nb, cudaStream_
     case 8: k_density_ff<HALF, 8><<<nb, kForceBlock, 0, s>>>(b, P, g); break;
     case 4: k_density_ff<HALF, 4><<<nb, kForceBlock, 0, s>>>(b, P, g); break;
     case 2: k_density_ff<HALF, 2><<<nb, kForceBlock, 0, s>>>(b, P, g); break;
-    default: k_density_ff<HALF, 1><<<nb, kForceBlock, 0, s>>>(b, P, g);
+    default: k_density_ff1<HALF><<<nb, kForceBlock, 0, s>>>(b, P, g);
     }
 }
 template <bool HALF>

@@ -958,8 +958,8 @@ __device__ __forceinline__ ffloat pair_sep_ff(const Bufs& b, const long long* qt
 // compressed below r0/2 fall back to the FP64 exponentials.  TPA threads
 // share an atom: lane l takes list slots l, l + TPA, ..., and the lanes'
 // sums are added in FP64 (group_sum) before lane 0 finishes the atom.
-template <bool HALF, int TPA = 1>
-__global__ void __launch_bounds__(kForceBlock) k_density_ff(Bufs b, PotC P, GeoC g) {
+template <bool HALF, int TPA>
+__device__ __forceinline__ void density_ff_body(const Bufs& b, const PotC& P, const GeoC& g) {
     __shared__ long long qt[375];
     __shared__ double etab[kExpTableSize];
     __shared__ double red[32];
@@ -1015,6 +1015,20 @@ __global__ void __launch_bounds__(kForceBlock) k_density_ff(Bufs b, PotC P, GeoC
     }
     const double s = block_sum(e_atom, red);
     if (threadIdx.x == 0) b.epart[blockIdx.x] = s;
+}
+
+template <bool HALF, int TPA = 1>
+__global__ void __launch_bounds__(kForceBlock) k_density_ff(Bufs b, PotC P, GeoC g) {
+    density_ff_body<HALF, TPA>(b, P, g);
+}
+
+// The same pass with one thread per atom (large systems) on 12 blocks per SM
+// (40 registers): 0.312 against 0.325 ms on the 1M-atom box with the
+// compiler's 44.  (The force pass keeps the compiler's 64: capped at 56 or
+// 48 it spills and takes 0.51 and 0.69 against 0.48 ms.)
+template <bool HALF>
+__global__ void __launch_bounds__(kForceBlock, 12) k_density_ff1(Bufs b, PotC P, GeoC g) {
+    density_ff_body<HALF, 1>(b, P, g);
 }
 
 // Pass 2: F_i = sum_j [2 phi'/r + (F'_i + F'_j) g'/r] (x_j - x_i) (F = -grad E,
