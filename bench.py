@@ -143,8 +143,8 @@ def potential_for(cfg_name, form="fp64"):
         return (fg.Potential(fg.FIRE_POT_LJ, eps=1.0, sigma=1.0, rc_lj=2.5, skin=0.3),
                 fi.LJ_MASS, fi.LJ_DT, 1e-8)
     prec = fg.FIRE_PREC_FP32_PAIR if form == "fp32pair" else fg.FIRE_PREC_FP64
-    # the FP32-pair form stops at ftol: the library confirms such a stop with
-    # one FP64 evaluation (fire_params_t.confirm64), so its structure meets
+    # the FP32-pair form stops at ftol on FP64 forces: by default the library
+    # evaluates in FP64 from 3 ftol on (fire_params_t.confirm64), so its structure meets
     # ftol in FP64 (which the line checks again)
     ftol = FTOL
     return (fg.Potential(fg.FIRE_POT_RGL, precision=prec, skin=0.3, **fi.RGL_CU), fi.CU_MASS,
@@ -329,7 +329,7 @@ def relax_form(fg, torch, cfg, form, pair, args, dev, stream, clocks=True, confi
     """Times args.steps relaxations of cfg (after args.warmup untimed ones) in
     one form; returns the measurement, the handle (still open) and the
     relaxed positions of the last step.  confirm64: the FP32-pair form's FP64
-    check (fire_fp64_check; None = the library default, confirmation)."""
+    check (fire_fp64_check; None = the library default, FP64 from 3 ftol on)."""
     pot, mass, dt, ftol = potential_for(args.config, form)
     pot.pair_eval = fg.FIRE_PAIR_ANALYTIC if pair == "analytic" else fg.FIRE_PAIR_TABLE
     pot.newton = {"auto": fg.FIRE_NEWTON_AUTO, "on": fg.FIRE_NEWTON_ON,
@@ -475,7 +475,7 @@ def batch_block(fg, torch, dev, steps=3, tuning=None, compare=True):
     """The batched form: 512 independent Cu boxes of 3^3..12^3 cells (1-3
     vacancies each, ~1.24 M atoms) relaxed in one persistent launch,
     FP32-pair with FP64 reductions, each to max|F_i| < 1e-6 eV/A (every
-    stop confirmed in FP64 by the library); launch shape from the library's
+    system finishing in FP64 from 3 ftol on, the library's default); launch shape from the library's
     autotuner; atom-iterations over all systems per second over `steps`
     timed batches after one untimed."""
     cfgs = fi.rgl_batch(n_sys=512, seed=4)
@@ -513,10 +513,10 @@ def batch_block(fg, torch, dev, steps=3, tuning=None, compare=True):
            "converged": int(sum(r.stop == fg.FIRE_STOP_FTOL for r in res)),
            "max_iterations": int(max(r.iterations for r in res))}
     if compare:
-        # the same batch finishing in FP64 below 3 ftol (a precision schedule,
-        # per system), at the same launch shape
+        # the same batch with one FP64 confirmation of each system's stop on
+        # ftol (the default finishes in FP64 below 3 ftol), same launch shape
         with fg.FireBatch(counts, fi.CU_MASS, pot, dt_start=fi.CU_DT,
-                          confirm64=fg.FIRE_FP64_CHECK_FINISH) as bf:
+                          confirm64=fg.FIRE_FP64_CHECK_CONFIRM) as bf:
             bf.set_tuning(tune["threads_per_block"], tune["ctas_per_sm"],
                           tune.get("cluster_size", 1) or 1)
             w.copy_(x0)
@@ -529,7 +529,7 @@ def batch_block(fg, torch, dev, steps=3, tuning=None, compare=True):
             e1.record()
             torch.cuda.synchronize()
         msf = e0.elapsed_time(e1)
-        out["finish64"] = {"ms_per_step": msf,
+        out["confirm64"] = {"ms_per_step": msf,
                            "value": sum(int(r.iterations) * int(n) for r, n in zip(rf, counts))
                            / (msf * 1e-3), "unit": UNIT,
                            "converged": int(sum(r.stop == fg.FIRE_STOP_FTOL for r in rf)),
@@ -703,7 +703,7 @@ def rgl32k_block(fg, torch, dev, stream):
     """Config 2: the RGL-Cu FCC 20^3-cell box with 1 % vacancies (31,680
     atoms, Gaussian 0.05 A noise, seed 2) relaxed to max_i |F_i| < 1e-6 eV/A
     in the FP64 form (double-float table terms, the library default) and the
-    FP32-pair form (each stop confirmed in FP64 by the library); each relaxed
+    FP32-pair form (finishing in FP64 from 3 ftol on, the library default); each relaxed
     structure re-evaluated with the IEEE-FP64 kernels."""
     cfg = CONFIGS["rgl32k"]()
     out = {"workload": f"{cfg.name} ({cfg.n} atoms), RGL Cu, max|F_i| < {FTOL:g} eV/A",
@@ -1088,13 +1088,14 @@ def run_gpu(args):
     # the other forms on the same workload, each relaxed state re-evaluated
     # with the IEEE FP64 exponential pair terms (k_density / k_force_rgl)
     if is_rgl and not args.no_forms and world == 1:
-        # (form, pair evaluation, FP32-pair FP64 check); the third FP32-pair
-        # entry finishes in FP64 below 3 ftol (a precision schedule)
+        # (form, pair evaluation, FP32-pair FP64 check): the FP32-pair form
+        # with the library's default (FP64 from 3 ftol on) and with one FP64
+        # confirmation of each stop on ftol
         others = [f for f in (("fp32pair", "analytic", None), ("fp64", "analytic", None),
                               ("fp64", "table", None))
                   if f[:2] != (args.form, pair)][:2]
         if args.form != "fp32pair":
-            others.append(("fp32pair", "analytic", fg.FIRE_FP64_CHECK_FINISH))
+            others.append(("fp32pair", "analytic", fg.FIRE_FP64_CHECK_CONFIRM))
         pot64, mass, dt, _ = potential_for(args.config, "fp64")
         pot64.pair_eval = fg.FIRE_PAIR_ANALYTIC
         out["forms"] = {}
@@ -1113,7 +1114,7 @@ def run_gpu(args):
                 ms2 = m2["ms"]
                 it2 = sum(rr["iterations"] for rr in m2["results"])
                 f64_fmax, e64 = check(x2)
-                key = f"{oform}_{opair}" + ("_finish64" if ocheck == fg.FIRE_FP64_CHECK_FINISH
+                key = f"{oform}_{opair}" + ("_confirm64" if ocheck == fg.FIRE_FP64_CHECK_CONFIRM
                                             else "")
                 out["forms"][key] = {
                     "value": n * it2 / (ms2 * 1e-3), "unit": UNIT,

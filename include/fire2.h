@@ -135,7 +135,11 @@ typedef enum {
  * FIRE_FP64_CHECK_FINISH: FP32-pair forces while the force norm is at least
  *   3 ftol, FP64 forces (double-float table terms, full list) from the first
  *   evaluation below it to the end; a precision schedule (per system in the
- *   batched form). */
+ *   batched form).  The default: below 3 ftol the FP32-pair force error
+ *   starts to steer FIRE, and with CONFIRM the number of iterations in that
+ *   tail depends on the trajectory's rounding (1M-atom Cu box to 1e-6 eV/A:
+ *   435 or 664 iterations after a change in the last bit of the update
+ *   arithmetic) where FINISH takes 353 both times, against 349 in FP64. */
 typedef enum {
     FIRE_FP64_CHECK_OFF = 0,
     FIRE_FP64_CHECK_CONFIRM = 1,
@@ -195,7 +199,7 @@ typedef struct {
     int32_t norm;               /* fire_norm for the ftol test       (default 0) */
     int32_t variant;            /* fire_variant                      (default 0) */
     int32_t confirm64;          /* fire_fp64_check, FP32-pair form only (default
-                                   FIRE_FP64_CHECK_CONFIRM) */
+                                   FIRE_FP64_CHECK_FINISH) */
     double dmax;                /* maximum displacement of any atom per step (the
                                    paper's dmax, Sec. 4 cases 1 and 7), 0 = no cap
                                    (default 0): the drift x += dt v uses

@@ -504,24 +504,17 @@ NebC neb_consts(const fire_handle* h) {
 
 // The FP64 reductions of (F, v); for NEB handles the projection that ends
 // with them.
-void launch_reduce(fire_handle* h, const GeoC& g, cudaStream_t s) {
-    if (h->neb) {   // nudged elastic band: project, then reduce (F^NEB, v)
+// The reductions and the control step (Algorithm 2) of one evaluation: one
+// launch (k_reduce_ctl, whose last block runs the control), or for NEB
+// handles the projection chain (which ends with the reductions of
+// (F^NEB, v)) followed by k_control.
+void launch_reduce_control(fire_handle* h, const GeoC& g, cudaStream_t s, int mode,
+                           cudaGraphConditionalHandle hc, int has_handle) {
+    if (h->neb) {
         const NebC c = neb_consts(h);
         k_neb_sums<<<dim3(c.nb, c.n_img), kNebBlock, 0, s>>>(h->b, g, c);
         k_neb_scalars<<<1, 256, (size_t)c.n_img * kNebSums * sizeof(double), s>>>(h->b, c);
         k_neb_project<<<h->neb->nb_proj, kNebBlock, 0, s>>>(h->b, g, c);
-        return;
-    }
-    k_reduce<<<h->b.nb_red, kElemBlock, 0, s>>>(h->b);
-}
-
-// The reductions and the control step (Algorithm 2) of one evaluation: one
-// launch (k_reduce_ctl, whose last block runs the control), or for NEB
-// handles the projection chain followed by k_control.
-void launch_reduce_control(fire_handle* h, const GeoC& g, cudaStream_t s, int mode,
-                           cudaGraphConditionalHandle hc, int has_handle) {
-    if (h->neb) {
-        launch_reduce(h, g, s);
         k_control<<<1, kCtlThreads, 0, s>>>(h->b, mode, hc, has_handle);
         return;
     }
@@ -860,7 +853,7 @@ fire_status fire_default_params(fire_params_t* out, double dt_start) {
     out->integrator = FIRE_INT_EULER_IMPLICIT;
     out->norm = FIRE_NORM_MAX_ATOM;
     out->variant = FIRE_VARIANT_FIRE2;
-    out->confirm64 = FIRE_FP64_CHECK_CONFIRM;
+    out->confirm64 = FIRE_FP64_CHECK_FINISH;
     out->dmax = 0.0;
     return FIRE_OK;
 }

@@ -303,6 +303,9 @@ struct FireScal {
     double lf_c;                 // v(-dt/2) = lf_c F (Leapfrog initialisation)
     double dt_cur;               // drift x += dt_cur v
     double mix_a, mix_fv_pre, mix_fv_post;   // mixing coefficients
+    // kick and mixing of the kicked velocity as one step (Algs. 4-6 when
+    // P > 0): v <- (1 - a) (v + c F) + a fv F = post_v v + post_f F
+    double post_v, post_f;
 };
 
 __host__ __device__ inline void fire_scal_init(const FireParamsD& p, FireScal& s) {
@@ -313,6 +316,7 @@ __host__ __device__ inline void fire_scal_init(const FireParamsD& p, FireScal& s
     s.zero_v = s.premix = s.postmix = s.lf_init = s.vv = s.pad0 = s.pad1 = 0;
     s.dtm = s.halfstep = s.kick_pre = s.kick_after = s.vv_half = s.lf_c = s.dt_cur = 0.0;
     s.mix_a = s.mix_fv_pre = s.mix_fv_post = 0.0;
+    s.post_v = s.post_f = 0.0;
 }
 
 // Called after every force evaluation with the FP64 reductions of the
@@ -418,6 +422,8 @@ __device__ inline bool fire_control_step(const FireParamsD& p, FireScal& s, doub
             const double c = s.kick_pre;
             s.postmix = 1;
             s.mix_fv_post = sqrt(fmax(V2 + 2.0 * c * P + c * c * F2, 0.0)) / fnorm;
+            s.post_v = 1.0 - s.alpha;
+            s.post_f = s.post_v * c + s.alpha * s.mix_fv_post;
         }
     }
     return false;
@@ -446,14 +452,17 @@ __device__ __forceinline__ void fire_update_pre(const FireScal& s, dvec4& x, dve
         v.y = (1.0 - a) * v.y + afv * f.y;
         v.z = (1.0 - a) * v.z + afv * f.z;
     }
-    v.x += s.kick_pre * f.x;
-    v.y += s.kick_pre * f.y;
-    v.z += s.kick_pre * f.z;
     if (s.postmix) {
-        const double a = s.mix_a, afv = s.mix_a * s.mix_fv_post;
-        v.x = (1.0 - a) * v.x + afv * f.x;
-        v.y = (1.0 - a) * v.y + afv * f.y;
-        v.z = (1.0 - a) * v.z + afv * f.z;
+        // the kick and the mixing of the kicked velocity together: one FP64
+        // multiply and one multiply-add per component in place of three
+        // (FP64 issues at 1/58 of the FP32 rate on this part)
+        v.x = fma(s.post_f, f.x, s.post_v * v.x);
+        v.y = fma(s.post_f, f.y, s.post_v * v.y);
+        v.z = fma(s.post_f, f.z, s.post_v * v.z);
+    } else {
+        v.x += s.kick_pre * f.x;
+        v.y += s.kick_pre * f.y;
+        v.z += s.kick_pre * f.z;
     }
 }
 

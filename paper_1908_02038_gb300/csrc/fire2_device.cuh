@@ -6,15 +6,17 @@
 //   [k_update_pre, with a maximum displacement per step] -> k_update
 //     -> [k_cell_zero/count/scan/fill/sort -> k_nbr_build, only when an atom
 //         moved > skin/2: a graph IF node set by k_update's last block]
-//     -> FP64:  k_density(_tab) -> k_embed -> k_force_rgl -> k_reduce
-//        FP32-pair: k_density32(_tab) -> k_force32(_tab) -> k_reduce
-//        LJ:    k_force_lj -> k_reduce
-//     -> k_control
+//     -> FP64:  k_density_ff(1) -> k_embed -> k_force_ff (tables; k_density /
+//               k_force_rgl with exponentials; k_*_tile on shared-memory tiles)
+//        FP32-pair: k_density32(_tab) -> k_force32(_tab)
+//        LJ:    k_force_lj
+//     -> k_reduce_ctl
 //
-// k_control finishes the FP64 reductions of P = F.v, |F|^2, |v|^2 and the
-// stopping norms (Sec. 3.4), runs the scalar dt / alpha / counter logic of
-// Algorithm 2 for the next iteration, and sets the CUDA-graph WHILE
-// condition, so the whole relaxation runs on the device without host syncs.
+// k_reduce_ctl forms the FP64 reductions of P = F.v, |F|^2, |v|^2 and the
+// stopping norms (Sec. 3.4); its last block adds them up, runs the scalar
+// dt / alpha / counter logic of Algorithm 2 for the next iteration and sets
+// the CUDA-graph WHILE condition, so the whole relaxation runs on the device
+// without host syncs.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -82,7 +84,6 @@ struct DevState {
     // the FP32 norm at the configuration being confirmed
     int vstate, vcount, vmode;
     double ftol_user, fn32, fsw;
-    int tile_over;         // tile builds whose stage overflowed (pairs then use global atomics)
     unsigned int red_blocks;   // k_reduce_ctl blocks finished (last-block test)
 };
 
@@ -682,7 +683,7 @@ __global__ void __launch_bounds__(kForceBlock) k_force_lj(Bufs b, PotC P, GeoC g
             const double r2 = dx * dx + dy * dy + dz * dz;
             if (!(r2 < P.rc2)) continue;
             // one correctly rounded reciprocal in place of two FP64 divisions
-            // (each a long FP64 sequence on a part where FP64 issues at 1/64
+            // (each a long FP64 sequence on a part where FP64 issues at 1/58
             // of the FP32 rate)
             const double ir2 = __drcp_rn(r2);
             const double sr2 = P.sigma2 * ir2;
@@ -751,8 +752,8 @@ __device__ __forceinline__ long long pair_sep_q(const Bufs& b, const int3* qt, i
 }
 
 // ---------------------------------------------------------------------------
-// Per-atom part of the FP64 reductions of (F, v) (see k_reduce), shared by
-// k_reduce and the force kernels that write whole forces.
+// Per-atom part of the FP64 reductions of (F, v) (see k_reduce_ctl), shared
+// by k_reduce_ctl and the NEB projection.
 
 struct RedAcc {
     double P = 0.0, F2 = 0.0, V2 = 0.0, fa2 = 0.0, fin = 0.0;
@@ -798,19 +799,43 @@ __device__ __forceinline__ void red_atom(const Bufs& b, int i, const dvec4& f, d
     a.fin = max_nonneg(a.fin, max_nonneg(abs_bits(f.x), max_nonneg(abs_bits(f.y), abs_bits(f.z))));
 }
 
-__device__ __forceinline__ void red_write(const RedAcc& a, double* red, double* rpart) {
+// The block's five reductions of (F, v) written to the partials: sums of P,
+// |F|^2 and |v|^2, maxima of |F_i|^2 and |F_i,d|.  All five in one sweep
+// (their shuffles interleave; two barriers in all), each in the order of a
+// block_sum / block_max of its own.  sh holds 5 x 32 doubles.
+__device__ __forceinline__ void red_write(const RedAcc& a, double* sh, double* rpart) {
     const int nb = gridDim.x;
-    double r;
-    r = block_sum(a.P, red);
-    if (threadIdx.x == 0) rpart[0 * nb + blockIdx.x] = r;
-    r = block_sum(a.F2, red);
-    if (threadIdx.x == 0) rpart[1 * nb + blockIdx.x] = r;
-    r = block_sum(a.V2, red);
-    if (threadIdx.x == 0) rpart[2 * nb + blockIdx.x] = r;
-    r = block_max(a.fa2, red);
-    if (threadIdx.x == 0) rpart[3 * nb + blockIdx.x] = r;
-    r = block_max(a.fin, red);
-    if (threadIdx.x == 0) rpart[4 * nb + blockIdx.x] = r;
+    double q[5] = {a.P, a.F2, a.V2, a.fa2, a.fin};
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            const double t = __shfl_down_sync(0xffffffffu, q[k], o);
+            q[k] = k < 3 ? q[k] + t : fmax(q[k], t);
+        }
+    }
+    __syncthreads();   // sh may hold an earlier use
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < 5; ++k) sh[k * 32 + w] = q[k];
+    __syncthreads();
+    if (w == 0) {
+        const bool in = lane < (int)(blockDim.x >> 5);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) q[k] = in ? sh[k * 32 + lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+            for (int k = 0; k < 5; ++k) {
+                const double t = __shfl_down_sync(0xffffffffu, q[k], o);
+                q[k] = k < 3 ? q[k] + t : fmax(q[k], t);
+            }
+        }
+        if (lane == 0)
+#pragma unroll
+            for (int k = 0; k < 5; ++k) rpart[k * nb + blockIdx.x] = q[k];
+    }
 }
 
 __device__ __forceinline__ double vv_half_of(const DevState* st) {
@@ -1095,7 +1120,7 @@ __global__ void __launch_bounds__(kForceBlock) k_force_ff(Bufs b, PotC P, GeoC g
     const double sy = group_sum<TPA>(ff_to_f64(fy));
     const double sz = group_sum<TPA>(ff_to_f64(fz));
     if (lane != 0) return;
-    if (HALF) {   // k_reduce applies the frozen-DOF mask
+    if (HALF) {   // k_reduce_ctl applies the frozen-DOF mask
         atomicAdd(&b.f[i].x, sx);
         atomicAdd(&b.f[i].y, sy);
         atomicAdd(&b.f[i].z, sz);
@@ -1198,19 +1223,8 @@ __global__ void __launch_bounds__(kTabBlock) k_force32_tab(Bufs b, PotC P, GeoC 
 // ---------------------------------------------------------------------------
 // FP64 reductions of the current (F, v): P = F.v, |F|^2, |v|^2 (Alg. 2 and
 // the mixing of Algs. 3-6) and the per-atom / per-component force maxima
-// (Sec. 3.4); for velocity Verlet first the second half kick (Alg. 6).
-__global__ void k_reduce(Bufs b) {
-    __shared__ double red[32];
-    if (b.st->done) return;
-    const double vvh = vv_half_of(b.st);
-    RedAcc acc;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < b.n; i += gridDim.x * blockDim.x) {
-        dvec4 f = b.f[i];
-        if (mask_force(b, i, f)) b.f[i] = f;
-        red_atom(b, i, f, b.v[i], vvh, acc);
-    }
-    red_write(acc, red, b.rpart);
-}
+// (Sec. 3.4); for velocity Verlet first the second half kick (Alg. 6).  They
+// run in k_reduce_ctl (below), whose last block also runs the control step.
 
 // Fixed-order final reductions of the partials by one block (deterministic):
 // the sums of P, |F|^2, |v|^2 and E and the maxima of |F_i|^2 and |F_i,d|,
@@ -1354,12 +1368,11 @@ __global__ void k_control(Bufs b, int mode, cudaGraphConditionalHandle h, int ha
     control_body(b, mode, h, has_handle, sh);
 }
 
-// The reductions of k_reduce and the control step of k_control in one
+// The reductions of (F, v) and the control step of k_control in one
 // launch (nb_red blocks): every block writes its partials, and the last
 // block to finish (a ticket counter, reset by that block) runs the control
 // step on all of them.  No block waits for another.
 __global__ void k_reduce_ctl(Bufs b, int mode, cudaGraphConditionalHandle h, int has_handle) {
-    __shared__ double red[32];
     __shared__ double sh[6 * 32];
     __shared__ int last;
     if (b.st->done) {   // chunked loop bodies past the stop
@@ -1374,7 +1387,7 @@ __global__ void k_reduce_ctl(Bufs b, int mode, cudaGraphConditionalHandle h, int
         if (mask_force(b, i, f)) b.f[i] = f;
         red_atom(b, i, f, b.v[i], vvh, acc);
     }
-    red_write(acc, red, b.rpart);
+    red_write(acc, sh, b.rpart);
     if (threadIdx.x == 0) {
         __threadfence();   // this block's partials before its ticket
         last = atomicAdd(&b.st->red_blocks, 1u) == gridDim.x - 1 ? 1 : 0;

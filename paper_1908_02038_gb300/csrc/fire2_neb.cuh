@@ -175,7 +175,7 @@ __global__ void k_neb_scalars(Bufs b, NebC c) {
 // grid-stride over all n_img x img_n atoms: F^NEB = mask(F + s t) written
 // over F, then the (F^NEB, v) reductions (with the velocity-Verlet half kick)
 __global__ void __launch_bounds__(kNebBlock) k_neb_project(Bufs b, GeoC g, NebC c) {
-    __shared__ double red[32];
+    __shared__ double red[5 * 32];
     if (b.st->done) return;
     const double vvh = vv_half_of(b.st);
     RedAcc acc;

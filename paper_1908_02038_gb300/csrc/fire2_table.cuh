@@ -394,7 +394,7 @@ __host__ __device__ __forceinline__ ffloat f64_to_ff(double d) {
 // 1/y^2 - rho, y1 = y0 + y0 (1 - rho y0^2) / 2, with 1 - rho y0^2 formed in
 // float pairs; y1 is then off by 1.5 e0^2 ~ 1e-13 (relative, from below),
 // the precision of the pair terms.  FP32 and integer instructions only (FP64
-// issues at 1/64 of the FP32 rate on this part).  Valid for rho in the
+// issues at 1/58 of the FP32 rate on this part).  Valid for rho in the
 // normal FP32 range; the caller takes the FP64 routine outside it.
 __device__ __forceinline__ void rgl_embed_ff(ffloat r, ffloat& sq, ffloat& fp) {
     const float y0 = rsqrtf(r.hi);

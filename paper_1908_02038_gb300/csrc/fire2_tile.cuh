@@ -5,7 +5,7 @@
 // takes part in; likewise rho_j).  Sending each j-side term to global memory
 // by an FP64 atomic costs, per pair, one FP64 addition (hi + lo of the
 // double-float term) per component and one L2 atomic per component; on this
-// part the FP64 pipe runs at 1/64 of the FP32 rate, and those additions and
+// part the FP64 pipe runs at 1/58 of the FP32 rate, and those additions and
 // atomics dominated the force pass.
 //
 // Here the atoms are processed in tiles: a tile is one brick of list cells
@@ -172,13 +172,13 @@ __device__ __forceinline__ int block_exscan(int v, int* ws, int* total) {
 
 // One block per tile (grid-stride): the stage of the tile and the slots of
 // its own atoms' list entries.  Slots: own atoms 0 .. nown - 1 (cell-sorted
-// order), then the other keys in hash-table order (deterministic for a
-// given list); at most stage_cap of them, the rest kSlotNone.
+// order), then the other keys in hash-table order (which depends on the
+// order of the concurrent insertions; the sums do not, being exact integer
+// sums); at most stage_cap of them, the rest kSlotNone.
 __global__ void __launch_bounds__(kTileThreads) k_tile_build(Bufs b, GeoC g, int force) {
     __shared__ uint32_t keys[kTileHash];
     __shared__ uint16_t slot_of[kTileHash];
     __shared__ int ws[kTileThreads / 32];
-    __shared__ int fail;
     if (!need_rebuild(b.st, g, force)) return;
     const int cap = g.stage_cap;
     for (int T = blockIdx.x; T < g.ntile; T += gridDim.x) {
@@ -189,7 +189,6 @@ __global__ void __launch_bounds__(kTileThreads) k_tile_build(Bufs b, GeoC g, int
             keys[h] = kKeyEmpty;
             slot_of[h] = kSlotNone;
         }
-        if (threadIdx.x == 0) fail = 0;
         __syncthreads();
         uint32_t* tkey = b.tile_key + (size_t)T * kStageMax;
         for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
@@ -197,17 +196,15 @@ __global__ void __launch_bounds__(kTileThreads) k_tile_build(Bufs b, GeoC g, int
             const int h = tile_insert(keys, key);
             const int so = p - p0;
             if (so < cap) tkey[so] = key;   // own slots are positional
-            if (h < 0)
-                fail = 1;   // lookups of this atom then miss: global path
-            else
-                slot_of[h] = so < cap ? (uint16_t)so : kSlotOwnOver;
+            // a full table (h < 0) leaves the atom out: lookups of it miss and
+            // its pairs take the global path
+            if (h >= 0) slot_of[h] = so < cap ? (uint16_t)so : kSlotOwnOver;
         }
         __syncthreads();
         for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
             const int i = b.cell_atoms[p];
             const int m = b.nnbr[i];
-            for (int k = 0; k < m; ++k)
-                if (tile_insert(keys, b.nbr[(size_t)k * b.n + i]) < 0) fail = 1;
+            for (int k = 0; k < m; ++k) tile_insert(keys, b.nbr[(size_t)k * b.n + i]);
         }
         __syncthreads();
         constexpr int kPer = (kTileHash + kTileThreads - 1) / kTileThreads;
@@ -230,10 +227,7 @@ __global__ void __launch_bounds__(kTileThreads) k_tile_build(Bufs b, GeoC g, int
                 ++s;
             }
         }
-        if (threadIdx.x == 0) {
-            b.tile_ns[T] = min(cap, min(nown, cap) + nhalo);
-            if (nown + nhalo > cap || fail) atomicAdd(&b.st->tile_over, 1);
-        }
+        if (threadIdx.x == 0) b.tile_ns[T] = min(cap, min(nown, cap) + nhalo);
         __syncthreads();
         for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
             const int i = b.cell_atoms[p];
@@ -393,7 +387,7 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) k_density_tile(B
 
 // Pass 2 on tiles: F_i = sum_j [2 phi'/r + (F'_i + F'_j) g'/r] (x_j - x_i),
 // the j-side terms accumulated per staged atom and flushed (F = -grad E,
-// Sec. 2.1).  k_reduce applies the frozen-DOF mask afterwards.
+// Sec. 2.1).  k_reduce_ctl applies the frozen-DOF mask afterwards.
 __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) k_force_tile(Bufs b, PotC P, GeoC g) {
     extern __shared__ __align__(16) unsigned char smem[];
     long long* sx = reinterpret_cast<long long*>(smem);

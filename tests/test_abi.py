@@ -44,7 +44,7 @@ def test_abi_version_and_defaults(lib):
         (10.0, 0.02, 1.1, 0.5, 0.25, 0.99)
     assert (p.delaystep, p.vdfmax, p.halfstepback, p.initialdelay, p.integrator, p.norm) == \
         (20, 2000, 1, 1, 0, 0)
-    assert p.confirm64 == fg.FIRE_FP64_CHECK_CONFIRM
+    assert p.confirm64 == fg.FIRE_FP64_CHECK_FINISH
     with pytest.raises(fg.FireError) as e:
         fg.fire_default_params(0.0)
     assert e.value.status == fg.FIRE_ERR_ARG

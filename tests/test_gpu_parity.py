@@ -371,13 +371,13 @@ def test_fp32pair_1m_sampled_forces_vs_oracle():
 
 
 def test_fp32pair_relaxation_reaches_fp64_converged_state():
-    # default: a stop on the FP32-pair forces is confirmed by one FP64
-    # evaluation at the same positions, so the result meets ftol in FP64
+    # FIRE_FP64_CHECK_CONFIRM: a stop on the FP32-pair forces is confirmed by
+    # one FP64 evaluation at the same positions, so the result meets ftol in FP64
     c = fi.rgl_vacancy_box(ncell=20, seed=2)
     x64, x32 = c.x.copy(), c.x.copy()
     with fg.FireHandle(c.n, fi.CU_MASS, rgl_pot(), dt_start=fi.CU_DT) as h64, \
             fg.FireHandle(c.n, fi.CU_MASS, rgl_pot(precision=fg.FIRE_PREC_FP32_PAIR),
-                          dt_start=fi.CU_DT) as h32:
+                          dt_start=fi.CU_DT, confirm64=fg.FIRE_FP64_CHECK_CONFIRM) as h32:
         r64 = h64.minimize(x64, c.box, 1e-6, 100000)
         r32 = h32.minimize(x32, c.box, 1e-6, 100000)
         # the FP32 solution judged by FP64 forces
