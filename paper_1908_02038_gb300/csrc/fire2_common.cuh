@@ -27,6 +27,8 @@ constexpr int kTabBlock = 256;    // FP32 table kernels (more warps per shared t
 constexpr int kTabBlock64 = 512;  // FP64 table kernel (both tables, ~112 KB, in shared memory)
 constexpr int kElemBlock = 256;
 constexpr int kCtlThreads = 512;
+constexpr int kRedRows = 6;   // rows of the per-block partials: P, |F|^2, |v|^2, max |F_i|^2,
+                              // max |F_i,d|, energy (red_write)
 
 enum { ST_OK = 0, ST_NONFINITE = 4, ST_NBR_OVERFLOW = 5, ST_TIMEOUT = 6, ST_RANGE = 8,
        ST_CROWDED = 9 };

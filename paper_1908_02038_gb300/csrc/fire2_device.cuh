@@ -97,8 +97,10 @@ struct Bufs {
     double* eatom;         // per-atom energy (images' energies), or NULL
     int accum;             // 1: forces and densities accumulate with atomics (cleared
                            //    by k_update); 0: force kernels write them whole
-    dvec4 *x, *v, *f, *xref;
-    float4* xf;            // FP32 copy of x for the list build
+    dvec4 *x, *v;
+    double* f;             // forces, component-major: F_x,i at f[i], F_y,i at f[n + i],
+                           // F_z,i at f[2 n + i] (f_load / f_store / f_add below)
+    float4* xf;            // FP32 copy of x at the last list build
     int4* xq;              // FP32-pair form: x in fixed point (qscale units), modulo 2^32
     float* fp32;           // FP32-pair form: F'(rho_i)
     const float* exp32_table;
@@ -130,6 +132,25 @@ struct Bufs {
     double* f_out;         // N x 3 row-major forces (evaluation only)
     double* e_out;         // energy (evaluation only)
 };
+
+// Forces are stored component-major (three arrays of n doubles): the three
+// atomics of a pair term then go to three different 32-byte sectors, which
+// the L2 serves in parallel.  With the three components of an atom in one
+// sector its atomics queue behind each other: on the 1M-atom box the
+// double-float force pass took 0.473 ms that way against 0.423 ms.
+__device__ __forceinline__ dvec4 f_load(const Bufs& b, int i) {
+    return make_dvec4(b.f[i], b.f[b.n + i], b.f[2 * b.n + i], 0.0);   // 3 n < 2^27
+}
+__device__ __forceinline__ void f_store(const Bufs& b, int i, double x, double y, double z) {
+    b.f[i] = x;
+    b.f[b.n + i] = y;
+    b.f[2 * b.n + i] = z;
+}
+__device__ __forceinline__ void f_add(const Bufs& b, int i, double x, double y, double z) {
+    atomicAdd(b.f + i, x);
+    atomicAdd(b.f + b.n + i, y);
+    atomicAdd(b.f + 2 * b.n + i, z);
+}
 
 // Whether a force pass sits this evaluation out (pass_role above; the state
 // says whether the evaluation confirms an FP32-pair stop in FP64).
@@ -182,7 +203,7 @@ __global__ void k_prepare(Bufs b) {
         b.xq64[i] = {to_fixed64(p[0], kFixedBits64), to_fixed64(p[1], kFixedBits64),
                      to_fixed64(p[2], kFixedBits64), 0ll};
     b.v[i] = make_dvec4(0.0, 0.0, 0.0, 0.0);
-    b.f[i] = make_dvec4(0.0, 0.0, 0.0, 0.0);
+    f_store(b, i, 0.0, 0.0, 0.0);
     if (b.rho) b.rho[i] = 0.0;
 }
 
@@ -200,7 +221,7 @@ __global__ void k_export_forces(Bufs b) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0 && b.e_out) *b.e_out = b.st->energy;
     if (i >= b.n || !b.f_out) return;
-    const dvec4 f = b.f[i];
+    const dvec4 f = f_load(b, i);
     double* p = b.f_out + 3 * (size_t)i;
     p[0] = f.x;
     p[1] = f.y;
@@ -386,7 +407,9 @@ __global__ void k_nbr_build(Bufs b, GeoC g, int force) {
         cnt = b.cap;
     }
     b.nnbr[i] = cnt;
-    b.xref[i] = xi;
+    // the FP32 copy of x at this build, for the displacement test of k_update
+    // (with cell lists k_cell_count wrote it already)
+    if (g.brute) b.xf[i] = make_float4((float)xi.x, (float)xi.y, (float)xi.z, 0.f);
 }
 
 // ---------------------------------------------------------------------------
@@ -459,22 +482,32 @@ __global__ void k_embed(Bufs b) {
     __shared__ double red[32];
     if (b.st->done) return;
     double emb = 0.0;
+    ffloat emb_ff = {0.f, 0.f};
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < b.n; i += gridDim.x * blockDim.x) {
         const double rho = b.rho[i];
-        double sq, fp;
-        if (b.fpff) {
+        if (b.fpff && rho > 1e-30 && rho < 1e30) {
             // FP64 form with double-float pair terms: the embedding in float
-            // pairs too, F' as a float pair for the force pass
-            ffloat fpf;
-            rgl_embed_dd(rho, sq, fp, fpf);
+            // pairs too, F' as a float pair for the force pass (the only
+            // reader of F' in this form) and the energy summed in float pairs
+            ffloat sqf, fpf;
+            rgl_embed_ff(f64_to_ff(rho), sqf, fpf);
+            b.fpff[i] = make_float2(fpf.hi, fpf.lo);
+            emb_ff = ff_acc(emb_ff, {-sqf.hi, -sqf.lo});
+            if (b.eatom) b.eatom[i] -= ff_to_f64(sqf);
+            continue;
+        }
+        double sq, fp;
+        rgl_embed(rho, sq, fp);
+        if (b.fpff) {
+            const ffloat fpf = f64_to_ff(fp);
             b.fpff[i] = make_float2(fpf.hi, fpf.lo);
         } else {
-            rgl_embed(rho, sq, fp);
+            b.fp[i] = fp;
         }
-        b.fp[i] = fp;
         emb -= sq;
         if (b.eatom) b.eatom[i] -= sq;
     }
+    emb += ff_to_f64(emb_ff);
     const double s = block_sum(emb, red);
     if (threadIdx.x == 0) b.epart[b.ne_dens + blockIdx.x] = s;
 }
@@ -512,13 +545,9 @@ __global__ void __launch_bounds__(kForceBlock) k_force_rgl(Bufs b, GeoC g) {
         fx += fs * dx;
         fy += fs * dy;
         fz += fs * dz;
-        atomicAdd(&b.f[j].x, -fs * dx);
-        atomicAdd(&b.f[j].y, -fs * dy);
-        atomicAdd(&b.f[j].z, -fs * dz);
+        f_add(b, j, -fs * dx, -fs * dy, -fs * dz);
     }
-    atomicAdd(&b.f[i].x, fx);
-    atomicAdd(&b.f[i].y, fy);
-    atomicAdd(&b.f[i].z, fz);
+    f_add(b, i, fx, fy, fz);
 }
 
 // Stillinger-Weber, one pass over the full list (IEEE FP64): the pair term
@@ -634,16 +663,10 @@ __global__ void __launch_bounds__(kForceBlock) k_force_sw(Bufs b, PotC P, GeoC g
                 fx += gjx + gkx;
                 fy += gjy + gky;
                 fz += gjz + gkz;
-                atomicAdd(&b.f[nj[p]].x, -gjx);
-                atomicAdd(&b.f[nj[p]].y, -gjy);
-                atomicAdd(&b.f[nj[p]].z, -gjz);
-                atomicAdd(&b.f[nj[q]].x, -gkx);
-                atomicAdd(&b.f[nj[q]].y, -gky);
-                atomicAdd(&b.f[nj[q]].z, -gkz);
+                f_add(b, nj[p], -gjx, -gjy, -gjz);
+                f_add(b, nj[q], -gkx, -gky, -gkz);
             }
-        atomicAdd(&b.f[i].x, fx);
-        atomicAdd(&b.f[i].y, fy);
-        atomicAdd(&b.f[i].z, fz);
+        f_add(b, i, fx, fy, fz);
         if (b.eatom) b.eatom[i] = e_i;
     }
     const double bs = block_sum(e_i, red);
@@ -693,18 +716,14 @@ __global__ void __launch_bounds__(kForceBlock) k_force_lj(Bufs b, PotC P, GeoC g
             fx -= w * dx;
             fy -= w * dy;
             fz -= w * dz;
-            atomicAdd(&b.f[j].x, w * dx);
-            atomicAdd(&b.f[j].y, w * dy);
-            atomicAdd(&b.f[j].z, w * dz);
+            f_add(b, j, w * dx, w * dy, w * dz);
         }
         fx = group_sum<TPA>(fx);
         fy = group_sum<TPA>(fy);
         fz = group_sum<TPA>(fz);
         const double ep = group_sum<TPA>(epair);
         if (lane == 0) {
-            atomicAdd(&b.f[i].x, fx);
-            atomicAdd(&b.f[i].y, fy);
-            atomicAdd(&b.f[i].z, fz);
+            f_add(b, i, fx, fy, fz);
             if (b.eatom) b.eatom[i] = ep;
         }
     }
@@ -757,6 +776,7 @@ __device__ __forceinline__ long long pair_sep_q(const Bufs& b, const int3* qt, i
 
 struct RedAcc {
     double P = 0.0, F2 = 0.0, V2 = 0.0, fa2 = 0.0, fin = 0.0;
+    double E = 0.0;   // the block's slice of the energy partials (k_reduce_ctl)
 };
 
 // max(a, b) of non-negative doubles (NaN propagates: its pattern is larger
@@ -799,42 +819,43 @@ __device__ __forceinline__ void red_atom(const Bufs& b, int i, const dvec4& f, d
     a.fin = max_nonneg(a.fin, max_nonneg(abs_bits(f.x), max_nonneg(abs_bits(f.y), abs_bits(f.z))));
 }
 
-// The block's five reductions of (F, v) written to the partials: sums of P,
-// |F|^2 and |v|^2, maxima of |F_i|^2 and |F_i,d|.  All five in one sweep
-// (their shuffles interleave; two barriers in all), each in the order of a
-// block_sum / block_max of its own.  sh holds 5 x 32 doubles.
+// The block's six reductions written to the partials (kRedRows rows of
+// gridDim.x): sums of P, |F|^2 and |v|^2, maxima of |F_i|^2 and |F_i,d|, and
+// the sum of the block's energy terms.  All six in one sweep (their shuffles
+// interleave; two barriers in all), each in the order of a block_sum /
+// block_max of its own.  sh holds kRedRows x 32 doubles.
 __device__ __forceinline__ void red_write(const RedAcc& a, double* sh, double* rpart) {
     const int nb = gridDim.x;
-    double q[5] = {a.P, a.F2, a.V2, a.fa2, a.fin};
+    double q[kRedRows] = {a.P, a.F2, a.V2, a.fa2, a.fin, a.E};
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
-        for (int k = 0; k < 5; ++k) {
+        for (int k = 0; k < kRedRows; ++k) {
             const double t = __shfl_down_sync(0xffffffffu, q[k], o);
-            q[k] = k < 3 ? q[k] + t : fmax(q[k], t);
+            q[k] = (k == 3 || k == 4) ? fmax(q[k], t) : q[k] + t;
         }
     }
     __syncthreads();   // sh may hold an earlier use
     if (lane == 0)
 #pragma unroll
-        for (int k = 0; k < 5; ++k) sh[k * 32 + w] = q[k];
+        for (int k = 0; k < kRedRows; ++k) sh[k * 32 + w] = q[k];
     __syncthreads();
     if (w == 0) {
         const bool in = lane < (int)(blockDim.x >> 5);
 #pragma unroll
-        for (int k = 0; k < 5; ++k) q[k] = in ? sh[k * 32 + lane] : 0.0;
+        for (int k = 0; k < kRedRows; ++k) q[k] = in ? sh[k * 32 + lane] : 0.0;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
-            for (int k = 0; k < 5; ++k) {
+            for (int k = 0; k < kRedRows; ++k) {
                 const double t = __shfl_down_sync(0xffffffffu, q[k], o);
-                q[k] = k < 3 ? q[k] + t : fmax(q[k], t);
+                q[k] = (k == 3 || k == 4) ? fmax(q[k], t) : q[k] + t;
             }
         }
         if (lane == 0)
 #pragma unroll
-            for (int k = 0; k < 5; ++k) rpart[k * nb + blockIdx.x] = q[k];
+            for (int k = 0; k < kRedRows; ++k) rpart[k * nb + blockIdx.x] = q[k];
     }
 }
 
@@ -921,7 +942,7 @@ __global__ void __launch_bounds__(kForceBlock) k_force32(Bufs b, PotC P, GeoC g)
         if (lane != 0) continue;
         dvec4 f = make_dvec4(sx, sy, sz, 0.0);
         mask_force(b, i, f);
-        b.f[i] = f;
+        f_store(b, i, f.x, f.y, f.z);
     }
 }
 
@@ -1058,9 +1079,10 @@ __global__ void __launch_bounds__(kForceBlock, 12) k_density_ff1(Bufs b, PotC P,
 
 // Pass 2: F_i = sum_j [2 phi'/r + (F'_i + F'_j) g'/r] (x_j - x_i) (F = -grad E,
 // Sec. 2.1); full list: written whole; half list: F_i and F_j by FP64 atomics.
-// TPA threads per atom as in k_density_ff.
-template <bool HALF, int TPA = 1>
-__global__ void __launch_bounds__(kForceBlock) k_force_ff(Bufs b, PotC P, GeoC g) {
+// TPA threads per atom as in k_density_ff; blocks of BLK threads (the pass
+// writes no per-block partials, so its grid is free: force_ff picks it).
+template <bool HALF, int TPA, int BLK>
+__global__ void __launch_bounds__(BLK) k_force_ff(Bufs b, PotC P, GeoC g) {
     __shared__ long long qt[375];
     __shared__ double etab[kExpTableSize];
     if (pass_skipped(b)) return;
@@ -1111,9 +1133,7 @@ __global__ void __launch_bounds__(kForceBlock) k_force_ff(Bufs b, PotC P, GeoC g
         fy = ff_acc(fy, ty);
         fz = ff_acc(fz, tz);
         if (HALF) {
-            atomicAdd(&b.f[j].x, -ff_to_f64(tx));
-            atomicAdd(&b.f[j].y, -ff_to_f64(ty));
-            atomicAdd(&b.f[j].z, -ff_to_f64(tz));
+            f_add(b, j, -ff_to_f64(tx), -ff_to_f64(ty), -ff_to_f64(tz));
         }
     }
     const double sx = group_sum<TPA>(ff_to_f64(fx));
@@ -1121,13 +1141,11 @@ __global__ void __launch_bounds__(kForceBlock) k_force_ff(Bufs b, PotC P, GeoC g
     const double sz = group_sum<TPA>(ff_to_f64(fz));
     if (lane != 0) return;
     if (HALF) {   // k_reduce_ctl applies the frozen-DOF mask
-        atomicAdd(&b.f[i].x, sx);
-        atomicAdd(&b.f[i].y, sy);
-        atomicAdd(&b.f[i].z, sz);
+        f_add(b, i, sx, sy, sz);
     } else {
         dvec4 f = make_dvec4(sx, sy, sz, 0.0);
         mask_force(b, i, f);
-        b.f[i] = f;
+        f_store(b, i, f.x, f.y, f.z);
     }
 }
 
@@ -1216,7 +1234,7 @@ __global__ void __launch_bounds__(kTabBlock) k_force32_tab(Bufs b, PotC P, GeoC 
         }
         dvec4 f = make_dvec4(fx.value(), fy.value(), fz.value(), 0.0);
         mask_force(b, i, f);
-        b.f[i] = f;
+        f_store(b, i, f.x, f.y, f.z);
     }
 }
 
@@ -1230,14 +1248,16 @@ __global__ void __launch_bounds__(kTabBlock) k_force32_tab(Bufs b, PotC P, GeoC 
 // the sums of P, |F|^2, |v|^2 and E and the maxima of |F_i|^2 and |F_i,d|,
 // all six in one sweep so that their loads are in flight together.  Each
 // quantity is added up in the order of a block_sum / block_max of its own.
+// The energy is the sum of the partials' energy row plus, when ne > 0, the
+// first ne energy partials of the passes (epart; the NEB chain leaves its
+// energy there, k_reduce_ctl has already folded it into the rows).
 struct CtlSums {
     double P, F2, V2, fa2, fin, E;
 };
 __device__ __forceinline__ CtlSums ctl_reduce(const Bufs& b, int ne, double* sh /* 6 x 32 */) {
-    double a[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    double a[kRedRows] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     const int nr = b.nb_red;
-    // unrolled so that a thread's loads are in flight together (the sums
-    // keep their order; one partial per density block, ~7,800 at 1M atoms)
+    // unrolled so that a thread's loads are in flight together
 #pragma unroll 4
     for (int k = threadIdx.x; k < nr; k += blockDim.x) {
         a[0] += b.rpart[k];
@@ -1245,8 +1265,9 @@ __device__ __forceinline__ CtlSums ctl_reduce(const Bufs& b, int ne, double* sh 
         a[2] += b.rpart[2 * nr + k];
         a[3] = fmax(a[3], b.rpart[3 * nr + k]);
         a[4] = fmax(a[4], b.rpart[4 * nr + k]);
+        a[5] += b.rpart[5 * nr + k];
     }
-    {   // four independent sums per thread, so that its loads overlap
+    if (ne > 0) {   // four independent sums per thread, so that its loads overlap
         const int bd = blockDim.x;
         double e0 = 0.0, e1 = 0.0, e2 = 0.0, e3 = 0.0;
         int k = threadIdx.x;
@@ -1257,28 +1278,28 @@ __device__ __forceinline__ CtlSums ctl_reduce(const Bufs& b, int ne, double* sh 
             e3 += b.epart[k + 3 * bd];
         }
         for (; k < ne; k += bd) e0 += b.epart[k];
-        a[5] = (e0 + e1) + (e2 + e3);
+        a[5] += (e0 + e1) + (e2 + e3);
     }
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
-        for (int q = 0; q < 6; ++q) {
+        for (int q = 0; q < kRedRows; ++q) {
             const double t = __shfl_down_sync(0xffffffffu, a[q], o);
             a[q] = (q == 3 || q == 4) ? fmax(a[q], t) : a[q] + t;
         }
     }
     if (lane == 0)
 #pragma unroll
-        for (int q = 0; q < 6; ++q) sh[q * 32 + w] = a[q];
+        for (int q = 0; q < kRedRows; ++q) sh[q * 32 + w] = a[q];
     __syncthreads();
     if (w == 0) {
 #pragma unroll
-        for (int q = 0; q < 6; ++q) a[q] = lane < (int)(blockDim.x >> 5) ? sh[q * 32 + lane] : 0.0;
+        for (int q = 0; q < kRedRows; ++q) a[q] = lane < (int)(blockDim.x >> 5) ? sh[q * 32 + lane] : 0.0;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
-            for (int q = 0; q < 6; ++q) {
+            for (int q = 0; q < kRedRows; ++q) {
                 const double t = __shfl_down_sync(0xffffffffu, a[q], o);
                 a[q] = (q == 3 || q == 4) ? fmax(a[q], t) : a[q] + t;
             }
@@ -1287,14 +1308,20 @@ __device__ __forceinline__ CtlSums ctl_reduce(const Bufs& b, int ne, double* sh 
     return {a[0], a[1], a[2], a[3], a[4], a[5]};   // valid in thread 0
 }
 
+// The number of energy partials the passes of this evaluation wrote: the
+// FP64 confirming passes' while an FP32-pair stop is confirmed, else the
+// density (or only) pass's and the embedding's.
+__device__ __forceinline__ int energy_partials(const Bufs& b) {
+    return b.st->vstate >= 2 ? b.nb_verify : b.ne_dens + b.nb_embed;
+}
+
 // Scalar FIRE 2.0 control (Algorithm 2, fire_control_step), one block: the
 // fixed-order final reductions, the error checks, then the convergence test
 // and the preparation of the next iteration; sets the WHILE condition.
 // The control step proper: every thread of one block enters (the final
 // reductions), thread 0 runs the scalar part.
 __device__ void control_body(const Bufs& b, int mode, cudaGraphConditionalHandle h,
-                             int has_handle, double* sh) {
-    const int ne = b.st->vstate >= 2 ? b.nb_verify : b.ne_dens + b.nb_embed;
+                             int has_handle, double* sh, int ne) {
     const CtlSums r = ctl_reduce(b, ne, sh);
     if (threadIdx.x != 0) return;
     const double P = r.P, F2 = r.F2, V2 = r.V2, fa2 = r.fa2, fin = r.fin, E = r.E;
@@ -1359,13 +1386,13 @@ __device__ void control_body(const Bufs& b, int mode, cudaGraphConditionalHandle
 }
 
 __global__ void k_control(Bufs b, int mode, cudaGraphConditionalHandle h, int has_handle) {
-    __shared__ double sh[6 * 32];
+    __shared__ double sh[kRedRows * 32];
     // chunked execution runs loop bodies past the stop; they must not count
     if (mode == CTL_LOOP && b.st->done) {
         if (has_handle && threadIdx.x == 0) cudaGraphSetConditional(h, 0u);
         return;
     }
-    control_body(b, mode, h, has_handle, sh);
+    control_body(b, mode, h, has_handle, sh, energy_partials(b));
 }
 
 // The reductions of (F, v) and the control step of k_control in one
@@ -1373,7 +1400,7 @@ __global__ void k_control(Bufs b, int mode, cudaGraphConditionalHandle h, int ha
 // block to finish (a ticket counter, reset by that block) runs the control
 // step on all of them.  No block waits for another.
 __global__ void k_reduce_ctl(Bufs b, int mode, cudaGraphConditionalHandle h, int has_handle) {
-    __shared__ double sh[6 * 32];
+    __shared__ double sh[kRedRows * 32];
     __shared__ int last;
     if (b.st->done) {   // chunked loop bodies past the stop
         if (mode == CTL_LOOP && has_handle && blockIdx.x == 0 && threadIdx.x == 0)
@@ -1382,9 +1409,14 @@ __global__ void k_reduce_ctl(Bufs b, int mode, cudaGraphConditionalHandle h, int
     }
     const double vvh = vv_half_of(b.st);
     RedAcc acc;
+    {   // this block's slice of the passes' energy partials, in a fixed order
+        const int ne = energy_partials(b), per = (ne + gridDim.x - 1) / gridDim.x;
+        const int e1 = min(ne, (int)(blockIdx.x + 1) * per);
+        for (int k = blockIdx.x * per + threadIdx.x; k < e1; k += blockDim.x) acc.E += b.epart[k];
+    }
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < b.n; i += gridDim.x * blockDim.x) {
-        dvec4 f = b.f[i];
-        if (mask_force(b, i, f)) b.f[i] = f;
+        dvec4 f = f_load(b, i);
+        if (mask_force(b, i, f)) f_store(b, i, f.x, f.y, f.z);
         red_atom(b, i, f, b.v[i], vvh, acc);
     }
     red_write(acc, sh, b.rpart);
@@ -1396,7 +1428,7 @@ __global__ void k_reduce_ctl(Bufs b, int mode, cudaGraphConditionalHandle h, int
     if (!last) return;
     if (threadIdx.x == 0) b.st->red_blocks = 0u;
     __threadfence();       // every other block's partials are visible from here
-    control_body(b, mode, h, has_handle, sh);
+    control_body(b, mode, h, has_handle, sh, 0);
 }
 
 // Element-wise part of one iteration: optional half step back and v = 0
@@ -1420,13 +1452,14 @@ __device__ void update_body(const Bufs& b, const GeoC& g, const FireScal& s, int
         if (has_if && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(hif, 0u);
         return;
     }
-    // displacement since the last build in FP32 (truncated copies): off by
-    // < 1e-4 A at most, far inside the list build's FP32 margin
+    // displacement since the last build in FP32: x truncated against the
+    // copy rounded at the build, off by < 2 FP32 ulps of the coordinate, far
+    // inside the list radius's margin (1e-3 rc + 8 FP32 ulps of the box)
     float d2max = 0.f;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < b.n; i += gridDim.x * blockDim.x) {
         dvec4 x = b.x[i], v = b.v[i];
-        const dvec4 f = b.f[i];
-        const dvec4 r = b.xref[i];   // loaded with the rest, before the stores
+        const dvec4 f = f_load(b, i);
+        const float4 r = b.xf[i];    // x at the last build; loaded before the stores
         if (after_pre)
             fire_update_drift(s, dt, x, v, f);
         else
@@ -1440,12 +1473,12 @@ __device__ void update_body(const Bufs& b, const GeoC& g, const FireScal& s, int
                          to_fixed64(x.z, kFixedBits64), 0ll};
         b.v[i] = v;
         if (b.accum) {
-            b.f[i] = make_dvec4(0.0, 0.0, 0.0, 0.0);
+            f_store(b, i, 0.0, 0.0, 0.0);
             if (b.rho) b.rho[i] = 0.0;
         }
-        const float ddx = f64_to_f32_trunc(x.x) - f64_to_f32_trunc(r.x);
-        const float ddy = f64_to_f32_trunc(x.y) - f64_to_f32_trunc(r.y);
-        const float ddz = f64_to_f32_trunc(x.z) - f64_to_f32_trunc(r.z);
+        const float ddx = f64_to_f32_trunc(x.x) - r.x;
+        const float ddy = f64_to_f32_trunc(x.y) - r.y;
+        const float ddz = f64_to_f32_trunc(x.z) - r.z;
         d2max = fmaxf(d2max, ddx * ddx + ddy * ddy + ddz * ddz);
     }
     const double bm = block_max(f32_to_f64(d2max), red);
@@ -1486,7 +1519,7 @@ __global__ void k_update_pre(Bufs b) {
     double vm = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < b.n; i += gridDim.x * blockDim.x) {
         dvec4 x = b.x[i], v = b.v[i];
-        fire_update_pre(s, x, v, b.f[i]);
+        fire_update_pre(s, x, v, f_load(b, i));
         if (s.zero_v) b.x[i] = x;      // the half step back moved x
         b.v[i] = v;
         vm = fmax(vm, v.x * v.x + v.y * v.y + v.z * v.z);

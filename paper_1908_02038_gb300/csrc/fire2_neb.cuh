@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(kNebBlock) k_neb_sums(Bufs b, GeoC g, NebC c) 
         neb_neighbours(b, c, img, a, rm, rp);
         double tp[3], tm[3];
         neb_seps(g, r, rm, rp, tp, tm);
-        dvec4 f = b.f[gi];
+        dvec4 f = f_load(b, (int)gi);
         mask_force(b, (int)gi, f);
         const double fv[3] = {f.x, f.y, f.z};
         const unsigned m = neb_mask(b, gi);
@@ -175,7 +175,7 @@ __global__ void k_neb_scalars(Bufs b, NebC c) {
 // grid-stride over all n_img x img_n atoms: F^NEB = mask(F + s t) written
 // over F, then the (F^NEB, v) reductions (with the velocity-Verlet half kick)
 __global__ void __launch_bounds__(kNebBlock) k_neb_project(Bufs b, GeoC g, NebC c) {
-    __shared__ double red[5 * 32];
+    __shared__ double red[kRedRows * 32];
     if (b.st->done) return;
     const double vvh = vv_half_of(b.st);
     RedAcc acc;
@@ -188,12 +188,12 @@ __global__ void __launch_bounds__(kNebBlock) k_neb_project(Bufs b, GeoC g, NebC 
         neb_neighbours(b, c, img, a, rm, rp);
         double tp[3], tm[3];
         neb_seps(g, r, rm, rp, tp, tm);
-        dvec4 f = b.f[gi];
+        dvec4 f = f_load(b, gi);
         f.x += o[2] * (o[0] * tp[0] + o[1] * tm[0]);
         f.y += o[2] * (o[0] * tp[1] + o[1] * tm[1]);
         f.z += o[2] * (o[0] * tp[2] + o[1] * tm[2]);
         mask_force(b, gi, f);
-        b.f[gi] = f;
+        f_store(b, gi, f.x, f.y, f.z);
         red_atom(b, gi, f, b.v[gi], vvh, acc);
     }
     red_write(acc, red, b.rpart);

@@ -484,7 +484,7 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) k_force_tile(Buf
                         atomicAdd(&aL[cc * kStageMax + sl], L);
                     } else {
                         const int j = (int)((sl != kSlotNone ? tkey[sl] : e) & kIdxMask);
-                        double* fj = cc == 0 ? &b.f[j].x : (cc == 1 ? &b.f[j].y : &b.f[j].z);
+                        double* fj = b.f + cc * (size_t)b.n + j;
                         atomicAdd(fj, -ff_to_f64(t[cc]));
                     }
                 }
@@ -497,7 +497,7 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) k_force_tile(Buf
                     atomicAdd(&aH[cc * kStageMax + so], H);
                     atomicAdd(&aL[cc * kStageMax + so], L);
                 } else {
-                    double* f = cc == 0 ? &b.f[i].x : (cc == 1 ? &b.f[i].y : &b.f[i].z);
+                    double* f = b.f + cc * (size_t)b.n + i;
                     atomicAdd(f, ff_to_f64(fi[cc]));
                 }
             }
@@ -508,9 +508,9 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) k_force_tile(Buf
             const double vx = fx_to_double(aH[s], aL[s]);
             const double vy = fx_to_double(aH[kStageMax + s], aL[kStageMax + s]);
             const double vz = fx_to_double(aH[2 * kStageMax + s], aL[2 * kStageMax + s]);
-            if (vx != 0.0) atomicAdd(&b.f[j].x, vx);
-            if (vy != 0.0) atomicAdd(&b.f[j].y, vy);
-            if (vz != 0.0) atomicAdd(&b.f[j].z, vz);
+            if (vx != 0.0) atomicAdd(b.f + j, vx);
+            if (vy != 0.0) atomicAdd(b.f + b.n + j, vy);
+            if (vz != 0.0) atomicAdd(b.f + 2 * (size_t)b.n + j, vz);
         }
         __syncthreads();   // the stage is reused by the next tile
     }
