@@ -153,6 +153,14 @@ bool fixed64_form(const fire_potential_t& p) {
 bool fixed64_half(const fire_potential_t& p) {
     return fixed64_form(p) && p.newton != FIRE_NEWTON_OFF;
 }
+// Blocks of the double-float density pass: one thread per atom on blocks of
+// kDensFF1Block (3 per SM at 40 registers: 0.289 against 0.312 ms with
+// blocks of 128 on the 1M-atom box, 0.302 with 256, 0.357 with 1024),
+// split lists on blocks of kForceBlock.
+inline int dens_ff_block(int tpa) { return tpa == 1 ? kDensFF1Block : kForceBlock; }
+inline int dens_ff_grid(int n, int tpa) {
+    return (int)(((long long)n * tpa + dens_ff_block(tpa) - 1) / dens_ff_block(tpa));
+}
 
 // The pair passes that can split an atom's list over several threads: the
 // FP64 table form and the FP32-pair form with exponentials.
@@ -356,7 +364,8 @@ fire_status ensure_buffers(fire_handle* h, const GeoC& g, int cap) {
         }
     }
     // energy partials of the density (or only) pass, then the embedding's
-    h->b.ne_dens = g.tiled ? tile_grid(h, g) : h->b.nb_force;
+    h->b.ne_dens = g.tiled ? tile_grid(h, g)
+                 : fixed64_form(h->pot) ? dens_ff_grid(h->n, h->b.tpa) : h->b.nb_force;
     return FIRE_OK;
 }
 
@@ -377,14 +386,16 @@ void launch_build(fire_handle* h, const GeoC& g, int force, cudaStream_t s) {
                                                                                          force);
 }
 
-// The pair passes for the handle's threads per atom (b.tpa).
+// The pair passes for the handle's threads per atom (b.tpa).  The density
+// pass writes one energy partial per block: dens_ff_grid blocks.
 template <bool HALF>
-void density_ff(const Bufs& b, const PotC& P, const GeoC& g, int nb, cudaStream_t s) {
+void density_ff(const Bufs& b, const PotC& P, const GeoC& g, cudaStream_t s) {
+    const int nb = dens_ff_grid(b.n, b.tpa), bs = dens_ff_block(b.tpa);
     switch (b.tpa) {
-    case 8: k_density_ff<HALF, 8><<<nb, kForceBlock, 0, s>>>(b, P, g); break;
-    case 4: k_density_ff<HALF, 4><<<nb, kForceBlock, 0, s>>>(b, P, g); break;
-    case 2: k_density_ff<HALF, 2><<<nb, kForceBlock, 0, s>>>(b, P, g); break;
-    default: k_density_ff1<HALF><<<nb, kForceBlock, 0, s>>>(b, P, g);
+    case 8: k_density_ff<HALF, 8><<<nb, bs, 0, s>>>(b, P, g); break;
+    case 4: k_density_ff<HALF, 4><<<nb, bs, 0, s>>>(b, P, g); break;
+    case 2: k_density_ff<HALF, 2><<<nb, bs, 0, s>>>(b, P, g); break;
+    default: k_density_ff1<HALF><<<nb, bs, 0, s>>>(b, P, g);
     }
 }
 template <bool HALF>
@@ -448,7 +459,7 @@ void hvp_cached(const GradBufs& b, const double* u, double* hu, const int* skip,
 void launch_confirm(fire_handle* h, const GeoC& g, cudaStream_t s) {
     Bufs bv = h->b;
     bv.pass_role = 2;
-    density_ff<false>(bv, h->potc, g, h->b.nb_verify, s);
+    density_ff<false>(bv, h->potc, g, s);
     force_ff<false>(bv, h->potc, g, s);
 }
 
@@ -467,11 +478,11 @@ void launch_forces(fire_handle* h, const GeoC& g, cudaStream_t s, bool confirm_p
         k_embed<<<h->b.nb_embed, kElemBlock, 0, s>>>(h->b);
         k_force_tile<<<nt, kTileThreads, kForceTileSmem, s>>>(h->b, h->potc, g);
     } else if (tab && fixed64_half(h->pot)) {
-        density_ff<true>(h->b, h->potc, g, h->b.nb_force, s);
+        density_ff<true>(h->b, h->potc, g, s);
         k_embed<<<h->b.nb_embed, kElemBlock, 0, s>>>(h->b);
         force_ff<true>(h->b, h->potc, g, s);
     } else if (tab) {
-        density_ff<false>(h->b, h->potc, g, h->b.nb_force, s);
+        density_ff<false>(h->b, h->potc, g, s);
         force_ff<false>(h->b, h->potc, g, s);
     } else if (h->pot.kind == FIRE_POT_RGL && h->pot.precision == FIRE_PREC_FP32_PAIR) {
         density32(h->b, h->potc, g, s);
@@ -1109,7 +1120,7 @@ static fire_status init_handle(fire_handle_t** hp, const fire_system_t* sys,
         if (ts != FIRE_OK) return bail(ts);
         if (fp32pair && pot->pair_eval == FIRE_PAIR_TABLE) b.nb_force = h->nb_tab_d;
     }
-    b.nb_verify = h->verify ? ceil_div((long long)h->n * b.tpa, kForceBlock) : 0;
+    b.nb_verify = h->verify ? dens_ff_grid(h->n, b.tpa) : 0;
     b.pass_role = h->verify ? 1 : 0;
     b.ne_dens = b.nb_force;
     CKI(cudaMalloc(&b.x, n * sizeof(dvec4)));
@@ -1304,7 +1315,7 @@ fire_status fire_set_threads_per_atom(fire_handle_t* h, int32_t tpa, int32_t* ch
         h->b.tpa = t;
         if (!(h->pot.precision == FIRE_PREC_FP32_PAIR && h->pot.pair_eval == FIRE_PAIR_TABLE))
             h->b.nb_force = ceil_div((long long)h->n * t, kForceBlock);
-        if (h->verify) h->b.nb_verify = ceil_div((long long)h->n * t, kForceBlock);
+        if (h->verify) h->b.nb_verify = dens_ff_grid(h->n, t);
     }
     if (chosen) *chosen = t;
     return FIRE_OK;
@@ -1903,8 +1914,8 @@ fire_status fire_profile_stages(fire_handle_t* h, const double* pos, const doubl
         if (tab && f32) k_density32_tab<<<h->nb_tab_d, kTabBlock, h->smem_d, s>>>(h->b, h->potc, g);
         else if (tab && fixed64_half(h->pot) && g.tiled)
             k_density_tile<<<tile_grid(h, g), kTileThreads, kDensTileSmem, s>>>(h->b, h->potc, g);
-        else if (tab && fixed64_half(h->pot)) density_ff<true>(h->b, h->potc, g, h->b.nb_force, s);
-        else if (tab) density_ff<false>(h->b, h->potc, g, h->b.nb_force, s);
+        else if (tab && fixed64_half(h->pot)) density_ff<true>(h->b, h->potc, g, s);
+        else if (tab) density_ff<false>(h->b, h->potc, g, s);
         else if (rgl && f32) density32(h->b, h->potc, g, s);
         else if (rgl) k_density<<<h->b.nb_force, kForceBlock, 0, s>>>(h->b, h->potc, g);
         cudaEventRecord(ev[2], s);

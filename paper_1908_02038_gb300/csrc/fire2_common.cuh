@@ -26,6 +26,7 @@ constexpr int kForceBlock = 128;
 constexpr int kTabBlock = 256;    // FP32 table kernels (more warps per shared table copy)
 constexpr int kTabBlock64 = 512;  // FP64 table kernel (both tables, ~112 KB, in shared memory)
 constexpr int kElemBlock = 256;
+constexpr int kDensFF1Block = 512;   // double-float density pass, one thread per atom
 constexpr int kCtlThreads = 512;
 constexpr int kRedRows = 6;   // rows of the per-block partials: P, |F|^2, |v|^2, max |F_i|^2,
                               // max |F_i,d|, energy (red_write)

@@ -1007,11 +1007,12 @@ __device__ __forceinline__ ffloat pair_sep_ff(const Bufs& b, const long long* qt
 template <bool HALF, int TPA>
 __device__ __forceinline__ void density_ff_body(const Bufs& b, const PotC& P, const GeoC& g) {
     __shared__ long long qt[375];
-    __shared__ double etab[kExpTableSize];
     __shared__ double red[32];
+    // the exponentials' table is read through L1: only pairs compressed below
+    // r0/2 use it, and a shared copy per block costs more than it saves
+    const double* etab = b.exp_table;
     if (pass_skipped(b)) return;
     fill_qshift64_table(qt, g);
-    for (int t = threadIdx.x; t < kExpTableSize; t += blockDim.x) etab[t] = b.exp_table[t];
     __syncthreads();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = t / TPA, lane = t % TPA;
@@ -1068,12 +1069,12 @@ __global__ void __launch_bounds__(kForceBlock) k_density_ff(Bufs b, PotC P, GeoC
     density_ff_body<HALF, TPA>(b, P, g);
 }
 
-// The same pass with one thread per atom (large systems) on 12 blocks per SM
-// (40 registers): 0.312 against 0.325 ms on the 1M-atom box with the
-// compiler's 44.  (The force pass keeps the compiler's 64: capped at 56 or
+// The same pass with one thread per atom (large systems) on blocks of 512,
+// 3 per SM (40 registers; with the compiler's 44 it fits fewer threads and
+// ran 4 % slower).  (The force pass keeps the compiler's 64: capped at 56 or
 // 48 it spills and takes 0.51 and 0.69 against 0.48 ms.)
 template <bool HALF>
-__global__ void __launch_bounds__(kForceBlock, 12) k_density_ff1(Bufs b, PotC P, GeoC g) {
+__global__ void __launch_bounds__(kDensFF1Block, 3) k_density_ff1(Bufs b, PotC P, GeoC g) {
     density_ff_body<HALF, 1>(b, P, g);
 }
 
@@ -1084,10 +1085,9 @@ __global__ void __launch_bounds__(kForceBlock, 12) k_density_ff1(Bufs b, PotC P,
 template <bool HALF, int TPA, int BLK>
 __global__ void __launch_bounds__(BLK) k_force_ff(Bufs b, PotC P, GeoC g) {
     __shared__ long long qt[375];
-    __shared__ double etab[kExpTableSize];
+    const double* etab = b.exp_table;   // through L1, as in the density pass
     if (pass_skipped(b)) return;
     fill_qshift64_table(qt, g);
-    for (int t = threadIdx.x; t < kExpTableSize; t += blockDim.x) etab[t] = b.exp_table[t];
     __syncthreads();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = t / TPA, lane = t % TPA;
