@@ -85,6 +85,35 @@ __device__ __forceinline__ double warp_max(double v) {
     return v;
 }
 
+// FP64 instructions issue at 1/58 of the FP32 rate on this part and a warp
+// pays for all 32 lanes of each, so the reductions below keep them few.
+//
+// Four sums over the warp with 6 FP64 additions in place of 4 x 5: the first
+// two butterfly steps halve the set of quantities each lane carries (lanes
+// 0-15 go on with q0, q1 and lanes 16-31 with q2, q3; then lanes with bit 3
+// clear keep the first of the two), the last three add one value.  On return
+// lanes 8k .. 8k + 7 hold the total of q_k (fixed order: deterministic).
+__device__ __forceinline__ double warp_sum4(double q0, double q1, double q2, double q3) {
+    const unsigned lane = threadIdx.x & 31u;
+    const bool b4 = (lane & 16u) != 0u, b3 = (lane & 8u) != 0u;
+    const double r0 = __shfl_xor_sync(0xffffffffu, b4 ? q0 : q2, 16);
+    const double r1 = __shfl_xor_sync(0xffffffffu, b4 ? q1 : q3, 16);
+    const double a0 = (b4 ? q2 : q0) + r0, a1 = (b4 ? q3 : q1) + r1;
+    double v = (b3 ? a1 : a0) + __shfl_xor_sync(0xffffffffu, b3 ? a0 : a1, 8);
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+// Maximum over the warp of non-negative doubles (NaN propagates) on the
+// integer pipes: their IEEE patterns order like the values; every lane
+// receives it.
+__device__ __forceinline__ double warp_max_nonneg(double v) {
+    long long b = __double_as_longlong(v);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) b = max(b, __shfl_xor_sync(0xffffffffu, b, o));
+    return __longlong_as_double(b);
+}
+
 // Sum over the TPA consecutive lanes that share one atom in the pair passes
 // (TPA = 1, 2, 4 or 8 threads per atom); every lane of the group receives
 // the total.  Only the group's own lanes are named in the mask, so groups
@@ -113,6 +142,18 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
         r = (lane < (int)(blockDim.x >> 5)) ? sh[lane] : 0.0;
         r = warp_sum(r);
     }
+    return r;
+}
+// Block-wide maximum of non-negative doubles on the integer pipes; result
+// valid in thread 0.
+__device__ __forceinline__ double block_max_nonneg(double v, double* sh) {
+    v = warp_max_nonneg(v);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (w == 0) r = warp_max_nonneg((lane < (int)(blockDim.x >> 5)) ? sh[lane] : 0.0);
     return r;
 }
 __device__ __forceinline__ double block_max(double v, double* sh) {

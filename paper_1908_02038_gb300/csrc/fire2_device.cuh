@@ -774,6 +774,10 @@ __device__ __forceinline__ long long pair_sep_q(const Bufs& b, const int3* qt, i
 // Per-atom part of the FP64 reductions of (F, v) (see k_reduce_ctl), shared
 // by k_reduce_ctl and the NEB projection.
 
+// Row of the partials that holds the k-th sum of warp_sum4 (P, |F|^2, |v|^2,
+// energy); rows 3 and 4 hold the maxima of |F_i|^2 and |F_i,d|.
+__device__ __forceinline__ int red_row(int k) { return k == 3 ? 5 : k; }
+
 struct RedAcc {
     double P = 0.0, F2 = 0.0, V2 = 0.0, fa2 = 0.0, fin = 0.0;
     double E = 0.0;   // the block's slice of the energy partials (k_reduce_ctl)
@@ -820,42 +824,33 @@ __device__ __forceinline__ void red_atom(const Bufs& b, int i, const dvec4& f, d
 }
 
 // The block's six reductions written to the partials (kRedRows rows of
-// gridDim.x): sums of P, |F|^2 and |v|^2, maxima of |F_i|^2 and |F_i,d|, and
-// the sum of the block's energy terms.  All six in one sweep (their shuffles
-// interleave; two barriers in all), each in the order of a block_sum /
-// block_max of its own.  sh holds kRedRows x 32 doubles.
+// gridDim.x): sums of P, |F|^2, |v|^2 and of the block's energy terms
+// (warp_sum4), maxima of |F_i|^2 and |F_i,d| (integer maxima); per warp,
+// then over the warps in warp 0, in a fixed order.  sh holds kRedRows x 32
+// doubles.
 __device__ __forceinline__ void red_write(const RedAcc& a, double* sh, double* rpart) {
     const int nb = gridDim.x;
-    double q[kRedRows] = {a.P, a.F2, a.V2, a.fa2, a.fin, a.E};
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-        for (int k = 0; k < kRedRows; ++k) {
-            const double t = __shfl_down_sync(0xffffffffu, q[k], o);
-            q[k] = (k == 3 || k == 4) ? fmax(q[k], t) : q[k] + t;
-        }
-    }
+    double s = warp_sum4(a.P, a.F2, a.V2, a.E);
+    double m0 = warp_max_nonneg(a.fa2), m1 = warp_max_nonneg(a.fin);
     __syncthreads();   // sh may hold an earlier use
-    if (lane == 0)
-#pragma unroll
-        for (int k = 0; k < kRedRows; ++k) sh[k * 32 + w] = q[k];
+    if ((lane & 7) == 0) sh[red_row(lane >> 3) * 32 + w] = s;   // lanes 0, 8, 16, 24
+    if (lane == 0) {
+        sh[3 * 32 + w] = m0;
+        sh[4 * 32 + w] = m1;
+    }
     __syncthreads();
     if (w == 0) {
         const bool in = lane < (int)(blockDim.x >> 5);
-#pragma unroll
-        for (int k = 0; k < kRedRows; ++k) q[k] = in ? sh[k * 32 + lane] : 0.0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-            for (int k = 0; k < kRedRows; ++k) {
-                const double t = __shfl_down_sync(0xffffffffu, q[k], o);
-                q[k] = (k == 3 || k == 4) ? fmax(q[k], t) : q[k] + t;
-            }
+        s = warp_sum4(in ? sh[lane] : 0.0, in ? sh[32 + lane] : 0.0, in ? sh[2 * 32 + lane] : 0.0,
+                      in ? sh[5 * 32 + lane] : 0.0);
+        m0 = warp_max_nonneg(in ? sh[3 * 32 + lane] : 0.0);
+        m1 = warp_max_nonneg(in ? sh[4 * 32 + lane] : 0.0);
+        if ((lane & 7) == 0) rpart[red_row(lane >> 3) * nb + blockIdx.x] = s;
+        if (lane == 0) {
+            rpart[3 * nb + blockIdx.x] = m0;
+            rpart[4 * nb + blockIdx.x] = m1;
         }
-        if (lane == 0)
-#pragma unroll
-            for (int k = 0; k < kRedRows; ++k) rpart[k * nb + blockIdx.x] = q[k];
     }
 }
 
@@ -1263,8 +1258,8 @@ __device__ __forceinline__ CtlSums ctl_reduce(const Bufs& b, int ne, double* sh 
         a[0] += b.rpart[k];
         a[1] += b.rpart[nr + k];
         a[2] += b.rpart[2 * nr + k];
-        a[3] = fmax(a[3], b.rpart[3 * nr + k]);
-        a[4] = fmax(a[4], b.rpart[4 * nr + k]);
+        a[3] = max_nonneg(a[3], b.rpart[3 * nr + k]);
+        a[4] = max_nonneg(a[4], b.rpart[4 * nr + k]);
         a[5] += b.rpart[5 * nr + k];
     }
     if (ne > 0) {   // four independent sums per thread, so that its loads overlap
@@ -1281,29 +1276,27 @@ __device__ __forceinline__ CtlSums ctl_reduce(const Bufs& b, int ne, double* sh 
         a[5] += (e0 + e1) + (e2 + e3);
     }
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-        for (int q = 0; q < kRedRows; ++q) {
-            const double t = __shfl_down_sync(0xffffffffu, a[q], o);
-            a[q] = (q == 3 || q == 4) ? fmax(a[q], t) : a[q] + t;
-        }
+    double t = warp_sum4(a[0], a[1], a[2], a[5]);
+    double m0 = warp_max_nonneg(a[3]), m1 = warp_max_nonneg(a[4]);
+    if ((lane & 7) == 0) sh[red_row(lane >> 3) * 32 + w] = t;
+    if (lane == 0) {
+        sh[3 * 32 + w] = m0;
+        sh[4 * 32 + w] = m1;
     }
-    if (lane == 0)
-#pragma unroll
-        for (int q = 0; q < kRedRows; ++q) sh[q * 32 + w] = a[q];
     __syncthreads();
     if (w == 0) {
-#pragma unroll
-        for (int q = 0; q < kRedRows; ++q) a[q] = lane < (int)(blockDim.x >> 5) ? sh[q * 32 + lane] : 0.0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-            for (int q = 0; q < kRedRows; ++q) {
-                const double t = __shfl_down_sync(0xffffffffu, a[q], o);
-                a[q] = (q == 3 || q == 4) ? fmax(a[q], t) : a[q] + t;
-            }
-        }
+        const bool in = lane < (int)(blockDim.x >> 5);
+        t = warp_sum4(in ? sh[lane] : 0.0, in ? sh[32 + lane] : 0.0, in ? sh[2 * 32 + lane] : 0.0,
+                      in ? sh[5 * 32 + lane] : 0.0);
+        m0 = warp_max_nonneg(in ? sh[3 * 32 + lane] : 0.0);
+        m1 = warp_max_nonneg(in ? sh[4 * 32 + lane] : 0.0);
+        // the four sums sit in lanes 0, 8, 16, 24: gather them in lane 0
+        a[0] = t;
+        a[1] = __shfl_sync(0xffffffffu, t, 8);
+        a[2] = __shfl_sync(0xffffffffu, t, 16);
+        a[5] = __shfl_sync(0xffffffffu, t, 24);
+        a[3] = m0;
+        a[4] = m1;
     }
     return {a[0], a[1], a[2], a[3], a[4], a[5]};   // valid in thread 0
 }
@@ -1481,7 +1474,7 @@ __device__ void update_body(const Bufs& b, const GeoC& g, const FireScal& s, int
         const float ddz = f64_to_f32_trunc(x.z) - r.z;
         d2max = fmaxf(d2max, ddx * ddx + ddy * ddy + ddz * ddz);
     }
-    const double bm = block_max(f32_to_f64(d2max), red);
+    const double bm = block_max_nonneg(f32_to_f64(d2max), red);
     if (threadIdx.x == 0) {
         atomicMax(&b.st->max_disp2, (unsigned long long)__double_as_longlong(bm));
         if (has_if) {
@@ -1524,7 +1517,7 @@ __global__ void k_update_pre(Bufs b) {
         b.v[i] = v;
         vm = fmax(vm, v.x * v.x + v.y * v.y + v.z * v.z);
     }
-    const double bm = block_max(vm, red);
+    const double bm = block_max_nonneg(vm, red);
     if (threadIdx.x == 0) atomicMax(&b.st->vmax2, (unsigned long long)__double_as_longlong(bm));
 }
 
