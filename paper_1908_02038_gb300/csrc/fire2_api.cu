@@ -1137,7 +1137,6 @@ static fire_status init_handle(fire_handle_t** hp, const fire_system_t* sys,
     }
     if (fixed64 || h->verify) {
         CKI(cudaMalloc(&b.xq64, n * sizeof(lvec4)));
-        CKI(cudaMalloc(&b.fpff, n * sizeof(float2)));
     }
     CKI(cudaMalloc(&b.nnbr, n * sizeof(int)));
     CKI(cudaMalloc(&b.cell_of, n * sizeof(int)));
@@ -1207,7 +1206,7 @@ void fire_destroy(fire_handle_t* h) {
     if (h->stream) cudaStreamSynchronize(h->stream);
     drop_graph(h);
     Bufs& b = h->b;
-    void* ptrs[] = {b.x, b.v, b.f, b.xf, b.xq, b.xq64, b.fpff, b.fp32, (void*)b.exp32_table,
+    void* ptrs[] = {b.x, b.v, b.f, b.xf, b.xq, b.xq64, b.fp32, (void*)b.exp32_table,
                     (void*)b.exp_table, b.rho, b.fp, b.nbr, b.nnbr, b.crep, b.cden,
                     b.cell_of, b.cell_count, b.cell_start, b.cell_atoms, b.epart, b.rpart,
                     b.st, b.pos_io, b.nbr_loc, b.tile_key, b.tile_ns};

@@ -109,8 +109,8 @@ struct Bufs {
     const double* exp_table;  // 2^(j/256), j = 0..255
     // tabulated RGL pair functions (fire2_table.cuh); nullptr when analytic
     const float *tab_ffd, *tab_fff;   // FP64 form: density / force rows (kFFRow floats)
-    lvec4* xq64;               // FP64 form: positions in 2^-44 A units
-    float2* fpff;              // FP64 form: F'(rho) as a float pair
+    lvec4* xq64;               // FP64 form: positions in 2^-44 A units (x, y, z) and
+                               //    F'(rho) as a float pair in w (fp_store / fp_load)
     int pass_role;             // 0: always run; 1: FP32-pair pass that sits out the FP64
                                //    confirmation; 2: FP64 pass that runs only for it
     int nb_verify;             // blocks of the FP64 confirming passes
@@ -150,6 +150,20 @@ __device__ __forceinline__ void f_add(const Bufs& b, int i, double x, double y, 
     atomicAdd(b.f + i, x);
     atomicAdd(b.f + b.n + i, y);
     atomicAdd(b.f + 2 * b.n + i, z);
+}
+
+// F'(rho_i) of the double-float form as a float pair, kept in the fourth
+// word of the atom's fixed-point position record: the force pass gathers
+// one 32-byte record per neighbour for both (1M-atom box: 0.414 against
+// 0.423 ms with F' in an array of its own).  The update rewrites x, y, z
+// only after the force pass, and the embedding rewrites w before the next.
+__device__ __forceinline__ void fp_store(const Bufs& b, int i, ffloat f) {
+    b.xq64[i].w = (long long)((unsigned long long)__float_as_uint(f.hi) |
+                              ((unsigned long long)__float_as_uint(f.lo) << 32));
+}
+__device__ __forceinline__ ffloat fp_load(const lvec4& q) {
+    return {__uint_as_float((unsigned)((unsigned long long)q.w & 0xffffffffull)),
+            __uint_as_float((unsigned)((unsigned long long)q.w >> 32))};
 }
 
 // Whether a force pass sits this evaluation out (pass_role above; the state
@@ -485,22 +499,21 @@ __global__ void k_embed(Bufs b) {
     ffloat emb_ff = {0.f, 0.f};
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < b.n; i += gridDim.x * blockDim.x) {
         const double rho = b.rho[i];
-        if (b.fpff && rho > 1e-30 && rho < 1e30) {
+        if (b.xq64 && rho > 1e-30 && rho < 1e30) {
             // FP64 form with double-float pair terms: the embedding in float
             // pairs too, F' as a float pair for the force pass (the only
             // reader of F' in this form) and the energy summed in float pairs
             ffloat sqf, fpf;
             rgl_embed_ff(f64_to_ff(rho), sqf, fpf);
-            b.fpff[i] = make_float2(fpf.hi, fpf.lo);
+            fp_store(b, i, fpf);
             emb_ff = ff_acc(emb_ff, {-sqf.hi, -sqf.lo});
             if (b.eatom) b.eatom[i] -= ff_to_f64(sqf);
             continue;
         }
         double sq, fp;
         rgl_embed(rho, sq, fp);
-        if (b.fpff) {
-            const ffloat fpf = f64_to_ff(fp);
-            b.fpff[i] = make_float2(fpf.hi, fpf.lo);
+        if (b.xq64) {
+            fp_store(b, i, f64_to_ff(fp));
         } else {
             b.fp[i] = fp;
         }
@@ -1050,7 +1063,7 @@ __device__ __forceinline__ void density_ff_body(const Bufs& b, const PotC& P, co
             rgl_embed_dd(rho_d, sq, fp, fpf);
             b.rho[i] = rho_d;
             b.fp[i] = fp;
-            b.fpff[i] = make_float2(fpf.hi, fpf.lo);
+            fp_store(b, i, fpf);
             e_atom = erep_d - sq;
             if (b.eatom) b.eatom[i] = e_atom;
         }
@@ -1088,23 +1101,19 @@ __global__ void __launch_bounds__(BLK) k_force_ff(Bufs b, PotC P, GeoC g) {
     const int i = t / TPA, lane = t % TPA;
     if (i >= b.n) return;   // the whole group leaves
     const lvec4 qi = b.xq64[i];
-    const float2 fpi2 = b.fpff[i];
-    const ffloat fpi = {fpi2.x, fpi2.y};
+    const ffloat fpi = fp_load(qi);
     const int m = b.nnbr[i];
     ffloat fx = {0.f, 0.f}, fy = {0.f, 0.f}, fz = {0.f, 0.f};
-    // software pipeline: the next list entry, and the position and F' of its
-    // atom, load while this pair is evaluated
+    // software pipeline: the next list entry and its atom's record (position
+    // and F') load while this pair is evaluated
     uint32_t e_nx = lane < m ? b.nbr[(size_t)lane * b.n + i] : 0u;
     lvec4 q_nx = b.xq64[lane < m ? (int)(e_nx & kIdxMask) : i];
-    float2 p_nx = b.fpff[lane < m ? (int)(e_nx & kIdxMask) : i];
     for (int k = lane; k < m; k += TPA) {
         const uint32_t e = e_nx;
         const lvec4 qj = q_nx;
-        const float2 fpj2 = p_nx;
         if (k + TPA < m) {
             e_nx = b.nbr[(size_t)(k + TPA) * b.n + i];
             q_nx = b.xq64[e_nx & kIdxMask];
-            p_nx = b.fpff[e_nx & kIdxMask];
         }
         ffloat dx, dy, dz;
         int j;
@@ -1122,7 +1131,7 @@ __global__ void __launch_bounds__(BLK) k_force_ff(Bufs b, PotC P, GeoC g) {
             c[0] = f64_to_ff(2.0 * dphi * rinv);
             c[1] = f64_to_ff(dg * rinv);
         }
-        const ffloat fs = ff_add(c[0], ff_mul(ff_add(fpi, {fpj2.x, fpj2.y}), c[1]));
+        const ffloat fs = ff_add(c[0], ff_mul(ff_add(fpi, fp_load(qj)), c[1]));
         const ffloat tx = ff_mul(fs, dx), ty = ff_mul(fs, dy), tz = ff_mul(fs, dz);
         fx = ff_acc(fx, tx);
         fy = ff_acc(fy, ty);

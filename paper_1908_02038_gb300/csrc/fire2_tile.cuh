@@ -408,7 +408,8 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) k_force_tile(Buf
             sx[s] = q.x;
             sy[s] = q.y;
             sz[s] = q.z;
-            sfp[s] = b.fpff[e & kIdxMask];
+            const ffloat fq = fp_load(q);
+            sfp[s] = make_float2(fq.hi, fq.lo);
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 aH[c * kStageMax + s] = 0;
@@ -431,7 +432,8 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) k_force_tile(Buf
                 qix = q.x;
                 qiy = q.y;
                 qiz = q.z;
-                fpi2 = b.fpff[i];
+                const ffloat fq = fp_load(q);
+                fpi2 = make_float2(fq.hi, fq.lo);
             }
             const ffloat fpi = {fpi2.x, fpi2.y};
             const int m = b.nnbr[i];
@@ -454,7 +456,8 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) k_force_tile(Buf
                     qjx = q.x;
                     qjy = q.y;
                     qjz = q.z;
-                    fpj2 = b.fpff[e & kIdxMask];
+                    const ffloat fq = fp_load(q);
+                    fpj2 = make_float2(fq.hi, fq.lo);
                 }
                 ffloat dx, dy, dz;
                 const ffloat r2 = tile_sep(qjx - qix, qjy - qiy, qjz - qiz, dx, dy, dz);
