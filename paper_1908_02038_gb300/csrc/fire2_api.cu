@@ -1111,11 +1111,11 @@ static fire_status init_handle(fire_handle_t** hp, const fire_system_t* sys,
     h->sms = sms;
     b.tpa = tpa_form(*pot) ? auto_tpa(*pot, h->n, sms) : 1;
     b.nb_force = ceil_div((long long)h->n * b.tpa, kForceBlock);
-    // the embedding and the reductions run best on two blocks per SM (1M
-    // atoms, measured: embed 37 / 39 / 41 us at 2 / 4 / 8 blocks per SM;
-    // reduce 51 / 49 / 55 / 62 us at 1 / 2 / 4 / 8)
+    // blocks per SM of the embedding and the reductions, measured on 1M
+    // atoms: embedding 16.4 / 14.3 / 18.4 / 22.1 us at 2 / 4 / 8 / 16;
+    // reductions + control 53 / 51 / 57 / 70 us at 1 / 2 / 4 / 8
     b.nb_embed = (pot->kind == FIRE_POT_RGL && !whole)
-                     ? std::max(1, std::min(ceil_div(h->n, kElemBlock), sms * 2)) : 0;
+                     ? std::max(1, std::min(ceil_div(h->n, kElemBlock), sms * 4)) : 0;
     b.nb_red = std::max(1, std::min(ceil_div(h->n, kElemBlock), sms * 2));
     // an FP32-pair stop on ftol is confirmed with the FP64 table passes
     h->verify = fp32pair && pot->kind == FIRE_POT_RGL && params->confirm64 != 0;
