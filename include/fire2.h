@@ -349,8 +349,9 @@ typedef enum {
     FIRE_STAGE_FORCE = 3,       /* force pass (RGL pass 2, or LJ) */
     FIRE_STAGE_REDUCE = 4,      /* FP64 reductions of P, |F|^2, |v|^2, max|F_i|, with the
                                    scalar FIRE control (Algorithm 2) in the same launch */
-    FIRE_STAGE_CONTROL = 5,     /* the control as a launch of its own: NEB handles only
-                                   (otherwise ~0, its work is in FIRE_STAGE_REDUCE) */
+    FIRE_STAGE_CONTROL = 5,     /* ~0: the control runs in the last block of the reduction
+                                   launch (for NEB handles, of the projection launch), whose
+                                   time FIRE_STAGE_REDUCE holds */
     FIRE_STAGE_UPDATE = 6,      /* element-wise half step back / kick / mix / drift */
     FIRE_NSTAGES = 7
 } fire_stage;

@@ -428,11 +428,14 @@ void density32(const Bufs& b, const PotC& P, const GeoC& g, cudaStream_t s) {
     }
 }
 void force32(const Bufs& b, const PotC& P, const GeoC& g, cudaStream_t s) {
+    // one thread per atom on blocks of 512 (1M-atom box: 0.232 against
+    // 0.239 ms with blocks of 128); the pass writes no per-block partials
+    constexpr int B1 = 512;
     switch (b.tpa) {
-    case 8: k_force32<8><<<b.nb_force, kForceBlock, 0, s>>>(b, P, g); break;
-    case 4: k_force32<4><<<b.nb_force, kForceBlock, 0, s>>>(b, P, g); break;
-    case 2: k_force32<2><<<b.nb_force, kForceBlock, 0, s>>>(b, P, g); break;
-    default: k_force32<1><<<b.nb_force, kForceBlock, 0, s>>>(b, P, g);
+    case 8: k_force32<8, kForceBlock><<<b.nb_force, kForceBlock, 0, s>>>(b, P, g); break;
+    case 4: k_force32<4, kForceBlock><<<b.nb_force, kForceBlock, 0, s>>>(b, P, g); break;
+    case 2: k_force32<2, kForceBlock><<<b.nb_force, kForceBlock, 0, s>>>(b, P, g); break;
+    default: k_force32<1, B1><<<ceil_div(b.n, B1), B1, 0, s>>>(b, P, g);
     }
 }
 
@@ -517,20 +520,18 @@ NebC neb_consts(const fire_handle* h) {
     return c;
 }
 
-// The FP64 reductions of (F, v); for NEB handles the projection that ends
-// with them.
 // The reductions and the control step (Algorithm 2) of one evaluation: one
 // launch (k_reduce_ctl, whose last block runs the control), or for NEB
-// handles the projection chain (which ends with the reductions of
-// (F^NEB, v)) followed by k_control.
+// handles two (k_neb_sums, whose last block sets the band's coefficients,
+// and k_neb_project, which ends with the reductions of (F^NEB, v) and whose
+// last block runs the control).
 void launch_reduce_control(fire_handle* h, const GeoC& g, cudaStream_t s, int mode,
                            cudaGraphConditionalHandle hc, int has_handle) {
     if (h->neb) {
         const NebC c = neb_consts(h);
-        k_neb_sums<<<dim3(c.nb, c.n_img), kNebBlock, 0, s>>>(h->b, g, c);
-        k_neb_scalars<<<1, 256, (size_t)c.n_img * kNebSums * sizeof(double), s>>>(h->b, c);
-        k_neb_project<<<h->neb->nb_proj, kNebBlock, 0, s>>>(h->b, g, c);
-        k_control<<<1, kCtlThreads, 0, s>>>(h->b, mode, hc, has_handle);
+        k_neb_sums<<<dim3(c.nb, c.n_img), kNebBlock, (size_t)c.n_img * kNebSums * sizeof(double),
+                     s>>>(h->b, g, c);
+        k_neb_project<<<h->neb->nb_proj, kNebBlock, 0, s>>>(h->b, g, c, mode, hc, has_handle);
         return;
     }
     k_reduce_ctl<<<h->b.nb_red, kElemBlock, 0, s>>>(h->b, mode, hc, has_handle);
@@ -1935,7 +1936,7 @@ fire_status fire_profile_stages(fire_handle_t* h, const double* pos, const doubl
         else force_lj(h->b, h->potc, g, s);
         cudaEventRecord(ev[4], s);
         // the control step runs in the last block of the reductions' launch
-        // (k_reduce_ctl); NEB handles run it as a kernel of its own
+        // (k_reduce_ctl; for NEB handles, k_neb_project after k_neb_sums)
         const cudaGraphConditionalHandle none{};
         launch_reduce_control(h, g, s, CTL_EVAL, none, 0);
         cudaEventRecord(ev[5], s);

@@ -84,7 +84,8 @@ struct DevState {
     // the FP32 norm at the configuration being confirmed
     int vstate, vcount, vmode;
     double ftol_user, fn32, fsw;
-    unsigned int red_blocks;   // k_reduce_ctl blocks finished (last-block test)
+    unsigned int red_blocks;   // k_reduce_ctl / k_neb_project blocks finished (last-block test)
+    unsigned int neb_blocks;   // k_neb_sums blocks finished (last-block test)
 };
 
 struct Bufs {
@@ -918,8 +919,8 @@ __global__ void __launch_bounds__(kForceBlock) k_density32(Bufs b, PotC P, GeoC 
 // Pass 2 (FP32-pair): F_i = sum_j [2 phi' + (F'_i + F'_j) g'] (x_j - x_i) / r,
 // Kahan-compensated per component, written as FP64 (no atomics); TPA
 // threads per atom as in k_density32.
-template <int TPA = 1>
-__global__ void __launch_bounds__(kForceBlock) k_force32(Bufs b, PotC P, GeoC g) {
+template <int TPA, int BLK>
+__global__ void __launch_bounds__(BLK) k_force32(Bufs b, PotC P, GeoC g) {
     __shared__ int3 qt[125];
     __shared__ float et[kExp32TableSize];
     if (pass_skipped(b)) return;
@@ -1387,18 +1388,8 @@ __device__ void control_body(const Bufs& b, int mode, cudaGraphConditionalHandle
     if (has_handle) cudaGraphSetConditional(h, stop ? 0u : 1u);
 }
 
-__global__ void k_control(Bufs b, int mode, cudaGraphConditionalHandle h, int has_handle) {
-    __shared__ double sh[kRedRows * 32];
-    // chunked execution runs loop bodies past the stop; they must not count
-    if (mode == CTL_LOOP && b.st->done) {
-        if (has_handle && threadIdx.x == 0) cudaGraphSetConditional(h, 0u);
-        return;
-    }
-    control_body(b, mode, h, has_handle, sh, energy_partials(b));
-}
-
-// The reductions of (F, v) and the control step of k_control in one
-// launch (nb_red blocks): every block writes its partials, and the last
+// The reductions of (F, v) and the control step in one launch (nb_red
+// blocks): every block writes its partials, and the last
 // block to finish (a ticket counter, reset by that block) runs the control
 // step on all of them.  No block waits for another.
 __global__ void k_reduce_ctl(Bufs b, int mode, cudaGraphConditionalHandle h, int has_handle) {

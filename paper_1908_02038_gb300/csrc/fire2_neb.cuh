@@ -20,11 +20,12 @@
 // arrays (N = img_n); the two fixed end states sit in `end` (2 N).  Per
 // iteration, after the force passes (which also write per-atom energies):
 //   k_neb_sums    per image and block: E, |t+|^2, |t-|^2 (unmasked, for the
-//                 springs), |t+m|^2, |t-m|^2, t+m.t-m, F.t+m, F.t-m (masked)
-//   k_neb_scalars one block: fixed-order sums, climbing image, tangent
-//                 weights, the per-image coefficients of F^NEB = F + s t
+//                 springs), |t+m|^2, |t-m|^2, t+m.t-m, F.t+m, F.t-m (masked);
+//                 its last block (ticket) then the fixed-order sums, climbing
+//                 image, tangent weights and the per-image coefficients of
+//                 F^NEB = F + s t (neb_scalars)
 //   k_neb_project F^NEB per atom, written over F, plus the FP64 reductions of
-//                 (F^NEB, v) that k_control reads
+//                 (F^NEB, v); its last block runs the control step
 #pragma once
 
 #include "fire2_device.cuh"
@@ -70,9 +71,13 @@ __device__ __forceinline__ unsigned neb_mask(const Bufs& b, size_t gi) {
     return b.dofmask ? (unsigned)b.dofmask[gi] : 0u;
 }
 
-// grid (nb, n_img)
+__device__ void neb_scalars(const Bufs& b, const NebC& c, double* sums);
+
+// grid (nb, n_img); dynamic shared memory: n_img x kNebSums doubles
 __global__ void __launch_bounds__(kNebBlock) k_neb_sums(Bufs b, GeoC g, NebC c) {
-    __shared__ double red[32];
+    __shared__ double red[kNebSums * 32];
+    __shared__ int last;
+    extern __shared__ double sums[];   // n_img x kNebSums (last block)
     if (b.st->done) return;
     const int img = blockIdx.y;
     double acc[kNebSums] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -99,17 +104,45 @@ __global__ void __launch_bounds__(kNebBlock) k_neb_sums(Bufs b, GeoC g, NebC c) 
             acc[7] += fv[d] * tm[d];
         }
     }
-    for (int q = 0; q < kNebSums; ++q) {
-        const double v = block_sum(acc[q], red);
-        if (threadIdx.x == 0) c.part[((size_t)img * kNebSums + q) * c.nb + blockIdx.x] = v;
+    // the eight block sums: two transposing butterflies per warp (warp_sum4),
+    // then over the warps in warp 0, in a fixed order
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const double s0 = warp_sum4(acc[0], acc[1], acc[2], acc[3]);
+    const double s1 = warp_sum4(acc[4], acc[5], acc[6], acc[7]);
+    if ((lane & 7) == 0) {
+        red[(lane >> 3) * 32 + w] = s0;
+        red[(4 + (lane >> 3)) * 32 + w] = s1;
     }
+    __syncthreads();
+    if (w == 0) {
+        const bool in = lane < (int)(blockDim.x >> 5);
+        double t[kNebSums];
+#pragma unroll
+        for (int q = 0; q < kNebSums; ++q) t[q] = in ? red[q * 32 + lane] : 0.0;
+        const double u0 = warp_sum4(t[0], t[1], t[2], t[3]);
+        const double u1 = warp_sum4(t[4], t[5], t[6], t[7]);
+        if ((lane & 7) == 0) {
+            double* o = c.part + (size_t)img * kNebSums * c.nb + blockIdx.x;
+            o[(size_t)(lane >> 3) * c.nb] = u0;
+            o[(size_t)(4 + (lane >> 3)) * c.nb] = u1;
+        }
+    }
+    // the last block of the grid runs the band's scalars on all partials
+    if (threadIdx.x == 0) {
+        __threadfence();   // this block's partials before its ticket
+        const unsigned nblk = gridDim.x * gridDim.y;
+        last = atomicAdd(&b.st->neb_blocks, 1u) == nblk - 1 ? 1 : 0;
+    }
+    __syncthreads();
+    if (!last) return;
+    if (threadIdx.x == 0) b.st->neb_blocks = 0u;
+    __threadfence();       // every other block's partials are visible from here
+    neb_scalars(b, c, sums);
 }
 
-// One block; warp w reduces the partials of images w, w + 32, ... in a fixed
+// One block; warp w reduces the partials of images w, w + nw, ... in a fixed
 // order, then thread 0 picks the climbing image and sets the coefficients.
-__global__ void k_neb_scalars(Bufs b, NebC c) {
-    extern __shared__ double sums[];   // n_img x kNebSums
-    if (b.st->done) return;
+__device__ void neb_scalars(const Bufs& b, const NebC& c, double* sums /* n_img x kNebSums */) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int img = warp; img < c.n_img; img += nw)
         for (int q = 0; q < kNebSums; ++q) {
@@ -173,10 +206,19 @@ __global__ void k_neb_scalars(Bufs b, NebC c) {
 }
 
 // grid-stride over all n_img x img_n atoms: F^NEB = mask(F + s t) written
-// over F, then the (F^NEB, v) reductions (with the velocity-Verlet half kick)
-__global__ void __launch_bounds__(kNebBlock) k_neb_project(Bufs b, GeoC g, NebC c) {
+// over F, then the (F^NEB, v) reductions (with the velocity-Verlet half
+// kick); the last block (ticket) runs the control step on all partials, as
+// k_reduce_ctl does for single systems.
+__global__ void __launch_bounds__(kNebBlock) k_neb_project(Bufs b, GeoC g, NebC c, int mode,
+                                                           cudaGraphConditionalHandle h,
+                                                           int has_handle) {
     __shared__ double red[kRedRows * 32];
-    if (b.st->done) return;
+    __shared__ int last;
+    if (b.st->done) {   // chunked loop bodies past the stop
+        if (mode == CTL_LOOP && has_handle && blockIdx.x == 0 && threadIdx.x == 0)
+            cudaGraphSetConditional(h, 0u);
+        return;
+    }
     const double vvh = vv_half_of(b.st);
     RedAcc acc;
     const int total = c.n_img * c.img_n;
@@ -197,6 +239,15 @@ __global__ void __launch_bounds__(kNebBlock) k_neb_project(Bufs b, GeoC g, NebC 
         red_atom(b, gi, f, b.v[gi], vvh, acc);
     }
     red_write(acc, red, b.rpart);
+    if (threadIdx.x == 0) {
+        __threadfence();   // this block's partials before its ticket
+        last = atomicAdd(&b.st->red_blocks, 1u) == gridDim.x - 1 ? 1 : 0;
+    }
+    __syncthreads();
+    if (!last) return;
+    if (threadIdx.x == 0) b.st->red_blocks = 0u;
+    __threadfence();       // every other block's partials are visible from here
+    control_body(b, mode, h, has_handle, red, energy_partials(b));
 }
 
 }  // namespace fire2
