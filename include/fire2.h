@@ -271,9 +271,15 @@ typedef enum {
                                    cannot look inside conditional graphs) */
 } fire_exec_mode;
 
-/* Selects the execution mode of later fire_minimize* calls on h; chunk is the
- * number of iterations per graph launch in FIRE_EXEC_CHUNKED (1..4096,
- * ignored otherwise).  Results do not depend on the mode.  The paper has no
+/* Selects the execution mode of later fire_minimize* calls on h.  chunk is,
+ * in FIRE_EXEC_CHUNKED, the number of iterations per graph launch (1..4096);
+ * in FIRE_EXEC_GRAPH_WHILE, the number of iterations per launch of the WHILE
+ * node's body (0..64): 1 puts the list build and the FP64 confirming passes
+ * of FP32-pair handles under conditional IF nodes; more puts that many
+ * iterations in the body, with the build and the confirming passes launched
+ * in every iteration and returning at once unless due (iterations past the
+ * stop return at once too); 0 (the default) takes 8 below 262,144 atoms and 1
+ * from there.  Results do not depend on the mode.  The paper has no
  * counterpart (it describes the loop of Algorithm 2, not how it is driven).
  * Errors: FIRE_ERR_ARG. */
 fire_status fire_set_exec_mode(fire_handle_t* h, int32_t mode, int32_t chunk);

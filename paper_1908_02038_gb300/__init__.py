@@ -230,7 +230,11 @@ def fire_set_dof_mask(handle, mask) -> None:
     _check(load_library().fire_set_dof_mask(handle, m.ctypes.data_as(C.c_void_p)), handle)
 
 
-def fire_set_exec_mode(handle, mode: int, chunk: int = 32) -> None:
+def fire_set_exec_mode(handle, mode: int, chunk: int | None = None) -> None:
+    """chunk: iterations per graph launch (chunked mode, default 32) or per
+    WHILE-body launch (graph mode, default 0 = automatic)."""
+    if chunk is None:
+        chunk = 32 if mode == FIRE_EXEC_CHUNKED else 0
     _check(load_library().fire_set_exec_mode(handle, int(mode), int(chunk)), handle)
 
 
@@ -591,7 +595,7 @@ class FireHandle:
     def set_rgl_params(self, theta):
         fire_set_rgl_params(self.h, theta)
 
-    def set_exec_mode(self, mode, chunk=32):
+    def set_exec_mode(self, mode, chunk=None):
         fire_set_exec_mode(self.h, mode, chunk)
 
     def set_threads_per_atom(self, tpa=0):
@@ -678,7 +682,7 @@ class FireNEB:
             raise ValueError("the mask holds one byte per atom of an image")
         fire_set_dof_mask(self.h, mask)
 
-    def set_exec_mode(self, mode, chunk=32):
+    def set_exec_mode(self, mode, chunk=None):
         fire_set_exec_mode(self.h, mode, chunk)
 
     def set_threads_per_atom(self, tpa=0):

@@ -93,6 +93,7 @@ struct fire_handle {
     double budget_s = 3600.0;
     int exec_mode = FIRE_EXEC_GRAPH_WHILE;
     int chunk = 32;                  // iterations per graph launch, chunked mode
+    int body_iters = 0;              // iterations per WHILE-body launch, graph mode (0: auto)
     cudaGraphExec_t exec_init = nullptr, exec_chunk = nullptr, exec_final = nullptr;
     fire_batch_state* batch = nullptr;   // set for handles made by fire_batch_init
     GradState grad;
@@ -585,9 +586,10 @@ cudaError_t add_conditional(cudaStream_t s, cudaGraphConditionalHandle hc,
 //     forces, reductions, control (sets the WHILE condition)
 //   finalize
 // Small systems: iterations per WHILE-body launch, and the size below which
-// the body holds that many (build_graph).
+// the body holds that many (build_graph; fire_set_exec_mode can set it).
 constexpr int kLoopUnroll = 8;
 constexpr int kUnrollMaxAtoms = 262144;
+constexpr int kMaxBodyIters = 64;
 
 fire_status build_graph(fire_handle* h, const GeoC& g) {
     drop_graph(h);
@@ -620,7 +622,8 @@ fire_status build_graph(fire_handle* h, const GeoC& g) {
     // launches (graph loop, per iteration: LJ 255 atoms 41.3 -> 33.4 us,
     // RGL 3,957 atoms 45.7 -> 42.6 us, 31,647 atoms 77.0 -> 75.0 us; 1M atoms
     // 808.7 against 810.8 us).  Iterations past the stop return at once.
-    const int unroll = h->n < kUnrollMaxAtoms ? kLoopUnroll : 1;
+    const int unroll = h->body_iters > 0 ? h->body_iters
+                                         : (h->n < kUnrollMaxAtoms ? kLoopUnroll : 1);
     if (e == cudaSuccess && unroll > 1) {
         e = cudaStreamBeginCaptureToGraph(h->cap1, body, nullptr, nullptr, 0,
                                           cudaStreamCaptureModeRelaxed);
@@ -1372,9 +1375,12 @@ fire_status fire_set_exec_mode(fire_handle_t* h, int32_t mode, int32_t chunk) {
         return fail(h, FIRE_ERR_ARG, "unknown execution mode %d", mode);
     if (mode == FIRE_EXEC_CHUNKED && (chunk < 1 || chunk > 4096))
         return fail(h, FIRE_ERR_ARG, "chunk must be in [1, 4096]");
+    if (mode == FIRE_EXEC_GRAPH_WHILE && (chunk < 0 || chunk > kMaxBodyIters))
+        return fail(h, FIRE_ERR_ARG, "iterations per loop body must be in [0, %d]", kMaxBodyIters);
     drop_graph(h);
     h->exec_mode = mode;
     if (mode == FIRE_EXEC_CHUNKED) h->chunk = chunk;
+    else h->body_iters = chunk;
     return FIRE_OK;
 }
 

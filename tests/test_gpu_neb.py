@@ -62,15 +62,16 @@ def test_neb_small_box_matches_oracle(climb):
     assert (E[3] - E[0] > 0.5) if climb else (E.max() - E[0] > 0.5)
 
 
-@pytest.mark.parametrize("mode", [fg.FIRE_EXEC_GRAPH_WHILE, fg.FIRE_EXEC_CHUNKED])
-def test_neb_cell_list_box_matches_oracle(mode):
+@pytest.mark.parametrize("mode,chunk", [(fg.FIRE_EXEC_GRAPH_WHILE, 0), (fg.FIRE_EXEC_GRAPH_WHILE, 1),
+                                        (fg.FIRE_EXEC_CHUNKED, 16)])
+def test_neb_cell_list_box_matches_oracle(mode, chunk):
     # 6^3 cells: the list build runs in cell mode, each image in its own cells
     c, path = hop_path(6, 7, seed=8, mode=oracle.FORCE_CELLS)
     po, ro, Eo, clo = oracle.neb(path, c.box, ora_rgl(), oracle.Params(dt_start=fi.CU_DT),
                                  fi.CU_MASS, 2.0, True, 1e-6, 100000, mode=oracle.FORCE_CELLS)
     p = path.copy()
     with fg.FireNEB(7, path.shape[1], fi.CU_MASS, rgl_pot(), 2.0, True, dt_start=fi.CU_DT) as h:
-        h.set_exec_mode(mode, 16)
+        h.set_exec_mode(mode, chunk)
         r, E, cl = h.minimize(p, c.box, 1e-6, 100000)
     assert_neb_parity(c, r, E, cl, ro, Eo, clo, 7)
     assert cl == 4

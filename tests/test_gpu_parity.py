@@ -319,23 +319,39 @@ def test_chunked_execution_matches_graph_loop():
 @pytest.mark.parametrize("check", [fg.FIRE_FP64_CHECK_CONFIRM, fg.FIRE_FP64_CHECK_FINISH])
 def test_fp32pair_graph_and_chunked_runs_are_identical(check):
     # The FP32-pair passes write whole forces and sum in a fixed order, so the
-    # graph loop (rebuild decided by the update kernel's last block, build
-    # chain under an IF node) and the chunked loop (every build kernel tests
-    # the displacement itself) must follow the same trajectory bit for bit.
+    # graph loop with one iteration per body (rebuild decided by the update
+    # kernel's last block, build chain and confirming passes under IF nodes),
+    # with several iterations per body (8 and 3: build and confirming passes
+    # gated in their kernels, iterations past the stop returning at once) and
+    # the chunked loop must follow the same trajectory bit for bit.
     c = fi.rgl_vacancy_box(ncell=12, seed=14, n_vac=4, sigma=0.1)
     pot = rgl_pot(precision=fg.FIRE_PREC_FP32_PAIR)
+    runs = []
     with fg.FireHandle(c.n, fi.CU_MASS, pot, dt_start=fi.CU_DT, confirm64=check) as h:
-        x1 = c.x.copy()
-        r1 = h.minimize(x1, c.box, 1e-6, 100000)
-        h.set_exec_mode(fg.FIRE_EXEC_CHUNKED, 16)
-        x2 = c.x.copy()
-        r2 = h.minimize(x2, c.box, 1e-6, 100000)
-    assert r1.stop == r2.stop == fg.FIRE_STOP_FTOL
+        for mode, chunk in ((fg.FIRE_EXEC_GRAPH_WHILE, 1), (fg.FIRE_EXEC_GRAPH_WHILE, 8),
+                            (fg.FIRE_EXEC_GRAPH_WHILE, 3), (fg.FIRE_EXEC_CHUNKED, 16)):
+            h.set_exec_mode(mode, chunk)
+            x = c.x.copy()
+            runs.append((x, h.minimize(x, c.box, 1e-6, 100000)))
+    x1, r1 = runs[0]
+    assert r1.stop == fg.FIRE_STOP_FTOL
     assert r1.nbr_builds > 2
-    assert (r1.iterations, r1.nbr_builds, r1.force_evals) == (r2.iterations, r2.nbr_builds,
-                                                               r2.force_evals)
-    assert r1.energy == r2.energy
-    assert np.array_equal(x1, x2)
+    for x2, r2 in runs[1:]:
+        assert r2.stop == fg.FIRE_STOP_FTOL
+        assert (r1.iterations, r1.nbr_builds, r1.force_evals) == (r2.iterations, r2.nbr_builds,
+                                                                   r2.force_evals)
+        assert r1.energy == r2.energy
+        assert np.array_equal(x1, x2)
+
+
+def test_loop_body_setting_rejects_bad_values():
+    c = fi.rgl_vacancy_box(ncell=5, seed=12, n_vac=2)
+    with fg.FireHandle(c.n, fi.CU_MASS, rgl_pot(), dt_start=fi.CU_DT) as h:
+        for mode, chunk in ((fg.FIRE_EXEC_GRAPH_WHILE, -1), (fg.FIRE_EXEC_GRAPH_WHILE, 65),
+                            (fg.FIRE_EXEC_CHUNKED, 0), (fg.FIRE_EXEC_CHUNKED, 4097), (2, 1)):
+            with pytest.raises(fg.FireError) as e:
+                h.set_exec_mode(mode, chunk)
+            assert e.value.status == fg.FIRE_ERR_ARG
 
 
 # ----------------------------------------------------------------------------
@@ -539,14 +555,15 @@ def test_dmax_state_after_60_iterations_matches_oracle(integ):
     assert r.energy == pytest.approx(ro.energy, rel=1e-12)
 
 
-@pytest.mark.parametrize("mode", [fg.FIRE_EXEC_GRAPH_WHILE, fg.FIRE_EXEC_CHUNKED])
-def test_dmax_relaxation_parity(mode):
+@pytest.mark.parametrize("mode,chunk", [(fg.FIRE_EXEC_GRAPH_WHILE, 0), (fg.FIRE_EXEC_GRAPH_WHILE, 1),
+                                        (fg.FIRE_EXEC_CHUNKED, 16)])
+def test_dmax_relaxation_parity(mode, chunk):
     c = fi.rgl_vacancy_box(ncell=5, seed=92, n_vac=2, sigma=0.1)
     xo, ro, _ = oracle.fire2(c.x, c.box, ora_rgl(), oracle.Params(dt_start=fi.CU_DT, dmax=0.002),
                              fi.CU_MASS, 1e-6, 100000)
     x = c.x.copy()
     with fg.FireHandle(c.n, fi.CU_MASS, rgl_pot(), dt_start=fi.CU_DT, dmax=0.002) as h:
-        h.set_exec_mode(mode, 16)
+        h.set_exec_mode(mode, chunk)
         r = h.minimize(x, c.box, 1e-6, 100000)
     assert_relax_parity(c, r, ro, 1e-6)
 

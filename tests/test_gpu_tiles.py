@@ -99,13 +99,15 @@ def test_tiled_forces_open_axis_match_oracle():
     assert e == pytest.approx(eo, rel=E_REL)
 
 
-@pytest.mark.parametrize("exec_mode", [fg.FIRE_EXEC_GRAPH_WHILE, fg.FIRE_EXEC_CHUNKED])
-def test_tiled_relaxation_32k_parity(exec_mode, oracle_32k):
+@pytest.mark.parametrize("exec_mode,chunk", [(fg.FIRE_EXEC_GRAPH_WHILE, 1),
+                                             (fg.FIRE_EXEC_GRAPH_WHILE, 0),
+                                             (fg.FIRE_EXEC_CHUNKED, 32)])
+def test_tiled_relaxation_32k_parity(exec_mode, chunk, oracle_32k):
     c, xo, ro = oracle_32k
     x = c.x.copy()
     with fg.FireHandle(c.n, fi.CU_MASS, rgl_pot(), dt_start=fi.CU_DT) as h:
         h.set_pair_tiles(fg.FIRE_TILES_ON)
-        h.set_exec_mode(exec_mode, 32)
+        h.set_exec_mode(exec_mode, chunk)
         r = h.minimize(x, c.box, 1e-6, 100000)
     assert r.stop == fg.FIRE_STOP_FTOL and r.fmax_atom < 1e-6
     assert r.force_evals == r.iterations + 1 and r.nbr_builds >= 1
