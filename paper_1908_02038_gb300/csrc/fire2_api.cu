@@ -193,11 +193,11 @@ int auto_tpa(const fire_potential_t& p, long long n, int sms) {
 // Whether the FP64 half-list passes of this geometry run on tiles: the FP64
 // table form on a half list, cell mode, one system, and tiles asked for.
 // FIRE_TILES_AUTO takes the untiled passes: on GB300 the tiled ones remove
-// the FP64 additions and L2 atomics of the neighbour terms (FP64 pipe 64 % ->
-// 2 %, L2 56 % -> 7 % in the force pass) but both passes are bound by the
+// the FP64 additions and L2 atomics of the neighbour terms (FP64 pipe 62 % ->
+// 3 %, L2 40 % -> 8 % in the force pass) but both passes are bound by the
 // issue of their double-float arithmetic, and the tiles' staging, barriers
 // and fixed-point splits cost more issue than they save (1M-atom box: force
-// 0.60-0.62 ms against 0.51, density 0.44 against 0.34 over four tile shapes).
+// 0.49 ms against 0.41, density 0.38 against 0.29).
 bool tiles_wanted(const fire_handle* h, const GeoC& g) {
     if (!fixed64_half(h->pot) || g.brute || h->neb || g.img_n != h->n) return false;
     return h->tile_mode == FIRE_TILES_ON;

@@ -219,6 +219,24 @@ def test_maxiter_stop_matches_oracle_state():
     assert np.abs(x - xo).max() < 1e-9
 
 
+@pytest.mark.parametrize("body", [1, 3, 8])
+def test_maxiter_stop_with_every_loop_body(body):
+    # 61 iterations: not a multiple of the bodies' lengths, so the last body
+    # launch runs iterations past the stop, which must leave the state alone
+    c = fi.rgl_vacancy_box(ncell=4, seed=3, n_vac=2)
+    xo, ro, _ = oracle.fire2(c.x, c.box, ora_rgl(), oracle.Params(dt_start=fi.CU_DT), fi.CU_MASS,
+                             1e-12, 61)
+    x = c.x.copy()
+    with fg.FireHandle(c.n, fi.CU_MASS, rgl_pot(), dt_start=fi.CU_DT) as h:
+        h.set_exec_mode(fg.FIRE_EXEC_GRAPH_WHILE, body)
+        r = h.minimize(x, c.box, 1e-12, 61)
+    assert r.stop == fg.FIRE_STOP_MAXITER == ro.stop
+    assert r.iterations == 61 and r.force_evals == 62
+    assert r.dt_final == pytest.approx(ro.dt_final, rel=1e-12)
+    assert r.alpha_final == pytest.approx(ro.alpha_final, rel=1e-12)
+    assert np.abs(x - xo).max() < 1e-9
+
+
 def test_nonfinite_positions_rejected_and_untouched():
     c = fi.lj_fcc_vacancy(seed=1)
     x = c.x.copy()
