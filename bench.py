@@ -249,15 +249,42 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm), "sampled_gpu": self.smi_id}
 
 
+def _strip_comments(src):
+    """C/CUDA source without comments and with whitespace collapsed, so that
+    an edit to a comment or to the layout leaves the hash unchanged."""
+    out, i, n = [], 0, len(src)
+    while i < n:
+        c = src[i]
+        if src.startswith("//", i):
+            j = src.find("\n", i)
+            i = n if j < 0 else j
+        elif src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            out.append(" ")
+        elif c in "\"'":   # string or character literal, copied whole
+            j = i + 1
+            while j < n and src[j] != c:
+                j += 2 if src[j] == "\\" else 1
+            out.append(src[i:j + 1])
+            i = j + 1
+        else:
+            out.append(c)
+            i += 1
+    return " ".join("".join(out).split())
+
+
 def _device_src_hash():
-    """Hash of every kernel source (csrc/*.cu, *.cuh): ncu figures recorded
-    under another hash describe other code."""
+    """Hash of the code of every kernel source (csrc/*.cu, *.cuh; comments
+    and whitespace left out): ncu figures recorded under another hash
+    describe other code."""
     import glob
     import hashlib
     h = hashlib.sha256()
-    for path in sorted(glob.glob(os.path.join(ROOT, "paper_1908_02038_gb300", "csrc", "*.cu*"))):
+    paths = glob.glob(os.path.join(ROOT, "paper_1908_02038_gb300", "csrc", "*.cu*"))
+    for path in sorted(paths, key=os.path.basename):
         h.update(os.path.basename(path).encode())
-        h.update(open(path, "rb").read())
+        h.update(_strip_comments(open(path, encoding="utf-8").read()).encode())
     return h.hexdigest()[:16]
 
 
