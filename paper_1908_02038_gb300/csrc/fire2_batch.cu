@@ -381,10 +381,10 @@ __device__ __forceinline__ double b_forces(const BArgs& a, const BInst& I, int l
                     c[1] = f64_to_ff(dg * rinv);
                 }
                 const float2 fpj2 = a.fpff[I.off + (int)(e & kIdxMask)];
-                const ffloat fs = ff_add(c[0], ff_mul(ff_add(fpi, {fpj2.x, fpj2.y}), c[1]));
-                fx = ff_acc(fx, ff_mul(fs, dx));
-                fy = ff_acc(fy, ff_mul(fs, dy));
-                fz = ff_acc(fz, ff_mul(fs, dz));
+                const ffloat fs = ff_madd(ff_add(fpi, {fpj2.x, fpj2.y}), c[1], c[0]);
+                fx = ff_acc(fx, ff_mul_nn(fs, dx));
+                fy = ff_acc(fy, ff_mul_nn(fs, dy));
+                fz = ff_acc(fz, ff_mul_nn(fs, dz));
             }
             a.f[gi] = make_dvec4(ff_to_f64(fx), ff_to_f64(fy), ff_to_f64(fz), 0.0);
         } else {

@@ -1132,8 +1132,9 @@ __global__ void __launch_bounds__(BLK) k_force_ff(Bufs b, PotC P, GeoC g) {
             c[0] = f64_to_ff(2.0 * dphi * rinv);
             c[1] = f64_to_ff(dg * rinv);
         }
-        const ffloat fs = ff_add(c[0], ff_mul(ff_add(fpi, fp_load(qj)), c[1]));
-        const ffloat tx = ff_mul(fs, dx), ty = ff_mul(fs, dy), tz = ff_mul(fs, dz);
+        const ffloat fs = ff_madd(ff_add(fpi, fp_load(qj)), c[1], c[0]);
+        // unnormalised products: ff_acc and ff_to_f64 take any pair
+        const ffloat tx = ff_mul_nn(fs, dx), ty = ff_mul_nn(fs, dy), tz = ff_mul_nn(fs, dz);
         fx = ff_acc(fx, tx);
         fy = ff_acc(fy, ty);
         fz = ff_acc(fz, tz);

@@ -366,10 +366,27 @@ __host__ __device__ __forceinline__ ffloat ff_mul(ffloat a, ffloat b) {
     const float e = fmaf(a.hi, b.hi, -p);
     return fast_two_sum(p, fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e)));
 }
-__host__ __device__ __forceinline__ ffloat ff_mul_f(ffloat a, float b) {
+// a b as an unnormalised pair (p, t): p = fl(a.hi b.hi), t its error plus
+// the cross terms, |t| ~ 2^-23 |p|; exact input for ff_acc, ff_to_f64 and
+// the TwoSum of ff_madd, which take any pair
+__host__ __device__ __forceinline__ ffloat ff_mul_nn(ffloat a, ffloat b) {
+    const float p = mul_rn(a.hi, b.hi);
+    return {p, fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, fmaf(a.hi, b.hi, -p)))};
+}
+// c + a b with one renormalisation: the product's error and cross terms
+// join the low part of the TwoSum of c.hi and fl(a.hi b.hi) (a.lo b.lo
+// dropped, as in ff_mul); 15 FP32 instructions against 18 for
+// ff_add(c, ff_mul(a, b)), the same error bound
+__host__ __device__ __forceinline__ ffloat ff_madd(ffloat a, ffloat b, ffloat c) {
+    const ffloat p = ff_mul_nn(a, b);
+    const ffloat s = two_sum(c.hi, p.hi);
+    return fast_two_sum(s.hi, add_rn(s.lo, add_rn(c.lo, p.lo)));
+}
+// c + a b for a float b
+__host__ __device__ __forceinline__ ffloat ff_madd_f(ffloat a, float b, ffloat c) {
     const float p = mul_rn(a.hi, b);
-    const float e = fmaf(a.hi, b, -p);
-    return fast_two_sum(p, fmaf(a.lo, b, e));
+    const ffloat s = two_sum(c.hi, p);
+    return fast_two_sum(s.hi, add_rn(s.lo, add_rn(c.lo, fmaf(a.lo, b, fmaf(a.hi, b, -p)))));
 }
 __host__ __device__ __forceinline__ double ff_to_f64(ffloat a) {
     return f32_to_f64(a.hi) + f32_to_f64(a.lo);
@@ -422,11 +439,12 @@ __device__ __forceinline__ void rgl_embed_dd(double rho, double& sq, double& fp,
 }
 
 // One quintic of a row: c = 9 floats (see the layout above), s as a float pair.
+// Horner steps c_k + s r as fused double-float multiply-adds.
 __host__ __device__ __forceinline__ ffloat ff_poly(const float* c, ffloat s) {
     const float q = fmaf(fmaf(c[8], s.hi, c[7]), s.hi, c[6]);
-    ffloat r = ff_add({c[4], c[5]}, ff_mul_f(s, q));
-    r = ff_add({c[2], c[3]}, ff_mul(s, r));
-    return ff_add({c[0], c[1]}, ff_mul(s, r));
+    ffloat r = ff_madd_f(s, q, {c[4], c[5]});
+    r = ff_madd(s, r, {c[2], c[3]});
+    return ff_madd(s, r, {c[0], c[1]});
 }
 
 __host__ __device__ __forceinline__ ffloat ff_neg(ffloat a) { return {-a.hi, -a.lo}; }

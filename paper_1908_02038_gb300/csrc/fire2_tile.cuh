@@ -474,7 +474,8 @@ __global__ void __launch_bounds__(kTileThreads, kTileMinBlocks) k_force_tile(Buf
                     c[0] = f64_to_ff(2.0 * dphi * rinv);
                     c[1] = f64_to_ff(dg * rinv);
                 }
-                const ffloat fs = ff_add(c[0], ff_mul(ff_add(fpi, {fpj2.x, fpj2.y}), c[1]));
+                const ffloat fs = ff_madd(ff_add(fpi, {fpj2.x, fpj2.y}), c[1], c[0]);
+                // normalised products, as fx_split_pair assumes
                 const ffloat t[3] = {ff_mul(fs, dx), ff_mul(fs, dy), ff_mul(fs, dz)};
                 fx = ff_acc(fx, t[0]);
                 fy = ff_acc(fy, t[1]);
