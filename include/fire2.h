@@ -285,12 +285,13 @@ typedef enum {
 fire_status fire_set_exec_mode(fire_handle_t* h, int32_t mode, int32_t chunk);
 
 /* Threads per atom in the RGL pair passes of the FP64 table form and of the
- * FP32-pair form with exponentials, and in the LJ force pass: tpa = 1, 2, 4
- * or 8, or 0 for the
+ * FP32-pair form with exponentials, and in the LJ force pass: tpa = 1, 2, 4,
+ * 8, 16 or 32, or 0 for the
  * automatic choice, which handles start with (the fewest that give a pass at
- * least 1024 threads per SM in the FP64 form, 512 in the FP32-pair form: on a
- * 152-SM device one thread per atom from about 155,000 and 78,000 atoms, 8
- * below about 39,000 and 19,000).  The threads of an atom
+ * least 1024 threads per SM in the FP64 form, 512 in the FP32-pair form, at
+ * most 8 for RGL and 32 for LJ: on a 152-SM device one thread per atom from
+ * about 155,000 and 78,000 atoms, 8 below about 39,000 and 19,000, and for
+ * LJ 32 below about 4,900 atoms).  The threads of an atom
  * take every tpa-th entry of its neighbour list and their partial sums are
  * added in FP64, so results change only in the rounding of the per-atom sums
  * (far below the FP64 form's 1e-10 relative force error).  Other forms run

@@ -171,23 +171,30 @@ bool tpa_form(const fire_potential_t& p) {
             p.pair_eval == FIRE_PAIR_ANALYTIC);
 }
 
-constexpr int kMaxTpa = 8;
+constexpr int kMaxTpa = 32;
+constexpr int kMaxHvpTpa = 8;   // the Hessian-vector product passes
 
-// Threads per atom chosen when the caller sets none: the fewest (1, 2, 4 or
-// 8) that give a pair pass at least 1024 threads per SM in the FP64 table
-// form, 512 in the FP32-pair form.  Measured on GB300 (152 SMs, us per
-// iteration at 1 / 2 / 4 / 8 threads per atom): FP64 form 3,751 atoms
-// 110 / 94 / 78 / 57, 29,931 atoms 116 / 104 / 93 / 90, 59,762 atoms
-// 135 / 126 / 119 / 122, 128,277 atoms 187 / 194 / 189 / 204, 997,450 atoms
-// 986 / 1031 / 1090 / 1307; FP32-pair form 29,931 atoms 108 / 81 / 73 / 78,
-// 59,762 atoms 115 / 92 / 92 / 102, 997,450 atoms 652 / 680 / 753 / 963.
-int tpa_for(long long n, int sms, int per_sm) {
+// Threads per atom chosen when the caller sets none: the fewest (1, 2, 4, ...)
+// that give a pair pass at least 1024 threads per SM in the FP64 forms, 512
+// in the FP32-pair form, up to 8 for RGL and 32 for LJ.  Measured on GB300
+// (152 SMs, us per iteration at 1 / 2 / 4 / 8 threads per atom): FP64 form
+// 3,751 atoms 110 / 94 / 78 / 57, 29,931 atoms 116 / 104 / 93 / 90, 59,762
+// atoms 135 / 126 / 119 / 122, 128,277 atoms 187 / 194 / 189 / 204, 997,450
+// atoms 986 / 1031 / 1090 / 1307; FP32-pair form 29,931 atoms
+// 108 / 81 / 73 / 78, 59,762 atoms 115 / 92 / 92 / 102, 997,450 atoms
+// 652 / 680 / 753 / 963.  Beyond 8 (us per iteration at 8 / 16 / 32): the
+// RGL passes gain nothing (3,960 atoms, FP64 form 46.4 / 46.7 / 50.3,
+// FP32-pair form 45.8 / 48.9 / 54.3), while the LJ force pass, whose pair
+// terms are FP64 arithmetic at 1/58 of the FP32 rate, spreads them over more
+// SMs (255 atoms 30.7 / 28.0 / 25.8).
+int tpa_for(long long n, int sms, int per_sm, int cap = kMaxTpa) {
     int t = 1;
-    while (t < kMaxTpa && n * t < (long long)sms * per_sm) t *= 2;
+    while (t < cap && n * t < (long long)sms * per_sm) t *= 2;
     return t;
 }
 int auto_tpa(const fire_potential_t& p, long long n, int sms) {
-    return tpa_for(n, sms, p.precision == FIRE_PREC_FP32_PAIR ? 512 : 1024);
+    return tpa_for(n, sms, p.precision == FIRE_PREC_FP32_PAIR ? 512 : 1024,
+                   p.kind == FIRE_POT_LJ ? kMaxTpa : 8);
 }
 
 // Whether the FP64 half-list passes of this geometry run on tiles: the FP64
@@ -393,6 +400,8 @@ template <bool HALF>
 void density_ff(const Bufs& b, const PotC& P, const GeoC& g, cudaStream_t s) {
     const int nb = dens_ff_grid(b.n, b.tpa), bs = dens_ff_block(b.tpa);
     switch (b.tpa) {
+    case 32: k_density_ff<HALF, 32><<<nb, bs, 0, s>>>(b, P, g); break;
+    case 16: k_density_ff<HALF, 16><<<nb, bs, 0, s>>>(b, P, g); break;
     case 8: k_density_ff<HALF, 8><<<nb, bs, 0, s>>>(b, P, g); break;
     case 4: k_density_ff<HALF, 4><<<nb, bs, 0, s>>>(b, P, g); break;
     case 2: k_density_ff<HALF, 2><<<nb, bs, 0, s>>>(b, P, g); break;
@@ -406,6 +415,8 @@ void force_ff(const Bufs& b, const PotC& P, const GeoC& g, cudaStream_t s) {
     constexpr int B1 = 512;
     const long long n = b.n;
     switch (b.tpa) {
+    case 32: k_force_ff<HALF, 32, kForceBlock><<<ceil_div(n * 32, kForceBlock), kForceBlock, 0, s>>>(b, P, g); break;
+    case 16: k_force_ff<HALF, 16, kForceBlock><<<ceil_div(n * 16, kForceBlock), kForceBlock, 0, s>>>(b, P, g); break;
     case 8: k_force_ff<HALF, 8, kForceBlock><<<ceil_div(n * 8, kForceBlock), kForceBlock, 0, s>>>(b, P, g); break;
     case 4: k_force_ff<HALF, 4, kForceBlock><<<ceil_div(n * 4, kForceBlock), kForceBlock, 0, s>>>(b, P, g); break;
     case 2: k_force_ff<HALF, 2, kForceBlock><<<ceil_div(n * 2, kForceBlock), kForceBlock, 0, s>>>(b, P, g); break;
@@ -414,6 +425,8 @@ void force_ff(const Bufs& b, const PotC& P, const GeoC& g, cudaStream_t s) {
 }
 void force_lj(const Bufs& b, const PotC& P, const GeoC& g, cudaStream_t s) {
     switch (b.tpa) {
+    case 32: k_force_lj<32><<<b.nb_force, kForceBlock, 0, s>>>(b, P, g); break;
+    case 16: k_force_lj<16><<<b.nb_force, kForceBlock, 0, s>>>(b, P, g); break;
     case 8: k_force_lj<8><<<b.nb_force, kForceBlock, 0, s>>>(b, P, g); break;
     case 4: k_force_lj<4><<<b.nb_force, kForceBlock, 0, s>>>(b, P, g); break;
     case 2: k_force_lj<2><<<b.nb_force, kForceBlock, 0, s>>>(b, P, g); break;
@@ -422,6 +435,8 @@ void force_lj(const Bufs& b, const PotC& P, const GeoC& g, cudaStream_t s) {
 }
 void density32(const Bufs& b, const PotC& P, const GeoC& g, cudaStream_t s) {
     switch (b.tpa) {
+    case 32: k_density32<32><<<b.nb_force, kForceBlock, 0, s>>>(b, P, g); break;
+    case 16: k_density32<16><<<b.nb_force, kForceBlock, 0, s>>>(b, P, g); break;
     case 8: k_density32<8><<<b.nb_force, kForceBlock, 0, s>>>(b, P, g); break;
     case 4: k_density32<4><<<b.nb_force, kForceBlock, 0, s>>>(b, P, g); break;
     case 2: k_density32<2><<<b.nb_force, kForceBlock, 0, s>>>(b, P, g); break;
@@ -433,6 +448,8 @@ void force32(const Bufs& b, const PotC& P, const GeoC& g, cudaStream_t s) {
     // 0.239 ms with blocks of 128); the pass writes no per-block partials
     constexpr int B1 = 512;
     switch (b.tpa) {
+    case 32: k_force32<32, kForceBlock><<<b.nb_force, kForceBlock, 0, s>>>(b, P, g); break;
+    case 16: k_force32<16, kForceBlock><<<b.nb_force, kForceBlock, 0, s>>>(b, P, g); break;
     case 8: k_force32<8, kForceBlock><<<b.nb_force, kForceBlock, 0, s>>>(b, P, g); break;
     case 4: k_force32<4, kForceBlock><<<b.nb_force, kForceBlock, 0, s>>>(b, P, g); break;
     case 2: k_force32<2, kForceBlock><<<b.nb_force, kForceBlock, 0, s>>>(b, P, g); break;
@@ -1342,8 +1359,8 @@ static fire_status run_minimize(fire_handle* h, const GeoC& g, double ftol, int6
 fire_status fire_set_threads_per_atom(fire_handle_t* h, int32_t tpa, int32_t* chosen) {
     if (!h) return FIRE_ERR_ARG;
     if (h->batch) return fail(h, FIRE_ERR_ARG, "batched handle: use fire_batch_set_tuning");
-    if (tpa != 0 && tpa != 1 && tpa != 2 && tpa != 4 && tpa != kMaxTpa)
-        return fail(h, FIRE_ERR_ARG, "threads per atom must be 0 (automatic), 1, 2, 4 or 8");
+    if (tpa != 0 && tpa != 1 && tpa != 2 && tpa != 4 && tpa != 8 && tpa != 16 && tpa != 32)
+        return fail(h, FIRE_ERR_ARG, "threads per atom must be 0 (automatic), 1, 2, 4, 8, 16 or 32");
     const int t = !tpa_form(h->pot) ? 1 : tpa == 0 ? auto_tpa(h->pot, h->n, h->sms) : tpa;
     if (t != h->b.tpa) {
         drop_graph(h);
@@ -1676,7 +1693,7 @@ fire_status fire_rgl_energy_grad_dev(fire_handle_t* h, const double* d_pos, cons
 static void launch_hvp(fire_handle* h, const GradBufs& b, const PotC& pc, const double box[3],
                        const double* u, double* hu, cudaStream_t s) {
     GeoL L{{box[0], box[1], box[2]}};
-    const int tpa = tpa_for(h->n, h->sms, 1024);   // small systems: split the lists
+    const int tpa = tpa_for(h->n, h->sms, 1024, kMaxHvpTpa);   // small systems: split the lists
     const int nb = ceil_div((long long)h->n * tpa, kForceBlock);
     const double* et = h->b.exp_table;
     switch (tpa) {
@@ -1827,7 +1844,7 @@ fire_status fire_rgl_implicit_grad_dev(fire_handle_t* h, const double* d_pos, co
     const int* skip = &gs.cs->done;
     // the cached HVP passes are FP64 pair loops like the force passes: split
     // each atom's list over several threads on small systems
-    const int tpa = tpa_for(n, h->sms, 1024);
+    const int tpa = tpa_for(n, h->sms, 1024, kMaxHvpTpa);
     constexpr int kCgBatch = 16;
     int done = c0.done;
     // the kCgBatch iterations between two reads of the state form one CUDA

@@ -115,15 +115,17 @@ __device__ __forceinline__ double warp_max_nonneg(double v) {
 }
 
 // Sum over the TPA consecutive lanes that share one atom in the pair passes
-// (TPA = 1, 2, 4 or 8 threads per atom); every lane of the group receives
+// (TPA = 1, 2, 4, 8, 16 or 32 threads per atom); every lane of the group receives
 // the total.  Only the group's own lanes are named in the mask, so groups
 // whose atom index is past the end may have left the kernel.
 template <int TPA>
 __device__ __forceinline__ double group_sum(double v) {
-    static_assert(TPA == 1 || TPA == 2 || TPA == 4 || TPA == 8, "threads per atom");
+    static_assert(TPA == 1 || TPA == 2 || TPA == 4 || TPA == 8 || TPA == 16 || TPA == 32,
+                  "threads per atom");
     if (TPA > 1) {
         const unsigned lane = threadIdx.x & 31u;
-        const unsigned gmask = ((1u << TPA) - 1u) << (lane & ~(unsigned)(TPA - 1));
+        const unsigned gmask = TPA == 32 ? 0xffffffffu
+                                         : ((1u << (TPA & 31)) - 1u) << (lane & ~(unsigned)(TPA - 1));
 #pragma unroll
         for (int o = TPA / 2; o > 0; o >>= 1) v += __shfl_xor_sync(gmask, v, o, TPA);
     }

@@ -1,6 +1,6 @@
 """Several threads per atom in the RGL pair passes (fire_set_threads_per_atom),
 GPU vs the FP64 oracle through the C ABI.  Splitting an atom's neighbour list
-over 2, 4 or 8 threads only reorders the per-atom sums, so every setting must
+over 2 to 32 threads only reorders the per-atom sums, so every setting must
 meet the one-thread bars: FP64 forces within 1e-10 relative, FP32-pair forces
 within a few 1e-6 eV/A, and relaxations to the oracle's energy and iteration
 count."""
@@ -16,7 +16,7 @@ pytestmark = pytest.mark.gpu
 F_REL = 1e-10
 F32_ABS = 3e-6       # eV/A
 E32_PER_ATOM = 1e-6  # eV/atom
-TPAS = (1, 2, 4, 8)
+TPAS = (1, 2, 4, 8, 16, 32)
 
 FORMS = {
     "fp64_half": dict(precision=fg.FIRE_PREC_FP64, pair_eval=fg.FIRE_PAIR_TABLE,
@@ -105,9 +105,9 @@ def test_full_list_runs_are_identical_for_a_fixed_threads_per_atom():
 def test_threads_per_atom_choice_and_errors():
     c = fi.rgl_vacancy_box(ncell=4, seed=34, n_vac=1)
     with fg.FireHandle(c.n, fi.CU_MASS, rgl_pot("fp64_half"), dt_start=fi.CU_DT) as h:
-        # a few hundred atoms: the automatic choice is the largest
+        # a few hundred atoms: the automatic choice is the largest for RGL
         assert h.set_threads_per_atom(0) == 8
-        for bad in (-1, 3, 16):
+        for bad in (-1, 3, 12, 64):
             with pytest.raises(fg.FireError):
                 h.set_threads_per_atom(bad)
         assert h.set_threads_per_atom(2) == 2
@@ -177,7 +177,7 @@ def test_lj_every_threads_per_atom_matches_oracle():
     eo, fo = oracle.energy_forces(c.x, c.box, opot)
     pot = fg.Potential(fg.FIRE_POT_LJ, eps=1.0, sigma=1.0, rc_lj=2.5, skin=0.3)
     with fg.FireHandle(c.n, fi.LJ_MASS, pot, dt_start=fi.LJ_DT) as h:
-        assert h.set_threads_per_atom(0) == 8   # 255 atoms: the automatic choice
+        assert h.set_threads_per_atom(0) == 32   # 255 atoms: the automatic choice
         for t in TPAS:
             assert h.set_threads_per_atom(t) == t
             e, f = h.energy_forces(c.x, c.box)
