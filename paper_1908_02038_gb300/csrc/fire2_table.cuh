@@ -487,9 +487,12 @@ __host__ __device__ __forceinline__ void ff_row_eval(const float* row, ffloat r2
 // float pair (both parts exact: 24 + 23 bits).
 __host__ __device__ __forceinline__ ffloat fixed_to_ff(long long n) {
     const long long a = n >> 23;                          // floor(n / 2^23)
-    const int b = (int)(n - (a << 23));                   // 0 <= b < 2^23
+    const unsigned b = (unsigned)n & 0x7fffffu;           // n - a 2^23, 0 <= b < 2^23
     const float hi = (float)(int)a * 0x1p-21f;            // 2^(23 - 44)
-    const float lo = (float)b * 0x1p-44f;
+    // b 2^-44 without an integer-to-float conversion: the float with
+    // exponent -21 and significand bits b is 2^-21 (1 + b 2^-23), and taking
+    // 2^-21 from it is exact (Sterbenz)
+    const float lo = add_rn(flt_from_bits((106u << 23) | b), -0x1p-21f);
     return fast_two_sum(hi, lo);   // |hi| >= 2^-21 > lo >= 0, or hi = 0
 }
 
