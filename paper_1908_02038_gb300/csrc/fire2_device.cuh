@@ -837,6 +837,17 @@ __device__ __forceinline__ void red_atom(const Bufs& b, int i, const dvec4& f, d
     a.fin = max_nonneg(a.fin, max_nonneg(abs_bits(f.x), max_nonneg(abs_bits(f.y), abs_bits(f.z))));
 }
 
+// Reductions of the atoms of this thread (grid-stride), with the frozen-DOF
+// mask applied; VV: velocity Verlet's second half kick first.
+template <bool VV>
+__device__ __forceinline__ void red_range(const Bufs& b, double vvh, RedAcc& acc) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < b.n; i += gridDim.x * blockDim.x) {
+        dvec4 f = f_load(b, i);
+        if (mask_force(b, i, f)) f_store(b, i, f.x, f.y, f.z);
+        red_atom(b, i, f, b.v[i], VV ? vvh : 0.0, acc);
+    }
+}
+
 // The block's six reductions written to the partials (kRedRows rows of
 // gridDim.x): sums of P, |F|^2, |v|^2 and of the block's energy terms
 // (warp_sum4), maxima of |F_i|^2 and |F_i,d| (integer maxima); per warp,
@@ -1408,11 +1419,12 @@ __global__ void k_reduce_ctl(Bufs b, int mode, cudaGraphConditionalHandle h, int
         const int e1 = min(ne, (int)(blockIdx.x + 1) * per);
         for (int k = blockIdx.x * per + threadIdx.x; k < e1; k += blockDim.x) acc.E += b.epart[k];
     }
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < b.n; i += gridDim.x * blockDim.x) {
-        dvec4 f = f_load(b, i);
-        if (mask_force(b, i, f)) f_store(b, i, f.x, f.y, f.z);
-        red_atom(b, i, f, b.v[i], vvh, acc);
-    }
+    // the velocity-Verlet test outside the loop: an FP64 comparison per atom
+    // costs as much as a multiply-add on the FP64 pipe, which bounds this pass
+    if (vvh != 0.0)
+        red_range<true>(b, vvh, acc);
+    else
+        red_range<false>(b, 0.0, acc);
     red_write(acc, sh, b.rpart);
     if (threadIdx.x == 0) {
         __threadfence();   // this block's partials before its ticket
