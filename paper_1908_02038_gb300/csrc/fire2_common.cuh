@@ -85,6 +85,15 @@ __device__ __forceinline__ double warp_max(double v) {
     return v;
 }
 
+// max(a, b) of non-negative doubles (NaN propagates: its pattern is larger
+// than that of +inf) and |x|, both on the integer pipes.
+__device__ __forceinline__ double max_nonneg(double a, double b) {
+    return __longlong_as_double(max(__double_as_longlong(a), __double_as_longlong(b)));
+}
+__device__ __forceinline__ double abs_bits(double x) {
+    return __longlong_as_double(__double_as_longlong(x) & 0x7fffffffffffffffll);
+}
+
 // FP64 instructions issue at 1/58 of the FP32 rate on this part and a warp
 // pays for all 32 lanes of each, so the reductions below keep them few.
 //
@@ -512,16 +521,26 @@ __device__ __forceinline__ void fire_update_pre(const FireScal& s, dvec4& x, dve
     }
 }
 
-__device__ __forceinline__ void fire_update_drift(const FireScal& s, double dt, dvec4& x,
-                                                  dvec4& v, const dvec4& f) {
+// KICK: the kick after the drift (explicit Euler, s.kick_after != 0), a
+// choice the caller makes once per pass rather than once per atom
+template <bool KICK>
+__device__ __forceinline__ void fire_update_drift_k(const FireScal& s, double dt, dvec4& x,
+                                                    dvec4& v, const dvec4& f) {
     x.x += dt * v.x;
     x.y += dt * v.y;
     x.z += dt * v.z;
-    if (s.kick_after != 0.0) {   // explicit Euler only
+    if (KICK) {
         v.x += s.kick_after * f.x;
         v.y += s.kick_after * f.y;
         v.z += s.kick_after * f.z;
     }
+}
+__device__ __forceinline__ void fire_update_drift(const FireScal& s, double dt, dvec4& x,
+                                                  dvec4& v, const dvec4& f) {
+    if (s.kick_after != 0.0)   // explicit Euler only
+        fire_update_drift_k<true>(s, dt, x, v, f);
+    else
+        fire_update_drift_k<false>(s, dt, x, v, f);
 }
 
 __device__ __forceinline__ void fire_update_atom(const FireScal& s, dvec4& x, dvec4& v,

@@ -500,12 +500,14 @@ __global__ void k_embed(Bufs b) {
     ffloat emb_ff = {0.f, 0.f};
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < b.n; i += gridDim.x * blockDim.x) {
         const double rho = b.rho[i];
-        if (b.xq64 && rho > 1e-30 && rho < 1e30) {
+        if (b.xq64 && ff_range(rho)) {
             // FP64 form with double-float pair terms: the embedding in float
             // pairs too, F' as a float pair for the force pass (the only
-            // reader of F' in this form) and the energy summed in float pairs
+            // reader of F' in this form) and the energy summed in float
+            // pairs; the range test and the split of rho on the integer
+            // pipes (FP64 instructions issue at 1/58 of the FP32 rate)
             ffloat sqf, fpf;
-            rgl_embed_ff(f64_to_ff(rho), sqf, fpf);
+            rgl_embed_ff(f64_to_ff_int(rho), sqf, fpf);
             fp_store(b, i, fpf);
             emb_ff = ff_acc(emb_ff, {-sqf.hi, -sqf.lo});
             if (b.eatom) b.eatom[i] -= ff_to_f64(sqf);
@@ -796,15 +798,6 @@ struct RedAcc {
     double P = 0.0, F2 = 0.0, V2 = 0.0, fa2 = 0.0, fin = 0.0;
     double E = 0.0;   // the block's slice of the energy partials (k_reduce_ctl)
 };
-
-// max(a, b) of non-negative doubles (NaN propagates: its pattern is larger
-// than that of +inf) and |x|, both on the integer pipes.
-__device__ __forceinline__ double max_nonneg(double a, double b) {
-    return __longlong_as_double(max(__double_as_longlong(a), __double_as_longlong(b)));
-}
-__device__ __forceinline__ double abs_bits(double x) {
-    return __longlong_as_double(__double_as_longlong(x) & 0x7fffffffffffffffll);
-}
 
 // Zeroes the frozen components of f (if any); true when f changed.
 __device__ __forceinline__ bool mask_force(const Bufs& b, int i, dvec4& f) {
@@ -1437,6 +1430,41 @@ __global__ void k_reduce_ctl(Bufs b, int mode, cudaGraphConditionalHandle h, int
     control_body(b, mode, h, has_handle, sh, 0);
 }
 
+// The element-wise step over this thread's atoms (grid-stride); returns the
+// largest squared displacement since the last list build, in FP32: x
+// truncated against the copy rounded at the build, off by < 2 FP32 ulps of
+// the coordinate, far inside the list radius's margin (1e-3 rc + 8 FP32 ulps
+// of the box).  KICK: explicit Euler's kick after the drift.
+template <bool KICK>
+__device__ __forceinline__ float update_range(const Bufs& b, const FireScal& s, double dt,
+                                              int after_pre) {
+    float d2max = 0.f;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < b.n; i += gridDim.x * blockDim.x) {
+        dvec4 x = b.x[i], v = b.v[i];
+        const dvec4 f = f_load(b, i);
+        const float4 r = b.xf[i];    // x at the last build; loaded before the stores
+        if (!after_pre) fire_update_pre(s, x, v, f);
+        fire_update_drift_k<KICK>(s, dt, x, v, f);
+        b.x[i] = x;
+        if (b.xq)
+            b.xq[i] = make_int4(to_fixed(x.x, b.qscale), to_fixed(x.y, b.qscale),
+                                to_fixed(x.z, b.qscale), 0);
+        if (b.xq64)
+            b.xq64[i] = {to_fixed64(x.x, kFixedBits64), to_fixed64(x.y, kFixedBits64),
+                         to_fixed64(x.z, kFixedBits64), 0ll};
+        b.v[i] = v;
+        if (b.accum) {
+            f_store(b, i, 0.0, 0.0, 0.0);
+            if (b.rho) b.rho[i] = 0.0;
+        }
+        const float ddx = f64_to_f32_trunc(x.x) - r.x;
+        const float ddy = f64_to_f32_trunc(x.y) - r.y;
+        const float ddz = f64_to_f32_trunc(x.z) - r.z;
+        d2max = fmaxf(d2max, ddx * ddx + ddy * ddy + ddz * ddz);
+    }
+    return d2max;
+}
+
 // Element-wise part of one iteration: optional half step back and v = 0
 // (P <= 0, Alg. 2), then Algorithm 4: v += dt F / m, mixing
 // v = (1 - alpha) v + alpha |v| F / |F| (P > 0), x += dt v.  Clears F and rho
@@ -1458,35 +1486,10 @@ __device__ void update_body(const Bufs& b, const GeoC& g, const FireScal& s, int
         if (has_if && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(hif, 0u);
         return;
     }
-    // displacement since the last build in FP32: x truncated against the
-    // copy rounded at the build, off by < 2 FP32 ulps of the coordinate, far
-    // inside the list radius's margin (1e-3 rc + 8 FP32 ulps of the box)
-    float d2max = 0.f;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < b.n; i += gridDim.x * blockDim.x) {
-        dvec4 x = b.x[i], v = b.v[i];
-        const dvec4 f = f_load(b, i);
-        const float4 r = b.xf[i];    // x at the last build; loaded before the stores
-        if (after_pre)
-            fire_update_drift(s, dt, x, v, f);
-        else
-            fire_update_atom(s, x, v, f);
-        b.x[i] = x;
-        if (b.xq)
-            b.xq[i] = make_int4(to_fixed(x.x, b.qscale), to_fixed(x.y, b.qscale),
-                                to_fixed(x.z, b.qscale), 0);
-        if (b.xq64)
-            b.xq64[i] = {to_fixed64(x.x, kFixedBits64), to_fixed64(x.y, kFixedBits64),
-                         to_fixed64(x.z, kFixedBits64), 0ll};
-        b.v[i] = v;
-        if (b.accum) {
-            f_store(b, i, 0.0, 0.0, 0.0);
-            if (b.rho) b.rho[i] = 0.0;
-        }
-        const float ddx = f64_to_f32_trunc(x.x) - r.x;
-        const float ddy = f64_to_f32_trunc(x.y) - r.y;
-        const float ddz = f64_to_f32_trunc(x.z) - r.z;
-        d2max = fmaxf(d2max, ddx * ddx + ddy * ddy + ddz * ddz);
-    }
+    // the explicit-Euler test once per pass (an FP64 comparison per atom would
+    // cost the FP64 pipe as much as a multiply-add)
+    const float d2max = s.kick_after != 0.0 ? update_range<true>(b, s, dt, after_pre)
+                                            : update_range<false>(b, s, dt, after_pre);
     const double bm = block_max_nonneg(f32_to_f64(d2max), red);
     if (threadIdx.x == 0) {
         atomicMax(&b.st->max_disp2, (unsigned long long)__double_as_longlong(bm));

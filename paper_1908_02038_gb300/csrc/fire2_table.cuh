@@ -424,12 +424,31 @@ __device__ __forceinline__ void rgl_embed_ff(ffloat r, ffloat& sq, ffloat& fp) {
     fp = {-0.5f * y1.hi, -0.5f * y1.lo};                    // exact scaling
 }
 
+// Whether 2^-60 < d < 2^60, on the integer pipes (positive doubles order
+// like their bit patterns; negative values and NaN fail).
+__device__ __forceinline__ bool ff_range(double d) {
+    const long long bits = __double_as_longlong(d);
+    return bits > 0x3C30000000000000ll && bits < 0x43B0000000000000ll;
+}
+
+// d with ff_range(d) as a float pair without an FP64 instruction: hi is d
+// truncated to 24 significant bits (f64_to_f32_trunc), lo the remaining 29
+// bits of the significand, rem 2^(e - 52), rounded to 24 bits
+// (|d - hi - lo| <= 2^-48 |d|).
+__device__ __forceinline__ ffloat f64_to_ff_int(double d) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(d);
+    const int e = (int)((bits >> 52) & 0x7ffull) - 1023;               // -60 <= e < 60
+    const float scale = __int_as_float((e - 52 + 127) << 23);          // 2^(e - 52)
+    const float lo = __uint2float_rn((unsigned)(bits & 0x1fffffffull)) * scale;
+    return {f64_to_f32_trunc(d), lo};
+}
+
 // The embedding of the double-float form at an FP64 density: sqrt(rho) and
 // F'(rho) in FP64, and F' as the float pair the force pass reads.
 __device__ __forceinline__ void rgl_embed_dd(double rho, double& sq, double& fp, ffloat& fpf) {
-    if (rho > 1e-30 && rho < 1e30) {
+    if (ff_range(rho)) {
         ffloat sqf;
-        rgl_embed_ff(f64_to_ff(rho), sqf, fpf);
+        rgl_embed_ff(f64_to_ff_int(rho), sqf, fpf);
         sq = ff_to_f64(sqf);
         fp = ff_to_f64(fpf);
     } else {
