@@ -457,6 +457,45 @@ __device__ __forceinline__ void cl_combine(ClX& x, const double* v, int nsum, in
     __syncthreads();
 }
 
+// The element-wise step of atoms [lo, hi) of one system (Algorithm 2's half
+// step back and Algorithm 4, as fire_update_atom); returns the largest squared
+// displacement since the last list build.  The tests that hold for the whole
+// pass (explicit Euler's kick, the displacement cap) are taken once, and the
+// FP32 copy of x and the displacement are formed on the integer and FP32
+// pipes: FP64 instructions issue at 1/58 of the FP32 rate on this part.  The
+// copies are truncated (off by < 1 FP32 ulp of the coordinate, the
+// displacement by < 2), far inside the list radius's margin of 1e-3 rc + 8
+// FP32 ulps of the box.
+template <bool F32, bool KICK>
+__device__ __forceinline__ float b_update(const BArgs& a, const BInst& I, int lo, int hi,
+                                          const FireScal& fs, double dt_drift, bool capped,
+                                          bool fp64_phase) {
+    float dmax = 0.f;
+    for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        const long long gi = I.off + i;
+        dvec4 x = a.x[gi], v = a.v[gi];
+        const dvec4 f = a.f[gi];
+        const dvec4 r = a.xref[gi];
+        if (!capped) fire_update_pre(fs, x, v, f);   // capped: done by the first pass
+        fire_update_drift_k<KICK>(fs, dt_drift, x, v, f);
+        a.x[gi] = x;
+        a.v[gi] = v;
+        const float fx = f64_to_f32_trunc(x.x), fy = f64_to_f32_trunc(x.y),
+                    fz = f64_to_f32_trunc(x.z);
+        a.xf[gi] = make_float4(fx, fy, fz, 0.f);
+        if (F32)
+            a.xq[gi] = make_int4(to_fixed(x.x, a.qscale), to_fixed(x.y, a.qscale),
+                                 to_fixed(x.z, a.qscale), 0);
+        if (a.ff && (!F32 || fp64_phase))
+            a.xq64[gi] = {to_fixed64(x.x, kFixedBits64), to_fixed64(x.y, kFixedBits64),
+                          to_fixed64(x.z, kFixedBits64), 0ll};
+        const float ddx = fx - f64_to_f32_trunc(r.x), ddy = fy - f64_to_f32_trunc(r.y),
+                    ddz = fz - f64_to_f32_trunc(r.z);
+        dmax = fmaxf(dmax, ddx * ddx + ddy * ddy + ddz * ddz);
+    }
+    return dmax;
+}
+
 // FP64 reductions of (F, v) of atoms [lo, hi) (combined over the cluster),
 // then Algorithm 2 in thread 0 of every CTA on identical inputs.  Kept out of
 // line: inlined, its FP64 scalar state raised the kernel's register peak and
@@ -475,12 +514,14 @@ __device__ __noinline__ void b_reduce_control(const BArgs& a, const BInst& I, in
             fire_vv_kick(fs, v, f);
             a.v[I.off + i] = v;
         }
-        P += f.x * v.x + f.y * v.y + f.z * v.z;
-        const double q = f.x * f.x + f.y * f.y + f.z * f.z;
+        // products chained into the sums; maxima of non-negative values on
+        // the integer pipes (as in the single-system reductions)
+        P = fma(f.z, v.z, fma(f.y, v.y, fma(f.x, v.x, P)));
+        const double q = fma(f.z, f.z, fma(f.y, f.y, f.x * f.x));
         F2 += q;
-        V2 += v.x * v.x + v.y * v.y + v.z * v.z;
-        fa2 = fmax(fa2, q);
-        fin = fmax(fin, fmax(fabs(f.x), fmax(fabs(f.y), fabs(f.z))));
+        V2 = fma(v.z, v.z, fma(v.y, v.y, fma(v.x, v.x, V2)));
+        fa2 = max_nonneg(fa2, q);
+        fin = max_nonneg(fin, max_nonneg(abs_bits(f.x), max_nonneg(abs_bits(f.y), abs_bits(f.z))));
     }
     double v[8];
     v[0] = bsum(P, red);
@@ -678,29 +719,12 @@ __global__ void __launch_bounds__(MAXT, 1) k_batch_relax(BArgs a) {
                 cl_combine<CL>(X, &vb, 0, 1);
                 dt_drift = fire_capped_dt(fs.dt_cur, a.prm.dmax, X.res[0]);
             }
-            double dmax = 0.0;
-            for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-                const long long gi = I.off + i;
-                dvec4 x = a.x[gi], v = a.v[gi];
-                if (a.prm.dmax > 0.0)
-                    fire_update_drift(fs, dt_drift, x, v, a.f[gi]);
-                else
-                    fire_update_atom(fs, x, v, a.f[gi]);
-                a.x[gi] = x;
-                a.v[gi] = v;
-                a.xf[gi] = make_float4((float)x.x, (float)x.y, (float)x.z, 0.f);
-                if (F32)
-                    a.xq[gi] = make_int4(to_fixed(x.x, a.qscale), to_fixed(x.y, a.qscale),
-                                         to_fixed(x.z, a.qscale), 0);
-                if (a.ff && (!F32 || fp64_phase))
-                    a.xq64[gi] = {to_fixed64(x.x, kFixedBits64), to_fixed64(x.y, kFixedBits64),
-                                  to_fixed64(x.z, kFixedBits64), 0ll};
-                const dvec4 r = a.xref[gi];
-                const double ddx = x.x - r.x, ddy = x.y - r.y, ddz = x.z - r.z;
-                dmax = fmax(dmax, ddx * ddx + ddy * ddy + ddz * ddz);
-            }
+            const bool capped = a.prm.dmax > 0.0;
+            const float dmax = fs.kick_after != 0.0
+                                   ? b_update<F32, true>(a, I, lo, hi, fs, dt_drift, capped, fp64_phase)
+                                   : b_update<F32, false>(a, I, lo, hi, fs, dt_drift, capped, fp64_phase);
             // the exchange's barrier also publishes every CTA's new positions
-            const double db = bmax(dmax, red);
+            const double db = bmax((double)dmax, red);
             cl_combine<CL>(X, &db, 0, 1);
             if (X.res[0] > I.half_skin2) {
                 bst = b_build(a, I, lo, hi, s_count, s_start, s_atoms, red);
