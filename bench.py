@@ -61,6 +61,9 @@ CONFIGS = {
 #   LJ force pass: separation 8; 1/r^2 1; (s/r)^6, ^12: 3; w = 24 eps
 #   (2 s12 - s6) / r^2: 4; pair energy 3; F_i and F_j 12              31
 METHOD_FLOP_PER_PAIR = {"density": 39, "force": 56, "force_lj": 31}
+# the square roots, exponentials and divisions inside those counts, per pair
+TRANSCENDENTALS_PER_PAIR = {"density": {"sqrt": 1, "exp": 2}, "force": {"sqrt": 1, "exp": 2},
+                            "force_lj": {"div": 1}}
 # the kernel each stage runs, per (form, pair evaluation), and the unit it
 # issues on ("fp64": FP64 pipe; "ff": double-float arithmetic on the FP32
 # pipe; "fp32")
@@ -75,11 +78,11 @@ STAGE_KERNELS = {
 # the FP64 table form on a half list runs its pair passes on shared-memory
 # tiles when asked (--tiles on); the library's automatic choice is untiled
 TILED_KERNELS = {"density": ("k_density_tile", "ff"), "force": ("k_force_tile", "ff")}
-# FP32 instructions of one double-float multiply-add (ff_mul 7 + ff_add 11,
-# counted from fire2_table.cuh): the emulation's own ceiling is the FP32 FMA
-# rate / 18 in FP64-equivalent FLOP/s (reported as emulation_efficiency,
-# not as the roofline)
-FF_FP32_PER_FMA = 18
+# FP32 instructions of one double-float multiply-add (ff_madd, counted from
+# fire2_table.cuh): the emulation's own ceiling is the FP32 FMA rate / 15 in
+# FP64-equivalent FLOP/s (reported as emulation_efficiency, not as the
+# roofline)
+FF_FP32_PER_FMA = 15
 # Algorithmic HBM bytes per atom and iteration (x, v read+write, F'(rho)
 # write+read): 112 for RGL, 96 for LJ.
 ALG_BYTES_PER_ATOM_ITER = {"rgl": 112, "lj": 96}
@@ -988,16 +991,20 @@ def roofline_block(fg, args, is_rgl, pair, stages, pairs, workload="rgl1m", n=0)
            "pipe": {"ff": "FP32 (double-float arithmetic)", "fp32": "FP32",
                     "fp64": "FP64"}[unit],
            "flop_per_pair": METHOD_FLOP_PER_PAIR[key], "flop_count": "method (per pass)",
+           "transcendentals_per_pair": TRANSCENDENTALS_PER_PAIR[key],
            "pairs_within_rc": pairs, "stage_ms": stages,
            "fp64_peak": fp64 / 1e12, "fp32_peak": fp32 / 1e12,
            "vs_fp64_peak": achieved / fp64}
     if unit == "ff":
-        # the emulation's own ceiling: one double-float multiply-add is 18 FP32
+        # the emulation's own ceiling: one double-float multiply-add is 15 FP32
         # instructions; not a hardware roof
         out["emulation_efficiency"] = achieved / (fp32 / FF_FP32_PER_FMA)
     ncu = read_ncu(kname, workload)
     out["traffic"] = (ncu or {}).get("dram_bytes")
     out["ncu"] = ncu
+    if ncu and ncu.get("dram_bytes") and ncu.get("time_ms"):
+        # DRAM bytes the kernel moved (ncu) over its ncu duration
+        out["dram_gbs_ncu"] = ncu["dram_bytes"] / (ncu["time_ms"] * 1e-3) / 1e9
     return out
 
 
