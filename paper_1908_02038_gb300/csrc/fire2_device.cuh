@@ -846,8 +846,9 @@ __device__ __forceinline__ void red_range(const Bufs& b, double vvh, RedAcc& acc
 // (warp_sum4), maxima of |F_i|^2 and |F_i,d| (integer maxima); per warp,
 // then over the warps in warp 0, in a fixed order.  sh holds kRedRows x 32
 // doubles.
-__device__ __forceinline__ void red_write(const RedAcc& a, double* sh, double* rpart) {
-    const int nb = gridDim.x;
+// Row k goes to out[k * stride]: the global partials (red_write), or one row
+// in shared memory (stride 1) when a single block reduces every atom.
+__device__ __forceinline__ void red_write_to(const RedAcc& a, double* sh, double* out, int stride) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     double s = warp_sum4(a.P, a.F2, a.V2, a.E);
     double m0 = warp_max_nonneg(a.fa2), m1 = warp_max_nonneg(a.fin);
@@ -864,12 +865,15 @@ __device__ __forceinline__ void red_write(const RedAcc& a, double* sh, double* r
                       in ? sh[5 * 32 + lane] : 0.0);
         m0 = warp_max_nonneg(in ? sh[3 * 32 + lane] : 0.0);
         m1 = warp_max_nonneg(in ? sh[4 * 32 + lane] : 0.0);
-        if ((lane & 7) == 0) rpart[red_row(lane >> 3) * nb + blockIdx.x] = s;
+        if ((lane & 7) == 0) out[red_row(lane >> 3) * stride] = s;
         if (lane == 0) {
-            rpart[3 * nb + blockIdx.x] = m0;
-            rpart[4 * nb + blockIdx.x] = m1;
+            out[3 * stride] = m0;
+            out[4 * stride] = m1;
         }
     }
+}
+__device__ __forceinline__ void red_write(const RedAcc& a, double* sh, double* rpart) {
+    red_write_to(a, sh, rpart + blockIdx.x, gridDim.x);
 }
 
 __device__ __forceinline__ double vv_half_of(const DevState* st) {
@@ -1323,15 +1327,11 @@ __device__ __forceinline__ int energy_partials(const Bufs& b) {
     return b.st->vstate >= 2 ? b.nb_verify : b.ne_dens + b.nb_embed;
 }
 
-// Scalar FIRE 2.0 control (Algorithm 2, fire_control_step), one block: the
-// fixed-order final reductions, the error checks, then the convergence test
-// and the preparation of the next iteration; sets the WHILE condition.
-// The control step proper: every thread of one block enters (the final
-// reductions), thread 0 runs the scalar part.
-__device__ void control_body(const Bufs& b, int mode, cudaGraphConditionalHandle h,
-                             int has_handle, double* sh, int ne) {
-    const CtlSums r = ctl_reduce(b, ne, sh);
-    if (threadIdx.x != 0) return;
+// Scalar FIRE 2.0 control (Algorithm 2, fire_control_step) on the final
+// sums r, by one thread: the error checks, then the convergence test and the
+// preparation of the next iteration; sets the WHILE condition.
+__device__ void control_apply(const Bufs& b, int mode, cudaGraphConditionalHandle h,
+                              int has_handle, const CtlSums& r) {
     const double P = r.P, F2 = r.F2, V2 = r.V2, fa2 = r.fa2, fin = r.fin, E = r.E;
     DevState& s = *b.st;
     s.P = P;
@@ -1393,6 +1393,14 @@ __device__ void control_body(const Bufs& b, int mode, cudaGraphConditionalHandle
     if (has_handle) cudaGraphSetConditional(h, stop ? 0u : 1u);
 }
 
+// The control step of one block: every thread enters (the fixed-order final
+// reductions of the partials), thread 0 runs the scalar part.
+__device__ void control_body(const Bufs& b, int mode, cudaGraphConditionalHandle h,
+                             int has_handle, double* sh, int ne) {
+    const CtlSums r = ctl_reduce(b, ne, sh);
+    if (threadIdx.x == 0) control_apply(b, mode, h, has_handle, r);
+}
+
 // The reductions of (F, v) and the control step in one launch (nb_red
 // blocks): every block writes its partials, and the last
 // block to finish (a ticket counter, reset by that block) runs the control
@@ -1418,6 +1426,17 @@ __global__ void k_reduce_ctl(Bufs b, int mode, cudaGraphConditionalHandle h, int
         red_range<true>(b, vvh, acc);
     else
         red_range<false>(b, 0.0, acc);
+    if (gridDim.x == 1) {
+        // one block (a few hundred atoms): its sums are the final ones, and
+        // the round trip of the partials, the ticket and the second tree of
+        // ctl_reduce (several microseconds of latency) are left out
+        __shared__ double row[kRedRows];
+        red_write_to(acc, sh, row, 1);
+        __syncthreads();
+        if (threadIdx.x == 0)
+            control_apply(b, mode, h, has_handle, {row[0], row[1], row[2], row[3], row[4], row[5]});
+        return;
+    }
     red_write(acc, sh, b.rpart);
     if (threadIdx.x == 0) {
         __threadfence();   // this block's partials before its ticket
