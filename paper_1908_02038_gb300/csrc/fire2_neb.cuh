@@ -205,6 +205,30 @@ __device__ void neb_scalars(const Bufs& b, const NebC& c, double* sums /* n_img 
     }
 }
 
+// This thread's atoms of the projection (grid-stride): F^NEB written over F,
+// then its reductions; VV: velocity Verlet's second half kick first.
+template <bool VV>
+__device__ __forceinline__ void neb_project_range(const Bufs& b, const GeoC& g, const NebC& c,
+                                                  double vvh, RedAcc& acc) {
+    const int total = c.n_img * c.img_n;
+    for (int gi = blockIdx.x * blockDim.x + threadIdx.x; gi < total; gi += gridDim.x * blockDim.x) {
+        const int img = gi / c.img_n, a = gi - img * c.img_n;
+        const double* o = c.coef + 4 * img;
+        const dvec4 r = b.x[gi];
+        dvec4 rm, rp;
+        neb_neighbours(b, c, img, a, rm, rp);
+        double tp[3], tm[3];
+        neb_seps(g, r, rm, rp, tp, tm);
+        dvec4 f = f_load(b, gi);
+        f.x += o[2] * (o[0] * tp[0] + o[1] * tm[0]);
+        f.y += o[2] * (o[0] * tp[1] + o[1] * tm[1]);
+        f.z += o[2] * (o[0] * tp[2] + o[1] * tm[2]);
+        mask_force(b, gi, f);
+        f_store(b, gi, f.x, f.y, f.z);
+        red_atom(b, gi, f, b.v[gi], VV ? vvh : 0.0, acc);
+    }
+}
+
 // grid-stride over all n_img x img_n atoms: F^NEB = mask(F + s t) written
 // over F, then the (F^NEB, v) reductions (with the velocity-Verlet half
 // kick); the last block (ticket) runs the control step on all partials, as
@@ -221,23 +245,12 @@ __global__ void __launch_bounds__(kNebBlock) k_neb_project(Bufs b, GeoC g, NebC 
     }
     const double vvh = vv_half_of(b.st);
     RedAcc acc;
-    const int total = c.n_img * c.img_n;
-    for (int gi = blockIdx.x * blockDim.x + threadIdx.x; gi < total; gi += gridDim.x * blockDim.x) {
-        const int img = gi / c.img_n, a = gi - img * c.img_n;
-        const double* o = c.coef + 4 * img;
-        const dvec4 r = b.x[gi];
-        dvec4 rm, rp;
-        neb_neighbours(b, c, img, a, rm, rp);
-        double tp[3], tm[3];
-        neb_seps(g, r, rm, rp, tp, tm);
-        dvec4 f = f_load(b, gi);
-        f.x += o[2] * (o[0] * tp[0] + o[1] * tm[0]);
-        f.y += o[2] * (o[0] * tp[1] + o[1] * tm[1]);
-        f.z += o[2] * (o[0] * tp[2] + o[1] * tm[2]);
-        mask_force(b, gi, f);
-        f_store(b, gi, f.x, f.y, f.z);
-        red_atom(b, gi, f, b.v[gi], vvh, acc);
-    }
+    // the velocity-Verlet test once per pass, not per atom (an FP64
+    // comparison costs the FP64 pipe as much as a multiply-add)
+    if (vvh != 0.0)
+        neb_project_range<true>(b, g, c, vvh, acc);
+    else
+        neb_project_range<false>(b, g, c, 0.0, acc);
     red_write(acc, red, b.rpart);
     if (threadIdx.x == 0) {
         __threadfence();   // this block's partials before its ticket
