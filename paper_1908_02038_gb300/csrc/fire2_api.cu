@@ -634,11 +634,14 @@ fire_status build_graph(fire_handle* h, const GeoC& g) {
     e = add_conditional(h->cap0, hw, cudaGraphCondTypeWhile, &body);
     // The WHILE body: on large systems one iteration, with the list build and
     // the confirming passes under IF nodes; on small ones kLoopUnroll
-    // iterations with both gated inside their kernels (as in the chunked
-    // mode): there a body launch and an IF node cost more than the gated
-    // launches (graph loop, per iteration: LJ 255 atoms 41.3 -> 33.4 us,
-    // RGL 3,957 atoms 45.7 -> 42.6 us, 31,647 atoms 77.0 -> 75.0 us; 1M atoms
-    // 808.7 against 810.8 us).  Iterations past the stop return at once.
+    // iterations, as a body launch costs more than the launches it saves
+    // (graph loop, per iteration: LJ 255 atoms 41.3 -> 33.4 us, RGL 3,957
+    // atoms 45.7 -> 42.6 us, 31,647 atoms 77.0 -> 75.0 us; 1M atoms 808.7
+    // against 810.8 us).  There each iteration's cell-list chain sits under
+    // an IF node of its own (six gated launches cost more: 3,960 atoms 45.6
+    // -> 42.4 us, 61,875 atoms 105 -> 101 us); an all-pairs build (one
+    // kernel) and the confirming passes stay gated inside their kernels.
+    // Iterations past the stop return at once.
     const int unroll = h->body_iters > 0 ? h->body_iters
                                          : (h->n < kUnrollMaxAtoms ? kLoopUnroll : 1);
     if (e == cudaSuccess && unroll > 1) {
@@ -646,9 +649,29 @@ fire_status build_graph(fire_handle* h, const GeoC& g) {
                                           cudaStreamCaptureModeRelaxed);
         if (e == cudaSuccess) {
             const cudaGraphConditionalHandle none{};
-            for (int u = 0; u < unroll; ++u) {
-                launch_update(h, g, h->cap1, none, 0);
-                launch_build(h, g, 0, h->cap1);
+            for (int u = 0; u < unroll && e == cudaSuccess; ++u) {
+                if (g.brute) {   // one gated list kernel
+                    launch_update(h, g, h->cap1, none, 0);
+                    launch_build(h, g, 0, h->cap1);
+                } else {
+                    // the cell-list chain (six kernels) under an IF node of its
+                    // own, set by this iteration's update
+                    cudaGraphConditionalHandle hb;
+                    e = cudaGraphConditionalHandleCreate(&hb, body, 0, cudaGraphCondAssignDefault);
+                    if (e != cudaSuccess) break;
+                    launch_update(h, g, h->cap1, hb, 1);
+                    cudaGraph_t bb = nullptr;
+                    e = add_conditional(h->cap1, hb, cudaGraphCondTypeIf, &bb);
+                    if (e == cudaSuccess)
+                        e = cudaStreamBeginCaptureToGraph(h->cap2, bb, nullptr, nullptr, 0,
+                                                          cudaStreamCaptureModeRelaxed);
+                    if (e == cudaSuccess) {
+                        launch_build(h, g, 1, h->cap2);
+                        cudaGraph_t bb_out = nullptr;
+                        e = cudaStreamEndCapture(h->cap2, &bb_out);
+                    }
+                    if (e != cudaSuccess) break;
+                }
                 launch_forces(h, g, h->cap1);
                 launch_reduce_control(h, g, h->cap1, CTL_LOOP, hw, 1);
             }
