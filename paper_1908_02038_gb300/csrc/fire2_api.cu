@@ -637,10 +637,10 @@ fire_status build_graph(fire_handle* h, const GeoC& g) {
     // iterations, as a body launch costs more than the launches it saves
     // (graph loop, per iteration: LJ 255 atoms 41.3 -> 33.4 us, RGL 3,957
     // atoms 45.7 -> 42.6 us, 31,647 atoms 77.0 -> 75.0 us; 1M atoms 808.7
-    // against 810.8 us).  There each iteration's cell-list chain sits under
-    // an IF node of its own (six gated launches cost more: 3,960 atoms 45.6
-    // -> 42.4 us, 61,875 atoms 105 -> 101 us); an all-pairs build (one
-    // kernel) and the confirming passes stay gated inside their kernels.
+    // against 810.8 us).  There each iteration's cell-list chain and
+    // confirming passes sit under IF nodes of their own (six gated launches
+    // cost more: 3,960 atoms 45.6 -> 42.4 us, 61,875 atoms 105 -> 101 us);
+    // an all-pairs build (one kernel) stays gated inside its kernel.
     // Iterations past the stop return at once.
     const int unroll = h->body_iters > 0 ? h->body_iters
                                          : (h->n < kUnrollMaxAtoms ? kLoopUnroll : 1);
@@ -649,30 +649,39 @@ fire_status build_graph(fire_handle* h, const GeoC& g) {
                                           cudaStreamCaptureModeRelaxed);
         if (e == cudaSuccess) {
             const cudaGraphConditionalHandle none{};
-            for (int u = 0; u < unroll && e == cudaSuccess; ++u) {
-                if (g.brute) {   // one gated list kernel
-                    launch_update(h, g, h->cap1, none, 0);
-                    launch_build(h, g, 0, h->cap1);
-                } else {
-                    // the cell-list chain (six kernels) under an IF node of its
-                    // own, set by this iteration's update
-                    cudaGraphConditionalHandle hb;
-                    e = cudaGraphConditionalHandleCreate(&hb, body, 0, cudaGraphCondAssignDefault);
-                    if (e != cudaSuccess) break;
-                    launch_update(h, g, h->cap1, hb, 1);
-                    cudaGraph_t bb = nullptr;
-                    e = add_conditional(h->cap1, hb, cudaGraphCondTypeIf, &bb);
-                    if (e == cudaSuccess)
-                        e = cudaStreamBeginCaptureToGraph(h->cap2, bb, nullptr, nullptr, 0,
-                                                          cudaStreamCaptureModeRelaxed);
-                    if (e == cudaSuccess) {
-                        launch_build(h, g, 1, h->cap2);
-                        cudaGraph_t bb_out = nullptr;
-                        e = cudaStreamEndCapture(h->cap2, &bb_out);
-                    }
-                    if (e != cudaSuccess) break;
+            // an IF node of this body whose branch `fill` captures on cap2
+            auto if_node = [&](cudaGraphConditionalHandle hc, auto fill) {
+                cudaGraph_t bb = nullptr;
+                cudaError_t r = add_conditional(h->cap1, hc, cudaGraphCondTypeIf, &bb);
+                if (r == cudaSuccess)
+                    r = cudaStreamBeginCaptureToGraph(h->cap2, bb, nullptr, nullptr, 0,
+                                                      cudaStreamCaptureModeRelaxed);
+                if (r == cudaSuccess) {
+                    fill(h->cap2);
+                    cudaGraph_t bb_out = nullptr;
+                    r = cudaStreamEndCapture(h->cap2, &bb_out);
                 }
-                launch_forces(h, g, h->cap1);
+                return r;
+            };
+            for (int u = 0; u < unroll && e == cudaSuccess; ++u) {
+                // the cell-list chain (six kernels) and the FP64 confirming
+                // passes under IF nodes of their own, set by this iteration's
+                // update; an all-pairs build (one kernel) stays gated
+                cudaGraphConditionalHandle hb = none, hc = none;
+                const int has_b = g.brute ? 0 : 1, has_c = h->verify ? 1 : 0;
+                if (has_b) e = cudaGraphConditionalHandleCreate(&hb, body, 0, cudaGraphCondAssignDefault);
+                if (e == cudaSuccess && has_c)
+                    e = cudaGraphConditionalHandleCreate(&hc, body, 0, cudaGraphCondAssignDefault);
+                if (e != cudaSuccess) break;
+                launch_update(h, g, h->cap1, hb, has_b, hc, has_c);
+                if (has_b)
+                    e = if_node(hb, [&](cudaStream_t s2) { launch_build(h, g, 1, s2); });
+                else
+                    launch_build(h, g, 0, h->cap1);
+                if (e != cudaSuccess) break;
+                launch_forces(h, g, h->cap1, !has_c);
+                if (has_c) e = if_node(hc, [&](cudaStream_t s2) { launch_confirm(h, g, s2); });
+                if (e != cudaSuccess) break;
                 launch_reduce_control(h, g, h->cap1, CTL_LOOP, hw, 1);
             }
             cudaGraph_t body_out = nullptr;
