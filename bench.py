@@ -402,27 +402,35 @@ class _NoClock:
         return None
 
 
-def launches_of(results, is_rgl, fp32, cell_mode, chunked=False, tiled=False):
+def launches_of(results, is_rgl, fp32, cell_mode, chunked=False, tiled=False, body=8, chunk=32):
     """Kernels one relaxation launches: prepare, list build, forces, the
-    reductions with the control step (one launch), finalize once; per loop
-    pass update, forces, reductions + control;
-    the build chain (binning + list) once per rebuild.  The FP32-pair form
-    also has the two FP64 confirming passes: launched once in the set-up,
-    then in the graph loop only in the passes that confirm a stop (an IF
-    node), in the chunked loop with every pass (they return at once unless
-    a stop is being confirmed).  Each confirmation is one more loop pass
-    (force evaluations - iterations - 1)."""
+    reductions with the control step (one launch), finalize once; then the
+    loop passes, launched a whole WHILE body (`body` iterations, graph mode)
+    or a whole chunk (`chunk`, chunked mode) at a time, the passes after the
+    stop returning at once: per pass update, forces, reductions + control.
+    The build chain (binning + list) runs under an IF node once per rebuild
+    in graph mode with cell lists, and is launched with every pass (returning
+    at once unless due) in the chunked mode and for all-pairs lists.  The
+    FP32-pair form also has the two FP64 confirming passes: launched once in
+    the set-up, then in the graph loop only in the passes that confirm a
+    stop (an IF node), in the chunked loop with every pass.  Each
+    confirmation is one more loop pass (force evaluations - iterations - 1)."""
     build_k = (6 + (1 if tiled else 0)) if cell_mode else 1
     force_k = (2 if fp32 else 3) if is_rgl else 1
+    per = chunk if chunked else body
     total = 0
     for rr in results:
         conf = max(0, rr["force_evals"] - rr["iterations"] - 1) if fp32 else 0
         passes = rr["iterations"] + conf
+        launched = -(-passes // per) * per
         total += (1 + build_k + force_k + 1 + 1) + (2 if fp32 else 0)
-        total += (1 + force_k + 1) * passes
+        total += (1 + force_k + 1) * launched
+        if chunked or not cell_mode:
+            total += build_k * launched
+        else:
+            total += build_k * max(0, rr["nbr_builds"] - 1)
         if fp32:
-            total += 2 * (passes if chunked else conf)
-        total += build_k * max(0, rr["nbr_builds"] - 1)
+            total += 2 * (launched if chunked else conf)
     return total
 
 

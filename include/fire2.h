@@ -274,14 +274,13 @@ typedef enum {
 /* Selects the execution mode of later fire_minimize* calls on h.  chunk is,
  * in FIRE_EXEC_CHUNKED, the number of iterations per graph launch (1..4096);
  * in FIRE_EXEC_GRAPH_WHILE, the number of iterations per launch of the WHILE
- * node's body (0..64): 1 puts the list build and the FP64 confirming passes
- * of FP32-pair handles under conditional IF nodes; more puts that many
- * iterations in the body, with the build and the confirming passes launched
- * in every iteration and returning at once unless due (iterations past the
- * stop return at once too); 0 (the default) takes 8 below 262,144 atoms and 1
- * from there.  Results do not depend on the mode.  The paper has no
- * counterpart (it describes the loop of Algorithm 2, not how it is driven).
- * Errors: FIRE_ERR_ARG. */
+ * node's body (0..64), each with its cell-list build and the FP64 confirming
+ * passes of FP32-pair handles under conditional IF nodes (an all-pairs list
+ * build, used for boxes under three cells per axis, is launched in every
+ * iteration and returns at once unless due; iterations past the stop return
+ * at once too); 0 (the default) takes 8.  Results do not depend on the mode.
+ * The paper has no counterpart (it describes the loop of Algorithm 2, not how
+ * it is driven).  Errors: FIRE_ERR_ARG. */
 fire_status fire_set_exec_mode(fire_handle_t* h, int32_t mode, int32_t chunk);
 
 /* Threads per atom in the RGL pair passes of the FP64 table form and of the

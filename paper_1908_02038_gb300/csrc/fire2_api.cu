@@ -602,10 +602,9 @@ cudaError_t add_conditional(cudaStream_t s, cudaGraphConditionalHandle hc,
 //     IF (rebuild): cell binning + neighbour list
 //     forces, reductions, control (sets the WHILE condition)
 //   finalize
-// Small systems: iterations per WHILE-body launch, and the size below which
-// the body holds that many (build_graph; fire_set_exec_mode can set it).
+// Iterations per WHILE-body launch (build_graph; fire_set_exec_mode can set
+// it).
 constexpr int kLoopUnroll = 8;
-constexpr int kUnrollMaxAtoms = 262144;
 constexpr int kMaxBodyIters = 64;
 
 fire_status build_graph(fire_handle* h, const GeoC& g) {
@@ -632,18 +631,17 @@ fire_status build_graph(fire_handle* h, const GeoC& g) {
 
     cudaGraph_t body = nullptr;
     e = add_conditional(h->cap0, hw, cudaGraphCondTypeWhile, &body);
-    // The WHILE body: on large systems one iteration, with the list build and
-    // the confirming passes under IF nodes; on small ones kLoopUnroll
-    // iterations, as a body launch costs more than the launches it saves
-    // (graph loop, per iteration: LJ 255 atoms 41.3 -> 33.4 us, RGL 3,957
-    // atoms 45.7 -> 42.6 us, 31,647 atoms 77.0 -> 75.0 us; 1M atoms 808.7
-    // against 810.8 us).  There each iteration's cell-list chain and
-    // confirming passes sit under IF nodes of their own (six gated launches
-    // cost more: 3,960 atoms 45.6 -> 42.4 us, 61,875 atoms 105 -> 101 us);
-    // an all-pairs build (one kernel) stays gated inside its kernel.
-    // Iterations past the stop return at once.
-    const int unroll = h->body_iters > 0 ? h->body_iters
-                                         : (h->n < kUnrollMaxAtoms ? kLoopUnroll : 1);
+    // The WHILE body: kLoopUnroll iterations, as a body launch costs more
+    // than the launches it saves (graph loop, one against eight iterations
+    // per body: LJ 255 atoms 41.3 -> 33.4 us per iteration, RGL 3,957 atoms
+    // 45.7 -> 42.6 us, 31,647 atoms 77.0 -> 75.0 us; the 1M-atom relaxation
+    // 264.3 -> 262.5 ms).  Each iteration's cell-list chain and confirming
+    // passes sit under IF nodes of their own (six gated launches cost more:
+    // 3,960 atoms 45.6 -> 42.4 us, 61,875 atoms 105 -> 101 us); an
+    // all-pairs build (one kernel) stays gated inside its kernel.  With one
+    // iteration per body (fire_set_exec_mode) the same IF nodes sit in the
+    // body.  Iterations past the stop return at once.
+    const int unroll = h->body_iters > 0 ? h->body_iters : kLoopUnroll;
     if (e == cudaSuccess && unroll > 1) {
         e = cudaStreamBeginCaptureToGraph(h->cap1, body, nullptr, nullptr, 0,
                                           cudaStreamCaptureModeRelaxed);
