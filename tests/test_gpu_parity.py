@@ -337,17 +337,19 @@ def test_chunked_execution_matches_graph_loop():
 @pytest.mark.parametrize("check", [fg.FIRE_FP64_CHECK_CONFIRM, fg.FIRE_FP64_CHECK_FINISH])
 def test_fp32pair_graph_and_chunked_runs_are_identical(check):
     # The FP32-pair passes write whole forces and sum in a fixed order, so the
-    # graph loop with one iteration per body (rebuild decided by the update
-    # kernel's last block, build chain and confirming passes under IF nodes),
-    # with several iterations per body (8 and 3: build and confirming passes
-    # gated in their kernels, iterations past the stop returning at once) and
-    # the chunked loop must follow the same trajectory bit for bit.
+    # graph loop with one iteration per body and with several (8, 3 and the
+    # largest setting, 64: each iteration's build chain and confirming passes
+    # under IF nodes of their own, set by the update kernel's last block;
+    # iterations past the stop returning at once) and the chunked loop (build
+    # and confirming passes gated in their kernels) must follow the same
+    # trajectory bit for bit.
     c = fi.rgl_vacancy_box(ncell=12, seed=14, n_vac=4, sigma=0.1)
     pot = rgl_pot(precision=fg.FIRE_PREC_FP32_PAIR)
     runs = []
     with fg.FireHandle(c.n, fi.CU_MASS, pot, dt_start=fi.CU_DT, confirm64=check) as h:
         for mode, chunk in ((fg.FIRE_EXEC_GRAPH_WHILE, 1), (fg.FIRE_EXEC_GRAPH_WHILE, 8),
-                            (fg.FIRE_EXEC_GRAPH_WHILE, 3), (fg.FIRE_EXEC_CHUNKED, 16)):
+                            (fg.FIRE_EXEC_GRAPH_WHILE, 3), (fg.FIRE_EXEC_GRAPH_WHILE, 64),
+                            (fg.FIRE_EXEC_CHUNKED, 16)):
             h.set_exec_mode(mode, chunk)
             x = c.x.copy()
             runs.append((x, h.minimize(x, c.box, 1e-6, 100000)))
