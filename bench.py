@@ -1111,9 +1111,10 @@ def run_gpu(args):
                            "achieved_gbs": value * alg_b / 1e9, "peak_gbs": hbm,
                            "peak_source": hsrc, "frac": value * alg_b / 1e9 / hbm}
 
-    # end to end through the host-pointer API (H2D of positions, D2H of result)
+    # end to end through the host-pointer API (H2D of positions, D2H of
+    # result), the positions in pinned host memory
     if not args.no_e2e:
-        xh = np.empty_like(cfg.x)
+        xh = torch.empty(cfg.x.shape, dtype=torch.float64, pin_memory=True).numpy()
         t_e2e, it_e2e = 0.0, 0
         for k in range(max(1, args.steps)):
             xh[...] = cfg.x

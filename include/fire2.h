@@ -239,7 +239,9 @@ fire_status fire_init(fire_handle_t** h, const fire_system_t* sys,
 /* Relaxes pos (host, N x 3, in/out) in box[3] until the chosen force norm is
  * below ftol, maxiter iterations are done, or MAXVDOTF triggers (Alg. 2).
  * pos is overwritten only when FIRE_OK is returned; a MAXITER or MAXVDOTF stop
- * is FIRE_OK with out->stop set.  out may not be NULL.
+ * is FIRE_OK with out->stop set.  out may not be NULL.  pos in page-locked
+ * host memory (cudaMallocHost, cudaHostRegister) is copied to and from the
+ * device directly; other host memory takes a staging copy on the way back.
  * Errors: FIRE_ERR_ARG (ftol < 0, maxiter < 0, box), FIRE_ERR_NONFINITE,
  * FIRE_ERR_NBR_OVERFLOW, FIRE_ERR_TIMEOUT, FIRE_ERR_CUDA. */
 fire_status fire_minimize(fire_handle_t* h, double* pos, const double box[3], double ftol,

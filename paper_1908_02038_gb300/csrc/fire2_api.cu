@@ -1455,6 +1455,23 @@ fire_status fire_minimize_dev(fire_handle_t* h, double* d_pos, const double box[
     return FIRE_OK;
 }
 
+// Device-to-host copy of a call's result into the caller's array, with the
+// stream synchronised: straight into page-locked (pinned or registered)
+// memory, through the handle's pinned staging buffer otherwise.
+cudaError_t copy_to_host(fire_handle* h, double* dst, const double* src, size_t bytes,
+                         cudaStream_t s) {
+    cudaPointerAttributes a{};
+    bool locked = false;
+    if (cudaPointerGetAttributes(&a, dst) == cudaSuccess)
+        locked = a.type == cudaMemoryTypeHost;
+    else
+        cudaGetLastError();   // the query's own error: take the staging copy
+    cudaError_t e = cudaMemcpyAsync(locked ? dst : h->h_pos, src, bytes, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess && !locked) std::memcpy(dst, h->h_pos, bytes);
+    return e;
+}
+
 fire_status fire_minimize(fire_handle_t* h, double* pos, const double box[3], double ftol,
                           int64_t maxiter, fire_result_t* out) {
     if (!h) return FIRE_ERR_ARG;
@@ -1473,9 +1490,7 @@ fire_status fire_minimize(fire_handle_t* h, double* pos, const double box[3], do
         if (st != FIRE_OK) return st;
     }
     if (st != FIRE_OK) return st;
-    CK(h, cudaMemcpyAsync(h->h_pos, h->b.pos_io, bytes, cudaMemcpyDeviceToHost, s));
-    CK(h, cudaStreamSynchronize(s));
-    std::memcpy(pos, h->h_pos, bytes);
+    CK(h, copy_to_host(h, pos, h->b.pos_io, bytes, s));
     fill_result(h, out);
     return FIRE_OK;
 }
@@ -1551,9 +1566,7 @@ fire_status fire_energy_forces(fire_handle_t* h, const double* pos, const double
         k_export_forces<<<ceil_div(h->n, kElemBlock), kElemBlock, 0, s>>>(h->b);
         h->b.f_out = nullptr;
         CK(h, cudaGetLastError());
-        CK(h, cudaMemcpyAsync(h->h_pos, h->b.pos_io, bytes, cudaMemcpyDeviceToHost, s));
-        CK(h, cudaStreamSynchronize(s));
-        std::memcpy(forces, h->h_pos, bytes);
+        CK(h, copy_to_host(h, forces, h->b.pos_io, bytes, s));
     }
     if (energy) *energy = h->h_state->energy;
     return FIRE_OK;
