@@ -458,7 +458,7 @@ __device__ __forceinline__ void cl_combine(ClX& x, const double* v, int nsum, in
 }
 
 // The element-wise step of atoms [lo, hi) of one system (Algorithm 2's half
-// step back and Algorithm 4, as fire_update_atom); returns the largest squared
+// step back and Algorithm 4: fire_update_pre, fire_update_drift_k); returns the largest squared
 // displacement since the last list build.  The tests that hold for the whole
 // pass (explicit Euler's kick, the displacement cap) are taken once, and the
 // FP32 copy of x and the displacement are formed on the integer and FP32

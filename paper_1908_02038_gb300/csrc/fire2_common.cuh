@@ -345,7 +345,7 @@ struct FireParamsD {
 };
 
 // Scalar state of Algorithms 1/2 plus the coefficients the next element-wise
-// update applies (see fire_update_atom).
+// update applies (see fire_update_pre and fire_update_drift_k).
 struct FireScal {
     double dt, alpha;
     long long npos, nneg, iter, evals;
@@ -491,7 +491,8 @@ __device__ inline bool fire_control_step(const FireParamsD& p, FireScal& s, doub
 // drift x += dt v, and the explicit-Euler kick with the force at x(t).
 // The part before the drift (everything the maximum-displacement cap needs
 // to know the drift velocity), then the drift with a given dt and the
-// explicit-Euler kick; fire_update_atom chains the two with the FIRE dt.
+// explicit-Euler kick (fire_update_drift_k); the update passes chain the
+// two with the FIRE dt.
 __device__ __forceinline__ void fire_update_pre(const FireScal& s, dvec4& x, dvec4& v,
                                                 const dvec4& f) {
     if (s.lf_init) v = make_dvec4(s.lf_c * f.x, s.lf_c * f.y, s.lf_c * f.z, 0.0);
@@ -535,20 +536,6 @@ __device__ __forceinline__ void fire_update_drift_k(const FireScal& s, double dt
         v.z += s.kick_after * f.z;
     }
 }
-__device__ __forceinline__ void fire_update_drift(const FireScal& s, double dt, dvec4& x,
-                                                  dvec4& v, const dvec4& f) {
-    if (s.kick_after != 0.0)   // explicit Euler only
-        fire_update_drift_k<true>(s, dt, x, v, f);
-    else
-        fire_update_drift_k<false>(s, dt, x, v, f);
-}
-
-__device__ __forceinline__ void fire_update_atom(const FireScal& s, dvec4& x, dvec4& v,
-                                                 const dvec4& f) {
-    fire_update_pre(s, x, v, f);
-    fire_update_drift(s, s.dt_cur, x, v, f);
-}
-
 // Drift timestep under the maximum-displacement cap: dmax / max_i |v_i| when
 // dt max_i |v_i| exceeds dmax > 0, else dt.
 __host__ __device__ inline double fire_capped_dt(double dt, double dmax, double vmax2) {

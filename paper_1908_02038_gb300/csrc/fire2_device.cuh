@@ -345,10 +345,10 @@ struct SkinBuf {
 };
 
 // FP32 positions come from xf (refreshed by k_cell_count) in cell mode and
-// are converted from x in the all-pairs mode (small systems).
+// are converted from x in the all-pairs mode (small systems); the caller
+// passes candidate j's position xj.
 __device__ __forceinline__ void try_add_pair(const Bufs& b, const GeoC& g, int i, float4 xi,
-                                             int j, int& cnt, SkinBuf& sk) {
-    const float4 xj = g.brute ? xf_of(b, j) : b.xf[j];
+                                             int j, float4 xj, int& cnt, SkinBuf& sk) {
     float d[3] = {xj.x - xi.x, xj.y - xi.y, xj.z - xi.z};
     int s[3] = {0, 0, 0};
 #pragma unroll
@@ -390,7 +390,7 @@ __global__ void k_nbr_build(Bufs b, GeoC g, int force) {
     const int img = i / g.img_n;
     if (g.brute) {
         for (int j = img * g.img_n; j < (img + 1) * g.img_n; ++j)
-            if (j != i) try_add_pair(b, g, i, xif, j, cnt, sk);
+            if (j != i) try_add_pair(b, g, i, xif, j, xf_of(b, j), cnt, sk);
     } else {
         const int cx = cell_coord(xi.x, g.Linv[0], g.nc[0], g.per[0]);
         const int cy = cell_coord(xi.y, g.Linv[1], g.nc[1], g.per[1]);
@@ -405,9 +405,25 @@ __global__ void k_nbr_build(Bufs b, GeoC g, int force) {
                     const int az = cell_step(cz, oz, g.nc[2], g.per[2]);
                     if (az < 0) continue;
                     const int c = cell_index(g, img, ax, ay, az);
-                    for (int k = b.cell_start[c]; k < b.cell_start[c + 1]; ++k) {
+                    const int k1 = b.cell_start[c + 1];
+                    int k = b.cell_start[c];
+                    // four candidates' indices and positions loaded before
+                    // any is tested, so that their loads are in flight
+                    // together (the same candidates in the same order)
+                    for (; k + 4 <= k1; k += 4) {
+                        int jj[4];
+                        float4 xx[4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) jj[u] = b.cell_atoms[k + u];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) xx[u] = b.xf[jj[u]];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u)
+                            if (jj[u] != i) try_add_pair(b, g, i, xif, jj[u], xx[u], cnt, sk);
+                    }
+                    for (; k < k1; ++k) {
                         const int j = b.cell_atoms[k];
-                        if (j != i) try_add_pair(b, g, i, xif, j, cnt, sk);
+                        if (j != i) try_add_pair(b, g, i, xif, j, b.xf[j], cnt, sk);
                     }
                 }
             }
