@@ -186,7 +186,9 @@ constexpr int kMaxHvpTpa = 8;   // the Hessian-vector product passes
 // RGL passes gain nothing (3,960 atoms, FP64 form 46.4 / 46.7 / 50.3,
 // FP32-pair form 45.8 / 48.9 / 54.3), while the LJ force pass, whose pair
 // terms are FP64 arithmetic at 1/58 of the FP32 rate, spreads them over more
-// SMs (255 atoms 30.7 / 28.0 / 25.8).
+// SMs (255 atoms 30.7 / 28.0 / 25.8).  Later, with the current passes
+// (us per iteration, 31,680 atoms): FP64 form 71.8 / 71.6 / 86.1 at
+// 4 / 8 / 16, FP32-pair form 64.9 / 58.5 / 64.3 at 2 / 4 / 8.
 int tpa_for(long long n, int sms, int per_sm, int cap = kMaxTpa) {
     int t = 1;
     while (t < cap && n * t < (long long)sms * per_sm) t *= 2;
